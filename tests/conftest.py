@@ -1,0 +1,55 @@
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2201_01446_gb300 import inputs  # noqa: E402
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: longer CPU test")
+
+
+# copper model of the paper's shape (embedding 1-32-64-128, M<=16, fitting
+# 2048-240-240-240-1); std 0.1 is the configured synthetic model, std 1.0 a
+# stress model whose forces are O(0.1-1) eV/A so that error bounds bite
+CU_RC, CU_RCS, CU_SEL = 8.0, 0.5, 256
+CU_SMAX = 1.0 / 1.5
+TABLE_H = 0.01
+
+
+@pytest.fixture(scope="session")
+def model_dir(tmp_path_factory):
+    return tmp_path_factory.mktemp("models")
+
+
+@pytest.fixture(scope="session")
+def cu_model_path(model_dir):
+    p = model_dir / "cu_std0.1.model"
+    inputs.write_seeded_model(p, inputs.COPPER_SPEC, seed=0, std=0.1)
+    return str(p)
+
+
+@pytest.fixture(scope="session")
+def cu_stress_path(model_dir):
+    p = model_dir / "cu_std1.0.model"
+    inputs.write_seeded_model(p, inputs.COPPER_SPEC, seed=0, std=1.0)
+    return str(p)
+
+
+@pytest.fixture(scope="session")
+def water_model_path(model_dir):
+    p = model_dir / "water_std1.0.model"
+    inputs.write_seeded_model(p, inputs.WATER_SPEC, seed=4, std=1.0)
+    return str(p)
+
+
+def rmse(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.sqrt(np.mean((a - b) ** 2))) if a.size else 0.0
