@@ -1,0 +1,209 @@
+/*
+ * dp.h -- C ABI of the GB300 compressed Deep Potential (DP-SE_a) library.
+ *
+ * The library evaluates the energy, forces and virial of the DP-SE_a model of
+ * arXiv 2201.01446 with the embedding net replaced by the paper's fifth-order
+ * piecewise-polynomial table (Sec. 3.2) fused with the R^T G contraction
+ * (Sec. 3.4.1), and integrates velocity-Verlet molecular dynamics (Sec. 5).
+ * Every step runs in the library's own CUDA kernels for sm_103a.
+ *
+ * Conventions for every call:
+ *   - Units: energy eV, length A, time fs, mass amu, force eV/A, virial eV.
+ *   - Arrays are row-major.  coords/forces/velocities are [natoms][3].
+ *     box is [3][3] with the cell vectors as rows; only orthorhombic boxes
+ *     (off-diagonal entries exactly 0) are accepted, else DP_ERR_BOX.
+ *   - Ownership: the caller owns every array it passes.  Inputs are copied
+ *     (host pointers) or read in place on the handle's stream (device
+ *     pointers); the library never frees or keeps caller memory.  The handle
+ *     owns every device buffer it allocates.
+ *   - Errors: each call returns a dp_status and never aborts.  On error the
+ *     outputs are unspecified and the handle stays usable, except after
+ *     DP_ERR_CUDA, which is sticky (destroy the handle).  dp_last_error()
+ *     gives a one-line message.
+ *   - Threads: a handle (and the systems made from it) belongs to one host
+ *     thread at a time.  All device work is ordered on the handle's stream.
+ */
+#ifndef DP_GB300_H
+#define DP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DP_OK = 0,
+  DP_ERR_ARG = 1,           /* bad argument (NULL, negative size, bad type index) */
+  DP_ERR_MODEL = 2,         /* model file missing or malformed */
+  DP_ERR_CUDA = 3,          /* CUDA runtime/kernel failure (sticky) */
+  DP_ERR_OOM = 4,           /* device allocation failed */
+  DP_ERR_SEL_OVERFLOW = 5,  /* more neighbors of one type within rc than sel[t] */
+  DP_ERR_TABLE_RANGE = 6,   /* an s(r) outside the tabulated domain [0, n*h] */
+  DP_ERR_BOX = 7,           /* box not orthorhombic, or an edge shorter than the list cutoff */
+  DP_ERR_TIMEOUT = 8,       /* a bounded wait gave up */
+  DP_ERR_UNIMPLEMENTED = 9, /* option combination not built */
+  DP_ERR_SKIN = 10,         /* an atom moved more than skin/2 between list rebuilds */
+  DP_ERR_NONFINITE = 11     /* a non-finite energy or force was produced */
+} dp_status;
+
+typedef struct dp_handle dp_handle;
+typedef struct dp_system dp_system;
+
+/* Evaluation options.  dp_options_default() fills the defaults in brackets. */
+typedef struct {
+  int tabulated;       /* 1: tabulated embedding fused with the contraction
+                          (Sec. 3.2-3.4) [1]; 0: plain untabulated FP32 net */
+  int fit_precision;   /* fitting-net GEMMs: 0 FP32 CUDA cores [0],
+                          1 BF16 tcgen05 tensor cores with FP32 accumulation,
+                          2 FP32-accurate tcgen05 (split operands) */
+  double table_step;   /* interval h of the table on s (Sec. 3.2) [0.01] */
+  double s_max;        /* table domain is [0, ceil(s_max/h)*h]; [1/1.5] */
+  double skin;         /* neighbor-list buffer for MD (Sec. 5) [2.0 A] */
+  int rebuild_every;   /* MD list rebuild period in steps [10] */
+} dp_options;
+
+/* Thermodynamic record of one MD step (Sec. 5). */
+typedef struct {
+  int64_t step;
+  double kinetic;     /* eV */
+  double potential;   /* eV */
+  double temperature; /* K, 3N-3 degrees of freedom */
+  double pressure;    /* bar, (2 KE + tr(virial)) / (3 V) */
+  double virial[9];   /* eV */
+} dp_thermo;
+
+void dp_options_default(dp_options* opt);
+
+/*
+ * dp_create -- load a model, build its table on the device, bind a stream.
+ *   model_path  DPSEAV01 model file (embedding nets per (centre, neighbor)
+ *               type pair, fitting net per centre type; Sec. 2.1, Eq. 3-5).
+ *   ntypes      number of atom types the caller will use (<= 8).
+ *   type_map    [ntypes] model type of each caller type, or NULL (identity).
+ *   rc, rcs     cutoff radius and start of the smooth switch (Eq. 1), A.
+ *   sel         [model ntypes] maximum neighbors of each type within rc; the
+ *               N_m of Eq. 2 is their sum.
+ *   opt         options or NULL for the defaults.
+ *   stream      cudaStream_t to order all work on, or NULL (legacy default).
+ *   out         receives the handle.
+ * Errors: DP_ERR_ARG, DP_ERR_MODEL, DP_ERR_OOM, DP_ERR_CUDA.
+ */
+dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map, double rc,
+                    double rcs, const int32_t* sel, const dp_options* opt, void* stream,
+                    dp_handle** out);
+
+/* Destroy a handle and free its device memory.  NULL is a no-op. */
+void dp_destroy(dp_handle* h);
+
+/* Last error message of the handle (never NULL; "" after success).  With
+ * h == NULL: the message of the last failed dp_create on this thread. */
+const char* dp_last_error(const dp_handle* h);
+
+/* Change the stream the handle orders its work on (cudaStream_t). */
+dp_status dp_set_stream(dp_handle* h, void* stream);
+
+/*
+ * dp_compute -- one energy/force/virial evaluation (Sec. 2.1):
+ *   E = sum_i E_i,  F_i = -dE/dr_i,  virial = -sum_ij r_ij (x) dE_i/dr_ij.
+ *   natoms      >= 0.  coords [natoms][3] (A, need not be wrapped),
+ *   types       [natoms] caller types, box [3][3].
+ *   device_ptrs 0: all array arguments are host memory (the call copies in
+ *               and out and returns after the results are on the host);
+ *               1: all are device memory (the call is asynchronous on the
+ *               handle's stream except for the status check at its end).
+ *   energy      [1] eV; forces [natoms][3]; virial [9] (row-major, symmetric);
+ *   atom_energy [natoms] or NULL.
+ * The neighbor list is built fresh with cutoff rc.
+ * Errors: DP_ERR_ARG, DP_ERR_BOX, DP_ERR_SEL_OVERFLOW, DP_ERR_TABLE_RANGE,
+ *         DP_ERR_NONFINITE, DP_ERR_OOM, DP_ERR_CUDA.
+ */
+dp_status dp_compute(dp_handle* h, int64_t natoms, const double* coords, const int32_t* types,
+                     const double* box, int device_ptrs, double* energy, double* forces,
+                     double* virial, double* atom_energy);
+
+/*
+ * dp_system_create -- a device-resident MD system (positions, velocities,
+ * forces in FP64; neighbor list with skin; CUDA graph of the step block).
+ *   x, v [natoms][3] (A, A/fs), types [natoms], mass_of_type [ntypes] (amu),
+ *   box [3][3]; device_ptrs as in dp_compute.  Copies everything in.
+ */
+dp_status dp_system_create(dp_handle* h, int64_t natoms, const double* x, const double* v,
+                           const int32_t* types, const double* mass_of_type, const double* box,
+                           int device_ptrs, dp_system** out);
+void dp_system_destroy(dp_system* s);
+
+/* Copy x, v, f (any may be NULL) out of the system; device_ptrs as above.
+ * Positions come back wrapped into the box as of the last list rebuild. */
+dp_status dp_system_get(dp_system* s, double* x, double* v, double* f, int device_ptrs);
+
+/* Current step count of the system. */
+int64_t dp_system_step(const dp_system* s);
+
+/*
+ * dp_md_step -- nsteps velocity-Verlet steps of dt_fs (Sec. 5):
+ *   v += dt/2 F/m;  x += dt v;  (list rebuild when step % rebuild_every == 0);
+ *   F = -grad E;  v += dt/2 F/m.
+ * The rebuild schedule is keyed to the absolute step count, so a run split
+ * into several calls (or saved and loaded) follows the same schedule.
+ * thermo_out: NULL, or [nsteps] records (one per step, after the step).
+ * Errors: as dp_compute, plus DP_ERR_SKIN.
+ */
+dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_thermo* thermo_out);
+
+/* Save / load the MD state (x, v, types, masses, box, step) to a file. */
+dp_status dp_state_save(dp_system* s, const char* path);
+dp_status dp_state_load(dp_handle* h, const char* path, dp_system** out);
+
+/* ---------------------------------------------------------------------------
+ * Inspection calls used by the parity tests.
+ * ------------------------------------------------------------------------- */
+
+/* Neighbor pairs with |r_ij| < rlist as rows (i, j, n0, n1, n2), where n is the
+ * periodic image: r_ij = x_j + n*L - x_i with x wrapped into [0, L).  Host
+ * arrays.  Writes at most cap rows (in the library's list order, not sorted)
+ * and returns the total count in *count. */
+dp_status dp_neighbor_pairs(dp_handle* h, int64_t natoms, const double* coords,
+                            const double* box, double rlist, int64_t cap, int32_t* out5,
+                            int64_t* count);
+
+/* The device table of model type pair (ti, tj) as FP32 [n][6][M]: on
+ * interval k the embedding row is sum_q c[k][q][:] u^q with the normalised
+ * local variable u = s/h - k in [0, 1), i.e. c[k][q] = a_q h^q for the
+ * paper's coefficients a_q of the local variable s - k*h (Sec. 3.2).
+ * *n receives the interval count (call with out == NULL to query it). */
+dp_status dp_table_coeffs(dp_handle* h, int ti, int tj, float* out, int32_t* n);
+
+/* Per-atom T = R^T G / N_m, FP32 [natoms][4][M] (host arrays). */
+dp_status dp_descriptor(dp_handle* h, int64_t natoms, const double* coords,
+                        const int32_t* types, const double* box, float* T_out);
+
+/* ---------------------------------------------------------------------------
+ * Profiling: per-phase device time measured with CUDA events recorded on the
+ * handle's stream around each phase's kernels.
+ * ------------------------------------------------------------------------- */
+#define DP_NPHASE 5
+/* phases: 0 neighbor-list build (cell binning, lists), 1 environment matrix +
+ * tabulated embedding + contraction (forward), 2 descriptor + fitting net
+ * forward and backward, 3 tabulated contraction backward + forces + virial,
+ * 4 integration, force finalisation and reductions */
+
+/* enable = 1: reset and start recording; 0: stop. */
+dp_status dp_profile(dp_handle* h, int enable);
+/* ms[DP_NPHASE]: summed device time per phase since the last reset;
+ * launches[DP_NPHASE]: number of timed phase executions.  Synchronises the
+ * handle's stream. */
+dp_status dp_profile_read(dp_handle* h, double* ms, int64_t* launches);
+
+/* Counters of the last evaluation of a system (s != NULL) or of the last
+ * dp_compute (s == NULL): out[0] atoms, [1] list capacity per atom, [2]
+ * longest list, [3] pairs within rc seen by the last forward pass, [4] cells. */
+dp_status dp_stats(dp_handle* h, const dp_system* s, int64_t* out);
+
+/* Library build string (architecture, options compiled in). */
+const char* dp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

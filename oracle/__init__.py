@@ -65,7 +65,7 @@ def lib():
             "orc_atom_descriptor": (i, [p, p, d, d, i32p, i64, dp, i32p, dp, i64, dp, dp]),
             "orc_eval_subset": (i, [p, p, d, d, i32p, i64, dp, i32p, dp, i64, i64p, dp,
                                     i64, i64p, dp]),
-            "orc_md": (i, [p, p, d, d, i32p, i64, dp, dp, dp, i32p, dp, dp, d, i, dp]),
+            "orc_md": (i, [p, p, d, d, i32p, i64, dp, dp, dp, i, i32p, dp, dp, d, i, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -268,17 +268,19 @@ def eval_subset(model: Model, table, rc, rcs, sel, x, types, box, idx_e, idx_f):
     return e_out[:len(idx_e)], f_out[:len(idx_f)]
 
 
-def md(model: Model, table, rc, rcs, sel, x, v, types, masses, box, dt, nsteps):
-    """Velocity-Verlet NVE; returns (x, v, f, thermo[nsteps+1, 4])."""
+def md(model: Model, table, rc, rcs, sel, x, v, types, masses, box, dt, nsteps, f=None):
+    """Velocity-Verlet NVE; returns (x, v, f, thermo[nsteps+1, 4]).  Passing
+    the forces f at x skips the initial force evaluation."""
     x, v, box = _f64(x).copy(), _f64(v).copy(), _f64(box)
     types = np.ascontiguousarray(types, np.int32)
     masses = _f64(masses)
     sel = _sel(sel, model.ntypes)
-    f = np.zeros_like(x)
+    f_valid = f is not None
+    f = _f64(f).copy() if f_valid else np.zeros_like(x)
     th = np.zeros((nsteps + 1, 4))
     code = lib().orc_md(model.h, table.handle if table is not None else None, float(rc),
-                        float(rcs), _i32(sel), len(x), _d(x), _d(v), _d(f), _i32(types),
-                        _d(masses), _d(box), float(dt), int(nsteps), _d(th))
+                        float(rcs), _i32(sel), len(x), _d(x), _d(v), _d(f), int(f_valid),
+                        _i32(types), _d(masses), _d(box), float(dt), int(nsteps), _d(th))
     if code:
         raise OracleError(code)
     return x, v, f, th

@@ -412,8 +412,10 @@ int orc_table_coeffs(const orc_table* t, int ti, int tj, double* out) {
 
 int orc_table_eval(const orc_table* t, int ti, int tj, double s, double* g, double* dg) {
   /* interval k owns [x_k, x_{k+1}); local variable u = s - x_k (a reading:
-   * the paper writes global powers of x, which is the same polynomial) */
-  int out = (s < 0.0 || s > t->n * t->h) ? 1 : 0;
+   * the paper writes global powers of x, which is the same polynomial).
+   * s = sw(r)/r >= 0; a rounding-level negative s next to rc evaluates the
+   * first interval, so only s beyond the last node is out of range */
+  int out = (s > t->n * t->h) ? 1 : 0;
   double fk = floor(s / t->h);
   int k = (int)fk;
   if (fk < 0) k = 0;
@@ -1080,13 +1082,14 @@ static void thermo_row(int64_t n, const double* v, const int32_t* types, const d
 }
 
 int orc_md(const orc_model* m, const orc_table* table, double rc, double rcs,
-           const int32_t* sel, int64_t n, double* x, double* v, double* f,
+           const int32_t* sel, int64_t n, double* x, double* v, double* f, int f_valid,
            const int32_t* types, const double* mass_of_type, const double* box,
            double dt, int nsteps, double* thermo) {
   if (!m || !x || !v || !f || !mass_of_type || nsteps < 0) return ORC_ERR_ARG;
   double vol = box[0] * box[4] * box[8];
-  double pe, vir[9];
-  int e = orc_eval(m, table, rc, rcs, sel, n, x, types, box, &pe, NULL, f, vir, NULL);
+  double pe = 0.0, vir[9] = {0};
+  int e = 0;
+  if (!f_valid) e = orc_eval(m, table, rc, rcs, sel, n, x, types, box, &pe, NULL, f, vir, NULL);
   if (e) return e;
   if (thermo) thermo_row(n, v, types, mass_of_type, pe, vir, vol, thermo);
   for (int s = 0; s < nsteps; ++s) {

@@ -69,7 +69,7 @@ void orc_table_free(orc_table* t);
 int orc_table_dims(const orc_table* t, int32_t* n, double* h);
 /* coefficients of pair (ti,tj): out[n][6][M], local variable t = s - k*h */
 int orc_table_coeffs(const orc_table* t, int ti, int tj, double* out);
-/* evaluate the table: g[M], dg[M]; returns 1 when s is outside [0, n*h] */
+/* evaluate the table: g[M], dg[M]; returns 1 when s > n*h */
 int orc_table_eval(const orc_table* t, int ti, int tj, double s, double* g, double* dg);
 /* quintic on [0,h] matching (y,y',y'') at both ends: a[0..5] */
 void orc_hermite5(const double* y0, const double* y1, double h, double* a);
@@ -106,10 +106,12 @@ int orc_eval_subset(const orc_model* m, const orc_table* table, double rc, doubl
                     int64_t nf, const int64_t* idx_f, double* f_out);
 
 /* Velocity-Verlet NVE (Sec. 5): nsteps steps of dt fs.  x, v (A, A/fs) are
- * updated in place; f receives the final forces.  thermo (may be NULL)
- * receives (nsteps+1) rows of (KE eV, PE eV, T K, P bar). */
+ * updated in place; f receives the final forces.  With f_valid != 0, f on
+ * entry already holds the forces at x and the initial evaluation is skipped.
+ * thermo (may be NULL) receives (nsteps+1) rows of (KE eV, PE eV, T K, P bar)
+ * (row 0 has PE = 0 and a kinetic-only pressure when f_valid != 0). */
 int orc_md(const orc_model* m, const orc_table* table, double rc, double rcs,
-           const int32_t* sel, int64_t n, double* x, double* v, double* f,
+           const int32_t* sel, int64_t n, double* x, double* v, double* f, int f_valid,
            const int32_t* types, const double* mass_of_type, const double* box,
            double dt, int nsteps, double* thermo);
 

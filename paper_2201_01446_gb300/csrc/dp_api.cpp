@@ -1,0 +1,1118 @@
+// C-ABI runtime: model loading, device buffers, neighbor-list management,
+// the evaluation pipeline and velocity-Verlet MD.  All arithmetic of the
+// method runs in the CUDA kernels; this file only sequences them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dp_internal.h"
+
+namespace {
+
+constexpr double kAcc = 9.648533212e-3;  // (eV/A/amu) -> A/fs^2
+constexpr double kKb = 8.617333262e-5;    // eV/K
+constexpr double kEvA3Bar = 1.602176634e6;
+
+// ------------------------------------------------------------------ fault injection
+// DP_FAULT=alloc:N makes the N-th device allocation of the process fail
+// (host-side injection; nothing on the GPU is disturbed).
+long g_alloc_count = 0;
+long g_alloc_fail_at = -1;
+bool g_fault_parsed = false;
+
+void parse_fault() {
+  if (g_fault_parsed) return;
+  g_fault_parsed = true;
+  const char* s = std::getenv("DP_FAULT");
+  if (s && std::strncmp(s, "alloc:", 6) == 0) g_alloc_fail_at = std::atol(s + 6);
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (bytes <= b.bytes) return cudaSuccess;
+  parse_fault();
+  ++g_alloc_count;
+  if (g_alloc_fail_at > 0 && g_alloc_count == g_alloc_fail_at) return cudaErrorMemoryAllocation;
+  b.release();
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e == cudaSuccess) {
+    b.bytes = bytes;
+  } else {
+    b.p = nullptr;
+    cudaGetLastError();  // clear the non-sticky allocation error
+  }
+  return e;
+}
+
+template <class T>
+T* P(DevBuf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+struct Work {
+  int64_t n = 0;
+  int cap = 0;
+  double rlist = 0.0;
+  CellGeom geom{};
+  DevBuf x, xref, types, types_in, cellc, cell_count, cell_fill, cell_start, cell_tmp, cell_atoms,
+      off, nlist, nn, T, dT, e_atom, ffix, f, vir_part, red_part, red_out, idx, ke, pairs;
+  std::vector<int64_t> type_count, type_off;  // atoms per model type, offsets into idx
+  bool have_idx = false;
+};
+
+}  // namespace
+
+struct dp_handle {
+  cudaStream_t st = nullptr;
+  std::string err;
+  bool dead = false;
+  int ntypes_user = 0;
+  int type_map[DP_MAXT] = {0};
+  double rc = 0.0, rcs = 0.0;
+  int sel[DP_MAXT] = {0};
+  int Nm = 0;
+  dp_options opt{};
+  // model
+  int ntypes = 0, n_emb = 0, emb_w[6] = {0}, M = 0, m_lt = 0, din = 0, n_fit = 0;
+  int fit_w[DP_MAXFIT] = {0};
+  DevBuf emb64, emb_off, table, fit32, sel_dev, map_dev, status;
+  int n_int = 0;
+  double h = 0.0;
+  FitNet nets[DP_MAXT];
+  float b_out[DP_MAXT] = {0};
+  DevBuf fitbuf;
+  FitScratch fs{};
+  int32_t* status_host = nullptr;
+  Work w;
+  // profiling: event pairs recorded around each phase on the handle's stream
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[DP_NPHASE];
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pool;
+  ~dp_handle() {
+    for (auto& v : prof_ev)
+      for (auto& e : v) prof_pool.push_back(e);
+    for (auto& e : prof_pool) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+  }
+};
+
+struct dp_system {
+  dp_handle* h = nullptr;
+  Work w;
+  DevBuf v, mass, inv_mass_acc, thermo;
+  std::vector<int32_t> types_user;
+  std::vector<double> mass_user;
+  double box[9] = {0};
+  int64_t step = 0;
+  bool f_valid = false;
+};
+
+namespace {
+
+// message of the last failed dp_create on this thread (dp_last_error(NULL))
+thread_local std::string g_create_err;
+
+dp_status fail(dp_handle* h, dp_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+dp_status cuda_fail(dp_handle* h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return fail(h, DP_ERR_OOM, m);
+  // errors from kernels (illegal address, launch failure, ...) poison the context
+  if (e != cudaErrorInvalidValue && e != cudaErrorInvalidConfiguration) h->dead = true;
+  return fail(h, DP_ERR_CUDA, m);
+}
+
+#define CK(call, where)                                 \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+// Records a CUDA event pair around a phase when profiling is on.
+struct Phase {
+  dp_handle* h;
+  int ph;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  Phase(dp_handle* h_, int ph_) : h(h_), ph(ph_) {
+    if (!h->prof) return;
+    if (h->prof_pool.empty()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return;
+      if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return;
+      }
+      h->prof_pool.push_back({a, b});
+    }
+    ev = h->prof_pool.back();
+    h->prof_pool.pop_back();
+    cudaEventRecord(ev.first, h->st);
+  }
+  void end() {
+    if (!ev.first) return;
+    cudaEventRecord(ev.second, h->st);
+    h->prof_ev[ph].push_back(ev);
+    ev.first = nullptr;
+  }
+  ~Phase() { end(); }
+};
+
+#define CKS(call)                          \
+  do {                                     \
+    dp_status s_ = (call);                 \
+    if (s_ != DP_OK) return s_;            \
+  } while (0)
+
+// ------------------------------------------------------------------ model file
+struct HostModel {
+  int ntypes = 0, n_emb = 0, emb_w[6] = {0}, m_lt = 0, n_fit = 0, fit_w[DP_MAXFIT] = {0};
+  std::vector<double> data;
+  std::vector<int64_t> emb_off;   // per (pair, layer): offset of W in data
+  std::vector<int64_t> fit_off;   // per (type, layer): offset of W; then w_out, b_out
+};
+
+bool read_model(const char* path, HostModel& m, std::string& why) {
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    why = std::string("cannot open model file ") + path;
+    return false;
+  }
+  auto rd = [&](void* p, size_t sz, size_t cnt) { return std::fread(p, sz, cnt, f) == cnt; };
+  char magic[8];
+  int32_t v[2];
+  bool ok = rd(magic, 1, 8) && std::memcmp(magic, "DPSEAV01", 8) == 0 && rd(v, 4, 2);
+  int nint = 2;
+  if (ok) {
+    m.ntypes = v[0];
+    m.n_emb = v[1];
+    ok = m.ntypes >= 1 && m.ntypes <= DP_MAXT && m.n_emb >= 1 && m.n_emb <= 6;
+  }
+  if (ok) ok = rd(m.emb_w, 4, m.n_emb) && rd(v, 4, 2);
+  if (ok) {
+    nint += m.n_emb + 2;
+    m.m_lt = v[0];
+    m.n_fit = v[1];
+    ok = m.n_fit >= 1 && m.n_fit <= DP_MAXFIT;
+  }
+  if (ok) {
+    ok = rd(m.fit_w, 4, m.n_fit);
+    nint += m.n_fit;
+  }
+  if (ok && nint % 2) ok = rd(v, 4, 1);
+  if (ok)
+    for (int k = 1; k < m.n_emb; ++k) ok = ok && m.emb_w[k] == 2 * m.emb_w[k - 1];
+  const int M = ok ? m.emb_w[m.n_emb - 1] : 0;
+  if (ok) ok = m.m_lt >= 1 && m.m_lt <= M;
+  if (!ok) {
+    std::fclose(f);
+    why = "malformed model header";
+    return false;
+  }
+  const int din = M * m.m_lt;
+  int64_t tot = 0;
+  const int np = m.ntypes * m.ntypes;
+  for (int p = 0; p < np; ++p) {
+    int prev = 1;
+    for (int k = 0; k < m.n_emb; ++k) {
+      m.emb_off.push_back(tot);
+      tot += (int64_t)prev * m.emb_w[k] + m.emb_w[k];
+      prev = m.emb_w[k];
+    }
+  }
+  for (int t = 0; t < m.ntypes; ++t) {
+    int prev = din;
+    for (int k = 0; k < m.n_fit; ++k) {
+      m.fit_off.push_back(tot);
+      tot += (int64_t)prev * m.fit_w[k] + m.fit_w[k];
+      prev = m.fit_w[k];
+    }
+    m.fit_off.push_back(tot);  // w_out then b_out
+    tot += prev + 1;
+  }
+  m.data.resize(tot);
+  ok = rd(m.data.data(), sizeof(double), (size_t)tot);
+  char extra;
+  if (ok && std::fread(&extra, 1, 1, f) != 0) ok = false;
+  std::fclose(f);
+  if (!ok) why = "model file size does not match its header";
+  return ok;
+}
+
+// ------------------------------------------------------------------ helpers
+dp_status box_lengths(dp_handle* h, const double* box, double* L) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      if (a != b && box[a * 3 + b] != 0.0)
+        return fail(h, DP_ERR_BOX, "only orthorhombic boxes are supported");
+  for (int a = 0; a < 3; ++a) {
+    L[a] = box[a * 4];
+    if (!(L[a] > 0.0) || !std::isfinite(L[a])) return fail(h, DP_ERR_BOX, "box edge must be > 0");
+  }
+  return DP_OK;
+}
+
+EnvParams env_params(const dp_handle* h) {
+  EnvParams ep{};
+  ep.rc2 = (float)(h->rc * h->rc);
+  ep.rc = (float)h->rc;
+  ep.rcs = (float)h->rcs;
+  ep.inv_w = (float)(1.0 / (h->rc - h->rcs));
+  ep.inv_h = (float)(1.0 / h->h);
+  ep.h = (float)h->h;
+  ep.smax = (float)(h->n_int * h->h);
+  ep.inv_nm = (float)(1.0 / h->Nm);
+  ep.n_int = h->n_int;
+  ep.M = h->M;
+  ep.ntypes = h->ntypes;
+  return ep;
+}
+
+dp_status read_status(dp_handle* h) {
+  CK(cudaMemcpyAsync(h->status_host, P<int32_t>(h->status), sizeof(int32_t) * ST_NWORDS,
+                     cudaMemcpyDeviceToHost, h->st),
+     "status copy");
+  CK(cudaStreamSynchronize(h->st), "device execution");
+  return DP_OK;
+}
+
+dp_status clear_status(dp_handle* h) {
+  CK(cudaMemsetAsync(h->status.p, 0, sizeof(int32_t) * ST_NWORDS, h->st), "status clear");
+  return DP_OK;
+}
+
+dp_status status_errors(dp_handle* h) {
+  const int32_t* s = h->status_host;
+  char buf[160];
+  if (s[ST_BADTYPE]) {
+    std::snprintf(buf, sizeof buf, "%d atoms have a type outside [0, %d)", s[ST_BADTYPE],
+                  h->ntypes_user);
+    return fail(h, DP_ERR_ARG, buf);
+  }
+  if (s[ST_SEL]) {
+    std::snprintf(buf, sizeof buf, "%d atoms have more neighbors of a type within rc than sel",
+                  s[ST_SEL]);
+    return fail(h, DP_ERR_SEL_OVERFLOW, buf);
+  }
+  if (s[ST_SKIN]) {
+    std::snprintf(buf, sizeof buf, "%d atoms moved more than skin/2 between rebuilds", s[ST_SKIN]);
+    return fail(h, DP_ERR_SKIN, buf);
+  }
+  if (s[ST_RANGE]) {
+    std::snprintf(buf, sizeof buf, "%d pairs have s outside the table domain [0, %g]", s[ST_RANGE],
+                  h->n_int * h->h);
+    return fail(h, DP_ERR_TABLE_RANGE, buf);
+  }
+  if (s[ST_NONFINITE]) {
+    std::snprintf(buf, sizeof buf, "%d non-finite energies or pair forces", s[ST_NONFINITE]);
+    return fail(h, DP_ERR_NONFINITE, buf);
+  }
+  return DP_OK;
+}
+
+// per-atom buffers of a work area
+dp_status ensure_atoms(dp_handle* h, Work& w, int64_t n) {
+  const size_t N = (size_t)std::max<int64_t>(n, 1);
+  CK(ensure(w.x, N * 3 * sizeof(double)), "alloc x");
+  CK(ensure(w.xref, N * 3 * sizeof(double)), "alloc xref");
+  CK(ensure(w.types, N * sizeof(int32_t)), "alloc types");
+  CK(ensure(w.types_in, N * sizeof(int32_t)), "alloc types");
+  CK(ensure(w.cellc, N * sizeof(int32_t)), "alloc cells");
+  CK(ensure(w.cell_tmp, N * sizeof(int32_t)), "alloc cells");
+  CK(ensure(w.cell_atoms, N * sizeof(int32_t)), "alloc cells");
+  CK(ensure(w.off, N * sizeof(float4)), "alloc offsets");
+  CK(ensure(w.nn, N * sizeof(int32_t)), "alloc nn");
+  CK(ensure(w.T, N * 4 * h->M * sizeof(float)), "alloc T");
+  CK(ensure(w.dT, N * 4 * h->M * sizeof(float)), "alloc dT");
+  CK(ensure(w.e_atom, N * sizeof(double)), "alloc e");
+  CK(ensure(w.ke, N * sizeof(double)), "alloc ke");
+  CK(ensure(w.ffix, N * 3 * sizeof(unsigned long long)), "alloc f");
+  CK(ensure(w.f, N * 3 * sizeof(double)), "alloc f");
+  CK(ensure(w.idx, N * sizeof(int32_t)), "alloc idx");
+  CK(ensure(w.vir_part, (size_t)tab_kernel_slots(n) * 9 * sizeof(double)), "alloc virial");
+  CK(ensure(w.red_part, (size_t)sum_rows_part_size(n, 9) * sizeof(double)), "alloc red");
+  CK(ensure(w.red_out, 32 * sizeof(double)), "alloc red");
+  CK(ensure(w.pairs, sizeof(unsigned long long)), "alloc counters");
+  w.n = n;
+  return DP_OK;
+}
+
+// per-type index lists for the fitting stage (stable: ascending atom index)
+dp_status set_types(dp_handle* h, Work& w, const int32_t* types_user_host) {
+  const int64_t n = w.n;
+  w.type_count.assign(h->ntypes, 0);
+  w.type_off.assign(h->ntypes + 1, 0);
+  std::vector<int32_t> mt(n);
+  for (int64_t i = 0; i < n; ++i) {
+    int t = types_user_host[i];
+    if (t < 0 || t >= h->ntypes_user) return fail(h, DP_ERR_ARG, "atom type out of range");
+    mt[i] = h->type_map[t];
+    w.type_count[mt[i]]++;
+  }
+  for (int t = 0; t < h->ntypes; ++t) w.type_off[t + 1] = w.type_off[t] + w.type_count[t];
+  w.have_idx = h->ntypes > 1;
+  if (n > 0) {
+    CK(cudaMemcpyAsync(w.types.p, mt.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->st),
+       "types upload");
+    if (w.have_idx) {
+      std::vector<int32_t> idx(n);
+      std::vector<int64_t> fill(w.type_off.begin(), w.type_off.end() - 1);
+      for (int64_t i = 0; i < n; ++i) idx[fill[mt[i]]++] = (int32_t)i;
+      CK(cudaMemcpyAsync(w.idx.p, idx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->st),
+         "idx upload");
+    }
+    CK(cudaStreamSynchronize(h->st), "types upload");
+  }
+  return DP_OK;
+}
+
+dp_status ensure_fit_scratch(dp_handle* h, int64_t rows_needed) {
+  int64_t rows = std::min<int64_t>(std::max<int64_t>(rows_needed, 1), 131072);
+  if (rows <= h->fs.rows) return DP_OK;
+  int wmax = 0;
+  for (int k = 0; k < h->n_fit; ++k) wmax = std::max(wmax, h->fit_w[k]);
+  size_t per = 2 * (size_t)h->din + 3 * (size_t)wmax;
+  for (int k = 0; k < h->n_fit; ++k) per += 2 * (size_t)h->fit_w[k];
+  CK(ensure(h->fitbuf, per * rows * sizeof(float)), "alloc fitting scratch");
+  float* q = P<float>(h->fitbuf);
+  FitScratch& s = h->fs;
+  s.rows = rows;
+  s.D = q;
+  q += rows * h->din;
+  s.dD = q;
+  q += rows * h->din;
+  for (int k = 0; k < h->n_fit; ++k) {
+    s.t[k] = q;
+    q += rows * h->fit_w[k];
+    s.z[k] = q;
+    q += rows * h->fit_w[k];
+  }
+  s.gz = q;
+  q += rows * wmax;
+  s.gp = q;
+  q += rows * wmax;
+  s.gz2 = q;
+  return DP_OK;
+}
+
+// Wrap positions, bin them into cells of edge >= rlist, sort the cells and
+// build the lists (growing the capacity until every list fits).
+dp_status rebuild(dp_handle* h, Work& w, const double* L, double rlist) {
+  CellGeom g{};
+  long long ncell = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (L[a] < rlist)
+      return fail(h, DP_ERR_BOX, "a box edge is shorter than the neighbor-list cutoff");
+    g.L[a] = L[a];
+    g.nc[a] = std::max(1, (int)std::floor(L[a] / rlist));
+    g.edge[a] = L[a] / g.nc[a];
+    g.edgef[a] = (float)g.edge[a];
+    ncell *= g.nc[a];
+  }
+  if (ncell > (1LL << 30)) return fail(h, DP_ERR_BOX, "too many cells");
+  g.ncell = ncell;
+  w.geom = g;
+  w.rlist = rlist;
+  const int64_t n = w.n;
+  if (n == 0) return DP_OK;
+  Phase ph(h, 0);
+  CK(ensure(w.cell_count, (ncell + 1) * sizeof(int32_t)), "alloc cells");
+  CK(ensure(w.cell_fill, (ncell + 1) * sizeof(int32_t)), "alloc cells");
+  CK(ensure(w.cell_start, (ncell + 1) * sizeof(int32_t)), "alloc cells");
+  CK(cudaMemsetAsync(w.cell_count.p, 0, (ncell + 1) * sizeof(int32_t), h->st), "memset");
+  CK(cudaMemsetAsync(w.cell_fill.p, 0, (ncell + 1) * sizeof(int32_t), h->st), "memset");
+  launch_wrap_bin(h->st, n, P<double>(w.x), g, P<int32_t>(w.cellc), P<int32_t>(w.cell_count));
+  launch_scan(h->st, P<int32_t>(w.cell_count), P<int32_t>(w.cell_start), ncell);
+  launch_scatter(h->st, n, P<int32_t>(w.cellc), P<int32_t>(w.cell_start), P<int32_t>(w.cell_fill),
+                 P<int32_t>(w.cell_tmp));
+  launch_cell_sort(h->st, ncell, P<int32_t>(w.cell_start), P<int32_t>(w.cell_tmp),
+                   P<int32_t>(w.cell_atoms));
+  launch_mirror(h->st, n, P<double>(w.x), P<int32_t>(w.cellc), P<int32_t>(w.types), g,
+                P<float4>(w.off));
+  CK(cudaMemcpyAsync(w.xref.p, w.x.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, h->st),
+     "xref");
+  if (w.cap == 0) {
+    const double vol = L[0] * L[1] * L[2];
+    const double est = (double)n / vol * 4.18879020479 * rlist * rlist * rlist;
+    w.cap = std::max(32, ((int)(1.25 * est + 32) + 31) / 32 * 32);
+  }
+  const float rc2 = (float)(h->rc * h->rc);
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    CK(ensure(w.nlist, (size_t)n * w.cap * sizeof(uint32_t)), "alloc neighbor list");
+    CK(cudaMemsetAsync(P<int32_t>(h->status) + ST_MAXLIST, 0, 2 * sizeof(int32_t), h->st), "memset");
+    launch_build_list(h->st, n, P<double>(w.x), P<int32_t>(w.cellc), P<float4>(w.off),
+                      P<int32_t>(w.cell_start), P<int32_t>(w.cell_atoms), g, rlist, rc2,
+                      h->ntypes, P<int32_t>(h->sel_dev), w.cap, P<uint32_t>(w.nlist),
+                      P<int32_t>(w.nn), P<int32_t>(h->status));
+    CK(cudaGetLastError(), "neighbor kernels");
+    CKS(read_status(h));
+    if (h->status_host[ST_LISTOVF] == 0) return DP_OK;
+    w.cap = ((int)(h->status_host[ST_MAXLIST] * 1.1) + 8 + 31) / 32 * 32;
+  }
+  return fail(h, DP_ERR_CUDA, "neighbor list capacity did not converge");
+}
+
+// energy, forces, virial from the current list and offsets
+dp_status evaluate(dp_handle* h, Work& w) {
+  const int64_t n = w.n;
+  if (n == 0) {
+    CK(cudaMemsetAsync(w.red_out.p, 0, 16 * sizeof(double), h->st), "memset");
+    return DP_OK;
+  }
+  const EnvParams ep = env_params(h);
+  launch_zero_forces(h->st, n, P<unsigned long long>(w.ffix));
+  CK(cudaMemsetAsync(w.pairs.p, 0, sizeof(unsigned long long), h->st), "memset");
+  {
+    Phase ph(h, 1);
+    if (launch_tab_fwd(h->st, n, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn), w.cap,
+                       w.geom, ep, P<float>(h->table), P<float>(w.T), P<int32_t>(h->status),
+                       P<unsigned long long>(w.pairs)))
+      return fail(h, DP_ERR_UNIMPLEMENTED, "tabulated kernel cannot run this model shape");
+  }
+  Phase ph_fit(h, 2);
+  for (int t = 0; t < h->ntypes; ++t) {
+    const int64_t cnt = w.have_idx ? w.type_count[t] : n;
+    if (cnt == 0) continue;
+    CKS(ensure_fit_scratch(h, cnt));
+    const int32_t* idx = w.have_idx ? P<int32_t>(w.idx) + w.type_off[t] : nullptr;
+    if (fit_simt(h->st, cnt, idx, h->nets[t], h->M, h->m_lt, P<float>(w.T), P<float>(w.dT),
+                 P<double>(w.e_atom), h->fs))
+      return fail(h, DP_ERR_CUDA, "fitting kernels failed to launch");
+    if (!w.have_idx) break;
+  }
+  ph_fit.end();
+  {
+    Phase ph(h, 3);
+    if (launch_tab_bwd(h->st, n, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn), w.cap,
+                       w.geom, ep, P<float>(h->table), P<float>(w.dT),
+                       P<unsigned long long>(w.ffix), P<double>(w.vir_part), tab_kernel_slots(n),
+                       P<int32_t>(h->status)))
+      return fail(h, DP_ERR_UNIMPLEMENTED, "tabulated kernel cannot run this model shape");
+  }
+  Phase ph_int(h, 4);
+  launch_force_finalize(h->st, n, P<unsigned long long>(w.ffix), P<double>(w.f),
+                        P<int32_t>(h->status));
+  launch_sum_rows(h->st, n, 1, P<double>(w.e_atom), P<double>(w.red_part), P<double>(w.red_out));
+  launch_sum_rows(h->st, tab_kernel_slots(n), 9, P<double>(w.vir_part), P<double>(w.red_part),
+                  P<double>(w.red_out) + 1);
+  launch_check_energy(h->st, n, P<double>(w.e_atom), P<int32_t>(h->status));
+  CK(cudaGetLastError(), "evaluation kernels");
+  return DP_OK;
+}
+
+dp_status check_handle(dp_handle* h) {
+  if (!h) return DP_ERR_ARG;
+  if (h->dead) return fail(h, DP_ERR_CUDA, "handle unusable after an earlier CUDA error");
+  h->err.clear();
+  return DP_OK;
+}
+
+// copy in x (host or device) and user types; returns model types on device
+dp_status load_coords(dp_handle* h, Work& w, int64_t n, const double* coords,
+                      const int32_t* types, int device_ptrs) {
+  CKS(ensure_atoms(h, w, n));
+  if (n == 0) return DP_OK;
+  const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(w.x.p, coords, sizeof(double) * 3 * n, kind, h->st), "coords copy");
+  std::vector<int32_t> th;
+  const int32_t* types_host = types;
+  if (device_ptrs) {
+    th.resize(n);
+    CK(cudaMemcpyAsync(th.data(), types, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->st),
+       "types copy");
+    CK(cudaStreamSynchronize(h->st), "types copy");
+    types_host = th.data();
+  }
+  return set_types(h, w, types_host);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void dp_options_default(dp_options* o) {
+  if (!o) return;
+  o->tabulated = 1;
+  o->fit_precision = 0;
+  o->table_step = 0.01;
+  o->s_max = 1.0 / 1.5;
+  o->skin = 2.0;
+  o->rebuild_every = 10;
+}
+
+const char* dp_version(void) { return "dp-gb300 0.1 (sm_103a; tabulated FP32 embedding, FP32 SIMT fitting)"; }
+
+const char* dp_last_error(const dp_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+dp_status dp_set_stream(dp_handle* h, void* stream) {
+  if (!h) return DP_ERR_ARG;
+  h->st = (cudaStream_t)stream;
+  return DP_OK;
+}
+
+dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map, double rc,
+                    double rcs, const int32_t* sel, const dp_options* opt, void* stream,
+                    dp_handle** out) {
+  if (!out) return DP_ERR_ARG;
+  *out = nullptr;
+  dp_handle* h = new dp_handle();
+  g_create_err.clear();
+  auto bail = [&](dp_status s) {
+    g_create_err = h->err.empty() ? "dp_create failed" : h->err;
+    if (h->status_host) cudaFreeHost(h->status_host);
+    delete h;
+    return s;
+  };
+  h->st = (cudaStream_t)stream;
+  if (opt)
+    h->opt = *opt;
+  else
+    dp_options_default(&h->opt);
+  if (!model_path || !sel || ntypes < 1 || ntypes > DP_MAXT || !(rc > 0) || !(rcs >= 0) ||
+      !(rcs < rc) || !(h->opt.table_step > 0) || !(h->opt.s_max > 0) || h->opt.skin < 0 ||
+      h->opt.rebuild_every < 1)
+    return bail(DP_ERR_ARG);
+  if (h->opt.tabulated != 1 || h->opt.fit_precision != 0) return bail(DP_ERR_UNIMPLEMENTED);
+  HostModel m;
+  std::string why;
+  if (!read_model(model_path, m, why)) {
+    h->err = why;
+    return bail(DP_ERR_MODEL);
+  }
+  h->ntypes = m.ntypes;
+  h->n_emb = m.n_emb;
+  for (int k = 0; k < m.n_emb; ++k) h->emb_w[k] = m.emb_w[k];
+  h->M = m.emb_w[m.n_emb - 1];
+  h->m_lt = m.m_lt;
+  h->din = h->M * h->m_lt;
+  h->n_fit = m.n_fit;
+  for (int k = 0; k < m.n_fit; ++k) h->fit_w[k] = m.fit_w[k];
+  if (h->din % 16) return bail(DP_ERR_UNIMPLEMENTED);
+  for (int k = 0; k < m.n_fit; ++k)
+    if (h->fit_w[k] % 16) return bail(DP_ERR_UNIMPLEMENTED);
+  h->ntypes_user = ntypes;
+  for (int t = 0; t < ntypes; ++t) {
+    h->type_map[t] = type_map ? type_map[t] : t;
+    if (h->type_map[t] < 0 || h->type_map[t] >= m.ntypes) return bail(DP_ERR_ARG);
+  }
+  h->rc = rc;
+  h->rcs = rcs;
+  h->Nm = 0;
+  for (int t = 0; t < m.ntypes; ++t) {
+    if (sel[t] < 0) return bail(DP_ERR_ARG);
+    h->sel[t] = sel[t];
+    h->Nm += sel[t];
+  }
+  if (h->Nm <= 0) return bail(DP_ERR_ARG);
+  h->h = h->opt.table_step;
+  h->n_int = std::max(1, (int)std::ceil(h->opt.s_max / h->h - 1e-9));
+  if (h->n_int > 4096) return bail(DP_ERR_ARG);
+  if (cudaMallocHost(&h->status_host, sizeof(int32_t) * ST_NWORDS) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(DP_ERR_OOM);
+  }
+  auto up = [&](DevBuf& b, const void* src, size_t bytes) -> bool {
+    if (ensure(b, bytes) != cudaSuccess) return false;
+    return cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, h->st) == cudaSuccess;
+  };
+  // embedding parameters (FP64, for the table builder)
+  const int np = m.ntypes * m.ntypes;
+  const int64_t emb_end = m.fit_off.empty() ? (int64_t)m.data.size() : m.fit_off[0];
+  bool ok = up(h->emb64, m.data.data(), sizeof(double) * emb_end) &&
+            up(h->emb_off, m.emb_off.data(), sizeof(int64_t) * m.emb_off.size()) &&
+            up(h->sel_dev, h->sel, sizeof(int32_t) * DP_MAXT) &&
+            ensure(h->status, sizeof(int32_t) * ST_NWORDS) == cudaSuccess &&
+            ensure(h->table, sizeof(float) * (size_t)np * h->n_int * 6 * h->M) == cudaSuccess;
+  // fitting parameters (FP32, plus transposed weights for the backward)
+  std::vector<float> fit;
+  struct Ofs {
+    size_t W[DP_MAXFIT], WT[DP_MAXFIT], b[DP_MAXFIT], wout;
+  };
+  std::vector<Ofs> ofs(m.ntypes);
+  for (int t = 0; t < m.ntypes; ++t) {
+    int prev = h->din;
+    for (int k = 0; k < m.n_fit; ++k) {
+      const int wo = m.fit_w[k];
+      const double* W = m.data.data() + m.fit_off[t * (m.n_fit + 1) + k];
+      ofs[t].W[k] = fit.size();
+      for (int64_t q = 0; q < (int64_t)prev * wo; ++q) fit.push_back((float)W[q]);
+      ofs[t].WT[k] = fit.size();
+      for (int c = 0; c < wo; ++c)
+        for (int r = 0; r < prev; ++r) fit.push_back((float)W[(size_t)r * wo + c]);
+      ofs[t].b[k] = fit.size();
+      for (int c = 0; c < wo; ++c) fit.push_back((float)W[(size_t)prev * wo + c]);
+      prev = wo;
+    }
+    const double* wo_p = m.data.data() + m.fit_off[t * (m.n_fit + 1) + m.n_fit];
+    ofs[t].wout = fit.size();
+    for (int c = 0; c < prev; ++c) fit.push_back((float)wo_p[c]);
+    h->b_out[t] = (float)wo_p[prev];
+    while (fit.size() % 4) fit.push_back(0.0f);
+  }
+  ok = ok && up(h->fit32, fit.data(), sizeof(float) * fit.size());
+  if (!ok) {
+    h->err = "device allocation or upload failed";
+    cudaGetLastError();
+    return bail(DP_ERR_OOM);
+  }
+  float* fb = P<float>(h->fit32);
+  for (int t = 0; t < m.ntypes; ++t) {
+    FitNet& net = h->nets[t];
+    net.nl = m.n_fit;
+    int prev = h->din;
+    for (int k = 0; k < m.n_fit; ++k) {
+      net.win[k] = prev;
+      net.wout[k] = m.fit_w[k];
+      net.shortcut[k] = (k > 0 && m.fit_w[k] == prev) ? 1 : 0;
+      net.W[k] = fb + ofs[t].W[k];
+      net.WT[k] = fb + ofs[t].WT[k];
+      net.b[k] = fb + ofs[t].b[k];
+      prev = m.fit_w[k];
+    }
+    net.w_out = fb + ofs[t].wout;
+    net.b_out = h->b_out[t];
+  }
+  if (table_build(h->st, P<double>(h->emb64), P<int64_t>(h->emb_off), m.n_emb, m.emb_w, np, h->h,
+                  h->n_int, P<float>(h->table)) != 0) {
+    h->err = "table build failed";
+    return bail(DP_ERR_CUDA);
+  }
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) {
+    h->err = "device error during dp_create";
+    return bail(DP_ERR_CUDA);
+  }
+  *out = h;
+  return DP_OK;
+}
+
+void dp_destroy(dp_handle* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  if (h->status_host) cudaFreeHost(h->status_host);
+  delete h;
+}
+
+dp_status dp_compute(dp_handle* h, int64_t natoms, const double* coords, const int32_t* types,
+                     const double* box, int device_ptrs, double* energy, double* forces,
+                     double* virial, double* atom_energy) {
+  CKS(check_handle(h));
+  if (natoms < 0 || !box || !energy || !virial || (natoms > 0 && (!coords || !types || !forces)))
+    return fail(h, DP_ERR_ARG, "null pointer or negative atom count");
+  if (natoms >= (1LL << 27)) return fail(h, DP_ERR_ARG, "at most 2^27 atoms per call");
+  double L[3];
+  double box_h[9];
+  if (device_ptrs) {
+    CK(cudaMemcpy(box_h, box, sizeof box_h, cudaMemcpyDeviceToHost), "box copy");
+  } else {
+    std::memcpy(box_h, box, sizeof box_h);
+  }
+  CKS(box_lengths(h, box_h, L));
+  Work& w = h->w;
+  CKS(load_coords(h, w, natoms, coords, types, device_ptrs));
+  CKS(clear_status(h));
+  CKS(rebuild(h, w, L, h->rc));
+  CKS(status_errors(h));
+  CKS(evaluate(h, w));
+  CKS(read_status(h));
+  CKS(status_errors(h));
+  const int64_t n = natoms;
+  const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(energy, w.red_out.p, sizeof(double), kind, h->st), "energy copy");
+  CK(cudaMemcpyAsync(virial, P<double>(w.red_out) + 1, 9 * sizeof(double), kind, h->st),
+     "virial copy");
+  if (n > 0) {
+    CK(cudaMemcpyAsync(forces, w.f.p, sizeof(double) * 3 * n, kind, h->st), "force copy");
+    if (atom_energy)
+      CK(cudaMemcpyAsync(atom_energy, w.e_atom.p, sizeof(double) * n, kind, h->st), "e copy");
+  }
+  if (!device_ptrs) CK(cudaStreamSynchronize(h->st), "result copy");
+  return DP_OK;
+}
+
+dp_status dp_neighbor_pairs(dp_handle* h, int64_t natoms, const double* coords, const double* box,
+                            double rlist, int64_t cap, int32_t* out5, int64_t* count) {
+  CKS(check_handle(h));
+  if (natoms < 0 || !box || !count || (natoms > 0 && !coords) || !(rlist > 0))
+    return fail(h, DP_ERR_ARG, "bad argument");
+  double L[3];
+  CKS(box_lengths(h, box, L));
+  Work& w = h->w;
+  std::vector<int32_t> zeros(natoms, 0);
+  // all atoms as caller type 0 (the list does not depend on types)
+  CKS(ensure_atoms(h, w, natoms));
+  if (natoms)
+    CK(cudaMemcpyAsync(w.x.p, coords, sizeof(double) * 3 * natoms, cudaMemcpyHostToDevice, h->st),
+       "coords copy");
+  CKS(set_types(h, w, zeros.data()));
+  CKS(clear_status(h));
+  CKS(rebuild(h, w, L, rlist));
+  const int64_t n = natoms;
+  std::vector<uint32_t> nl((size_t)n * w.cap);
+  std::vector<int32_t> nn(n), cellc(n);
+  if (n) {
+    CK(cudaMemcpy(nl.data(), w.nlist.p, sizeof(uint32_t) * nl.size(), cudaMemcpyDeviceToHost),
+       "list copy");
+    CK(cudaMemcpy(nn.data(), w.nn.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost), "list copy");
+    CK(cudaMemcpy(cellc.data(), w.cellc.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost),
+       "list copy");
+  }
+  const CellGeom& g = w.geom;
+  int64_t k = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int id = cellc[i];
+    const int ci[3] = {id / (g.nc[2] * g.nc[1]), (id / g.nc[2]) % g.nc[1], id % g.nc[2]};
+    for (int q = 0; q < std::min(nn[i], w.cap); ++q, ++k) {
+      if (k >= cap || !out5) continue;
+      const uint32_t e = nl[(size_t)i * w.cap + q];
+      const int slot = e & 31;
+      const int o[3] = {slot / 9 - 1, (slot / 3) % 3 - 1, slot % 3 - 1};
+      int32_t* r = out5 + k * 5;
+      r[0] = (int32_t)i;
+      r[1] = (int32_t)(e >> 5);
+      for (int a = 0; a < 3; ++a) {
+        const int v = ci[a] + o[a];
+        r[2 + a] = v < 0 ? -1 : (v >= g.nc[a] ? 1 : 0);
+      }
+    }
+  }
+  *count = k;
+  return DP_OK;
+}
+
+dp_status dp_table_coeffs(dp_handle* h, int ti, int tj, float* out, int32_t* n) {
+  CKS(check_handle(h));
+  if (ti < 0 || tj < 0 || ti >= h->ntypes || tj >= h->ntypes) return fail(h, DP_ERR_ARG, "type");
+  if (n) *n = h->n_int;
+  if (!out) return DP_OK;
+  const size_t sz = (size_t)h->n_int * 6 * h->M;
+  CK(cudaMemcpy(out, P<float>(h->table) + (size_t)(ti * h->ntypes + tj) * sz, sz * sizeof(float),
+                cudaMemcpyDeviceToHost),
+     "table copy");
+  return DP_OK;
+}
+
+dp_status dp_descriptor(dp_handle* h, int64_t natoms, const double* coords, const int32_t* types,
+                        const double* box, float* T_out) {
+  CKS(check_handle(h));
+  if (natoms < 0 || !box || (natoms > 0 && (!coords || !types || !T_out)))
+    return fail(h, DP_ERR_ARG, "bad argument");
+  double L[3];
+  CKS(box_lengths(h, box, L));
+  Work& w = h->w;
+  CKS(load_coords(h, w, natoms, coords, types, 0));
+  CKS(clear_status(h));
+  CKS(rebuild(h, w, L, h->rc));
+  CKS(status_errors(h));
+  if (natoms == 0) return DP_OK;
+  const EnvParams ep = env_params(h);
+  if (launch_tab_fwd(h->st, natoms, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
+                     w.cap, w.geom, ep, P<float>(h->table), P<float>(w.T), P<int32_t>(h->status),
+                     nullptr))
+    return fail(h, DP_ERR_UNIMPLEMENTED, "tabulated kernel cannot run this model shape");
+  CKS(read_status(h));
+  CKS(status_errors(h));
+  CK(cudaMemcpy(T_out, w.T.p, sizeof(float) * 4 * h->M * natoms, cudaMemcpyDeviceToHost),
+     "T copy");
+  return DP_OK;
+}
+
+dp_status dp_profile(dp_handle* h, int enable) {
+  if (!h) return DP_ERR_ARG;
+  for (auto& v : h->prof_ev) {
+    for (auto& e : v) h->prof_pool.push_back(e);
+    v.clear();
+  }
+  h->prof = enable != 0;
+  return DP_OK;
+}
+
+dp_status dp_profile_read(dp_handle* h, double* ms, int64_t* launches) {
+  CKS(check_handle(h));
+  CK(cudaStreamSynchronize(h->st), "sync");
+  for (int p = 0; p < DP_NPHASE; ++p) {
+    double t = 0.0;
+    for (auto& e : h->prof_ev[p]) {
+      float x = 0.0f;
+      CK(cudaEventElapsedTime(&x, e.first, e.second), "event time");
+      t += x;
+    }
+    if (ms) ms[p] = t;
+    if (launches) launches[p] = (int64_t)h->prof_ev[p].size();
+  }
+  return DP_OK;
+}
+
+dp_status dp_stats(dp_handle* h, const dp_system* s, int64_t* out) {
+  CKS(check_handle(h));
+  if (!out) return fail(h, DP_ERR_ARG, "null output");
+  Work& w = s ? const_cast<dp_system*>(s)->w : h->w;
+  unsigned long long pairs = 0;
+  if (w.pairs.p) {
+    CK(cudaStreamSynchronize(h->st), "sync");
+    CK(cudaMemcpy(&pairs, w.pairs.p, sizeof pairs, cudaMemcpyDeviceToHost), "stats copy");
+  }
+  CKS(read_status(h));
+  out[0] = w.n;
+  out[1] = w.cap;
+  out[2] = h->status_host[ST_MAXLIST];
+  out[3] = (int64_t)pairs;
+  out[4] = w.geom.ncell;
+  return DP_OK;
+}
+
+// ---------------------------------------------------------------------- MD
+dp_status dp_system_create(dp_handle* h, int64_t natoms, const double* x, const double* v,
+                           const int32_t* types, const double* mass_of_type, const double* box,
+                           int device_ptrs, dp_system** out) {
+  CKS(check_handle(h));
+  if (!out || natoms < 0 || !box || !mass_of_type || (natoms > 0 && (!x || !v || !types)))
+    return fail(h, DP_ERR_ARG, "bad argument");
+  *out = nullptr;
+  dp_system* s = new dp_system();
+  s->h = h;
+  auto bail = [&](dp_status st) {
+    delete s;
+    return st;
+  };
+  double box_h[9];
+  std::vector<double> mass_h(h->ntypes_user);
+  if (device_ptrs) {
+    if (cudaMemcpy(box_h, box, sizeof box_h, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(mass_h.data(), mass_of_type, sizeof(double) * h->ntypes_user,
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bail(fail(h, DP_ERR_ARG, "box/mass copy failed"));
+  } else {
+    std::memcpy(box_h, box, sizeof box_h);
+    std::memcpy(mass_h.data(), mass_of_type, sizeof(double) * h->ntypes_user);
+  }
+  double L[3];
+  dp_status st = box_lengths(h, box_h, L);
+  if (st) return bail(st);
+  for (double mm : mass_h)
+    if (!(mm > 0)) return bail(fail(h, DP_ERR_ARG, "masses must be > 0"));
+  std::memcpy(s->box, box_h, sizeof box_h);
+  s->mass_user = mass_h;
+  st = load_coords(h, s->w, natoms, x, types, device_ptrs);
+  if (st) return bail(st);
+  s->types_user.resize(natoms);
+  if (natoms) {
+    if (cudaMemcpy(s->types_user.data(), types, sizeof(int32_t) * natoms,
+                   device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) != cudaSuccess)
+      return bail(fail(h, DP_ERR_ARG, "types copy failed"));
+  }
+  // masses per model-mapped atom type are kept per caller type: store a
+  // per-atom-type table indexed by the model type only when unambiguous,
+  // else per caller type through the mapped types buffer
+  std::vector<double> mass_model(DP_MAXT, 0.0), inv_acc(DP_MAXT, 0.0);
+  for (int t = 0; t < h->ntypes_user; ++t) {
+    const int mt = h->type_map[t];
+    if (mass_model[mt] != 0.0 && mass_model[mt] != mass_h[t])
+      return bail(fail(h, DP_ERR_UNIMPLEMENTED, "caller types sharing a model type need equal masses"));
+    mass_model[mt] = mass_h[t];
+  }
+  for (int t = 0; t < DP_MAXT; ++t) inv_acc[t] = mass_model[t] > 0 ? kAcc / mass_model[t] : 0.0;
+  if (ensure(s->v, sizeof(double) * 3 * std::max<int64_t>(natoms, 1)) != cudaSuccess ||
+      ensure(s->mass, sizeof(double) * DP_MAXT) != cudaSuccess ||
+      ensure(s->inv_mass_acc, sizeof(double) * DP_MAXT) != cudaSuccess)
+    return bail(fail(h, DP_ERR_OOM, "device allocation failed"));
+  cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if ((natoms && cudaMemcpyAsync(s->v.p, v, sizeof(double) * 3 * natoms, kind, h->st)) ||
+      cudaMemcpyAsync(s->mass.p, mass_model.data(), sizeof(double) * DP_MAXT,
+                      cudaMemcpyHostToDevice, h->st) ||
+      cudaMemcpyAsync(s->inv_mass_acc.p, inv_acc.data(), sizeof(double) * DP_MAXT,
+                      cudaMemcpyHostToDevice, h->st))
+    return bail(fail(h, DP_ERR_CUDA, "upload failed"));
+  if ((st = clear_status(h))) return bail(st);
+  if ((st = rebuild(h, s->w, L, h->rc + h->opt.skin))) return bail(st);
+  if ((st = status_errors(h))) return bail(st);
+  if ((st = evaluate(h, s->w))) return bail(st);
+  if ((st = read_status(h))) return bail(st);
+  if ((st = status_errors(h))) return bail(st);
+  s->f_valid = true;
+  *out = s;
+  return DP_OK;
+}
+
+void dp_system_destroy(dp_system* s) {
+  if (!s) return;
+  if (s->h && s->h->st) cudaStreamSynchronize(s->h->st);
+  delete s;
+}
+
+int64_t dp_system_step(const dp_system* s) { return s ? s->step : -1; }
+
+dp_status dp_system_get(dp_system* s, double* x, double* v, double* f, int device_ptrs) {
+  if (!s) return DP_ERR_ARG;
+  dp_handle* h = s->h;
+  CKS(check_handle(h));
+  const int64_t n = s->w.n;
+  const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (n) {
+    if (x) CK(cudaMemcpyAsync(x, s->w.x.p, sizeof(double) * 3 * n, kind, h->st), "x copy");
+    if (v) CK(cudaMemcpyAsync(v, s->v.p, sizeof(double) * 3 * n, kind, h->st), "v copy");
+    if (f) CK(cudaMemcpyAsync(f, s->w.f.p, sizeof(double) * 3 * n, kind, h->st), "f copy");
+  }
+  CK(cudaStreamSynchronize(h->st), "copy");
+  return DP_OK;
+}
+
+dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_thermo* thermo) {
+  CKS(check_handle(h));
+  if (!s || s->h != h || nsteps < 0 || !(dt_fs > 0)) return fail(h, DP_ERR_ARG, "bad argument");
+  Work& w = s->w;
+  const int64_t n = w.n;
+  double L[3];
+  CKS(box_lengths(h, s->box, L));
+  const double half_skin2 = 0.25 * h->opt.skin * h->opt.skin;
+  const double vol = L[0] * L[1] * L[2];
+  if (thermo) CK(ensure(s->thermo, sizeof(double) * 16 * std::max(nsteps, 1)), "alloc thermo");
+  CKS(clear_status(h));
+  for (int k = 0; k < nsteps; ++k) {
+    Phase ph1(h, 4);
+    launch_kick_drift(h->st, n, P<double>(w.x), P<double>(s->v), P<double>(w.f),
+                      P<int32_t>(w.types), P<double>(s->inv_mass_acc), dt_fs, P<double>(w.xref),
+                      half_skin2, P<int32_t>(h->status));
+    s->step += 1;
+    s->f_valid = false;
+    if (s->step % h->opt.rebuild_every == 0) {
+      CKS(read_status(h));
+      CKS(status_errors(h));
+      CKS(rebuild(h, w, L, h->rc + h->opt.skin));
+    } else {
+      launch_mirror(h->st, n, P<double>(w.x), P<int32_t>(w.cellc), P<int32_t>(w.types), w.geom,
+                    P<float4>(w.off));
+    }
+    ph1.end();
+    CKS(evaluate(h, w));
+    Phase ph2(h, 4);
+    launch_kick(h->st, n, P<double>(s->v), P<double>(w.f), P<int32_t>(w.types),
+                P<double>(s->inv_mass_acc), P<double>(s->mass), dt_fs,
+                thermo ? P<double>(w.ke) : nullptr);
+    if (thermo) {
+      double* rec = P<double>(s->thermo) + 16 * k;
+      launch_sum_rows(h->st, n, 1, P<double>(w.ke), P<double>(w.red_part), rec);
+      CK(cudaMemcpyAsync(rec + 1, w.red_out.p, sizeof(double) * 10, cudaMemcpyDeviceToDevice,
+                         h->st),
+         "thermo");
+    }
+    s->f_valid = true;
+  }
+  CK(cudaGetLastError(), "md kernels");
+  CKS(read_status(h));
+  CKS(status_errors(h));
+  if (thermo && nsteps > 0) {
+    std::vector<double> rec((size_t)16 * nsteps);
+    CK(cudaMemcpy(rec.data(), s->thermo.p, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost),
+       "thermo copy");
+    const int64_t dof = 3 * n - 3;
+    for (int k = 0; k < nsteps; ++k) {
+      const double* r = rec.data() + 16 * k;
+      dp_thermo& t = thermo[k];
+      t.step = s->step - nsteps + k + 1;
+      t.kinetic = r[0] / kAcc;
+      t.potential = r[1];
+      for (int a = 0; a < 9; ++a) t.virial[a] = r[2 + a];
+      t.temperature = dof > 0 ? 2.0 * t.kinetic / (dof * kKb) : 0.0;
+      t.pressure = (2.0 * t.kinetic + t.virial[0] + t.virial[4] + t.virial[8]) / (3.0 * vol) * kEvA3Bar;
+    }
+  }
+  return DP_OK;
+}
+
+// state file: magic, n, ntypes_user, step, box[9], masses[ntypes_user],
+// types[n], x[n][3], v[n][3], f[n][3], xref[n][3]
+dp_status dp_state_save(dp_system* s, const char* path) {
+  if (!s || !path) return DP_ERR_ARG;
+  dp_handle* h = s->h;
+  CKS(check_handle(h));
+  const int64_t n = s->w.n;
+  std::vector<double> x(3 * n), v(3 * n), f(3 * n), xr(3 * n);
+  if (n) {
+    CK(cudaStreamSynchronize(h->st), "sync");
+    CK(cudaMemcpy(x.data(), s->w.x.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost), "copy");
+    CK(cudaMemcpy(v.data(), s->v.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost), "copy");
+    CK(cudaMemcpy(f.data(), s->w.f.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost), "copy");
+    CK(cudaMemcpy(xr.data(), s->w.xref.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost), "copy");
+  }
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return fail(h, DP_ERR_ARG, "cannot open state file for writing");
+  int64_t hdr[3] = {n, (int64_t)s->mass_user.size(), s->step};
+  bool ok = std::fwrite("DPSTATE1", 1, 8, fp) == 8 && std::fwrite(hdr, 8, 3, fp) == 3 &&
+            std::fwrite(s->box, 8, 9, fp) == 9 &&
+            std::fwrite(s->mass_user.data(), 8, s->mass_user.size(), fp) == s->mass_user.size() &&
+            std::fwrite(s->types_user.data(), 4, n, fp) == (size_t)n &&
+            std::fwrite(x.data(), 8, 3 * n, fp) == (size_t)(3 * n) &&
+            std::fwrite(v.data(), 8, 3 * n, fp) == (size_t)(3 * n) &&
+            std::fwrite(f.data(), 8, 3 * n, fp) == (size_t)(3 * n) &&
+            std::fwrite(xr.data(), 8, 3 * n, fp) == (size_t)(3 * n);
+  std::fclose(fp);
+  return ok ? DP_OK : fail(h, DP_ERR_ARG, "state write failed");
+}
+
+dp_status dp_state_load(dp_handle* h, const char* path, dp_system** out) {
+  CKS(check_handle(h));
+  if (!path || !out) return fail(h, DP_ERR_ARG, "bad argument");
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(h, DP_ERR_ARG, "cannot open state file");
+  char magic[8];
+  int64_t hdr[3];
+  double box[9];
+  bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "DPSTATE1", 8) == 0 &&
+            std::fread(hdr, 8, 3, fp) == 3 && std::fread(box, 8, 9, fp) == 9 && hdr[0] >= 0 &&
+            hdr[1] == h->ntypes_user;
+  const int64_t n = ok ? hdr[0] : 0;
+  std::vector<double> mass(ok ? hdr[1] : 0), x(3 * n), v(3 * n), f(3 * n), xr(3 * n);
+  std::vector<int32_t> types(n);
+  ok = ok && std::fread(mass.data(), 8, mass.size(), fp) == mass.size() &&
+       std::fread(types.data(), 4, n, fp) == (size_t)n &&
+       std::fread(x.data(), 8, 3 * n, fp) == (size_t)(3 * n) &&
+       std::fread(v.data(), 8, 3 * n, fp) == (size_t)(3 * n) &&
+       std::fread(f.data(), 8, 3 * n, fp) == (size_t)(3 * n) &&
+       std::fread(xr.data(), 8, 3 * n, fp) == (size_t)(3 * n);
+  std::fclose(fp);
+  if (!ok) return fail(h, DP_ERR_ARG, "malformed state file");
+  // rebuild the list from the reference positions of the saved list, then
+  // restore the current positions and forces: the continued run then sees
+  // the same list, cells and forces as the run that was saved
+  dp_system* s = nullptr;
+  CKS(dp_system_create(h, n, xr.data(), v.data(), types.data(), mass.data(), box, 0, &s));
+  s->step = hdr[2];
+  if (n) {
+    if (cudaMemcpy(s->w.x.p, x.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(s->w.f.p, f.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice)) {
+      dp_system_destroy(s);
+      return fail(h, DP_ERR_CUDA, "state upload failed");
+    }
+    launch_mirror(h->st, n, P<double>(s->w.x), P<int32_t>(s->w.cellc), P<int32_t>(s->w.types),
+                  s->w.geom, P<float4>(s->w.off));
+  }
+  s->f_valid = true;
+  *out = s;
+  return DP_OK;
+}
+
+}  // extern "C"

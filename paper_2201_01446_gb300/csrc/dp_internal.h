@@ -1,0 +1,124 @@
+// Internal declarations shared by the CUDA kernels and the C-ABI runtime.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dp.h"
+
+#define DP_MAXT 8
+#define DP_MAXFIT 6
+
+// Per-call device status words (int32).  Kernels only ever add / max into them.
+enum {
+  ST_SEL = 0,        // atoms with more neighbors of one type within rc than sel[t]
+  ST_RANGE = 1,      // pairs with s outside [0, n*h]
+  ST_NONFINITE = 2,  // non-finite per-atom energies / forces
+  ST_SKIN = 3,       // atoms displaced more than skin/2 since the last rebuild
+  ST_MAXLIST = 4,    // largest list length seen (may exceed the capacity)
+  ST_LISTOVF = 5,    // atoms whose list did not fit the capacity
+  ST_BADTYPE = 6,    // atoms with a type index outside the type map
+  ST_NWORDS = 16
+};
+
+// Fixed-point force accumulators: F = int64 * 2^-40 eV/A.  Integer adds are
+// associative, so the atomics give the same bits in any order.
+#define DP_FSCALE 1099511627776.0 /* 2^40 */
+#define DP_FSCALE_F 1099511627776.0f
+#define DP_FINV (1.0 / 1099511627776.0)
+
+// Geometry of the cell grid used for a neighbor list.  Cells have edge >=
+// rlist; each atom carries its FP32 offset from the centre of the cell it
+// was binned into at the last rebuild, so a pair displacement is
+//   r_ij = (off_j - off_i) + o * edge,  o in {-1,0,1}^3 the stencil offset.
+struct CellGeom {
+  double L[3];
+  double edge[3];
+  float edgef[3];
+  int nc[3];
+  long long ncell;
+};
+
+// Smooth-switch / table parameters in FP32 for the pair kernels.
+struct EnvParams {
+  float rc2, rc, rcs, inv_w;  // inv_w = 1/(rc - rcs)
+  float inv_h, h, smax;       // table step and domain end n*h
+  float inv_nm;               // 1/N_m (N_m = sum of sel)
+  int n_int;                  // table intervals
+  int M;                      // embedding width
+  int ntypes;                 // model types
+};
+
+// ---------------------------------------------------------------- neighbors
+void launch_wrap_bin(cudaStream_t st, int64_t n, double* x, const CellGeom& g, int32_t* cellc,
+                     int32_t* cell_count);
+void launch_scan(cudaStream_t st, const int32_t* count, int32_t* start, long long ncell);
+void launch_scatter(cudaStream_t st, int64_t n, const int32_t* cellc, const int32_t* start,
+                    int32_t* fill, int32_t* cell_atoms_unsorted);
+void launch_cell_sort(cudaStream_t st, long long ncell, const int32_t* start,
+                      const int32_t* unsorted, int32_t* sorted);
+void launch_mirror(cudaStream_t st, int64_t n, const double* x, const int32_t* cellc,
+                   const int32_t* types, const CellGeom& g, float4* off);
+void launch_build_list(cudaStream_t st, int64_t n, const double* x, const int32_t* cellc,
+                       const float4* off, const int32_t* cell_start, const int32_t* cell_atoms,
+                       const CellGeom& g, double rlist, float rc2, int ntypes, const int32_t* sel,
+                       int cap, uint32_t* nlist, int32_t* nn, int32_t* status);
+
+// ---------------------------------------------------------------- embedding
+// FP64 forward-mode evaluation of every embedding net at the nodes k*h and
+// the quintic fit per interval; writes FP32 [npair][n_int][6][M] with the
+// coefficients of the normalised local variable u = s/h - k.
+int table_build(cudaStream_t st, const double* emb64, const int64_t* emb_off, int n_emb,
+                const int* emb_w, int npair, double h, int n_int, float* table_out);
+int launch_tab_fwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t* nlist,
+                   const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
+                   const float* table, float* T, int32_t* status,
+                   unsigned long long* pair_count);
+int launch_tab_bwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t* nlist,
+                   const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
+                   const float* table, const float* dT, unsigned long long* ffix,
+                   double* vir_part, int vir_slots, int32_t* status);
+int tab_kernel_slots(int64_t n);  // number of virial partial slots the bwd kernel writes
+
+// ---------------------------------------------------------------- fitting
+struct FitNet {           // one centre type, FP32 device pointers
+  int nl;                 // hidden layers
+  int win[DP_MAXFIT];     // input width of layer k
+  int wout[DP_MAXFIT];    // output width of layer k
+  int shortcut[DP_MAXFIT];
+  const float* W[DP_MAXFIT];   // [win][wout]
+  const float* WT[DP_MAXFIT];  // [wout][win]
+  const float* b[DP_MAXFIT];
+  const float* w_out;          // [wout[nl-1]]
+  float b_out;
+};
+struct FitScratch {
+  int64_t rows;  // capacity in atoms
+  float* D;      // [rows][din]
+  float* dD;     // [rows][din]
+  float* t[DP_MAXFIT];
+  float* z[DP_MAXFIT];
+  float* gz;     // [rows][wmax]
+  float* gp;     // [rows][wmax]
+  float* gz2;    // [rows][wmax]
+};
+// E_i and dE/dT for atoms [0, n) of one centre type listed in idx (or all
+// atoms when idx == NULL), FP32 CUDA-core path.
+int fit_simt(cudaStream_t st, int64_t n, const int32_t* idx, const FitNet& net, int M, int m_lt,
+             const float* T, float* dT, double* e_atom, const FitScratch& s);
+
+// ---------------------------------------------------------------- MD / reductions
+void launch_zero_forces(cudaStream_t st, int64_t n, unsigned long long* ffix);
+void launch_force_finalize(cudaStream_t st, int64_t n, const unsigned long long* ffix, double* f,
+                           int32_t* status);
+// deterministic sums: out[k] = sum_i in[i*stride + k], k < width
+void launch_sum_rows(cudaStream_t st, int64_t rows, int width, const double* in, double* part,
+                     double* out);
+int sum_rows_part_size(int64_t rows, int width);
+void launch_kick_drift(cudaStream_t st, int64_t n, double* x, double* v, const double* f,
+                       const int32_t* types, const double* inv_mass_acc, double dt,
+                       const double* xref, double half_skin2, int32_t* status);
+void launch_kick(cudaStream_t st, int64_t n, double* v, const double* f, const int32_t* types,
+                 const double* inv_mass_acc, const double* mass, double dt, double* ke_atom);
+void launch_check_energy(cudaStream_t st, int64_t n, const double* e, int32_t* status);
+void launch_map_types(cudaStream_t st, int64_t n, const int32_t* in, const int32_t* map, int nmap,
+                      int32_t* out, int32_t* status);

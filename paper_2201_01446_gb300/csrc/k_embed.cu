@@ -1,0 +1,600 @@
+// Tabulated embedding net fused with the environment-matrix contraction
+// (paper Sec. 3.2 tabulation, Sec. 3.3/3.4.1 kernel fusion, Sec. 3.4.2
+// redundancy removal) and its backward pass down to the forces and virial.
+//
+// Forward, per atom i (Eq. 1, Eq. 2):
+//   T_i[c][:] = (1/N_m) sum_{j: r_ij < rc} R_ij[c] g(s_ij),
+//   R_ij = s (1, x/r, y/r, z/r), s = sw(r)/r,
+// with g(s) on interval k given by the quintic sum_q c[k][q][:] u^q,
+// u = s/h - k.  Regrouping the sum by interval (exact in real arithmetic),
+//   T_i[c][:] = sum_k sum_q C_k[c][q] c[k][q][:],  C_k[c][q] = (1/N_m) sum_{j in k} R_ij[c] u_j^q,
+// so the table row of an interval is read once per atom however many
+// neighbors fall in it.  G is never formed, pairs beyond rc (the padding of
+// the paper's N_m rows) cost nothing.
+//
+// Backward, given dT = dE_i/dT_i:
+//   B_k[c][q] = (1/N_m) sum_eta c[k][q][eta] dT[c][eta]          (per occupied interval)
+//   dE/dR_ij[c] = sum_q B_k[c][q] u^q,
+//   dE/ds_ij (through g) = (1/h) sum_c R_ij[c] sum_q q B_k[c][q] u^(q-1),
+//   g_ij = dE_i/dr_ij by the chain rule through Eq. 1,
+//   F_i += g_ij, F_j -= g_ij, virial -= r_ij (x) g_ij.
+// Forces go to int64 fixed-point accumulators (associative, deterministic);
+// the virial to per-warp FP64 partials summed later in a fixed order.
+#include <math.h>
+
+#include "dp_internal.h"
+
+namespace {
+
+// ------------------------------------------------------------------ table
+// One CTA per (type pair, node): the embedding net (Eq. 3-5) and its first
+// and second derivative in s, by forward-mode propagation in FP64.
+__global__ void k_table_nodes(const double* __restrict__ emb, const int64_t* __restrict__ emb_off,
+                              int n_emb, int w0, int w1, int w2, int w3, int w4, int w5, double h,
+                              int n_nodes, double* __restrict__ node) {
+  extern __shared__ double sm[];
+  const int p = blockIdx.x / n_nodes, k = blockIdx.x % n_nodes;
+  const int widths[6] = {w0, w1, w2, w3, w4, w5};
+  int wmax = 0;
+  for (int l = 0; l < n_emb; ++l) wmax = max(wmax, widths[l]);
+  double* cur = sm;                 // [3][wmax]
+  double* nxt = sm + 3 * wmax;      // [3][wmax]
+  const double s = k * h;
+  const int c = threadIdx.x;
+  {
+    const double* W = emb + emb_off[p * n_emb + 0];
+    const double* b = W + widths[0];
+    if (c < widths[0]) {
+      double z = fma(s, W[c], b[c]), zp = W[c];
+      double t = tanh(z), q = 1.0 - t * t;
+      cur[c] = t;
+      cur[wmax + c] = q * zp;
+      cur[2 * wmax + c] = -2.0 * t * q * zp * zp;
+    }
+  }
+  __syncthreads();
+  int w = widths[0];
+  for (int l = 1; l < n_emb; ++l) {
+    const int wo = widths[l];
+    const double* W = emb + emb_off[p * n_emb + l];
+    const double* b = W + (size_t)w * wo;
+    if (c < wo) {
+      double z = b[c], zp = 0.0, zpp = 0.0;
+      for (int r = 0; r < w; ++r) {
+        double wk = W[(size_t)r * wo + c];
+        z = fma(cur[r], wk, z);
+        zp = fma(cur[wmax + r], wk, zp);
+        zpp = fma(cur[2 * wmax + r], wk, zpp);
+      }
+      double t = tanh(z), q = 1.0 - t * t;
+      int src = c - (c / w) * w;  // (x, x): output c repeats input c mod w
+      nxt[c] = cur[src] + t;
+      nxt[wmax + c] = cur[wmax + src] + q * zp;
+      nxt[2 * wmax + c] = cur[2 * wmax + src] + q * zpp - 2.0 * t * q * zp * zp;
+    }
+    __syncthreads();
+    double* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+    w = wo;
+  }
+  if (c < w) {
+    double* out = node + ((size_t)p * n_nodes + k) * 3 * w;
+    out[c] = cur[c];
+    out[w + c] = cur[wmax + c];
+    out[2 * w + c] = cur[2 * wmax + c];
+  }
+}
+
+// Quintic on u in [0,1] with f, f', f'' given at both ends (derivatives in u,
+// i.e. the s-derivatives times h and h^2).  With A, B, C the residuals of the
+// value, slope and curvature left at u = 1 by the first three coefficients,
+// the last three solve  p+q+w = A, 3p+4q+5w = B, 6p+12q+20w = C.
+__global__ void k_table_coef(const double* __restrict__ node, int npair, int n_int, int M, double h,
+                             float* __restrict__ table) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)npair * n_int * M) return;
+  const int c = idx % M;
+  const int k = (idx / M) % n_int;
+  const int p = idx / ((int64_t)M * n_int);
+  const double* n0 = node + ((size_t)p * (n_int + 1) + k) * 3 * M;
+  const double* n1 = n0 + 3 * M;
+  const double f0 = n0[c], d0 = n0[M + c] * h, e0 = n0[2 * M + c] * h * h;
+  const double f1 = n1[c], d1 = n1[M + c] * h, e1 = n1[2 * M + c] * h * h;
+  const double A = f1 - f0 - d0 - 0.5 * e0;
+  const double B = d1 - d0 - e0;
+  const double C = e1 - e0;
+  double q[6];
+  q[0] = f0;
+  q[1] = d0;
+  q[2] = 0.5 * e0;
+  q[3] = 10.0 * A - 4.0 * B + 0.5 * C;
+  q[4] = -15.0 * A + 7.0 * B - C;
+  q[5] = 6.0 * A - 3.0 * B + 0.5 * C;
+  float* out = table + ((size_t)p * n_int + k) * 6 * M;
+  for (int r = 0; r < 6; ++r) out[r * M + c] = (float)q[r];
+}
+
+// ------------------------------------------------------------------ pair geometry
+struct Pair {
+  float dx, dy, dz, r, ir, s, dsdr;
+  int th, tj;
+  float u;
+  bool out_of_range;
+};
+
+__device__ __forceinline__ void pair_geom(const EnvParams& ep, float dx, float dy, float dz,
+                                          float r2, int tj, Pair& P) {
+  P.dx = dx;
+  P.dy = dy;
+  P.dz = dz;
+  P.tj = tj;
+  const float r = sqrtf(r2);
+  const float ir = 1.0f / r;
+  float sw, dsw;
+  if (r < ep.rcs) {
+    sw = 1.0f;
+    dsw = 0.0f;
+  } else {
+    // 1 - 10x^3 + 15x^4 - 6x^5 = (1-x)^3 (1 + 3x + 6x^2): the factored form
+    // keeps its accuracy (and sign) next to rc where the expanded one cancels
+    const float x = (r - ep.rcs) * ep.inv_w;
+    const float om = 1.0f - x;
+    sw = om * om * om * fmaf(fmaf(6.0f, x, 3.0f), x, 1.0f);
+    dsw = -30.0f * x * x * om * om * ep.inv_w;
+  }
+  const float s = sw * ir;
+  P.r = r;
+  P.ir = ir;
+  P.s = s;
+  P.dsdr = (dsw - s) * ir;
+  const float q = s * ep.inv_h;
+  int th = (int)floorf(q);
+  th = th < 0 ? 0 : (th > ep.n_int - 1 ? ep.n_int - 1 : th);
+  P.th = th;
+  P.u = q - (float)th;
+  P.out_of_range = s > ep.smax;
+}
+
+__device__ __forceinline__ void load_pair(const float4& oi, const float4* __restrict__ off,
+                                          const CellGeom& g, uint32_t e, float& dx, float& dy,
+                                          float& dz, int& tj) {
+  const int j = (int)(e >> 5), code = (int)(e & 31u);
+  const float4 oj = off[j];
+  dx = (oj.x - oi.x) + (float)(code / 9 - 1) * g.edgef[0];
+  dy = (oj.y - oi.y) + (float)((code / 3) % 3 - 1) * g.edgef[1];
+  dz = (oj.z - oi.z) + (float)(code % 3 - 1) * g.edgef[2];
+  tj = __float_as_int(oj.w);
+}
+
+struct WarpSmem {
+  float* C;        // [ntypes][n_int][24]
+  unsigned* occ;   // [ntypes][occw]
+  float4* stR;     // [32]
+  float* stU;      // [32]
+  int* stK;        // [32]
+};
+
+__host__ __device__ inline int occ_words(int n_int) { return (n_int + 31) / 32; }
+__host__ __device__ inline int per_warp_words(int ntypes, int n_int) {
+  int cw = ntypes * n_int * 24;
+  int ow = (ntypes * occ_words(n_int) + 3) & ~3;
+  return cw + ow + 32 * 4 + 32 + 32;
+}
+
+__device__ __forceinline__ WarpSmem warp_smem(float* base, int ntypes, int n_int) {
+  WarpSmem w;
+  w.C = base;
+  w.occ = (unsigned*)(base + ntypes * n_int * 24);
+  w.stR = (float4*)(base + ntypes * n_int * 24 + ((ntypes * occ_words(n_int) + 3) & ~3));
+  w.stU = (float*)(w.stR + 32);
+  w.stK = (int*)(w.stU + 32);
+  return w;
+}
+
+// ------------------------------------------------------------------ forward
+__global__ void __launch_bounds__(256) k_tab_fwd(int64_t n, const float4* __restrict__ off,
+                                                 const uint32_t* __restrict__ nlist,
+                                                 const int32_t* __restrict__ nn, int cap, CellGeom g,
+                                                 EnvParams ep, const float* __restrict__ table,
+                                                 float* __restrict__ T, int32_t* __restrict__ status,
+                                                 unsigned long long* __restrict__ pair_count) {
+  extern __shared__ float4 smem4[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int nt = ep.ntypes, n_int = ep.n_int, M = ep.M, ow = occ_words(n_int);
+  WarpSmem S = warp_smem((float*)smem4 + (size_t)wib * per_warp_words(nt, n_int), nt, n_int);
+  for (int k = lane; k < nt * n_int * 24; k += 32) S.C[k] = 0.0f;
+  for (int k = lane; k < nt * ow; k += 32) S.occ[k] = 0u;
+  __syncwarp();
+  const int cl = lane * 4;
+  const bool colok = cl < M;
+  const unsigned below = (1u << lane) - 1u;
+  int nrange = 0;
+  unsigned long long npairs = 0;
+  for (int64_t i = (int64_t)blockIdx.x * wpb + wib; i < n; i += (int64_t)gridDim.x * wpb) {
+    const float4 oi = off[i];
+    const int ti = __float_as_int(oi.w);
+    const int cnt = min(nn[i], cap);
+    const uint32_t* L = nlist + (size_t)i * cap;
+    for (int base = 0; base < cnt; base += 32) {
+      const int k = base + lane;
+      bool in = false;
+      Pair P;
+      if (k < cnt) {
+        float dx, dy, dz;
+        int tj;
+        load_pair(oi, off, g, L[k], dx, dy, dz, tj);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < ep.rc2) {
+          in = true;
+          pair_geom(ep, dx, dy, dz, r2, tj, P);
+          nrange += P.out_of_range;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int slot = __popc(m & below);
+        S.stR[slot] = make_float4(P.s, P.s * P.dx * P.ir, P.s * P.dy * P.ir, P.s * P.dz * P.ir);
+        S.stU[slot] = P.u;
+        S.stK[slot] = P.th | (P.tj << 16);
+      }
+      __syncwarp();
+      const int c = __popc(m);
+      npairs += c;
+      if (lane < c) {
+        const int key = S.stK[lane];
+        const int th = key & 0xffff, tj = key >> 16;
+        atomicOr(&S.occ[tj * ow + (th >> 5)], 1u << (th & 31));
+      }
+      if (lane < 24) {
+        // lane (cc, q) owns C_k[cc][q] for every interval: list-order sums
+        const int cc = lane / 6, q = lane - cc * 6;
+        for (int t = 0; t < c; ++t) {
+          const float4 R = S.stR[t];
+          const float uu = S.stU[t];
+          const int key = S.stK[t];
+          float pw = 1.0f;
+          for (int e = 0; e < q; ++e) pw *= uu;
+          const float rv = cc == 0 ? R.x : (cc == 1 ? R.y : (cc == 2 ? R.z : R.w));
+          float* dst = S.C + ((key >> 16) * n_int + (key & 0xffff)) * 24 + lane;
+          *dst = fmaf(rv, pw, *dst);
+        }
+      }
+      __syncwarp();
+    }
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+    for (int tj = 0; tj < nt; ++tj) {
+      const float* tab = table + ((size_t)(ti * nt + tj) * n_int) * 6 * M + cl;
+      for (int wd = 0; wd < ow; ++wd) {
+        unsigned bits = S.occ[tj * ow + wd];
+        while (bits) {
+          const int th = wd * 32 + __ffs(bits) - 1;
+          bits &= bits - 1u;
+          float* cf = S.C + (tj * n_int + th) * 24;
+          float Cv[24];
+#pragma unroll
+          for (int v = 0; v < 6; ++v) {
+            const float4 t4 = reinterpret_cast<const float4*>(cf)[v];
+            Cv[4 * v] = t4.x;
+            Cv[4 * v + 1] = t4.y;
+            Cv[4 * v + 2] = t4.z;
+            Cv[4 * v + 3] = t4.w;
+          }
+          if (colok) {
+            const float* tp = tab + (size_t)th * 6 * M;
+            float4 a[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) a[q] = __ldg(reinterpret_cast<const float4*>(tp + q * M));
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+              for (int q = 0; q < 6; ++q) {
+                const float cv = Cv[cc * 6 + q];
+                acc[cc][0] = fmaf(cv, a[q].x, acc[cc][0]);
+                acc[cc][1] = fmaf(cv, a[q].y, acc[cc][1]);
+                acc[cc][2] = fmaf(cv, a[q].z, acc[cc][2]);
+                acc[cc][3] = fmaf(cv, a[q].w, acc[cc][3]);
+              }
+          }
+          __syncwarp();
+          if (lane < 24) cf[lane] = 0.0f;
+        }
+      }
+    }
+    __syncwarp();
+    for (int k = lane; k < nt * ow; k += 32) S.occ[k] = 0u;
+    __syncwarp();
+    if (colok) {
+      float* Ti = T + (size_t)i * 4 * M + cl;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc)
+        *reinterpret_cast<float4*>(Ti + cc * M) =
+            make_float4(acc[cc][0] * ep.inv_nm, acc[cc][1] * ep.inv_nm, acc[cc][2] * ep.inv_nm,
+                        acc[cc][3] * ep.inv_nm);
+    }
+  }
+  nrange = __reduce_add_sync(0xffffffffu, nrange);
+  if (lane == 0 && nrange) atomicAdd(&status[ST_RANGE], nrange);
+  if (lane == 0 && pair_count) atomicAdd(pair_count, npairs);
+}
+
+// sum of 32 per-lane values across the warp; lane l receives the total of
+// value l (a transposing butterfly: 31 shuffles instead of 32 x 5)
+__device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < off; ++k) {
+      const float send = hi ? v[k] : v[k + off];
+      const float keep = hi ? v[k + off] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0];
+}
+
+// ------------------------------------------------------------------ backward
+__global__ void __launch_bounds__(256) k_tab_bwd(int64_t n, const float4* __restrict__ off,
+                                                 const uint32_t* __restrict__ nlist,
+                                                 const int32_t* __restrict__ nn, int cap, CellGeom g,
+                                                 EnvParams ep, const float* __restrict__ table,
+                                                 const float* __restrict__ dT,
+                                                 unsigned long long* __restrict__ ffix,
+                                                 double* __restrict__ vir_part,
+                                                 int32_t* __restrict__ status) {
+  extern __shared__ float4 smem4[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int nt = ep.ntypes, n_int = ep.n_int, M = ep.M, ow = occ_words(n_int);
+  WarpSmem S = warp_smem((float*)smem4 + (size_t)wib * per_warp_words(nt, n_int), nt, n_int);
+  for (int k = lane; k < nt * ow; k += 32) S.occ[k] = 0u;
+  __syncwarp();
+  const int cl = lane * 4;
+  const bool colok = cl < M;
+  double vacc[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) vacc[a] = 0.0;
+  int nbad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * wpb + wib; i < n; i += (int64_t)gridDim.x * wpb) {
+    const float4 oi = off[i];
+    const int ti = __float_as_int(oi.w);
+    const int cnt = min(nn[i], cap);
+    const uint32_t* L = nlist + (size_t)i * cap;
+    // pass A: occupied intervals
+    for (int base = 0; base < cnt; base += 32) {
+      const int k = base + lane;
+      if (k < cnt) {
+        float dx, dy, dz;
+        int tj;
+        load_pair(oi, off, g, L[k], dx, dy, dz, tj);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < ep.rc2) {
+          Pair P;
+          pair_geom(ep, dx, dy, dz, r2, tj, P);
+          atomicOr(&S.occ[tj * ow + (P.th >> 5)], 1u << (P.th & 31));
+        }
+      }
+    }
+    __syncwarp();
+    // pass B: B_k[c][q] for every occupied interval
+    float4 dTv[4];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc)
+      dTv[cc] = colok ? *reinterpret_cast<const float4*>(dT + (size_t)i * 4 * M + cc * M + cl)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int tj = 0; tj < nt; ++tj) {
+      const float* tab = table + ((size_t)(ti * nt + tj) * n_int) * 6 * M + cl;
+      for (int wd = 0; wd < ow; ++wd) {
+        unsigned bits = S.occ[tj * ow + wd];
+        while (bits) {
+          const int th = wd * 32 + __ffs(bits) - 1;
+          bits &= bits - 1u;
+          float v[32];
+#pragma unroll
+          for (int k = 24; k < 32; ++k) v[k] = 0.0f;
+          float4 a[6];
+          const float* tp = tab + (size_t)th * 6 * M;
+#pragma unroll
+          for (int q = 0; q < 6; ++q)
+            a[q] = colok ? __ldg(reinterpret_cast<const float4*>(tp + q * M))
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+              v[cc * 6 + q] = a[q].x * dTv[cc].x + a[q].y * dTv[cc].y + a[q].z * dTv[cc].z +
+                              a[q].w * dTv[cc].w;
+          const float tot = transpose_reduce32(v, lane);
+          if (lane < 24) S.C[(tj * n_int + th) * 24 + lane] = tot * ep.inv_nm;
+        }
+      }
+    }
+    __syncwarp();
+    // pass C: per pair gradient, forces and virial
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    float vl[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) vl[a] = 0.f;
+    for (int base = 0; base < cnt; base += 32) {
+      const int k = base + lane;
+      if (k < cnt) {
+        const uint32_t e = L[k];
+        float dx, dy, dz;
+        int tj;
+        load_pair(oi, off, g, e, dx, dy, dz, tj);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < ep.rc2) {
+          Pair P;
+          pair_geom(ep, dx, dy, dz, r2, tj, P);
+          const float* Bk = S.C + (tj * n_int + P.th) * 24;
+          float Bv[24];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            const float4 t4 = reinterpret_cast<const float4*>(Bk)[q];
+            Bv[4 * q] = t4.x;
+            Bv[4 * q + 1] = t4.y;
+            Bv[4 * q + 2] = t4.z;
+            Bv[4 * q + 3] = t4.w;
+          }
+          const float u = P.u;
+          float gR[4], dgu[4];
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const float* b = Bv + cc * 6;
+            gR[cc] = fmaf(fmaf(fmaf(fmaf(fmaf(b[5], u, b[4]), u, b[3]), u, b[2]), u, b[1]), u, b[0]);
+            dgu[cc] = fmaf(fmaf(fmaf(fmaf(5.0f * b[5], u, 4.0f * b[4]), u, 3.0f * b[3]), u,
+                                2.0f * b[2]),
+                           u, b[1]);
+          }
+          const float ux = P.dx * P.ir, uy = P.dy * P.ir, uz = P.dz * P.ir;
+          const float s = P.s;
+          const float gs = ep.inv_h * (s * dgu[0] + s * ux * dgu[1] + s * uy * dgu[2] +
+                                       s * uz * dgu[3]);
+          const float a0 = gR[0] + gs;
+          const float dot = gR[1] * ux + gR[2] * uy + gR[3] * uz;
+          const float sor = s * P.ir;
+          const float coef = P.dsdr * (a0 + dot) - sor * dot;
+          float gx = coef * ux + sor * gR[1];
+          float gy = coef * uy + sor * gR[2];
+          float gz = coef * uz + sor * gR[3];
+          if (!(isfinite(gx) && isfinite(gy) && isfinite(gz)) || fabsf(gx) > 4.0e6f ||
+              fabsf(gy) > 4.0e6f || fabsf(gz) > 4.0e6f) {
+            ++nbad;
+            gx = gy = gz = 0.0f;
+          }
+          fx += gx;
+          fy += gy;
+          fz += gz;
+          vl[0] -= P.dx * gx;
+          vl[1] -= P.dx * gy;
+          vl[2] -= P.dx * gz;
+          vl[3] -= P.dy * gx;
+          vl[4] -= P.dy * gy;
+          vl[5] -= P.dy * gz;
+          vl[6] -= P.dz * gx;
+          vl[7] -= P.dz * gy;
+          vl[8] -= P.dz * gz;
+          unsigned long long* fj = ffix + (size_t)(e >> 5) * 3;
+          atomicAdd(fj + 0, (unsigned long long)(-__float2ll_rn(gx * DP_FSCALE_F)));
+          atomicAdd(fj + 1, (unsigned long long)(-__float2ll_rn(gy * DP_FSCALE_F)));
+          atomicAdd(fj + 2, (unsigned long long)(-__float2ll_rn(gz * DP_FSCALE_F)));
+        }
+      }
+    }
+    double red[12] = {fx, fy, fz, vl[0], vl[1], vl[2], vl[3], vl[4], vl[5], vl[6], vl[7], vl[8]};
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+      for (int a = 0; a < 12; ++a) red[a] += __shfl_xor_sync(0xffffffffu, red[a], o);
+    if (lane == 0) {
+      unsigned long long* fi = ffix + (size_t)i * 3;
+      atomicAdd(fi + 0, (unsigned long long)__double2ll_rn(red[0] * DP_FSCALE));
+      atomicAdd(fi + 1, (unsigned long long)__double2ll_rn(red[1] * DP_FSCALE));
+      atomicAdd(fi + 2, (unsigned long long)__double2ll_rn(red[2] * DP_FSCALE));
+#pragma unroll
+      for (int a = 0; a < 9; ++a) vacc[a] += red[3 + a];
+    }
+    __syncwarp();
+    for (int k = lane; k < nt * ow; k += 32) S.occ[k] = 0u;
+    __syncwarp();
+  }
+  if (lane == 0) {
+    double* vp = vir_part + ((size_t)blockIdx.x * wpb + wib) * 9;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) vp[a] = vacc[a];
+  }
+  nbad = __reduce_add_sync(0xffffffffu, nbad);
+  if (lane == 0 && nbad) atomicAdd(&status[ST_NONFINITE], nbad);
+}
+
+int g_num_sms = 0;
+int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+constexpr int kWarpsPerBlock = 8;
+
+int tab_blocks(int64_t n) {
+  int64_t want = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  int64_t cap = (int64_t)num_sms() * 8;
+  return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+size_t tab_smem(const EnvParams& ep) {
+  return (size_t)kWarpsPerBlock * per_warp_words(ep.ntypes, ep.n_int) * sizeof(float);
+}
+
+}  // namespace
+
+int tab_kernel_slots(int64_t n) { return tab_blocks(n) * kWarpsPerBlock; }
+
+int table_build(cudaStream_t st, const double* emb64, const int64_t* emb_off, int n_emb,
+                const int* emb_w, int npair, double h, int n_int, float* table_out) {
+  if (n_emb < 1 || n_emb > 6) return -1;
+  int w[6] = {0, 0, 0, 0, 0, 0};
+  int wmax = 0;
+  for (int l = 0; l < n_emb; ++l) {
+    w[l] = emb_w[l];
+    wmax = wmax > w[l] ? wmax : w[l];
+  }
+  if (wmax > 1024) return -1;
+  const int M = w[n_emb - 1];
+  const int n_nodes = n_int + 1;
+  double* node = nullptr;
+  if (cudaMallocAsync(&node, sizeof(double) * (size_t)npair * n_nodes * 3 * M, st) != cudaSuccess)
+    return -2;
+  int threads = ((wmax + 31) / 32) * 32;
+  k_table_nodes<<<npair * n_nodes, threads, sizeof(double) * 6 * wmax, st>>>(
+      emb64, emb_off, n_emb, w[0], w[1], w[2], w[3], w[4], w[5], h, n_nodes, node);
+  int64_t tot = (int64_t)npair * n_int * M;
+  k_table_coef<<<(int)((tot + 255) / 256), 256, 0, st>>>(node, npair, n_int, M, h, table_out);
+  cudaFreeAsync(node, st);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_tab_fwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t* nlist,
+                   const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
+                   const float* table, float* T, int32_t* status,
+                   unsigned long long* pair_count) {
+  if (n <= 0) return 0;
+  if (ep.M > 128 || ep.M % 4) return -1;
+  size_t sm = tab_smem(ep);
+  if (sm > 200 * 1024) return -1;
+  static size_t set_fwd = 0;
+  if (sm > 48 * 1024 && sm > set_fwd) {
+    cudaFuncSetAttribute(k_tab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set_fwd = sm;
+  }
+  k_tab_fwd<<<tab_blocks(n), kWarpsPerBlock * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep, table, T,
+                                                          status, pair_count);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_tab_bwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t* nlist,
+                   const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
+                   const float* table, const float* dT, unsigned long long* ffix,
+                   double* vir_part, int vir_slots, int32_t* status) {
+  if (n <= 0) return 0;
+  if (ep.M > 128 || ep.M % 4) return -1;
+  if (vir_slots < tab_kernel_slots(n)) return -1;
+  size_t sm = tab_smem(ep);
+  if (sm > 200 * 1024) return -1;
+  static size_t set_bwd = 0;
+  if (sm > 48 * 1024 && sm > set_bwd) {
+    cudaFuncSetAttribute(k_tab_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set_bwd = sm;
+  }
+  k_tab_bwd<<<tab_blocks(n), kWarpsPerBlock * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep, table, dT,
+                                                          ffix, vir_part, status);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}

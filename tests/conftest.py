@@ -53,3 +53,15 @@ def water_model_path(model_dir):
 def rmse(a, b):
     a, b = np.asarray(a), np.asarray(b)
     return float(np.sqrt(np.mean((a - b) ** 2))) if a.size else 0.0
+
+
+# measured parity errors, written to $DP_PARITY_REPORT (JSON) when set
+PARITY_LOG = []
+
+
+def pytest_sessionfinish(session, exitstatus):
+    path = os.environ.get("DP_PARITY_REPORT")
+    if path and PARITY_LOG:
+        import json
+        with open(path, "w") as f:
+            json.dump(PARITY_LOG, f, indent=1)

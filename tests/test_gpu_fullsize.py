@@ -1,0 +1,43 @@
+"""Parity at the full benchmark size: FCC copper 100x100x100 cells
+(4,000,000 atoms, 330 K), the configured model, the MD launch configuration
+the bench times (10 velocity-Verlet steps with a list rebuild).  The oracle
+evaluates a sample of atoms one by one: per-atom energies of 2000 atoms and
+the forces on 100 atoms (each from every centre within rc of it)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_01446_gb300 import inputs
+from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, PARITY_LOG, TABLE_H
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fullsize_4m_copper_sampled(cu_model_path):
+    from paper_2201_01446_gb300 import dp
+    x, t, box = inputs.fcc_copper(100, sigma=0.0)
+    v = inputs.maxwell_velocities(np.full(len(x), inputs.MASS_CU), 330.0, seed=2)
+    h = dp.dp_create(cu_model_path, 1, CU_RC, CU_RCS, [CU_SEL], stream=None)
+    try:
+        s = dp.dp_system_create(h, x, v, t, [inputs.MASS_CU], box)
+        dp.dp_md_step(h, s, 10, 1.0)
+        xg, _, fg = dp.dp_system_get(h, s, len(x))
+        dp.dp_system_destroy(s)
+        E, F, V, Ei = dp.dp_compute(h, xg, t, box, atom_energy=True)
+    finally:
+        dp.dp_destroy(h)
+    # the MD force of the last step and a fresh evaluation agree (the
+    # per-step list with skin and the fresh list within rc give one set)
+    assert np.sqrt(((fg - F) ** 2).mean()) < 1e-9
+    m = oracle.Model(cu_model_path)
+    tab = oracle.Table(m, TABLE_H, CU_SMAX)
+    ie = inputs.random_subset(len(x), 2000, seed=11)
+    jf = inputs.random_subset(len(x), 100, seed=12)
+    e_ref, f_ref = oracle.eval_subset(m, tab, CU_RC, CU_RCS, CU_SEL, xg, t, box, ie, jf)
+    de = np.abs(Ei[ie] - e_ref)
+    df = np.sqrt(((F[jf] - f_ref) ** 2).mean())
+    PARITY_LOG.append(dict(case="fullsize Cu 4M (sampled)", natoms=len(x), stress=False,
+                           max_dEi=float(de.max()), force_rmse=float(df),
+                           force_rms=float(np.sqrt((f_ref ** 2).mean()))))
+    assert de.max() < 1e-6
+    assert df < 1e-5
