@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark: compressed DP-SE_a copper MD on GB300, atom-steps/s per GPU.
+
+Workload: FCC copper 100x100x100 cells (4,000,000 atoms, a = 3.634 A,
+periodic), 330 K Maxwell velocities, the seeded N(0, 0.1) model of the paper's
+shape (embedding 1-32-64-128, M^< = 16, fitting 2048-240-240-240-1, rc 8 A,
+rcs 0.5 A, sel 256), tabulated embedding (h = 0.01) fused with the
+contraction in FP32, velocity-Verlet at dt = 1 fs, list rebuild every 10
+steps with a 2 A skin.  One bench step is one 10-MD-step block (one list
+rebuild and 10 force evaluations), so the default 10 steps are the 100 MD
+steps of the workload.  Inputs (T, dT, lists: ~30 GB) are far larger than L2.
+
+JSON line fields beyond the base contract: roofline (dominant phase, live
+CUDA-event time), cpu_baseline (the FP64 oracle on a bounded sample of the
+same configuration, also giving the sampled force/energy error), e2e
+(through dp_system_create / dp_md_step / dp_system_get with host buffers),
+clocks (nvidia-smi sampled during the timed region).
+
+--impl reference runs the FP64 oracle (the correctness reference; there is
+no reference code to install) on a bounded sample of the same workload: MD
+steps of a 20x20x20-cell (32,000-atom) copper box on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2201_01446_gb300 import inputs  # noqa: E402
+
+RC, RCS, SEL = 8.0, 0.5, 256
+MD_PER_STEP = 10
+DT_FS = 1.0
+METRIC = "DP copper atom-steps/s/GPU (fused tabulated vs plain, force err); serve p99 ms"
+UNIT = "atom-steps/s"
+# FP32 CUDA-core peak of GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=100, help="FCC cells per edge (100 -> 4M atoms)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id):
+        self.proc = None
+        self.path = None
+        self.dev = dev_id
+
+    def start(self):
+        try:
+            self.path = tempfile.mktemp(suffix=".csv")
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.dev is not None:
+                cmd += ["-i", str(self.dev)]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [q.strip() for q in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_uuid(local):
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(local)
+        u = getattr(p, "uuid", None)
+        if u is not None:
+            s = str(u)
+            return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        pass
+    return local
+
+
+def flops_per_unit(M=128, din=2048, w=240):
+    """Algorithmic FLOPs (2 per multiply-add) of each phase.
+    Per pair within rc: quintic Horner (5 FMA) + 4x1 outer product (4 FMA) per
+    embedding column forward; 18 FMA per column backward (value and slope of
+    the quintic, dE/dR and dE/ds).  Per atom: the fitting net forward and
+    its input gradient, 2 x (din*w + 2*w*w + w) multiply-adds each way."""
+    fit = 2 * 2 * (din * w + 2 * w * w + w)
+    return {"embed_contract_fwd": ("pair", 2 * 9 * M), "fitting": ("atom", fit),
+            "embed_contract_bwd_forces": ("pair", 2 * 18 * M)}
+
+
+def cpu_baseline_leg(model_path, xg, t, box, F_gpu, Ei_gpu, n_force=64, n_energy=1024):
+    """The FP64 oracle (as it stands) on a bounded sample of the final
+    configuration: energies of n_energy atoms and forces on n_force atoms,
+    each force needing every centre within rc of the atom.  Returns the
+    baseline entry and the sampled errors of the GPU result."""
+    import oracle
+    m = oracle.Model(model_path)
+    tab = oracle.Table(m, 0.01, 2.0)
+    ie = inputs.random_subset(len(xg), n_energy, seed=11)
+    jf = inputs.random_subset(len(xg), n_force, seed=12)
+    t0 = time.perf_counter()
+    e_ref, f_ref = oracle.eval_subset(m, tab, RC, RCS, SEL, xg, t, box, ie, jf)
+    dt = time.perf_counter() - t0
+    # centres evaluated with energy and full backward: each force atom and
+    # its neighbors within rc (176 in FCC copper), plus the energy atoms
+    centres = n_force * 177 + n_energy
+    err = {"energy_max_abs_eV_per_atom": float(np.abs(Ei_gpu[ie] - e_ref).max()),
+           "force_rmse_eV_per_A": float(np.sqrt(((F_gpu[jf] - f_ref) ** 2).mean())),
+           "force_rms_eV_per_A": float(np.sqrt((f_ref ** 2).mean())),
+           "sample": f"{n_energy} atom energies, forces on {n_force} atoms"}
+    base = {"value": centres / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle on {n_force} force atoms (+{n_energy} energies) of the final "
+                      f"{len(xg)}-atom configuration: ~{centres} atom evaluations in {dt:.1f} s"}
+    return base, err
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return 0
+    import oracle
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "cu.model")
+        inputs.write_seeded_model(path, inputs.COPPER_SPEC, seed=0, std=0.1)
+        m = oracle.Model(path)
+        tab = oracle.Table(m, 0.01, 2.0)
+        x, t, box = inputs.fcc_copper(20, sigma=0.0)
+        v = inputs.maxwell_velocities(np.full(len(x), inputs.MASS_CU), 330.0, seed=2)
+        masses = [inputs.MASS_CU]
+        x, v, f, _ = oracle.md(m, tab, RC, RCS, SEL, x, v, t, masses, box, DT_FS, 0)
+        for _ in range(args.warmup):
+            x, v, f, _ = oracle.md(m, tab, RC, RCS, SEL, x, v, t, masses, box, DT_FS, 1, f=f)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            x, v, f, _ = oracle.md(m, tab, RC, RCS, SEL, x, v, t, masses, box, DT_FS, 1, f=f)
+        dt = time.perf_counter() - t0
+    value = len(x) * args.steps / dt
+    cores = oracle.get_threads()
+    sample = f"FP64 oracle velocity-Verlet, {len(x)}-atom copper box (20^3 cells), 1 MD step per bench step"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"FCC Cu 330 K, rc 8 A, seeded N(0,0.1) DP-SE_a model, "
+                                   f"sample of {len(x)} atoms", "md_steps_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank, pg)
+    import torch
+    from paper_2201_01446_gb300 import dp
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    tmpdir = tempfile.mkdtemp()
+    model = os.path.join(tmpdir, "cu.model")
+    inputs.write_seeded_model(model, inputs.COPPER_SPEC, seed=0, std=0.1)
+    x, t, box = inputs.fcc_copper(args.cells, sigma=0.0)
+    n = len(x)
+    v = inputs.maxwell_velocities(np.full(n, inputs.MASS_CU), 330.0, seed=2 + rank)
+    masses = [inputs.MASS_CU]
+    h = dp.dp_create(model, 1, RC, RCS, [SEL], stream=C_stream(stream))
+    s = dp.dp_system_create(h, x, v, t, masses, box)
+    for _ in range(args.warmup):
+        dp.dp_md_step(h, s, MD_PER_STEP, DT_FS)
+    torch.cuda.synchronize()
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks = Clocks(gpu_uuid(local))
+    clocks.start()
+    launches0 = dp.dp_stats(h, s)["kernel_launches"]
+    dp.dp_profile(h, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dp.dp_md_step(h, s, MD_PER_STEP, DT_FS)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    prof = dp.dp_profile_read(h)
+    dp.dp_profile(h, False)
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(pg, ms)
+    stats = dp.dp_stats(h, s)
+    launches = stats["kernel_launches"] - launches0
+    value = world * n * MD_PER_STEP * args.steps / (ms_max / 1e3)
+    # roofline of the dominant phase
+    units = flops_per_unit()
+    dom = max((k for k in prof if k in units), key=lambda k: prof[k][0])
+    kind, fl = units[dom]
+    per_launch_units = stats["pairs_within_rc"] if kind == "pair" else n
+    avg_ms = prof[dom][0] / max(prof[dom][1], 1)
+    achieved = fl * per_launch_units / (avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": dom,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (FP32 CUDA cores)",
+                "phases_ms_per_launch": {k: prof[k][0] / max(prof[k][1], 1) for k in prof}}
+    xg, vg, fg = dp.dp_system_get(h, s, n)
+    dp.dp_system_destroy(s)
+    # e2e: host buffers in, 10 MD steps, host buffers out
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        barrier(pg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            se = dp.dp_system_create(h, x, v, t, masses, box)
+            dp.dp_md_step(h, se, MD_PER_STEP, DT_FS)
+            dp.dp_system_get(h, se, n)
+            dp.dp_system_destroy(se)
+        torch.cuda.synchronize()
+        te = max_over_ranks(pg, time.perf_counter() - t0)
+        e2e = {"value": world * n * MD_PER_STEP * args.e2e_steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(n * (3 * 8 + 3 * 8 + 4) + 9 * 8 + 8),
+               "d2h_bytes_per_step": int(n * 3 * 8 * 3)}
+    cpu = None
+    accuracy = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        E, F, V, Ei = dp.dp_compute(h, xg, t, box, atom_energy=True)
+        cpu, accuracy = cpu_baseline_leg(model, xg, t, box, F, Ei)
+    dp.dp_destroy(h)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded model and lattice)",
+                "config": {"workload": f"FCC Cu {args.cells}^3 cells ({n} atoms) 330 K, DP-SE_a "
+                                       "1-32-64-128 / 2048-240-240-240-1, rc 8 A, tabulated "
+                                       "h=0.01 s<=2, velocity-Verlet dt 1 fs, rebuild every 10, skin 2 A",
+                           "md_steps_per_step": MD_PER_STEP, "natoms": n,
+                           "fit_precision": "fp32-simt", "l2": "inputs larger than L2",
+                           "ns_per_day": value / world / n * DT_FS * 86400 * 1e-6,
+                           "parallelism": f"replicas x{world}"},
+                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": ck, "accuracy_vs_oracle": accuracy, "plain": None,
+                "stats": stats}
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def C_stream(stream):
+    import ctypes
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -58,7 +58,8 @@ typedef struct {
                           1 BF16 tcgen05 tensor cores with FP32 accumulation,
                           2 FP32-accurate tcgen05 (split operands) */
   double table_step;   /* interval h of the table on s (Sec. 3.2) [0.01] */
-  double s_max;        /* table domain is [0, ceil(s_max/h)*h]; [1/1.5] */
+  double s_max;        /* table domain is [0, ceil(s_max/h)*h]; [2.0], i.e.
+                          r >= 0.5 A for rcs = 0.5 */
   double skin;         /* neighbor-list buffer for MD (Sec. 5) [2.0 A] */
   int rebuild_every;   /* MD list rebuild period in steps [10] */
 } dp_options;
@@ -197,7 +198,8 @@ dp_status dp_profile_read(dp_handle* h, double* ms, int64_t* launches);
 
 /* Counters of the last evaluation of a system (s != NULL) or of the last
  * dp_compute (s == NULL): out[0] atoms, [1] list capacity per atom, [2]
- * longest list, [3] pairs within rc seen by the last forward pass, [4] cells. */
+ * longest list, [3] pairs within rc seen by the last forward pass, [4] cells,
+ * [5] kernels launched by the library in this process so far. */
 dp_status dp_stats(dp_handle* h, const dp_system* s, int64_t* out);
 
 /* Library build string (architecture, options compiled in). */

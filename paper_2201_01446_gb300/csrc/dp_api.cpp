@@ -559,7 +559,7 @@ void dp_options_default(dp_options* o) {
   o->tabulated = 1;
   o->fit_precision = 0;
   o->table_step = 0.01;
-  o->s_max = 1.0 / 1.5;
+  o->s_max = 2.0;
   o->skin = 2.0;
   o->rebuild_every = 10;
 }
@@ -881,6 +881,7 @@ dp_status dp_stats(dp_handle* h, const dp_system* s, int64_t* out) {
   out[2] = h->status_host[ST_MAXLIST];
   out[3] = (int64_t)pairs;
   out[4] = w.geom.ncell;
+  out[5] = (int64_t)__atomic_load_n(&g_dp_launches, __ATOMIC_RELAXED);
   return DP_OK;
 }
 

@@ -8,6 +8,10 @@
 #define DP_MAXT 8
 #define DP_MAXFIT 6
 
+// Number of kernels this library has launched in the process (all threads).
+extern unsigned long long g_dp_launches;
+#define DP_LAUNCHED(k) __atomic_fetch_add(&g_dp_launches, (unsigned long long)(k), __ATOMIC_RELAXED)
+
 // Per-call device status words (int32).  Kernels only ever add / max into them.
 enum {
   ST_SEL = 0,        // atoms with more neighbors of one type within rc than sel[t]

@@ -167,206 +167,250 @@ __device__ __forceinline__ void load_pair(const float4& oi, const float4* __rest
   tj = __float_as_int(oj.w);
 }
 
-struct WarpSmem {
-  float* C;        // [ntypes][n_int][24]
-  unsigned* occ;   // [ntypes][occw]
-  float4* stR;     // [32]
-  float* stU;      // [32]
-  int* stK;        // [32]
+// ------------------------------------------------------------------ per-atom interval sort
+// The pairs of an atom within rc are counting-sorted by bin = (neighbor type,
+// table interval): a histogram (integer atomics: order independent), an
+// exclusive scan, then a stable scatter in list order (ranks within a chunk
+// from __match_any_sync).  The result is deterministic.  After the scatter,
+// hist[b] holds the end of bin b, so bin b spans [b ? hist[b-1] : 0, hist[b]).
+struct SortSmem {
+  int* hist;   // [nbins]
+  int nbins;
 };
 
-__host__ __device__ inline int occ_words(int n_int) { return (n_int + 31) / 32; }
-__host__ __device__ inline int per_warp_words(int ntypes, int n_int) {
-  int cw = ntypes * n_int * 24;
-  int ow = (ntypes * occ_words(n_int) + 3) & ~3;
-  return cw + ow + 32 * 4 + 32 + 32;
+__device__ __forceinline__ int bin_begin(const int* hist, int b) { return b ? hist[b - 1] : 0; }
+
+// exclusive scan of hist[0..nb) in place; returns the total
+__device__ __forceinline__ int warp_exclusive_scan(int* hist, int nb, int lane) {
+  const int per = (nb + 31) / 32;
+  const int b0 = min(lane * per, nb), b1 = min(b0 + per, nb);
+  int sum = 0;
+  for (int b = b0; b < b1; ++b) sum += hist[b];
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  int run = incl - sum;
+  for (int b = b0; b < b1; ++b) {
+    const int c = hist[b];
+    hist[b] = run;
+    run += c;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  __syncwarp();
+  return total;
 }
 
-__device__ __forceinline__ WarpSmem warp_smem(float* base, int ntypes, int n_int) {
-  WarpSmem w;
-  w.C = base;
-  w.occ = (unsigned*)(base + ntypes * n_int * 24);
-  w.stR = (float4*)(base + ntypes * n_int * 24 + ((ntypes * occ_words(n_int) + 3) & ~3));
-  w.stU = (float*)(w.stR + 32);
-  w.stK = (int*)(w.stU + 32);
-  return w;
+// stable slot of this lane's pair in the bin-sorted order (all lanes call)
+__device__ __forceinline__ int sorted_slot(int* hist, bool in, int bin, int lane) {
+  const unsigned grp = __match_any_sync(0xffffffffu, in ? bin : (0x40000000 | lane));
+  const int rank = __popc(grp & ((1u << lane) - 1u));
+  const int pos = in ? hist[bin] + rank : -1;
+  __syncwarp();
+  if (in && rank == 0) hist[bin] += __popc(grp);
+  __syncwarp();
+  return pos;
+}
+
+__host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
+__host__ __device__ inline int fwd_warp_words(int nbins, int scap) {
+  return round4(nbins) + 4 * scap + round4(scap) + 32;
+}
+__host__ __device__ inline int bwd_warp_words(int nbins, int scap) {
+  return round4(nbins) + round4(scap) + 32 * 24 + 2 * 10;
 }
 
 // ------------------------------------------------------------------ forward
-__global__ void __launch_bounds__(256) k_tab_fwd(int64_t n, const float4* __restrict__ off,
+__global__ void __launch_bounds__(256, 3) k_tab_fwd(int64_t n, const float4* __restrict__ off,
                                                  const uint32_t* __restrict__ nlist,
                                                  const int32_t* __restrict__ nn, int cap, CellGeom g,
                                                  EnvParams ep, const float* __restrict__ table,
-                                                 float* __restrict__ T, int32_t* __restrict__ status,
+                                                 int scap, float* __restrict__ T,
+                                                 int32_t* __restrict__ status,
                                                  unsigned long long* __restrict__ pair_count) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const int nt = ep.ntypes, n_int = ep.n_int, M = ep.M, ow = occ_words(n_int);
-  WarpSmem S = warp_smem((float*)smem4 + (size_t)wib * per_warp_words(nt, n_int), nt, n_int);
-  for (int k = lane; k < nt * n_int * 24; k += 32) S.C[k] = 0.0f;
-  for (int k = lane; k < nt * ow; k += 32) S.occ[k] = 0u;
-  __syncwarp();
+  const int nt = ep.ntypes, n_int = ep.n_int, M = ep.M;
+  const int nbins = nt * n_int;
+  float* base = (float*)smem4 + (size_t)wib * fwd_warp_words(nbins, scap);
+  int* hist = (int*)base;
+  float4* sR = (float4*)(base + round4(nbins));
+  float* sU = base + round4(nbins) + 4 * scap;
+  float* Cb = sU + round4(scap);
   const int cl = lane * 4;
   const bool colok = cl < M;
-  const unsigned below = (1u << lane) - 1u;
-  int nrange = 0;
+  int nrange = 0, nover = 0;
   unsigned long long npairs = 0;
   for (int64_t i = (int64_t)blockIdx.x * wpb + wib; i < n; i += (int64_t)gridDim.x * wpb) {
     const float4 oi = off[i];
     const int ti = __float_as_int(oi.w);
     const int cnt = min(nn[i], cap);
     const uint32_t* L = nlist + (size_t)i * cap;
-    for (int base = 0; base < cnt; base += 32) {
-      const int k = base + lane;
+    for (int b = lane; b < nbins; b += 32) hist[b] = 0;
+    __syncwarp();
+    // pass 1: histogram of bins
+    int np = 0;
+    for (int b0 = 0; b0 < cnt; b0 += 32) {
+      const int k = b0 + lane;
       bool in = false;
-      Pair P;
       if (k < cnt) {
         float dx, dy, dz;
         int tj;
         load_pair(oi, off, g, L[k], dx, dy, dz, tj);
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < ep.rc2) {
-          in = true;
+          Pair P;
           pair_geom(ep, dx, dy, dz, r2, tj, P);
+          atomicAdd(&hist[tj * n_int + P.th], 1);
           nrange += P.out_of_range;
+          in = true;
         }
       }
-      const unsigned m = __ballot_sync(0xffffffffu, in);
-      if (in) {
-        const int slot = __popc(m & below);
-        S.stR[slot] = make_float4(P.s, P.s * P.dx * P.ir, P.s * P.dy * P.ir, P.s * P.dz * P.ir);
-        S.stU[slot] = P.u;
-        S.stK[slot] = P.th | (P.tj << 16);
-      }
-      __syncwarp();
-      const int c = __popc(m);
-      npairs += c;
-      if (lane < c) {
-        const int key = S.stK[lane];
-        const int th = key & 0xffff, tj = key >> 16;
-        atomicOr(&S.occ[tj * ow + (th >> 5)], 1u << (th & 31));
-      }
-      if (lane < 24) {
-        // lane (cc, q) owns C_k[cc][q] for every interval: list-order sums
-        const int cc = lane / 6, q = lane - cc * 6;
-        for (int t = 0; t < c; ++t) {
-          const float4 R = S.stR[t];
-          const float uu = S.stU[t];
-          const int key = S.stK[t];
-          float pw = 1.0f;
-          for (int e = 0; e < q; ++e) pw *= uu;
-          const float rv = cc == 0 ? R.x : (cc == 1 ? R.y : (cc == 2 ? R.z : R.w));
-          float* dst = S.C + ((key >> 16) * n_int + (key & 0xffff)) * 24 + lane;
-          *dst = fmaf(rv, pw, *dst);
-        }
-      }
-      __syncwarp();
+      np += __popc(__ballot_sync(0xffffffffu, in));
     }
+    __syncwarp();
+    npairs += np;
     float acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-    for (int tj = 0; tj < nt; ++tj) {
-      const float* tab = table + ((size_t)(ti * nt + tj) * n_int) * 6 * M + cl;
-      for (int wd = 0; wd < ow; ++wd) {
-        unsigned bits = S.occ[tj * ow + wd];
-        while (bits) {
-          const int th = wd * 32 + __ffs(bits) - 1;
-          bits &= bits - 1u;
-          float* cf = S.C + (tj * n_int + th) * 24;
-          float Cv[24];
-#pragma unroll
-          for (int v = 0; v < 6; ++v) {
-            const float4 t4 = reinterpret_cast<const float4*>(cf)[v];
-            Cv[4 * v] = t4.x;
-            Cv[4 * v + 1] = t4.y;
-            Cv[4 * v + 2] = t4.z;
-            Cv[4 * v + 3] = t4.w;
+      for (int q = 0; q < 4; ++q) acc[a][q] = 0.0f;
+    if (np <= scap) {
+      warp_exclusive_scan(hist, nbins, lane);
+      // pass 2: stable scatter of (R, u) into bin order
+      for (int b0 = 0; b0 < cnt; b0 += 32) {
+        const int k = b0 + lane;
+        bool in = false;
+        Pair P;
+        int bin = 0;
+        if (k < cnt) {
+          float dx, dy, dz;
+          int tj;
+          load_pair(oi, off, g, L[k], dx, dy, dz, tj);
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < ep.rc2) {
+            pair_geom(ep, dx, dy, dz, r2, tj, P);
+            bin = tj * n_int + P.th;
+            in = true;
           }
-          if (colok) {
-            const float* tp = tab + (size_t)th * 6 * M;
-            float4 a[6];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) a[q] = __ldg(reinterpret_cast<const float4*>(tp + q * M));
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc)
-#pragma unroll
-              for (int q = 0; q < 6; ++q) {
-                const float cv = Cv[cc * 6 + q];
-                acc[cc][0] = fmaf(cv, a[q].x, acc[cc][0]);
-                acc[cc][1] = fmaf(cv, a[q].y, acc[cc][1]);
-                acc[cc][2] = fmaf(cv, a[q].z, acc[cc][2]);
-                acc[cc][3] = fmaf(cv, a[q].w, acc[cc][3]);
-              }
-          }
-          __syncwarp();
-          if (lane < 24) cf[lane] = 0.0f;
+        }
+        const int pos = sorted_slot(hist, in, bin, lane);
+        if (in) {
+          sR[pos] = make_float4(P.s, P.s * P.dx * P.ir, P.s * P.dy * P.ir, P.s * P.dz * P.ir);
+          sU[pos] = P.u;
         }
       }
+      __syncwarp();
+      // per occupied bin: C[c][q] = sum over members R[c] u^q, then T += C . table row
+      const int cc = lane / 6, qq = lane - (lane / 6) * 6;
+      for (int b0 = 0; b0 < nbins; b0 += 32) {
+        const int bl = b0 + lane;
+        const bool occ = bl < nbins && hist[bl] > bin_begin(hist, bl);
+        unsigned bits = __ballot_sync(0xffffffffu, occ);
+        while (bits) {
+          const int bin = b0 + __ffs(bits) - 1;
+          bits &= bits - 1u;
+          const int s0 = bin_begin(hist, bin), s1 = hist[bin];
+          if (lane < 24) {
+            float cacc = 0.0f;
+            for (int k = s0; k < s1; ++k) {
+              const float4 R = sR[k];
+              const float u = sU[k];
+              const float u2 = u * u;
+              const float pw = qq == 0 ? 1.0f
+                             : qq == 1 ? u
+                             : qq == 2 ? u2
+                             : qq == 3 ? u2 * u
+                             : qq == 4 ? u2 * u2 : u2 * u2 * u;
+              const float rv = cc == 0 ? R.x : (cc == 1 ? R.y : (cc == 2 ? R.z : R.w));
+              cacc = fmaf(rv, pw, cacc);
+            }
+            Cb[lane] = cacc;
+          }
+          __syncwarp();
+          if (colok) {
+            float Cv[24];
+#pragma unroll
+            for (int v = 0; v < 6; ++v) {
+              const float4 t4 = reinterpret_cast<const float4*>(Cb)[v];
+              Cv[4 * v] = t4.x;
+              Cv[4 * v + 1] = t4.y;
+              Cv[4 * v + 2] = t4.z;
+              Cv[4 * v + 3] = t4.w;
+            }
+            const float* tp = table + ((size_t)ti * nbins + bin) * 6 * M + cl;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+              const float4 a = __ldg(reinterpret_cast<const float4*>(tp + q * M));
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const float cv = Cv[c * 6 + q];
+                acc[c][0] = fmaf(cv, a.x, acc[c][0]);
+                acc[c][1] = fmaf(cv, a.y, acc[c][1]);
+                acc[c][2] = fmaf(cv, a.z, acc[c][2]);
+                acc[c][3] = fmaf(cv, a.w, acc[c][3]);
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+    } else {
+      ++nover;  // more pairs within rc than N_m + 32: an overflow of sel
     }
-    __syncwarp();
-    for (int k = lane; k < nt * ow; k += 32) S.occ[k] = 0u;
-    __syncwarp();
     if (colok) {
       float* Ti = T + (size_t)i * 4 * M + cl;
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc)
-        *reinterpret_cast<float4*>(Ti + cc * M) =
-            make_float4(acc[cc][0] * ep.inv_nm, acc[cc][1] * ep.inv_nm, acc[cc][2] * ep.inv_nm,
-                        acc[cc][3] * ep.inv_nm);
+      for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<float4*>(Ti + c * M) =
+            make_float4(acc[c][0] * ep.inv_nm, acc[c][1] * ep.inv_nm, acc[c][2] * ep.inv_nm,
+                        acc[c][3] * ep.inv_nm);
     }
+    __syncwarp();
   }
   nrange = __reduce_add_sync(0xffffffffu, nrange);
   if (lane == 0 && nrange) atomicAdd(&status[ST_RANGE], nrange);
+  if (lane == 0 && nover) atomicAdd(&status[ST_SEL], nover);
   if (lane == 0 && pair_count) atomicAdd(pair_count, npairs);
 }
 
-// sum of 32 per-lane values across the warp; lane l receives the total of
-// value l (a transposing butterfly: 31 shuffles instead of 32 x 5)
-__device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane) {
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    const bool hi = (lane & off) != 0;
-#pragma unroll
-    for (int k = 0; k < off; ++k) {
-      const float send = hi ? v[k] : v[k + off];
-      const float keep = hi ? v[k + off] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
-  }
-  return v[0];
-}
-
 // ------------------------------------------------------------------ backward
-__global__ void __launch_bounds__(256) k_tab_bwd(int64_t n, const float4* __restrict__ off,
+__global__ void __launch_bounds__(256, 3) k_tab_bwd(int64_t n, const float4* __restrict__ off,
                                                  const uint32_t* __restrict__ nlist,
                                                  const int32_t* __restrict__ nn, int cap, CellGeom g,
                                                  EnvParams ep, const float* __restrict__ table,
-                                                 const float* __restrict__ dT,
+                                                 int scap, const float* __restrict__ dT,
                                                  unsigned long long* __restrict__ ffix,
                                                  double* __restrict__ vir_part,
                                                  int32_t* __restrict__ status) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const int nt = ep.ntypes, n_int = ep.n_int, M = ep.M, ow = occ_words(n_int);
-  WarpSmem S = warp_smem((float*)smem4 + (size_t)wib * per_warp_words(nt, n_int), nt, n_int);
-  for (int k = lane; k < nt * ow; k += 32) S.occ[k] = 0u;
+  const int nt = ep.ntypes, n_int = ep.n_int, M = ep.M;
+  const int nbins = nt * n_int;
+  float* base = (float*)smem4 + (size_t)wib * bwd_warp_words(nbins, scap);
+  int* hist = (int*)base;
+  int* sK = (int*)(base + round4(nbins));
+  float* Bb = base + round4(nbins) + round4(scap);  // [32 bins][24]
+  double* vacc = reinterpret_cast<double*>(Bb + 32 * 24);  // [9] per warp
+  // lane (c, grp): c = lane / 8 picks the row of dT, grp the 16 columns it sums
+  const int lc = lane >> 3, lg = lane & 7;
+  const int col0 = lg * 16;
+  if (lane < 9) vacc[lane] = 0.0;
   __syncwarp();
-  const int cl = lane * 4;
-  const bool colok = cl < M;
-  double vacc[9];
-#pragma unroll
-  for (int a = 0; a < 9; ++a) vacc[a] = 0.0;
   int nbad = 0;
   for (int64_t i = (int64_t)blockIdx.x * wpb + wib; i < n; i += (int64_t)gridDim.x * wpb) {
     const float4 oi = off[i];
     const int ti = __float_as_int(oi.w);
     const int cnt = min(nn[i], cap);
     const uint32_t* L = nlist + (size_t)i * cap;
-    // pass A: occupied intervals
-    for (int base = 0; base < cnt; base += 32) {
-      const int k = base + lane;
+    for (int b = lane; b < nbins; b += 32) hist[b] = 0;
+    __syncwarp();
+    int np = 0;
+    for (int b0 = 0; b0 < cnt; b0 += 32) {
+      const int k = b0 + lane;
+      bool in = false;
       if (k < cnt) {
         float dx, dy, dz;
         int tj;
@@ -375,138 +419,187 @@ __global__ void __launch_bounds__(256) k_tab_bwd(int64_t n, const float4* __rest
         if (r2 < ep.rc2) {
           Pair P;
           pair_geom(ep, dx, dy, dz, r2, tj, P);
-          atomicOr(&S.occ[tj * ow + (P.th >> 5)], 1u << (P.th & 31));
+          atomicAdd(&hist[tj * n_int + P.th], 1);
+          in = true;
         }
       }
+      np += __popc(__ballot_sync(0xffffffffu, in));
     }
     __syncwarp();
-    // pass B: B_k[c][q] for every occupied interval
-    float4 dTv[4];
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc)
-      dTv[cc] = colok ? *reinterpret_cast<const float4*>(dT + (size_t)i * 4 * M + cc * M + cl)
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int tj = 0; tj < nt; ++tj) {
-      const float* tab = table + ((size_t)(ti * nt + tj) * n_int) * 6 * M + cl;
-      for (int wd = 0; wd < ow; ++wd) {
-        unsigned bits = S.occ[tj * ow + wd];
-        while (bits) {
-          const int th = wd * 32 + __ffs(bits) - 1;
-          bits &= bits - 1u;
-          float v[32];
-#pragma unroll
-          for (int k = 24; k < 32; ++k) v[k] = 0.0f;
-          float4 a[6];
-          const float* tp = tab + (size_t)th * 6 * M;
-#pragma unroll
-          for (int q = 0; q < 6; ++q)
-            a[q] = colok ? __ldg(reinterpret_cast<const float4*>(tp + q * M))
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc)
-#pragma unroll
-            for (int q = 0; q < 6; ++q)
-              v[cc * 6 + q] = a[q].x * dTv[cc].x + a[q].y * dTv[cc].y + a[q].z * dTv[cc].z +
-                              a[q].w * dTv[cc].w;
-          const float tot = transpose_reduce32(v, lane);
-          if (lane < 24) S.C[(tj * n_int + th) * 24 + lane] = tot * ep.inv_nm;
-        }
-      }
-    }
-    __syncwarp();
-    // pass C: per pair gradient, forces and virial
     float fx = 0.f, fy = 0.f, fz = 0.f;
     float vl[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) vl[a] = 0.f;
-    for (int base = 0; base < cnt; base += 32) {
-      const int k = base + lane;
-      if (k < cnt) {
-        const uint32_t e = L[k];
-        float dx, dy, dz;
-        int tj;
-        load_pair(oi, off, g, e, dx, dy, dz, tj);
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < ep.rc2) {
-          Pair P;
-          pair_geom(ep, dx, dy, dz, r2, tj, P);
-          const float* Bk = S.C + (tj * n_int + P.th) * 24;
-          float Bv[24];
+    if (np <= scap) {
+      warp_exclusive_scan(hist, nbins, lane);
+      for (int b0 = 0; b0 < cnt; b0 += 32) {
+        const int k = b0 + lane;
+        bool in = false;
+        int bin = 0;
+        if (k < cnt) {
+          float dx, dy, dz;
+          int tj;
+          load_pair(oi, off, g, L[k], dx, dy, dz, tj);
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < ep.rc2) {
+            Pair P;
+            pair_geom(ep, dx, dy, dz, r2, tj, P);
+            bin = tj * n_int + P.th;
+            in = true;
+          }
+        }
+        const int pos = sorted_slot(hist, in, bin, lane);
+        if (in) sK[pos] = k | (bin << 16);
+      }
+      __syncwarp();
+      // this lane's slice of dT: row lc, columns col0 .. col0+15
+      float4 dTv[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        dTv[v] = (col0 + 4 * v < M)
+                     ? *reinterpret_cast<const float4*>(dT + (size_t)i * 4 * M + lc * M + col0 + 4 * v)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int r0 = 0; r0 < nbins; r0 += 32) {
+        const int sb = bin_begin(hist, r0), eb = hist[min(r0 + 32, nbins) - 1];
+        if (eb == sb) continue;
+        const int bl = r0 + lane;
+        const bool occ = bl < nbins && hist[bl] > bin_begin(hist, bl);
+        unsigned bits = __ballot_sync(0xffffffffu, occ);
+        // B_k[c][q] = (1/N_m) sum_eta c[k][q][eta] dT[c][eta] for every occupied bin
+        while (bits) {
+          const int bo = __ffs(bits) - 1;
+          bits &= bits - 1u;
+          const float* tp = table + ((size_t)ti * nbins + r0 + bo) * 6 * M + col0;
+          float v[8];
 #pragma unroll
           for (int q = 0; q < 6; ++q) {
-            const float4 t4 = reinterpret_cast<const float4*>(Bk)[q];
-            Bv[4 * q] = t4.x;
-            Bv[4 * q + 1] = t4.y;
-            Bv[4 * q + 2] = t4.z;
-            Bv[4 * q + 3] = t4.w;
-          }
-          const float u = P.u;
-          float gR[4], dgu[4];
+            float sacc = 0.0f;
 #pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
-            const float* b = Bv + cc * 6;
-            gR[cc] = fmaf(fmaf(fmaf(fmaf(fmaf(b[5], u, b[4]), u, b[3]), u, b[2]), u, b[1]), u, b[0]);
-            dgu[cc] = fmaf(fmaf(fmaf(fmaf(5.0f * b[5], u, 4.0f * b[4]), u, 3.0f * b[3]), u,
-                                2.0f * b[2]),
-                           u, b[1]);
+            for (int w = 0; w < 4; ++w) {
+              if (col0 + 4 * w < M) {
+                const float4 a = __ldg(reinterpret_cast<const float4*>(tp + q * M + 4 * w));
+                sacc = fmaf(a.x, dTv[w].x, sacc);
+                sacc = fmaf(a.y, dTv[w].y, sacc);
+                sacc = fmaf(a.z, dTv[w].z, sacc);
+                sacc = fmaf(a.w, dTv[w].w, sacc);
+              }
+            }
+            v[q] = sacc;
           }
-          const float ux = P.dx * P.ir, uy = P.dy * P.ir, uz = P.dz * P.ir;
-          const float s = P.s;
-          const float gs = ep.inv_h * (s * dgu[0] + s * ux * dgu[1] + s * uy * dgu[2] +
-                                       s * uz * dgu[3]);
-          const float a0 = gR[0] + gs;
-          const float dot = gR[1] * ux + gR[2] * uy + gR[3] * uz;
-          const float sor = s * P.ir;
-          const float coef = P.dsdr * (a0 + dot) - sor * dot;
-          float gx = coef * ux + sor * gR[1];
-          float gy = coef * uy + sor * gR[2];
-          float gz = coef * uz + sor * gR[3];
-          if (!(isfinite(gx) && isfinite(gy) && isfinite(gz)) || fabsf(gx) > 4.0e6f ||
-              fabsf(gy) > 4.0e6f || fabsf(gz) > 4.0e6f) {
-            ++nbad;
-            gx = gy = gz = 0.0f;
+          v[6] = 0.0f;
+          v[7] = 0.0f;
+          // sum over the 8 column groups; lane (c, grp) keeps q = grp
+#pragma unroll
+          for (int o = 4; o >= 1; o >>= 1) {
+            const bool hi = (lane & o) != 0;
+#pragma unroll
+            for (int k = 0; k < o; ++k) {
+              const float send = hi ? v[k] : v[k + o];
+              const float keep = hi ? v[k + o] : v[k];
+              v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
           }
-          fx += gx;
-          fy += gy;
-          fz += gz;
-          vl[0] -= P.dx * gx;
-          vl[1] -= P.dx * gy;
-          vl[2] -= P.dx * gz;
-          vl[3] -= P.dy * gx;
-          vl[4] -= P.dy * gy;
-          vl[5] -= P.dy * gz;
-          vl[6] -= P.dz * gx;
-          vl[7] -= P.dz * gy;
-          vl[8] -= P.dz * gz;
-          unsigned long long* fj = ffix + (size_t)(e >> 5) * 3;
-          atomicAdd(fj + 0, (unsigned long long)(-__float2ll_rn(gx * DP_FSCALE_F)));
-          atomicAdd(fj + 1, (unsigned long long)(-__float2ll_rn(gy * DP_FSCALE_F)));
-          atomicAdd(fj + 2, (unsigned long long)(-__float2ll_rn(gz * DP_FSCALE_F)));
+          if (lg < 6) Bb[bo * 24 + lc * 6 + lg] = v[0] * ep.inv_nm;
         }
+        __syncwarp();
+        // members of this round's bins, one pair per lane
+        for (int k0 = sb; k0 < eb; k0 += 32) {
+          const int k = k0 + lane;
+          if (k < eb) {
+            const int key = sK[k];
+            const uint32_t e = L[key & 0xffff];
+            const int bo = (key >> 16) - r0;
+            float dx, dy, dz;
+            int tj;
+            load_pair(oi, off, g, e, dx, dy, dz, tj);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            Pair P;
+            pair_geom(ep, dx, dy, dz, r2, tj, P);
+            const float* Bk = Bb + bo * 24;
+            float Bv[24];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+              const float4 t4 = reinterpret_cast<const float4*>(Bk)[q];
+              Bv[4 * q] = t4.x;
+              Bv[4 * q + 1] = t4.y;
+              Bv[4 * q + 2] = t4.z;
+              Bv[4 * q + 3] = t4.w;
+            }
+            const float u = P.u;
+            float gR[4], dgu[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const float* b = Bv + c * 6;
+              gR[c] = fmaf(fmaf(fmaf(fmaf(fmaf(b[5], u, b[4]), u, b[3]), u, b[2]), u, b[1]), u, b[0]);
+              dgu[c] = fmaf(fmaf(fmaf(fmaf(5.0f * b[5], u, 4.0f * b[4]), u, 3.0f * b[3]), u,
+                                  2.0f * b[2]),
+                             u, b[1]);
+            }
+            const float ux = P.dx * P.ir, uy = P.dy * P.ir, uz = P.dz * P.ir;
+            const float s = P.s;
+            const float gs = ep.inv_h * s * (dgu[0] + ux * dgu[1] + uy * dgu[2] + uz * dgu[3]);
+            const float a0 = gR[0] + gs;
+            const float dot = gR[1] * ux + gR[2] * uy + gR[3] * uz;
+            const float sor = s * P.ir;
+            const float coef = P.dsdr * (a0 + dot) - sor * dot;
+            float gx = coef * ux + sor * gR[1];
+            float gy = coef * uy + sor * gR[2];
+            float gz = coef * uz + sor * gR[3];
+            if (!(isfinite(gx) && isfinite(gy) && isfinite(gz)) || fabsf(gx) > 4.0e6f ||
+                fabsf(gy) > 4.0e6f || fabsf(gz) > 4.0e6f) {
+              ++nbad;
+              gx = gy = gz = 0.0f;
+            }
+            fx += gx;
+            fy += gy;
+            fz += gz;
+            vl[0] -= P.dx * gx;
+            vl[1] -= P.dx * gy;
+            vl[2] -= P.dx * gz;
+            vl[3] -= P.dy * gx;
+            vl[4] -= P.dy * gy;
+            vl[5] -= P.dy * gz;
+            vl[6] -= P.dz * gx;
+            vl[7] -= P.dz * gy;
+            vl[8] -= P.dz * gz;
+            unsigned long long* fj = ffix + (size_t)(e >> 5) * 3;
+            atomicAdd(fj + 0, (unsigned long long)(-__float2ll_rn(gx * DP_FSCALE_F)));
+            atomicAdd(fj + 1, (unsigned long long)(-__float2ll_rn(gy * DP_FSCALE_F)));
+            atomicAdd(fj + 2, (unsigned long long)(-__float2ll_rn(gz * DP_FSCALE_F)));
+          }
+        }
+        __syncwarp();
       }
+    } else {
+      ++nbad;
     }
-    double red[12] = {fx, fy, fz, vl[0], vl[1], vl[2], vl[3], vl[4], vl[5], vl[6], vl[7], vl[8]};
+    // the centre's own force: lane partials (a few pairs each, FP32) summed
+    // across the warp in FP64, where the pair terms largely cancel
+    double red[3] = {fx, fy, fz};
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1)
 #pragma unroll
-      for (int a = 0; a < 12; ++a) red[a] += __shfl_xor_sync(0xffffffffu, red[a], o);
+      for (int a = 0; a < 3; ++a) red[a] += __shfl_xor_sync(0xffffffffu, red[a], o);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+      for (int a = 0; a < 9; ++a) vl[a] += __shfl_xor_sync(0xffffffffu, vl[a], o);
     if (lane == 0) {
       unsigned long long* fi = ffix + (size_t)i * 3;
       atomicAdd(fi + 0, (unsigned long long)__double2ll_rn(red[0] * DP_FSCALE));
       atomicAdd(fi + 1, (unsigned long long)__double2ll_rn(red[1] * DP_FSCALE));
       atomicAdd(fi + 2, (unsigned long long)__double2ll_rn(red[2] * DP_FSCALE));
+    }
+    if (lane < 9) {
+      float vv = vl[0];
 #pragma unroll
-      for (int a = 0; a < 9; ++a) vacc[a] += red[3 + a];
+      for (int a = 1; a < 9; ++a) vv = lane == a ? vl[a] : vv;
+      vacc[lane] += (double)vv;
     }
     __syncwarp();
-    for (int k = lane; k < nt * ow; k += 32) S.occ[k] = 0u;
-    __syncwarp();
   }
-  if (lane == 0) {
-    double* vp = vir_part + ((size_t)blockIdx.x * wpb + wib) * 9;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) vp[a] = vacc[a];
-  }
+  __syncwarp();
+  if (lane < 9) vir_part[((size_t)blockIdx.x * wpb + wib) * 9 + lane] = vacc[lane];
   nbad = __reduce_add_sync(0xffffffffu, nbad);
   if (lane == 0 && nbad) atomicAdd(&status[ST_NONFINITE], nbad);
 }
@@ -530,8 +623,13 @@ int tab_blocks(int64_t n) {
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
-size_t tab_smem(const EnvParams& ep) {
-  return (size_t)kWarpsPerBlock * per_warp_words(ep.ntypes, ep.n_int) * sizeof(float);
+int stage_cap(const EnvParams& ep) { return ((int)(1.0f / ep.inv_nm + 0.5f) + 32 + 31) / 32 * 32; }
+
+size_t fwd_smem(const EnvParams& ep) {
+  return (size_t)kWarpsPerBlock * fwd_warp_words(ep.ntypes * ep.n_int, stage_cap(ep)) * sizeof(float);
+}
+size_t bwd_smem(const EnvParams& ep) {
+  return (size_t)kWarpsPerBlock * bwd_warp_words(ep.ntypes * ep.n_int, stage_cap(ep)) * sizeof(float);
 }
 
 }  // namespace
@@ -554,6 +652,7 @@ int table_build(cudaStream_t st, const double* emb64, const int64_t* emb_off, in
   if (cudaMallocAsync(&node, sizeof(double) * (size_t)npair * n_nodes * 3 * M, st) != cudaSuccess)
     return -2;
   int threads = ((wmax + 31) / 32) * 32;
+  DP_LAUNCHED(2);
   k_table_nodes<<<npair * n_nodes, threads, sizeof(double) * 6 * wmax, st>>>(
       emb64, emb_off, n_emb, w[0], w[1], w[2], w[3], w[4], w[5], h, n_nodes, node);
   int64_t tot = (int64_t)npair * n_int * M;
@@ -567,16 +666,17 @@ int launch_tab_fwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t
                    const float* table, float* T, int32_t* status,
                    unsigned long long* pair_count) {
   if (n <= 0) return 0;
-  if (ep.M > 128 || ep.M % 4) return -1;
-  size_t sm = tab_smem(ep);
+  if (ep.M > 128 || ep.M % 4 || ep.ntypes * ep.n_int > 32768) return -1;
+  size_t sm = fwd_smem(ep);
   if (sm > 200 * 1024) return -1;
   static size_t set_fwd = 0;
   if (sm > 48 * 1024 && sm > set_fwd) {
     cudaFuncSetAttribute(k_tab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set_fwd = sm;
   }
-  k_tab_fwd<<<tab_blocks(n), kWarpsPerBlock * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep, table, T,
-                                                          status, pair_count);
+  DP_LAUNCHED(1);
+  k_tab_fwd<<<tab_blocks(n), kWarpsPerBlock * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep, table,
+                                                          stage_cap(ep), T, status, pair_count);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -585,16 +685,17 @@ int launch_tab_bwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t
                    const float* table, const float* dT, unsigned long long* ffix,
                    double* vir_part, int vir_slots, int32_t* status) {
   if (n <= 0) return 0;
-  if (ep.M > 128 || ep.M % 4) return -1;
+  if (ep.M > 128 || ep.M % 4 || ep.ntypes * ep.n_int > 32768) return -1;
   if (vir_slots < tab_kernel_slots(n)) return -1;
-  size_t sm = tab_smem(ep);
+  size_t sm = bwd_smem(ep);
   if (sm > 200 * 1024) return -1;
   static size_t set_bwd = 0;
   if (sm > 48 * 1024 && sm > set_bwd) {
     cudaFuncSetAttribute(k_tab_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set_bwd = sm;
   }
-  k_tab_bwd<<<tab_blocks(n), kWarpsPerBlock * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep, table, dT,
-                                                          ffix, vir_part, status);
+  DP_LAUNCHED(1);
+  k_tab_bwd<<<tab_blocks(n), kWarpsPerBlock * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep, table,
+                                                          stage_cap(ep), dT, ffix, vir_part, status);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* 
 template <int EPI>
 void gemm(cudaStream_t st, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
           const GemmEpi& ep) {
+  DP_LAUNCHED(1);
   if (N <= 256 && N % 80 == 0) {
     dim3 grid((M + 127) / 128, (N + 79) / 80);
     k_gemm<80, 5, EPI><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, ep);
@@ -212,6 +213,7 @@ int fit_simt(cudaStream_t st, int64_t n, const int32_t* idx, const FitNet& net, 
     // T -> D  (rows gathered through idx; without idx the chunk starts at r0)
     const float* Tc = idx ? T : T + (size_t)r0 * 4 * M;
     float* dTc = idx ? dT : dT + (size_t)r0 * 4 * M;
+    DP_LAUNCHED(4);  // descriptor, energy, last-layer gradient, descriptor backward
     k_descr<<<rows, 128, sizeof(float) * 4 * M, st>>>(rows, id, Tc, M, m_lt, s.D);
     // forward
     const float* in = s.D;

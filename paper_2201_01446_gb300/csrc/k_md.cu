@@ -2,6 +2,8 @@
 // deterministic reductions for energy, virial and kinetic energy.
 #include "dp_internal.h"
 
+unsigned long long g_dp_launches = 0;
+
 namespace {
 
 __global__ void k_force_finalize(int64_t n, const unsigned long long* __restrict__ ffix,
@@ -108,7 +110,7 @@ void launch_zero_forces(cudaStream_t st, int64_t n, unsigned long long* ffix) {
 
 void launch_force_finalize(cudaStream_t st, int64_t n, const unsigned long long* ffix, double* f,
                            int32_t* status) {
-  if (n > 0) k_force_finalize<<<nblk(n * 3, 256), 256, 0, st>>>(n, ffix, f, status);
+  if (n > 0) DP_LAUNCHED(1), k_force_finalize<<<nblk(n * 3, 256), 256, 0, st>>>(n, ffix, f, status);
 }
 
 int sum_rows_part_size(int64_t rows, int width) { return kSumBlocks * width; }
@@ -117,6 +119,7 @@ void launch_sum_rows(cudaStream_t st, int64_t rows, int width, const double* in,
                      double* out) {
   int64_t chunk = (rows + kSumBlocks - 1) / kSumBlocks;
   if (chunk < 1) chunk = 1;
+  DP_LAUNCHED(2);
   k_sum_stage1<<<kSumBlocks, 256, 0, st>>>(rows, width, chunk, in, part);
   k_sum_stage2<<<1, 32, 0, st>>>(kSumBlocks, width, part, out);
 }
@@ -125,20 +128,20 @@ void launch_kick_drift(cudaStream_t st, int64_t n, double* x, double* v, const d
                        const int32_t* types, const double* inv_mass_acc, double dt,
                        const double* xref, double half_skin2, int32_t* status) {
   if (n > 0)
-    k_kick_drift<<<nblk(n, 256), 256, 0, st>>>(n, x, v, f, types, inv_mass_acc, dt, xref,
+    DP_LAUNCHED(1), k_kick_drift<<<nblk(n, 256), 256, 0, st>>>(n, x, v, f, types, inv_mass_acc, dt, xref,
                                                half_skin2, status);
 }
 
 void launch_kick(cudaStream_t st, int64_t n, double* v, const double* f, const int32_t* types,
                  const double* inv_mass_acc, const double* mass, double dt, double* ke) {
-  if (n > 0) k_kick<<<nblk(n, 256), 256, 0, st>>>(n, v, f, types, inv_mass_acc, mass, dt, ke);
+  if (n > 0) DP_LAUNCHED(1), k_kick<<<nblk(n, 256), 256, 0, st>>>(n, v, f, types, inv_mass_acc, mass, dt, ke);
 }
 
 void launch_check_energy(cudaStream_t st, int64_t n, const double* e, int32_t* status) {
-  if (n > 0) k_check_energy<<<nblk(n, 256), 256, 0, st>>>(n, e, status);
+  if (n > 0) DP_LAUNCHED(1), k_check_energy<<<nblk(n, 256), 256, 0, st>>>(n, e, status);
 }
 
 void launch_map_types(cudaStream_t st, int64_t n, const int32_t* in, const int32_t* map, int nmap,
                       int32_t* out, int32_t* status) {
-  if (n > 0) k_map_types<<<nblk(n, 256), 256, 0, st>>>(n, in, map, nmap, out, status);
+  if (n > 0) DP_LAUNCHED(1), k_map_types<<<nblk(n, 256), 256, 0, st>>>(n, in, map, nmap, out, status);
 }

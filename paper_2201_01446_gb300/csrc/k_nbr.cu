@@ -222,26 +222,28 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 void launch_wrap_bin(cudaStream_t st, int64_t n, double* x, const CellGeom& g, int32_t* cellc,
                      int32_t* cell_count) {
-  if (n > 0) k_wrap_bin<<<nblk(n, 256), 256, 0, st>>>(n, x, g, cellc, cell_count);
+  if (n > 0) DP_LAUNCHED(1), k_wrap_bin<<<nblk(n, 256), 256, 0, st>>>(n, x, g, cellc, cell_count);
 }
 
 void launch_scan(cudaStream_t st, const int32_t* count, int32_t* start, long long ncell) {
+  DP_LAUNCHED(1);
   k_scan<<<1, 1024, 0, st>>>(count, start, ncell);
 }
 
 void launch_scatter(cudaStream_t st, int64_t n, const int32_t* cellc, const int32_t* start,
                     int32_t* fill, int32_t* out) {
-  if (n > 0) k_scatter<<<nblk(n, 256), 256, 0, st>>>(n, cellc, start, fill, out);
+  if (n > 0) DP_LAUNCHED(1), k_scatter<<<nblk(n, 256), 256, 0, st>>>(n, cellc, start, fill, out);
 }
 
 void launch_cell_sort(cudaStream_t st, long long ncell, const int32_t* start, const int32_t* in,
                       int32_t* out) {
+  DP_LAUNCHED(1);
   k_cell_sort<<<nblk(ncell * 32, 256), 256, 0, st>>>(ncell, start, in, out);
 }
 
 void launch_mirror(cudaStream_t st, int64_t n, const double* x, const int32_t* cellc,
                    const int32_t* types, const CellGeom& g, float4* off) {
-  if (n > 0) k_mirror<<<nblk(n, 256), 256, 0, st>>>(n, x, cellc, types, g, off);
+  if (n > 0) DP_LAUNCHED(1), k_mirror<<<nblk(n, 256), 256, 0, st>>>(n, x, cellc, types, g, off);
 }
 
 void launch_build_list(cudaStream_t st, int64_t n, const double* x, const int32_t* cellc,
@@ -249,7 +251,7 @@ void launch_build_list(cudaStream_t st, int64_t n, const double* x, const int32_
                        const CellGeom& g, double rlist, float rc2, int ntypes, const int32_t* sel,
                        int cap, uint32_t* nlist, int32_t* nn, int32_t* status) {
   if (n > 0)
-    k_build_list<<<nblk(n * 32, 128), 128, 0, st>>>(n, x, cellc, off, cell_start, cell_atoms, g,
+    DP_LAUNCHED(1), k_build_list<<<nblk(n * 32, 128), 128, 0, st>>>(n, x, cellc, off, cell_start, cell_atoms, g,
                                                      rlist, rc2, ntypes, sel, cap, nlist, nn,
                                                      status);
 }

@@ -295,7 +295,7 @@ def dp_profile_read(h):
 
 
 def dp_stats(h, s=None):
-    out = np.zeros(5, np.int64)
+    out = np.zeros(6, np.int64)
     _check(lib.dp_stats(h, s, out.ctypes.data_as(C.c_void_p)), h)
     return dict(natoms=int(out[0]), list_capacity=int(out[1]), max_list=int(out[2]),
-                pairs_within_rc=int(out[3]), cells=int(out[4]))
+                pairs_within_rc=int(out[3]), cells=int(out[4]), kernel_launches=int(out[5]))

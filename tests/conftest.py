@@ -20,7 +20,7 @@ def pytest_configure(config):
 # 2048-240-240-240-1); std 0.1 is the configured synthetic model, std 1.0 a
 # stress model whose forces are O(0.1-1) eV/A so that error bounds bite
 CU_RC, CU_RCS, CU_SEL = 8.0, 0.5, 256
-CU_SMAX = 1.0 / 1.5
+CU_SMAX = 2.0  # table domain s <= 2 (r >= 0.5 A)
 TABLE_H = 0.01
 
 

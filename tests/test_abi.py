@@ -38,7 +38,7 @@ def test_library_is_built_for_sm_103a():
 def test_defaults_and_version():
     o = dp.dp_options_default()
     assert o.tabulated == 1 and o.fit_precision == 0
-    assert abs(o.table_step - 0.01) < 1e-15 and abs(o.s_max - 1 / 1.5) < 1e-15
+    assert abs(o.table_step - 0.01) < 1e-15 and o.s_max == 2.0
     assert o.skin == 2.0 and o.rebuild_every == 10
     assert "sm_103a" in dp.dp_version()
 

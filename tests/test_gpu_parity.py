@@ -198,6 +198,15 @@ def test_edge_cases(dp, cu_stress):
                 tag=f"stress {len(x)} atoms")
 
 
+def test_close_contacts(dp, cu_stress):
+    # pairs at 1.2-1.6 A: s up to 0.8, far into the table, few members per interval
+    h, m, tab = cu_stress
+    x, t, box = inputs.fcc_copper(3, sigma=0.05, seed=9)
+    x[1] = x[0] + np.array([1.2, 0.1, 0.0])
+    x[7] = x[5] + np.array([0.2, 1.6, 0.3])
+    _parity(dp, h, m, tab, x, t, box, stress=True, tag="close contacts")
+
+
 def test_error_statuses(dp, cu_stress):
     h, m, tab = cu_stress
     x, t, box = inputs.fcc_copper(3, sigma=0.0)
@@ -211,7 +220,7 @@ def test_error_statuses(dp, cu_stress):
         dp.dp_compute(h, x, t, skew)
     assert e.value.code == 7
     x2 = x.copy()
-    x2[1] = x2[0] + np.array([1.2, 0, 0])  # s = sw(1.2)/1.2 > 1/1.5
+    x2[1] = x2[0] + np.array([0.45, 0, 0])  # s = 1/0.45 > 2
     with pytest.raises(dp.DPError) as e:
         dp.dp_compute(h, x2, t, box)
     assert e.value.code == 6

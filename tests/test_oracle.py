@@ -161,8 +161,8 @@ def test_hermite5_exact_on_quintics():
 def test_table_matches_net_at_nodes(cu_stress_path):
     m = oracle.Model(cu_stress_path)
     tab = oracle.Table(m, TABLE_H, CU_SMAX)
-    assert tab.n == 67
-    for k in [0, 1, 17, 40, 66]:
+    assert tab.n == 200
+    for k in [0, 1, 17, 40, 66, 150, 199]:
         x = k * TABLE_H
         g, dg, _ = m.embed(0, 0, x)
         for eps in [0.0, 1e-12]:
@@ -173,7 +173,7 @@ def test_table_matches_net_at_nodes(cu_stress_path):
         # left limit equals right limit (value, slope)
         tg_l, tdg_l, _ = tab.eval(0, 0, x - 1e-12) if k else tab.eval(0, 0, x)
         assert np.allclose(tg_l, g, atol=1e-10) and np.allclose(tdg_l, dg, atol=1e-6)
-    assert tab.eval(0, 0, 0.7)[2]  # beyond n*h: reported out of range
+    assert tab.eval(0, 0, 2.01)[2]  # beyond n*h: reported out of range
 
 
 def test_table_converges_sixth_order(tmp_path):
@@ -384,7 +384,7 @@ def test_sel_overflow_and_table_range_reported(stress):
     r = oracle.evaluate(m, tab, CU_RC, CU_RCS, 100, x, t, box, check=False)
     assert r["status"] == 5 and r["n_sel"] == len(x)
     x2 = x.copy()
-    x2[1] = x2[0] + np.array([1.2, 0, 0])  # r = 1.2 A -> s > 1/1.5
+    x2[1] = x2[0] + np.array([0.45, 0, 0])  # r = 0.45 A -> s = 1/0.45 > 2
     r = oracle.evaluate(m, tab, CU_RC, CU_RCS, CU_SEL, x2, t, box, check=False)
     assert r["status"] == 6 and r["n_range"] >= 2
 
