@@ -4,7 +4,7 @@
  * The library evaluates the energy, forces and virial of the DP-SE_a model of
  * arXiv 2201.01446 with the embedding net replaced by the paper's fifth-order
  * piecewise-polynomial table (Sec. 3.2) fused with the R^T G contraction
- * (Sec. 3.4.1), and integrates velocity-Verlet molecular dynamics (Sec. 5).
+ * (Sec. 3.4.1), and integrates velocity-Verlet molecular dynamics (Sec. 4).
  * Every step runs in the library's own CUDA kernels for sm_103a.
  *
  * Conventions for every call:
@@ -60,11 +60,11 @@ typedef struct {
   double table_step;   /* interval h of the table on s (Sec. 3.2) [0.01] */
   double s_max;        /* table domain is [0, ceil(s_max/h)*h]; [2.0], i.e.
                           r >= 0.5 A for rcs = 0.5 */
-  double skin;         /* neighbor-list buffer for MD (Sec. 5) [2.0 A] */
+  double skin;         /* neighbor-list buffer for MD (Sec. 4) [2.0 A] */
   int rebuild_every;   /* MD list rebuild period in steps [10] */
 } dp_options;
 
-/* Thermodynamic record of one MD step (Sec. 5). */
+/* Thermodynamic record of one MD step (Sec. 4). */
 typedef struct {
   int64_t step;
   double kinetic;     /* eV */
@@ -142,7 +142,7 @@ dp_status dp_system_get(dp_system* s, double* x, double* v, double* f, int devic
 int64_t dp_system_step(const dp_system* s);
 
 /*
- * dp_md_step -- nsteps velocity-Verlet steps of dt_fs (Sec. 5):
+ * dp_md_step -- nsteps velocity-Verlet steps of dt_fs (Sec. 4):
  *   v += dt/2 F/m;  x += dt v;  (list rebuild when step % rebuild_every == 0);
  *   F = -grad E;  v += dt/2 F/m.
  * The rebuild schedule is keyed to the absolute step count, so a run split

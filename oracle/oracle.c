@@ -1060,7 +1060,7 @@ int orc_eval_subset(const orc_model* m, const orc_table* table, double rc, doubl
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sec. 5: velocity-Verlet NVE                                                */
+/* Sec. 4: velocity-Verlet NVE                                                */
 /* ------------------------------------------------------------------------ */
 #define ORC_ACC 9.648533212e-3 /* (eV/A/amu) -> A/fs^2 */
 #define ORC_KB 8.617333262e-5  /* eV/K */

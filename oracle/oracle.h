@@ -13,7 +13,7 @@
  *   Sec. 2.1 fitting net with shortcuts, E = sum_i E_i, F = -grad E
  *   Sec. 3.2 fifth-order piecewise polynomial table matching value, first
  *            and second derivative at the interval nodes
- *   Sec. 5   velocity-Verlet MD
+ *   Sec. 4   velocity-Verlet MD
  * Readings of passages the paper leaves open (switch function, 1/N_m
  * scaling, descriptor flattening order, virial sign, local polynomial
  * variable) are stated beside the code that takes them.
@@ -105,7 +105,7 @@ int orc_eval_subset(const orc_model* m, const orc_table* table, double rc, doubl
                     const double* box, int64_t ne, const int64_t* idx_e, double* e_out,
                     int64_t nf, const int64_t* idx_f, double* f_out);
 
-/* Velocity-Verlet NVE (Sec. 5): nsteps steps of dt fs.  x, v (A, A/fs) are
+/* Velocity-Verlet NVE (Sec. 4): nsteps steps of dt fs.  x, v (A, A/fs) are
  * updated in place; f receives the final forces.  With f_valid != 0, f on
  * entry already holds the forces at x and the initial evaluation is skipped.
  * thermo (may be NULL) receives (nsteps+1) rows of (KE eV, PE eV, T K, P bar)

@@ -1,4 +1,4 @@
-// Velocity-Verlet integration (paper Sec. 5), force finalisation and the
+// Velocity-Verlet integration (paper Sec. 4), force finalisation and the
 // deterministic reductions for energy, virial and kinetic energy.
 #include "dp_internal.h"
 

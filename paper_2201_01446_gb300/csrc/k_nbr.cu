@@ -1,5 +1,5 @@
 // Cell-list neighbor build (paper Sec. 2.1: the neighbor set within the
-// cutoff; Sec. 5: list with a buffer region, rebuilt periodically).
+// cutoff; Sec. 4: list with a buffer region, rebuilt periodically).
 //
 // The list of atom i holds every periodic image (j, n) with
 // |x_j + n*L - x_i| < rlist, (j, n) != (i, 0), where x is wrapped into

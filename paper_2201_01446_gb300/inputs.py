@@ -8,7 +8,7 @@ any computation.
 
 The paper's trained copper and water models, its DFT data and its
 equilibrated 192-atom water box are not available; these generators stand in
-for them (Sec. 5 describes the paper's systems: FCC copper with lattice
+for them (Sec. 4 describes the paper's systems: FCC copper with lattice
 constant 3.634 A, a 192-atom water box, 330 K initial velocities).
 
 Model file format ("DPSEAV01", little endian):

@@ -1,4 +1,4 @@
-"""Velocity-Verlet MD on the GPU (Sec. 5) against the oracle's MD, plus energy
+"""Velocity-Verlet MD on the GPU (Sec. 4) against the oracle's MD, plus energy
 conservation, checkpoint/resume identity and the list-skin guard."""
 import numpy as np
 import pytest

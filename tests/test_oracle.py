@@ -409,7 +409,7 @@ def test_tabulation_error_small(stress):
     assert rmse(a["force"], b["force"]) < 1e-6
 
 
-# ------------------------------------------------------------ MD (Sec. 5)
+# ------------------------------------------------------------ MD (Sec. 4)
 def test_md_energy_conservation_and_reversibility(stress):
     m, tab = stress
     x, t, box = inputs.fcc_copper(3, sigma=0.05, seed=14)
