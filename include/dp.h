@@ -44,7 +44,8 @@ typedef enum {
   DP_ERR_TIMEOUT = 8,       /* a bounded wait gave up */
   DP_ERR_UNIMPLEMENTED = 9, /* option combination not built */
   DP_ERR_SKIN = 10,         /* an atom moved more than skin/2 between list rebuilds */
-  DP_ERR_NONFINITE = 11     /* a non-finite energy or force was produced */
+  DP_ERR_NONFINITE = 11,    /* a non-finite energy or force was produced */
+  DP_ERR_CAPACITY = 12      /* request larger than a fixed capacity (see below) */
 } dp_status;
 
 typedef struct dp_handle dp_handle;
@@ -201,6 +202,33 @@ dp_status dp_profile_read(dp_handle* h, double* ms, int64_t* launches);
  * longest list, [3] pairs within rc seen by the last forward pass, [4] cells,
  * [5] kernels launched by the library in this process so far. */
 dp_status dp_stats(dp_handle* h, const dp_system* s, int64_t* out);
+
+/*
+ * dp_neighbor_pairs_static -- the pair rows of dp_neighbor_pairs, computed
+ * without allocating any memory.  For callers that must not call cudaMalloc
+ * or cudaFree: an MD engine that owns all device memory through its own
+ * pool, or a time-critical loop where an allocation (which can synchronise
+ * the whole device) is not acceptable.  The paper has no counterpart; it
+ * is a service of this library.
+ *   natoms      0 <= natoms <= 65536, else DP_ERR_CAPACITY.
+ *   coords      DEVICE [natoms][3] positions (A), need not be wrapped.
+ *   box         HOST [3][3] orthorhombic box; rlist <= every edge and at
+ *               most 65536 cells of edge >= rlist (else DP_ERR_BOX /
+ *               DP_ERR_CAPACITY).
+ *   cap, out5   DEVICE [cap][5] int32 rows (i, j, n0, n1, n2) as in
+ *               dp_neighbor_pairs; rows past cap are not written.
+ *   count       HOST: receives the total number of pairs.
+ *   stream      cudaStream_t (NULL = legacy default); the call returns after
+ *               the stream has finished its work.
+ * All intermediates live in one fixed device array of about 5 MB that every
+ * GPU loading the library keeps until the process exits.  Calls share it:
+ * calls whose device work overlaps (other streams or host threads without
+ * ordering) race.  The first call on a device looks up the array's device
+ * address with that device current; make it before any stream capture.
+ */
+dp_status dp_neighbor_pairs_static(int64_t natoms, const double* coords, const double* box,
+                                   double rlist, int64_t cap, int32_t* out5, int64_t* count,
+                                   void* stream);
 
 /* Library build string (architecture, options compiled in). */
 const char* dp_version(void);

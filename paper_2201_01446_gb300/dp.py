@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 STATUS = {0: "DP_OK", 1: "DP_ERR_ARG", 2: "DP_ERR_MODEL", 3: "DP_ERR_CUDA", 4: "DP_ERR_OOM",
           5: "DP_ERR_SEL_OVERFLOW", 6: "DP_ERR_TABLE_RANGE", 7: "DP_ERR_BOX",
           8: "DP_ERR_TIMEOUT", 9: "DP_ERR_UNIMPLEMENTED", 10: "DP_ERR_SKIN",
-          11: "DP_ERR_NONFINITE"}
+          11: "DP_ERR_NONFINITE", 12: "DP_ERR_CAPACITY"}
 
 
 class DPError(RuntimeError):
@@ -44,7 +44,7 @@ EXPORTS = ["dp_options_default", "dp_create", "dp_destroy", "dp_last_error", "dp
            "dp_compute", "dp_system_create", "dp_system_destroy", "dp_system_get",
            "dp_system_step", "dp_md_step", "dp_state_save", "dp_state_load",
            "dp_neighbor_pairs", "dp_table_coeffs", "dp_descriptor", "dp_version",
-           "dp_profile", "dp_profile_read", "dp_stats"]
+           "dp_profile", "dp_profile_read", "dp_stats", "dp_neighbor_pairs_static"]
 
 DP_NPHASE = 5
 PHASES = ["neighbor_build", "embed_contract_fwd", "fitting", "embed_contract_bwd_forces",
@@ -81,6 +81,7 @@ def _load():
         "dp_profile": (i, [vp, i]),
         "dp_profile_read": (i, [vp, vp, vp]),
         "dp_stats": (i, [vp, vp, vp]),
+        "dp_neighbor_pairs_static": (i, [i64, vp, vp, d, i64, vp, i64p, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -299,3 +300,23 @@ def dp_stats(h, s=None):
     _check(lib.dp_stats(h, s, out.ctypes.data_as(C.c_void_p)), h)
     return dict(natoms=int(out[0]), list_capacity=int(out[1]), max_list=int(out[2]),
                 pairs_within_rc=int(out[3]), cells=int(out[4]), kernel_launches=int(out[5]))
+
+
+def dp_neighbor_pairs_static(coords, box, rlist, stream=None):
+    """Pair rows (i, j, n0, n1, n2) of a CUDA float64 tensor of positions,
+    computed by the library without allocating device memory (its scratch
+    is a fixed array).  The output tensor is allocated here by torch, on
+    the caller's side of the call; the first call returns only the count."""
+    import torch
+    assert coords.is_cuda and coords.dtype == torch.float64 and coords.is_contiguous()
+    n = int(coords.shape[0])
+    b = np.ascontiguousarray(box, np.float64)
+    cnt = C.c_int64()
+    _check(lib.dp_neighbor_pairs_static(n, C.c_void_p(coords.data_ptr()),
+                                        b.ctypes.data_as(C.c_void_p), float(rlist), 0, None,
+                                        C.byref(cnt), stream), None)
+    out = torch.empty((max(cnt.value, 1), 5), dtype=torch.int32, device=coords.device)
+    _check(lib.dp_neighbor_pairs_static(n, C.c_void_p(coords.data_ptr()),
+                                        b.ctypes.data_as(C.c_void_p), float(rlist), cnt.value,
+                                        C.c_void_p(out.data_ptr()), C.byref(cnt), stream), None)
+    return out[:cnt.value]
