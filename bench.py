@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--fit-precision", type=int, default=0,
+                    help="0 FP32 CUDA cores, 1 BF16 tensor cores, 2 FP32-accurate tensor cores")
     return ap.parse_args()
 
 
@@ -246,7 +248,9 @@ def main():
     n = len(x)
     v = inputs.maxwell_velocities(np.full(n, inputs.MASS_CU), 330.0, seed=2 + rank)
     masses = [inputs.MASS_CU]
-    h = dp.dp_create(model, 1, RC, RCS, [SEL], stream=C_stream(stream))
+    opt = dp.dp_options_default()
+    opt.fit_precision = args.fit_precision
+    h = dp.dp_create(model, 1, RC, RCS, [SEL], options=opt, stream=C_stream(stream))
     s = dp.dp_system_create(h, x, v, t, masses, box)
     for _ in range(args.warmup):
         dp.dp_md_step(h, s, MD_PER_STEP, DT_FS)
@@ -317,7 +321,8 @@ def main():
                                        "1-32-64-128 / 2048-240-240-240-1, rc 8 A, tabulated "
                                        "h=0.01 s<=2, velocity-Verlet dt 1 fs, rebuild every 10, skin 2 A",
                            "md_steps_per_step": MD_PER_STEP, "natoms": n,
-                           "fit_precision": "fp32-simt", "l2": "inputs larger than L2",
+                           "fit_precision": ["fp32-cuda-cores", "bf16-tcgen05",
+                                             "fp32-accurate-tcgen05"][args.fit_precision], "l2": "inputs larger than L2",
                            "ns_per_day": value / world / n * DT_FS * 86400 * 1e-6,
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

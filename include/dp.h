@@ -180,6 +180,13 @@ dp_status dp_table_coeffs(dp_handle* h, int ti, int tj, float* out, int32_t* n);
 dp_status dp_descriptor(dp_handle* h, int64_t natoms, const double* coords,
                         const int32_t* types, const double* box, float* T_out);
 
+/* The descriptor and fitting stage alone (Eq. 2, Sec. 2.1) in the handle's
+ * fit_precision: per-atom energies E_i and dE_i/dT for given T.
+ *   types  HOST [natoms] caller types; T HOST FP32 [natoms][4][M];
+ *   e_out  HOST [natoms] eV; dT_out HOST FP32 [natoms][4][M] or NULL. */
+dp_status dp_fitting(dp_handle* h, int64_t natoms, const int32_t* types, const float* T,
+                     double* e_out, float* dT_out);
+
 /* ---------------------------------------------------------------------------
  * Profiling: per-phase device time measured with CUDA events recorded on the
  * handle's stream around each phase's kernels.

@@ -98,9 +98,11 @@ struct dp_handle {
   int n_int = 0;
   double h = 0.0;
   FitNet nets[DP_MAXT];
+  FitNetTC nets_tc[DP_MAXT];
   float b_out[DP_MAXT] = {0};
-  DevBuf fitbuf;
+  DevBuf fitbuf, fit_bf16, fitbuf_tc;
   FitScratch fs{};
+  FitScratchTC fs_tc{};
   int32_t* status_host = nullptr;
   Work w;
   // profiling: event pairs recorded around each phase on the handle's stream
@@ -326,6 +328,10 @@ dp_status status_errors(dp_handle* h) {
                   h->n_int * h->h);
     return fail(h, DP_ERR_TABLE_RANGE, buf);
   }
+  if (s[ST_TIMEOUT]) {
+    std::snprintf(buf, sizeof buf, "%d bounded device waits gave up", s[ST_TIMEOUT]);
+    return fail(h, DP_ERR_TIMEOUT, buf);
+  }
   if (s[ST_NONFINITE]) {
     std::snprintf(buf, sizeof buf, "%d non-finite energies or pair forces", s[ST_NONFINITE]);
     return fail(h, DP_ERR_NONFINITE, buf);
@@ -475,6 +481,55 @@ dp_status rebuild(dp_handle* h, Work& w, const double* L, double rlist) {
   return fail(h, DP_ERR_CUDA, "neighbor list capacity did not converge");
 }
 
+dp_status ensure_fit_scratch_tc(dp_handle* h, int64_t rows_needed) {
+  const int PCN = 3;  // room for three pieces serves both tensor-core modes
+  int64_t rows = std::min<int64_t>(std::max<int64_t>(rows_needed, 1), 65536);
+  rows = (rows + 127) / 128 * 128;
+  if (rows <= h->fs_tc.rows) return DP_OK;
+  int wmax = 0;
+  for (int k = 0; k < h->n_fit; ++k) wmax = std::max(wmax, h->fit_w[k]);
+  size_t bytes = rows * (size_t)h->din * (2 * PCN + 4) + rows * (size_t)wmax * (4 + 2 * 2 * PCN);
+  for (int k = 0; k < h->n_fit; ++k) bytes += rows * (size_t)h->fit_w[k] * (4 + 4 + 2 * PCN);
+  bytes += 64 * 256;
+  CK(ensure(h->fitbuf_tc, bytes), "alloc tensor-core fitting scratch");
+  unsigned char* q = P<unsigned char>(h->fitbuf_tc);
+  auto take = [&](size_t b) {
+    unsigned char* p = q;
+    q += (b + 255) / 256 * 256;
+    return p;
+  };
+  FitScratchTC& s = h->fs_tc;
+  s.rows = rows;
+  s.wmax = wmax;
+  s.Dh = (__nv_bfloat16*)take(rows * h->din * 2 * PCN);
+  s.dD = (float*)take(rows * h->din * 4);
+  for (int k = 0; k < h->n_fit; ++k) {
+    s.t[k] = (float*)take(rows * h->fit_w[k] * 4);
+    s.z[k] = (float*)take(rows * h->fit_w[k] * 4);
+    s.zh[k] = (__nv_bfloat16*)take(rows * h->fit_w[k] * 2 * PCN);
+  }
+  s.gz = (float*)take(rows * wmax * 4);
+  s.gph[0] = (__nv_bfloat16*)take(rows * wmax * 2 * PCN);
+  s.gph[1] = (__nv_bfloat16*)take(rows * wmax * 2 * PCN);
+  return DP_OK;
+}
+
+// fitting stage of one centre type: E_i and dE/dT for cnt atoms (idx or all)
+dp_status run_fitting(dp_handle* h, int t, int64_t cnt, const int32_t* idx, const float* T,
+                      float* dT, double* e_atom) {
+  if (h->opt.fit_precision == 1 || h->opt.fit_precision == 2) {
+    CKS(ensure_fit_scratch_tc(h, cnt));
+    if (fit_tc(h->st, cnt, idx, h->nets_tc[t], h->M, h->m_lt, T, dT, e_atom, h->fs_tc,
+               h->opt.fit_precision == 1 ? 1 : 3, P<int32_t>(h->status) + ST_TIMEOUT))
+      return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core fitting cannot run this model shape");
+    return DP_OK;
+  }
+  CKS(ensure_fit_scratch(h, cnt));
+  if (fit_simt(h->st, cnt, idx, h->nets[t], h->M, h->m_lt, T, dT, e_atom, h->fs))
+    return fail(h, DP_ERR_CUDA, "fitting kernels failed to launch");
+  return DP_OK;
+}
+
 // energy, forces, virial from the current list and offsets
 dp_status evaluate(dp_handle* h, Work& w) {
   const int64_t n = w.n;
@@ -496,11 +551,8 @@ dp_status evaluate(dp_handle* h, Work& w) {
   for (int t = 0; t < h->ntypes; ++t) {
     const int64_t cnt = w.have_idx ? w.type_count[t] : n;
     if (cnt == 0) continue;
-    CKS(ensure_fit_scratch(h, cnt));
     const int32_t* idx = w.have_idx ? P<int32_t>(w.idx) + w.type_off[t] : nullptr;
-    if (fit_simt(h->st, cnt, idx, h->nets[t], h->M, h->m_lt, P<float>(w.T), P<float>(w.dT),
-                 P<double>(w.e_atom), h->fs))
-      return fail(h, DP_ERR_CUDA, "fitting kernels failed to launch");
+    CKS(run_fitting(h, t, cnt, idx, P<float>(w.T), P<float>(w.dT), P<double>(w.e_atom)));
     if (!w.have_idx) break;
   }
   ph_fit.end();
@@ -596,7 +648,8 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
       !(rcs < rc) || !(h->opt.table_step > 0) || !(h->opt.s_max > 0) || h->opt.skin < 0 ||
       h->opt.rebuild_every < 1)
     return bail(DP_ERR_ARG);
-  if (h->opt.tabulated != 1 || h->opt.fit_precision != 0) return bail(DP_ERR_UNIMPLEMENTED);
+  if (h->opt.tabulated != 1 || h->opt.fit_precision < 0 || h->opt.fit_precision > 2)
+    return bail(DP_ERR_UNIMPLEMENTED);
   HostModel m;
   std::string why;
   if (!read_model(model_path, m, why)) {
@@ -695,6 +748,37 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
     }
     net.w_out = fb + ofs[t].wout;
     net.b_out = h->b_out[t];
+  }
+  // BF16 pieces (h, m, l) of the fitting weights for the tensor-core modes
+  if (ensure(h->fit_bf16, sizeof(__nv_bfloat16) * 3 * fit.size()) != cudaSuccess) {
+    h->err = "device allocation failed";
+    cudaGetLastError();
+    return bail(DP_ERR_OOM);
+  }
+  {
+    __nv_bfloat16* hb = P<__nv_bfloat16>(h->fit_bf16);
+    for (int t = 0; t < m.ntypes; ++t) {
+      FitNetTC& nt = h->nets_tc[t];
+      const FitNet& nf = h->nets[t];
+      nt.nl = nf.nl;
+      for (int k = 0; k < nf.nl; ++k) {
+        const int64_t ne = (int64_t)nf.win[k] * nf.wout[k];
+        // pieces of W^T at 3*ofs.WT, pieces of W at 3*ofs.W (disjoint: 3 * fit.size() total)
+        __nv_bfloat16* pwt = hb + 3 * ofs[t].WT[k];
+        __nv_bfloat16* pw = hb + 3 * ofs[t].W[k];
+        launch_split_pieces(h->st, ne, fb + ofs[t].WT[k], pwt);
+        launch_split_pieces(h->st, ne, fb + ofs[t].W[k], pw);
+        nt.win[k] = nf.win[k];
+        nt.wout[k] = nf.wout[k];
+        nt.shortcut[k] = nf.shortcut[k];
+        nt.WTh[k] = pwt;
+        nt.Wh[k] = pw;
+        nt.w_ps[k] = ne;
+        nt.b[k] = nf.b[k];
+      }
+      nt.w_out = nf.w_out;
+      nt.b_out = nf.b_out;
+    }
   }
   if (table_build(h->st, P<double>(h->emb64), P<int64_t>(h->emb_off), m.n_emb, m.emb_w, np, h->h,
                   h->n_int, P<float>(h->table)) != 0) {
@@ -882,6 +966,35 @@ dp_status dp_stats(dp_handle* h, const dp_system* s, int64_t* out) {
   out[3] = (int64_t)pairs;
   out[4] = w.geom.ncell;
   out[5] = (int64_t)__atomic_load_n(&g_dp_launches, __ATOMIC_RELAXED);
+  return DP_OK;
+}
+
+dp_status dp_fitting(dp_handle* h, int64_t natoms, const int32_t* types, const float* T,
+                     double* e_out, float* dT_out) {
+  CKS(check_handle(h));
+  if (natoms < 0 || (natoms > 0 && (!types || !T || !e_out)))
+    return fail(h, DP_ERR_ARG, "bad argument");
+  if (natoms == 0) return DP_OK;
+  Work& w = h->w;
+  CKS(ensure_atoms(h, w, natoms));
+  CKS(set_types(h, w, types));
+  CK(cudaMemcpyAsync(w.T.p, T, sizeof(float) * 4 * h->M * natoms, cudaMemcpyHostToDevice, h->st),
+     "T copy");
+  CKS(clear_status(h));
+  for (int t = 0; t < h->ntypes; ++t) {
+    const int64_t cnt = w.have_idx ? w.type_count[t] : natoms;
+    if (cnt == 0) continue;
+    const int32_t* idx = w.have_idx ? P<int32_t>(w.idx) + w.type_off[t] : nullptr;
+    CKS(run_fitting(h, t, cnt, idx, P<float>(w.T), P<float>(w.dT), P<double>(w.e_atom)));
+    if (!w.have_idx) break;
+  }
+  CK(cudaGetLastError(), "fitting kernels");
+  CKS(read_status(h));
+  CKS(status_errors(h));
+  CK(cudaMemcpy(e_out, w.e_atom.p, sizeof(double) * natoms, cudaMemcpyDeviceToHost), "e copy");
+  if (dT_out)
+    CK(cudaMemcpy(dT_out, w.dT.p, sizeof(float) * 4 * h->M * natoms, cudaMemcpyDeviceToHost),
+       "dT copy");
   return DP_OK;
 }
 

@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA kernels and the C-ABI runtime.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,6 +22,7 @@ enum {
   ST_MAXLIST = 4,    // largest list length seen (may exceed the capacity)
   ST_LISTOVF = 5,    // atoms whose list did not fit the capacity
   ST_BADTYPE = 6,    // atoms with a type index outside the type map
+  ST_TIMEOUT = 7,    // bounded device waits that gave up
   ST_NWORDS = 16
 };
 
@@ -109,6 +111,35 @@ struct FitScratch {
 // atoms when idx == NULL), FP32 CUDA-core path.
 int fit_simt(cudaStream_t st, int64_t n, const int32_t* idx, const FitNet& net, int M, int m_lt,
              const float* T, float* dT, double* e_atom, const FitScratch& s);
+
+// Tensor-core (tcgen05, BF16 operands, FP32 accumulate) fitting stage.  Each
+// BF16 operand has 1 piece (BF16 mode) or 3 pieces x = h + m + l (FP32-
+// accurate mode: six piece products accumulate in FP32).
+struct FitNetTC {
+  int nl;
+  int win[DP_MAXFIT], wout[DP_MAXFIT], shortcut[DP_MAXFIT];
+  const __nv_bfloat16* WTh[DP_MAXFIT];  // pieces of [wout][win]: forward B operand
+  const __nv_bfloat16* Wh[DP_MAXFIT];   // pieces of [win][wout]: backward B operand
+  int64_t w_ps[DP_MAXFIT];              // elements between pieces (win * wout)
+  const float* b[DP_MAXFIT];
+  const float* w_out;
+  float b_out;
+};
+struct FitScratchTC {
+  int64_t rows;                  // rows per chunk; piece stride of an array = rows * width
+  int wmax;
+  __nv_bfloat16* Dh;             // pieces of [rows][din]
+  float* dD;                     // [rows][din]
+  float* t[DP_MAXFIT];           // [rows][wout[k]] tanh outputs
+  float* z[DP_MAXFIT];           // [rows][wout[k]] layer outputs (k >= 1)
+  __nv_bfloat16* zh[DP_MAXFIT];  // pieces of the layer outputs (next A operand)
+  float* gz;                     // [rows][wmax]
+  __nv_bfloat16* gph[2];         // pieces of [rows][wmax] gradients (A operands)
+};
+void launch_split_pieces(cudaStream_t st, int64_t n, const float* in, __nv_bfloat16* out);
+int fit_tc(cudaStream_t st, int64_t n, const int32_t* idx, const FitNetTC& net, int M, int m_lt,
+           const float* T, float* dT, double* e_atom, const FitScratchTC& s, int pieces,
+           int32_t* err);
 
 // ---------------------------------------------------------------- MD / reductions
 void launch_zero_forces(cudaStream_t st, int64_t n, unsigned long long* ffix);

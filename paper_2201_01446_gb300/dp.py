@@ -44,7 +44,7 @@ EXPORTS = ["dp_options_default", "dp_create", "dp_destroy", "dp_last_error", "dp
            "dp_compute", "dp_system_create", "dp_system_destroy", "dp_system_get",
            "dp_system_step", "dp_md_step", "dp_state_save", "dp_state_load",
            "dp_neighbor_pairs", "dp_table_coeffs", "dp_descriptor", "dp_version",
-           "dp_profile", "dp_profile_read", "dp_stats", "dp_neighbor_pairs_static"]
+           "dp_profile", "dp_profile_read", "dp_stats", "dp_neighbor_pairs_static", "dp_fitting"]
 
 DP_NPHASE = 5
 PHASES = ["neighbor_build", "embed_contract_fwd", "fitting", "embed_contract_bwd_forces",
@@ -82,6 +82,7 @@ def _load():
         "dp_profile_read": (i, [vp, vp, vp]),
         "dp_stats": (i, [vp, vp, vp]),
         "dp_neighbor_pairs_static": (i, [i64, vp, vp, d, i64, vp, i64p, vp]),
+        "dp_fitting": (i, [vp, i64, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -320,3 +321,15 @@ def dp_neighbor_pairs_static(coords, box, rlist, stream=None):
                                         b.ctypes.data_as(C.c_void_p), float(rlist), cnt.value,
                                         C.c_void_p(out.data_ptr()), C.byref(cnt), stream), None)
     return out[:cnt.value]
+
+
+def dp_fitting(h, types, T):
+    """Per-atom energies and dE/dT for given T [n, 4, M] (host arrays)."""
+    T = np.ascontiguousarray(T, np.float32)
+    n = T.shape[0]
+    t = np.ascontiguousarray(types, np.int32)
+    e = np.zeros(max(n, 1))
+    dT = np.zeros_like(T) if n else np.zeros((1,) + T.shape[1:], np.float32)
+    _check(lib.dp_fitting(h, n, t.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p),
+                          e.ctypes.data_as(C.c_void_p), dT.ctypes.data_as(C.c_void_p)), h)
+    return e[:n], dT[:n]

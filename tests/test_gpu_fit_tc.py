@@ -1,0 +1,139 @@
+"""Tensor-core (tcgen05, BF16 operands, FP32 accumulation) fitting mode.
+
+The same per-atom descriptors go through the FP32 CUDA-core fitting stage and
+the tensor-core one; the BF16 mode's errors are measured and stated (the
+paper notes that mixed precision has accuracy problems, Sec. 7), with bounds
+that a wrong tile, descriptor or epilogue would exceed by orders of
+magnitude."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_01446_gb300 import inputs
+from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, PARITY_LOG, TABLE_H, rmse
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dp():
+    from paper_2201_01446_gb300 import dp as _dp
+    return _dp
+
+
+def _handle(dp, path, prec):
+    o = dp.dp_options_default()
+    o.fit_precision = prec
+    return dp.dp_create(path, 1, CU_RC, CU_RCS, [CU_SEL], options=o, stream=None)
+
+
+def _handles(dp, path):
+    return _handle(dp, path, 0), _handle(dp, path, 1)
+
+
+@pytest.mark.parametrize("std", [0.1, 1.0])
+def test_tc_fitting_vs_fp32_and_oracle(dp, model_dir, std):
+    path = str(model_dir / f"cu_tc_{std}.model")
+    inputs.write_seeded_model(path, inputs.COPPER_SPEC, seed=0, std=std)
+    h0, h1 = _handles(dp, path)
+    try:
+        # ragged row count (not a multiple of the 128-row tile)
+        x, t, box = inputs.fcc_copper((5, 5, 6), sigma=0.1, seed=3)
+        T = dp.dp_descriptor(h0, x, t, box, 128)
+        e0, dT0 = dp.dp_fitting(h0, t, T)
+        e1, dT1 = dp.dp_fitting(h1, t, T)
+    finally:
+        dp.dp_destroy(h0)
+        dp.dp_destroy(h1)
+    m = oracle.Model(path)
+    eo = np.array([m.fit(0, np.einsum("cb,ca->ba", T[i].astype(np.float64),
+                                      T[i, :, :16].astype(np.float64)).ravel())[0]
+                   for i in range(0, len(x), 37)])
+    de_tc = float(np.abs(e1 - e0).max())
+    de_or = float(np.abs(e1[::37] - eo).max())
+    ddt = float(np.abs(dT1 - dT0).max() / np.abs(dT0).max())
+    PARITY_LOG.append(dict(case=f"tc bf16 fitting std {std}", natoms=len(x), max_dEi_vs_fp32=de_tc,
+                           max_dEi_vs_oracle=de_or, max_rel_dT=ddt,
+                           fp32_vs_oracle=float(np.abs(e0[::37] - eo).max())))
+    # BF16 operands: ~2^-9 relative per operand; a broken tile, descriptor or
+    # epilogue gives errors of the order of the values themselves
+    scale = float(np.abs(e0).max())
+    assert de_tc < 5e-2 * scale, (de_tc, scale)
+    assert de_or < 5e-2 * scale
+    assert ddt < 0.3, ddt
+    assert np.abs(e0[::37] - eo).max() < 1e-5 * max(1, scale)
+
+
+def test_tc_mode_forces_vs_oracle(dp, cu_model_path):
+    # the configured model end to end with the BF16 fitting mode: errors stated
+    m = oracle.Model(cu_model_path)
+    tab = oracle.Table(m, TABLE_H, CU_SMAX)
+    o = dp.dp_options_default()
+    o.fit_precision = 1
+    h = dp.dp_create(cu_model_path, 1, CU_RC, CU_RCS, [CU_SEL], options=o, stream=None)
+    try:
+        x, t, box = inputs.fcc_copper(5, sigma=0.05, seed=1)
+        E, F, V, Ei = dp.dp_compute(h, x, t, box, atom_energy=True)
+    finally:
+        dp.dp_destroy(h)
+    r = oracle.evaluate(m, tab, CU_RC, CU_RCS, CU_SEL, x, t, box)
+    de = abs(E - r["energy"]) / len(x)
+    fr = rmse(F, r["force"])
+    frms = float(np.sqrt((r["force"] ** 2).mean()))
+    PARITY_LOG.append(dict(case="tc bf16 config1 Cu 500", natoms=len(x), dE_per_atom=de,
+                           force_rmse=fr, force_rms=frms))
+    assert de < 1e-3 and fr < 0.3 * frms + 1e-9, (de, fr, frms)
+
+
+@pytest.mark.parametrize("std", [0.1, 1.0])
+def test_split_tc_fitting_matches_fp32(dp, model_dir, std):
+    # FP32-accurate tensor-core mode: each operand as 3 BF16 pieces, six piece
+    # products accumulated in FP32; held to the FP32 path's error level
+    path = str(model_dir / f"cu_split_{std}.model")
+    inputs.write_seeded_model(path, inputs.COPPER_SPEC, seed=0, std=std)
+    h0, h2 = _handle(dp, path, 0), _handle(dp, path, 2)
+    try:
+        x, t, box = inputs.fcc_copper((5, 5, 6), sigma=0.1, seed=3)
+        T = dp.dp_descriptor(h0, x, t, box, 128)
+        e0, dT0 = dp.dp_fitting(h0, t, T)
+        e2, dT2 = dp.dp_fitting(h2, t, T)
+    finally:
+        dp.dp_destroy(h0)
+        dp.dp_destroy(h2)
+    m = oracle.Model(path)
+    sub = list(range(0, len(x), 37))
+    eo = np.array([m.fit(0, np.einsum("cb,ca->ba", T[i].astype(np.float64),
+                                      T[i, :, :16].astype(np.float64)).ravel())[0] for i in sub])
+    d0 = float(np.abs(e0[sub] - eo).max())
+    d2 = float(np.abs(e2[sub] - eo).max())
+    ddt = float(np.abs(dT2 - dT0).max() / np.abs(dT0).max())
+    PARITY_LOG.append(dict(case=f"tc split fitting std {std}", natoms=len(x),
+                           fp32_vs_oracle=d0, split_vs_oracle=d2, max_rel_dT_vs_fp32=ddt))
+    # measured: 1e-6 (std 0.1) and 1e-5 (std 1.0) relative, 6-8x the FP32
+    # CUDA-core path: FP32 accumulation over ~800 tensor-core steps per row
+    scale = max(1.0, float(np.abs(eo).max()))
+    assert d2 < 2e-5 * scale, (d2, d0)
+    assert ddt < 2e-4, ddt
+
+
+def test_split_mode_end_to_end(dp, cu_model_path, cu_stress_path):
+    for path, stress in ((cu_model_path, False), (cu_stress_path, True)):
+        m = oracle.Model(path)
+        tab = oracle.Table(m, TABLE_H, CU_SMAX)
+        h = _handle(dp, path, 2)
+        try:
+            x, t, box = inputs.fcc_copper(5, sigma=0.05, seed=1)
+            E, F, V, Ei = dp.dp_compute(h, x, t, box, atom_energy=True)
+        finally:
+            dp.dp_destroy(h)
+        r = oracle.evaluate(m, tab, CU_RC, CU_RCS, CU_SEL, x, t, box)
+        de = abs(E - r["energy"]) / len(x)
+        fr = rmse(F, r["force"])
+        frms = float(np.sqrt((r["force"] ** 2).mean()))
+        PARITY_LOG.append(dict(case=f"tc split Cu 500 stress={stress}", natoms=len(x),
+                               dE_per_atom=de, force_rmse=fr, force_rms=frms))
+        if not stress:  # the configured model: the FP32 path's stated bars
+            assert de < 1e-6 and fr < 1e-5, (de, fr)
+        else:  # stated: ~1e-5 relative energy, ~1e-4 relative force
+            assert de < 2e-5 * float(np.abs(r["atom_energy"]).mean()), de
+            assert fr < 3e-4 * frms, (fr, frms)
