@@ -100,7 +100,7 @@ struct dp_handle {
   FitNet nets[DP_MAXT];
   FitNetTC nets_tc[DP_MAXT];
   float b_out[DP_MAXT] = {0};
-  DevBuf fitbuf, fit_bf16, fitbuf_tc;
+  DevBuf fitbuf, fit_bf16, fitbuf_tc, plain_w, plain_nets;
   FitScratch fs{};
   FitScratchTC fs_tc{};
   int32_t* status_host = nullptr;
@@ -358,7 +358,9 @@ dp_status ensure_atoms(dp_handle* h, Work& w, int64_t n) {
   CK(ensure(w.ffix, N * 3 * sizeof(unsigned long long)), "alloc f");
   CK(ensure(w.f, N * 3 * sizeof(double)), "alloc f");
   CK(ensure(w.idx, N * sizeof(int32_t)), "alloc idx");
-  CK(ensure(w.vir_part, (size_t)tab_kernel_slots(n) * 9 * sizeof(double)), "alloc virial");
+  CK(ensure(w.vir_part,
+            (size_t)std::max(tab_kernel_slots(n), plain_kernel_slots(n)) * 9 * sizeof(double)),
+     "alloc virial");
   CK(ensure(w.red_part, (size_t)sum_rows_part_size(n, 9) * sizeof(double)), "alloc red");
   CK(ensure(w.red_out, 32 * sizeof(double)), "alloc red");
   CK(ensure(w.pairs, sizeof(unsigned long long)), "alloc counters");
@@ -530,6 +532,22 @@ dp_status run_fitting(dp_handle* h, int t, int64_t cnt, const int32_t* idx, cons
   return DP_OK;
 }
 
+// environment matrix + embedding + contraction: T of every atom
+dp_status embed_forward(dp_handle* h, Work& w, const EnvParams& ep) {
+  if (h->opt.tabulated) {
+    if (launch_tab_fwd(h->st, w.n, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
+                       w.cap, w.geom, ep, P<float>(h->table), P<float>(w.T),
+                       P<int32_t>(h->status), P<unsigned long long>(w.pairs)))
+      return fail(h, DP_ERR_UNIMPLEMENTED, "tabulated kernel cannot run this model shape");
+  } else {
+    if (launch_plain_fwd(h->st, w.n, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
+                         w.cap, w.geom, ep, h->plain_nets.p, h->emb_w[0], P<float>(w.T),
+                         P<unsigned long long>(w.pairs)))
+      return fail(h, DP_ERR_UNIMPLEMENTED, "plain kernel cannot run this model shape");
+  }
+  return DP_OK;
+}
+
 // energy, forces, virial from the current list and offsets
 dp_status evaluate(dp_handle* h, Work& w) {
   const int64_t n = w.n;
@@ -542,10 +560,7 @@ dp_status evaluate(dp_handle* h, Work& w) {
   CK(cudaMemsetAsync(w.pairs.p, 0, sizeof(unsigned long long), h->st), "memset");
   {
     Phase ph(h, 1);
-    if (launch_tab_fwd(h->st, n, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn), w.cap,
-                       w.geom, ep, P<float>(h->table), P<float>(w.T), P<int32_t>(h->status),
-                       P<unsigned long long>(w.pairs)))
-      return fail(h, DP_ERR_UNIMPLEMENTED, "tabulated kernel cannot run this model shape");
+    CKS(embed_forward(h, w, ep));
   }
   Phase ph_fit(h, 2);
   for (int t = 0; t < h->ntypes; ++t) {
@@ -558,18 +573,27 @@ dp_status evaluate(dp_handle* h, Work& w) {
   ph_fit.end();
   {
     Phase ph(h, 3);
-    if (launch_tab_bwd(h->st, n, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn), w.cap,
-                       w.geom, ep, P<float>(h->table), P<float>(w.dT),
-                       P<unsigned long long>(w.ffix), P<double>(w.vir_part), tab_kernel_slots(n),
-                       P<int32_t>(h->status)))
-      return fail(h, DP_ERR_UNIMPLEMENTED, "tabulated kernel cannot run this model shape");
+    if (h->opt.tabulated) {
+      if (launch_tab_bwd(h->st, n, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
+                         w.cap, w.geom, ep, P<float>(h->table), P<float>(w.dT),
+                         P<unsigned long long>(w.ffix), P<double>(w.vir_part),
+                         tab_kernel_slots(n), P<int32_t>(h->status)))
+        return fail(h, DP_ERR_UNIMPLEMENTED, "tabulated kernel cannot run this model shape");
+    } else {
+      CK(cudaMemsetAsync(w.vir_part.p, 0, w.vir_part.bytes, h->st), "memset");
+      if (launch_plain_bwd(h->st, n, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
+                           w.cap, w.geom, ep, h->plain_nets.p, h->emb_w[0], P<float>(w.dT),
+                           P<unsigned long long>(w.ffix), P<double>(w.vir_part),
+                           plain_kernel_slots(n), P<int32_t>(h->status)))
+        return fail(h, DP_ERR_UNIMPLEMENTED, "plain kernel cannot run this model shape");
+    }
   }
   Phase ph_int(h, 4);
   launch_force_finalize(h->st, n, P<unsigned long long>(w.ffix), P<double>(w.f),
                         P<int32_t>(h->status));
   launch_sum_rows(h->st, n, 1, P<double>(w.e_atom), P<double>(w.red_part), P<double>(w.red_out));
-  launch_sum_rows(h->st, tab_kernel_slots(n), 9, P<double>(w.vir_part), P<double>(w.red_part),
-                  P<double>(w.red_out) + 1);
+  launch_sum_rows(h->st, h->opt.tabulated ? tab_kernel_slots(n) : plain_kernel_slots(n), 9,
+                  P<double>(w.vir_part), P<double>(w.red_part), P<double>(w.red_out) + 1);
   launch_check_energy(h->st, n, P<double>(w.e_atom), P<int32_t>(h->status));
   CK(cudaGetLastError(), "evaluation kernels");
   return DP_OK;
@@ -648,7 +672,8 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
       !(rcs < rc) || !(h->opt.table_step > 0) || !(h->opt.s_max > 0) || h->opt.skin < 0 ||
       h->opt.rebuild_every < 1)
     return bail(DP_ERR_ARG);
-  if (h->opt.tabulated != 1 || h->opt.fit_precision < 0 || h->opt.fit_precision > 2)
+  if (h->opt.tabulated < 0 || h->opt.tabulated > 1 || h->opt.fit_precision < 0 ||
+      h->opt.fit_precision > 2)
     return bail(DP_ERR_UNIMPLEMENTED);
   HostModel m;
   std::string why;
@@ -779,6 +804,60 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
       nt.w_out = nf.w_out;
       nt.b_out = nf.b_out;
     }
+  }
+  // FP32 embedding weights (and transposes) for the plain untabulated path
+  if (m.n_emb == 3 && m.emb_w[0] <= 32) {
+    const int d1 = m.emb_w[0], d2 = m.emb_w[1], Me = m.emb_w[2];
+    // every sub-array starts on a 16-byte boundary (the kernels read float4)
+    auto pad4 = [](size_t v) { return (v + 3) & ~(size_t)3; };
+    const size_t oW0 = 0, ob0 = pad4(d1), oW1 = ob0 + pad4(d1), ob1 = oW1 + pad4((size_t)d1 * d2),
+                 oW2 = ob1 + pad4(d2), ob2 = oW2 + pad4((size_t)d2 * Me),
+                 oW1T = ob2 + pad4(Me), oW2T = oW1T + pad4((size_t)d1 * d2),
+                 per = oW2T + pad4((size_t)d2 * Me);
+    std::vector<float> pw((size_t)np * per, 0.0f);
+    for (int p = 0; p < np; ++p) {
+      float* q = pw.data() + (size_t)p * per;
+      const double* W0 = m.data.data() + m.emb_off[p * 3 + 0];  // W0[d1], b0[d1]
+      const double* W1 = m.data.data() + m.emb_off[p * 3 + 1];  // W1[d1][d2], b1[d2]
+      const double* W2 = m.data.data() + m.emb_off[p * 3 + 2];  // W2[d2][Me], b2[Me]
+      for (int k = 0; k < d1; ++k) {
+        q[oW0 + k] = (float)W0[k];
+        q[ob0 + k] = (float)W0[d1 + k];
+      }
+      for (size_t k = 0; k < (size_t)d1 * d2; ++k) q[oW1 + k] = (float)W1[k];
+      for (int k = 0; k < d2; ++k) q[ob1 + k] = (float)W1[(size_t)d1 * d2 + k];
+      for (size_t k = 0; k < (size_t)d2 * Me; ++k) q[oW2 + k] = (float)W2[k];
+      for (int k = 0; k < Me; ++k) q[ob2 + k] = (float)W2[(size_t)d2 * Me + k];
+      for (int mm = 0; mm < d2; ++mm)
+        for (int k = 0; k < d1; ++k) q[oW1T + (size_t)mm * d1 + k] = (float)W1[(size_t)k * d2 + mm];
+      for (int c = 0; c < Me; ++c)
+        for (int l = 0; l < d2; ++l) q[oW2T + (size_t)c * d2 + l] = (float)W2[(size_t)l * Me + c];
+    }
+    const size_t rb = plain_net_bytes();
+    std::vector<unsigned char> recs((size_t)np * rb);
+    if (!up(h->plain_w, pw.data(), sizeof(float) * pw.size())) {
+      h->err = "device allocation failed";
+      cudaGetLastError();
+      return bail(DP_ERR_OOM);
+    }
+    const float* dpw = P<float>(h->plain_w);
+    for (int p = 0; p < np; ++p) {
+      const float* b = dpw + (size_t)p * per;
+      if (!plain_net_fill(recs.data() + (size_t)p * rb, b + oW0, b + ob0, b + oW1, b + ob1,
+                          b + oW2, b + ob2, b + oW1T, b + oW2T) ||
+          Me % 4) {
+        h->err = "plain embedding weights are not 16-byte aligned";
+        return bail(DP_ERR_UNIMPLEMENTED);
+      }
+    }
+    if (!up(h->plain_nets, recs.data(), recs.size())) {
+      h->err = "device allocation failed";
+      cudaGetLastError();
+      return bail(DP_ERR_OOM);
+    }
+  } else if (h->opt.tabulated == 0) {
+    h->err = "the plain path needs three doubling embedding layers with d1 <= 32";
+    return bail(DP_ERR_UNIMPLEMENTED);
   }
   if (table_build(h->st, P<double>(h->emb64), P<int64_t>(h->emb_off), m.n_emb, m.emb_w, np, h->h,
                   h->n_int, P<float>(h->table)) != 0) {
@@ -913,10 +992,7 @@ dp_status dp_descriptor(dp_handle* h, int64_t natoms, const double* coords, cons
   CKS(status_errors(h));
   if (natoms == 0) return DP_OK;
   const EnvParams ep = env_params(h);
-  if (launch_tab_fwd(h->st, natoms, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
-                     w.cap, w.geom, ep, P<float>(h->table), P<float>(w.T), P<int32_t>(h->status),
-                     nullptr))
-    return fail(h, DP_ERR_UNIMPLEMENTED, "tabulated kernel cannot run this model shape");
+  CKS(embed_forward(h, w, ep));
   CKS(read_status(h));
   CKS(status_errors(h));
   CK(cudaMemcpy(T_out, w.T.p, sizeof(float) * 4 * h->M * natoms, cudaMemcpyDeviceToHost),

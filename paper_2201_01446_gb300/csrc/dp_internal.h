@@ -85,6 +85,19 @@ int launch_tab_bwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t
                    double* vir_part, int vir_slots, int32_t* status);
 int tab_kernel_slots(int64_t n);  // number of virial partial slots the bwd kernel writes
 
+// plain untabulated embedding (the comparator of the tabulation), FP32
+int plain_kernel_slots(int64_t n);
+size_t plain_net_bytes();
+bool plain_net_fill(void* rec, const float* W0, const float* b0, const float* W1, const float* b1,
+                    const float* W2, const float* b2, const float* W1T, const float* W2T);
+int launch_plain_fwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t* nlist,
+                     const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
+                     const void* nets, int d1, float* T, unsigned long long* pair_count);
+int launch_plain_bwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t* nlist,
+                     const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
+                     const void* nets, int d1, const float* dT, unsigned long long* ffix,
+                     double* vir_part, int vir_slots, int32_t* status);
+
 // ---------------------------------------------------------------- fitting
 struct FitNet {           // one centre type, FP32 device pointers
   int nl;                 // hidden layers

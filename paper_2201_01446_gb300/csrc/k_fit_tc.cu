@@ -21,7 +21,13 @@
 namespace {
 
 constexpr int kBM = 128;        // rows per tile (one TMEM lane per row)
-constexpr int kTmemCols = 256;  // accumulator columns (NT <= 256)
+// TMEM columns: one accumulator of NT <= 256 columns, or (split operands) the
+// exact hi*hi products in columns 0..255 and the five small piece products
+// in columns 256..511, so the dominant sum sees 6x fewer FP32 accumulations
+template <int PC>
+struct TmemCols {
+  static constexpr int value = PC == 1 ? 256 : 512;
+};
 constexpr long long kSpinLimit = 20000000;  // bounded mbarrier waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -177,7 +183,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(kTmemCols));
+                 "r"(TmemCols<PC>::value));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -251,10 +257,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
           const uint64_t ad = make_desc(st0 + pa * C::A_BYTES + j * 256, 128, C::SBO);
           const uint64_t bd = make_desc(st0 + PC * C::A_BYTES + pb * C::B_BYTES + j * 256, 128,
                                         C::SBO);
-          const uint32_t acc = (kc > 0 || j > 0 || q > 0) ? 1u : 0u;
+          // accumulator 0: (h,h); accumulator 1 (PC = 3): the other products
+          const uint32_t dst = tmem + (q > 0 ? 256u : 0u);
+          const uint32_t acc = (kc > 0 || j > 0 || q > 1) ? 1u : 0u;
           asm volatile(
               "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
               "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
         }
       }
@@ -287,6 +295,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
       const int c0 = ch * 16;
       float v[16];
       tmem_ld16(tbase + (uint32_t)c0, v);
+      if (PC > 1) {
+        float v2[16];
+        tmem_ld16(tbase + 256u + (uint32_t)c0, v2);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] += v2[k];
+      }
       if (!rok) continue;
       const int n = n0 + c0;
       const size_t o = (size_t)row * ep.ldo + n;
@@ -366,7 +380,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
-                 "r"(kTmemCols));
+                 "r"(TmemCols<PC>::value));
 }
 
 template <int EPI, int PC>

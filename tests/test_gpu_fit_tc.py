@@ -109,11 +109,11 @@ def test_split_tc_fitting_matches_fp32(dp, model_dir, std):
     ddt = float(np.abs(dT2 - dT0).max() / np.abs(dT0).max())
     PARITY_LOG.append(dict(case=f"tc split fitting std {std}", natoms=len(x),
                            fp32_vs_oracle=d0, split_vs_oracle=d2, max_rel_dT_vs_fp32=ddt))
-    # measured: 1e-6 (std 0.1) and 1e-5 (std 1.0) relative, 6-8x the FP32
-    # CUDA-core path: FP32 accumulation over ~800 tensor-core steps per row
+    # measured: about twice the FP32 CUDA-core path's error (the hi*hi
+    # products and the small piece products accumulate in separate TMEM sums)
     scale = max(1.0, float(np.abs(eo).max()))
-    assert d2 < 2e-5 * scale, (d2, d0)
-    assert ddt < 2e-4, ddt
+    assert d2 < 5e-6 * scale, (d2, d0)
+    assert ddt < 5e-5, ddt
 
 
 def test_split_mode_end_to_end(dp, cu_model_path, cu_stress_path):
@@ -132,8 +132,9 @@ def test_split_mode_end_to_end(dp, cu_model_path, cu_stress_path):
         frms = float(np.sqrt((r["force"] ** 2).mean()))
         PARITY_LOG.append(dict(case=f"tc split Cu 500 stress={stress}", natoms=len(x),
                                dE_per_atom=de, force_rmse=fr, force_rms=frms))
-        if not stress:  # the configured model: the FP32 path's stated bars
+        # the FP32 path's bars (configured: absolute; stress: FP32-relative)
+        if not stress:
             assert de < 1e-6 and fr < 1e-5, (de, fr)
-        else:  # stated: ~1e-5 relative energy, ~1e-4 relative force
-            assert de < 2e-5 * float(np.abs(r["atom_energy"]).mean()), de
-            assert fr < 3e-4 * frms, (fr, frms)
+        else:
+            assert de < max(1e-6, 2e-6 * float(np.abs(r["atom_energy"]).mean())), de
+            assert fr < max(1e-5, 3e-5 * frms), (fr, frms)

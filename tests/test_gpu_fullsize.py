@@ -13,11 +13,15 @@ from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, PARITY_LOG, TABLE_H
 pytestmark = pytest.mark.gpu
 
 
-def test_fullsize_4m_copper_sampled(cu_model_path):
+@pytest.mark.parametrize("prec", [0, 2])
+def test_fullsize_4m_copper_sampled(cu_model_path, prec):
+    # fit_precision 0: FP32 CUDA cores; 2: FP32-accurate tensor cores (the bench's mode)
     from paper_2201_01446_gb300 import dp
     x, t, box = inputs.fcc_copper(100, sigma=0.0)
     v = inputs.maxwell_velocities(np.full(len(x), inputs.MASS_CU), 330.0, seed=2)
-    h = dp.dp_create(cu_model_path, 1, CU_RC, CU_RCS, [CU_SEL], stream=None)
+    o = dp.dp_options_default()
+    o.fit_precision = prec
+    h = dp.dp_create(cu_model_path, 1, CU_RC, CU_RCS, [CU_SEL], options=o, stream=None)
     try:
         s = dp.dp_system_create(h, x, v, t, [inputs.MASS_CU], box)
         dp.dp_md_step(h, s, 10, 1.0)
@@ -36,7 +40,8 @@ def test_fullsize_4m_copper_sampled(cu_model_path):
     e_ref, f_ref = oracle.eval_subset(m, tab, CU_RC, CU_RCS, CU_SEL, xg, t, box, ie, jf)
     de = np.abs(Ei[ie] - e_ref)
     df = np.sqrt(((F[jf] - f_ref) ** 2).mean())
-    PARITY_LOG.append(dict(case="fullsize Cu 4M (sampled)", natoms=len(x), stress=False,
+    PARITY_LOG.append(dict(case=f"fullsize Cu 4M (sampled) fit_precision {prec}", natoms=len(x),
+                           stress=False,
                            max_dEi=float(de.max()), force_rmse=float(df),
                            force_rms=float(np.sqrt((f_ref ** 2).mean()))))
     assert de.max() < 1e-6

@@ -263,3 +263,32 @@ def test_device_pointer_path(dp, cu_stress):
     Eh, Fh, Vh, Eih = dp.dp_compute(h, x, t, box, atom_energy=True)
     assert float(E.cpu()[0]) == Eh
     assert np.array_equal(F.cpu().numpy(), Fh) and np.array_equal(V.cpu().numpy(), Vh)
+
+
+# ------------------------------------------------------------------ plain untabulated path
+@pytest.mark.parametrize("which", ["configured", "stress"])
+def test_plain_untabulated_parity(dp, cu_model_path, cu_stress_path, which):
+    # the comparator path evaluates the embedding net itself: compared with
+    # the oracle's untabulated model (table = None)
+    path = cu_model_path if which == "configured" else cu_stress_path
+    m = oracle.Model(path)
+    h = _handle(dp, path, tabulated=0)
+    try:
+        x, t, box = inputs.fcc_copper(5, sigma=0.05, seed=1)
+        _parity(dp, h, m, None, x, t, box, stress=which == "stress", tag=f"plain Cu 500 {which}")
+        xr, tr, br = inputs.fcc_copper((3, 4, 5), sigma=0.15, seed=2)
+        _parity(dp, h, m, None, xr, tr, br, stress=which == "stress", tag=f"plain Cu 240 {which}")
+    finally:
+        dp.dp_destroy(h)
+
+
+def test_plain_water_two_types(dp, water_model_path):
+    m = oracle.Model(water_model_path)
+    h = _handle(dp, water_model_path, ntypes=2, rc=6.0, rcs=0.5, sel=(46, 92), s_max=1.25,
+                tabulated=0)
+    try:
+        x, t, box = inputs.water_like(64, L=12.417, seed=3)
+        _parity(dp, h, m, None, x, t, box, sel=[46, 92], rc=6.0, rcs=0.5, stress=True,
+                tag="plain water 192 std 1.0")
+    finally:
+        dp.dp_destroy(h)
