@@ -141,8 +141,7 @@ struct FitNetTC {
 struct FitScratchTC {
   int64_t rows;                  // rows per chunk; piece stride of an array = rows * width
   int wmax;
-  __nv_bfloat16* Dh;             // pieces of [rows][din]
-  float* dD;                     // [rows][din]
+  float* part;                   // [din/256][rows][64] partials of dE/dT (x < 16)
   float* t[DP_MAXFIT];           // [rows][wout[k]] tanh outputs
   float* z[DP_MAXFIT];           // [rows][wout[k]] layer outputs (k >= 1)
   __nv_bfloat16* zh[DP_MAXFIT];  // pieces of the layer outputs (next A operand)

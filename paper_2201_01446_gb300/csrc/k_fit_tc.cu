@@ -94,7 +94,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-enum { TC_PLAIN = 0, TC_L0 = 1, TC_MID = 2, TC_LAST = 3, TC_BWD = 4 };
+// TC_L0: layer 0, its A operand (the descriptor D of Eq. 2) formed from T in
+// the producer; TC_DT: the input gradient dE/dD contracted with T into dE/dT
+// in the epilogue (D and dE/dD never reach global memory)
+enum { TC_PLAIN = 0, TC_L0 = 1, TC_MID = 2, TC_LAST = 3, TC_BWD = 4, TC_DT = 5 };
 
 struct TcEpi {
   const float* bias;       // [N]
@@ -112,6 +115,12 @@ struct TcEpi {
   double* e_atom;          // TC_LAST: E_i written at idx[row] (or row)
   const int32_t* idx;
   int32_t* err;            // error word (timeouts)
+  const float* T;          // TC_L0 / TC_DT: T rows [4][Mw] at tidx[row] (or row)
+  float* dT;               // TC_DT: dE/dT rows, same indexing as T
+  const int32_t* tidx;
+  int Mw;                  // embedding width M
+  float* part;             // TC_DT: per (N tile, half) partial sums [slot][rows][64]
+  int64_t part_ps;         // elements between slots
 };
 
 // x = h + m + l with h, m, l BF16 (the FP32 value to ~2^-25 relative)
@@ -196,15 +205,68 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
   constexpr int KG = C::BK / 8;  // 16-byte K groups per row in a stage
 
   auto stage_ptr = [&](int s) { return base + s * C::STAGE; };
+  // TC_L0: this thread's T[row][c][hal*8 .. hal*8+7], kept for every K chunk
+  float ta[4][8];
+  const float* trow_ptr = nullptr;
+  if (EPI == TC_L0) {
+    const int r = tid >> 1, hal = tid & 1;
+    const int gm = m0 + r;
+    if (gm < M) trow_ptr = ep.T + (size_t)(ep.tidx ? ep.tidx[gm] : gm) * 4 * ep.Mw;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ta[c][j] = trow_ptr ? __ldg(trow_ptr + c * ep.Mw + hal * 8 + j) : 0.0f;
+  }
   // fill stage s with chunk kc: every piece of A rows m0.. and B rows n0..
   auto load_stage = [&](int s, int kc) {
     const int k0 = kc * C::BK;
     const uint32_t st0 = smem_u32(stage_ptr(s));
+    if (EPI == TC_L0) {
+      // D[r][k] = sum_c T[c][k/16] T[c][k%16]: two threads per row, thread
+      // (row, hal) forms the 8-wide groups whose a-range is hal*8..hal*8+7
+      const int r = tid >> 1, hal = tid & 1;
+      const int gm = m0 + r;
+      unsigned char* sa = stage_ptr(s);
+      for (int kg = hal; kg < KG; kg += 2) {
+        const int k = k0 + kg * 8;
+        float x[8];
+        if (gm < M && k < K) {
+          const int b = k >> 4;
+          float tb[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) tb[c] = __ldg(trow_ptr + c * ep.Mw + b);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc = fmaf(tb[c], ta[c][j], acc);
+            x[j] = acc;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) x[j] = 0.0f;
+        }
+        __align__(16) __nv_bfloat16 pv[3][8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          pv[0][j] = __float2bfloat16_rn(x[j]);
+          if (PC > 1) {
+            const float r1 = x[j] - __bfloat162float(pv[0][j]);
+            pv[1][j] = __float2bfloat16_rn(r1);
+            pv[2][j] = __float2bfloat16_rn(r1 - __bfloat162float(pv[1][j]));
+          }
+        }
+        const int off = (r >> 3) * C::SBO + kg * 128 + (r & 7) * 16;
+#pragma unroll
+        for (int p = 0; p < PC; ++p)
+          *reinterpret_cast<uint4*>(sa + p * C::A_BYTES + off) = *reinterpret_cast<const uint4*>(pv[p]);
+      }
+    }
 #pragma unroll
     for (int p = 0; p < PC; ++p) {
       const uint32_t a0 = st0 + p * C::A_BYTES;
       const __nv_bfloat16* Ap = A + p * a_ps;
-      for (int q = tid; q < kBM * KG; q += kTcThreads) {
+      for (int q = tid; q < (EPI == TC_L0 ? 0 : kBM * KG); q += kTcThreads) {
         const int r = q / KG, kg = q % KG;
         const int gm = m0 + r, gk = k0 + kg * 8;
         const bool ok = gm < M && gk < K;
@@ -276,8 +338,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
   bool done = ok_run;
   for (int t = 0; t < 2; ++t)
     if (uses[t] > 0 && !mbar_wait(&bars[t], (uses[t] - 1) & 1)) done = false;
+  if (!done) atomicExch(&s_abort, 1);
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   __syncthreads();
+  done = s_abort == 0;  // uniform over the CTA (the epilogue synchronises)
   if (!done) {
     if (tid == 0 && ep.err) atomicAdd(ep.err, 1);
   } else {
@@ -291,6 +355,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
     const int nch = ntile / 16;
     const int c_beg = half ? (nch + 1) / 2 : 0, c_end = half ? nch : (nch + 1) / 2;
     float e_acc = 0.0f;
+    // TC_DT: T[row][c][0..15] and the partial sums of the second factor
+    float tl[4][16], part[4][16];
+    const float* tr = nullptr;
+    float* dtr = nullptr;
+    if (EPI == TC_DT) {
+      if (rok) {
+        const size_t trow = (size_t)(ep.tidx ? ep.tidx[row] : row) * 4 * ep.Mw;
+        tr = ep.T + trow;
+        dtr = ep.dT + trow;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int a = 0; a < 16; ++a) {
+          tl[c][a] = tr ? __ldg(tr + c * ep.Mw + a) : 0.0f;
+          part[c][a] = 0.0f;
+        }
+    }
     for (int ch = c_beg; ch < c_end; ++ch) {
       const int c0 = ch * 16;
       float v[16];
@@ -303,6 +385,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
       }
       if (!rok) continue;
       const int n = n0 + c0;
+      if (EPI == TC_DT) {
+        // v = dE/dD[b][0..15] with b = n/16 (Eq. 2: D[b][a] = sum_c T[c][b] T[c][a])
+        const int b = n >> 4;
+        float tb[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          tb[c] = __ldg(tr + c * ep.Mw + b);
+          float acc = 0.0f;
+#pragma unroll
+          for (int a = 0; a < 16; ++a) acc = fmaf(v[a], tl[c][a], acc);
+          dtr[c * ep.Mw + b] = acc;  // first factor: complete for this b
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int a = 0; a < 16; ++a) part[c][a] = fmaf(v[a], tb[c], part[c][a]);
+        continue;
+      }
       const size_t o = (size_t)row * ep.ldo + n;
       float r[16], b[16], tt[16], oa[16], ob[16], oh[16];
       if (EPI == TC_L0 || EPI == TC_MID || EPI == TC_LAST) {
@@ -368,6 +468,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
     if (EPI == TC_LAST) {
       s_e[half][row_t] = e_acc;
     }
+    if (EPI == TC_DT) {
+      // second factor (a < 16): the two halves meet in the (now idle) stage
+      // memory, row stride 65 floats (conflict-free); one partial per N tile
+      float* sp = reinterpret_cast<float*>(base) + row_t * 65;
+      if (half) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int a = 0; a < 16; ++a) sp[c * 16 + a] = part[c][a];
+      }
+      __syncthreads();
+      if (!half && rok) {
+        float* pp = ep.part + (size_t)blockIdx.y * ep.part_ps + (size_t)row * 64;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int a = 0; a < 16; a += 4)
+            *reinterpret_cast<float4*>(pp + c * 16 + a) =
+                make_float4(part[c][a] + sp[c * 16 + a], part[c][a + 1] + sp[c * 16 + a + 1],
+                            part[c][a + 2] + sp[c * 16 + a + 2], part[c][a + 3] + sp[c * 16 + a + 3]);
+      }
+    }
   }
   if (EPI == TC_LAST) {
     __syncthreads();
@@ -403,60 +525,18 @@ int tc_gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A, int ld
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-// D rows as BF16 pieces from T (gathered through idx):
-// D[r][b*m_lt + a] = sum_c T[c][b] T[c][a]
-template <int PC>
-__global__ void k_descr_pieces(int64_t rows, const int32_t* __restrict__ idx,
-                               const float* __restrict__ T, int M, int m_lt, int64_t ps,
-                               __nv_bfloat16* __restrict__ D) {
-  extern __shared__ float Ts[];
-  const int64_t r = blockIdx.x;
+// dE/dT[c][x] for x < 16 gets the second factor of Eq. 2's derivative,
+// sum_b dE/dD[b][x] T[c][b], as the fixed-order sum of the per-N-tile partials
+__global__ void k_dt_reduce(int64_t rows, const int32_t* __restrict__ idx, int M, int slots,
+                            int64_t part_ps, const float* __restrict__ part, float* __restrict__ dT) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * 64) return;
+  const int64_t r = i >> 6;
+  const int e = (int)(i & 63);  // c * 16 + x
+  float acc = 0.0f;
+  for (int sl = 0; sl < slots; ++sl) acc += part[(size_t)sl * part_ps + (size_t)r * 64 + e];
   const int64_t a = idx ? idx[r] : r;
-  for (int k = threadIdx.x; k < 4 * M; k += blockDim.x) Ts[k] = T[(size_t)a * 4 * M + k];
-  __syncthreads();
-  const int din = M * m_lt;
-  for (int e0 = threadIdx.x * 8; e0 < din; e0 += blockDim.x * 8) {
-    float x[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int e = e0 + k, b = e / m_lt, q = e - (e / m_lt) * m_lt;
-      float s = 0.0f;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) s = fmaf(Ts[c * M + b], Ts[c * M + q], s);
-      x[k] = s;
-    }
-    split_store<PC>(D, ps, (size_t)r * din + e0, x);
-  }
-}
-
-// dT from the FP32 dD rows (gathered through idx), as in the CUDA-core path
-__global__ void k_descr_bwd_tc(int64_t rows, const int32_t* __restrict__ idx,
-                               const float* __restrict__ T, const float* __restrict__ dD, int M,
-                               int m_lt, float* __restrict__ dT) {
-  extern __shared__ float sm[];
-  float* Ts = sm;
-  float* dDs = sm + 4 * M;
-  const int64_t r = blockIdx.x;
-  const int64_t a = idx ? idx[r] : r;
-  for (int k = threadIdx.x; k < 4 * M; k += blockDim.x) Ts[k] = T[(size_t)a * 4 * M + k];
-  for (int k = threadIdx.x; k < M * m_lt; k += blockDim.x) dDs[k] = dD[(size_t)r * M * m_lt + k];
-  __syncthreads();
-  for (int x = threadIdx.x; x < M; x += blockDim.x) {
-    float g[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int q = 0; q < m_lt; ++q) {
-      const float d = dDs[x * m_lt + q];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) g[c] = fmaf(d, Ts[c * M + q], g[c]);
-    }
-    if (x < m_lt)
-      for (int b = 0; b < M; ++b) {
-        const float d = dDs[b * m_lt + x];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) g[c] = fmaf(d, Ts[c * M + b], g[c]);
-      }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) dT[(size_t)a * 4 * M + c * M + x] = g[c];
-  }
+  dT[(size_t)a * 4 * M + (e >> 4) * M + (e & 15)] += acc;
 }
 
 // FP32 -> PC BF16 pieces, piece p at out + p*n
@@ -489,18 +569,16 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
   if (nl < 2 || nl > DP_MAXFIT) return -1;
   for (int k = 0; k < nl; ++k)
     if (net.wout[k] > 256 || net.wout[k] % 16) return -1;
-  if (din % 16) return -1;
+  if (din % 16 || m_lt != 16 || M < 16) return -1;  // the fused descriptor wants M< = 16
   const int64_t R = s.rows;  // piece strides of the activation scratch: R * width
   for (int64_t r0 = 0; r0 < n; r0 += R) {
     const int rows = (int)((n - r0) < R ? (n - r0) : R);
     const int32_t* id = idx ? idx + r0 : nullptr;
     const float* Tc = idx ? T : T + (size_t)r0 * 4 * M;
     float* dTc = idx ? dT : dT + (size_t)r0 * 4 * M;
-    DP_LAUNCHED(2);
-    k_descr_pieces<PC><<<rows, 128, sizeof(float) * 4 * M, st>>>(rows, id, Tc, M, m_lt,
-                                                               R * din, s.Dh);
-    // forward: layer 0 (no shortcut), hidden layers, last layer with the energy
-    const __nv_bfloat16* in = s.Dh;
+    // forward: layer 0 (its A operand D formed from T in the producer), hidden
+    // layers, last layer with the energy
+    const __nv_bfloat16* in = nullptr;
     int win = din;
     for (int k = 0; k < nl; ++k) {
       TcEpi ep{};
@@ -514,7 +592,10 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
         ep.out_a = s.t[0];
         ep.out_h = s.zh[0];
         ep.h_ps = R * net.wout[0];
-        rc = tc_gemm<TC_L0, PC>(st, rows, net.wout[0], din, in, din, R * din, net.WTh[0], din,
+        ep.T = Tc;
+        ep.tidx = id;
+        ep.Mw = M;
+        rc = tc_gemm<TC_L0, PC>(st, rows, net.wout[0], din, in, din, 0, net.WTh[0], din,
                                 net.w_ps[0], ep);
       } else if (k == nl - 1) {
         ep.R = net.shortcut[k] ? zb : nullptr;
@@ -567,16 +648,25 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       gi ^= 1;
     }
     {
+      // dE/dD = gp_0 W_0^T never leaves the chip: the epilogue contracts it
+      // with T into dE/dT and leaves per-N-tile partials of the x < 16 term
       TcEpi ep{};
-      ep.out_a = s.dD;
       ep.ldo = din;
       ep.err = err;
-      const int rc = tc_gemm<TC_PLAIN, PC>(st, rows, din, net.wout[0], s.gph[gi], net.wout[0],
-                                           R * s.wmax, net.Wh[0], net.wout[0], net.w_ps[0], ep);
+      ep.T = Tc;
+      ep.dT = dTc;
+      ep.tidx = id;
+      ep.Mw = M;
+      ep.part = s.part;
+      ep.part_ps = R * 64;
+      const int rc = tc_gemm<TC_DT, PC>(st, rows, din, net.wout[0], s.gph[gi], net.wout[0],
+                                        R * s.wmax, net.Wh[0], net.wout[0], net.w_ps[0], ep);
       if (rc) return rc;
     }
-    k_descr_bwd_tc<<<rows, 128, sizeof(float) * (4 * M + M * m_lt), st>>>(rows, id, Tc, s.dD, M,
-                                                                         m_lt, dTc);
+    const int slots = din <= 256 ? 1 : din / 256;
+    DP_LAUNCHED(1);
+    k_dt_reduce<<<(int)((rows * 64 + 255) / 256), 256, 0, st>>>(rows, id, M, slots, R * 64, s.part,
+                                                                dTc);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
