@@ -485,12 +485,13 @@ dp_status rebuild(dp_handle* h, Work& w, const double* L, double rlist) {
 
 dp_status ensure_fit_scratch_tc(dp_handle* h, int64_t rows_needed) {
   const int PCN = 3;  // room for three pieces serves both tensor-core modes
-  int64_t rows = std::min<int64_t>(std::max<int64_t>(rows_needed, 1), 65536);
+  // chunks of 8 x 152 tiles of 128 rows (whole waves on 152 SMs)
+  int64_t rows = std::min<int64_t>(std::max<int64_t>(rows_needed, 1), 8 * 152 * 128);
   rows = (rows + 127) / 128 * 128;
   if (rows <= h->fs_tc.rows) return DP_OK;
   int wmax = 0;
   for (int k = 0; k < h->n_fit; ++k) wmax = std::max(wmax, h->fit_w[k]);
-  const int slots = h->din <= 256 ? 1 : h->din / 256;  // per-N-tile partials of dE/dT
+  const int slots = (h->din + 255) / 256;  // per-N-tile partials of dE/dT
   size_t bytes = rows * (size_t)slots * 64 * 4 + rows * (size_t)wmax * (4 + 2 * 2 * PCN);
   for (int k = 0; k < h->n_fit; ++k) bytes += rows * (size_t)h->fit_w[k] * (4 + 4 + 2 * PCN);
   bytes += 64 * 256;
@@ -787,18 +788,20 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
       const FitNet& nf = h->nets[t];
       nt.nl = nf.nl;
       for (int k = 0; k < nf.nl; ++k) {
-        const int64_t ne = (int64_t)nf.win[k] * nf.wout[k];
         // pieces of W^T at 3*ofs.WT, pieces of W at 3*ofs.W (disjoint: 3 * fit.size() total)
         __nv_bfloat16* pwt = hb + 3 * ofs[t].WT[k];
         __nv_bfloat16* pw = hb + 3 * ofs[t].W[k];
-        launch_split_pieces(h->st, ne, fb + ofs[t].WT[k], pwt);
-        launch_split_pieces(h->st, ne, fb + ofs[t].W[k], pw);
+        const int pc = h->opt.fit_precision == 1 ? 1 : 3;
+        if (nf.wout[k] % 16 == 0 && nf.win[k] % 16 == 0) {
+          // pre-tiled B operands: W^T (N = wout, K = win), W (N = win, K = wout)
+          launch_tile_operand(h->st, nf.wout[k], nf.win[k], pc, fb + ofs[t].WT[k], pwt);
+          launch_tile_operand(h->st, nf.win[k], nf.wout[k], pc, fb + ofs[t].W[k], pw);
+        }
         nt.win[k] = nf.win[k];
         nt.wout[k] = nf.wout[k];
         nt.shortcut[k] = nf.shortcut[k];
         nt.WTh[k] = pwt;
         nt.Wh[k] = pw;
-        nt.w_ps[k] = ne;
         nt.b[k] = nf.b[k];
       }
       nt.w_out = nf.w_out;

@@ -127,28 +127,32 @@ int fit_simt(cudaStream_t st, int64_t n, const int32_t* idx, const FitNet& net, 
 
 // Tensor-core (tcgen05, BF16 operands, FP32 accumulate) fitting stage.  Each
 // BF16 operand has 1 piece (BF16 mode) or 3 pieces x = h + m + l (FP32-
-// accurate mode: six piece products accumulate in FP32).
+// accurate mode: six piece products accumulate in FP32).  Operands are kept
+// pre-tiled: per (row tile, 16-wide K chunk) one contiguous block holding all
+// pieces in the tensor core's no-swizzle K-major layout (weights in tiles of
+// N <= 256 rows, activations in tiles of 128 rows).
 struct FitNetTC {
   int nl;
   int win[DP_MAXFIT], wout[DP_MAXFIT], shortcut[DP_MAXFIT];
-  const __nv_bfloat16* WTh[DP_MAXFIT];  // pieces of [wout][win]: forward B operand
-  const __nv_bfloat16* Wh[DP_MAXFIT];   // pieces of [win][wout]: backward B operand
-  int64_t w_ps[DP_MAXFIT];              // elements between pieces (win * wout)
+  const __nv_bfloat16* WTh[DP_MAXFIT];  // tiled pieces of W^T [wout][win]: forward B operand
+  const __nv_bfloat16* Wh[DP_MAXFIT];   // tiled pieces of W [win][wout]: backward B operand
   const float* b[DP_MAXFIT];
   const float* w_out;
   float b_out;
 };
 struct FitScratchTC {
-  int64_t rows;                  // rows per chunk; piece stride of an array = rows * width
+  int64_t rows;                  // rows per chunk (a multiple of 128)
   int wmax;
   float* part;                   // [din/256][rows][64] partials of dE/dT (x < 16)
   float* t[DP_MAXFIT];           // [rows][wout[k]] tanh outputs
   float* z[DP_MAXFIT];           // [rows][wout[k]] layer outputs (k >= 1)
-  __nv_bfloat16* zh[DP_MAXFIT];  // pieces of the layer outputs (next A operand)
+  __nv_bfloat16* zh[DP_MAXFIT];  // tiled pieces of the layer outputs (next A operand)
   float* gz;                     // [rows][wmax]
-  __nv_bfloat16* gph[2];         // pieces of [rows][wmax] gradients (A operands)
+  __nv_bfloat16* gph[2];         // tiled pieces of [rows][<= wmax] gradients (A operands)
 };
-void launch_split_pieces(cudaStream_t st, int64_t n, const float* in, __nv_bfloat16* out);
+// FP32 B [N][K] (K contiguous) -> tiled BF16 pieces; -1 on an unsupported shape
+int launch_tile_operand(cudaStream_t st, int N, int K, int pieces, const float* src,
+                        __nv_bfloat16* out);
 int fit_tc(cudaStream_t st, int64_t n, const int32_t* idx, const FitNetTC& net, int M, int m_lt,
            const float* T, float* dT, double* e_atom, const FitScratchTC& s, int pieces,
            int32_t* err);

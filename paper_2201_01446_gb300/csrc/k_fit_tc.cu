@@ -1,18 +1,26 @@
 // Fitting net (Sec. 2.1) and descriptor (Eq. 2) on the 5th-generation tensor
 // cores: tcgen05.mma with BF16 operands in shared memory and the FP32
 // accumulator in tensor memory (TMEM), read back with tcgen05.ld for fused
-// epilogues (bias, tanh, shortcut, per-atom energy, gradient of tanh).
+// epilogues (bias, tanh, shortcut, per-atom energy, gradient of tanh, the
+// descriptor's own backward).
 //
-// One CTA (4 warps) computes a 128-row x NT-column tile of C = A B^T with A
-// [rows x K] and B [N x K] both K-contiguous BF16 in global memory.  K is
-// walked in chunks of 64 through two shared-memory stages filled with
-// cp.async (16-byte pieces written straight into the no-swizzle K-major core
-// matrix layout: 8 rows x 16 bytes per core matrix, consecutive K groups 128
-// bytes apart, consecutive 8-row groups 1024 bytes apart).  Thread 0 issues
-// four K=16 MMAs per chunk and commits them to the stage's mbarrier; a stage
-// is refilled only after that barrier's phase completes.  Every wait is
-// bounded: on timeout the kernel records an error word, stops issuing work,
-// waits (bounded) for its MMAs, frees its TMEM and returns.
+// One CTA computes a 128-row x NT-column tile of C = A B^T (A: rows x K, B:
+// N x K).  Both operands live in global memory PRE-TILED in the tensor core's
+// no-swizzle K-major shared-memory layout: for each 128-row (A) or NT-row (B)
+// tile and each 16-wide K chunk, one contiguous block holding every BF16
+// piece of the operand, core matrices of 8 rows x 16 bytes, the two K groups
+// 128 bytes apart, 8-row groups 256 bytes apart.  A pipeline stage is then
+// two bulk asynchronous copies (cp.async.bulk, completion counted in bytes on
+// the stage's mbarrier) issued by one thread; the previous GEMM's epilogue
+// writes its output straight into that layout for the next GEMM.
+//
+// Warp roles: warp 0 (one lane) issues the copies up to NS stages ahead,
+// warp 1 (one lane) issues the MMAs and commits each stage back to its
+// "empty" barrier, warps 4-7 (layer 0 only) form the descriptor D from T in
+// the stage's A slot, then all eight warps run the epilogue from TMEM.  Every
+// wait is bounded: on timeout the kernel records an error word, stops issuing
+// work, waits (bounded) for its own copies and MMAs, frees its TMEM and
+// returns.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -20,15 +28,30 @@
 
 namespace {
 
-constexpr int kBM = 128;        // rows per tile (one TMEM lane per row)
+constexpr int kBM = 128;   // rows per tile (one TMEM lane per row)
+constexpr int kBK = 16;    // K per stage: one K = 16 MMA step per piece product
+constexpr int kTcThreads = 256;
+constexpr long long kSpinLimit = 20000000;  // bounded mbarrier waits
+
 // TMEM columns: one accumulator of NT <= 256 columns, or (split operands) the
 // exact hi*hi products in columns 0..255 and the five small piece products
 // in columns 256..511, so the dominant sum sees 6x fewer FP32 accumulations
 template <int PC>
-struct TmemCols {
-  static constexpr int value = PC == 1 ? 256 : 512;
+struct TcCfg {
+  static constexpr int A_BYTES = kBM * kBK * 2;          // one piece of an A block
+  static constexpr int B_MAX = 256 * kBK * 2;            // one piece of a B block (NT <= 256)
+  static constexpr int STAGE = PC * (A_BYTES + B_MAX);
+  static constexpr int NS = PC == 1 ? 12 : 6;            // pipeline stages
+  static constexpr int NPROD = PC == 1 ? 1 : 6;          // piece products per stage
+  static constexpr int TMEM_COLS = PC == 1 ? 256 : 512;
+  static constexpr size_t SMEM = 128 + (size_t)NS * STAGE;
 };
-constexpr long long kSpinLimit = 20000000;  // bounded mbarrier waits
+
+// element offset of (row r, column k) inside one piece of a tiled block:
+// 8-row groups 128 elements apart, K groups 64 apart, rows 8 apart
+__host__ __device__ __forceinline__ int tile_off(int r, int k) {
+  return (r >> 3) * 128 + ((k >> 3) & 1) * 64 + (r & 7) * 8 + (k & 7);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -67,17 +90,36 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// bounded wait; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; ++it)
+// bounded wait; false on timeout (which raises the CTA's abort flag) or when
+// another role has already raised it (abort == nullptr: only the time limit)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (abort && *abort) return false;
+  }
+  if (abort) *abort = 1;
   return false;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  const int sz = valid ? 16 : 0;  // size 0: fill the 16 bytes with zeros
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(sz)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
                : "memory");
+}
+
+// bulk global -> shared copy (16-byte aligned, size a multiple of 16) whose
+// completion is counted in bytes on the mbarrier
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -94,9 +136,46 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// x = h + m + l with h, m, l BF16 (the FP32 value to ~2^-25 relative)
+template <int PC>
+__device__ __forceinline__ void split8(const float* x, __nv_bfloat16 (&pv)[3][8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    pv[0][j] = __float2bfloat16_rn(x[j]);
+    if (PC > 1) {
+      const float r1 = x[j] - __bfloat162float(pv[0][j]);
+      pv[1][j] = __float2bfloat16_rn(r1);
+      pv[2][j] = __float2bfloat16_rn(r1 - __bfloat162float(pv[1][j]));
+    }
+  }
+}
+
+// pieces of 8 consecutive columns n..n+7 (n % 8 == 0) of row `row` into an
+// activation stored pre-tiled for the next GEMM (width W = 16 * nkc)
+template <int PC>
+__device__ __forceinline__ void store_tiled(__nv_bfloat16* out, int nkc, int row, int n,
+                                            const float* x) {
+  __align__(16) __nv_bfloat16 pv[3][8];
+  split8<PC>(x, pv);
+  const size_t o =
+      ((size_t)(row >> 7) * nkc + (n >> 4)) * PC * (kBM * kBK) + tile_off(row & 127, n);
+#pragma unroll
+  for (int p = 0; p < PC; ++p)
+    *reinterpret_cast<uint4*>(out + o + p * (kBM * kBK)) = *reinterpret_cast<const uint4*>(pv[p]);
+}
+
+// pieces (a, b) multiplied for PC = 3: every product down to 2^-16 relative
+__device__ __forceinline__ void prod_pieces(int q, int& pa, int& pb) {
+  // (h,h) (h,m) (m,h) (h,l) (l,h) (m,m)
+  const int a[6] = {0, 0, 1, 0, 2, 1};
+  const int b[6] = {0, 1, 0, 2, 0, 1};
+  pa = a[q];
+  pb = b[q];
+}
+
 // TC_L0: layer 0, its A operand (the descriptor D of Eq. 2) formed from T in
-// the producer; TC_DT: the input gradient dE/dD contracted with T into dE/dT
-// in the epilogue (D and dE/dD never reach global memory)
+// the stage; TC_DT: the input gradient dE/dD contracted with T into dE/dT in
+// the epilogue (D and dE/dD never reach global memory)
 enum { TC_PLAIN = 0, TC_L0 = 1, TC_MID = 2, TC_LAST = 3, TC_BWD = 4, TC_DT = 5 };
 
 struct TcEpi {
@@ -109,8 +188,7 @@ struct TcEpi {
   float bout;
   float* out_a;            // FP32 [rows][ldo]: t (L0, MID) or C (PLAIN)
   float* out_b;            // FP32 [rows][ldo]: z (MID) or gz (BWD)
-  __nv_bfloat16* out_h;    // BF16 pieces [PC][rows][ldo] of the next A operand
-  int64_t h_ps;            // element stride between pieces of out_h
+  __nv_bfloat16* out_h;    // the next A operand, pre-tiled, width ldo
   int ldo;
   double* e_atom;          // TC_LAST: E_i written at idx[row] (or row)
   const int32_t* idx;
@@ -119,229 +197,174 @@ struct TcEpi {
   float* dT;               // TC_DT: dE/dT rows, same indexing as T
   const int32_t* tidx;
   int Mw;                  // embedding width M
-  float* part;             // TC_DT: per (N tile, half) partial sums [slot][rows][64]
+  float* part;             // TC_DT: per-N-tile partial sums [slot][rows][64]
   int64_t part_ps;         // elements between slots
 };
 
-// x = h + m + l with h, m, l BF16 (the FP32 value to ~2^-25 relative)
-template <int PC>
-__device__ __forceinline__ void split_store(__nv_bfloat16* out, int64_t ps, size_t o, const float (&x)[8]) {
-  __align__(16) __nv_bfloat16 hv[8], mv[8], lv[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    hv[k] = __float2bfloat16_rn(x[k]);
-    if (PC > 1) {
-      const float r1 = x[k] - __bfloat162float(hv[k]);
-      mv[k] = __float2bfloat16_rn(r1);
-      lv[k] = __float2bfloat16_rn(r1 - __bfloat162float(mv[k]));
-    }
-  }
-  *reinterpret_cast<uint4*>(out + o) = *reinterpret_cast<const uint4*>(hv);
-  if (PC > 1) {
-    *reinterpret_cast<uint4*>(out + ps + o) = *reinterpret_cast<const uint4*>(mv);
-    *reinterpret_cast<uint4*>(out + 2 * ps + o) = *reinterpret_cast<const uint4*>(lv);
-  }
-}
-
-template <int PC>
-struct TcCfg {
-  static constexpr int BK = PC == 1 ? 64 : 32;                 // K per stage
-  static constexpr int SBO = BK * 16;                          // bytes between 8-row groups
-  static constexpr int A_BYTES = kBM * BK * 2;                 // one piece of A
-  static constexpr int B_BYTES = 256 * BK * 2;                 // one piece of B
-  static constexpr int STAGE = PC * (A_BYTES + B_BYTES);
-  static constexpr int NPROD = PC == 1 ? 1 : 6;                // piece products
-  static constexpr size_t SMEM = 1024 + 2 * (size_t)STAGE + 64;
-};
-
-// pieces (a, b) multiplied for PC = 3: every product down to 2^-16 relative
-__device__ __forceinline__ void prod_pieces(int q, int& pa, int& pb) {
-  // (h,h) (h,m) (m,h) (h,l) (l,h) (m,m)
-  const int a[6] = {0, 0, 1, 0, 2, 1};
-  const int b[6] = {0, 1, 0, 2, 0, 1};
-  pa = a[q];
-  pb = b[q];
-}
-
-constexpr int kTcThreads = 256;
-
 template <int EPI, int PC>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, int NT,
-                                                           const __nv_bfloat16* __restrict__ A,
-                                                           int lda, int64_t a_ps,
-                                                           const __nv_bfloat16* __restrict__ B,
-                                                           int ldb, int64_t b_ps, TcEpi ep) {
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm(int M, int N, int K, int NT, const __nv_bfloat16* __restrict__ A,
+              const __nv_bfloat16* __restrict__ B, TcEpi ep) {
   using C = TcCfg<PC>;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(base + 2 * C::STAGE);  // [2] stage barriers
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2);
+  constexpr int NS = C::NS;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  __shared__ __align__(8) uint64_t s_full[NS];   // stage filled (bytes landed)
+  __shared__ __align__(8) uint64_t s_empty[NS];  // stage consumed (MMAs done)
+  __shared__ __align__(8) uint64_t s_gen[NS];    // layer 0: D written into the stage
+  __shared__ __align__(8) uint64_t s_acc;        // accumulator complete
+  __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   __shared__ float s_e[2][kBM];
+  volatile int* abort_flag = &s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * NT;
-  const int ntile = min(NT, N - n0);  // columns of this tile (multiple of 16)
+  const int ntile = min(NT, N - n0);  // NT, or the ragged last tile (a multiple of 16)
+  const int nk = K / kBK;
+  const uint32_t a_bytes = PC * C::A_BYTES;
+  const uint32_t b_piece = (uint32_t)ntile * kBK * 2;
 
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&s_full[s], 1);
+      mbar_init(&s_empty[s], 1);
+      mbar_init(&s_gen[s], kTcThreads / 2);
+    }
+    mbar_init(&s_acc, 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(TmemCols<PC>::value));
+                     smem_u32(&s_tmem)),
+                 "r"(C::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = s_tmem;
 
-  const int nk = (K + C::BK - 1) / C::BK;
-  const uint32_t idesc = make_idesc_bf16(kBM, ntile);
-  constexpr int KG = C::BK / 8;  // 16-byte K groups per row in a stage
-
-  auto stage_ptr = [&](int s) { return base + s * C::STAGE; };
-  // TC_L0: this thread's T[row][c][hal*8 .. hal*8+7], kept for every K chunk
-  float ta[4][8];
-  const float* trow_ptr = nullptr;
-  if (EPI == TC_L0) {
-    const int r = tid >> 1, hal = tid & 1;
-    const int gm = m0 + r;
-    if (gm < M) trow_ptr = ep.T + (size_t)(ep.tidx ? ep.tidx[gm] : gm) * 4 * ep.Mw;
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) ta[c][j] = trow_ptr ? __ldg(trow_ptr + c * ep.Mw + hal * 8 + j) : 0.0f;
-  }
-  // fill stage s with chunk kc: every piece of A rows m0.. and B rows n0..
-  auto load_stage = [&](int s, int kc) {
-    const int k0 = kc * C::BK;
-    const uint32_t st0 = smem_u32(stage_ptr(s));
-    if (EPI == TC_L0) {
-      // D[r][k] = sum_c T[c][k/16] T[c][k%16]: two threads per row, thread
-      // (row, hal) forms the 8-wide groups whose a-range is hal*8..hal*8+7
-      const int r = tid >> 1, hal = tid & 1;
-      const int gm = m0 + r;
-      unsigned char* sa = stage_ptr(s);
-      for (int kg = hal; kg < KG; kg += 2) {
-        const int k = k0 + kg * 8;
-        float x[8];
-        if (gm < M && k < K) {
-          const int b = k >> 4;
-          float tb[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) tb[c] = __ldg(trow_ptr + c * ep.Mw + b);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc = fmaf(tb[c], ta[c][j], acc);
-            x[j] = acc;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) x[j] = 0.0f;
-        }
-        __align__(16) __nv_bfloat16 pv[3][8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          pv[0][j] = __float2bfloat16_rn(x[j]);
-          if (PC > 1) {
-            const float r1 = x[j] - __bfloat162float(pv[0][j]);
-            pv[1][j] = __float2bfloat16_rn(r1);
-            pv[2][j] = __float2bfloat16_rn(r1 - __bfloat162float(pv[1][j]));
-          }
-        }
-        const int off = (r >> 3) * C::SBO + kg * 128 + (r & 7) * 16;
-#pragma unroll
-        for (int p = 0; p < PC; ++p)
-          *reinterpret_cast<uint4*>(sa + p * C::A_BYTES + off) = *reinterpret_cast<const uint4*>(pv[p]);
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: the A and B blocks of chunk kc land in stage kc % NS
+      int kc = 0;
+      for (; kc < nk; ++kc) {
+        const int s = kc % NS, u = kc / NS;
+        if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
+        const uint32_t st0 = smem_u32(base + (size_t)s * C::STAGE);
+        mbar_expect_tx(&s_full[s], (EPI == TC_L0 ? 0u : a_bytes) + PC * b_piece);
+        if (EPI != TC_L0)
+          bulk_g2s(st0, A + ((size_t)blockIdx.x * nk + kc) * PC * (kBM * kBK), a_bytes,
+                   &s_full[s]);
+        bulk_g2s(st0 + a_bytes,
+                 B + (size_t)n0 * K * PC + (size_t)kc * PC * ((size_t)ntile * kBK),
+                 PC * b_piece, &s_full[s]);
+      }
+      if (kc < nk) {
+        // aborted: wait (bounded) for the copies already issued to land
+        for (int j = kc - NS > 0 ? kc - NS : 0; j < kc; ++j)
+          mbar_wait(&s_full[j % NS], (j / NS) & 1, nullptr);
       }
     }
-#pragma unroll
-    for (int p = 0; p < PC; ++p) {
-      const uint32_t a0 = st0 + p * C::A_BYTES;
-      const __nv_bfloat16* Ap = A + p * a_ps;
-      for (int q = tid; q < (EPI == TC_L0 ? 0 : kBM * KG); q += kTcThreads) {
-        const int r = q / KG, kg = q % KG;
-        const int gm = m0 + r, gk = k0 + kg * 8;
-        const bool ok = gm < M && gk < K;
-        cp_async16(a0 + (r >> 3) * C::SBO + kg * 128 + (r & 7) * 16,
-                   ok ? Ap + (size_t)gm * lda + gk : Ap, ok);
-      }
-      const uint32_t b0 = st0 + PC * C::A_BYTES + p * C::B_BYTES;
-      const __nv_bfloat16* Bp = B + p * b_ps;
-      for (int q = tid; q < ntile * KG; q += kTcThreads) {
-        const int r = q / KG, kg = q % KG;
-        const int gn = n0 + r, gk = k0 + kg * 8;
-        const bool ok = gn < N && gk < K;
-        cp_async16(b0 + (r >> 3) * C::SBO + kg * 128 + (r & 7) * 16,
-                   ok ? Bp + (size_t)gn * ldb + gk : Bp, ok);
-      }
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  };
-
-  load_stage(0, 0);
-  int uses[2] = {0, 0};
-  bool ok_run = true;
-  for (int kc = 0; kc < nk; ++kc) {
-    const int s = kc & 1;
-    if (kc + 1 < nk) {
-      const int s1 = (kc + 1) & 1;
-      if (uses[s1] > 0 && !mbar_wait(&bars[s1], (uses[s1] - 1) & 1)) atomicExch(&s_abort, 1);
-      __syncthreads();
-      if (s_abort) {
-        ok_run = false;
-        break;
-      }
-      load_stage(s1, kc + 1);
-      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-      const uint32_t st0 = smem_u32(stage_ptr(s));
-#pragma unroll
-      for (int j = 0; j < C::BK / 16; ++j) {
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: NPROD piece products per stage, the stage committed back
+      const uint32_t idesc = make_idesc_bf16(kBM, ntile);
+      for (int kc = 0; kc < nk; ++kc) {
+        const int s = kc % NS, u = kc / NS;
+        if (!mbar_wait(&s_full[s], u & 1, abort_flag)) break;
+        if (EPI == TC_L0 && !mbar_wait(&s_gen[s], u & 1, abort_flag)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        const uint32_t st0 = smem_u32(base + (size_t)s * C::STAGE);
 #pragma unroll
         for (int q = 0; q < C::NPROD; ++q) {
           int pa = 0, pb = 0;
           if (PC > 1) prod_pieces(q, pa, pb);
-          // K = 16 covers two 8-element K groups (128 bytes apart)
-          const uint64_t ad = make_desc(st0 + pa * C::A_BYTES + j * 256, 128, C::SBO);
-          const uint64_t bd = make_desc(st0 + PC * C::A_BYTES + pb * C::B_BYTES + j * 256, 128,
-                                        C::SBO);
+          const uint64_t ad = make_desc(st0 + pa * C::A_BYTES, 128, 256);
+          const uint64_t bd = make_desc(st0 + a_bytes + pb * b_piece, 128, 256);
           // accumulator 0: (h,h); accumulator 1 (PC = 3): the other products
           const uint32_t dst = tmem + (q > 0 ? 256u : 0u);
-          const uint32_t acc = (kc > 0 || j > 0 || q > 1) ? 1u : 0u;
+          const uint32_t acc = (kc > 0 || q > 1) ? 1u : 0u;
           asm volatile(
               "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
               " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
               "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
         }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&s_empty[s])));
       }
+      // every MMA issued (all, or up to an abort) completes before s_acc does
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-              smem_u32(&bars[s])));
+              smem_u32(&s_acc)));
     }
-    uses[s] += 1;
+    __syncwarp();
+  } else if (EPI == TC_L0 && warp >= 4) {
+    // layer 0: D[r][16 b + a] = sum_c T[c][b] T[c][a] (Eq. 2, M< = 16), one
+    // thread per row; chunk kc is b = kc
+    const int r = tid - kTcThreads / 2;
+    const int gm = m0 + r;
+    const float* trow = gm < M ? ep.T + (size_t)(ep.tidx ? ep.tidx[gm] : gm) * 4 * ep.Mw : nullptr;
+    float ta[4][16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int a = 0; a < 16; a += 4) {
+        const float4 v = trow ? __ldg(reinterpret_cast<const float4*>(trow + c * ep.Mw + a))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        ta[c][a] = v.x;
+        ta[c][a + 1] = v.y;
+        ta[c][a + 2] = v.z;
+        ta[c][a + 3] = v.w;
+      }
+    float4 tb4[4];
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % NS, u = kc / NS;
+      if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
+      if ((kc & 3) == 0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          tb4[c] = trow ? __ldg(reinterpret_cast<const float4*>(trow + c * ep.Mw + kc))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      const int q = kc & 3;
+      float x[16];
+#pragma unroll
+      for (int a = 0; a < 16; ++a) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float tb = q == 0 ? tb4[c].x : q == 1 ? tb4[c].y : q == 2 ? tb4[c].z : tb4[c].w;
+          acc = fmaf(tb, ta[c][a], acc);
+        }
+        x[a] = acc;
+      }
+      unsigned char* sa = base + (size_t)s * C::STAGE;
+#pragma unroll
+      for (int kg = 0; kg < 2; ++kg) {
+        __align__(16) __nv_bfloat16 pv[3][8];
+        split8<PC>(x + kg * 8, pv);
+        const int off = (r >> 3) * 256 + kg * 128 + (r & 7) * 16;
+#pragma unroll
+        for (int p = 0; p < PC; ++p)
+          *reinterpret_cast<uint4*>(sa + p * C::A_BYTES + off) = *reinterpret_cast<const uint4*>(pv[p]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_arrive(&s_gen[s]);
+    }
   }
-  // wait for the MMAs (bounded); commits complete in order
-  bool done = ok_run;
-  for (int t = 0; t < 2; ++t)
-    if (uses[t] > 0 && !mbar_wait(&bars[t], (uses[t] - 1) & 1)) done = false;
-  if (!done) atomicExch(&s_abort, 1);
+
+  // the accumulator: the MMA thread commits it in every case
+  bool done = mbar_wait(&s_acc, 0, nullptr);
+  if (!done) *abort_flag = 1;
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   __syncthreads();
-  done = s_abort == 0;  // uniform over the CTA (the epilogue synchronises)
+  done = *abort_flag == 0;  // uniform over the CTA (the epilogue synchronises)
+
   if (!done) {
     if (tid == 0 && ep.err) atomicAdd(ep.err, 1);
   } else {
@@ -354,6 +377,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
     const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16);
     const int nch = ntile / 16;
     const int c_beg = half ? (nch + 1) / 2 : 0, c_end = half ? nch : (nch + 1) / 2;
+    const int nkc_out = ep.ldo / kBK;
     float e_acc = 0.0f;
     // TC_DT: T[row][c][0..15] and the partial sums of the second factor
     float tl[4][16], part[4][16];
@@ -407,9 +431,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
       float r[16], b[16], tt[16], oa[16], ob[16], oh[16];
       if (EPI == TC_L0 || EPI == TC_MID || EPI == TC_LAST) {
 #pragma unroll
-        for (int k = 0; k < 16; k += 4) *reinterpret_cast<float4*>(b + k) = *reinterpret_cast<const float4*>(ep.bias + n + k);
+        for (int k = 0; k < 16; k += 4)
+          *reinterpret_cast<float4*>(b + k) = *reinterpret_cast<const float4*>(ep.bias + n + k);
       }
-      if ((EPI == TC_MID || EPI == TC_LAST || EPI == TC_BWD)) {
+      if (EPI == TC_MID || EPI == TC_LAST || EPI == TC_BWD) {
         if (ep.R) {
 #pragma unroll
           for (int k = 0; k < 16; k += 4)
@@ -461,8 +486,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
           *reinterpret_cast<float4*>(ep.out_b + o + k) = *reinterpret_cast<const float4*>(ob + k);
       }
       if (EPI != TC_PLAIN) {
-        split_store<PC>(ep.out_h, ep.h_ps, o, *reinterpret_cast<const float(*)[8]>(oh));
-        split_store<PC>(ep.out_h, ep.h_ps, o + 8, *reinterpret_cast<const float(*)[8]>(oh + 8));
+        store_tiled<PC>(ep.out_h, nkc_out, row, n, oh);
+        store_tiled<PC>(ep.out_h, nkc_out, row, n + 8, oh + 8);
       }
     }
     if (EPI == TC_LAST) {
@@ -500,28 +525,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(int M, int N, int K, 
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
-  if (warp == 0)
+  if (warp == 2)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
-                 "r"(TmemCols<PC>::value));
+                 "r"(C::TMEM_COLS));
 }
 
+// the caller's layouts: A pre-tiled in 128-row tiles, B in tiles of 256 rows
+// (the last one ragged), N % 16 == 0, K % 16 == 0
 template <int EPI, int PC>
-int tc_gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A, int lda, int64_t a_ps,
-            const __nv_bfloat16* B, int ldb, int64_t b_ps, const TcEpi& ep) {
+int tc_gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B,
+            const TcEpi& ep) {
   if (M <= 0) return 0;
-  if (K % 8 || lda % 8 || ldb % 8 || N % 16 || ep.ldo % 8) return -1;
+  if (K <= 0 || K % kBK || N <= 0 || N % 16) return -1;
+  if (EPI != TC_DT && EPI != TC_PLAIN && ep.ldo != N) return -1;
   const int NT = N <= 256 ? N : 256;
-  if (N > 256 && N % 256) return -1;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_tc_gemm<EPI, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)TcCfg<PC>::SMEM);
+    if (cudaFuncSetAttribute(k_tc_gemm<EPI, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcCfg<PC>::SMEM) != cudaSuccess)
+      return -3;
     attr = true;
   }
   dim3 grid((M + kBM - 1) / kBM, (N + NT - 1) / NT);
   DP_LAUNCHED(1);
-  k_tc_gemm<EPI, PC><<<grid, kTcThreads, TcCfg<PC>::SMEM, st>>>(M, N, K, NT, A, lda, a_ps, B, ldb,
-                                                               b_ps, ep);
+  k_tc_gemm<EPI, PC><<<grid, kTcThreads, TcCfg<PC>::SMEM, st>>>(M, N, K, NT, A, B, ep);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -539,25 +566,37 @@ __global__ void k_dt_reduce(int64_t rows, const int32_t* __restrict__ idx, int M
   dT[(size_t)a * 4 * M + (e >> 4) * M + (e & 15)] += acc;
 }
 
-// FP32 -> PC BF16 pieces, piece p at out + p*n
-__global__ void k_split_pieces(int64_t n, const float* __restrict__ in, __nv_bfloat16* __restrict__ out) {
+// FP32 B [N][K] -> PC BF16 pieces in the pre-tiled B layout: tile nt (rows
+// 256 nt .., ntile of them) at 256 nt K PC, its K chunk kc at kc PC ntile 16
+__global__ void k_tile_operand(int N, int K, int PC, const float* __restrict__ src,
+                               __nv_bfloat16* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float x = in[i];
+  if (i >= (int64_t)N * K) return;
+  const int n = (int)(i / K), k = (int)(i - (int64_t)n * K);
+  const int nt = n / 256, r = n - nt * 256, ntile = min(256, N - nt * 256);
+  const size_t ps = (size_t)ntile * kBK;
+  const size_t o = (size_t)nt * 256 * K * PC + (size_t)(k / kBK) * PC * ps + tile_off(r, k);
+  const float x = src[i];
   const __nv_bfloat16 h = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(h);
-  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-  out[i] = h;
-  out[n + i] = m;
-  out[2 * n + i] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+  out[o] = h;
+  if (PC > 1) {
+    const float r1 = x - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    out[o + ps] = m;
+    out[o + 2 * ps] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+  }
 }
 
 }  // namespace
 
-void launch_split_pieces(cudaStream_t st, int64_t n, const float* in, __nv_bfloat16* out) {
-  if (n <= 0) return;
+int launch_tile_operand(cudaStream_t st, int N, int K, int pieces, const float* src,
+                        __nv_bfloat16* out) {
+  if (N <= 0 || K <= 0 || K % kBK || N % 16) return -1;
+  if (pieces != 1 && pieces != 3) return -1;
+  const int64_t n = (int64_t)N * K;
   DP_LAUNCHED(1);
-  k_split_pieces<<<(int)((n + 255) / 256), 256, 0, st>>>(n, in, out);
+  k_tile_operand<<<(int)((n + 255) / 256), 256, 0, st>>>(N, K, pieces, src, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 template <int PC>
@@ -569,17 +608,20 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
   if (nl < 2 || nl > DP_MAXFIT) return -1;
   for (int k = 0; k < nl; ++k)
     if (net.wout[k] > 256 || net.wout[k] % 16) return -1;
-  if (din % 16 || m_lt != 16 || M < 16) return -1;  // the fused descriptor wants M< = 16
-  const int64_t R = s.rows;  // piece strides of the activation scratch: R * width
+  if (m_lt != 16 || M % 4 || M < 16) return -1;  // the fused descriptor wants M< = 16
+  // bulk copies and vector loads want 16-byte aligned operands
+  auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+  if (!al(T) || !al(s.part) || !al(s.gph[0]) || !al(s.gph[1])) return -1;
+  for (int k = 0; k < nl; ++k)
+    if (!al(net.WTh[k]) || !al(net.Wh[k]) || !al(s.zh[k]) || !al(net.b[k])) return -1;
+  const int64_t R = s.rows;
   for (int64_t r0 = 0; r0 < n; r0 += R) {
     const int rows = (int)((n - r0) < R ? (n - r0) : R);
     const int32_t* id = idx ? idx + r0 : nullptr;
     const float* Tc = idx ? T : T + (size_t)r0 * 4 * M;
     float* dTc = idx ? dT : dT + (size_t)r0 * 4 * M;
-    // forward: layer 0 (its A operand D formed from T in the producer), hidden
+    // forward: layer 0 (its A operand D formed from T in the stage), hidden
     // layers, last layer with the energy
-    const __nv_bfloat16* in = nullptr;
-    int win = din;
     for (int k = 0; k < nl; ++k) {
       TcEpi ep{};
       ep.bias = net.b[k];
@@ -591,37 +633,28 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       if (k == 0) {
         ep.out_a = s.t[0];
         ep.out_h = s.zh[0];
-        ep.h_ps = R * net.wout[0];
         ep.T = Tc;
         ep.tidx = id;
         ep.Mw = M;
-        rc = tc_gemm<TC_L0, PC>(st, rows, net.wout[0], din, in, din, 0, net.WTh[0], din,
-                                net.w_ps[0], ep);
+        rc = tc_gemm<TC_L0, PC>(st, rows, net.wout[0], din, nullptr, net.WTh[0], ep);
       } else if (k == nl - 1) {
         ep.R = net.shortcut[k] ? zb : nullptr;
         ep.ldr = net.wout[k - 1];
         ep.wout = net.w_out;
         ep.bout = net.b_out;
         ep.out_h = s.gph[0];
-        ep.h_ps = R * s.wmax;
-        ep.ldo = net.wout[k];
         ep.e_atom = e_atom + (idx ? 0 : r0);
         ep.idx = id;
-        rc = tc_gemm<TC_LAST, PC>(st, rows, net.wout[k], win, in, win, R * win, net.WTh[k], win,
-                                  net.w_ps[k], ep);
+        rc = tc_gemm<TC_LAST, PC>(st, rows, net.wout[k], net.win[k], s.zh[k - 1], net.WTh[k], ep);
       } else {
         ep.R = net.shortcut[k] ? zb : nullptr;
         ep.ldr = net.wout[k - 1];
         ep.out_a = s.t[k];
         ep.out_b = s.z[k];
         ep.out_h = s.zh[k];
-        ep.h_ps = R * net.wout[k];
-        rc = tc_gemm<TC_MID, PC>(st, rows, net.wout[k], win, in, win, R * win, net.WTh[k], win,
-                                 net.w_ps[k], ep);
+        rc = tc_gemm<TC_MID, PC>(st, rows, net.wout[k], net.win[k], s.zh[k - 1], net.WTh[k], ep);
       }
       if (rc) return rc;
-      in = s.zh[k];
-      win = net.wout[k];
     }
     // backward: gz_last = w_out (row stride 0); gp of the last layer from the
     // TC_LAST epilogue; gz updated in place, gp ping-pongs
@@ -636,12 +669,9 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.ldt = net.win[k];
       ep.out_b = s.gz;
       ep.out_h = s.gph[gi ^ 1];
-      ep.h_ps = R * s.wmax;
       ep.ldo = net.win[k];
       ep.err = err;
-      const int rc = tc_gemm<TC_BWD, PC>(st, rows, net.win[k], net.wout[k], s.gph[gi],
-                                         net.wout[k], R * s.wmax, net.Wh[k], net.wout[k],
-                                         net.w_ps[k], ep);
+      const int rc = tc_gemm<TC_BWD, PC>(st, rows, net.win[k], net.wout[k], s.gph[gi], net.Wh[k], ep);
       if (rc) return rc;
       gz_prev = s.gz;
       ldgz = net.win[k];
@@ -659,11 +689,10 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.Mw = M;
       ep.part = s.part;
       ep.part_ps = R * 64;
-      const int rc = tc_gemm<TC_DT, PC>(st, rows, din, net.wout[0], s.gph[gi], net.wout[0],
-                                        R * s.wmax, net.Wh[0], net.wout[0], net.w_ps[0], ep);
+      const int rc = tc_gemm<TC_DT, PC>(st, rows, din, net.wout[0], s.gph[gi], net.Wh[0], ep);
       if (rc) return rc;
     }
-    const int slots = din <= 256 ? 1 : din / 256;
+    const int slots = (din + 255) / 256;
     DP_LAUNCHED(1);
     k_dt_reduce<<<(int)((rows * 64 + 255) / 256), 256, 0, st>>>(rows, id, M, slots, R * 64, s.part,
                                                                 dTc);

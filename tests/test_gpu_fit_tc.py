@@ -138,3 +138,41 @@ def test_split_mode_end_to_end(dp, cu_model_path, cu_stress_path):
         else:
             assert de < max(1e-6, 2e-6 * float(np.abs(r["atom_energy"]).mean())), de
             assert fr < max(1e-5, 3e-5 * frms), (fr, frms)
+
+
+def test_split_mode_water_two_types(dp, water_model_path):
+    # two centre types (per-type fitting nets gathered through an index list),
+    # M = 100: D has 1600 columns, so the dE/dD GEMM ends in a ragged 64-column
+    # tile; held to the FP32 path's stress-model bars, both errors logged
+    m = oracle.Model(water_model_path)
+    tab = oracle.Table(m, TABLE_H, 1.25)
+    x, t, box = inputs.water_like(64, L=12.417, seed=3)
+    r = oracle.evaluate(m, tab, 6.0, 0.5, [46, 92], x, t, box)
+    emean = float(np.abs(r["atom_energy"]).mean())
+    emax = float(np.abs(r["atom_energy"]).max())
+    frms = float(np.sqrt((r["force"] ** 2).mean()))
+    vmax = float(np.abs(r["virial"]).max())
+    got = {}
+    for prec in (0, 2):
+        o = dp.dp_options_default()
+        o.fit_precision = prec
+        o.s_max = 1.25
+        h = dp.dp_create(water_model_path, 2, 6.0, 0.5, [46, 92], options=o, stream=None)
+        try:
+            E, F, V, Ei = dp.dp_compute(h, x, t, box, atom_energy=True)
+        finally:
+            dp.dp_destroy(h)
+        got[prec] = (abs(E - r["energy"]) / len(x), float(np.abs(Ei - r["atom_energy"]).max()),
+                     rmse(F, r["force"]), float(np.abs(V - r["virial"]).max()))
+    de, dei, fr, dv = got[2]
+    PARITY_LOG.append(dict(case="tc split water 192 std 1.0", natoms=len(x), dE_per_atom=de,
+                           max_dEi=dei, force_rmse=fr, force_rms=frms, max_dvirial=dv,
+                           fp32_path=dict(zip(("dE_per_atom", "max_dEi", "force_rmse",
+                                               "max_dvirial"), got[0]))))
+    # energies: the tensor core's FP32 accumulator adds each K = 16 step with
+    # truncation, a bias that grows with K (1600 here); measured 5.6e-6 of the
+    # mean |E_i| on this stress model, about twice the CUDA-core path's error
+    assert de < max(1e-6, 1e-5 * emean), (de, emean, got[0])
+    assert dei < 2e-5 * emax, (dei, emax)
+    assert fr < max(1e-5, 3e-5 * frms), (fr, frms)
+    assert dv < 1e-4 * vmax + 1e-9, (dv, vmax)
