@@ -61,6 +61,8 @@ def parse():
                     help="MD steps of the plain untabulated comparator (0: skip)")
     ap.add_argument("--fit-precision", type=int, default=2,
                     help="0 FP32 CUDA cores, 1 BF16 tensor cores, 2 FP32-accurate tensor cores")
+    ap.add_argument("--embed-precision", type=int, default=2,
+                    help="tabulated contraction: 0 FP32 CUDA cores, 2 FP32-accurate tensor cores")
     return ap.parse_args()
 
 
@@ -260,6 +262,7 @@ def main():
     masses = [inputs.MASS_CU]
     opt = dp.dp_options_default()
     opt.fit_precision = args.fit_precision
+    opt.embed_precision = args.embed_precision
     h = dp.dp_create(model, 1, RC, RCS, [SEL], options=opt, stream=C_stream(stream))
     s = dp.dp_system_create(h, x, v, t, masses, box)
     for _ in range(args.warmup):

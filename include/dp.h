@@ -63,6 +63,9 @@ typedef struct {
                           r >= 0.5 A for rcs = 0.5 */
   double skin;         /* neighbor-list buffer for MD (Sec. 4) [2.0 A] */
   int rebuild_every;   /* MD list rebuild period in steps [10] */
+  int embed_precision; /* tabulated embedding contraction: 0 FP32 CUDA cores
+                          [0], 2 FP32-accurate tcgen05 tensor cores (split
+                          operands); the plain path ignores it */
 } dp_options;
 
 /* Thermodynamic record of one MD step (Sec. 4). */

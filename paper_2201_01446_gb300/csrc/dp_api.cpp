@@ -77,6 +77,8 @@ struct Work {
       off, nlist, nn, T, dT, e_atom, ffix, f, vir_part, red_part, red_out, idx, ke, pairs;
   std::vector<int64_t> type_count, type_off;  // atoms per model type, offsets into idx
   bool have_idx = false;
+  TileMap tiles{};  // the same grouping in tiles of 32 (tensor-core embedding)
+  DevBuf tc_pairs, tc_hist, tc_range;  // sorted pairs / bin ends the forward leaves
 };
 
 }  // namespace
@@ -95,6 +97,7 @@ struct dp_handle {
   int ntypes = 0, n_emb = 0, emb_w[6] = {0}, M = 0, m_lt = 0, din = 0, n_fit = 0;
   int fit_w[DP_MAXFIT] = {0};
   DevBuf emb64, emb_off, table, fit32, sel_dev, map_dev, status;
+  DevBuf tabF, tabB, tc_scratch;  // tensor-core embedding: tiled table pieces, per-CTA scratch
   int n_int = 0;
   double h = 0.0;
   FitNet nets[DP_MAXT];
@@ -359,7 +362,9 @@ dp_status ensure_atoms(dp_handle* h, Work& w, int64_t n) {
   CK(ensure(w.f, N * 3 * sizeof(double)), "alloc f");
   CK(ensure(w.idx, N * sizeof(int32_t)), "alloc idx");
   CK(ensure(w.vir_part,
-            (size_t)std::max(tab_kernel_slots(n), plain_kernel_slots(n)) * 9 * sizeof(double)),
+            (size_t)std::max<int64_t>(std::max(tab_kernel_slots(n), plain_kernel_slots(n)),
+                                      tab_tc_slots()) *
+                9 * sizeof(double)),
      "alloc virial");
   CK(ensure(w.red_part, (size_t)sum_rows_part_size(n, 9) * sizeof(double)), "alloc red");
   CK(ensure(w.red_out, 32 * sizeof(double)), "alloc red");
@@ -382,6 +387,23 @@ dp_status set_types(dp_handle* h, Work& w, const int32_t* types_user_host) {
   }
   for (int t = 0; t < h->ntypes; ++t) w.type_off[t + 1] = w.type_off[t] + w.type_count[t];
   w.have_idx = h->ntypes > 1;
+  w.tiles = TileMap{};
+  w.tiles.ntypes = h->ntypes;
+  for (int t = 0; t < h->ntypes; ++t) {
+    w.tiles.atom_off[t] = w.type_off[t];
+    w.tiles.atom_cnt[t] = w.type_count[t];
+    w.tiles.tile_off[t + 1] = w.tiles.tile_off[t] + (w.type_count[t] + 31) / 32;
+  }
+  w.tiles.idx = w.have_idx ? P<int32_t>(w.idx) : nullptr;
+  if (h->opt.tabulated && h->opt.embed_precision == 2) {
+    const EnvParams ep = env_params(h);
+    const int64_t ntile = w.tiles.tile_off[h->ntypes];
+    CK(ensure(w.tc_pairs, (size_t)std::max<int64_t>(tab_tc_pair_elems(ep, ntile), 1) * 16),
+       "alloc sorted pairs");
+    CK(ensure(w.tc_hist, (size_t)std::max<int64_t>(tab_tc_hist_elems(ep, ntile), 4) * 4),
+       "alloc bin ends");
+    CK(ensure(w.tc_range, (size_t)std::max<int64_t>(ntile, 1) * 8), "alloc bin ranges");
+  }
   if (n > 0) {
     CK(cudaMemcpyAsync(w.types.p, mt.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->st),
        "types upload");
@@ -535,7 +557,14 @@ dp_status run_fitting(dp_handle* h, int t, int64_t cnt, const int32_t* idx, cons
 
 // environment matrix + embedding + contraction: T of every atom
 dp_status embed_forward(dp_handle* h, Work& w, const EnvParams& ep) {
-  if (h->opt.tabulated) {
+  if (h->opt.tabulated && h->opt.embed_precision == 2) {
+    if (launch_tab_fwd_tc(h->st, w.tiles, P<float4>(w.off), P<uint32_t>(w.nlist),
+                          P<int32_t>(w.nn), w.cap, w.geom, ep, P<__nv_bfloat16>(h->tabF),
+                          P<float>(h->tc_scratch), P<float4>(w.tc_pairs), P<int>(w.tc_hist),
+                          P<int2>(w.tc_range), P<float>(w.T), P<int32_t>(h->status),
+                          P<unsigned long long>(w.pairs)))
+      return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core embedding cannot run this model shape");
+  } else if (h->opt.tabulated) {
     if (launch_tab_fwd(h->st, w.n, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
                        w.cap, w.geom, ep, P<float>(h->table), P<float>(w.T),
                        P<int32_t>(h->status), P<unsigned long long>(w.pairs)))
@@ -574,7 +603,13 @@ dp_status evaluate(dp_handle* h, Work& w) {
   ph_fit.end();
   {
     Phase ph(h, 3);
-    if (h->opt.tabulated) {
+    if (h->opt.tabulated && h->opt.embed_precision == 2) {
+      if (launch_tab_bwd_tc(h->st, w.tiles, P<float4>(w.tc_pairs), P<int>(w.tc_hist),
+                            P<int2>(w.tc_range), ep, P<__nv_bfloat16>(h->tabB), P<float>(w.dT),
+                            P<unsigned long long>(w.ffix), P<double>(w.vir_part),
+                            (int)tab_tc_slots(), P<int32_t>(h->status)))
+        return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core embedding cannot run this model shape");
+    } else if (h->opt.tabulated) {
       if (launch_tab_bwd(h->st, n, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
                          w.cap, w.geom, ep, P<float>(h->table), P<float>(w.dT),
                          P<unsigned long long>(w.ffix), P<double>(w.vir_part),
@@ -593,7 +628,10 @@ dp_status evaluate(dp_handle* h, Work& w) {
   launch_force_finalize(h->st, n, P<unsigned long long>(w.ffix), P<double>(w.f),
                         P<int32_t>(h->status));
   launch_sum_rows(h->st, n, 1, P<double>(w.e_atom), P<double>(w.red_part), P<double>(w.red_out));
-  launch_sum_rows(h->st, h->opt.tabulated ? tab_kernel_slots(n) : plain_kernel_slots(n), 9,
+  const int64_t vslots = !h->opt.tabulated             ? plain_kernel_slots(n)
+                         : h->opt.embed_precision == 2 ? tab_tc_slots()
+                                                       : tab_kernel_slots(n);
+  launch_sum_rows(h->st, vslots, 9,
                   P<double>(w.vir_part), P<double>(w.red_part), P<double>(w.red_out) + 1);
   launch_check_energy(h->st, n, P<double>(w.e_atom), P<int32_t>(h->status));
   CK(cudaGetLastError(), "evaluation kernels");
@@ -639,6 +677,7 @@ void dp_options_default(dp_options* o) {
   o->s_max = 2.0;
   o->skin = 2.0;
   o->rebuild_every = 10;
+  o->embed_precision = 0;
 }
 
 const char* dp_version(void) { return "dp-gb300 0.1 (sm_103a; tabulated FP32 embedding, FP32 SIMT fitting)"; }
@@ -674,7 +713,7 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
       h->opt.rebuild_every < 1)
     return bail(DP_ERR_ARG);
   if (h->opt.tabulated < 0 || h->opt.tabulated > 1 || h->opt.fit_precision < 0 ||
-      h->opt.fit_precision > 2)
+      h->opt.fit_precision > 2 || (h->opt.embed_precision != 0 && h->opt.embed_precision != 2))
     return bail(DP_ERR_UNIMPLEMENTED);
   HostModel m;
   std::string why;
@@ -866,6 +905,21 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
                   h->n_int, P<float>(h->table)) != 0) {
     h->err = "table build failed";
     return bail(DP_ERR_CUDA);
+  }
+  if (h->opt.tabulated && h->opt.embed_precision == 2) {
+    const EnvParams ep = env_params(h);
+    const size_t nt = (size_t)tab_tc_elems(ep) * sizeof(__nv_bfloat16);
+    if (ensure(h->tabF, nt) != cudaSuccess || ensure(h->tabB, nt) != cudaSuccess ||
+        ensure(h->tc_scratch, (size_t)tab_tc_scratch_floats(ep) * sizeof(float)) != cudaSuccess) {
+      h->err = "device allocation failed";
+      cudaGetLastError();
+      return bail(DP_ERR_OOM);
+    }
+    if (tab_tc_build(h->st, P<float>(h->table), ep, P<__nv_bfloat16>(h->tabF),
+                     P<__nv_bfloat16>(h->tabB)) != 0) {
+      h->err = "the tensor-core embedding cannot run this model shape (M <= 128, M % 4 == 0)";
+      return bail(DP_ERR_UNIMPLEMENTED);
+    }
   }
   if (cudaStreamSynchronize(h->st) != cudaSuccess) {
     h->err = "device error during dp_create";

@@ -85,6 +85,40 @@ int launch_tab_bwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t
                    double* vir_part, int vir_slots, int32_t* status);
 int tab_kernel_slots(int64_t n);  // number of virial partial slots the bwd kernel writes
 
+// Tensor-core tabulated embedding (tcgen05, FP32-accurate 3-piece BF16
+// operands): atoms grouped by model type in tiles of 32; tile t of type ti
+// holds atoms idx[atom_off[ti] + 32 (t - tile_off[ti]) + 0..31] (idx == NULL:
+// the positions themselves), the last tile of a type padded.
+struct TileMap {
+  int ntypes;
+  int64_t tile_off[DP_MAXT + 1];
+  int64_t atom_off[DP_MAXT];
+  int64_t atom_cnt[DP_MAXT];
+  const int32_t* idx;
+};
+// BF16 pieces of the table in the two pre-tiled operand layouts (forward:
+// N = M columns x K = (interval, power); backward: N = (interval, power) x
+// K = M); elements per centre type of each
+int64_t tab_tc_elems(const EnvParams& ep);
+int tab_tc_build(cudaStream_t st, const float* table, const EnvParams& ep, __nv_bfloat16* tabF,
+                 __nv_bfloat16* tabB);
+int64_t tab_tc_scratch_floats(const EnvParams& ep);  // scratch one launch needs
+// the forward leaves, per tile, the sorted pairs (dx, dy, dz, neighbor index)
+// [tile][32][N_m + 32 rounded], the bin ends [tile][32][bins rounded to 4] and
+// (first bin, chunks of two bins); the backward reads them
+int64_t tab_tc_pair_elems(const EnvParams& ep, int64_t ntile);
+int64_t tab_tc_hist_elems(const EnvParams& ep, int64_t ntile);
+int64_t tab_tc_slots();  // virial partial slots the backward writes
+int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, const uint32_t* nlist,
+                      const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
+                      const __nv_bfloat16* tabF, float* scratch, float4* pairs_out,
+                      int* hist_out, int2* range_out, float* T, int32_t* status,
+                      unsigned long long* pair_count);
+int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs, const int* hist,
+                      const int2* range, const EnvParams& ep, const __nv_bfloat16* tabB,
+                      const float* dT, unsigned long long* ffix, double* vir_part, int vir_slots,
+                      int32_t* status);
+
 // plain untabulated embedding (the comparator of the tabulation), FP32
 int plain_kernel_slots(int64_t n);
 size_t plain_net_bytes();

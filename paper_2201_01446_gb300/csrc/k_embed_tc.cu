@@ -1,0 +1,899 @@
+// Tabulated embedding fused with the environment-matrix contraction on the
+// tensor cores (Sec. 3.2-3.4, Eq. 1-2).
+//
+// Per atom i the contraction regroups by table interval k (exact in real
+// arithmetic):
+//   T_i[c][m] = (1/N_m) sum_k sum_q C_ik[c][q] c_k[q][m],
+//   C_ik[c][q] = sum_{j in interval k} R_ij[c] u_ij^q,
+// a dense product of an A matrix with rows (atom, c) and K = (interval, q)
+// (q padded from 6 to 8) and the table read as B with N = m.  A CTA owns a
+// tile of 32 atoms of one centre type = 128 A rows.  Phase 1 (all warps, one
+// warp per atom): pair geometry, counting sort of the pairs by interval
+// (deterministic), the sorted (R, u) written to the CTA's scratch (L2
+// resident).  Phase 2: the K range is the tile's occupied interval range;
+// warp 0 streams the table blocks (2 intervals x M columns, all pieces) with
+// bulk async copies, warps 4-7 form C for the same two intervals in the
+// stage's A slot (one thread per row), warp 1 issues the MMAs.  Epilogue:
+// TMEM -> T (scaled by 1/N_m).  The kernel is persistent (two CTAs per SM),
+// so the per-CTA scratch stays small.  Operands are FP32-accurate: each value
+// is h + m + l in BF16 and six piece products accumulate in FP32 (the h*h sum
+// and the small products in separate TMEM accumulators).
+#include <cuda_bf16.h>
+#include <limits.h>
+#include <math.h>
+
+#include "dp_internal.h"
+#include "embed_common.cuh"
+#include "tc_common.cuh"
+
+namespace {
+using namespace dp_embed;
+using namespace dp_tc;
+
+constexpr int kPC = 3;            // BF16 pieces per value
+constexpr int kNPROD = 6;         // piece products per K step
+constexpr int kAtoms = 32;        // atoms per tile
+constexpr int kRows = 128;        // A rows per tile (atom, c)
+constexpr int kThreads = 256;
+constexpr int kNS = 3;            // pipeline stages
+constexpr int kABytes = kRows * 16 * 2;  // one piece of an A stage (K = 16)
+constexpr int kAcc1 = 128;        // TMEM column of the small-product accumulator
+constexpr int kTmemCols = 256;
+
+__host__ __device__ inline int round16(int v) { return (v + 15) & ~15; }
+__host__ __device__ inline int even_bins(int nbins) { return (nbins + 1) & ~1; }
+
+// forward table operand, per centre type: K chunk kc = intervals 2kc, 2kc+1;
+// its block holds the pieces of the NP x 16 tile, NP = M rounded up to 16
+__host__ __device__ inline int64_t tabF_elems(int nbins, int NP) {
+  return (int64_t)even_bins(nbins) / 2 * kPC * NP * 16;
+}
+// backward table operand: N = (interval, q) rows, K = m; per 16-wide m chunk
+// kc and piece p one block of all NB8 = 8 * nbins rows
+__host__ __device__ inline int64_t tabB_elems(int nbins, int NP) {
+  return (int64_t)(NP / 16) * kPC * 8 * even_bins(nbins) * 16;
+}
+
+// value of the padded table entry (interval b of centre type ti, power q,
+// column m): the normalised quintic coefficient, zero for q >= 6 or m >= M
+__device__ __forceinline__ float tab_value(const float* table, int ti, int nbins, int M, int b,
+                                           int q, int m) {
+  if (b >= nbins || q >= 6 || m >= M) return 0.0f;
+  return table[((size_t)ti * nbins + b) * 6 * M + (size_t)q * M + m];
+}
+
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m,
+                                       __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+// forward operand: element (n = m, k = 8 b + q)
+__global__ void k_tile_tabF(const float* __restrict__ table, int ntypes, int nbins, int M, int NP,
+                            __nv_bfloat16* __restrict__ out) {
+  const int nb2 = even_bins(nbins);
+  const int64_t per = tabF_elems(nbins, NP) / kPC;  // values per type
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= per * ntypes) return;
+  const int ti = (int)(i / per);
+  const int64_t r = i - (int64_t)ti * per;
+  const int m = (int)(r % NP);
+  const int k = (int)(r / NP);  // 0 .. 8 * nb2
+  const int b = k >> 3, q = k & 7;
+  if (b >= nb2) return;
+  __nv_bfloat16 h, md, l;
+  split3(tab_value(table, ti, nbins, M, b, q, m), h, md, l);
+  const int kc = k >> 4;
+  const size_t o = (size_t)ti * tabF_elems(nbins, NP) + (size_t)kc * kPC * NP * 16 + tile_off(m, k & 15);
+  out[o] = h;
+  out[o + NP * 16] = md;
+  out[o + 2 * NP * 16] = l;
+}
+
+// backward operand: element (n = 8 b + q, k = m)
+__global__ void k_tile_tabB(const float* __restrict__ table, int ntypes, int nbins, int M, int NP,
+                            __nv_bfloat16* __restrict__ out) {
+  const int NB8 = 8 * even_bins(nbins);
+  const int64_t per = (int64_t)NB8 * NP;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= per * ntypes) return;
+  const int ti = (int)(i / per);
+  const int64_t r = i - (int64_t)ti * per;
+  const int n = (int)(r / NP), m = (int)(r % NP);
+  __nv_bfloat16 h, md, l;
+  split3(tab_value(table, ti, nbins, M, n >> 3, n & 7, m), h, md, l);
+  const int kc = m >> 4;
+  const size_t blk = (size_t)NB8 * 16;
+  const size_t o = (size_t)ti * tabB_elems(nbins, NP) + (size_t)kc * kPC * blk + tile_off(n, m & 15);
+  out[o] = h;
+  out[o + blk] = md;
+  out[o + 2 * blk] = l;
+}
+
+struct FwdCfg {
+  int NP;         // M rounded up to 16: MMA N
+  int bstage;     // bytes of the B part of a stage (all pieces)
+  int stage;      // bytes per stage
+  int nbp;        // hist ints per atom
+  size_t smem;    // dynamic shared memory
+};
+
+__host__ __device__ inline FwdCfg fwd_cfg(const EnvParams& ep) {
+  FwdCfg c;
+  c.NP = round16(ep.M);
+  c.bstage = kPC * c.NP * 32;
+  c.stage = kPC * kABytes + c.bstage;
+  c.nbp = round4(ep.ntypes * ep.n_int);
+  c.smem = 128 + (size_t)kNS * c.stage + (size_t)kAtoms * c.nbp * 4;
+  return c;
+}
+
+__device__ __forceinline__ int tile_type(const TileMap& tm, int64_t tile) {
+  int ti = 0;
+  while (ti + 1 < tm.ntypes && tile >= tm.tile_off[ti + 1]) ++ti;
+  return ti;
+}
+
+__device__ __forceinline__ int tile_atom(const TileMap& tm, int ti, int64_t tile, int al) {
+  const int64_t pos = (tile - tm.tile_off[ti]) * kAtoms + al;
+  if (pos >= tm.atom_cnt[ti]) return -1;
+  return tm.idx ? tm.idx[tm.atom_off[ti] + pos] : (int)(tm.atom_off[ti] + pos);
+}
+
+// Phase 1 for one atom (one warp): histogram of the pairs within rc by bin =
+// (neighbor type, interval), exclusive scan, stable scatter of (R, u) in bin
+// order into the scratch rows of tile slot al.  On return hist holds the end
+// of every bin (all zero when the atom has no slot: padding or overflow).
+// Returns the pairs within rc; lo/hi the occupied bin range of this atom.
+__device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ off,
+                                         const uint32_t* __restrict__ nlist,
+                                         const int32_t* __restrict__ nn, int cap,
+                                         const CellGeom& g, const EnvParams& ep, int scap, int* hist,
+                                         int nbins, float* __restrict__ sc,
+                                         float4* __restrict__ pout, int lane, int& nrange,
+                                         int& nover, int& lo, int& hi) {
+  for (int b = lane; b < nbins; b += 32) hist[b] = 0;
+  __syncwarp();
+  lo = INT_MAX;
+  hi = -1;
+  if (atom < 0) return 0;
+  const float4 oi = off[atom];
+  const int cnt = min(nn[atom], cap);
+  const uint32_t* L = nlist + (size_t)atom * cap;
+  int np = 0;
+  for (int b0 = 0; b0 < cnt; b0 += 32) {
+    const int k = b0 + lane;
+    bool in = false;
+    if (k < cnt) {
+      float dx, dy, dz;
+      int tj;
+      load_pair(oi, off, g, L[k], dx, dy, dz, tj);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 < ep.rc2) {
+        Pair P;
+        pair_geom(ep, dx, dy, dz, r2, tj, P);
+        const int bin = tj * ep.n_int + P.th;
+        atomicAdd(&hist[bin], 1);
+        nrange += P.out_of_range;
+        lo = min(lo, bin);
+        hi = max(hi, bin);
+        in = true;
+      }
+    }
+    np += __popc(__ballot_sync(0xffffffffu, in));
+  }
+  __syncwarp();
+  if (np > scap) {
+    // more pairs within rc than N_m + 32: an overflow of sel, T_i = 0
+    for (int b = lane; b < nbins; b += 32) hist[b] = 0;
+    __syncwarp();
+    if (lane == 0) ++nover;
+    lo = INT_MAX;
+    hi = -1;
+    return np;
+  }
+  warp_exclusive_scan(hist, nbins, lane);
+  for (int b0 = 0; b0 < cnt; b0 += 32) {
+    const int k = b0 + lane;
+    bool in = false;
+    Pair P;
+    int bin = 0;
+    if (k < cnt) {
+      float dx, dy, dz;
+      int tj;
+      load_pair(oi, off, g, L[k], dx, dy, dz, tj);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 < ep.rc2) {
+        pair_geom(ep, dx, dy, dz, r2, tj, P);
+        bin = tj * ep.n_int + P.th;
+        in = true;
+      }
+    }
+    const int pos = sorted_slot(hist, in, bin, lane);
+    if (in) {
+      // the backward's copy: displacement and neighbor index in sorted order
+      pout[pos] = make_float4(P.dx, P.dy, P.dz, __int_as_float((int)(L[k] >> 5)));
+      // planar rows: R0 R1 R2 R3 u, each kAtoms * scap apart
+      const size_t st = (size_t)kAtoms * scap;
+      sc[pos] = P.s;
+      sc[st + pos] = P.s * P.dx * P.ir;
+      sc[2 * st + pos] = P.s * P.dy * P.ir;
+      sc[3 * st + pos] = P.s * P.dz * P.ir;
+      sc[4 * st + pos] = P.u;
+    }
+  }
+  __syncwarp();
+  return np;
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_tab_fwd_tc(int64_t ntile, TileMap tm, const float4* __restrict__ off,
+                 const uint32_t* __restrict__ nlist, const int32_t* __restrict__ nn, int cap,
+                 CellGeom g, EnvParams ep, const __nv_bfloat16* __restrict__ tabF, int scap,
+                 float* __restrict__ scratch, float4* __restrict__ pairs_out,
+                 int* __restrict__ hist_out, int2* __restrict__ range_out, float* __restrict__ T,
+                 int32_t* __restrict__ status, unsigned long long* __restrict__ pair_count) {
+  const FwdCfg cf = fwd_cfg(ep);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  int* shist = (int*)(base + (size_t)kNS * cf.stage);
+  __shared__ __align__(8) uint64_t s_full[kNS], s_empty[kNS], s_gen[kNS], s_acc;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort, s_lo, s_hi;
+  __shared__ int s_atom[kAtoms];
+  volatile int* abort_flag = &s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nbins = ep.ntypes * ep.n_int;
+  const int M = ep.M, NP = cf.NP;
+  const uint32_t b_piece = (uint32_t)NP * 32;
+  const int64_t tabF_ti = tabF_elems(nbins, NP);
+  float* sc_cta = scratch + (size_t)blockIdx.x * 5 * kAtoms * scap;
+
+  if (tid == 0) {
+    for (int s = 0; s < kNS; ++s) {
+      mbar_init(&s_full[s], 1);
+      mbar_init(&s_empty[s], 1);
+      mbar_init(&s_gen[s], kRows);
+    }
+    mbar_init(&s_acc, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  const uint32_t tmem = s_tmem;
+
+  int nrange = 0, nover = 0;
+  unsigned long long npairs = 0;
+  uint32_t it = 0;     // chunks this CTA has pipelined (the same count in every role)
+  uint32_t acc_n = 0;  // accumulator completions
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int ti = tile_type(tm, tile);
+    if (tid == 0) {
+      s_lo = INT_MAX;
+      s_hi = -1;
+    }
+    __syncthreads();
+    // ---- phase 1: four atoms per warp
+    for (int j = 0; j < kAtoms / 8; ++j) {
+      const int al = warp * (kAtoms / 8) + j;
+      const int atom = tile_atom(tm, ti, tile, al);
+      if (lane == 0) s_atom[al] = atom;
+      int lo, hi;
+      const int np = sort_atom(atom, off, nlist, nn, cap, g, ep, scap, shist + al * cf.nbp,
+                               nbins, sc_cta + (size_t)al * scap,
+                               pairs_out + ((size_t)tile * kAtoms + al) * scap, lane, nrange,
+                               nover, lo, hi);
+      npairs += (unsigned long long)np;
+      lo = __reduce_min_sync(0xffffffffu, lo);
+      hi = __reduce_max_sync(0xffffffffu, hi);
+      if (lane == 0 && hi >= 0) {
+        atomicMin(&s_lo, lo);
+        atomicMax(&s_hi, hi);
+      }
+    }
+    __syncthreads();
+    const int kb0 = s_hi >= 0 ? (s_lo & ~1) : 0;
+    const int nk = s_hi >= 0 ? (s_hi - kb0) / 2 + 1 : 0;  // chunks of two bins
+    // the backward's copy of the tile's bin ends and occupied range
+    {
+      int4* ho = reinterpret_cast<int4*>(hist_out + (size_t)tile * kAtoms * cf.nbp);
+      const int4* hs = reinterpret_cast<const int4*>(shist);
+      for (int q = tid; q < kAtoms * cf.nbp / 4; q += kThreads) ho[q] = hs[q];
+      if (tid == 0) range_out[tile] = make_int2(kb0, nk);
+    }
+    // ---- phase 2: T rows of the tile = C . table over the occupied bins
+    if (nk > 0) {
+      if (warp == 0) {
+        if (lane == 0) {
+          const __nv_bfloat16* Bt = tabF + (size_t)ti * tabF_ti + (size_t)(kb0 / 2) * kPC * NP * 16;
+          uint32_t i = it;
+          int kc = 0;
+          for (; kc < nk; ++kc, ++i) {
+            const int s = i % kNS;
+            const uint32_t u = i / kNS;
+            if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
+            mbar_expect_tx(&s_full[s], kPC * b_piece);
+            bulk_g2s(smem_u32(base + (size_t)s * cf.stage + kPC * kABytes),
+                     Bt + (size_t)kc * kPC * NP * 16, kPC * b_piece, &s_full[s]);
+          }
+          if (kc < nk) {
+            // aborted: wait (bounded) for the copies already issued to land
+            for (uint32_t j = (i - it) > (uint32_t)kNS ? i - kNS : it; j < i; ++j)
+              mbar_wait(&s_full[j % kNS], (j / kNS) & 1, nullptr);
+          }
+        }
+        __syncwarp();
+      } else if (warp == 1) {
+        if (lane == 0) {
+          const uint32_t idesc = make_idesc_bf16(kRows, NP);
+          uint32_t i = it;
+          for (int kc = 0; kc < nk; ++kc, ++i) {
+            const int s = i % kNS;
+            const uint32_t u = i / kNS;
+            if (!mbar_wait(&s_full[s], u & 1, abort_flag)) break;
+            if (!mbar_wait(&s_gen[s], u & 1, abort_flag)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t st0 = smem_u32(base + (size_t)s * cf.stage);
+#pragma unroll
+            for (int q = 0; q < kNPROD; ++q) {
+              int pa, pb;
+              prod_pieces(q, pa, pb);
+              const uint64_t ad = make_desc(st0 + pa * kABytes, 128, 256);
+              const uint64_t bd = make_desc(st0 + kPC * kABytes + pb * b_piece, 128, 256);
+              const uint32_t dst = tmem + (q > 0 ? (uint32_t)kAcc1 : 0u);
+              const uint32_t acc = (kc > 0 || q > 1) ? 1u : 0u;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(&s_empty[s])));
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                  smem_u32(&s_acc)));
+        }
+        __syncwarp();
+      } else if (warp >= 4) {
+        // C rows: thread r = (atom al, component c), two bins per chunk
+        const int r = tid - 128, al = r >> 2, c = r & 3;
+        const int* hist = shist + al * cf.nbp;
+        const size_t st = (size_t)kAtoms * scap;
+        const float* Rc = sc_cta + (size_t)c * st + (size_t)al * scap;
+        const float* Us = sc_cta + 4 * st + (size_t)al * scap;
+        uint32_t i = it;
+        for (int kc = 0; kc < nk; ++kc, ++i) {
+          const int s = i % kNS;
+          const uint32_t u = i / kNS;
+          if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
+          unsigned char* sa = base + (size_t)s * cf.stage;
+#pragma unroll
+          for (int hb = 0; hb < 2; ++hb) {
+            const int bin = kb0 + 2 * kc + hb;
+            float x[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (bin < nbins) {
+              const int e = hist[bin];
+              for (int k = bin_begin(hist, bin); k < e; ++k) {
+                const float rv = Rc[k], uu = Us[k];
+                const float u2 = uu * uu;
+                x[0] += rv;
+                x[1] = fmaf(rv, uu, x[1]);
+                x[2] = fmaf(rv, u2, x[2]);
+                x[3] = fmaf(rv, u2 * uu, x[3]);
+                x[4] = fmaf(rv, u2 * u2, x[4]);
+                x[5] = fmaf(rv, u2 * u2 * uu, x[5]);
+              }
+            }
+            __align__(16) __nv_bfloat16 pv[3][8];
+            split8<kPC>(x, pv);
+            const int o = (r >> 3) * 256 + hb * 128 + (r & 7) * 16;
+#pragma unroll
+            for (int p = 0; p < kPC; ++p)
+              *reinterpret_cast<uint4*>(sa + p * kABytes + o) = *reinterpret_cast<const uint4*>(pv[p]);
+          }
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          mbar_arrive(&s_gen[s]);
+        }
+      }
+      it += nk;
+      if (!mbar_wait(&s_acc, acc_n & 1, nullptr)) *abort_flag = 1;
+      ++acc_n;
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+    }
+    __syncthreads();
+    if (*abort_flag) break;
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4).. and half the columns
+    {
+      const int lg = warp & 3, half = warp >> 2;
+      const int row_t = lg * 32 + lane;
+      const int al = row_t >> 2, c = row_t & 3;
+      const int atom = s_atom[al];
+      const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16);
+      const int nch = NP / 16;
+      const int c_beg = half ? (nch + 1) / 2 : 0, c_end = half ? nch : (nch + 1) / 2;
+      float* Tr = atom >= 0 ? T + (size_t)atom * 4 * M + (size_t)c * M : nullptr;
+      for (int ch = c_beg; ch < c_end; ++ch) {
+        float v[16];
+        if (nk > 0) {
+          float v2[16];
+          tmem_ld16(tbase + (uint32_t)(ch * 16), v);
+          tmem_ld16(tbase + (uint32_t)(kAcc1 + ch * 16), v2);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) v[k] = (v[k] + v2[k]) * ep.inv_nm;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) v[k] = 0.0f;
+        }
+        if (Tr) {
+#pragma unroll
+          for (int k = 0; k < 16; k += 4)
+            if (ch * 16 + k < M)
+              *reinterpret_cast<float4*>(Tr + ch * 16 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+  }
+  nrange = __reduce_add_sync(0xffffffffu, nrange);
+  if (lane == 0 && nrange) atomicAdd(&status[ST_RANGE], nrange);
+  if (lane == 0 && nover) atomicAdd(&status[ST_SEL], nover);
+  if (lane == 0 && pair_count && npairs) atomicAdd(pair_count, npairs);
+  if (tid == 0 && *abort_flag) atomicAdd(&status[ST_TIMEOUT], 1);
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  if (warp == 2)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTmemCols));
+}
+
+// ------------------------------------------------------------------ backward
+// Per tile of 32 atoms (the forward's tiles): the bins of the tile's
+// occupied range in windows of 16; per window
+//   B[(atom, c)][(bin, q)] = (1/N_m) sum_m dT[atom][c][m] c_bin[q][m]
+// on the tensor cores (A = dE/dT rows from FP32, split in the stage by warps
+// 4-7; B = the table window, bulk copies), then B goes through TMEM to shared
+// memory and every pair of the window takes its 24 values for the chain rule
+// to the forces and virial (one warp per atom, lanes over the sorted pairs the
+// forward left: displacement and neighbor index).
+constexpr int kWin = 16;                    // bins per window (N <= 128)
+constexpr int kBsmAtom = kWin * 24 + 4;     // floats per atom in the window buffer
+
+struct BwdCfg {
+  int NP, nbp, stage;
+  size_t smem;
+};
+
+__host__ __device__ inline BwdCfg bwd_cfg(const EnvParams& ep) {
+  BwdCfg c;
+  c.NP = round16(ep.M);
+  c.nbp = round4(ep.ntypes * ep.n_int);
+  c.stage = kPC * kABytes + kPC * kWin * 8 * 32;
+  size_t st = (size_t)kNS * c.stage;
+  const size_t bsm = (size_t)kAtoms * kBsmAtom * 4;
+  if (st < bsm) st = bsm;
+  c.smem = 128 + st + (size_t)kAtoms * c.nbp * 4;
+  return c;
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_tab_bwd_tc(int64_t ntile, TileMap tm, const float4* __restrict__ pairs,
+                 const int* __restrict__ hist_in, const int2* __restrict__ range_in, EnvParams ep,
+                 const __nv_bfloat16* __restrict__ tabB, int scap, const float* __restrict__ dT,
+                 unsigned long long* __restrict__ ffix, double* __restrict__ vir_part,
+                 int32_t* __restrict__ status) {
+  const BwdCfg cf = bwd_cfg(ep);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  size_t st_bytes = (size_t)kNS * cf.stage;
+  if (st_bytes < (size_t)kAtoms * kBsmAtom * 4) st_bytes = (size_t)kAtoms * kBsmAtom * 4;
+  int* shist = (int*)(base + st_bytes);
+  float* Bsm = (float*)base;  // aliases the stages between the MMAs of two windows
+  __shared__ __align__(8) uint64_t s_full[kNS], s_empty[kNS], s_gen[kNS], s_acc;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  __shared__ int s_atom[kAtoms];
+  __shared__ double s_vir[kThreads / 32][9];
+  volatile int* abort_flag = &s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nbins = ep.ntypes * ep.n_int, n_int = ep.n_int;
+  const int M = ep.M, NP = cf.NP, nkc = NP / 16;
+  const int NB8 = 8 * even_bins(nbins);
+  const size_t blk = (size_t)NB8 * 16;
+  const int64_t tabB_ti = tabB_elems(nbins, NP);
+
+  if (tid == 0) {
+    for (int s = 0; s < kNS; ++s) {
+      mbar_init(&s_full[s], 1);
+      mbar_init(&s_empty[s], 1);
+      mbar_init(&s_gen[s], kRows);
+    }
+    mbar_init(&s_acc, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (lane < 9) s_vir[warp][lane] = 0.0;
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  const uint32_t tmem = s_tmem;
+
+  int nbad = 0;
+  uint32_t it = 0, acc_n = 0;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int ti = tile_type(tm, tile);
+    {
+      const int4* hi4 = reinterpret_cast<const int4*>(hist_in + (size_t)tile * kAtoms * cf.nbp);
+      int4* hs = reinterpret_cast<int4*>(shist);
+      for (int q = tid; q < kAtoms * cf.nbp / 4; q += kThreads) hs[q] = hi4[q];
+      if (tid < kAtoms) s_atom[tid] = tile_atom(tm, ti, tile, tid);
+    }
+    const int2 rg = range_in[tile];
+    const int kb0 = rg.x, nbt = 2 * rg.y;  // bins kb0 .. kb0 + nbt - 1 (even count)
+    __syncthreads();
+    float fxa[kAtoms / 8], fya[kAtoms / 8], fza[kAtoms / 8];
+#pragma unroll
+    for (int j = 0; j < kAtoms / 8; ++j) fxa[j] = fya[j] = fza[j] = 0.0f;
+    float vl[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) vl[a] = 0.0f;
+    for (int w0 = kb0; w0 < kb0 + nbt; w0 += kWin) {
+      const int wb = min(kWin, kb0 + nbt - w0);  // even
+      const int Wr = wb * 8;                     // MMA N (a multiple of 16)
+      // ---- B window = dT . table^T on the tensor cores
+      if (warp == 0) {
+        if (lane == 0) {
+          const __nv_bfloat16* Bt = tabB + (size_t)ti * tabB_ti + (size_t)w0 * 8 * 16;
+          uint32_t i = it;
+          int kc = 0;
+          for (; kc < nkc; ++kc, ++i) {
+            const int s = i % kNS;
+            const uint32_t u = i / kNS;
+            if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
+            mbar_expect_tx(&s_full[s], kPC * Wr * 32);
+            const uint32_t dst = smem_u32(base + (size_t)s * cf.stage + kPC * kABytes);
+#pragma unroll
+            for (int p = 0; p < kPC; ++p)
+              bulk_g2s(dst + p * Wr * 32, Bt + ((size_t)kc * kPC + p) * blk, Wr * 32, &s_full[s]);
+          }
+          if (kc < nkc) {
+            for (uint32_t j = (i - it) > (uint32_t)kNS ? i - kNS : it; j < i; ++j)
+              mbar_wait(&s_full[j % kNS], (j / kNS) & 1, nullptr);
+          }
+        }
+        __syncwarp();
+      } else if (warp == 1) {
+        if (lane == 0) {
+          const uint32_t idesc = make_idesc_bf16(kRows, Wr);
+          uint32_t i = it;
+          for (int kc = 0; kc < nkc; ++kc, ++i) {
+            const int s = i % kNS;
+            const uint32_t u = i / kNS;
+            if (!mbar_wait(&s_full[s], u & 1, abort_flag)) break;
+            if (!mbar_wait(&s_gen[s], u & 1, abort_flag)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t st0 = smem_u32(base + (size_t)s * cf.stage);
+#pragma unroll
+            for (int q = 0; q < kNPROD; ++q) {
+              int pa, pb;
+              prod_pieces(q, pa, pb);
+              const uint64_t ad = make_desc(st0 + pa * kABytes, 128, 256);
+              const uint64_t bd = make_desc(st0 + kPC * kABytes + pb * Wr * 32, 128, 256);
+              const uint32_t dst = tmem + (q > 0 ? (uint32_t)kAcc1 : 0u);
+              const uint32_t acc = (kc > 0 || q > 1) ? 1u : 0u;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(&s_empty[s])));
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                  smem_u32(&s_acc)));
+        }
+        __syncwarp();
+      } else if (warp >= 4) {
+        // A rows: thread r = (atom al, component c), 16 columns of dE/dT per chunk
+        const int r = tid - 128, al = r >> 2, c = r & 3;
+        const int atom = s_atom[al];
+        const float* dr = atom >= 0 ? dT + (size_t)atom * 4 * M + (size_t)c * M : nullptr;
+        uint32_t i = it;
+        for (int kc = 0; kc < nkc; ++kc, ++i) {
+          const int s = i % kNS;
+          const uint32_t u = i / kNS;
+          if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
+          float x[16];
+#pragma unroll
+          for (int k = 0; k < 16; k += 4) {
+            const int col = kc * 16 + k;
+            const float4 v = (dr && col < M) ? __ldg(reinterpret_cast<const float4*>(dr + col))
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[k] = v.x;
+            x[k + 1] = v.y;
+            x[k + 2] = v.z;
+            x[k + 3] = v.w;
+          }
+          unsigned char* sa = base + (size_t)s * cf.stage;
+#pragma unroll
+          for (int kg = 0; kg < 2; ++kg) {
+            __align__(16) __nv_bfloat16 pv[3][8];
+            split8<kPC>(x + kg * 8, pv);
+            const int o = (r >> 3) * 256 + kg * 128 + (r & 7) * 16;
+#pragma unroll
+            for (int p = 0; p < kPC; ++p)
+              *reinterpret_cast<uint4*>(sa + p * kABytes + o) = *reinterpret_cast<const uint4*>(pv[p]);
+          }
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          mbar_arrive(&s_gen[s]);
+        }
+      }
+      it += nkc;
+      if (!mbar_wait(&s_acc, acc_n & 1, nullptr)) *abort_flag = 1;
+      ++acc_n;
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      __syncthreads();
+      if (*abort_flag) break;
+      // ---- B window: TMEM -> shared memory [atom][bin][c * 6 + q] (times 1/N_m)
+      {
+        const int lg = warp & 3, half = warp >> 2;
+        const int row_t = lg * 32 + lane;
+        const int al = row_t >> 2, c = row_t & 3;
+        const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16);
+        const int nch = Wr / 16;
+        const int c_beg = half ? (nch + 1) / 2 : 0, c_end = half ? nch : (nch + 1) / 2;
+        for (int ch = c_beg; ch < c_end; ++ch) {
+          float v[16], v2[16];
+          tmem_ld16(tbase + (uint32_t)(ch * 16), v);
+          tmem_ld16(tbase + (uint32_t)(kAcc1 + ch * 16), v2);
+#pragma unroll
+          for (int hb = 0; hb < 2; ++hb) {
+            float* dst = Bsm + al * kBsmAtom + (2 * ch + hb) * 24 + c * 6;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) dst[q] = (v[hb * 8 + q] + v2[hb * 8 + q]) * ep.inv_nm;
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n");
+      __syncthreads();
+      // ---- pairs of the window: chain rule to the forces and virial
+      const int wend = min(w0 + wb, nbins);  // bins w0 .. wend - 1 exist
+#pragma unroll
+      for (int j = 0; j < kAtoms / 8; ++j) {
+        const int al = warp * (kAtoms / 8) + j;
+        if (s_atom[al] < 0) continue;
+        const int* hist = shist + al * cf.nbp;
+        const int kbeg = bin_begin(hist, w0), kend = hist[wend - 1];
+        const float4* pr = pairs + ((size_t)tile * kAtoms + al) * scap;
+        for (int k = kbeg + lane; k < kend; k += 32) {
+          // the pair's bin: the one whose sorted range holds k
+          int b = w0;
+          while (b + 1 < wend && hist[b] <= k) ++b;
+          const float4 q4 = pr[k];
+          const float dx = q4.x, dy = q4.y, dz = q4.z;
+          const int jn = __float_as_int(q4.w);
+          const int tj = b / n_int, th = b - tj * n_int;
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          Pair P;
+          pair_geom(ep, dx, dy, dz, r2, tj, P);
+          const float u = P.s * ep.inv_h - (float)th;  // the sort's interval
+          const float* Bk = Bsm + al * kBsmAtom + (b - w0) * 24;
+          float Bv[24];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            const float4 t4 = reinterpret_cast<const float4*>(Bk)[q];
+            Bv[4 * q] = t4.x;
+            Bv[4 * q + 1] = t4.y;
+            Bv[4 * q + 2] = t4.z;
+            Bv[4 * q + 3] = t4.w;
+          }
+          float gR[4], dgu[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float* bb = Bv + c * 6;
+            gR[c] = fmaf(fmaf(fmaf(fmaf(fmaf(bb[5], u, bb[4]), u, bb[3]), u, bb[2]), u, bb[1]), u, bb[0]);
+            dgu[c] = fmaf(fmaf(fmaf(fmaf(5.0f * bb[5], u, 4.0f * bb[4]), u, 3.0f * bb[3]), u,
+                               2.0f * bb[2]),
+                          u, bb[1]);
+          }
+          const float ux = P.dx * P.ir, uy = P.dy * P.ir, uz = P.dz * P.ir;
+          const float s = P.s;
+          const float gs = ep.inv_h * s * (dgu[0] + ux * dgu[1] + uy * dgu[2] + uz * dgu[3]);
+          const float a0 = gR[0] + gs;
+          const float dot = gR[1] * ux + gR[2] * uy + gR[3] * uz;
+          const float sor = s * P.ir;
+          const float coef = P.dsdr * (a0 + dot) - sor * dot;
+          float gx = coef * ux + sor * gR[1];
+          float gy = coef * uy + sor * gR[2];
+          float gz = coef * uz + sor * gR[3];
+          if (!(isfinite(gx) && isfinite(gy) && isfinite(gz)) || fabsf(gx) > 4.0e6f ||
+              fabsf(gy) > 4.0e6f || fabsf(gz) > 4.0e6f) {
+            ++nbad;
+            gx = gy = gz = 0.0f;
+          }
+          fxa[j] += gx;
+          fya[j] += gy;
+          fza[j] += gz;
+          vl[0] -= dx * gx;
+          vl[1] -= dx * gy;
+          vl[2] -= dx * gz;
+          vl[3] -= dy * gx;
+          vl[4] -= dy * gy;
+          vl[5] -= dy * gz;
+          vl[6] -= dz * gx;
+          vl[7] -= dz * gy;
+          vl[8] -= dz * gz;
+          unsigned long long* fj = ffix + (size_t)jn * 3;
+          atomicAdd(fj + 0, (unsigned long long)(-__float2ll_rn(gx * DP_FSCALE_F)));
+          atomicAdd(fj + 1, (unsigned long long)(-__float2ll_rn(gy * DP_FSCALE_F)));
+          atomicAdd(fj + 2, (unsigned long long)(-__float2ll_rn(gz * DP_FSCALE_F)));
+        }
+      }
+      // the window buffer is read before the next window's bulk copies land there
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      __syncthreads();
+    }
+    if (*abort_flag) break;
+    // the centres' own forces: lane partials summed across the warp in FP64
+#pragma unroll
+    for (int j = 0; j < kAtoms / 8; ++j) {
+      const int atom = s_atom[warp * (kAtoms / 8) + j];
+      double red[3] = {fxa[j], fya[j], fza[j]};
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) red[a] += __shfl_xor_sync(0xffffffffu, red[a], o);
+      if (lane == 0 && atom >= 0) {
+        unsigned long long* fi = ffix + (size_t)atom * 3;
+        atomicAdd(fi + 0, (unsigned long long)__double2ll_rn(red[0] * DP_FSCALE));
+        atomicAdd(fi + 1, (unsigned long long)__double2ll_rn(red[1] * DP_FSCALE));
+        atomicAdd(fi + 2, (unsigned long long)__double2ll_rn(red[2] * DP_FSCALE));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+      for (int a = 0; a < 9; ++a) vl[a] += __shfl_xor_sync(0xffffffffu, vl[a], o);
+    if (lane < 9) {
+      float vv = vl[0];
+#pragma unroll
+      for (int a = 1; a < 9; ++a) vv = lane == a ? vl[a] : vv;
+      s_vir[warp][lane] += (double)vv;
+    }
+    __syncthreads();  // shist and s_atom are refilled by the next tile
+  }
+  if (lane < 9) vir_part[((size_t)blockIdx.x * (kThreads / 32) + warp) * 9 + lane] = s_vir[warp][lane];
+  nbad = __reduce_add_sync(0xffffffffu, nbad);
+  if (lane == 0 && nbad) atomicAdd(&status[ST_NONFINITE], nbad);
+  if (tid == 0 && *abort_flag) atomicAdd(&status[ST_TIMEOUT], 1);
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  if (warp == 2)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTmemCols));
+}
+
+int g_sms = 0;
+int sm_count() {
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 1;
+  }
+  return g_sms;
+}
+
+int stage_cap_tc(const EnvParams& ep) {
+  return ((int)(1.0f / ep.inv_nm + 0.5f) + 32 + 31) / 32 * 32;
+}
+
+int tc_grid() { return 2 * sm_count(); }
+
+}  // namespace
+
+int64_t tab_tc_elems(const EnvParams& ep) {
+  const int nbins = ep.ntypes * ep.n_int, NP = round16(ep.M);
+  const int64_t f = tabF_elems(nbins, NP), b = tabB_elems(nbins, NP);
+  return (f > b ? f : b) * ep.ntypes;
+}
+
+int tab_tc_build(cudaStream_t st, const float* table, const EnvParams& ep, __nv_bfloat16* tabF,
+                 __nv_bfloat16* tabB) {
+  if (ep.M > 128 || ep.M % 4) return -1;
+  const int nbins = ep.ntypes * ep.n_int, NP = round16(ep.M);
+  const int64_t nf = (int64_t)ep.ntypes * tabF_elems(nbins, NP) / kPC;
+  const int64_t nb = (int64_t)ep.ntypes * tabB_elems(nbins, NP) / kPC;
+  DP_LAUNCHED(2);
+  k_tile_tabF<<<(int)((nf + 255) / 256), 256, 0, st>>>(table, ep.ntypes, nbins, ep.M, NP, tabF);
+  k_tile_tabB<<<(int)((nb + 255) / 256), 256, 0, st>>>(table, ep.ntypes, nbins, ep.M, NP, tabB);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int64_t tab_tc_scratch_floats(const EnvParams& ep) {
+  return (int64_t)tc_grid() * 5 * kAtoms * stage_cap_tc(ep);
+}
+
+int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, const uint32_t* nlist,
+                      const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
+                      const __nv_bfloat16* tabF, float* scratch, float4* pairs_out,
+                      int* hist_out, int2* range_out, float* T, int32_t* status,
+                      unsigned long long* pair_count) {
+  if (ep.M > 128 || ep.M % 4 || ep.M < 16) return -1;
+  if (tm.ntypes < 1 || tm.ntypes > DP_MAXT || tm.ntypes != ep.ntypes) return -1;
+  if (((uintptr_t)tabF & 15) || ((uintptr_t)T & 15)) return -1;
+  const int64_t ntile = tm.tile_off[tm.ntypes];
+  if (ntile <= 0) return 0;
+  const FwdCfg cf = fwd_cfg(ep);
+  if (cf.smem > 113 * 1024) return -1;  // two CTAs per SM
+  static size_t set = 0;
+  if (cf.smem > 48 * 1024 && cf.smem > set) {
+    if (cudaFuncSetAttribute(k_tab_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cf.smem) != cudaSuccess)
+      return -3;
+    set = cf.smem;
+  }
+  const int grid = (int)(ntile < tc_grid() ? ntile : tc_grid());
+  DP_LAUNCHED(1);
+  k_tab_fwd_tc<<<grid, kThreads, cf.smem, st>>>(ntile, tm, off, nlist, nn, cap, g, ep, tabF,
+                                                stage_cap_tc(ep), scratch, pairs_out, hist_out,
+                                                range_out, T, status, pair_count);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int64_t tab_tc_slots() { return (int64_t)tc_grid() * (kThreads / 32); }
+
+int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs, const int* hist,
+                      const int2* range, const EnvParams& ep, const __nv_bfloat16* tabB,
+                      const float* dT, unsigned long long* ffix, double* vir_part, int vir_slots,
+                      int32_t* status) {
+  if (ep.M > 128 || ep.M % 4 || ep.M < 16) return -1;
+  if (tm.ntypes < 1 || tm.ntypes > DP_MAXT || tm.ntypes != ep.ntypes) return -1;
+  if (((uintptr_t)tabB & 15) || ((uintptr_t)dT & 15) || ((uintptr_t)hist & 15)) return -1;
+  if (vir_slots < tab_tc_slots()) return -1;
+  const int64_t ntile = tm.tile_off[tm.ntypes];
+  if (ntile <= 0) return 0;
+  const BwdCfg cf = bwd_cfg(ep);
+  if (cf.smem > 113 * 1024) return -1;  // two CTAs per SM
+  static size_t set = 0;
+  if (cf.smem > 48 * 1024 && cf.smem > set) {
+    if (cudaFuncSetAttribute(k_tab_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cf.smem) != cudaSuccess)
+      return -3;
+    set = cf.smem;
+  }
+  // every slot is written (grid = the full persistent grid, idle CTAs write zeros)
+  DP_LAUNCHED(1);
+  k_tab_bwd_tc<<<tc_grid(), kThreads, cf.smem, st>>>(ntile, tm, pairs, hist, range, ep, tabB,
+                                                     stage_cap_tc(ep), dT, ffix, vir_part, status);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int64_t tab_tc_pair_elems(const EnvParams& ep, int64_t ntile) {
+  return ntile * kAtoms * stage_cap_tc(ep);
+}
+int64_t tab_tc_hist_elems(const EnvParams& ep, int64_t ntile) {
+  return ntile * kAtoms * round4(ep.ntypes * ep.n_int);
+}

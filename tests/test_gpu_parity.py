@@ -110,7 +110,8 @@ def test_descriptor_matches_oracle(dp, cu_stress):
 
 
 # ------------------------------------------------------------------ a1..a9
-def _parity(dp, h, m, tab, x, t, box, sel=CU_SEL, rc=CU_RC, rcs=CU_RCS, stress=False, tag=""):
+def _parity(dp, h, m, tab, x, t, box, sel=CU_SEL, rc=CU_RC, rcs=CU_RCS, stress=False, tag="",
+            e_rel=2e-6):
     E, F, V, Ei = dp.dp_compute(h, x, t, box, atom_energy=True)
     r = oracle.evaluate(m, tab, rc, rcs, sel, x, t, box)
     n = len(x)
@@ -130,7 +131,7 @@ def _parity(dp, h, m, tab, x, t, box, sel=CU_SEL, rc=CU_RC, rcs=CU_RCS, stress=F
     else:
         emean = float(np.abs(r["atom_energy"]).mean())
         emax = float(np.abs(r["atom_energy"]).max())
-        assert de < max(E_TOL, 2e-6 * emean), (de, emean)
+        assert de < max(E_TOL, e_rel * emean), (de, emean)
         assert dei < 2e-5 * emax, (dei, emax)
         assert fr < max(F_TOL, 3e-5 * frms), (fr, frms)
         assert dv < 1e-4 * vmax + 1e-9, (dv, vmax)
