@@ -108,7 +108,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   volatile int* abort_flag = &s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * NT;
+  // grid (N tiles, row tiles): the N tiles of one row tile are consecutive
+  // blocks, so its A rows are read from HBM once and then hit in L2
+  const int m_tile = blockIdx.y, n_tile = blockIdx.x;
+  const int m0 = m_tile * kBM, n0 = n_tile * NT;
   const int ntile = min(NT, N - n0);  // NT, or the ragged last tile (a multiple of 16)
   const int nk = K / kBK;
   const uint32_t a_bytes = PC * C::A_BYTES;
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t st0 = smem_u32(base + (size_t)s * C::STAGE);
         mbar_expect_tx(&s_full[s], (EPI == TC_L0 ? 0u : a_bytes) + PC * b_piece);
         if (EPI != TC_L0)
-          bulk_g2s(st0, A + ((size_t)blockIdx.x * nk + kc) * PC * (kBM * kBK), a_bytes,
+          bulk_g2s(st0, A + ((size_t)m_tile * nk + kc) * PC * (kBM * kBK), a_bytes,
                    &s_full[s]);
         bulk_g2s(st0 + a_bytes,
                  B + (size_t)n0 * K * PC + (size_t)kc * PC * ((size_t)ntile * kBK),
@@ -268,16 +271,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int c_beg = half ? (nch + 1) / 2 : 0, c_end = half ? nch : (nch + 1) / 2;
     const int nkc_out = ep.ldo / kBK;
     float e_acc = 0.0f;
-    // TC_DT: T[row][c][0..15] and the partial sums of the second factor
+    // TC_DT: T[row][c][0..15] and the partial sums of the second factor; the
+    // first factor of the tile's 16 b goes through shared memory [row][c][b]
+    // (the idle stage memory after the half-sum area) for row-contiguous stores
     float tl[4][16], part[4][16];
     const float* tr = nullptr;
-    float* dtr = nullptr;
+    float* sf = reinterpret_cast<float*>(base + 33280);
     if (EPI == TC_DT) {
-      if (rok) {
-        const size_t trow = (size_t)(ep.tidx ? ep.tidx[row] : row) * 4 * ep.Mw;
-        tr = ep.T + trow;
-        dtr = ep.dT + trow;
-      }
+      if (rok) tr = ep.T + (size_t)(ep.tidx ? ep.tidx[row] : row) * 4 * ep.Mw;
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           float acc = 0.0f;
 #pragma unroll
           for (int a = 0; a < 16; ++a) acc = fmaf(v[a], tl[c][a], acc);
-          dtr[c * ep.Mw + b] = acc;  // first factor: complete for this b
+          sf[row_t * 68 + c * 16 + ch] = acc;  // first factor: complete for this b
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c)
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       __syncthreads();
       if (!half && rok) {
-        float* pp = ep.part + (size_t)blockIdx.y * ep.part_ps + (size_t)row * 64;
+        float* pp = ep.part + (size_t)n_tile * ep.part_ps + (size_t)row * 64;
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -402,6 +403,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             *reinterpret_cast<float4*>(pp + c * 16 + a) =
                 make_float4(part[c][a] + sp[c * 16 + a], part[c][a + 1] + sp[c * 16 + a + 1],
                             part[c][a + 2] + sp[c * 16 + a + 2], part[c][a + 3] + sp[c * 16 + a + 3]);
+      }
+      // first factor: dE/dT[c][b] for the tile's b = n0/16 .., four threads
+      // per (row, c), 16-byte stores
+      const int nb = ntile / 16, b0 = n0 / 16;
+      for (int q = tid; q < kBM * 16; q += kTcThreads) {
+        const int rt = q >> 4, c = (q >> 2) & 3, f = (q & 3) * 4;
+        const int grow = m0 + rt;
+        if (grow >= M || f >= nb) continue;
+        const float* src = sf + rt * 68 + c * 16 + f;
+        float* dst = ep.dT + (size_t)(ep.tidx ? ep.tidx[grow] : grow) * 4 * ep.Mw +
+                     (size_t)c * ep.Mw + b0 + f;
+        if (f + 4 <= nb && ((b0 + f) & 3) == 0 && (ep.Mw & 3) == 0) {
+          *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
+        } else {
+          for (int k = 0; k < 4 && f + k < nb; ++k) dst[k] = src[k];
+        }
       }
     }
   }
@@ -435,7 +452,7 @@ int tc_gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A, const 
       return -3;
     attr = true;
   }
-  dim3 grid((M + kBM - 1) / kBM, (N + NT - 1) / NT);
+  dim3 grid((N + NT - 1) / NT, (M + kBM - 1) / kBM);
   DP_LAUNCHED(1);
   k_tc_gemm<EPI, PC><<<grid, kTcThreads, TcCfg<PC>::SMEM, st>>>(M, N, K, NT, A, B, ep);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
