@@ -5,10 +5,12 @@ Workload: FCC copper 100x100x100 cells (4,000,000 atoms, a = 3.634 A,
 periodic), 330 K Maxwell velocities, the seeded N(0, 0.1) model of the paper's
 shape (embedding 1-32-64-128, M^< = 16, fitting 2048-240-240-240-1, rc 8 A,
 rcs 0.5 A, sel 256), tabulated embedding (h = 0.01) fused with the
-contraction in FP32, velocity-Verlet at dt = 1 fs, list rebuild every 10
+contraction, FP32-accurate tensor-core modes for the contraction and the
+fitting net, velocity-Verlet at dt = 1 fs, list rebuild every 10
 steps with a 2 A skin.  One bench step is one 10-MD-step block (one list
 rebuild and 10 force evaluations), so the default 10 steps are the 100 MD
-steps of the workload.  Inputs (T, dT, lists: ~30 GB) are far larger than L2.
+steps of the workload.  Inputs (T, dT, lists, sorted pairs: ~50 GB) are far
+larger than L2.
 
 JSON line fields beyond the base contract: roofline (dominant phase, live
 CUDA-event time), cpu_baseline (the FP64 oracle on a bounded sample of the
@@ -61,6 +63,8 @@ def parse():
                     help="MD steps of the plain untabulated comparator (0: skip)")
     ap.add_argument("--fit-precision", type=int, default=2,
                     help="0 FP32 CUDA cores, 1 BF16 tensor cores, 2 FP32-accurate tensor cores")
+    ap.add_argument("--ref-cells", type=int, default=20,
+                    help="FCC cells per edge of the reference arm's oracle sample")
     ap.add_argument("--embed-precision", type=int, default=2,
                     help="tabulated contraction: 0 FP32 CUDA cores, 2 FP32-accurate tensor cores")
     return ap.parse_args()
@@ -216,7 +220,7 @@ def run_reference(args, world, rank, pg):
         inputs.write_seeded_model(path, inputs.COPPER_SPEC, seed=0, std=0.1)
         m = oracle.Model(path)
         tab = oracle.Table(m, 0.01, 2.0)
-        x, t, box = inputs.fcc_copper(20, sigma=0.0)
+        x, t, box = inputs.fcc_copper(args.ref_cells, sigma=0.0)
         v = inputs.maxwell_velocities(np.full(len(x), inputs.MASS_CU), 330.0, seed=2)
         masses = [inputs.MASS_CU]
         x, v, f, _ = oracle.md(m, tab, RC, RCS, SEL, x, v, t, masses, box, DT_FS, 0)
@@ -228,7 +232,8 @@ def run_reference(args, world, rank, pg):
         dt = time.perf_counter() - t0
     value = len(x) * args.steps / dt
     cores = oracle.get_threads()
-    sample = f"FP64 oracle velocity-Verlet, {len(x)}-atom copper box (20^3 cells), 1 MD step per bench step"
+    sample = (f"FP64 oracle velocity-Verlet, {len(x)}-atom copper box ({args.ref_cells}^3 cells), "
+              "1 MD step per bench step")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
