@@ -436,6 +436,374 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                  "r"(C::TMEM_COLS));
 }
 
+// ---------------------------------------------------------------- persistent
+// K-short GEMMs (K <= 240: hidden, last, backward and dE/dD layers): one CTA
+// per SM walks row tiles; a row tile's A (all K chunks, all pieces) stays in
+// shared memory while its N tiles of 128 columns stream B through kPNS stages.
+// The accumulators are double-buffered in TMEM (2 x 256 columns), so warps 4-7
+// drain N tile t (the fused epilogue, one thread per row) while warp 1 issues
+// the MMAs of tile t+1 and warp 0 the copies of t+2.  Per-row state across the
+// N tiles of a row tile (the energy sum, the dE/dT second factor) stays in the
+// epilogue thread's registers.
+constexpr int kPNT = 128;  // columns per N tile
+constexpr int kPNS = 3;    // B stages
+constexpr int kPMaxK = 16; // K chunks a row tile can hold (K <= 256)
+
+template <int PC>
+struct PCfg {
+  static constexpr int A_CHUNK = PC * kBM * kBK * 2;   // one K chunk of A, all pieces
+  static constexpr int B_PIECE = kPNT * kBK * 2;       // one piece of a B stage
+  static constexpr int B_STAGE = PC * B_PIECE;
+  static size_t smem(int nk) { return 128 + (size_t)nk * A_CHUNK + (size_t)kPNS * B_STAGE; }
+};
+
+template <int EPI, int PC>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm_p(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
+                const __nv_bfloat16* __restrict__ B, TcEpi ep) {
+  using C = PCfg<PC>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  const int nk = K / kBK;
+  unsigned char* a_smem = base;
+  unsigned char* b_smem = base + (size_t)nk * C::A_CHUNK;
+  __shared__ __align__(8) uint64_t a_full[kPMaxK], a_empty, b_full[kPNS], b_empty[kPNS];
+  __shared__ __align__(8) uint64_t t_full[2], t_empty[2], fin;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  volatile int* abort_flag = &s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mtiles = (M + kBM - 1) / kBM;
+  const int ntn = (N + kPNT - 1) / kPNT;
+  // B is pre-tiled in tiles of 256 rows (the last ragged)
+  auto b_src = [&](int n, int kc, int p) {
+    const int n0 = n * kPNT, t256 = n0 / 256, r0 = n0 - t256 * 256;
+    const int nt256 = min(256, N - t256 * 256);
+    return B + (size_t)t256 * 256 * K * PC + ((size_t)kc * PC + p) * nt256 * kBK +
+           (size_t)(r0 / 8) * 128;
+  };
+
+  if (tid == 0) {
+    for (int k = 0; k < kPMaxK; ++k) mbar_init(&a_full[k], 1);
+    mbar_init(&a_empty, 1);
+    for (int s = 0; s < kPNS; ++s) {
+      mbar_init(&b_full[s], 1);
+      mbar_init(&b_empty[s], 1);
+    }
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(&t_full[j], 1);
+      mbar_init(&t_empty[j], kBM);
+    }
+    mbar_init(&fin, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: a row tile's A once, then B for every (N tile, K chunk)
+      uint32_t bi = 0, im = 0;
+      bool ok = true;
+      for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x, ++im) {
+        if (im > 0 && !mbar_wait(&a_empty, (im - 1) & 1, abort_flag)) break;
+        for (int kc = 0; kc < nk; ++kc) {
+          mbar_expect_tx(&a_full[kc], C::A_CHUNK);
+          bulk_g2s(smem_u32(a_smem + (size_t)kc * C::A_CHUNK),
+                   A + ((size_t)mt * nk + kc) * PC * (kBM * kBK), C::A_CHUNK, &a_full[kc]);
+        }
+        for (int n = 0; n < ntn && ok; ++n) {
+          const int nt = min(kPNT, N - n * kPNT);
+          for (int kc = 0; kc < nk; ++kc, ++bi) {
+            const int s = bi % kPNS;
+            const uint32_t u = bi / kPNS;
+            if (u > 0 && !mbar_wait(&b_empty[s], (u - 1) & 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(&b_full[s], PC * nt * 32);
+            const uint32_t dst = smem_u32(b_smem + (size_t)s * C::B_STAGE);
+#pragma unroll
+            for (int p = 0; p < PC; ++p)
+              bulk_g2s(dst + p * C::B_PIECE, b_src(n, kc, p), nt * 32, &b_full[s]);
+          }
+        }
+      }
+      if (*abort_flag) {
+        // aborted: wait (bounded) for the copies already issued to land
+        for (uint32_t j = bi > (uint32_t)kPNS ? bi - kPNS : 0; j < bi; ++j)
+          mbar_wait(&b_full[j % kPNS], (j / kPNS) & 1, nullptr);
+        if (im > 0)
+          for (int kc = 0; kc < nk; ++kc) mbar_wait(&a_full[kc], (im - 1) & 1, nullptr);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t bi = 0, ti = 0, im = 0;
+      bool ok = true;
+      for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x, ++im) {
+        for (int n = 0; n < ntn && ok; ++n, ++ti) {
+          const int nt = min(kPNT, N - n * kPNT);
+          const uint32_t idesc = make_idesc_bf16(kBM, nt);
+          const int j = ti & 1;
+          if (ti >= 2 && !mbar_wait(&t_empty[j], ((ti >> 1) - 1) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n");
+          for (int kc = 0; kc < nk; ++kc, ++bi) {
+            if (n == 0 && !mbar_wait(&a_full[kc], im & 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            const int s = bi % kPNS;
+            if (!mbar_wait(&b_full[s], (bi / kPNS) & 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t a0 = smem_u32(a_smem + (size_t)kc * C::A_CHUNK);
+            const uint32_t b0 = smem_u32(b_smem + (size_t)s * C::B_STAGE);
+#pragma unroll
+            for (int q = 0; q < (PC == 1 ? 1 : 6); ++q) {
+              int pa = 0, pb = 0;
+              if (PC > 1) prod_pieces(q, pa, pb);
+              const uint64_t ad = make_desc(a0 + pa * (kBM * kBK * 2), 128, 256);
+              const uint64_t bd = make_desc(b0 + pb * C::B_PIECE, 128, 256);
+              const uint32_t dst = tmem + (uint32_t)(j * 256) + (q > 0 ? 128u : 0u);
+              const uint32_t acc = (kc > 0 || q > 1) ? 1u : 0u;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(&b_empty[s])));
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                  smem_u32(&t_full[j])));
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&a_empty)));
+      }
+      // the epilogue may be waiting for a buffer this thread will not fill
+      if (!ok) *abort_flag = 1;
+      // every MMA issued completes before fin does (TMEM is freed after it)
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              smem_u32(&fin)));
+    }
+    __syncwarp();
+  } else if (warp >= 4) {
+    // epilogue: thread = row of the tile (TMEM lane), all columns of each N tile
+    const int r = tid - 128;
+    const uint32_t tl_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    uint32_t ti = 0;
+    for (int mt = blockIdx.x; mt < mtiles; mt += gridDim.x) {
+      const int row = mt * kBM + r;
+      const bool rok = row < M;
+      float e_acc = 0.0f;
+      float tl[4][16], part[4][16];
+      const float* tr = nullptr;
+      float* dtr = nullptr;
+      if (EPI == TC_DT) {
+        if (rok) {
+          const size_t trow = (size_t)(ep.tidx ? ep.tidx[row] : row) * 4 * ep.Mw;
+          tr = ep.T + trow;
+          dtr = ep.dT + trow;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int a = 0; a < 16; ++a) {
+            tl[c][a] = tr ? __ldg(tr + c * ep.Mw + a) : 0.0f;
+            part[c][a] = 0.0f;
+          }
+      }
+      bool fail = false;
+      for (int n = 0; n < ntn; ++n, ++ti) {
+        const int j = ti & 1;
+        if (!mbar_wait(&t_full[j], (ti >> 1) & 1, abort_flag)) {
+          fail = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        const int nt = min(kPNT, N - n * kPNT), nch = nt / 16;
+        float f1[4][8];
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          if (ch < nch) {
+            float v[16], v2[16];
+            tmem_ld16(tl_base + (uint32_t)(j * 256 + ch * 16), v);
+            if (PC > 1) {
+              tmem_ld16(tl_base + (uint32_t)(j * 256 + 128 + ch * 16), v2);
+#pragma unroll
+              for (int k = 0; k < 16; ++k) v[k] += v2[k];
+            }
+            const int ncol = n * kPNT + ch * 16;
+            if (rok) {
+              if (EPI == TC_DT) {
+                // v = dE/dD[b][0..15], b = ncol / 16 (Eq. 2)
+                const int b = ncol >> 4;
+                float tb[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  tb[c] = __ldg(tr + c * ep.Mw + b);
+                  float acc = 0.0f;
+#pragma unroll
+                  for (int a = 0; a < 16; ++a) acc = fmaf(v[a], tl[c][a], acc);
+                  f1[c][ch] = acc;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                  for (int a = 0; a < 16; ++a) part[c][a] = fmaf(v[a], tb[c], part[c][a]);
+              } else {
+                const size_t o = (size_t)row * ep.ldo + ncol;
+                float rr[16], bb[16], tt[16], oh[16];
+                if (EPI == TC_MID || EPI == TC_LAST) {
+#pragma unroll
+                  for (int k = 0; k < 16; k += 4)
+                    *reinterpret_cast<float4*>(bb + k) = *reinterpret_cast<const float4*>(ep.bias + ncol + k);
+                }
+                if (ep.R) {
+#pragma unroll
+                  for (int k = 0; k < 16; k += 4)
+                    *reinterpret_cast<float4*>(rr + k) =
+                        *reinterpret_cast<const float4*>(ep.R + (size_t)row * ep.ldr + ncol + k);
+                } else {
+#pragma unroll
+                  for (int k = 0; k < 16; ++k) rr[k] = 0.0f;
+                }
+                if (EPI == TC_BWD) {
+#pragma unroll
+                  for (int k = 0; k < 16; k += 4)
+                    *reinterpret_cast<float4*>(tt + k) =
+                        *reinterpret_cast<const float4*>(ep.Tt + (size_t)row * ep.ldt + ncol + k);
+                }
+                float oa[16], ob[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                  if (EPI == TC_MID) {
+                    const float t = tanhf(v[k] + bb[k]);
+                    oa[k] = t;
+                    ob[k] = rr[k] + t;
+                    oh[k] = ob[k];
+                  } else if (EPI == TC_LAST) {
+                    const float t = tanhf(v[k] + bb[k]);
+                    const float w = ep.wout[ncol + k];
+                    e_acc = fmaf(rr[k] + t, w, e_acc);
+                    oh[k] = w * (1.0f - t * t);
+                  } else {  // TC_BWD
+                    const float gz = v[k] + rr[k];
+                    ob[k] = gz;
+                    oh[k] = gz * (1.0f - tt[k] * tt[k]);
+                  }
+                }
+                if (EPI == TC_MID) {
+#pragma unroll
+                  for (int k = 0; k < 16; k += 4)
+                    *reinterpret_cast<float4*>(ep.out_a + o + k) = *reinterpret_cast<const float4*>(oa + k);
+                }
+                if (EPI == TC_MID || EPI == TC_BWD) {
+#pragma unroll
+                  for (int k = 0; k < 16; k += 4)
+                    *reinterpret_cast<float4*>(ep.out_b + o + k) = *reinterpret_cast<const float4*>(ob + k);
+                }
+                const int nkc_out = ep.ldo / kBK;
+                store_tiled<PC>(ep.out_h, nkc_out, row, ncol, oh);
+                store_tiled<PC>(ep.out_h, nkc_out, row, ncol + 8, oh + 8);
+              }
+            }
+          }
+        }
+        // TMEM buffer j is drained: the MMAs of tile t+2 may overwrite it
+        asm volatile("tcgen05.fence::before_thread_sync;\n");
+        mbar_arrive(&t_empty[j]);
+        if (EPI == TC_DT && rok) {
+          // first factor dE/dT[c][b] for this N tile's b = 8n .. 8n + nch - 1
+          const int b0 = n * (kPNT / 16);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float* d = dtr + c * ep.Mw + b0;
+            if (nch == 8 && ((b0 | ep.Mw) & 3) == 0) {
+              *reinterpret_cast<float4*>(d) = make_float4(f1[c][0], f1[c][1], f1[c][2], f1[c][3]);
+              *reinterpret_cast<float4*>(d + 4) = make_float4(f1[c][4], f1[c][5], f1[c][6], f1[c][7]);
+            } else {
+#pragma unroll
+              for (int ch = 0; ch < 8; ++ch)
+                if (ch < nch) d[ch] = f1[c][ch];
+            }
+          }
+        }
+      }
+      if (fail) break;
+      if (EPI == TC_LAST && rok)
+        ep.e_atom[ep.idx ? ep.idx[row] : row] = (double)(e_acc + ep.bout);
+      if (EPI == TC_DT && rok) {
+        // second factor (x < 16): complete over all N tiles of the row tile;
+        // the first factor of b = x was written by this thread above
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int a = 0; a < 16; ++a) dtr[c * ep.Mw + a] += part[c][a];
+      }
+    }
+  }
+  if (tid == 0 && !mbar_wait(&fin, 0, nullptr)) *abort_flag = 1;
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  if (tid == 0 && *abort_flag && ep.err) atomicAdd(ep.err, 1);
+  if (warp == 2)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512));
+}
+
+int g_tc_sms = 0;
+
+// persistent launch of the K-short GEMMs; -2: the row tile's A does not fit
+template <int EPI, int PC>
+int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
+              const __nv_bfloat16* B, const TcEpi& ep) {
+  if (M <= 0) return 0;
+  if (K <= 0 || K % kBK || K / kBK > kPMaxK || N <= 0 || N % 16) return -1;
+  if (EPI != TC_DT && ep.ldo != N) return -1;
+  const size_t sm = PCfg<PC>::smem(K / kBK);
+  if (sm > 225 * 1024) return -2;
+  static size_t set = 0;
+  if (sm > set) {
+    if (cudaFuncSetAttribute(k_tc_gemm_p<EPI, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm) != cudaSuccess)
+      return -3;
+    set = sm;
+  }
+  if (!g_tc_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_tc_sms <= 0) g_tc_sms = 1;
+  }
+  const int mtiles = (M + kBM - 1) / kBM;
+  DP_LAUNCHED(1);
+  k_tc_gemm_p<EPI, PC><<<mtiles < g_tc_sms ? mtiles : g_tc_sms, kTcThreads, sm, st>>>(M, N, K, A,
+                                                                                    B, ep);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 // the caller's layouts: A pre-tiled in 128-row tiles, B in tiles of 256 rows
 // (the last one ragged), N % 16 == 0, K % 16 == 0
 template <int EPI, int PC>
@@ -505,6 +873,18 @@ int launch_tile_operand(cudaStream_t st, int N, int K, int pieces, const float* 
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
+// the K-short layers: persistent kernel when the row tile's A fits in shared
+// memory, the tiled kernel otherwise; *fused_dt tells whether the dE/dD GEMM
+// completed dE/dT itself (no partials to reduce)
+template <int EPI, int PC>
+static int gemm_k_short(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
+                        const __nv_bfloat16* B, const TcEpi& ep, bool* persistent) {
+  const int rc = tc_gemm_p<EPI, PC>(st, M, N, K, A, B, ep);
+  if (persistent) *persistent = rc == 0;
+  if (rc != -2) return rc;
+  return tc_gemm<EPI, PC>(st, M, N, K, A, B, ep);
+}
+
 template <int PC>
 static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const FitNetTC& net, int M,
                        int m_lt, const float* T, float* dT, double* e_atom, const FitScratchTC& s,
@@ -551,14 +931,16 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
         ep.out_h = s.gph[0];
         ep.e_atom = e_atom + (idx ? 0 : r0);
         ep.idx = id;
-        rc = tc_gemm<TC_LAST, PC>(st, rows, net.wout[k], net.win[k], s.zh[k - 1], net.WTh[k], ep);
+        rc = gemm_k_short<TC_LAST, PC>(st, rows, net.wout[k], net.win[k], s.zh[k - 1], net.WTh[k],
+                                       ep, nullptr);
       } else {
         ep.R = net.shortcut[k] ? zb : nullptr;
         ep.ldr = net.wout[k - 1];
         ep.out_a = s.t[k];
         ep.out_b = s.z[k];
         ep.out_h = s.zh[k];
-        rc = tc_gemm<TC_MID, PC>(st, rows, net.wout[k], net.win[k], s.zh[k - 1], net.WTh[k], ep);
+        rc = gemm_k_short<TC_MID, PC>(st, rows, net.wout[k], net.win[k], s.zh[k - 1], net.WTh[k],
+                                      ep, nullptr);
       }
       if (rc) return rc;
     }
@@ -577,15 +959,18 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.out_h = s.gph[gi ^ 1];
       ep.ldo = net.win[k];
       ep.err = err;
-      const int rc = tc_gemm<TC_BWD, PC>(st, rows, net.win[k], net.wout[k], s.gph[gi], net.Wh[k], ep);
+      const int rc = gemm_k_short<TC_BWD, PC>(st, rows, net.win[k], net.wout[k], s.gph[gi],
+                                              net.Wh[k], ep, nullptr);
       if (rc) return rc;
       gz_prev = s.gz;
       ldgz = net.win[k];
       gi ^= 1;
     }
+    bool dt_done = false;
     {
       // dE/dD = gp_0 W_0^T never leaves the chip: the epilogue contracts it
-      // with T into dE/dT and leaves per-N-tile partials of the x < 16 term
+      // with T into dE/dT (the tiled kernel leaves per-N-tile partials of the
+      // x < 16 term, the persistent one completes it in registers)
       TcEpi ep{};
       ep.ldo = din;
       ep.err = err;
@@ -595,9 +980,11 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.Mw = M;
       ep.part = s.part;
       ep.part_ps = R * 64;
-      const int rc = tc_gemm<TC_DT, PC>(st, rows, din, net.wout[0], s.gph[gi], net.Wh[0], ep);
+      const int rc = gemm_k_short<TC_DT, PC>(st, rows, din, net.wout[0], s.gph[gi], net.Wh[0], ep,
+                                             &dt_done);
       if (rc) return rc;
     }
+    if (dt_done) continue;
     const int slots = (din + 255) / 256;
     DP_LAUNCHED(1);
     k_dt_reduce<<<(int)((rows * 64 + 255) / 256), 256, 0, st>>>(rows, id, M, slots, R * 64, s.part,
