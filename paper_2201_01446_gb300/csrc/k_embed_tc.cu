@@ -378,27 +378,43 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int kc = 0; kc < nk; ++kc, ++i) {
           const int s = i % kNS;
           const uint32_t u = i / kNS;
+          // C of the two bins, computed before the wait for the stage: the
+          // pairs of both bins are one contiguous sorted range, loaded four at
+          // a time (independent loads in flight), each added to its bin's half
+          const int b0 = kb0 + 2 * kc;
+          const int kbeg = bin_begin(hist, min(b0, nbins));
+          const int kmid = b0 < nbins ? hist[b0] : kbeg;
+          const int kend = b0 + 1 < nbins ? hist[b0 + 1] : kmid;
+          float x[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) x[q] = 0.0f;
+          for (int k = kbeg; k < kend; k += 4) {
+            float rv[4], uv[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const bool ok = k + t < kend;
+              rv[t] = ok ? Rc[k + t] : 0.0f;
+              uv[t] = ok ? Us[k + t] : 0.0f;
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const float uu = uv[t], u2 = uu * uu;
+              const float ra = k + t < kmid ? rv[t] : 0.0f;  // first bin
+              const float rb = rv[t] - ra;                   // second bin (or padding 0)
+              const float pw[6] = {1.0f, uu, u2, u2 * uu, u2 * u2, u2 * u2 * uu};
+#pragma unroll
+              for (int q = 0; q < 6; ++q) {
+                x[q] = fmaf(ra, pw[q], x[q]);
+                x[8 + q] = fmaf(rb, pw[q], x[8 + q]);
+              }
+            }
+          }
           if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
           unsigned char* sa = base + (size_t)s * cf.stage;
 #pragma unroll
           for (int hb = 0; hb < 2; ++hb) {
-            const int bin = kb0 + 2 * kc + hb;
-            float x[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (bin < nbins) {
-              const int e = hist[bin];
-              for (int k = bin_begin(hist, bin); k < e; ++k) {
-                const float rv = Rc[k], uu = Us[k];
-                const float u2 = uu * uu;
-                x[0] += rv;
-                x[1] = fmaf(rv, uu, x[1]);
-                x[2] = fmaf(rv, u2, x[2]);
-                x[3] = fmaf(rv, u2 * uu, x[3]);
-                x[4] = fmaf(rv, u2 * u2, x[4]);
-                x[5] = fmaf(rv, u2 * u2 * uu, x[5]);
-              }
-            }
             __align__(16) __nv_bfloat16 pv[3][8];
-            split8<kPC>(x, pv);
+            split8<kPC>(x + 8 * hb, pv);
             const int o = (r >> 3) * 256 + hb * 128 + (r & 7) * 16;
 #pragma unroll
             for (int p = 0; p < kPC; ++p)
