@@ -120,13 +120,19 @@ struct FwdCfg {
   size_t smem;    // dynamic shared memory
 };
 
+// N_m + 32 rounded to 32: the most pairs within rc an atom may have
+__host__ __device__ inline int scap_of(const EnvParams& ep) {
+  return ((int)(1.0f / ep.inv_nm + 0.5f) + 32 + 31) / 32 * 32;
+}
+
 __host__ __device__ inline FwdCfg fwd_cfg(const EnvParams& ep) {
   FwdCfg c;
   c.NP = round16(ep.M);
   c.bstage = kPC * c.NP * 32;
   c.stage = kPC * kABytes + c.bstage;
   c.nbp = round4(ep.ntypes * ep.n_int);
-  c.smem = 128 + (size_t)kNS * c.stage + (size_t)kAtoms * c.nbp * 4;
+  c.smem = 128 + (size_t)kNS * c.stage + (size_t)kAtoms * c.nbp * 4 +
+           (size_t)(kThreads / 32) * scap_of(ep) * 4;
   return c;
 }
 
@@ -143,15 +149,17 @@ __device__ __forceinline__ int tile_atom(const TileMap& tm, int ti, int64_t tile
 }
 
 // Phase 1 for one atom (one warp): histogram of the pairs within rc by bin =
-// (neighbor type, interval), exclusive scan, stable scatter of (R, u) in bin
-// order into the scratch rows of tile slot al.  On return hist holds the end
+// (neighbor type, interval) with a compact key list (bin << 16 | list index,
+// list order) in the warp's shared memory, exclusive scan, then over the keys
+// only a stable scatter of (R, u) in bin order into the scratch rows of tile
+// slot al.  On return hist holds the end
 // of every bin (all zero when the atom has no slot: padding or overflow).
 // Returns the pairs within rc; lo/hi the occupied bin range of this atom.
 __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ off,
                                          const uint32_t* __restrict__ nlist,
                                          const int32_t* __restrict__ nn, int cap,
                                          const CellGeom& g, const EnvParams& ep, int scap, int* hist,
-                                         int nbins, float* __restrict__ sc,
+                                         int nbins, float* __restrict__ sc, int* keys,
                                          float4* __restrict__ pout, int lane, int& nrange,
                                          int& nover, int& lo, int& hi) {
   for (int b = lane; b < nbins; b += 32) hist[b] = 0;
@@ -162,10 +170,12 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
   const float4 oi = off[atom];
   const int cnt = min(nn[atom], cap);
   const uint32_t* L = nlist + (size_t)atom * cap;
+  const unsigned below = (1u << lane) - 1u;
   int np = 0;
   for (int b0 = 0; b0 < cnt; b0 += 32) {
     const int k = b0 + lane;
     bool in = false;
+    int bin = 0;
     if (k < cnt) {
       float dx, dy, dz;
       int tj;
@@ -174,7 +184,7 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
       if (r2 < ep.rc2) {
         Pair P;
         pair_geom(ep, dx, dy, dz, r2, tj, P);
-        const int bin = tj * ep.n_int + P.th;
+        bin = tj * ep.n_int + P.th;
         atomicAdd(&hist[bin], 1);
         nrange += P.out_of_range;
         lo = min(lo, bin);
@@ -182,7 +192,10 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
         in = true;
       }
     }
-    np += __popc(__ballot_sync(0xffffffffu, in));
+    const unsigned bal = __ballot_sync(0xffffffffu, in);
+    const int q = np + __popc(bal & below);
+    if (in && q < scap) keys[q] = (bin << 16) | k;
+    np += __popc(bal);
   }
   __syncwarp();
   if (np > scap) {
@@ -195,21 +208,18 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
     return np;
   }
   warp_exclusive_scan(hist, nbins, lane);
-  for (int b0 = 0; b0 < cnt; b0 += 32) {
-    const int k = b0 + lane;
-    bool in = false;
+  for (int b0 = 0; b0 < np; b0 += 32) {
+    const int kk = b0 + lane;
+    const bool in = kk < np;
+    const int key = in ? keys[kk] : 0;
+    const int bin = key >> 16, k = key & 0xffff;
     Pair P;
-    int bin = 0;
-    if (k < cnt) {
+    if (in) {
       float dx, dy, dz;
       int tj;
       load_pair(oi, off, g, L[k], dx, dy, dz, tj);
       const float r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < ep.rc2) {
-        pair_geom(ep, dx, dy, dz, r2, tj, P);
-        bin = tj * ep.n_int + P.th;
-        in = true;
-      }
+      pair_geom(ep, dx, dy, dz, r2, tj, P);
     }
     const int pos = sorted_slot(hist, in, bin, lane);
     if (in) {
@@ -239,6 +249,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   int* shist = (int*)(base + (size_t)kNS * cf.stage);
+  int* skeys = shist + kAtoms * cf.nbp;  // [8 warps][scap] pair keys
   __shared__ __align__(8) uint64_t s_full[kNS], s_empty[kNS], s_gen[kNS], s_acc;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort, s_lo, s_hi;
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (lane == 0) s_atom[al] = atom;
       int lo, hi;
       const int np = sort_atom(atom, off, nlist, nn, cap, g, ep, scap, shist + al * cf.nbp,
-                               nbins, sc_cta + (size_t)al * scap,
+                               nbins, sc_cta + (size_t)al * scap, skeys + warp * scap,
                                pairs_out + ((size_t)tile * kAtoms + al) * scap, lane, nrange,
                                nover, lo, hi);
       npairs += (unsigned long long)np;
@@ -822,9 +833,7 @@ int sm_count() {
   return g_sms;
 }
 
-int stage_cap_tc(const EnvParams& ep) {
-  return ((int)(1.0f / ep.inv_nm + 0.5f) + 32 + 31) / 32 * 32;
-}
+int stage_cap_tc(const EnvParams& ep) { return scap_of(ep); }
 
 int tc_grid() { return 2 * sm_count(); }
 
@@ -860,6 +869,7 @@ int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, con
   if (ep.M > 128 || ep.M % 4 || ep.M < 16) return -1;
   if (tm.ntypes < 1 || tm.ntypes > DP_MAXT || tm.ntypes != ep.ntypes) return -1;
   if (((uintptr_t)tabF & 15) || ((uintptr_t)T & 15)) return -1;
+  if (cap > 65535) return -1;  // pair keys hold the list index in 16 bits
   const int64_t ntile = tm.tile_off[tm.ntypes];
   if (ntile <= 0) return 0;
   const FwdCfg cf = fwd_cfg(ep);
