@@ -400,7 +400,7 @@ dp_status set_types(dp_handle* h, Work& w, const int32_t* types_user_host) {
     const int64_t ntile = w.tiles.tile_off[h->ntypes];
     CK(ensure(w.tc_pairs, (size_t)std::max<int64_t>(tab_tc_pair_elems(ep, ntile), 1) * 16),
        "alloc sorted pairs");
-    CK(ensure(w.tc_hist, (size_t)std::max<int64_t>(tab_tc_hist_elems(ep, ntile), 4) * 4),
+    CK(ensure(w.tc_hist, (size_t)std::max<int64_t>(tab_tc_hist_elems(ep, ntile), 8) * 2),
        "alloc bin ends");
     CK(ensure(w.tc_range, (size_t)std::max<int64_t>(ntile, 1) * 8), "alloc bin ranges");
   }
@@ -560,7 +560,7 @@ dp_status embed_forward(dp_handle* h, Work& w, const EnvParams& ep) {
   if (h->opt.tabulated && h->opt.embed_precision == 2) {
     if (launch_tab_fwd_tc(h->st, w.tiles, P<float4>(w.off), P<uint32_t>(w.nlist),
                           P<int32_t>(w.nn), w.cap, w.geom, ep, P<__nv_bfloat16>(h->tabF),
-                          P<float>(h->tc_scratch), P<float4>(w.tc_pairs), P<int>(w.tc_hist),
+                          P<float>(h->tc_scratch), P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist),
                           P<int2>(w.tc_range), P<float>(w.T), P<int32_t>(h->status),
                           P<unsigned long long>(w.pairs)))
       return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core embedding cannot run this model shape");
@@ -604,7 +604,7 @@ dp_status evaluate(dp_handle* h, Work& w) {
   {
     Phase ph(h, 3);
     if (h->opt.tabulated && h->opt.embed_precision == 2) {
-      if (launch_tab_bwd_tc(h->st, w.tiles, P<float4>(w.tc_pairs), P<int>(w.tc_hist),
+      if (launch_tab_bwd_tc(h->st, w.tiles, P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist),
                             P<int2>(w.tc_range), ep, P<__nv_bfloat16>(h->tabB), P<float>(w.dT),
                             P<unsigned long long>(w.ffix), P<double>(w.vir_part),
                             (int)tab_tc_slots(), P<int32_t>(h->status)))
@@ -908,6 +908,13 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
   }
   if (h->opt.tabulated && h->opt.embed_precision == 2) {
     const EnvParams ep = env_params(h);
+    const int sup = tab_tc_supported(ep);
+    if (sup) {
+      h->err = sup == -1 ? "tensor-core embedding needs M <= 128, M % 4 == 0"
+                         : "tensor-core embedding: ntypes x table intervals too large for the "
+                           "shared-memory histograms (lower s_max or raise table_step)";
+      return bail(DP_ERR_UNIMPLEMENTED);
+    }
     const size_t nt = (size_t)tab_tc_elems(ep) * sizeof(__nv_bfloat16);
     if (ensure(h->tabF, nt) != cudaSuccess || ensure(h->tabB, nt) != cudaSuccess ||
         ensure(h->tc_scratch, (size_t)tab_tc_scratch_floats(ep) * sizeof(float)) != cudaSuccess) {

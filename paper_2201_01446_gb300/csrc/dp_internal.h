@@ -104,17 +104,21 @@ int tab_tc_build(cudaStream_t st, const float* table, const EnvParams& ep, __nv_
                  __nv_bfloat16* tabB);
 int64_t tab_tc_scratch_floats(const EnvParams& ep);  // scratch one launch needs
 // the forward leaves, per tile, the sorted pairs (dx, dy, dz, neighbor index)
-// [tile][32][N_m + 32 rounded], the bin ends [tile][32][bins rounded to 4] and
+// [tile][32][N_m + 32 rounded], the bin ends (uint16) [tile][32][bins rounded
+// to 8] and
 // (first bin, chunks of two bins); the backward reads them
 int64_t tab_tc_pair_elems(const EnvParams& ep, int64_t ntile);
 int64_t tab_tc_hist_elems(const EnvParams& ep, int64_t ntile);
 int64_t tab_tc_slots();  // virial partial slots the backward writes
+// 0 if the tensor-core embedding can run this shape; -1 embedding width (M <=
+// 128, M % 4 == 0), -2 too many table bins for the shared-memory histograms
+int tab_tc_supported(const EnvParams& ep);
 int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, const uint32_t* nlist,
                       const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
                       const __nv_bfloat16* tabF, float* scratch, float4* pairs_out,
-                      int* hist_out, int2* range_out, float* T, int32_t* status,
+                      uint16_t* hist_out, int2* range_out, float* T, int32_t* status,
                       unsigned long long* pair_count);
-int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs, const int* hist,
+int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs, const uint16_t* hist,
                       const int2* range, const EnvParams& ep, const __nv_bfloat16* tabB,
                       const float* dT, unsigned long long* ffix, double* vir_part, int vir_slots,
                       int32_t* status);

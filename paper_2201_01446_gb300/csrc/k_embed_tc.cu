@@ -116,7 +116,7 @@ struct FwdCfg {
   int NP;         // M rounded up to 16: MMA N
   int bstage;     // bytes of the B part of a stage (all pieces)
   int stage;      // bytes per stage
-  int nbp;        // hist ints per atom
+  int nbp;        // bin ends per atom (uint16, rounded to 8)
   size_t smem;    // dynamic shared memory
 };
 
@@ -130,10 +130,19 @@ __host__ __device__ inline FwdCfg fwd_cfg(const EnvParams& ep) {
   c.NP = round16(ep.M);
   c.bstage = kPC * c.NP * 32;
   c.stage = kPC * kABytes + c.bstage;
-  c.nbp = round4(ep.ntypes * ep.n_int);
-  c.smem = 128 + (size_t)kNS * c.stage + (size_t)kAtoms * c.nbp * 4 +
-           (size_t)(kThreads / 32) * scap_of(ep) * 4;
+  c.nbp = (ep.ntypes * ep.n_int + 7) & ~7;
+  c.smem = 128 + (size_t)kNS * c.stage + (size_t)kAtoms * c.nbp * 2;
   return c;
+}
+
+// phase 1's per-warp scratch (int histogram, pair keys) lives in the stage
+// memory, idle between the previous tile's epilogue and this tile's MMAs
+__host__ __device__ inline int warp_scratch_words(const EnvParams& ep) {
+  return round4(ep.ntypes * ep.n_int) + scap_of(ep);
+}
+
+__device__ __forceinline__ int bin_begin16(const uint16_t* hist, int b) {
+  return b ? hist[b - 1] : 0;
 }
 
 __device__ __forceinline__ int tile_type(const TileMap& tm, int64_t tile) {
@@ -243,13 +252,15 @@ __global__ void __launch_bounds__(kThreads, 2)
                  const uint32_t* __restrict__ nlist, const int32_t* __restrict__ nn, int cap,
                  CellGeom g, EnvParams ep, const __nv_bfloat16* __restrict__ tabF, int scap,
                  float* __restrict__ scratch, float4* __restrict__ pairs_out,
-                 int* __restrict__ hist_out, int2* __restrict__ range_out, float* __restrict__ T,
+                 uint16_t* __restrict__ hist_out, int2* __restrict__ range_out,
+                 float* __restrict__ T,
                  int32_t* __restrict__ status, unsigned long long* __restrict__ pair_count) {
   const FwdCfg cf = fwd_cfg(ep);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  int* shist = (int*)(base + (size_t)kNS * cf.stage);
-  int* skeys = shist + kAtoms * cf.nbp;  // [8 warps][scap] pair keys
+  uint16_t* shist = (uint16_t*)(base + (size_t)kNS * cf.stage);  // [32 atoms][nbp] bin ends
+  int* whist = (int*)base + (size_t)(threadIdx.x >> 5) * warp_scratch_words(ep);
+  int* wkeys = whist + round4(ep.ntypes * ep.n_int);
   __shared__ __align__(8) uint64_t s_full[kNS], s_empty[kNS], s_gen[kNS], s_acc;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort, s_lo, s_hi;
@@ -294,6 +305,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       s_lo = INT_MAX;
       s_hi = -1;
     }
+    // the stage memory turns from the async proxy's (copies, MMAs) to phase 1's
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     // ---- phase 1: four atoms per warp
     for (int j = 0; j < kAtoms / 8; ++j) {
@@ -301,10 +314,13 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int atom = tile_atom(tm, ti, tile, al);
       if (lane == 0) s_atom[al] = atom;
       int lo, hi;
-      const int np = sort_atom(atom, off, nlist, nn, cap, g, ep, scap, shist + al * cf.nbp,
-                               nbins, sc_cta + (size_t)al * scap, skeys + warp * scap,
+      const int np = sort_atom(atom, off, nlist, nn, cap, g, ep, scap, whist, nbins,
+                               sc_cta + (size_t)al * scap, wkeys,
                                pairs_out + ((size_t)tile * kAtoms + al) * scap, lane, nrange,
                                nover, lo, hi);
+      // bin ends of this atom (<= N_m + 32 < 2^16)
+      for (int b = lane; b < cf.nbp; b += 32)
+        shist[al * cf.nbp + b] = (uint16_t)(b < nbins ? whist[b] : 0);
       npairs += (unsigned long long)np;
       lo = __reduce_min_sync(0xffffffffu, lo);
       hi = __reduce_max_sync(0xffffffffu, hi);
@@ -313,6 +329,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         atomicMax(&s_hi, hi);
       }
     }
+    // the stage memory goes back to the async proxy (this tile's copies)
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     const int kb0 = s_hi >= 0 ? (s_lo & ~1) : 0;
     const int nk = s_hi >= 0 ? (s_hi - kb0) / 2 + 1 : 0;  // chunks of two bins
@@ -320,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     {
       int4* ho = reinterpret_cast<int4*>(hist_out + (size_t)tile * kAtoms * cf.nbp);
       const int4* hs = reinterpret_cast<const int4*>(shist);
-      for (int q = tid; q < kAtoms * cf.nbp / 4; q += kThreads) ho[q] = hs[q];
+      for (int q = tid; q < kAtoms * cf.nbp / 8; q += kThreads) ho[q] = hs[q];
       if (tid == 0) range_out[tile] = make_int2(kb0, nk);
     }
     // ---- phase 2: T rows of the tile = C . table over the occupied bins
@@ -381,7 +399,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       } else if (warp >= 4) {
         // C rows: thread r = (atom al, component c), two bins per chunk
         const int r = tid - 128, al = r >> 2, c = r & 3;
-        const int* hist = shist + al * cf.nbp;
+        const uint16_t* hist = shist + al * cf.nbp;
         const size_t st = (size_t)kAtoms * scap;
         const float* Rc = sc_cta + (size_t)c * st + (size_t)al * scap;
         const float* Us = sc_cta + 4 * st + (size_t)al * scap;
@@ -393,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           // pairs of both bins are one contiguous sorted range, loaded four at
           // a time (independent loads in flight), each added to its bin's half
           const int b0 = kb0 + 2 * kc;
-          const int kbeg = bin_begin(hist, min(b0, nbins));
+          const int kbeg = bin_begin16(hist, min(b0, nbins));
           const int kmid = b0 < nbins ? hist[b0] : kbeg;
           const int kend = b0 + 1 < nbins ? hist[b0 + 1] : kmid;
           float x[16];
@@ -507,18 +525,19 @@ struct BwdCfg {
 __host__ __device__ inline BwdCfg bwd_cfg(const EnvParams& ep) {
   BwdCfg c;
   c.NP = round16(ep.M);
-  c.nbp = round4(ep.ntypes * ep.n_int);
+  c.nbp = (ep.ntypes * ep.n_int + 7) & ~7;
   c.stage = kPC * kABytes + kPC * kWin * 8 * 32;
   size_t st = (size_t)kNS * c.stage;
   const size_t bsm = (size_t)kAtoms * kBsmAtom * 4;
   if (st < bsm) st = bsm;
-  c.smem = 128 + st + (size_t)kAtoms * c.nbp * 4;
+  c.smem = 128 + st + (size_t)kAtoms * c.nbp * 2;
   return c;
 }
 
 __global__ void __launch_bounds__(kThreads, 2)
     k_tab_bwd_tc(int64_t ntile, TileMap tm, const float4* __restrict__ pairs,
-                 const int* __restrict__ hist_in, const int2* __restrict__ range_in, EnvParams ep,
+                 const uint16_t* __restrict__ hist_in, const int2* __restrict__ range_in,
+                 EnvParams ep,
                  const __nv_bfloat16* __restrict__ tabB, int scap, const float* __restrict__ dT,
                  unsigned long long* __restrict__ ffix, double* __restrict__ vir_part,
                  int32_t* __restrict__ status) {
@@ -527,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   size_t st_bytes = (size_t)kNS * cf.stage;
   if (st_bytes < (size_t)kAtoms * kBsmAtom * 4) st_bytes = (size_t)kAtoms * kBsmAtom * 4;
-  int* shist = (int*)(base + st_bytes);
+  uint16_t* shist = (uint16_t*)(base + st_bytes);
   float* Bsm = (float*)base;  // aliases the stages between the MMAs of two windows
   __shared__ __align__(8) uint64_t s_full[kNS], s_empty[kNS], s_gen[kNS], s_acc;
   __shared__ uint32_t s_tmem;
@@ -572,7 +591,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     {
       const int4* hi4 = reinterpret_cast<const int4*>(hist_in + (size_t)tile * kAtoms * cf.nbp);
       int4* hs = reinterpret_cast<int4*>(shist);
-      for (int q = tid; q < kAtoms * cf.nbp / 4; q += kThreads) hs[q] = hi4[q];
+      for (int q = tid; q < kAtoms * cf.nbp / 8; q += kThreads) hs[q] = hi4[q];
       if (tid < kAtoms) s_atom[tid] = tile_atom(tm, ti, tile, tid);
     }
     const int2 rg = range_in[tile];
@@ -711,8 +730,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int j = 0; j < kAtoms / 8; ++j) {
         const int al = warp * (kAtoms / 8) + j;
         if (s_atom[al] < 0) continue;
-        const int* hist = shist + al * cf.nbp;
-        const int kbeg = bin_begin(hist, w0), kend = hist[wend - 1];
+        const uint16_t* hist = shist + al * cf.nbp;
+        const int kbeg = bin_begin16(hist, w0), kend = hist[wend - 1];
         const float4* pr = pairs + ((size_t)tile * kAtoms + al) * scap;
         for (int k = kbeg + lane; k < kend; k += 32) {
           // the pair's bin: the one whose sorted range holds k
@@ -864,12 +883,13 @@ int64_t tab_tc_scratch_floats(const EnvParams& ep) {
 int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, const uint32_t* nlist,
                       const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
                       const __nv_bfloat16* tabF, float* scratch, float4* pairs_out,
-                      int* hist_out, int2* range_out, float* T, int32_t* status,
+                      uint16_t* hist_out, int2* range_out, float* T, int32_t* status,
                       unsigned long long* pair_count) {
   if (ep.M > 128 || ep.M % 4 || ep.M < 16) return -1;
   if (tm.ntypes < 1 || tm.ntypes > DP_MAXT || tm.ntypes != ep.ntypes) return -1;
   if (((uintptr_t)tabF & 15) || ((uintptr_t)T & 15)) return -1;
   if (cap > 65535) return -1;  // pair keys hold the list index in 16 bits
+  if (tab_tc_supported(ep)) return -1;
   const int64_t ntile = tm.tile_off[tm.ntypes];
   if (ntile <= 0) return 0;
   const FwdCfg cf = fwd_cfg(ep);
@@ -891,7 +911,8 @@ int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, con
 
 int64_t tab_tc_slots() { return (int64_t)tc_grid() * (kThreads / 32); }
 
-int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs, const int* hist,
+int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs,
+                      const uint16_t* hist,
                       const int2* range, const EnvParams& ep, const __nv_bfloat16* tabB,
                       const float* dT, unsigned long long* ffix, double* vir_part, int vir_slots,
                       int32_t* status) {
@@ -921,5 +942,13 @@ int64_t tab_tc_pair_elems(const EnvParams& ep, int64_t ntile) {
   return ntile * kAtoms * stage_cap_tc(ep);
 }
 int64_t tab_tc_hist_elems(const EnvParams& ep, int64_t ntile) {
-  return ntile * kAtoms * round4(ep.ntypes * ep.n_int);
+  return ntile * kAtoms * ((ep.ntypes * ep.n_int + 7) & ~7);
+}
+
+int tab_tc_supported(const EnvParams& ep) {
+  if (ep.M > 128 || ep.M % 4 || ep.M < 16) return -1;
+  if (fwd_cfg(ep).smem > 113 * 1024 || bwd_cfg(ep).smem > 113 * 1024) return -2;
+  if ((size_t)(kThreads / 32) * warp_scratch_words(ep) * 4 > (size_t)kNS * fwd_cfg(ep).stage)
+    return -2;
+  return 0;
 }

@@ -222,3 +222,67 @@ def random_subset(n: int, k: int, seed: int = 7):
     """k distinct atom indices out of n, sorted (seeded)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.sort(rng.choice(n, size=min(k, n), replace=False)).astype(np.int64)
+
+
+_WATER_BASE = {}
+
+
+def water_tiled(k: int, seed: int = 3):
+    """192*k-atom water-like box: the 64-molecule box of water_like tiled k
+    times (k a power of two up to 512, tiles as near a cube as possible)."""
+    if seed not in _WATER_BASE:
+        _WATER_BASE[seed] = water_like(64, seed=seed)
+    x0, t0, box0 = _WATER_BASE[seed]
+    L = box0[0, 0]
+    dims = [1, 1, 1]
+    kk, d = k, 0
+    while kk > 1:
+        dims[d % 3] *= 2
+        kk //= 2
+        d += 1
+    shifts = np.array([[i, j, l] for i in range(dims[0]) for j in range(dims[1])
+                       for l in range(dims[2])], np.float64) * L
+    x = (x0[None, :, :] + shifts[:, None, :]).reshape(-1, 3)
+    types = np.tile(t0, len(shifts))
+    box = np.diag([dims[0] * L, dims[1] * L, dims[2] * L]).astype(np.float64)
+    return np.ascontiguousarray(x), types.astype(np.int32), box
+
+
+def serve_requests(n: int, seed: int = 5, min_atoms: int = 500, max_atoms: int = 500000,
+                   p_md: float = 0.5, p_water: float = 0.5, md_steps: int = 50,
+                   water_md_steps: int = 10):
+    """Seeded request mix for the serving loop: copper boxes of log-uniform
+    size in [min_atoms, max_atoms] (FCC cells per edge rounded) and water-like
+    boxes of 192*k atoms (k log-uniform over powers of two 1..128), each an
+    energy/force evaluation or an MD run (md_steps steps for copper,
+    water_md_steps for water: the seeded water model has no bonding, so its H
+    atoms fly free and a longer run leaves the physical distance range), with
+    330 K Maxwell velocities.  Returns a list of dicts (model, kind, x, v, types, box,
+    masses, steps)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        water = rng.uniform() < p_water
+        kind = "md" if rng.uniform() < p_md else "eval"
+        if water:
+            k = 2 ** int(rng.integers(0, 8))
+            x, t, box = water_tiled(k, seed=3)
+            masses = [MASS_O, MASS_H]
+            m = np.where(t == 0, MASS_O, MASS_H)
+        else:
+            na = float(np.exp(rng.uniform(np.log(min_atoms), np.log(max_atoms))))
+            ncell = max(5, int(round((na / 4.0) ** (1.0 / 3.0))))
+            x, t, box = fcc_copper(ncell, sigma=0.05, seed=int(rng.integers(1 << 30)))
+            masses = [MASS_CU]
+            m = np.full(len(x), MASS_CU)
+        v = maxwell_velocities(m, 330.0, seed=int(rng.integers(1 << 30)))
+        steps = (water_md_steps if water else md_steps) if kind == "md" else 0
+        out.append(dict(model="water" if water else "cu", kind=kind, x=x, v=v, types=t, box=box,
+                        masses=masses, steps=steps))
+    return out
+
+
+def poisson_arrivals(n: int, rate: float, seed: int = 6):
+    """Arrival times (s) of a Poisson stream of n requests at `rate` per second."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))

@@ -1,0 +1,41 @@
+"""Serving loop on the GPU: a mixed request stream (copper and water boxes,
+evaluations and MD runs) through three concurrent slots gives, request by
+request, bitwise the results of the same request run alone on a fresh
+handle."""
+import numpy as np
+import pytest
+
+from paper_2201_01446_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_results_bitwise_alone_and_in_the_mix(cu_model_path, model_dir):
+    from paper_2201_01446_gb300 import dp, serve
+    wpath = str(model_dir / "water_serve.model")
+    inputs.write_seeded_model(wpath, inputs.WATER_SPEC, seed=4, std=0.1)
+
+    def opts(s_max):
+        o = dp.dp_options_default()
+        o.fit_precision = 2
+        o.embed_precision = 2
+        o.s_max = s_max
+        return o
+
+    models = {"cu": serve.ModelCfg(cu_model_path, 1, 8.0, 0.5, [256], opts(2.0)),
+              "water": serve.ModelCfg(wpath, 2, 6.0, 0.5, [46, 92], opts(2.0))}
+    specs = inputs.serve_requests(12, seed=9, max_atoms=20000, md_steps=12)
+    reqs = serve.make_requests(specs)
+    srv = serve.Server(models, slots=3)
+    st = srv.run(reqs, inputs.poisson_arrivals(len(reqs), 200.0, seed=2))
+    assert st["errors"] == 0, [r.error for r in reqs if r.error]
+    alone = serve._DpSlot(models)
+    try:
+        for r in serve.make_requests(specs):
+            ref = alone(r)
+            got = reqs[r.rid].result
+            for a, b in zip(got, ref):
+                assert np.array_equal(np.asarray(a), np.asarray(b)), (r.rid, r.model, r.kind)
+    finally:
+        alone.close()
+    assert st["p99_ms"] >= st["p50_ms"] > 0

@@ -1,0 +1,75 @@
+"""Host logic of the serving loop on CPU: FIFO admission under the device-
+memory budget, every request served once, latencies measured from arrival,
+with a stand-in executor that only sleeps (no GPU)."""
+import time
+
+import numpy as np
+
+from paper_2201_01446_gb300 import inputs, serve
+
+
+def _reqs(sizes, kinds):
+    out = []
+    for i, (n, k) in enumerate(zip(sizes, kinds)):
+        x = np.zeros((n, 3))
+        out.append(serve.Request(rid=i, model="cu", kind=k, x=x, v=x, types=np.zeros(n, np.int32),
+                                 box=np.eye(3), masses=[1.0], steps=50 if k == "md" else 0))
+    return out
+
+
+class _Sleep:
+    def __init__(self, log, slot):
+        self.log, self.slot = log, slot
+
+    def __call__(self, req):
+        self.log.append((req.rid, self.slot, time.perf_counter()))
+        time.sleep(0.002 + 1e-7 * req.atom_steps)
+        return ("ok", req.rid)
+
+
+def test_fifo_admission_under_budget():
+    models = {"cu": serve.ModelCfg("unused", 1, 8.0, 0.5, [256])}
+    rng = np.random.default_rng(0)
+    sizes = rng.integers(500, 50000, size=40)
+    reqs = _reqs(sizes, ["md" if i % 3 == 0 else "eval" for i in range(40)])
+    for r in reqs:
+        r.nbytes = int(len(r.x)) * 1000
+    budget = 120000 * 1000  # a few requests at a time
+    srv = serve.Server(models, slots=4, budget_bytes=budget)
+    log = []
+    arrivals = inputs.poisson_arrivals(len(reqs), rate=400.0, seed=1)
+    st = srv.run(reqs, arrivals, executor_factory=lambda s: _Sleep(log, s))
+    assert st["requests"] == 40 and st["errors"] == 0
+    assert sorted(r.rid for r in reqs if r.result) == list(range(40))
+    # admission is first come first served
+    started = [rid for rid, _, _ in sorted(log, key=lambda e: e[2])]
+    by_arrival = [r.rid for r in sorted(reqs, key=lambda r: r.arrival)]
+    assert started == by_arrival
+    assert srv.peak_in_use <= budget
+    for r in reqs:
+        assert r.t_start >= r.arrival - 1e-6 and r.t_done >= r.t_start
+    assert 0 < st["p50_ms"] <= st["p99_ms"]
+    assert st["atom_steps_per_s"] > 0
+
+
+def test_oversized_request_runs_alone():
+    models = {"cu": serve.ModelCfg("unused", 1, 8.0, 0.5, [256])}
+    reqs = _reqs([1000, 5000, 1000], ["eval", "eval", "eval"])
+    for r, b in zip(reqs, [10, 10_000, 10]):
+        r.nbytes = b
+    srv = serve.Server(models, slots=2, budget_bytes=100)
+    log = []
+    st = srv.run(reqs, np.zeros(3), executor_factory=lambda s: _Sleep(log, s))
+    assert st["errors"] == 0 and srv.peak_in_use == 10_000
+
+
+def test_request_mix_is_seeded():
+    a = inputs.serve_requests(6, seed=5)
+    b = inputs.serve_requests(6, seed=5)
+    for p, q in zip(a, b):
+        assert p["model"] == q["model"] and p["kind"] == q["kind"]
+        assert np.array_equal(p["x"], q["x"]) and np.array_equal(p["v"], q["v"])
+    for p in a:
+        assert 192 <= len(p["x"]) <= 500000
+    x, t, box = inputs.water_tiled(4)
+    assert len(x) == 768 and np.count_nonzero(t == 0) == 256
