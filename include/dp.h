@@ -66,6 +66,9 @@ typedef struct {
   int embed_precision; /* tabulated embedding contraction: 0 FP32 CUDA cores
                           [0], 2 FP32-accurate tcgen05 tensor cores (split
                           operands); the plain path ignores it */
+  int tanh_table;      /* fitting-net activation: 0 tanh [0]; 1 the tanh table
+                          of Sec. 3.5 (second order on [0, 8) in intervals of
+                          1/128, odd, 1 beyond 8; error < 2.3e-7) */
 } dp_options;
 
 /* Thermodynamic record of one MD step (Sec. 4). */

@@ -53,6 +53,8 @@ def lib():
             "orc_env_row": (d, [dp, d, d, dp, dp]),
             "orc_embed": (i, [p, i, i, d, dp, dp, dp]),
             "orc_fit": (i, [p, i, dp, dp, dp]),
+            "orc_set_tanh_table": (None, [i]),
+            "orc_act": (d, [d, dp]),
             "orc_table_build": (p, [p, d, d]),
             "orc_table_free": (None, [p]),
             "orc_table_dims": (i, [p, i32p, dp]),
@@ -98,6 +100,18 @@ class OracleError(RuntimeError):
     def __init__(self, code, what=""):
         super().__init__(f"oracle error {code} ({ERRORS.get(code, '?')}) {what}")
         self.code = code
+
+
+def set_tanh_table(on: bool) -> None:
+    """Fitting-net activation: exact tanh (default) or the Sec. 3.5 table."""
+    lib().orc_set_tanh_table(1 if on else 0)
+
+
+def act(a: float):
+    """(t, dt/da) of the fitting-net activation in the current mode."""
+    dt = C.c_double()
+    t = lib().orc_act(float(a), C.byref(dt))
+    return t, dt.value
 
 
 def set_threads(n: int) -> None:

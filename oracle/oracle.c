@@ -260,6 +260,55 @@ int orc_embed(const orc_model* m, int ti, int tj, double s, double* g, double* d
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 3.5: tanh of the fitting net tabulated on [0, 8) by a second-order    */
+/* polynomial per interval, odd symmetry, 1 for |x| >= 8.  Reading (the paper */
+/* fixes neither the step nor the conditions): step h = 1/128; on             */
+/* [x_k, x_k + h], p(u) = a0 + a1 u + a2 u^2 with p(0) = tanh(x_k),           */
+/* p'(0) = 1 - tanh(x_k)^2 and p(h) = tanh(x_k + h).  The derivative used in  */
+/* the gradient is p'(u), so forces stay the gradient of the computed energy. */
+/* ------------------------------------------------------------------------ */
+#define TT_N 1024
+#define TT_PER_UNIT 128.0
+static int g_tanh_table = 0;
+static int g_tt_ready = 0;
+static double g_tt[TT_N][3];
+
+void orc_set_tanh_table(int on) {
+  if (on && !g_tt_ready) {
+    const double h = 1.0 / TT_PER_UNIT;
+    for (int k = 0; k < TT_N; ++k) {
+      const double x0 = k * h;
+      const double y0 = tanh(x0), y1 = tanh(x0 + h);
+      g_tt[k][0] = y0;
+      g_tt[k][1] = 1.0 - y0 * y0;
+      g_tt[k][2] = (y1 - g_tt[k][0] - g_tt[k][1] * h) / (h * h);
+    }
+    g_tt_ready = 1;
+  }
+  g_tanh_table = on ? 1 : 0;
+}
+
+/* the fitting net's activation: t = tanh(a) (or its table), dt = dt/da */
+double orc_act(double a, double* dt) {
+  if (!g_tanh_table) {
+    const double t = tanh(a);
+    if (dt) *dt = 1.0 - t * t;
+    return t;
+  }
+  const double ax = fabs(a);
+  if (ax >= 8.0) {
+    if (dt) *dt = 0.0;
+    return a > 0 ? 1.0 : -1.0;
+  }
+  int k = (int)(ax * TT_PER_UNIT);
+  if (k > TT_N - 1) k = TT_N - 1;
+  const double u = ax - k / TT_PER_UNIT;
+  const double p = g_tt[k][0] + u * (g_tt[k][1] + u * g_tt[k][2]);
+  if (dt) *dt = g_tt[k][1] + 2.0 * g_tt[k][2] * u;
+  return a < 0 ? -p : p;
+}
+
+/* ------------------------------------------------------------------------ */
 /* fitting net (Sec. 2.1): hidden layers tanh, shortcut on equal widths       */
 /* ------------------------------------------------------------------------ */
 int orc_fit(const orc_model* m, int ti, const double* D, double* E, double* dD) {
@@ -269,7 +318,7 @@ int orc_fit(const orc_model* m, int ti, const double* D, double* E, double* dD) 
   for (int k = 0; k < nf; ++k) tot += (size_t)m->fit_w[k];
   double* z = (double*)malloc(sizeof(double) * (2 * tot + 2 * (size_t)m->din + 16));
   if (!z) return ORC_ERR_NOMEM;
-  double* tk = z + tot; /* tanh outputs per layer */
+  double* tk = z + tot; /* activation derivatives per layer */
   size_t off[MAXL + 1];
   off[0] = 0;
   for (int k = 0; k < nf; ++k) off[k + 1] = off[k] + (size_t)m->fit_w[k];
@@ -283,8 +332,9 @@ int orc_fit(const orc_model* m, int ti, const double* D, double* E, double* dD) 
     for (int c = 0; c < wo; ++c) {
       double a = b[c];
       for (int r = 0; r < win; ++r) a += in[r] * W[(size_t)r * wo + c];
-      double t = tanh(a);
-      tk[off[k] + c] = t;
+      double dt;
+      const double t = orc_act(a, &dt);
+      tk[off[k] + c] = dt;
       z[off[k] + c] = (shortcut ? in[c] : 0.0) + t;
     }
     in = z + off[k];
@@ -304,8 +354,7 @@ int orc_fit(const orc_model* m, int ti, const double* D, double* E, double* dD) 
       const double* W = m->fit_W[ti][k];
       for (int r = 0; r < wi; ++r) gn[r] = 0.0;
       for (int c = 0; c < wo; ++c) {
-        double t = tk[off[k] + c];
-        double gp = gz[c] * (1.0 - t * t); /* through tanh */
+        double gp = gz[c] * tk[off[k] + c]; /* through the activation */
         for (int r = 0; r < wi; ++r) gn[r] += W[(size_t)r * wo + c] * gp;
         if (shortcut) gn[c] += gz[c];
       }

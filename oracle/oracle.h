@@ -60,6 +60,12 @@ double orc_env_row(const double* d, double rc, double rcs, double* R, double* dR
  * second derivative in s (forward-mode).  dg / d2g may be NULL. */
 int orc_embed(const orc_model* m, int ti, int tj, double s, double* g, double* dg, double* d2g);
 
+/* Sec. 3.5 tanh table for the fitting net (off by default): second order on
+ * [0, 8) with step 1/128, odd, 1 beyond 8; orc_act is the activation the
+ * fitting net uses (dt: its derivative) */
+void orc_set_tanh_table(int on);
+double orc_act(double a, double* dt);
+
 /* fitting net of centre type ti: E(D); dD (length din) = dE/dD if not NULL */
 int orc_fit(const orc_model* m, int ti, const double* D, double* E, double* dD);
 

@@ -98,6 +98,7 @@ struct dp_handle {
   int fit_w[DP_MAXFIT] = {0};
   DevBuf emb64, emb_off, table, fit32, sel_dev, map_dev, status;
   DevBuf tabF, tabB, tc_scratch;  // tensor-core embedding: tiled table pieces, per-CTA scratch
+  DevBuf tanh_tab;                // Sec. 3.5 tanh table of the fitting net (tanh_table = 1)
   int n_int = 0;
   double h = 0.0;
   FitNet nets[DP_MAXT];
@@ -678,6 +679,7 @@ void dp_options_default(dp_options* o) {
   o->skin = 2.0;
   o->rebuild_every = 10;
   o->embed_precision = 0;
+  o->tanh_table = 0;
 }
 
 const char* dp_version(void) { return "dp-gb300 0.1 (sm_103a; tabulated FP32 embedding, FP32 SIMT fitting)"; }
@@ -713,7 +715,8 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
       h->opt.rebuild_every < 1)
     return bail(DP_ERR_ARG);
   if (h->opt.tabulated < 0 || h->opt.tabulated > 1 || h->opt.fit_precision < 0 ||
-      h->opt.fit_precision > 2 || (h->opt.embed_precision != 0 && h->opt.embed_precision != 2))
+      h->opt.fit_precision > 2 || (h->opt.embed_precision != 0 && h->opt.embed_precision != 2) ||
+      h->opt.tanh_table < 0 || h->opt.tanh_table > 1)
     return bail(DP_ERR_UNIMPLEMENTED);
   HostModel m;
   std::string why;
@@ -792,6 +795,22 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
     while (fit.size() % 4) fit.push_back(0.0f);
   }
   ok = ok && up(h->fit32, fit.data(), sizeof(float) * fit.size());
+  if (h->opt.tanh_table) {
+    // Sec. 3.5: on [x_k, x_k + h], h = 1/128, p(u) = a0 + a1 u + a2 u^2 with
+    // p(0) = tanh(x_k), p'(0) = 1 - tanh(x_k)^2, p(h) = tanh(x_k + h); FP64
+    // coefficients rounded to FP32
+    std::vector<float> tt(4 * 1024);
+    const double hh = 1.0 / 128.0;
+    for (int k = 0; k < 1024; ++k) {
+      const double y0 = std::tanh(k * hh), y1 = std::tanh((k + 1) * hh);
+      const double a1 = 1.0 - y0 * y0;
+      tt[4 * k] = (float)y0;
+      tt[4 * k + 1] = (float)a1;
+      tt[4 * k + 2] = (float)((y1 - y0 - a1 * hh) / (hh * hh));
+      tt[4 * k + 3] = 0.0f;
+    }
+    ok = ok && up(h->tanh_tab, tt.data(), sizeof(float) * tt.size());
+  }
   if (!ok) {
     h->err = "device allocation or upload failed";
     cudaGetLastError();
@@ -813,6 +832,7 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
     }
     net.w_out = fb + ofs[t].wout;
     net.b_out = h->b_out[t];
+    net.tanh_tab = h->opt.tanh_table ? P<float4>(h->tanh_tab) : nullptr;
   }
   // BF16 pieces (h, m, l) of the fitting weights for the tensor-core modes
   if (ensure(h->fit_bf16, sizeof(__nv_bfloat16) * 3 * fit.size()) != cudaSuccess) {
@@ -845,6 +865,7 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
       }
       nt.w_out = nf.w_out;
       nt.b_out = nf.b_out;
+      nt.tanh_tab = nf.tanh_tab;
     }
   }
   // FP32 embedding weights (and transposes) for the plain untabulated path

@@ -147,12 +147,13 @@ struct FitNet {           // one centre type, FP32 device pointers
   const float* b[DP_MAXFIT];
   const float* w_out;          // [wout[nl-1]]
   float b_out;
+  const float4* tanh_tab;      // Sec. 3.5 tanh table [1024] (a0, a1, a2, 0), or NULL
 };
 struct FitScratch {
   int64_t rows;  // capacity in atoms
   float* D;      // [rows][din]
   float* dD;     // [rows][din]
-  float* t[DP_MAXFIT];
+  float* t[DP_MAXFIT];  // activation derivatives (for the backward)
   float* z[DP_MAXFIT];
   float* gz;     // [rows][wmax]
   float* gp;     // [rows][wmax]
@@ -177,12 +178,13 @@ struct FitNetTC {
   const float* b[DP_MAXFIT];
   const float* w_out;
   float b_out;
+  const float4* tanh_tab;  // Sec. 3.5 tanh table, or NULL
 };
 struct FitScratchTC {
   int64_t rows;                  // rows per chunk (a multiple of 128)
   int wmax;
   float* part;                   // [din/256][rows][64] partials of dE/dT (x < 16)
-  float* t[DP_MAXFIT];           // [rows][wout[k]] tanh outputs
+  float* t[DP_MAXFIT];           // [rows][wout[k]] activation derivatives
   float* z[DP_MAXFIT];           // [rows][wout[k]] layer outputs (k >= 1)
   __nv_bfloat16* zh[DP_MAXFIT];  // tiled pieces of the layer outputs (next A operand)
   float* gz;                     // [rows][wmax]

@@ -12,6 +12,7 @@
 //   dT[c][x] = sum_a dD[x][a] T[c][a] + [x < M^<] sum_b dD[b][x] T[c][b].
 #include <math.h>
 
+#include "act.cuh"
 #include "dp_internal.h"
 
 namespace {
@@ -22,11 +23,12 @@ struct GemmEpi {
   const float* bias;  // [N]            (EPI_TANH)
   const float* R;     // residual, row stride ldr (0 = broadcast row)
   int ldr;
-  float* out0;        // C / t / gz
+  float* out0;        // C / activation derivative / gz
   float* out1;        // z / gp
   int ldc;
-  const float* Tt;    // tanh values of the previous layer (EPI_BWD)
+  const float* Tt;    // activation derivatives of the previous layer (EPI_BWD)
   int ldt;
+  const float4* tab;  // tanh table (EPI_TANH), NULL: tanhf
 };
 
 // C[M x N] = A[M x K] B[K x N], 128 x BN tiles, 8 x TN outputs per thread
@@ -103,14 +105,15 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* 
       if (EPI == EPI_PLAIN) {
         ep.out0[o] = v;
       } else if (EPI == EPI_TANH) {
-        const float t = tanhf(v + ep.bias[n]);
-        ep.out0[o] = t;
+        float d;
+        const float t = act_tanh(v + ep.bias[n], ep.tab, d);
+        ep.out0[o] = d;
         ep.out1[o] = (ep.R ? ep.R[(size_t)m * ep.ldr + n] : 0.0f) + t;
       } else {
         const float gz = v + (ep.R ? ep.R[(size_t)m * ep.ldr + n] : 0.0f);
         const float tt = ep.Tt[(size_t)m * ep.ldt + n];
         ep.out0[o] = gz;
-        ep.out1[o] = gz * (1.0f - tt * tt);
+        ep.out1[o] = gz * tt;
       }
     }
   }
@@ -191,13 +194,12 @@ __global__ void k_energy(int64_t rows, const int32_t* __restrict__ idx, const fl
   if (lane == 0) e[idx ? idx[r] : r] = (double)(s + b);
 }
 
-// gp = w (1 - t^2) for the last hidden layer
-__global__ void k_gp_last(int64_t rows, int W, const float* __restrict__ t,
+// gp = w act'(a) for the last hidden layer (d: the stored derivatives)
+__global__ void k_gp_last(int64_t rows, int W, const float* __restrict__ d,
                           const float* __restrict__ w, float* __restrict__ gp) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= rows * W) return;
-  const float tt = t[k];
-  gp[k] = w[k % W] * (1.0f - tt * tt);
+  gp[k] = w[k % W] * d[k];
 }
 
 }  // namespace
@@ -226,6 +228,7 @@ int fit_simt(cudaStream_t st, int64_t n, const int32_t* idx, const FitNet& net, 
       ep.out0 = s.t[k];
       ep.out1 = s.z[k];
       ep.ldc = net.wout[k];
+      ep.tab = net.tanh_tab;
       gemm<EPI_TANH>(st, rows, net.wout[k], win, in, win, net.W[k], net.wout[k], ep);
       in = s.z[k];
       win = net.wout[k];

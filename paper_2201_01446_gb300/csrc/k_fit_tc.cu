@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include "act.cuh"
 #include "dp_internal.h"
 #include "tc_common.cuh"
 
@@ -71,11 +72,11 @@ struct TcEpi {
   const float* bias;       // [N]
   const float* R;          // residual rows (ldr), ldr = 0: broadcast row
   int ldr;
-  const float* Tt;         // tanh values of the layer below (TC_BWD), ld = ldt
+  const float* Tt;         // activation derivatives of the layer below (TC_BWD), ld = ldt
   int ldt;
   const float* wout;       // output weights (TC_LAST)
   float bout;
-  float* out_a;            // FP32 [rows][ldo]: t (L0, MID) or C (PLAIN)
+  float* out_a;            // FP32 [rows][ldo]: activation derivative (L0, MID) or C (PLAIN)
   float* out_b;            // FP32 [rows][ldo]: z (MID) or gz (BWD)
   __nv_bfloat16* out_h;    // the next A operand, pre-tiled, width ldo
   int ldo;
@@ -88,9 +89,10 @@ struct TcEpi {
   int Mw;                  // embedding width M
   float* part;             // TC_DT: per-N-tile partial sums [slot][rows][64]
   int64_t part_ps;         // elements between slots
+  const float4* tab;       // tanh table (L0, MID, LAST), NULL: tanhf
 };
 
-template <int EPI, int PC>
+template <int EPI, int PC, bool TAB>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(int M, int N, int K, int NT, const __nv_bfloat16* __restrict__ A,
               const __nv_bfloat16* __restrict__ B, TcEpi ep) {
@@ -346,23 +348,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (EPI == TC_PLAIN) {
           oa[k] = v[k];
         } else if (EPI == TC_L0) {
-          const float t = tanhf(v[k] + b[k]);
-          oa[k] = t;
+          float d;
+          const float t = act_tanh_t<TAB>(v[k] + b[k], ep.tab, d);
+          oa[k] = d;
+          ob[k] = t;  // z_0 = t_0 (layer 0 has no shortcut)
           oh[k] = t;
         } else if (EPI == TC_MID) {
-          const float t = tanhf(v[k] + b[k]);
-          oa[k] = t;
+          float d;
+          const float t = act_tanh_t<TAB>(v[k] + b[k], ep.tab, d);
+          oa[k] = d;
           ob[k] = r[k] + t;
           oh[k] = ob[k];
         } else if (EPI == TC_LAST) {
-          const float t = tanhf(v[k] + b[k]);
+          float d;
+          const float t = act_tanh_t<TAB>(v[k] + b[k], ep.tab, d);
           const float w = ep.wout[n + k];
           e_acc = fmaf(r[k] + t, w, e_acc);
-          oh[k] = w * (1.0f - t * t);
+          oh[k] = w * d;
         } else {  // TC_BWD
           const float gz = v[k] + r[k];
           ob[k] = gz;
-          oh[k] = gz * (1.0f - tt[k] * tt[k]);
+          oh[k] = gz * tt[k];
         }
       }
       if (EPI == TC_PLAIN || EPI == TC_L0 || EPI == TC_MID) {
@@ -370,7 +376,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int k = 0; k < 16; k += 4)
           *reinterpret_cast<float4*>(ep.out_a + o + k) = *reinterpret_cast<const float4*>(oa + k);
       }
-      if (EPI == TC_MID || EPI == TC_BWD) {
+      if (EPI == TC_L0 || EPI == TC_MID || EPI == TC_BWD) {
 #pragma unroll
         for (int k = 0; k < 16; k += 4)
           *reinterpret_cast<float4*>(ep.out_b + o + k) = *reinterpret_cast<const float4*>(ob + k);
@@ -457,7 +463,7 @@ struct PCfg {
   static size_t smem(int nk) { return 128 + (size_t)nk * A_CHUNK + (size_t)kPNS * B_STAGE; }
 };
 
-template <int EPI, int PC>
+template <int EPI, int PC, bool TAB>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm_p(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
                 const __nv_bfloat16* __restrict__ B, TcEpi ep) {
@@ -699,19 +705,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                   if (EPI == TC_MID) {
-                    const float t = tanhf(v[k] + bb[k]);
-                    oa[k] = t;
+                    float d;
+                    const float t = act_tanh_t<TAB>(v[k] + bb[k], ep.tab, d);
+                    oa[k] = d;
                     ob[k] = rr[k] + t;
                     oh[k] = ob[k];
                   } else if (EPI == TC_LAST) {
-                    const float t = tanhf(v[k] + bb[k]);
+                    float d;
+                    const float t = act_tanh_t<TAB>(v[k] + bb[k], ep.tab, d);
                     const float w = ep.wout[ncol + k];
                     e_acc = fmaf(rr[k] + t, w, e_acc);
-                    oh[k] = w * (1.0f - t * t);
+                    oh[k] = w * d;
                   } else {  // TC_BWD
                     const float gz = v[k] + rr[k];
                     ob[k] = gz;
-                    oh[k] = gz * (1.0f - tt[k] * tt[k]);
+                    oh[k] = gz * tt[k];
                   }
                 }
                 if (EPI == TC_MID) {
@@ -776,7 +784,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 int g_tc_sms = 0;
 
 // persistent launch of the K-short GEMMs; -2: the row tile's A does not fit
-template <int EPI, int PC>
+template <int EPI, int PC, bool TAB>
 int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
               const __nv_bfloat16* B, const TcEpi& ep) {
   if (M <= 0) return 0;
@@ -786,7 +794,7 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
   if (sm > 225 * 1024) return -2;
   static size_t set = 0;
   if (sm > set) {
-    if (cudaFuncSetAttribute(k_tc_gemm_p<EPI, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_tc_gemm_p<EPI, PC, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm) != cudaSuccess)
       return -3;
     set = sm;
@@ -799,14 +807,14 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
   }
   const int mtiles = (M + kBM - 1) / kBM;
   DP_LAUNCHED(1);
-  k_tc_gemm_p<EPI, PC><<<mtiles < g_tc_sms ? mtiles : g_tc_sms, kTcThreads, sm, st>>>(M, N, K, A,
+  k_tc_gemm_p<EPI, PC, TAB><<<mtiles < g_tc_sms ? mtiles : g_tc_sms, kTcThreads, sm, st>>>(M, N, K, A,
                                                                                     B, ep);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 // the caller's layouts: A pre-tiled in 128-row tiles, B in tiles of 256 rows
 // (the last one ragged), N % 16 == 0, K % 16 == 0
-template <int EPI, int PC>
+template <int EPI, int PC, bool TAB>
 int tc_gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B,
             const TcEpi& ep) {
   if (M <= 0) return 0;
@@ -815,14 +823,14 @@ int tc_gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A, const 
   const int NT = N <= 256 ? N : 256;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(k_tc_gemm<EPI, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_tc_gemm<EPI, PC, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TcCfg<PC>::SMEM) != cudaSuccess)
       return -3;
     attr = true;
   }
   dim3 grid((N + NT - 1) / NT, (M + kBM - 1) / kBM);
   DP_LAUNCHED(1);
-  k_tc_gemm<EPI, PC><<<grid, kTcThreads, TcCfg<PC>::SMEM, st>>>(M, N, K, NT, A, B, ep);
+  k_tc_gemm<EPI, PC, TAB><<<grid, kTcThreads, TcCfg<PC>::SMEM, st>>>(M, N, K, NT, A, B, ep);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -876,16 +884,16 @@ int launch_tile_operand(cudaStream_t st, int N, int K, int pieces, const float* 
 // the K-short layers: persistent kernel when the row tile's A fits in shared
 // memory, the tiled kernel otherwise; *fused_dt tells whether the dE/dD GEMM
 // completed dE/dT itself (no partials to reduce)
-template <int EPI, int PC>
+template <int EPI, int PC, bool TAB>
 static int gemm_k_short(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
                         const __nv_bfloat16* B, const TcEpi& ep, bool* persistent) {
-  const int rc = tc_gemm_p<EPI, PC>(st, M, N, K, A, B, ep);
+  const int rc = tc_gemm_p<EPI, PC, TAB>(st, M, N, K, A, B, ep);
   if (persistent) *persistent = rc == 0;
   if (rc != -2) return rc;
-  return tc_gemm<EPI, PC>(st, M, N, K, A, B, ep);
+  return tc_gemm<EPI, PC, TAB>(st, M, N, K, A, B, ep);
 }
 
-template <int PC>
+template <int PC, bool TAB>
 static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const FitNetTC& net, int M,
                        int m_lt, const float* T, float* dT, double* e_atom, const FitScratchTC& s,
                        int32_t* err) {
@@ -913,16 +921,18 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.bias = net.b[k];
       ep.ldo = net.wout[k];
       ep.err = err;
-      // z of the layer below (z_0 = t_0: the first layer has no shortcut)
-      const float* zb = k == 0 ? nullptr : (k == 1 ? s.t[0] : s.z[k - 1]);
+      ep.tab = net.tanh_tab;
+      // z of the layer below (layer 0 writes z_0 = t_0: it has no shortcut)
+      const float* zb = k == 0 ? nullptr : s.z[k - 1];
       int rc;
       if (k == 0) {
         ep.out_a = s.t[0];
+        ep.out_b = s.z[0];
         ep.out_h = s.zh[0];
         ep.T = Tc;
         ep.tidx = id;
         ep.Mw = M;
-        rc = tc_gemm<TC_L0, PC>(st, rows, net.wout[0], din, nullptr, net.WTh[0], ep);
+        rc = tc_gemm<TC_L0, PC, TAB>(st, rows, net.wout[0], din, nullptr, net.WTh[0], ep);
       } else if (k == nl - 1) {
         ep.R = net.shortcut[k] ? zb : nullptr;
         ep.ldr = net.wout[k - 1];
@@ -931,7 +941,7 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
         ep.out_h = s.gph[0];
         ep.e_atom = e_atom + (idx ? 0 : r0);
         ep.idx = id;
-        rc = gemm_k_short<TC_LAST, PC>(st, rows, net.wout[k], net.win[k], s.zh[k - 1], net.WTh[k],
+        rc = gemm_k_short<TC_LAST, PC, TAB>(st, rows, net.wout[k], net.win[k], s.zh[k - 1], net.WTh[k],
                                        ep, nullptr);
       } else {
         ep.R = net.shortcut[k] ? zb : nullptr;
@@ -939,7 +949,7 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
         ep.out_a = s.t[k];
         ep.out_b = s.z[k];
         ep.out_h = s.zh[k];
-        rc = gemm_k_short<TC_MID, PC>(st, rows, net.wout[k], net.win[k], s.zh[k - 1], net.WTh[k],
+        rc = gemm_k_short<TC_MID, PC, TAB>(st, rows, net.wout[k], net.win[k], s.zh[k - 1], net.WTh[k],
                                       ep, nullptr);
       }
       if (rc) return rc;
@@ -959,7 +969,7 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.out_h = s.gph[gi ^ 1];
       ep.ldo = net.win[k];
       ep.err = err;
-      const int rc = gemm_k_short<TC_BWD, PC>(st, rows, net.win[k], net.wout[k], s.gph[gi],
+      const int rc = gemm_k_short<TC_BWD, PC, TAB>(st, rows, net.win[k], net.wout[k], s.gph[gi],
                                               net.Wh[k], ep, nullptr);
       if (rc) return rc;
       gz_prev = s.gz;
@@ -980,7 +990,7 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.Mw = M;
       ep.part = s.part;
       ep.part_ps = R * 64;
-      const int rc = gemm_k_short<TC_DT, PC>(st, rows, din, net.wout[0], s.gph[gi], net.Wh[0], ep,
+      const int rc = gemm_k_short<TC_DT, PC, TAB>(st, rows, din, net.wout[0], s.gph[gi], net.Wh[0], ep,
                                              &dt_done);
       if (rc) return rc;
     }
@@ -997,7 +1007,12 @@ int fit_tc(cudaStream_t st, int64_t n, const int32_t* idx, const FitNetTC& net, 
            const float* T, float* dT, double* e_atom, const FitScratchTC& s, int pieces,
            int32_t* err) {
   if (n <= 0) return 0;
-  if (pieces == 1) return fit_tc_impl<1>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err);
-  if (pieces == 3) return fit_tc_impl<3>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err);
+  const bool tab = net.tanh_tab != nullptr;
+  if (pieces == 1)
+    return tab ? fit_tc_impl<1, true>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err)
+               : fit_tc_impl<1, false>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err);
+  if (pieces == 3)
+    return tab ? fit_tc_impl<3, true>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err)
+               : fit_tc_impl<3, false>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err);
   return -1;
 }

@@ -428,3 +428,54 @@ def test_md_energy_conservation_and_reversibility(stress):
     x1, v1, _, _ = oracle.md(m, tab, CU_RC, CU_RCS, CU_SEL, x, v, t, masses, box, 1.0, 10)
     x2, v2, _, _ = oracle.md(m, tab, CU_RC, CU_RCS, CU_SEL, x1, -v1, t, masses, box, 1.0, 10)
     assert np.abs(x2 - x).max() < 1e-9 and np.abs(v2 + v).max() < 1e-10
+
+
+# ------------------------------------------------------------------ Sec. 3.5 tanh table
+def test_tanh_table_pins():
+    import math
+    oracle.set_tanh_table(True)
+    try:
+        h = 1.0 / 128
+        for k in [0, 1, 77, 500, 1023]:
+            x = k * h
+            t, d = oracle.act(x)
+            assert abs(t - math.tanh(x)) < 1e-15           # exact at the nodes
+            assert abs(d - (1 - math.tanh(x) ** 2)) < 1e-15  # slope matched at the left node
+            t1, _ = oracle.act(x + h * (1 - 1e-12))
+            assert abs(t1 - math.tanh(x + h)) < 1e-12       # value matched at the right node
+        xs = np.linspace(0.0, 7.999, 40001)
+        err = max(abs(oracle.act(x)[0] - math.tanh(x)) for x in xs)
+        assert err < 3e-8, err  # third-order error of a quadratic at h = 1/128
+        for x in [0.3, 2.7, 7.5]:
+            assert oracle.act(-x)[0] == -oracle.act(x)[0]  # odd
+            assert oracle.act(-x)[1] == oracle.act(x)[1]
+            # the stored derivative is the derivative of the table polynomial
+            e = 1e-6
+            fd = (oracle.act(x + e)[0] - oracle.act(x - e)[0]) / (2 * e)
+            assert abs(fd - oracle.act(x)[1]) < 1e-8
+        assert oracle.act(8.0) == (1.0, 0.0) and oracle.act(-9.5) == (-1.0, 0.0)
+    finally:
+        oracle.set_tanh_table(False)
+    assert oracle.act(0.3)[0] == math.tanh(0.3)
+
+
+def test_fit_gradient_with_tanh_table(cu_stress_path):
+    # forces stay the exact gradient of the energy the table gives
+    m = oracle.Model(cu_stress_path)
+    rng = np.random.default_rng(3)
+    D = rng.normal(scale=0.05, size=m.din)
+    oracle.set_tanh_table(True)
+    try:
+        E, dD = m.fit(0, D)
+        for j in rng.choice(m.din, 6, replace=False):
+            e = 1e-6
+            Dp, Dm = D.copy(), D.copy()
+            Dp[j] += e
+            Dm[j] -= e
+            fd = (m.fit(0, Dp)[0] - m.fit(0, Dm)[0]) / (2 * e)
+            assert abs(fd - dD[j]) < 2e-6 * max(1.0, abs(dD[j])), (j, fd, dD[j])
+        E0, _ = m.fit(0, D)
+    finally:
+        oracle.set_tanh_table(False)
+    Ex, _ = m.fit(0, D)
+    assert E0 == E and abs(E - Ex) < 1e-4 * max(1.0, abs(Ex))
