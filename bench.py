@@ -180,6 +180,15 @@ def flops_per_unit(M=128, din=2048, w=240):
             "embed_contract_bwd_forces": ("pair", 2 * 18 * M)}
 
 
+# DRAM bytes per launch of the embedding kernels, from one ncu capture of the
+# current build (dram__bytes_read.sum + dram__bytes_write.sum, FCC Cu 256,000
+# atoms, scaled per atom: the traffic grows in proportion to the atoms);
+# profiles/k_tab_tc_traffic_cu256k.md
+TRAFFIC_PER_ATOM = {"embed_contract_fwd": (405016064 + 1342494464) / 256000,
+                    "embed_contract_bwd_forces": (1354734080 + 5732352) / 256000}
+KERNEL_OF_PHASE = {"embed_contract_fwd": "k_tab_fwd_tc", "embed_contract_bwd_forces": "k_tab_bwd_tc"}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -332,37 +341,41 @@ def main():
     stats = dp.dp_stats(h, s)
     launches = stats["kernel_launches"] - launches0
     value = world * n * MD_PER_STEP * args.steps / (ms_max / 1e3)
-    # roofline of the dominant phase: FP32 CUDA-core bound for the embedding
-    # kernels (and the CUDA-core fitting mode), tensor-core bound for the
-    # tcgen05 fitting modes, against the measured sustained BF16 peak (a
-    # kernel timed inside a long step)
+    # roofline of the dominant kernel: the phases of one launch each (the
+    # embedding forward and backward) are single kernels; the fitting phase is
+    # a chain of seven GEMM launches per row chunk and is reported beside it
     units = flops_per_unit()
-    dom = max((k for k in prof if k in units), key=lambda k: prof[k][0])
-    kind, fl = units[dom]
-    per_launch_units = stats["pairs_within_rc"] if kind == "pair" else n
-    avg_ms = prof[dom][0] / max(prof[dom][1], 1)
-    achieved = fl * per_launch_units / (avg_ms / 1e3) / 1e12
     peaks = measured_peaks()
-    if dom == "fitting" and args.fit_precision > 0:
-        # the peak of the arithmetic the phase computes in: BF16 products for
-        # the BF16 mode; for the FP32-accurate mode, whose every multiply-add
-        # is six BF16 piece products, the BF16 peak / 6
+    per_launch = {k: prof[k][0] / max(prof[k][1], 1) for k in prof}
+
+    def phase_achieved(k):
+        kind, fl = units[k]
+        return fl * (stats["pairs_within_rc"] if kind == "pair" else n) / (per_launch[k] / 1e3) / 1e12
+
+    single = [k for k in KERNEL_OF_PHASE if prof.get(k, (0, 0))[1]]
+    dom = max(single, key=lambda k: per_launch[k])
+    achieved = phase_achieved(dom)
+    traffic = TRAFFIC_PER_ATOM[dom] * n if args.embed_precision == 2 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": KERNEL_OF_PHASE[dom] if args.embed_precision == 2 else dom,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (FP32 CUDA cores)",
+                "note": "achieved counts the method's per-pair FLOPs (2304 per pair within rc); "
+                        "the interval contraction inside runs on tcgen05"}
+    if args.fit_precision > 0 and prof.get("fitting", (0, 0))[1]:
+        # the fitting chain against the peak of the arithmetic it computes in:
+        # BF16 products for the BF16 mode; for the FP32-accurate mode, whose
+        # every multiply-add is six BF16 piece products, the BF16 peak / 6
         nprod = 6 if args.fit_precision == 2 else 1
         bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
-        peak = bf16 / nprod
-        executed = achieved * nprod
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": dom,
-                    "executed_bf16_tflops": executed, "bf16_peak": bf16,
-                    "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
-                                    + (" / 6 piece products" if nprod == 6 else "")
-                                    if peaks else "fallback 1.7 PFLOP/s sustained"),
-                    "note": "achieved counts the method's FLOPs (multiply-add = 2)"}
-    else:
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                    "kernel": dom,
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (FP32 CUDA cores)"}
+        fa = phase_achieved("fitting")
+        roofline["fitting_chain"] = {
+            "bound": "tensor", "achieved": fa, "peak": bf16 / nprod, "unit": "TFLOP/s",
+            "frac": fa / (bf16 / nprod), "executed_bf16_tflops": fa * nprod, "bf16_peak": bf16,
+            "ms_per_launch": per_launch["fitting"],
+            "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+                            + (" / 6 piece products" if nprod == 6 else "")
+                            if peaks else "fallback 1.7 PFLOP/s sustained")}
     roofline["phases_ms_per_launch"] = {k: prof[k][0] / max(prof[k][1], 1) for k in prof}
     roofline["phases_achieved_tflops"] = {
         k: units[k][1] * (stats["pairs_within_rc"] if units[k][0] == "pair" else n)

@@ -233,7 +233,9 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
     const int pos = sorted_slot(hist, in, bin, lane);
     if (in) {
       // the backward's copy: displacement and neighbor index in sorted order
-      pout[pos] = make_float4(P.dx, P.dy, P.dz, __int_as_float((int)(L[k] >> 5)));
+      // (streaming stores, evict-first in L2: read back only by the backward,
+      // they should not push the L2-resident scratch out)
+      __stcs(pout + pos, make_float4(P.dx, P.dy, P.dz, __int_as_float((int)(L[k] >> 5))));
       // planar rows: R0 R1 R2 R3 u, each kAtoms * scap apart
       const size_t st = (size_t)kAtoms * scap;
       sc[pos] = P.s;
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     {
       int4* ho = reinterpret_cast<int4*>(hist_out + (size_t)tile * kAtoms * cf.nbp);
       const int4* hs = reinterpret_cast<const int4*>(shist);
-      for (int q = tid; q < kAtoms * cf.nbp / 8; q += kThreads) ho[q] = hs[q];
+      for (int q = tid; q < kAtoms * cf.nbp / 8; q += kThreads) __stcs(ho + q, hs[q]);
       if (tid == 0) range_out[tile] = make_int2(kb0, nk);
     }
     // ---- phase 2: T rows of the tile = C . table over the occupied bins
@@ -486,7 +488,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
           for (int k = 0; k < 16; k += 4)
             if (ch * 16 + k < M)
-              *reinterpret_cast<float4*>(Tr + ch * 16 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+              __stcs(reinterpret_cast<float4*>(Tr + ch * 16 + k),
+                     make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]));
         }
       }
     }
