@@ -117,6 +117,7 @@ struct FwdCfg {
   int bstage;     // bytes of the B part of a stage (all pieces)
   int stage;      // bytes per stage
   int nbp;        // bin ends per atom (uint16, rounded to 8)
+  size_t region;  // the stages, or phase 1's per-warp scratch (the larger)
   size_t smem;    // dynamic shared memory
 };
 
@@ -125,20 +126,24 @@ __host__ __device__ inline int scap_of(const EnvParams& ep) {
   return ((int)(1.0f / ep.inv_nm + 0.5f) + 32 + 31) / 32 * 32;
 }
 
+// phase 1's per-warp scratch (int histogram, then the staged pairs: 32 bytes
+// each) lives in the stage memory, idle between the previous tile's epilogue
+// and this tile's MMAs
+__host__ __device__ inline size_t warp_scratch_bytes(const EnvParams& ep) {
+  return (size_t)round4(ep.ntypes * ep.n_int) * 4 + (size_t)scap_of(ep) * 32;
+}
+
 __host__ __device__ inline FwdCfg fwd_cfg(const EnvParams& ep) {
   FwdCfg c;
   c.NP = round16(ep.M);
   c.bstage = kPC * c.NP * 32;
   c.stage = kPC * kABytes + c.bstage;
   c.nbp = (ep.ntypes * ep.n_int + 7) & ~7;
-  c.smem = 128 + (size_t)kNS * c.stage + (size_t)kAtoms * c.nbp * 2;
+  c.region = (size_t)kNS * c.stage;
+  const size_t p1 = (size_t)(kThreads / 32) * warp_scratch_bytes(ep);
+  if (c.region < p1) c.region = p1;
+  c.smem = 128 + c.region + (size_t)kAtoms * c.nbp * 2;
   return c;
-}
-
-// phase 1's per-warp scratch (int histogram, pair keys) lives in the stage
-// memory, idle between the previous tile's epilogue and this tile's MMAs
-__host__ __device__ inline int warp_scratch_words(const EnvParams& ep) {
-  return round4(ep.ntypes * ep.n_int) + scap_of(ep);
 }
 
 __device__ __forceinline__ int bin_begin16(const uint16_t* hist, int b) {
@@ -157,18 +162,20 @@ __device__ __forceinline__ int tile_atom(const TileMap& tm, int ti, int64_t tile
   return tm.idx ? tm.idx[tm.atom_off[ti] + pos] : (int)(tm.atom_off[ti] + pos);
 }
 
-// Phase 1 for one atom (one warp): histogram of the pairs within rc by bin =
-// (neighbor type, interval) with a compact key list (bin << 16 | list index,
-// list order) in the warp's shared memory, exclusive scan, then over the keys
-// only a stable scatter of (R, u) in bin order into the scratch rows of tile
-// slot al.  On return hist holds the end
+// Phase 1 for one atom (one warp): one pass over the neighbor list computes
+// the geometry of every pair, the histogram of the pairs within rc by bin =
+// (neighbor type, interval) and a staged copy of those pairs in list order in
+// the warp's shared memory (bin, j, s, u, dx, dy, dz, 1/r); after the
+// exclusive scan a second pass over the staged pairs only scatters (R, u) in
+// stable bin order into the scratch rows of tile slot al, and (dx, dy, dz, j)
+// for the backward.  On return hist holds the end
 // of every bin (all zero when the atom has no slot: padding or overflow).
 // Returns the pairs within rc; lo/hi the occupied bin range of this atom.
 __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ off,
                                          const uint32_t* __restrict__ nlist,
                                          const int32_t* __restrict__ nn, int cap,
                                          const CellGeom& g, const EnvParams& ep, int scap, int* hist,
-                                         int nbins, float* __restrict__ sc, int* keys,
+                                         int nbins, float* __restrict__ sc, float4* stg,
                                          float4* __restrict__ pout, int lane, int& nrange,
                                          int& nover, int& lo, int& hi) {
   for (int b = lane; b < nbins; b += 32) hist[b] = 0;
@@ -185,13 +192,14 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
     const int k = b0 + lane;
     bool in = false;
     int bin = 0;
+    Pair Pk;
     if (k < cnt) {
       float dx, dy, dz;
       int tj;
       load_pair(oi, off, g, L[k], dx, dy, dz, tj);
       const float r2 = dx * dx + dy * dy + dz * dz;
       if (r2 < ep.rc2) {
-        Pair P;
+        Pair& P = Pk;
         pair_geom(ep, dx, dy, dz, r2, tj, P);
         bin = tj * ep.n_int + P.th;
         atomicAdd(&hist[bin], 1);
@@ -203,7 +211,10 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
     }
     const unsigned bal = __ballot_sync(0xffffffffu, in);
     const int q = np + __popc(bal & below);
-    if (in && q < scap) keys[q] = (bin << 16) | k;
+    if (in && q < scap) {
+      stg[2 * q] = make_float4(__int_as_float(bin), __int_as_float((int)(L[k] >> 5)), Pk.s, Pk.u);
+      stg[2 * q + 1] = make_float4(Pk.dx, Pk.dy, Pk.dz, Pk.ir);
+    }
     np += __popc(bal);
   }
   __syncwarp();
@@ -220,22 +231,25 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
   for (int b0 = 0; b0 < np; b0 += 32) {
     const int kk = b0 + lane;
     const bool in = kk < np;
-    const int key = in ? keys[kk] : 0;
-    const int bin = key >> 16, k = key & 0xffff;
-    Pair P;
+    float4 sa = make_float4(0.f, 0.f, 0.f, 0.f), sb = sa;
     if (in) {
-      float dx, dy, dz;
-      int tj;
-      load_pair(oi, off, g, L[k], dx, dy, dz, tj);
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      pair_geom(ep, dx, dy, dz, r2, tj, P);
+      sa = stg[2 * kk];
+      sb = stg[2 * kk + 1];
     }
+    const int bin = __float_as_int(sa.x);
+    Pair P;
+    P.s = sa.z;
+    P.u = sa.w;
+    P.dx = sb.x;
+    P.dy = sb.y;
+    P.dz = sb.z;
+    P.ir = sb.w;
     const int pos = sorted_slot(hist, in, bin, lane);
     if (in) {
       // the backward's copy: displacement and neighbor index in sorted order
       // (streaming stores, evict-first in L2: read back only by the backward,
       // they should not push the L2-resident scratch out)
-      __stcs(pout + pos, make_float4(P.dx, P.dy, P.dz, __int_as_float((int)(L[k] >> 5))));
+      __stcs(pout + pos, make_float4(P.dx, P.dy, P.dz, sa.y));
       // planar rows: R0 R1 R2 R3 u, each kAtoms * scap apart
       const size_t st = (size_t)kAtoms * scap;
       sc[pos] = P.s;
@@ -260,9 +274,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   const FwdCfg cf = fwd_cfg(ep);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  uint16_t* shist = (uint16_t*)(base + (size_t)kNS * cf.stage);  // [32 atoms][nbp] bin ends
-  int* whist = (int*)base + (size_t)(threadIdx.x >> 5) * warp_scratch_words(ep);
-  int* wkeys = whist + round4(ep.ntypes * ep.n_int);
+  uint16_t* shist = (uint16_t*)(base + cf.region);  // [32 atoms][nbp] bin ends
+  int* whist = (int*)(base + (size_t)(threadIdx.x >> 5) * warp_scratch_bytes(ep));
+  float4* wstg = (float4*)(whist + round4(ep.ntypes * ep.n_int));
   __shared__ __align__(8) uint64_t s_full[kNS], s_empty[kNS], s_gen[kNS], s_acc;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort, s_lo, s_hi;
@@ -317,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (lane == 0) s_atom[al] = atom;
       int lo, hi;
       const int np = sort_atom(atom, off, nlist, nn, cap, g, ep, scap, whist, nbins,
-                               sc_cta + (size_t)al * scap, wkeys,
+                               sc_cta + (size_t)al * scap, wstg,
                                pairs_out + ((size_t)tile * kAtoms + al) * scap, lane, nrange,
                                nover, lo, hi);
       // bin ends of this atom (<= N_m + 32 < 2^16)
@@ -891,7 +905,6 @@ int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, con
   if (ep.M > 128 || ep.M % 4 || ep.M < 16) return -1;
   if (tm.ntypes < 1 || tm.ntypes > DP_MAXT || tm.ntypes != ep.ntypes) return -1;
   if (((uintptr_t)tabF & 15) || ((uintptr_t)T & 15)) return -1;
-  if (cap > 65535) return -1;  // pair keys hold the list index in 16 bits
   if (tab_tc_supported(ep)) return -1;
   const int64_t ntile = tm.tile_off[tm.ntypes];
   if (ntile <= 0) return 0;
@@ -951,7 +964,6 @@ int64_t tab_tc_hist_elems(const EnvParams& ep, int64_t ntile) {
 int tab_tc_supported(const EnvParams& ep) {
   if (ep.M > 128 || ep.M % 4 || ep.M < 16) return -1;
   if (fwd_cfg(ep).smem > 113 * 1024 || bwd_cfg(ep).smem > 113 * 1024) return -2;
-  if ((size_t)(kThreads / 32) * warp_scratch_words(ep) * 4 > (size_t)kNS * fwd_cfg(ep).stage)
-    return -2;
+
   return 0;
 }
