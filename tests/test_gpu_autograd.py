@@ -25,7 +25,7 @@ def test_energy_gradient_is_minus_forces(cu_stress_path):
         (gx,) = torch.autograd.grad(E, x)
         E2, F, V2, _ = dp.dp_compute(h, torch.tensor(xn, device="cuda"), t, box)
         torch.cuda.synchronize()
-        assert float(E) == float(E2[0])
+        assert float(E.detach()) == float(E2[0])
         assert torch.equal(gx, -F) and torch.equal(V, V2)
         assert abs(float(Ei.sum()) - float(E)) < 1e-9 * abs(float(E))
         # composition: L = 2 E + sum(x^2)  ->  dL/dx = -2 F + 2 x
