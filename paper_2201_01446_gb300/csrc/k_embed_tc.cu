@@ -743,76 +743,122 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncthreads();
       // ---- pairs of the window: chain rule to the forces and virial
       const int wend = min(w0 + wb, nbins);  // bins w0 .. wend - 1 exist
+      // the window's pairs of the warp's four atoms as one range t = 0 ..
+      // total - 1 (atom j from the prefix counts cs, sorted index k), so the
+      // lanes stay busy across the atoms; the next pair is loaded while the
+      // current one is computed
+      const int al0 = warp * (kAtoms / 8);
+      int kb0 = 0, kb1 = 0, kb2 = 0, kb3 = 0, cs1, cs2, cs3, total;
+      {
+        int n4[4];
 #pragma unroll
-      for (int j = 0; j < kAtoms / 8; ++j) {
-        const int al = warp * (kAtoms / 8) + j;
-        if (s_atom[al] < 0) continue;
-        const uint16_t* hist = shist + al * cf.nbp;
-        const int kbeg = bin_begin16(hist, w0), kend = hist[wend - 1];
-        const float4* pr = pairs + ((size_t)tile * kAtoms + al) * scap;
-        for (int k = kbeg + lane; k < kend; k += 32) {
-          // the pair's bin: the one whose sorted range holds k
-          int b = w0;
-          while (b + 1 < wend && hist[b] <= k) ++b;
-          const float4 q4 = pr[k];
-          const float dx = q4.x, dy = q4.y, dz = q4.z;
-          const int jn = __float_as_int(q4.w);
-          const int tj = b / n_int, th = b - tj * n_int;
-          const float r2 = dx * dx + dy * dy + dz * dz;
-          Pair P;
-          pair_geom(ep, dx, dy, dz, r2, tj, P);
-          const float u = P.s * ep.inv_h - (float)th;  // the sort's interval
-          const float* Bk = Bsm + al * kBsmAtom + (b - w0) * 24;
-          float Bv[24];
-#pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            const float4 t4 = reinterpret_cast<const float4*>(Bk)[q];
-            Bv[4 * q] = t4.x;
-            Bv[4 * q + 1] = t4.y;
-            Bv[4 * q + 2] = t4.z;
-            Bv[4 * q + 3] = t4.w;
-          }
-          float gR[4], dgu[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float* bb = Bv + c * 6;
-            gR[c] = fmaf(fmaf(fmaf(fmaf(fmaf(bb[5], u, bb[4]), u, bb[3]), u, bb[2]), u, bb[1]), u, bb[0]);
-            dgu[c] = fmaf(fmaf(fmaf(fmaf(5.0f * bb[5], u, 4.0f * bb[4]), u, 3.0f * bb[3]), u,
-                               2.0f * bb[2]),
-                          u, bb[1]);
-          }
-          const float ux = P.dx * P.ir, uy = P.dy * P.ir, uz = P.dz * P.ir;
-          const float s = P.s;
-          const float gs = ep.inv_h * s * (dgu[0] + ux * dgu[1] + uy * dgu[2] + uz * dgu[3]);
-          const float a0 = gR[0] + gs;
-          const float dot = gR[1] * ux + gR[2] * uy + gR[3] * uz;
-          const float sor = s * P.ir;
-          const float coef = P.dsdr * (a0 + dot) - sor * dot;
-          float gx = coef * ux + sor * gR[1];
-          float gy = coef * uy + sor * gR[2];
-          float gz = coef * uz + sor * gR[3];
-          if (!(isfinite(gx) && isfinite(gy) && isfinite(gz)) || fabsf(gx) > 4.0e6f ||
-              fabsf(gy) > 4.0e6f || fabsf(gz) > 4.0e6f) {
-            ++nbad;
-            gx = gy = gz = 0.0f;
-          }
-          fxa[j] += gx;
-          fya[j] += gy;
-          fza[j] += gz;
-          vl[0] -= dx * gx;
-          vl[1] -= dx * gy;
-          vl[2] -= dx * gz;
-          vl[3] -= dy * gx;
-          vl[4] -= dy * gy;
-          vl[5] -= dy * gz;
-          vl[6] -= dz * gx;
-          vl[7] -= dz * gy;
-          vl[8] -= dz * gz;
-          unsigned long long* fj = ffix + (size_t)jn * 3;
-          atomicAdd(fj + 0, (unsigned long long)(-__float2ll_rn(gx * DP_FSCALE_F)));
-          atomicAdd(fj + 1, (unsigned long long)(-__float2ll_rn(gy * DP_FSCALE_F)));
-          atomicAdd(fj + 2, (unsigned long long)(-__float2ll_rn(gz * DP_FSCALE_F)));
+        for (int j = 0; j < 4; ++j) {
+          const uint16_t* hist = shist + (al0 + j) * cf.nbp;
+          const bool live = s_atom[al0 + j] >= 0;
+          const int b = live ? bin_begin16(hist, w0) : 0;
+          n4[j] = live ? hist[wend - 1] - b : 0;
+          if (j == 0) kb0 = b;
+          if (j == 1) kb1 = b;
+          if (j == 2) kb2 = b;
+          if (j == 3) kb3 = b;
         }
+        cs1 = n4[0];
+        cs2 = cs1 + n4[1];
+        cs3 = cs2 + n4[2];
+        total = cs3 + n4[3];
+      }
+      auto locate = [&](int t, int& j, int& k) {
+        j = (t >= cs1) + (t >= cs2) + (t >= cs3);
+        const int kbj = j == 0 ? kb0 : j == 1 ? kb1 : j == 2 ? kb2 : kb3;
+        const int csj = j == 0 ? 0 : j == 1 ? cs1 : j == 2 ? cs2 : cs3;
+        k = kbj + (t - csj);
+      };
+      const float4* pr_tile = pairs + (size_t)tile * kAtoms * scap;
+      float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (lane < total) {
+        int j, k;
+        locate(lane, j, k);
+        nxt = pr_tile[(size_t)(al0 + j) * scap + k];
+      }
+      for (int t = lane; t < total; t += 32) {
+        const float4 q4 = nxt;
+        int jq, kq;
+        locate(t, jq, kq);
+        if (t + 32 < total) {
+          int jn2, kn2;
+          locate(t + 32, jn2, kn2);
+          nxt = pr_tile[(size_t)(al0 + jn2) * scap + kn2];
+        }
+        const int al = al0 + jq;
+        const uint16_t* hist = shist + al * cf.nbp;
+        // the pair's bin: the first in [w0, wend) whose end exceeds kq
+        int b = w0, bh = wend - 1;
+        while (b < bh) {
+          const int mid = (b + bh) >> 1;
+          if (hist[mid] > kq) bh = mid;
+          else b = mid + 1;
+        }
+        const float dx = q4.x, dy = q4.y, dz = q4.z;
+        const int jn = __float_as_int(q4.w);
+        const int tj = b / n_int, th = b - tj * n_int;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        Pair P;
+        pair_geom(ep, dx, dy, dz, r2, tj, P);
+        const float u = P.s * ep.inv_h - (float)th;  // the sort's interval
+        const float* Bk = Bsm + al * kBsmAtom + (b - w0) * 24;
+        float Bv[24];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const float4 t4 = reinterpret_cast<const float4*>(Bk)[q];
+          Bv[4 * q] = t4.x;
+          Bv[4 * q + 1] = t4.y;
+          Bv[4 * q + 2] = t4.z;
+          Bv[4 * q + 3] = t4.w;
+        }
+        float gR[4], dgu[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float* bb = Bv + c * 6;
+          gR[c] = fmaf(fmaf(fmaf(fmaf(fmaf(bb[5], u, bb[4]), u, bb[3]), u, bb[2]), u, bb[1]), u, bb[0]);
+          dgu[c] = fmaf(fmaf(fmaf(fmaf(5.0f * bb[5], u, 4.0f * bb[4]), u, 3.0f * bb[3]), u,
+                             2.0f * bb[2]),
+                        u, bb[1]);
+        }
+        const float ux = P.dx * P.ir, uy = P.dy * P.ir, uz = P.dz * P.ir;
+        const float s = P.s;
+        const float gs = ep.inv_h * s * (dgu[0] + ux * dgu[1] + uy * dgu[2] + uz * dgu[3]);
+        const float a0 = gR[0] + gs;
+        const float dot = gR[1] * ux + gR[2] * uy + gR[3] * uz;
+        const float sor = s * P.ir;
+        const float coef = P.dsdr * (a0 + dot) - sor * dot;
+        float gx = coef * ux + sor * gR[1];
+        float gy = coef * uy + sor * gR[2];
+        float gz = coef * uz + sor * gR[3];
+        if (!(isfinite(gx) && isfinite(gy) && isfinite(gz)) || fabsf(gx) > 4.0e6f ||
+            fabsf(gy) > 4.0e6f || fabsf(gz) > 4.0e6f) {
+          ++nbad;
+          gx = gy = gz = 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (jq == j) {
+            fxa[j] += gx;
+            fya[j] += gy;
+            fza[j] += gz;
+          }
+        vl[0] -= dx * gx;
+        vl[1] -= dx * gy;
+        vl[2] -= dx * gz;
+        vl[3] -= dy * gx;
+        vl[4] -= dy * gy;
+        vl[5] -= dy * gz;
+        vl[6] -= dz * gx;
+        vl[7] -= dz * gy;
+        vl[8] -= dz * gz;
+        unsigned long long* fj = ffix + (size_t)jn * 3;
+        atomicAdd(fj + 0, (unsigned long long)(-__float2ll_rn(gx * DP_FSCALE_F)));
+        atomicAdd(fj + 1, (unsigned long long)(-__float2ll_rn(gy * DP_FSCALE_F)));
+        atomicAdd(fj + 2, (unsigned long long)(-__float2ll_rn(gz * DP_FSCALE_F)));
       }
       // the window buffer is read before the next window's bulk copies land there
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
