@@ -59,6 +59,16 @@ __device__ __forceinline__ void load_pair(const float4& oi, const float4* __rest
   tj = __float_as_int(oj.w);
 }
 
+// the same with the neighbor's offset record oj already loaded
+__device__ __forceinline__ void pair_from(const float4& oi, const float4& oj, const CellGeom& g,
+                                          uint32_t e, float& dx, float& dy, float& dz, int& tj) {
+  const int code = (int)(e & 31u);
+  dx = (oj.x - oi.x) + (float)(code / 9 - 1) * g.edgef[0];
+  dy = (oj.y - oi.y) + (float)((code / 3) % 3 - 1) * g.edgef[1];
+  dz = (oj.z - oi.z) + (float)(code % 3 - 1) * g.edgef[2];
+  tj = __float_as_int(oj.w);
+}
+
 // ------------------------------------------------------------------ per-atom interval sort
 // The pairs of an atom within rc are counting-sorted by bin = (neighbor type,
 // table interval): a histogram (integer atomics: order independent), an

@@ -188,15 +188,25 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
   const uint32_t* L = nlist + (size_t)atom * cap;
   const unsigned below = (1u << lane) - 1u;
   int np = 0;
+  // two-deep software pipeline over the list: while round r computes, the
+  // offsets of round r + 1 and the list entries of round r + 2 are in flight
+  uint32_t e_cur = lane < cnt ? L[lane] : 0u;
+  float4 o_cur = lane < cnt ? off[e_cur >> 5] : make_float4(0.f, 0.f, 0.f, 0.f);
+  uint32_t e_nxt = 32 + lane < cnt ? L[32 + lane] : 0u;
   for (int b0 = 0; b0 < cnt; b0 += 32) {
     const int k = b0 + lane;
+    const uint32_t e = e_cur;
+    const float4 oj = o_cur;
+    if (k + 32 < cnt) o_cur = off[e_nxt >> 5];
+    e_cur = e_nxt;
+    if (k + 64 < cnt) e_nxt = L[k + 64];
     bool in = false;
     int bin = 0;
     Pair Pk;
     if (k < cnt) {
       float dx, dy, dz;
       int tj;
-      load_pair(oi, off, g, L[k], dx, dy, dz, tj);
+      pair_from(oi, oj, g, e, dx, dy, dz, tj);
       const float r2 = dx * dx + dy * dy + dz * dz;
       if (r2 < ep.rc2) {
         Pair& P = Pk;
@@ -212,7 +222,7 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
     const unsigned bal = __ballot_sync(0xffffffffu, in);
     const int q = np + __popc(bal & below);
     if (in && q < scap) {
-      stg[2 * q] = make_float4(__int_as_float(bin), __int_as_float((int)(L[k] >> 5)), Pk.s, Pk.u);
+      stg[2 * q] = make_float4(__int_as_float(bin), __int_as_float((int)(e >> 5)), Pk.s, Pk.u);
       stg[2 * q + 1] = make_float4(Pk.dx, Pk.dy, Pk.dz, Pk.ir);
     }
     np += __popc(bal);
