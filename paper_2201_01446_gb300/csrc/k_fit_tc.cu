@@ -72,11 +72,12 @@ struct TcEpi {
   const float* bias;       // [N]
   const float* R;          // residual rows (ldr), ldr = 0: broadcast row
   int ldr;
-  const float* Tt;         // activation derivatives of the layer below (TC_BWD), ld = ldt
+  const float* Tt;         // t (derivatives in the table mode) of the layer below (TC_BWD)
   int ldt;
   const float* wout;       // output weights (TC_LAST)
   float bout;
-  float* out_a;            // FP32 [rows][ldo]: activation derivative (L0, MID) or C (PLAIN)
+  float* out_a;            // FP32 [rows][ldo]: t, or in the table mode the activation
+                           // derivative (L0, MID); C (PLAIN)
   float* out_b;            // FP32 [rows][ldo]: z (MID) or gz (BWD)
   __nv_bfloat16* out_h;    // the next A operand, pre-tiled, width ldo
   int ldo;
@@ -350,13 +351,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         } else if (EPI == TC_L0) {
           float d;
           const float t = act_tanh_t<TAB>(v[k] + b[k], ep.tab, d);
-          oa[k] = d;
-          ob[k] = t;  // z_0 = t_0 (layer 0 has no shortcut)
+          oa[k] = TAB ? d : t;
+          ob[k] = t;  // z_0 = t_0 (layer 0 has no shortcut; table mode only)
           oh[k] = t;
         } else if (EPI == TC_MID) {
           float d;
           const float t = act_tanh_t<TAB>(v[k] + b[k], ep.tab, d);
-          oa[k] = d;
+          oa[k] = TAB ? d : t;
           ob[k] = r[k] + t;
           oh[k] = ob[k];
         } else if (EPI == TC_LAST) {
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         } else {  // TC_BWD
           const float gz = v[k] + r[k];
           ob[k] = gz;
-          oh[k] = gz * tt[k];
+          oh[k] = gz * (TAB ? tt[k] : 1.0f - tt[k] * tt[k]);
         }
       }
       if (EPI == TC_PLAIN || EPI == TC_L0 || EPI == TC_MID) {
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int k = 0; k < 16; k += 4)
           *reinterpret_cast<float4*>(ep.out_a + o + k) = *reinterpret_cast<const float4*>(oa + k);
       }
-      if (EPI == TC_L0 || EPI == TC_MID || EPI == TC_BWD) {
+      if ((EPI == TC_L0 && TAB) || EPI == TC_MID || EPI == TC_BWD) {
 #pragma unroll
         for (int k = 0; k < 16; k += 4)
           *reinterpret_cast<float4*>(ep.out_b + o + k) = *reinterpret_cast<const float4*>(ob + k);
@@ -707,7 +708,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                   if (EPI == TC_MID) {
                     float d;
                     const float t = act_tanh_t<TAB>(v[k] + bb[k], ep.tab, d);
-                    oa[k] = d;
+                    oa[k] = TAB ? d : t;
                     ob[k] = rr[k] + t;
                     oh[k] = ob[k];
                   } else if (EPI == TC_LAST) {
@@ -719,7 +720,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                   } else {  // TC_BWD
                     const float gz = v[k] + rr[k];
                     ob[k] = gz;
-                    oh[k] = gz * tt[k];
+                    oh[k] = gz * (TAB ? tt[k] : 1.0f - tt[k] * tt[k]);
                   }
                 }
                 if (EPI == TC_MID) {
@@ -922,8 +923,9 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.ldo = net.wout[k];
       ep.err = err;
       ep.tab = net.tanh_tab;
-      // z of the layer below (layer 0 writes z_0 = t_0: it has no shortcut)
-      const float* zb = k == 0 ? nullptr : s.z[k - 1];
+      // z of the layer below (z_0 = t_0: layer 0 has no shortcut; the table
+      // mode keeps activation derivatives in t, so layer 0 writes z_0 then)
+      const float* zb = k == 0 ? nullptr : (k == 1 && !TAB ? s.t[0] : s.z[k - 1]);
       int rc;
       if (k == 0) {
         ep.out_a = s.t[0];
