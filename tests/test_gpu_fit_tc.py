@@ -176,3 +176,31 @@ def test_split_mode_water_two_types(dp, water_model_path):
     assert dei < 2e-5 * emax, (dei, emax)
     assert fr < max(1e-5, 3e-5 * frms), (fr, frms)
     assert dv < 1e-4 * vmax + 1e-9, (dv, vmax)
+
+
+def test_split_mode_wide_fitting_fallback(dp, model_dir):
+    # fitting layers 256 wide: a row tile's A (16 K chunks x 3 pieces) leaves
+    # too little shared memory for the persistent kernel, so these layers run
+    # on the tiled kernel (dE/dT second factor through per-N-tile partials)
+    spec = inputs.ModelSpec(1, (32, 64, 128), 16, (256, 256, 256))
+    path = str(model_dir / "cu_wide256.model")
+    inputs.write_seeded_model(path, spec, seed=7, std=1.0)
+    m = oracle.Model(path)
+    tab = oracle.Table(m, TABLE_H, CU_SMAX)
+    x, t, box = inputs.fcc_copper(5, sigma=0.05, seed=1)
+    r = oracle.evaluate(m, tab, CU_RC, CU_RCS, CU_SEL, x, t, box)
+    o = dp.dp_options_default()
+    o.fit_precision = 2
+    o.embed_precision = 2
+    h = dp.dp_create(path, 1, CU_RC, CU_RCS, [CU_SEL], options=o, stream=None)
+    try:
+        E, F, V, Ei = dp.dp_compute(h, x, t, box, atom_energy=True)
+    finally:
+        dp.dp_destroy(h)
+    dei = float(np.abs(Ei - r["atom_energy"]).max())
+    fr = rmse(F, r["force"])
+    frms = float(np.sqrt((r["force"] ** 2).mean()))
+    PARITY_LOG.append(dict(case="tc split Cu 500, 256-wide fitting (tiled fallback)",
+                           natoms=len(x), max_dEi=dei, force_rmse=fr, force_rms=frms))
+    assert dei < 2e-5 * float(np.abs(r["atom_energy"]).max()), dei
+    assert fr < max(1e-5, 3e-5 * frms), (fr, frms)
