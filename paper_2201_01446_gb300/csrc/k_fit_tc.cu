@@ -446,35 +446,52 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // ---------------------------------------------------------------- persistent
 // K-short GEMMs (K <= 240: hidden, last, backward and dE/dD layers): one CTA
 // per SM walks row tiles; a row tile's A (all K chunks, all pieces) stays in
-// shared memory while its N tiles of 128 columns stream B through kPNS stages.
+// shared memory (or, for one or two N tiles, streams with B) while its N
+// tiles of 128 columns stream B through the stages.
 // The accumulators are double-buffered in TMEM (2 x 256 columns), so warps 4-7
 // drain N tile t (the fused epilogue, one thread per row) while warp 1 issues
 // the MMAs of tile t+1 and warp 0 the copies of t+2.  Per-row state across the
 // N tiles of a row tile (the energy sum, the dE/dT second factor) stays in the
 // epilogue thread's registers.
-constexpr int kPNT = 128;  // columns per N tile
-constexpr int kPNS = 3;    // B stages
-constexpr int kPMaxK = 16; // K chunks a row tile can hold (K <= 256)
+constexpr int kPNT = 128;    // columns per N tile
+constexpr int kPMaxNS = 8;   // stages at most
+constexpr int kPMaxK = 16;   // K chunks a row tile can hold (K <= 256)
+constexpr size_t kPSmemMax = 225 * 1024;
 
+// Two ways to feed A: resident (the row tile's A loaded once, B streamed;
+// for many N tiles, where re-reading A from L2 per N tile would cost more
+// than the shallow B pipeline) or streamed (A and B chunks share each
+// stage, up to 8 stages deep; for the layers with one or two N tiles)
 template <int PC>
 struct PCfg {
   static constexpr int A_CHUNK = PC * kBM * kBK * 2;   // one K chunk of A, all pieces
   static constexpr int B_PIECE = kPNT * kBK * 2;       // one piece of a B stage
   static constexpr int B_STAGE = PC * B_PIECE;
-  static size_t smem(int nk) { return 128 + (size_t)nk * A_CHUNK + (size_t)kPNS * B_STAGE; }
+  __host__ __device__ static int stage_bytes(bool res) { return res ? B_STAGE : A_CHUNK + B_STAGE; }
+  static int stages(int nk, bool res) {
+    const long left = (long)kPSmemMax - 128 - (res ? (long)nk * A_CHUNK : 0L);
+    const long ns = left / stage_bytes(res);
+    return (int)(ns < kPMaxNS ? ns : kPMaxNS);
+  }
+  static size_t smem(int nk, bool res) {
+    return 128 + (res ? (size_t)nk * A_CHUNK : 0) + (size_t)stages(nk, res) * stage_bytes(res);
+  }
 };
 
 template <int EPI, int PC, bool TAB>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_tc_gemm_p(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
+    k_tc_gemm_p(int M, int N, int K, int res, int NS, const __nv_bfloat16* __restrict__ A,
                 const __nv_bfloat16* __restrict__ B, TcEpi ep) {
   using C = PCfg<PC>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   const int nk = K / kBK;
-  unsigned char* a_smem = base;
-  unsigned char* b_smem = base + (size_t)nk * C::A_CHUNK;
-  __shared__ __align__(8) uint64_t a_full[kPMaxK], a_empty, b_full[kPNS], b_empty[kPNS];
+  const int sbytes = C::stage_bytes(res != 0);
+  unsigned char* a_smem = base;                                          // resident A
+  unsigned char* st_smem = base + (res ? (size_t)nk * C::A_CHUNK : 0);   // the stages
+  // stage s: [A chunk (streamed mode)][B pieces]
+  const uint32_t st_b = res ? 0u : (uint32_t)C::A_CHUNK;
+  __shared__ __align__(8) uint64_t a_full[kPMaxK], a_empty, b_full[kPMaxNS], b_empty[kPMaxNS];
   __shared__ __align__(8) uint64_t t_full[2], t_empty[2], fin;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
@@ -494,7 +511,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (tid == 0) {
     for (int k = 0; k < kPMaxK; ++k) mbar_init(&a_full[k], 1);
     mbar_init(&a_empty, 1);
-    for (int s = 0; s < kPNS; ++s) {
+    for (int s = 0; s < kPMaxNS; ++s) {
       mbar_init(&b_full[s], 1);
       mbar_init(&b_empty[s], 1);
     }
@@ -519,38 +536,43 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: a row tile's A once, then B for every (N tile, K chunk)
+      // producer: resident mode loads a row tile's A once, then B for every
+      // (N tile, K chunk); streamed mode loads the A chunk with each B chunk
       uint32_t bi = 0, im = 0;
       bool ok = true;
       for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x, ++im) {
-        if (im > 0 && !mbar_wait(&a_empty, (im - 1) & 1, abort_flag)) break;
-        for (int kc = 0; kc < nk; ++kc) {
-          mbar_expect_tx(&a_full[kc], C::A_CHUNK);
-          bulk_g2s(smem_u32(a_smem + (size_t)kc * C::A_CHUNK),
-                   A + ((size_t)mt * nk + kc) * PC * (kBM * kBK), C::A_CHUNK, &a_full[kc]);
+        if (res) {
+          if (im > 0 && !mbar_wait(&a_empty, (im - 1) & 1, abort_flag)) break;
+          for (int kc = 0; kc < nk; ++kc) {
+            mbar_expect_tx(&a_full[kc], C::A_CHUNK);
+            bulk_g2s(smem_u32(a_smem + (size_t)kc * C::A_CHUNK),
+                     A + ((size_t)mt * nk + kc) * PC * (kBM * kBK), C::A_CHUNK, &a_full[kc]);
+          }
         }
         for (int n = 0; n < ntn && ok; ++n) {
           const int nt = min(kPNT, N - n * kPNT);
           for (int kc = 0; kc < nk; ++kc, ++bi) {
-            const int s = bi % kPNS;
-            const uint32_t u = bi / kPNS;
+            const int s = bi % NS;
+            const uint32_t u = bi / NS;
             if (u > 0 && !mbar_wait(&b_empty[s], (u - 1) & 1, abort_flag)) {
               ok = false;
               break;
             }
-            mbar_expect_tx(&b_full[s], PC * nt * 32);
-            const uint32_t dst = smem_u32(b_smem + (size_t)s * C::B_STAGE);
+            const uint32_t st0 = smem_u32(st_smem + (size_t)s * sbytes);
+            mbar_expect_tx(&b_full[s], (res ? 0u : (uint32_t)C::A_CHUNK) + PC * nt * 32);
+            if (!res)
+              bulk_g2s(st0, A + ((size_t)mt * nk + kc) * PC * (kBM * kBK), C::A_CHUNK, &b_full[s]);
 #pragma unroll
             for (int p = 0; p < PC; ++p)
-              bulk_g2s(dst + p * C::B_PIECE, b_src(n, kc, p), nt * 32, &b_full[s]);
+              bulk_g2s(st0 + st_b + p * C::B_PIECE, b_src(n, kc, p), nt * 32, &b_full[s]);
           }
         }
       }
       if (*abort_flag) {
         // aborted: wait (bounded) for the copies already issued to land
-        for (uint32_t j = bi > (uint32_t)kPNS ? bi - kPNS : 0; j < bi; ++j)
-          mbar_wait(&b_full[j % kPNS], (j / kPNS) & 1, nullptr);
-        if (im > 0)
+        for (uint32_t j = bi > (uint32_t)NS ? bi - NS : 0; j < bi; ++j)
+          mbar_wait(&b_full[j % NS], (j / NS) & 1, nullptr);
+        if (res && im > 0)
           for (int kc = 0; kc < nk; ++kc) mbar_wait(&a_full[kc], (im - 1) & 1, nullptr);
       }
     }
@@ -570,18 +592,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n");
           for (int kc = 0; kc < nk; ++kc, ++bi) {
-            if (n == 0 && !mbar_wait(&a_full[kc], im & 1, abort_flag)) {
+            if (res && n == 0 && !mbar_wait(&a_full[kc], im & 1, abort_flag)) {
               ok = false;
               break;
             }
-            const int s = bi % kPNS;
-            if (!mbar_wait(&b_full[s], (bi / kPNS) & 1, abort_flag)) {
+            const int s = bi % NS;
+            if (!mbar_wait(&b_full[s], (bi / NS) & 1, abort_flag)) {
               ok = false;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n");
-            const uint32_t a0 = smem_u32(a_smem + (size_t)kc * C::A_CHUNK);
-            const uint32_t b0 = smem_u32(b_smem + (size_t)s * C::B_STAGE);
+            const uint32_t st0 = smem_u32(st_smem + (size_t)s * sbytes);
+            const uint32_t a0 = res ? smem_u32(a_smem + (size_t)kc * C::A_CHUNK) : st0;
+            const uint32_t b0 = st0 + st_b;
 #pragma unroll
             for (int q = 0; q < (PC == 1 ? 1 : 6); ++q) {
               int pa = 0, pb = 0;
@@ -603,9 +626,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                   smem_u32(&t_full[j])));
         }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                smem_u32(&a_empty)));
+        if (res)
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                  smem_u32(&a_empty)));
       }
       // the epilogue may be waiting for a buffer this thread will not fill
       if (!ok) *abort_flag = 1;
@@ -791,8 +815,12 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
   if (M <= 0) return 0;
   if (K <= 0 || K % kBK || K / kBK > kPMaxK || N <= 0 || N % 16) return -1;
   if (EPI != TC_DT && ep.ldo != N) return -1;
-  const size_t sm = PCfg<PC>::smem(K / kBK);
-  if (sm > 225 * 1024) return -2;
+  // A resident for many N tiles (the dE/dD GEMM), streamed for one or two
+  const int nk = K / kBK, ntn = (N + kPNT - 1) / kPNT;
+  const bool res = ntn > 2;
+  const int NS = PCfg<PC>::stages(nk, res);
+  if (NS < 3) return -2;
+  const size_t sm = PCfg<PC>::smem(nk, res);
   static size_t set = 0;
   if (sm > set) {
     if (cudaFuncSetAttribute(k_tc_gemm_p<EPI, PC, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -808,8 +836,8 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
   }
   const int mtiles = (M + kBM - 1) / kBM;
   DP_LAUNCHED(1);
-  k_tc_gemm_p<EPI, PC, TAB><<<mtiles < g_tc_sms ? mtiles : g_tc_sms, kTcThreads, sm, st>>>(M, N, K, A,
-                                                                                    B, ep);
+  k_tc_gemm_p<EPI, PC, TAB><<<mtiles < g_tc_sms ? mtiles : g_tc_sms, kTcThreads, sm, st>>>(
+      M, N, K, res ? 1 : 0, NS, A, B, ep);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -179,9 +179,11 @@ def test_split_mode_water_two_types(dp, water_model_path):
 
 
 def test_split_mode_wide_fitting_fallback(dp, model_dir):
-    # fitting layers 256 wide: a row tile's A (16 K chunks x 3 pieces) leaves
-    # too little shared memory for the persistent kernel, so these layers run
-    # on the tiled kernel (dE/dT second factor through per-N-tile partials)
+    # fitting layers 256 wide: the hidden and backward layers (two N tiles)
+    # stream A with B through the persistent kernel's stages; the dE/dD GEMM
+    # keeps A resident, and 16 K chunks x 3 pieces leave too little shared
+    # memory for three B stages, so it runs on the tiled kernel (dE/dT second
+    # factor through per-N-tile partials)
     spec = inputs.ModelSpec(1, (32, 64, 128), 16, (256, 256, 256))
     path = str(model_dir / "cu_wide256.model")
     inputs.write_seeded_model(path, spec, seed=7, std=1.0)
