@@ -478,8 +478,10 @@ struct PCfg {
   }
 };
 
-template <int EPI, int PC, bool TAB>
-__global__ void __launch_bounds__(kTcThreads, 1)
+// EW epilogue warps: 4 (one thread per row, all columns) or 8 (two column
+// halves; for the layers whose epilogue keeps no per-row state across columns)
+template <int EPI, int PC, bool TAB, int EW>
+__global__ void __launch_bounds__(128 + EW * 32, 1)
     k_tc_gemm_p(int M, int N, int K, int res, int NS, const __nv_bfloat16* __restrict__ A,
                 const __nv_bfloat16* __restrict__ B, TcEpi ep) {
   using C = PCfg<PC>;
@@ -517,7 +519,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int j = 0; j < 2; ++j) {
       mbar_init(&t_full[j], 1);
-      mbar_init(&t_empty[j], kBM);
+      mbar_init(&t_empty[j], EW * 32);
     }
     mbar_init(&fin, 1);
     s_abort = 0;
@@ -640,8 +642,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     __syncwarp();
   } else if (warp >= 4) {
-    // epilogue: thread = row of the tile (TMEM lane), all columns of each N tile
-    const int r = tid - 128;
+    // epilogue: thread = row of the tile (TMEM lane; a warp reaches the lane
+    // quarter warp % 4), all columns of each N tile or one half of them
+    static_assert(EW == 4 || (EW == 8 && EPI != TC_DT && EPI != TC_LAST), "epilogue warps");
+    constexpr int CPW = 8 / (EW / 4);  // 16-column chunks per thread and N tile
+    const int r = (tid - 128) & (kBM - 1);
+    const int hf = EW == 8 ? (warp - 4) >> 2 : 0;
     const uint32_t tl_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     uint32_t ti = 0;
     for (int mt = blockIdx.x; mt < mtiles; mt += gridDim.x) {
@@ -676,7 +682,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int nt = min(kPNT, N - n * kPNT), nch = nt / 16;
         float f1[4][8];
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) {
+        for (int cc = 0; cc < CPW; ++cc) {
+          const int ch = hf * CPW + cc;
           if (ch < nch) {
             float v[16], v2[16];
             tmem_ld16(tl_base + (uint32_t)(j * 256 + ch * 16), v);
@@ -812,6 +819,7 @@ int g_tc_sms = 0;
 template <int EPI, int PC, bool TAB>
 int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
               const __nv_bfloat16* B, const TcEpi& ep) {
+  constexpr int EW = (EPI == TC_MID || EPI == TC_BWD) ? 8 : 4;
   if (M <= 0) return 0;
   if (K <= 0 || K % kBK || K / kBK > kPMaxK || N <= 0 || N % 16) return -1;
   if (EPI != TC_DT && ep.ldo != N) return -1;
@@ -823,7 +831,7 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
   const size_t sm = PCfg<PC>::smem(nk, res);
   static size_t set = 0;
   if (sm > set) {
-    if (cudaFuncSetAttribute(k_tc_gemm_p<EPI, PC, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_tc_gemm_p<EPI, PC, TAB, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm) != cudaSuccess)
       return -3;
     set = sm;
@@ -836,7 +844,7 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
   }
   const int mtiles = (M + kBM - 1) / kBM;
   DP_LAUNCHED(1);
-  k_tc_gemm_p<EPI, PC, TAB><<<mtiles < g_tc_sms ? mtiles : g_tc_sms, kTcThreads, sm, st>>>(
+  k_tc_gemm_p<EPI, PC, TAB, EW><<<mtiles < g_tc_sms ? mtiles : g_tc_sms, 128 + EW * 32, sm, st>>>(
       M, N, K, res ? 1 : 0, NS, A, B, ep);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
