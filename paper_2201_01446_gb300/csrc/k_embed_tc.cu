@@ -423,39 +423,57 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         __syncwarp();
       } else if (warp >= 4) {
-        // C rows: thread r = (atom al, component c), two bins per chunk
+        // C rows: thread r = (atom al, component c), two bins per chunk.  The
+        // pairs of the tile's chunks are one contiguous sorted range per atom,
+        // read in groups of four; the next group (of this chunk or the next)
+        // is always in flight while the current one is computed
         const int r = tid - 128, al = r >> 2, c = r & 3;
         const uint16_t* hist = shist + al * cf.nbp;
         const size_t st = (size_t)kAtoms * scap;
         const float* Rc = sc_cta + (size_t)c * st + (size_t)al * scap;
         const float* Us = sc_cta + 4 * st + (size_t)al * scap;
+        auto bounds = [&](int kc, int& kb, int& km, int& ke) {
+          const int b0 = kb0 + 2 * kc;
+          kb = bin_begin16(hist, min(b0, nbins));
+          km = b0 < nbins ? hist[b0] : kb;
+          ke = b0 + 1 < nbins ? hist[b0 + 1] : km;
+        };
+        float rv[4], uv[4];
+        auto load4 = [&](int k, int ke) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const bool ok = k + t < ke;
+            rv[t] = ok ? Rc[k + t] : 0.0f;
+            uv[t] = ok ? Us[k + t] : 0.0f;
+          }
+        };
+        int kbeg, kmid, kend;
+        bounds(0, kbeg, kmid, kend);
+        load4(kbeg, kend);
         uint32_t i = it;
         for (int kc = 0; kc < nk; ++kc, ++i) {
           const int s = i % kNS;
           const uint32_t u = i / kNS;
-          // C of the two bins, computed before the wait for the stage: the
-          // pairs of both bins are one contiguous sorted range, loaded four at
-          // a time (independent loads in flight), each added to its bin's half
-          const int b0 = kb0 + 2 * kc;
-          const int kbeg = bin_begin16(hist, min(b0, nbins));
-          const int kmid = b0 < nbins ? hist[b0] : kbeg;
-          const int kend = b0 + 1 < nbins ? hist[b0 + 1] : kmid;
+          int nbeg = 0, nmid = 0, nend = 0;
+          if (kc + 1 < nk) bounds(kc + 1, nbeg, nmid, nend);
           float x[16];
 #pragma unroll
           for (int q = 0; q < 16; ++q) x[q] = 0.0f;
+          if (kbeg >= kend) load4(nbeg, nend);  // empty chunk: on to the next
           for (int k = kbeg; k < kend; k += 4) {
-            float rv[4], uv[4];
+            float cr[4], cu[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-              const bool ok = k + t < kend;
-              rv[t] = ok ? Rc[k + t] : 0.0f;
-              uv[t] = ok ? Us[k + t] : 0.0f;
+              cr[t] = rv[t];
+              cu[t] = uv[t];
             }
+            if (k + 4 < kend) load4(k + 4, kend);
+            else load4(nbeg, nend);
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-              const float uu = uv[t], u2 = uu * uu;
-              const float ra = k + t < kmid ? rv[t] : 0.0f;  // first bin
-              const float rb = rv[t] - ra;                   // second bin (or padding 0)
+              const float uu = cu[t], u2 = uu * uu;
+              const float ra = k + t < kmid ? cr[t] : 0.0f;  // first bin
+              const float rb = cr[t] - ra;                   // second bin (or padding 0)
               const float pw[6] = {1.0f, uu, u2, u2 * uu, u2 * u2, u2 * u2 * uu};
 #pragma unroll
               for (int q = 0; q < 6; ++q) {
@@ -464,6 +482,9 @@ __global__ void __launch_bounds__(kThreads, 2)
               }
             }
           }
+          kbeg = nbeg;
+          kmid = nmid;
+          kend = nend;
           if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
           unsigned char* sa = base + (size_t)s * cf.stage;
 #pragma unroll
@@ -693,22 +714,31 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int r = tid - 128, al = r >> 2, c = r & 3;
         const int atom = s_atom[al];
         const float* dr = atom >= 0 ? dT + (size_t)atom * 4 * M + (size_t)c * M : nullptr;
+        // the next chunk's 16 values are loaded before this chunk's stage wait
+        float4 nx[4];
+        auto load16 = [&](int kc) {
+#pragma unroll
+          for (int k = 0; k < 16; k += 4) {
+            const int col = kc * 16 + k;
+            nx[k / 4] = (dr && col < M) ? __ldg(reinterpret_cast<const float4*>(dr + col))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        };
+        load16(0);
         uint32_t i = it;
         for (int kc = 0; kc < nkc; ++kc, ++i) {
           const int s = i % kNS;
           const uint32_t u = i / kNS;
-          if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
           float x[16];
 #pragma unroll
-          for (int k = 0; k < 16; k += 4) {
-            const int col = kc * 16 + k;
-            const float4 v = (dr && col < M) ? __ldg(reinterpret_cast<const float4*>(dr + col))
-                                             : make_float4(0.f, 0.f, 0.f, 0.f);
-            x[k] = v.x;
-            x[k + 1] = v.y;
-            x[k + 2] = v.z;
-            x[k + 3] = v.w;
+          for (int k = 0; k < 4; ++k) {
+            x[4 * k] = nx[k].x;
+            x[4 * k + 1] = nx[k].y;
+            x[4 * k + 2] = nx[k].z;
+            x[4 * k + 3] = nx[k].w;
           }
+          if (kc + 1 < nkc) load16(kc + 1);
+          if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
           unsigned char* sa = base + (size_t)s * cf.stage;
 #pragma unroll
           for (int kg = 0; kg < 2; ++kg) {
