@@ -175,7 +175,8 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
                                          const uint32_t* __restrict__ nlist,
                                          const int32_t* __restrict__ nn, int cap,
                                          const CellGeom& g, const EnvParams& ep, int scap, int* hist,
-                                         int nbins, float* __restrict__ sc, float4* stg,
+                                         int nbins, float4* __restrict__ scR,
+                                         float* __restrict__ scU, float4* stg,
                                          float4* __restrict__ pout, int lane, int& nrange,
                                          int& nover, int& lo, int& hi) {
   for (int b = lane; b < nbins; b += 32) hist[b] = 0;
@@ -260,13 +261,10 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
       // (streaming stores, evict-first in L2: read back only by the backward,
       // they should not push the L2-resident scratch out)
       __stcs(pout + pos, make_float4(P.dx, P.dy, P.dz, sa.y));
-      // planar rows: R0 R1 R2 R3 u, each kAtoms * scap apart
-      const size_t st = (size_t)kAtoms * scap;
-      sc[pos] = P.s;
-      sc[st + pos] = P.s * P.dx * P.ir;
-      sc[2 * st + pos] = P.s * P.dy * P.ir;
-      sc[3 * st + pos] = P.s * P.dz * P.ir;
-      sc[4 * st + pos] = P.u;
+      // the pair's row of R (one 16-byte record: the four generator threads
+      // of the atom read it as one sector) and its u
+      scR[pos] = make_float4(P.s, P.s * P.dx * P.ir, P.s * P.dy * P.ir, P.s * P.dz * P.ir);
+      scU[pos] = P.u;
     }
   }
   __syncwarp();
@@ -341,7 +339,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (lane == 0) s_atom[al] = atom;
       int lo, hi;
       const int np = sort_atom(atom, off, nlist, nn, cap, g, ep, scap, whist, nbins,
-                               sc_cta + (size_t)al * scap, wstg,
+                               reinterpret_cast<float4*>(sc_cta) + (size_t)al * scap,
+                               sc_cta + 4 * (size_t)kAtoms * scap + (size_t)al * scap, wstg,
                                pairs_out + ((size_t)tile * kAtoms + al) * scap, lane, nrange,
                                nover, lo, hi);
       // bin ends of this atom (<= N_m + 32 < 2^16)
@@ -430,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int r = tid - 128, al = r >> 2, c = r & 3;
         const uint16_t* hist = shist + al * cf.nbp;
         const size_t st = (size_t)kAtoms * scap;
-        const float* Rc = sc_cta + (size_t)c * st + (size_t)al * scap;
+        const float* Rc = sc_cta + (size_t)al * scap * 4 + c;  // stride 4: R records
         const float* Us = sc_cta + 4 * st + (size_t)al * scap;
         auto bounds = [&](int kc, int& kb, int& km, int& ke) {
           const int b0 = kb0 + 2 * kc;
@@ -443,7 +442,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
             const bool ok = k + t < ke;
-            rv[t] = ok ? Rc[k + t] : 0.0f;
+            rv[t] = ok ? Rc[4 * (k + t)] : 0.0f;
             uv[t] = ok ? Us[k + t] : 0.0f;
           }
         };
