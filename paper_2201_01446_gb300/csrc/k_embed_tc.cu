@@ -189,18 +189,24 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
   const uint32_t* L = nlist + (size_t)atom * cap;
   const unsigned below = (1u << lane) - 1u;
   int np = 0;
-  // two-deep software pipeline over the list: while round r computes, the
-  // offsets of round r + 1 and the list entries of round r + 2 are in flight
+  // three-deep software pipeline over the list: while round r computes, the
+  // offsets of rounds r + 1 and r + 2 and the list entries of round r + 3 are
+  // in flight
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   uint32_t e_cur = lane < cnt ? L[lane] : 0u;
-  float4 o_cur = lane < cnt ? off[e_cur >> 5] : make_float4(0.f, 0.f, 0.f, 0.f);
-  uint32_t e_nxt = 32 + lane < cnt ? L[32 + lane] : 0u;
+  uint32_t e_n1 = 32 + lane < cnt ? L[32 + lane] : 0u;
+  uint32_t e_n2 = 64 + lane < cnt ? L[64 + lane] : 0u;
+  float4 o_cur = lane < cnt ? off[e_cur >> 5] : z4;
+  float4 o_n1 = 32 + lane < cnt ? off[e_n1 >> 5] : z4;
   for (int b0 = 0; b0 < cnt; b0 += 32) {
     const int k = b0 + lane;
     const uint32_t e = e_cur;
     const float4 oj = o_cur;
-    if (k + 32 < cnt) o_cur = off[e_nxt >> 5];
-    e_cur = e_nxt;
-    if (k + 64 < cnt) e_nxt = L[k + 64];
+    o_cur = o_n1;
+    if (k + 64 < cnt) o_n1 = off[e_n2 >> 5];
+    e_cur = e_n1;
+    e_n1 = e_n2;
+    if (k + 96 < cnt) e_n2 = L[k + 96];
     bool in = false;
     int bin = 0;
     Pair Pk;
