@@ -68,6 +68,10 @@ def lib():
             "orc_eval_subset": (i, [p, p, d, d, i32p, i64, dp, i32p, dp, i64, i64p, dp,
                                     i64, i64p, dp]),
             "orc_md": (i, [p, p, d, d, i32p, i64, dp, dp, dp, i, i32p, dp, dp, d, i, dp]),
+            "orc_fit_param_count": (i64, [p]),
+            "orc_model_fit_params": (i, [p, i, dp, dp]),
+            "orc_table_set_coeffs": (i, [p, i, i, dp]),
+            "orc_param_grad": (i, [p, p, d, d, i32p, i64, dp, i32p, dp, dp, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -144,6 +148,26 @@ class Model:
             raise OracleError(e)
         return g, dg, d2g
 
+    @property
+    def n_fit_params(self) -> int:
+        """Length of one centre type's fitting-parameter layout (per layer k a
+        [(win_k + 1), wout_k] block: W_k rows then b_k; then w_out, b_out)."""
+        return int(lib().orc_fit_param_count(self.h))
+
+    def fit_params(self, ti):
+        out = np.zeros(self.n_fit_params)
+        e = lib().orc_model_fit_params(self.h, ti, _d(out), None)
+        if e:
+            raise OracleError(e)
+        return out
+
+    def set_fit_params(self, ti, values):
+        v = _f64(values)
+        assert v.size == self.n_fit_params
+        e = lib().orc_model_fit_params(self.h, ti, None, _d(v))
+        if e:
+            raise OracleError(e)
+
     def fit(self, ti, D):
         D = _f64(D)
         E = np.zeros(1)
@@ -180,6 +204,12 @@ class Table:
         if e:
             raise OracleError(e)
         return out
+
+    def set_coeffs(self, ti, tj, a):
+        a = _f64(a, (self.n, 6, self.model.M))
+        e = lib().orc_table_set_coeffs(self.h_ptr, ti, tj, _d(a))
+        if e:
+            raise OracleError(e)
 
     def eval(self, ti, tj, s):
         g, dg = np.zeros(self.model.M), np.zeros(self.model.M)
@@ -298,3 +328,24 @@ def md(model: Model, table, rc, rcs, sel, x, v, types, masses, box, dt, nsteps, 
     if code:
         raise OracleError(code)
     return x, v, f, th
+
+
+def param_grad(model: Model, table, rc, rcs, sel, x, types, box, with_table=True):
+    """(E, grad_fit [ntypes, n_fit_params], grad_table [ntypes, ntypes, n, 6, M]
+    or None): the energy's gradient with respect to the fitting parameters and
+    (tabulated model) the table coefficients of the normalised local variable
+    (s - k h)/h, i.e. c_q = a_q h^q."""
+    x, box = _f64(x), _f64(box)
+    types = np.ascontiguousarray(types, np.int32)
+    sel = _sel(sel, model.ntypes)
+    E = np.zeros(1)
+    gf = np.zeros((model.ntypes, model.n_fit_params))
+    gt = None
+    if with_table and table is not None:
+        gt = np.zeros((model.ntypes, model.ntypes, table.n, 6, model.M))
+    code = lib().orc_param_grad(model.h, table.handle if table is not None else None,
+                                float(rc), float(rcs), _i32(sel), len(x), _d(x), _i32(types),
+                                _d(box), _d(E), _d(gf), _d(gt) if gt is not None else None)
+    if code:
+        raise OracleError(code)
+    return float(E[0]), gf, gt

@@ -1159,3 +1159,244 @@ int orc_md(const orc_model* m, const orc_table* table, double rc, double rcs,
   }
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Parameter gradients: dE/d(fitting weights, biases) and dE/d(table        */
+/* coefficients) of the same energy (Sec. 2.1 network, Sec. 3.2 table)      */
+/* ------------------------------------------------------------------------ */
+/* per centre type: layer k as a [(win_k + 1)][wout_k] block (W_k rows, then
+ * b_k), then w_out and b_out as a [(w_last + 1)] block */
+int64_t orc_fit_param_count(const orc_model* m) {
+  if (!m) return -ORC_ERR_ARG;
+  int64_t c = 0;
+  int win = m->din;
+  for (int k = 0; k < m->n_fit; ++k) {
+    c += (int64_t)(win + 1) * m->fit_w[k];
+    win = m->fit_w[k];
+  }
+  return c + win + 1;
+}
+
+int orc_model_fit_params(orc_model* m, int ti, double* get, const double* set) {
+  if (!m || ti < 0 || ti >= m->ntypes) return ORC_ERR_ARG;
+  int64_t o = 0;
+  int win = m->din;
+  for (int k = 0; k < m->n_fit; ++k) {
+    const int wo = m->fit_w[k];
+    double* W = (double*)m->fit_W[ti][k];
+    double* b = (double*)m->fit_b[ti][k];
+    const size_t nw = (size_t)win * wo;
+    if (get) {
+      memcpy(get + o, W, sizeof(double) * nw);
+      memcpy(get + o + nw, b, sizeof(double) * wo);
+    }
+    if (set) {
+      memcpy(W, set + o, sizeof(double) * nw);
+      memcpy(b, set + o + nw, sizeof(double) * wo);
+    }
+    o += (int64_t)nw + wo;
+    win = wo;
+  }
+  double* wout = (double*)m->fit_wout[ti];
+  if (get) {
+    memcpy(get + o, wout, sizeof(double) * win);
+    get[o + win] = m->fit_bout[ti];
+  }
+  if (set) {
+    memcpy(wout, set + o, sizeof(double) * win);
+    m->fit_bout[ti] = set[o + win];
+  }
+  return ORC_OK;
+}
+
+int orc_table_set_coeffs(orc_table* t, int ti, int tj, const double* in) {
+  if (!t || !in || ti < 0 || tj < 0 || ti >= t->ntypes || tj >= t->ntypes) return ORC_ERR_ARG;
+  size_t sz = (size_t)t->n * 6 * t->M;
+  memcpy(t->a + (size_t)(ti * t->ntypes + tj) * sz, in, sizeof(double) * sz);
+  return ORC_OK;
+}
+
+/* The fitting net of type ti on D: E, dD = dE/dD and, added into g (the
+ * type's block of the gradient), dE/d(parameters).  Chain rule through
+ * z_k = [shortcut] z_{k-1} + act(z_{k-1} W_k + b_k), E = z_last . w + b:
+ * with gz_k = dE/dz_k and gp_k = gz_k act'(a_k),
+ *   dE/dW_k[r][c] = in_k[r] gp_k[c],  dE/db_k = gp_k,
+ *   gz_{k-1} = gp_k W_k^T + [shortcut] gz_k,  dE/dw = z_last, dE/db = 1. */
+static int fit_grad(const orc_model* m, int ti, const double* D, double* E, double* dD,
+                    double* g) {
+  const int nf = m->n_fit;
+  int wid[MAXL + 1];
+  wid[0] = m->din;
+  for (int k = 0; k < nf; ++k) wid[k + 1] = m->fit_w[k];
+  size_t zoff[MAXL + 1], goff[MAXL + 1];
+  zoff[0] = 0;
+  goff[0] = 0;
+  for (int k = 0; k < nf; ++k) {
+    zoff[k + 1] = zoff[k] + (size_t)wid[k + 1];
+    goff[k + 1] = goff[k] + (size_t)(wid[k] + 1) * wid[k + 1];
+  }
+  int wmax = m->din;
+  for (int k = 1; k <= nf; ++k) wmax = wid[k] > wmax ? wid[k] : wmax;
+  double* z = (double*)malloc(sizeof(double) * (2 * zoff[nf] + 3 * (size_t)wmax));
+  if (!z) return ORC_ERR_NOMEM;
+  double* dact = z + zoff[nf];
+  double* gz = dact + zoff[nf];
+  double* gn = gz + wmax;
+  double* gp = gn + wmax;
+  for (int k = 0; k < nf; ++k) {
+    const double* in = k ? z + zoff[k - 1] : D;
+    const int wi = wid[k], wo = wid[k + 1];
+    const int shortcut = (k > 0 && wo == wi);
+    for (int c = 0; c < wo; ++c) {
+      double a = m->fit_b[ti][k][c];
+      for (int r = 0; r < wi; ++r) a += in[r] * m->fit_W[ti][k][(size_t)r * wo + c];
+      double da;
+      const double t = orc_act(a, &da);
+      dact[zoff[k] + c] = da;
+      z[zoff[k] + c] = (shortcut ? in[c] : 0.0) + t;
+    }
+  }
+  const double* zl = z + zoff[nf - 1];
+  const int wl = wid[nf];
+  double e = m->fit_bout[ti];
+  for (int c = 0; c < wl; ++c) e += zl[c] * m->fit_wout[ti][c];
+  *E = e;
+  double* gout = g + goff[nf];
+  for (int c = 0; c < wl; ++c) {
+    gout[c] += zl[c];
+    gz[c] = m->fit_wout[ti][c];
+  }
+  gout[wl] += 1.0;
+  for (int k = nf - 1; k >= 0; --k) {
+    const double* in = k ? z + zoff[k - 1] : D;
+    const int wi = wid[k], wo = wid[k + 1];
+    const int shortcut = (k > 0 && wo == wi);
+    double* gW = g + goff[k];
+    double* gb = gW + (size_t)wi * wo;
+    for (int c = 0; c < wo; ++c) {
+      gp[c] = gz[c] * dact[zoff[k] + c];
+      gb[c] += gp[c];
+    }
+    for (int r = 0; r < wi; ++r) {
+      double s = shortcut ? gz[r] : 0.0;
+      for (int c = 0; c < wo; ++c) {
+        gW[(size_t)r * wo + c] += in[r] * gp[c];
+        s += m->fit_W[ti][k][(size_t)r * wo + c] * gp[c];
+      }
+      gn[r] = s;
+    }
+    double* sw = gz;
+    gz = gn;
+    gn = sw;
+  }
+  memcpy(dD, gz, sizeof(double) * m->din);
+  free(z);
+  return ORC_OK;
+}
+
+/* E and the parameter gradients of the whole system.  grad_fit: the blocks
+ * of every centre type in type order (orc_fit_param_count each).
+ * grad_table (tabulated model only, may be NULL): [ntypes*ntypes][n][6][M]
+ * with respect to the coefficients c_q = a_q h^q of the normalised local
+ * variable v = (s - k h)/h, the form the CUDA library stores.  Since
+ *   T_i[c][x] = (1/N_m) sum_j R_jc sum_q c_q[x] v_j^q,
+ * dE/dc[k][q][x] = (1/N_m) sum_i sum_{j in interval k} (sum_c dE/dT_i[c][x] R_jc) v_j^q.
+ * Serial over atoms (a fixed summation order). */
+int orc_param_grad(const orc_model* m, const orc_table* table, double rc, double rcs,
+                   const int32_t* sel, int64_t n, const double* x, const int32_t* types,
+                   const double* box, double* energy, double* grad_fit, double* grad_table) {
+  if (!grad_fit || !energy) return ORC_ERR_ARG;
+  if (grad_table && !table) return ORC_ERR_ARG;
+  ctx_t C;
+  cells_t cells;
+  int e = ctx_setup(&C, &cells, m, table, rc, rcs, sel, n, x, types, box);
+  if (e) return e;
+  const int64_t per = orc_fit_param_count(m);
+  const int M = m->M, mlt = m->m_lt;
+  memset(grad_fit, 0, sizeof(double) * (size_t)per * m->ntypes);
+  if (grad_table)
+    memset(grad_table, 0, sizeof(double) * (size_t)m->ntypes * m->ntypes * table->n * 6 * M);
+  const double inv_nm = 1.0 / (double)C.Nm;
+  work_t w;
+  double* Ei = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* dEdg = (double*)malloc(sizeof(double) * (size_t)M);
+  e = work_init(&w, m, cap_for(&C));
+  if (!Ei || !dEdg) e = e ? e : ORC_ERR_NOMEM;
+  int flags = 0;
+  for (int64_t i = 0; i < n && !e; ++i) {
+    const int ti = types[i];
+    int64_t k = cells_neighbors(C.cells, i, rc, w.nb, w.cap);
+    if (k > w.cap) {
+      e = ORC_ERR_SEL;
+      break;
+    }
+    int cnt_t[MAXT] = {0};
+    for (int64_t q = 0; q < k; ++q) cnt_t[types[w.nb[q].j]]++;
+    for (int t = 0; t < m->ntypes; ++t)
+      if (cnt_t[t] > sel[t]) flags |= 1;
+    /* T (Eq. 1 rows, table or net, 1/N_m) and D (Eq. 2), as orc_eval */
+    for (int c = 0; c < 4 * M; ++c) w.T[c] = 0.0;
+    for (int64_t q = 0; q < k; ++q) {
+      const int tj = types[w.nb[q].j];
+      double* R = w.R + q * 4;
+      const double s = orc_env_row(w.nb[q].d, rc, rcs, R, w.dR + q * 12);
+      double* G = w.G + q * M;
+      if (table) {
+        if (orc_table_eval(table, ti, tj, s, G, w.dG + q * M)) flags |= 2;
+      } else {
+        orc_embed(m, ti, tj, s, G, w.dG + q * M, NULL);
+      }
+      for (int c = 0; c < 4; ++c)
+        for (int a = 0; a < M; ++a) w.T[c * M + a] += R[c] * G[a] * inv_nm;
+    }
+    for (int b = 0; b < M; ++b)
+      for (int a = 0; a < mlt; ++a) {
+        double s = 0.0;
+        for (int c = 0; c < 4; ++c) s += w.T[c * M + b] * w.T[c * M + a];
+        w.D[b * mlt + a] = s;
+      }
+    e = fit_grad(m, ti, w.D, &Ei[i], w.dD, grad_fit + (size_t)ti * per);
+    if (e || !grad_table) continue;
+    /* dE/dT from dE/dD (both factors of Eq. 2) */
+    for (int c = 0; c < 4; ++c)
+      for (int a = 0; a < M; ++a) {
+        double s = 0.0;
+        for (int b = 0; b < mlt; ++b) s += w.dD[a * mlt + b] * w.T[c * M + b];
+        if (a < mlt)
+          for (int b = 0; b < M; ++b) s += w.dD[b * mlt + a] * w.T[c * M + b];
+        w.dT[c * M + a] = s;
+      }
+    for (int64_t q = 0; q < k; ++q) {
+      const int tj = types[w.nb[q].j];
+      const double* R = w.R + q * 4;
+      /* the interval and local variable of orc_table_eval */
+      const double s = R[0];
+      const double fk = floor(s / table->h);
+      int kk = (int)fk;
+      if (fk < 0) kk = 0;
+      if (fk > table->n - 1) kk = table->n - 1;
+      const double v = (s - kk * table->h) / table->h;
+      for (int a = 0; a < M; ++a) {
+        double g = 0.0;
+        for (int c = 0; c < 4; ++c) g += w.dT[c * M + a] * R[c];
+        dEdg[a] = g * inv_nm;
+      }
+      double* out = grad_table + ((size_t)(ti * m->ntypes + tj) * table->n + kk) * 6 * M;
+      double vp = 1.0;
+      for (int p = 0; p < 6; ++p) {
+        for (int a = 0; a < M; ++a) out[p * M + a] += dEdg[a] * vp;
+        vp *= v;
+      }
+    }
+  }
+  if (!e) {
+    *energy = neumaier(Ei, n);
+    if (flags & 1) e = ORC_ERR_SEL;
+    else if (flags & 2) e = ORC_ERR_TABLE_RANGE;
+  }
+  work_free(&w);
+  free(Ei);
+  free(dEdg);
+  cells_free(&cells);
+  return e;
+}

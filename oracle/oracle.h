@@ -121,6 +121,24 @@ int orc_md(const orc_model* m, const orc_table* table, double rc, double rcs,
            const int32_t* types, const double* mass_of_type, const double* box,
            double dt, int nsteps, double* thermo);
 
+/* Parameter gradients of the same energy.  Per centre type the fitting
+ * parameters are laid out as one [(win_k + 1)][wout_k] block per layer k
+ * (W_k rows, then b_k) followed by [(w_last + 1)] (w_out, then b_out);
+ * orc_fit_param_count gives the length of one type's layout. */
+int64_t orc_fit_param_count(const orc_model* m);
+/* copy type ti's fitting parameters out (get) and/or replace them (set) */
+int orc_model_fit_params(orc_model* m, int ti, double* get, const double* set);
+/* replace the coefficients of pair (ti,tj) ([n][6][M], local variable s - k*h) */
+int orc_table_set_coeffs(orc_table* t, int ti, int tj, const double* in);
+/* energy and dE/d(fitting parameters) of all centre types (grad_fit:
+ * ntypes x orc_fit_param_count) and, for a tabulated model, dE/d(table
+ * coefficients) grad_table [ntypes*ntypes][n][6][M] (may be NULL) with
+ * respect to c_q = a_q h^q, the coefficients of the normalised local
+ * variable (s - k*h)/h */
+int orc_param_grad(const orc_model* m, const orc_table* table, double rc, double rcs,
+                   const int32_t* sel, int64_t n, const double* x, const int32_t* types,
+                   const double* box, double* energy, double* grad_fit, double* grad_table);
+
 #ifdef __cplusplus
 }
 #endif
