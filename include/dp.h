@@ -194,6 +194,32 @@ dp_status dp_fitting(dp_handle* h, int64_t natoms, const int32_t* types, const f
                      double* e_out, float* dT_out);
 
 /* ---------------------------------------------------------------------------
+ * Parameter gradients (training use of the same energy, Sec. 2.1 and 3.2):
+ * dE/d(fitting-net parameters) and dE/d(table coefficients).
+ *
+ * Fitting layout, per model type in type order, per hidden layer k a block of
+ * [(win_k + 1)][wout_k] doubles (W_k row-major, then b_k), then [(w_last + 1)]
+ * (w_out, then b_out).  Table layout: [ntypes][ntypes][n][6][M], the layout
+ * of dp_table_coeffs: the derivative with respect to c[k][q][:], the
+ * coefficient of u^q with u = s/h - k.
+ * ------------------------------------------------------------------------- */
+/* *n_fit: doubles of the fitting gradient (all types); *n_table: doubles of
+ * the table gradient.  Either pointer may be NULL. */
+dp_status dp_param_sizes(dp_handle* h, int64_t* n_fit, int64_t* n_table);
+
+/* Energy and its parameter gradients for one configuration (HOST arrays,
+ * the conventions of dp_compute).  The fitting stage runs on the FP32 CUDA
+ * cores whatever fit_precision says; the gradients are summed per chunk in
+ * FP32 and across chunks in FP64 (deterministic).
+ *   grad_fit   HOST [n_fit] (required, overwritten);
+ *   grad_table HOST [n_table] or NULL.  Needs tabulated = 1 and
+ *              embed_precision = 2 (DP_ERR_UNIMPLEMENTED otherwise).
+ * Errors as dp_compute (DP_ERR_SEL_OVERFLOW, DP_ERR_TABLE_RANGE, ...). */
+dp_status dp_param_grad(dp_handle* h, int64_t natoms, const double* coords,
+                        const int32_t* types, const double* box, double* energy,
+                        double* grad_fit, double* grad_table);
+
+/* ---------------------------------------------------------------------------
  * Profiling: per-phase device time measured with CUDA events recorded on the
  * handle's stream around each phase's kernels.
  * ------------------------------------------------------------------------- */

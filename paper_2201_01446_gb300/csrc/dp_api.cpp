@@ -99,6 +99,7 @@ struct dp_handle {
   DevBuf emb64, emb_off, table, fit32, sel_dev, map_dev, status;
   DevBuf tabF, tabB, tc_scratch;  // tensor-core embedding: tiled table pieces, per-CTA scratch
   DevBuf tanh_tab;                // Sec. 3.5 tanh table of the fitting net (tanh_table = 1)
+  DevBuf pg, pg_fit_part, pg_tab_part;  // parameter gradients: FP64 result, FP32 partials
   int n_int = 0;
   double h = 0.0;
   FitNet nets[DP_MAXT];
@@ -1160,6 +1161,94 @@ dp_status dp_fitting(dp_handle* h, int64_t natoms, const int32_t* types, const f
 }
 
 // ---------------------------------------------------------------------- MD
+static int64_t fit_params_per_type(const dp_handle* h) {
+  int64_t c = 0;
+  int win = h->din;
+  for (int k = 0; k < h->n_fit; ++k) {
+    c += (int64_t)(win + 1) * h->fit_w[k];
+    win = h->fit_w[k];
+  }
+  return c + win + 1;
+}
+
+dp_status dp_param_sizes(dp_handle* h, int64_t* n_fit, int64_t* n_table) {
+  CKS(check_handle(h));
+  if (n_fit) *n_fit = fit_params_per_type(h) * h->ntypes;
+  if (n_table) *n_table = (int64_t)h->ntypes * h->ntypes * h->n_int * 6 * h->M;
+  return DP_OK;
+}
+
+dp_status dp_param_grad(dp_handle* h, int64_t natoms, const double* coords, const int32_t* types,
+                        const double* box, double* energy, double* grad_fit,
+                        double* grad_table) {
+  CKS(check_handle(h));
+  if (natoms < 0 || !box || !energy || !grad_fit || (natoms > 0 && (!coords || !types)))
+    return fail(h, DP_ERR_ARG, "null pointer or negative atom count");
+  if (natoms >= (1LL << 27)) return fail(h, DP_ERR_ARG, "at most 2^27 atoms per call");
+  if (grad_table && !(h->opt.tabulated && h->opt.embed_precision == 2))
+    return fail(h, DP_ERR_UNIMPLEMENTED,
+                "table gradients need the tabulated tensor-core embedding (embed_precision 2)");
+  double L[3];
+  CKS(box_lengths(h, box, L));
+  Work& w = h->w;
+  CKS(load_coords(h, w, natoms, coords, types, 0));
+  CKS(clear_status(h));
+  CKS(rebuild(h, w, L, h->rc));
+  CKS(status_errors(h));
+  const int64_t per = fit_params_per_type(h);
+  const int64_t nfit = per * h->ntypes;
+  const int64_t ntab = (int64_t)h->ntypes * h->ntypes * h->n_int * 6 * h->M;
+  CK(ensure(h->pg, sizeof(double) * (size_t)(nfit + ntab)), "alloc gradients");
+  CK(cudaMemsetAsync(h->pg.p, 0, sizeof(double) * (size_t)(nfit + ntab), h->st), "memset");
+  const int64_t n = natoms;
+  if (n > 0) {
+    const EnvParams ep = env_params(h);
+    CK(cudaMemsetAsync(w.pairs.p, 0, sizeof(unsigned long long), h->st), "memset");
+    CKS(embed_forward(h, w, ep));
+    // the fitting stage on the FP32 CUDA-core path, which keeps every
+    // layer's input and gradient for the parameter gradients
+    for (int t = 0; t < h->ntypes; ++t) {
+      const int64_t cnt = w.have_idx ? w.type_count[t] : n;
+      if (cnt == 0) continue;
+      const int32_t* idx = w.have_idx ? P<int32_t>(w.idx) + w.type_off[t] : nullptr;
+      CKS(ensure_fit_scratch(h, cnt));
+      const int64_t pf = fit_grad_part_floats(h->nets[t], h->din, h->fs.rows);
+      CK(ensure(h->pg_fit_part, sizeof(float) * (size_t)pf), "alloc gradient partials");
+      FitGrad fg{P<double>(h->pg) + (size_t)t * per, P<float>(h->pg_fit_part), pf};
+      if (fit_simt(h->st, cnt, idx, h->nets[t], h->M, h->m_lt, P<float>(w.T), P<float>(w.dT),
+                   P<double>(w.e_atom), h->fs, &fg))
+        return fail(h, DP_ERR_CUDA, "fitting kernels failed to launch");
+      if (!w.have_idx) break;
+    }
+    if (grad_table) {
+      const int64_t tp = tab_grad_part_floats(ep);
+      CK(ensure(h->pg_tab_part, sizeof(float) * (size_t)tp), "alloc gradient partials");
+      if (launch_tab_grad_tc(h->st, w.tiles, P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist),
+                             P<int2>(w.tc_range), ep, P<float>(w.dT), P<float>(h->pg_tab_part),
+                             P<double>(h->pg) + nfit))
+        return fail(h, DP_ERR_UNIMPLEMENTED, "table gradient cannot run this model shape");
+    }
+    launch_sum_rows(h->st, n, 1, P<double>(w.e_atom), P<double>(w.red_part), P<double>(w.red_out));
+    launch_check_energy(h->st, n, P<double>(w.e_atom), P<int32_t>(h->status));
+    CK(cudaGetLastError(), "gradient kernels");
+  } else {
+    CK(cudaMemsetAsync(w.red_out.p, 0, sizeof(double), h->st), "memset");
+  }
+  CKS(read_status(h));
+  CKS(status_errors(h));
+  CK(cudaMemcpyAsync(energy, w.red_out.p, sizeof(double), cudaMemcpyDeviceToHost, h->st),
+     "energy copy");
+  CK(cudaMemcpyAsync(grad_fit, h->pg.p, sizeof(double) * (size_t)nfit, cudaMemcpyDeviceToHost,
+                     h->st),
+     "gradient copy");
+  if (grad_table)
+    CK(cudaMemcpyAsync(grad_table, P<double>(h->pg) + nfit, sizeof(double) * (size_t)ntab,
+                       cudaMemcpyDeviceToHost, h->st),
+       "gradient copy");
+  CK(cudaStreamSynchronize(h->st), "gradient copy");
+  return DP_OK;
+}
+
 dp_status dp_system_create(dp_handle* h, int64_t natoms, const double* x, const double* v,
                            const int32_t* types, const double* mass_of_type, const double* box,
                            int device_ptrs, dp_system** out) {

@@ -113,6 +113,13 @@ int64_t tab_tc_slots();  // virial partial slots the backward writes
 // 0 if the tensor-core embedding can run this shape; -1 embedding width (M <=
 // 128, M % 4 == 0), -2 too many table bins for the shared-memory histograms
 int tab_tc_supported(const EnvParams& ep);
+// dE/d(table coefficients) [ntypes][ntypes][n_int][6][M] (FP64, the layout of
+// the device table) from the forward's sorted pairs, bin ends and ranges and
+// dE/dT; part: tab_grad_part_floats floats of per-CTA partials
+int64_t tab_grad_part_floats(const EnvParams& ep);
+int launch_tab_grad_tc(cudaStream_t st, const TileMap& tm, const float4* pairs,
+                       const uint16_t* hist, const int2* range, const EnvParams& ep,
+                       const float* dT, float* part, double* grad);
 int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, const uint32_t* nlist,
                       const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
                       const __nv_bfloat16* tabF, float* scratch, float4* pairs_out,
@@ -161,8 +168,19 @@ struct FitScratch {
 };
 // E_i and dE/dT for atoms [0, n) of one centre type listed in idx (or all
 // atoms when idx == NULL), FP32 CUDA-core path.
+// With fg != NULL the same pass also adds dE/d(parameters) of this type's net
+// into fg->g (FP64; per layer k a [(win_k + 1)][wout_k] block, W_k rows then
+// b_k, then [(w_last + 1)]: w_out, b_out), through FP32 partials in fg->part.
+struct FitGrad {
+  double* g;
+  float* part;
+  int64_t part_floats;
+};
 int fit_simt(cudaStream_t st, int64_t n, const int32_t* idx, const FitNet& net, int M, int m_lt,
-             const float* T, float* dT, double* e_atom, const FitScratch& s);
+             const float* T, float* dT, double* e_atom, const FitScratch& s,
+             const FitGrad* fg = nullptr);
+// floats of fg->part that fit_simt needs for a net and chunk size
+int64_t fit_grad_part_floats(const FitNet& net, int din, int64_t rows);
 
 // Tensor-core (tcgen05, BF16 operands, FP32 accumulate) fitting stage.  Each
 // BF16 operand has 1 piece (BF16 mode) or 3 pieces x = h + m + l (FP32-

@@ -949,6 +949,136 @@ __global__ void __launch_bounds__(kThreads, 2)
                  "r"(kTmemCols));
 }
 
+// ------------------------------------------------------------------ table gradient
+// dE/dc[ti][b][q][m] = (1/N_m) sum over the rows (atom i of type ti, c) of
+//   C[(i,c)][(b,q)] dE/dT_i[c][m],   C[(i,c)][(b,q)] = sum_{j in bin b} R_jc u_j^q
+// (T is linear in the table: the forward's contraction read the other way).
+// Per tile of the forward (its sorted displacements, bin ends and bin
+// range): the tile's dE/dT rows in shared memory; per window of 16 bins the
+// window's C is recomputed from the sorted displacements (the arithmetic of
+// the forward's sort) and multiplied with dE/dT on the CUDA cores; the
+// products go into the CTA's own FP32 partial (read-modify-write, no
+// atomics).  A second kernel sums the partials over the CTAs in FP64, in CTA
+// order, so the result is deterministic.
+constexpr int kGWin = 16;            // bins per window
+constexpr int kGCs = kGWin * 6 + 4;  // floats per row of the C window
+
+__host__ __device__ inline int grad_mp(int M) { return (M + 3) / 4 * 4; }
+__host__ __device__ inline size_t grad_smem(const EnvParams& ep) {
+  const int nbp = (ep.ntypes * ep.n_int + 7) & ~7;
+  return 128 + (size_t)kRows * grad_mp(ep.M) * 4 + (size_t)kRows * kGCs * 4 +
+         (size_t)kAtoms * nbp * 2;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tab_grad_tc(int64_t ntile, TileMap tm, const float4* __restrict__ pairs,
+                  const uint16_t* __restrict__ hist_in, const int2* __restrict__ range_in,
+                  EnvParams ep, int scap, const float* __restrict__ dT, float* __restrict__ part) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  const int M = ep.M, MP = grad_mp(M);
+  const int nbins = ep.ntypes * ep.n_int;
+  const int nbp = (nbins + 7) & ~7;
+  float* dTs = (float*)base;                   // [kRows][MP]
+  float* Cs = dTs + (size_t)kRows * MP;        // [kRows][kGCs]
+  uint16_t* shist = (uint16_t*)(Cs + (size_t)kRows * kGCs);  // [kAtoms][nbp]
+  __shared__ int s_atom[kAtoms];
+  const int tid = threadIdx.x;
+  float* part_cta = part + (size_t)blockIdx.x * ep.ntypes * nbins * 6 * M;
+
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int ti = tile_type(tm, tile);
+    {
+      const int4* hi4 = reinterpret_cast<const int4*>(hist_in + (size_t)tile * kAtoms * nbp);
+      int4* hs = reinterpret_cast<int4*>(shist);
+      for (int q = tid; q < kAtoms * nbp / 8; q += kThreads) hs[q] = hi4[q];
+      if (tid < kAtoms) s_atom[tid] = tile_atom(tm, ti, tile, tid);
+    }
+    __syncthreads();
+    for (int q = tid; q < kRows * M; q += kThreads) {
+      const int r = q / M, m = q - r * M;
+      const int atom = s_atom[r >> 2];
+      dTs[r * MP + m] = atom >= 0 ? dT[(size_t)atom * 4 * M + (size_t)(r & 3) * M + m] : 0.0f;
+    }
+    const int2 rg = range_in[tile];
+    const int kb0 = rg.x, nbt = 2 * rg.y;
+    for (int w0 = kb0; w0 < kb0 + nbt; w0 += kGWin) {
+      const int wb = min(kGWin, kb0 + nbt - w0);
+      {
+        // C window: thread (row r = (al, c), half hh) builds 8 bins of its row
+        const int r = tid & (kRows - 1), hh = tid >> 7;
+        const int al = r >> 2, c = r & 3;
+        const int atom = s_atom[al];
+        const uint16_t* hist = shist + al * nbp;
+        const float4* pr = pairs + ((size_t)tile * kAtoms + al) * scap;
+        for (int j = hh * 8; j < hh * 8 + 8; ++j) {
+          const int b = w0 + j;
+          float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          if (j < wb && b < nbins && atom >= 0) {
+            const int tj = b / ep.n_int;
+            const int kend = hist[b];
+            for (int k = bin_begin16(hist, b); k < kend; ++k) {
+              const float4 q4 = pr[k];
+              const float r2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z;
+              Pair P;
+              pair_geom(ep, q4.x, q4.y, q4.z, r2, tj, P);
+              const float d = c == 1 ? P.dx : (c == 2 ? P.dy : P.dz);
+              const float Rc = c == 0 ? P.s : P.s * d * P.ir;
+              float up = Rc;
+#pragma unroll
+              for (int t = 0; t < 6; ++t) {
+                acc[t] += up;
+                up *= P.u;
+              }
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < 6; ++t) Cs[r * kGCs + j * 6 + t] = acc[t];
+        }
+      }
+      __syncthreads();
+      {
+        // the window's products: thread (column m, half hh) owns 48 (b, q)
+        const int m = tid & (kRows - 1), hh = tid >> 7;
+        if (m < M) {
+          float acc[48];
+#pragma unroll
+          for (int j = 0; j < 48; ++j) acc[j] = 0.0f;
+          for (int r = 0; r < kRows; ++r) {
+            const float a = dTs[r * MP + m];
+            const float4* cr = reinterpret_cast<const float4*>(Cs + r * kGCs + hh * 48);
+#pragma unroll
+            for (int v = 0; v < 12; ++v) {
+              const float4 c4 = cr[v];
+              acc[4 * v] = fmaf(c4.x, a, acc[4 * v]);
+              acc[4 * v + 1] = fmaf(c4.y, a, acc[4 * v + 1]);
+              acc[4 * v + 2] = fmaf(c4.z, a, acc[4 * v + 2]);
+              acc[4 * v + 3] = fmaf(c4.w, a, acc[4 * v + 3]);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 48; ++j) {
+            const int bq = hh * 48 + j, b = w0 + bq / 6;
+            if (bq < wb * 6 && b < nbins)
+              part_cta[((size_t)(ti * nbins + b) * 6 + bq % 6) * M + m] += acc[j];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// out[e] = (1/N_m) sum over the CTAs (in order) of part[cta][e]
+__global__ void k_tab_grad_reduce(int nct, int64_t n, const float* __restrict__ part,
+                                  float inv_nm, double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double s = 0.0;
+  for (int k = 0; k < nct; ++k) s += (double)part[(size_t)k * n + e];
+  out[e] = s * (double)inv_nm;
+}
+
 int g_sms = 0;
 int sm_count() {
   if (!g_sms) {
@@ -1042,6 +1172,38 @@ int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs,
   DP_LAUNCHED(1);
   k_tab_bwd_tc<<<tc_grid(), kThreads, cf.smem, st>>>(ntile, tm, pairs, hist, range, ep, tabB,
                                                      stage_cap_tc(ep), dT, ffix, vir_part, status);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// ------------------------------------------------------------------ table gradient
+int64_t tab_grad_part_floats(const EnvParams& ep) {
+  return (int64_t)sm_count() * ep.ntypes * ep.ntypes * ep.n_int * 6 * ep.M;
+}
+
+int launch_tab_grad_tc(cudaStream_t st, const TileMap& tm, const float4* pairs,
+                       const uint16_t* hist, const int2* range, const EnvParams& ep,
+                       const float* dT, float* part, double* grad) {
+  if (ep.M > 128 || ep.M % 4 || ep.M < 16) return -1;
+  if (tm.ntypes < 1 || tm.ntypes > DP_MAXT || tm.ntypes != ep.ntypes) return -1;
+  if (((uintptr_t)hist & 15) || ((uintptr_t)part & 15)) return -1;
+  const int64_t n = (int64_t)ep.ntypes * ep.ntypes * ep.n_int * 6 * ep.M;
+  const int64_t ntile = tm.tile_off[tm.ntypes];
+  const size_t smem = grad_smem(ep);
+  if (smem > 225 * 1024) return -1;
+  static size_t set = 0;
+  if (smem > 48 * 1024 && smem > set) {
+    if (cudaFuncSetAttribute(k_tab_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return -3;
+    set = smem;
+  }
+  const int grid = sm_count();
+  if (cudaMemsetAsync(part, 0, sizeof(float) * (size_t)grid * n, st) != cudaSuccess) return -3;
+  DP_LAUNCHED(2);
+  if (ntile > 0)
+    k_tab_grad_tc<<<grid, kThreads, smem, st>>>(ntile, tm, pairs, hist, range, ep,
+                                                stage_cap_tc(ep), dT, part);
+  k_tab_grad_reduce<<<(int)((n + 255) / 256), 256, 0, st>>>(grid, n, part, ep.inv_nm, grad);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

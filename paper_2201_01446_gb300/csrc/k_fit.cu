@@ -202,13 +202,113 @@ __global__ void k_gp_last(int64_t rows, int W, const float* __restrict__ d,
   gp[k] = w[k % W] * d[k];
 }
 
+// Parameter gradients of one layer over a chunk of rows:
+//   part[s][r][c] = sum over the rows i of split s of Xe[i][r] Ge[i][c]
+// with Xe = [X | 1] (row r == win: the bias) and Ge = G, or a column of ones
+// when G == NULL (the output layer: dE/dw_out = sum_i z_i, dE/db_out = rows).
+// 64 x 64 output tiles, 4 x 4 per thread, rows staged 16 at a time.
+__global__ void __launch_bounds__(256) k_wgrad_part(int rows, int per_split,
+                                                    const float* __restrict__ X, int ldx, int win,
+                                                    const float* __restrict__ G, int ldg, int wo,
+                                                    float* __restrict__ part) {
+  __shared__ float Xs[16][64], Gs[16][64];
+  const int r0 = blockIdx.x * 64, c0 = blockIdx.y * 64, sp = blockIdx.z;
+  const int i_beg = sp * per_split, i_end = min(rows, i_beg + per_split);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+  for (int i0 = i_beg; i0 < i_end; i0 += 16) {
+    for (int q = threadIdx.x; q < 16 * 64; q += 256) {
+      const int ii = q >> 6, cc = q & 63, i = i0 + ii;
+      const int r = r0 + cc, c = c0 + cc;
+      const bool in = i < i_end;
+      Xs[ii][cc] = (in && r <= win) ? (r < win ? X[(size_t)i * ldx + r] : 1.0f) : 0.0f;
+      Gs[ii][cc] = (in && c < wo) ? (G ? G[(size_t)i * ldg + c] : 1.0f) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float xa[4], gb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xa[a] = Xs[kk][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) gb[b] = Gs[kk][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], gb[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int r = r0 + ty * 4 + a;
+    if (r > win) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = c0 + tx * 4 + b;
+      if (c < wo) part[((size_t)sp * (win + 1) + r) * wo + c] = acc[a][b];
+    }
+  }
+}
+
+// g[e] += sum over the splits (in order) of part[s][e], in FP64
+__global__ void k_wgrad_add(int nsplit, int64_t n, const float* __restrict__ part,
+                            double* __restrict__ g) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += (double)part[(size_t)k * n + e];
+  g[e] += s;
+}
+
+int wgrad_splits(int rows, int win, int wo) {
+  const int tiles = ((win + 1 + 63) / 64) * ((wo + 63) / 64);
+  int sp = (2 * 152 + tiles - 1) / tiles;
+  const int maxsp = (rows + 255) / 256;
+  return sp < 1 ? 1 : (sp > maxsp ? (maxsp < 1 ? 1 : maxsp) : sp);
+}
+
+// g_block [(win + 1)][wo] += [X | 1]^T G over rows
+void wgrad(cudaStream_t st, int rows, const float* X, int ldx, int win, const float* G, int ldg,
+           int wo, const FitGrad& fg, double* g_block) {
+  int sp = wgrad_splits(rows, win, wo);
+  const int64_t n = (int64_t)(win + 1) * wo;
+  while (sp > 1 && (int64_t)sp * n > fg.part_floats) --sp;
+  const int per = ((rows + sp - 1) / sp + 15) / 16 * 16;
+  dim3 grid((win + 1 + 63) / 64, (wo + 63) / 64, sp);
+  DP_LAUNCHED(2);
+  k_wgrad_part<<<grid, 256, 0, st>>>(rows, per, X, ldx, win, G, ldg, wo, fg.part);
+  k_wgrad_add<<<(int)((n + 255) / 256), 256, 0, st>>>(sp, n, fg.part, g_block);
+}
+
 }  // namespace
 
+int64_t fit_grad_part_floats(const FitNet& net, int din, int64_t rows) {
+  int64_t mx = 0;
+  int win = din;
+  for (int k = 0; k < net.nl; ++k) {
+    const int64_t v = (int64_t)wgrad_splits((int)rows, win, net.wout[k]) * (win + 1) * net.wout[k];
+    mx = v > mx ? v : mx;
+    win = net.wout[k];
+  }
+  const int64_t v = (int64_t)wgrad_splits((int)rows, win, 1) * (win + 1);
+  return v > mx ? v : mx;
+}
+
 int fit_simt(cudaStream_t st, int64_t n, const int32_t* idx, const FitNet& net, int M, int m_lt,
-             const float* T, float* dT, double* e_atom, const FitScratch& s) {
+             const float* T, float* dT, double* e_atom, const FitScratch& s,
+             const FitGrad* fg) {
   if (n <= 0) return 0;
   const int din = M * m_lt;
   const int nl = net.nl;
+  // offsets of the layers' gradient blocks
+  int64_t goff[DP_MAXFIT + 1];
+  goff[0] = 0;
+  for (int k = 0; k < nl; ++k) goff[k + 1] = goff[k] + (int64_t)(net.win[k] + 1) * net.wout[k];
   for (int64_t r0 = 0; r0 < n; r0 += s.rows) {
     const int rows = (int)((n - r0) < s.rows ? (n - r0) : s.rows);
     const int32_t* id = idx ? idx + r0 : nullptr;
@@ -246,7 +346,13 @@ int fit_simt(cudaStream_t st, int64_t n, const int32_t* idx, const FitNet& net, 
     int ldgz = 0;
     float* gpin = s.gp;
     float* gpout = s.gz2;
+    if (fg)  // dE/dw_out = sum_i z_i, dE/db_out = rows
+      wgrad(st, rows, s.z[nl - 1], W, W, nullptr, 0, 1, *fg, fg->g + goff[nl]);
     for (int k = nl - 1; k >= 1; --k) {
+      // gpin = gp_k: dE/dW_k = z_{k-1}^T gp_k, dE/db_k = sum_i gp_k
+      if (fg)
+        wgrad(st, rows, s.z[k - 1], net.win[k], net.win[k], gpin, net.wout[k], net.wout[k], *fg,
+              fg->g + goff[k]);
       GemmEpi ep{};
       ep.R = net.shortcut[k] ? gz_prev : nullptr;
       ep.ldr = ldgz;
@@ -262,6 +368,8 @@ int fit_simt(cudaStream_t st, int64_t n, const int32_t* idx, const FitNet& net, 
       gpin = gpout;
       gpout = tmp;
     }
+    if (fg)  // layer 0: dE/dW_0 = D^T gp_0
+      wgrad(st, rows, s.D, din, din, gpin, net.wout[0], net.wout[0], *fg, fg->g);
     {
       GemmEpi ep{};
       ep.out0 = s.dD;

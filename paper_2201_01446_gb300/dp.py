@@ -45,7 +45,8 @@ EXPORTS = ["dp_options_default", "dp_create", "dp_destroy", "dp_last_error", "dp
            "dp_compute", "dp_system_create", "dp_system_destroy", "dp_system_get",
            "dp_system_step", "dp_md_step", "dp_state_save", "dp_state_load",
            "dp_neighbor_pairs", "dp_table_coeffs", "dp_descriptor", "dp_version",
-           "dp_profile", "dp_profile_read", "dp_stats", "dp_neighbor_pairs_static", "dp_fitting"]
+           "dp_profile", "dp_profile_read", "dp_stats", "dp_neighbor_pairs_static", "dp_fitting",
+           "dp_param_sizes", "dp_param_grad"]
 
 DP_NPHASE = 5
 PHASES = ["neighbor_build", "embed_contract_fwd", "fitting", "embed_contract_bwd_forces",
@@ -84,6 +85,8 @@ def _load():
         "dp_stats": (i, [vp, vp, vp]),
         "dp_neighbor_pairs_static": (i, [i64, vp, vp, d, i64, vp, i64p, vp]),
         "dp_fitting": (i, [vp, i64, vp, vp, vp, vp]),
+        "dp_param_sizes": (i, [vp, i64p, i64p]),
+        "dp_param_grad": (i, [vp, i64, dp_, dp_, dp_, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -322,6 +325,32 @@ def dp_neighbor_pairs_static(coords, box, rlist, stream=None):
                                         b.ctypes.data_as(C.c_void_p), float(rlist), cnt.value,
                                         C.c_void_p(out.data_ptr()), C.byref(cnt), stream), None)
     return out[:cnt.value]
+
+
+def dp_param_sizes(h):
+    """(n_fit, n_table): doubles of the two parameter-gradient arrays."""
+    nf, nt = C.c_int64(), C.c_int64()
+    _check(lib.dp_param_sizes(h, C.byref(nf), C.byref(nt)), h)
+    return nf.value, nt.value
+
+
+def dp_param_grad(h, coords, types, box, table=True):
+    """Energy and its gradients with respect to the fitting parameters (flat,
+    per model type: per layer [(win + 1) x wout] W then b, then w_out and
+    b_out) and, with table=True, the table coefficients [ntypes, ntypes, n,
+    6, M] (coefficients of u^q, u = s/h - k; host arrays)."""
+    nf, nt = dp_param_sizes(h)
+    n = int(np.shape(coords)[0])
+    gf = np.zeros(nf)
+    gt = np.zeros(nt) if table else None
+    e = np.zeros(1)
+    c, ck, _ = _ptr(coords, np.float64)  # ck, tk, bk keep the arrays alive
+    t, tk, _ = _ptr(types, np.int32)
+    b, bk, _ = _ptr(box, np.float64)
+    _check(lib.dp_param_grad(h, n, c, t, b, e.ctypes.data_as(C.c_void_p),
+                             gf.ctypes.data_as(C.c_void_p),
+                             gt.ctypes.data_as(C.c_void_p) if gt is not None else None), h)
+    return float(e[0]), gf, gt
 
 
 def dp_fitting(h, types, T):
