@@ -219,6 +219,18 @@ dp_status dp_param_grad(dp_handle* h, int64_t natoms, const double* coords,
                         const int32_t* types, const double* box, double* energy,
                         double* grad_fit, double* grad_table);
 
+/* The model's current parameters in the same two layouts (HOST arrays of
+ * n_fit and n_table doubles; either may be NULL).  The device keeps FP32
+ * copies, so a get returns FP32 values. */
+dp_status dp_get_params(dp_handle* h, double* fit, double* table);
+
+/* Replace the fitting parameters and/or the table coefficients (either
+ * pointer may be NULL), e.g. after a gradient step; they are rounded to FP32
+ * and every derived device copy (transposes, BF16 pieces, tiled table
+ * operands) is rebuilt.  Synchronous.  A table on an untabulated handle is
+ * DP_ERR_ARG. */
+dp_status dp_set_params(dp_handle* h, const double* fit, const double* table);
+
 /* ---------------------------------------------------------------------------
  * Profiling: per-phase device time measured with CUDA events recorded on the
  * handle's stream around each phase's kernels.

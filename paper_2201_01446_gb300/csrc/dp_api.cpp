@@ -100,6 +100,12 @@ struct dp_handle {
   DevBuf tabF, tabB, tc_scratch;  // tensor-core embedding: tiled table pieces, per-CTA scratch
   DevBuf tanh_tab;                // Sec. 3.5 tanh table of the fitting net (tanh_table = 1)
   DevBuf pg, pg_fit_part, pg_tab_part;  // parameter gradients: FP64 result, FP32 partials
+  // offsets (floats) of each type's W, W^T, b, w_out in fit32
+  struct FitOfs {
+    size_t W[DP_MAXFIT], WT[DP_MAXFIT], b[DP_MAXFIT], wout;
+  };
+  std::vector<FitOfs> fit_ofs;
+  size_t fit_floats = 0;
   int n_int = 0;
   double h = 0.0;
   FitNet nets[DP_MAXT];
@@ -647,6 +653,24 @@ dp_status check_handle(dp_handle* h) {
   return DP_OK;
 }
 
+// BF16 pieces of every fitting weight (W^T and W, pre-tiled B operands of the
+// tensor-core fitting) from the FP32 copies in fit32
+void tile_fit_weights(dp_handle* h) {
+  const float* fb = P<float>(h->fit32);
+  __nv_bfloat16* hb = P<__nv_bfloat16>(h->fit_bf16);
+  const int pc = h->opt.fit_precision == 1 ? 1 : 3;
+  for (int t = 0; t < h->ntypes; ++t) {
+    const FitNet& nf = h->nets[t];
+    const auto& o = h->fit_ofs[t];
+    for (int k = 0; k < nf.nl; ++k)
+      if (nf.wout[k] % 16 == 0 && nf.win[k] % 16 == 0) {
+        // W^T (N = wout, K = win), W (N = win, K = wout)
+        launch_tile_operand(h->st, nf.wout[k], nf.win[k], pc, fb + o.WT[k], hb + 3 * o.WT[k]);
+        launch_tile_operand(h->st, nf.win[k], nf.wout[k], pc, fb + o.W[k], hb + 3 * o.W[k]);
+      }
+  }
+}
+
 // copy in x (host or device) and user types; returns model types on device
 dp_status load_coords(dp_handle* h, Work& w, int64_t n, const double* coords,
                       const int32_t* types, int device_ptrs) {
@@ -771,10 +795,8 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
             ensure(h->table, sizeof(float) * (size_t)np * h->n_int * 6 * h->M) == cudaSuccess;
   // fitting parameters (FP32, plus transposed weights for the backward)
   std::vector<float> fit;
-  struct Ofs {
-    size_t W[DP_MAXFIT], WT[DP_MAXFIT], b[DP_MAXFIT], wout;
-  };
-  std::vector<Ofs> ofs(m.ntypes);
+  h->fit_ofs.assign(m.ntypes, dp_handle::FitOfs{});
+  auto& ofs = h->fit_ofs;
   for (int t = 0; t < m.ntypes; ++t) {
     int prev = h->din;
     for (int k = 0; k < m.n_fit; ++k) {
@@ -796,6 +818,7 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
     while (fit.size() % 4) fit.push_back(0.0f);
   }
   ok = ok && up(h->fit32, fit.data(), sizeof(float) * fit.size());
+  h->fit_floats = fit.size();
   if (h->opt.tanh_table) {
     // Sec. 3.5: on [x_k, x_k + h], h = 1/128, p(u) = a0 + a1 u + a2 u^2 with
     // p(0) = tanh(x_k), p'(0) = 1 - tanh(x_k)^2, p(h) = tanh(x_k + h); FP64
@@ -851,12 +874,6 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
         // pieces of W^T at 3*ofs.WT, pieces of W at 3*ofs.W (disjoint: 3 * fit.size() total)
         __nv_bfloat16* pwt = hb + 3 * ofs[t].WT[k];
         __nv_bfloat16* pw = hb + 3 * ofs[t].W[k];
-        const int pc = h->opt.fit_precision == 1 ? 1 : 3;
-        if (nf.wout[k] % 16 == 0 && nf.win[k] % 16 == 0) {
-          // pre-tiled B operands: W^T (N = wout, K = win), W (N = win, K = wout)
-          launch_tile_operand(h->st, nf.wout[k], nf.win[k], pc, fb + ofs[t].WT[k], pwt);
-          launch_tile_operand(h->st, nf.win[k], nf.wout[k], pc, fb + ofs[t].W[k], pw);
-        }
         nt.win[k] = nf.win[k];
         nt.wout[k] = nf.wout[k];
         nt.shortcut[k] = nf.shortcut[k];
@@ -868,6 +885,7 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
       nt.b_out = nf.b_out;
       nt.tanh_tab = nf.tanh_tab;
     }
+    tile_fit_weights(h);
   }
   // FP32 embedding weights (and transposes) for the plain untabulated path
   if (m.n_emb == 3 && m.emb_w[0] <= 32) {
@@ -1246,6 +1264,90 @@ dp_status dp_param_grad(dp_handle* h, int64_t natoms, const double* coords, cons
                        cudaMemcpyDeviceToHost, h->st),
        "gradient copy");
   CK(cudaStreamSynchronize(h->st), "gradient copy");
+  return DP_OK;
+}
+
+dp_status dp_get_params(dp_handle* h, double* fit, double* table) {
+  CKS(check_handle(h));
+  if (fit) {
+    std::vector<float> fb(h->fit_floats);
+    CK(cudaMemcpyAsync(fb.data(), h->fit32.p, sizeof(float) * fb.size(), cudaMemcpyDeviceToHost,
+                       h->st),
+       "parameter copy");
+    CK(cudaStreamSynchronize(h->st), "parameter copy");
+    double* o = fit;
+    for (int t = 0; t < h->ntypes; ++t) {
+      const FitNet& net = h->nets[t];
+      const auto& ofs = h->fit_ofs[t];
+      for (int k = 0; k < net.nl; ++k) {
+        const size_t nw = (size_t)net.win[k] * net.wout[k];
+        for (size_t q = 0; q < nw; ++q) *o++ = fb[ofs.W[k] + q];
+        for (int c = 0; c < net.wout[k]; ++c) *o++ = fb[ofs.b[k] + c];
+      }
+      for (int c = 0; c < net.wout[net.nl - 1]; ++c) *o++ = fb[ofs.wout + c];
+      *o++ = h->b_out[t];
+    }
+  }
+  if (table) {
+    const size_t n = (size_t)h->ntypes * h->ntypes * h->n_int * 6 * h->M;
+    std::vector<float> tb(n);
+    CK(cudaMemcpy(tb.data(), h->table.p, sizeof(float) * n, cudaMemcpyDeviceToHost),
+       "table copy");
+    for (size_t q = 0; q < n; ++q) table[q] = tb[q];
+  }
+  return DP_OK;
+}
+
+dp_status dp_set_params(dp_handle* h, const double* fit, const double* table) {
+  CKS(check_handle(h));
+  if (table && !h->opt.tabulated) return fail(h, DP_ERR_ARG, "the untabulated path has no table");
+  if (fit) {
+    std::vector<float> fb(h->fit_floats);
+    CK(cudaMemcpyAsync(fb.data(), h->fit32.p, sizeof(float) * fb.size(), cudaMemcpyDeviceToHost,
+                       h->st),
+       "parameter copy");
+    CK(cudaStreamSynchronize(h->st), "parameter copy");
+    const double* in = fit;
+    for (int t = 0; t < h->ntypes; ++t) {
+      FitNet& net = h->nets[t];
+      const auto& ofs = h->fit_ofs[t];
+      for (int k = 0; k < net.nl; ++k) {
+        const int wi = net.win[k], wo = net.wout[k];
+        for (int r = 0; r < wi; ++r)
+          for (int c = 0; c < wo; ++c) {
+            const float v = (float)in[(size_t)r * wo + c];
+            fb[ofs.W[k] + (size_t)r * wo + c] = v;
+            fb[ofs.WT[k] + (size_t)c * wi + r] = v;
+          }
+        in += (size_t)wi * wo;
+        for (int c = 0; c < wo; ++c) fb[ofs.b[k] + c] = (float)in[c];
+        in += wo;
+      }
+      const int wl = net.wout[net.nl - 1];
+      for (int c = 0; c < wl; ++c) fb[ofs.wout + c] = (float)in[c];
+      h->b_out[t] = (float)in[wl];
+      net.b_out = h->b_out[t];
+      h->nets_tc[t].b_out = h->b_out[t];
+      in += wl + 1;
+    }
+    CK(cudaMemcpyAsync(h->fit32.p, fb.data(), sizeof(float) * fb.size(), cudaMemcpyHostToDevice,
+                       h->st),
+       "parameter upload");
+    tile_fit_weights(h);
+    CK(cudaStreamSynchronize(h->st), "parameter upload");
+  }
+  if (table) {
+    const size_t n = (size_t)h->ntypes * h->ntypes * h->n_int * 6 * h->M;
+    std::vector<float> tb(n);
+    for (size_t q = 0; q < n; ++q) tb[q] = (float)table[q];
+    CK(cudaMemcpyAsync(h->table.p, tb.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->st),
+       "table upload");
+    if (h->opt.embed_precision == 2 &&
+        tab_tc_build(h->st, P<float>(h->table), env_params(h), P<__nv_bfloat16>(h->tabF),
+                     P<__nv_bfloat16>(h->tabB)) != 0)
+      return fail(h, DP_ERR_CUDA, "table tiling failed");
+    CK(cudaStreamSynchronize(h->st), "table upload");
+  }
   return DP_OK;
 }
 

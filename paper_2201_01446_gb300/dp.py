@@ -46,7 +46,7 @@ EXPORTS = ["dp_options_default", "dp_create", "dp_destroy", "dp_last_error", "dp
            "dp_system_step", "dp_md_step", "dp_state_save", "dp_state_load",
            "dp_neighbor_pairs", "dp_table_coeffs", "dp_descriptor", "dp_version",
            "dp_profile", "dp_profile_read", "dp_stats", "dp_neighbor_pairs_static", "dp_fitting",
-           "dp_param_sizes", "dp_param_grad"]
+           "dp_param_sizes", "dp_param_grad", "dp_get_params", "dp_set_params"]
 
 DP_NPHASE = 5
 PHASES = ["neighbor_build", "embed_contract_fwd", "fitting", "embed_contract_bwd_forces",
@@ -87,6 +87,8 @@ def _load():
         "dp_fitting": (i, [vp, i64, vp, vp, vp, vp]),
         "dp_param_sizes": (i, [vp, i64p, i64p]),
         "dp_param_grad": (i, [vp, i64, dp_, dp_, dp_, vp, vp, vp]),
+        "dp_get_params": (i, [vp, vp, vp]),
+        "dp_set_params": (i, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -351,6 +353,28 @@ def dp_param_grad(h, coords, types, box, table=True):
                              gf.ctypes.data_as(C.c_void_p),
                              gt.ctypes.data_as(C.c_void_p) if gt is not None else None), h)
     return float(e[0]), gf, gt
+
+
+def dp_get_params(h):
+    """(fit [n_fit], table [n_table]) the model's current parameters (FP64
+    copies of the device's FP32 values; layouts as dp_param_grad)."""
+    nf, nt = dp_param_sizes(h)
+    fit, tab = np.zeros(nf), np.zeros(nt)
+    _check(lib.dp_get_params(h, fit.ctypes.data_as(C.c_void_p), tab.ctypes.data_as(C.c_void_p)), h)
+    return fit, tab
+
+
+def dp_set_params(h, fit=None, table=None):
+    """Replace the fitting parameters and/or the table coefficients."""
+    nf, nt = dp_param_sizes(h)
+    f = np.ascontiguousarray(fit, np.float64).ravel() if fit is not None else None
+    t = np.ascontiguousarray(table, np.float64).ravel() if table is not None else None
+    if f is not None and f.size != nf:
+        raise ValueError(f"fit has {f.size} values, the model {nf}")
+    if t is not None and t.size != nt:
+        raise ValueError(f"table has {t.size} values, the model {nt}")
+    _check(lib.dp_set_params(h, f.ctypes.data_as(C.c_void_p) if f is not None else None,
+                             t.ctypes.data_as(C.c_void_p) if t is not None else None), h)
 
 
 def dp_fitting(h, types, T):

@@ -27,7 +27,7 @@ def test_energy_gradient_is_minus_forces(cu_stress_path):
         torch.cuda.synchronize()
         assert float(E.detach()) == float(E2[0])
         assert torch.equal(gx, -F) and torch.equal(V, V2)
-        assert abs(float(Ei.sum()) - float(E)) < 1e-9 * abs(float(E))
+        assert abs(float(Ei.sum()) - float(E.detach())) < 1e-9 * abs(float(E.detach()))
         # composition: L = 2 E + sum(x^2)  ->  dL/dx = -2 F + 2 x
         E, _, _ = autograd.energy(h, x, t, box)
         loss = 2.0 * E + (x * x).sum()

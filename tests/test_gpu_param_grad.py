@@ -162,3 +162,54 @@ def test_param_grad_edge_cases(dp, cu_model_path):
         assert gt is None and gf[-1] == len(x)
     finally:
         dp.dp_destroy(h0)
+
+
+def test_set_params_matches_oracle_and_autograd(dp, cu_stress_path):
+    torch = pytest.importorskip("torch")
+    from paper_2201_01446_gb300 import autograd
+    m = oracle.Model(cu_stress_path)
+    tab = oracle.Table(m, TABLE_H, CU_SMAX)
+    x, t, box = inputs.fcc_copper(4, sigma=0.05, seed=5)
+    h = _handle(dp, cu_stress_path, 1, CU_RC, CU_RCS, (CU_SEL,), CU_SMAX)
+    try:
+        fit0, tab0 = dp.dp_get_params(h)
+        dp.dp_set_params(h, fit0, tab0)
+        f1, t1 = dp.dp_get_params(h)
+        assert np.array_equal(f1, fit0) and np.array_equal(t1, tab0)  # FP32 values round-trip
+        # new parameters on both sides: scaled fitting weights, a reshaped table
+        rng = np.random.default_rng(0)
+        fit = fit0 * (1.0 + 0.05 * rng.standard_normal(fit0.size))
+        table = tab0 * (1.0 + 0.02 * rng.standard_normal(tab0.size))
+        dp.dp_set_params(h, fit, table)
+        fit32, table32 = dp.dp_get_params(h)
+        E, F, V, _ = dp.dp_compute(h, x, t, box)
+        m.set_fit_params(0, fit32)
+        n, M = tab.n, m.M
+        tab.set_coeffs(0, 0, table32.reshape(n, 6, M) / TABLE_H ** np.arange(6)[None, :, None])
+        r = oracle.evaluate(m, tab, CU_RC, CU_RCS, CU_SEL, x, t, box)
+        frms = float(np.sqrt((r["force"] ** 2).mean()))
+        assert abs(E - r["energy"]) / len(x) < max(1e-6, 2e-6 * float(np.abs(r["atom_energy"]).mean()))
+        assert float(np.sqrt(((F - r["force"]) ** 2).mean())) < max(1e-5, 3e-5 * frms)
+        # the energy as a torch function of the parameters
+        pf = torch.tensor(fit32, requires_grad=True)
+        pt = torch.tensor(table32, requires_grad=True)
+        Et = autograd.energy_params(h, pf, pt, x, t, box)
+        Et.backward()
+        E2, gf, gt = dp.dp_param_grad(h, x, t, box)
+        assert float(Et) == E2
+        assert np.array_equal(pf.grad.numpy(), gf) and np.array_equal(pt.grad.numpy(), gt)
+        # a gradient step on the fitting parameters lowers E by eta |g|^2 to
+        # first order: E(p - eta g) = E - eta |g|^2 + O(eta^2); two step
+        # sizes remove the second-order term (Richardson)
+        g2 = float(gf @ gf)
+        eta = 1e-3 * abs(E2) / g2
+        ratios = []
+        for step in (eta, eta / 2):
+            E3 = float(autograd.energy_params(h, torch.tensor(fit32 - step * gf), None, x, t, box))
+            ratios.append((E2 - E3) / (step * g2))
+        r_ex = 2 * ratios[1] - ratios[0]
+        PARITY_LOG.append(dict(case="param set + gradient step Cu 256", ratios=ratios,
+                               extrapolated=r_ex))
+        assert ratios[0] > 0 and abs(r_ex - 1.0) < 0.05, ratios
+    finally:
+        dp.dp_destroy(h)
