@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=120,
                     help="requests of the serving leg (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--grad-cells", type=int, default=40,
+                    help="copper cells per edge of the parameter-gradient leg (0: skip)")
     ap.add_argument("--ref-cells", type=int, default=20,
                     help="FCC cells per edge of the reference arm's oracle sample")
     ap.add_argument("--embed-precision", type=int, default=2,
@@ -257,6 +259,31 @@ def serve_leg(args, cu_model, pg):
                    "(Cu 50 steps, water 10), Poisson arrivals at 0.7 x closed-loop capacity"}
 
 
+def grad_leg(args, model_path, stream):
+    """Parameter gradients (dE/d fitting parameters and table coefficients)
+    of one copper box through dp_param_grad: wall time of the synchronous
+    call (host coordinates in, gradients out) after one warm-up call."""
+    from paper_2201_01446_gb300 import dp
+    o = dp.dp_options_default()
+    o.embed_precision = args.embed_precision
+    o.fit_precision = args.fit_precision
+    h = dp.dp_create(model_path, 1, RC, RCS, [SEL], options=o, stream=C_stream(stream))
+    try:
+        x, t, box = inputs.fcc_copper(args.grad_cells, sigma=0.05, seed=7)
+        dp.dp_param_grad(h, x, t, box, table=args.embed_precision == 2)
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            dp.dp_param_grad(h, x, t, box, table=args.embed_precision == 2)
+        ms = (time.perf_counter() - t0) / reps * 1e3
+        nf, nt = dp.dp_param_sizes(h)
+    finally:
+        dp.dp_destroy(h)
+    return {"natoms": len(x), "ms_per_call": ms, "atoms_per_s": len(x) / (ms / 1e3),
+            "n_fit_params": nf, "n_table_params": nt if args.embed_precision == 2 else 0,
+            "timing": "host wall clock of the synchronous call, coordinates in, gradients out"}
+
+
 def run_reference(args, world, rank, pg):
     if rank != 0:
         return 0
@@ -430,6 +457,7 @@ def main():
         E, F, V, Ei = dp.dp_compute(h, xg, t, box, atom_energy=True)
         cpu, accuracy = cpu_baseline_leg(model, xg, t, box, F, Ei)
     dp.dp_destroy(h)
+    grad_info = grad_leg(args, model, stream) if args.grad_cells > 0 else None
     serve_info = serve_leg(args, model, pg) if args.serve_requests > 0 else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -446,7 +474,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": ck, "accuracy_vs_oracle": accuracy, "plain": plain,
-                "serve": serve_info, "stats": stats}
+                "serve": serve_info, "param_grad": grad_info, "stats": stats}
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

@@ -521,8 +521,7 @@ dp_status ensure_fit_scratch_tc(dp_handle* h, int64_t rows_needed) {
   if (rows <= h->fs_tc.rows) return DP_OK;
   int wmax = 0;
   for (int k = 0; k < h->n_fit; ++k) wmax = std::max(wmax, h->fit_w[k]);
-  const int slots = (h->din + 255) / 256;  // per-N-tile partials of dE/dT
-  size_t bytes = rows * (size_t)slots * 64 * 4 + rows * (size_t)wmax * (4 + 2 * 2 * PCN);
+  size_t bytes = rows * (size_t)wmax * (4 + 2 * 2 * PCN);
   for (int k = 0; k < h->n_fit; ++k) bytes += rows * (size_t)h->fit_w[k] * (4 + 4 + 2 * PCN);
   bytes += 64 * 256;
   CK(ensure(h->fitbuf_tc, bytes), "alloc tensor-core fitting scratch");
@@ -535,7 +534,6 @@ dp_status ensure_fit_scratch_tc(dp_handle* h, int64_t rows_needed) {
   FitScratchTC& s = h->fs_tc;
   s.rows = rows;
   s.wmax = wmax;
-  s.part = (float*)take(rows * (size_t)slots * 64 * 4);
   for (int k = 0; k < h->n_fit; ++k) {
     s.t[k] = (float*)take(rows * h->fit_w[k] * 4);
     s.z[k] = (float*)take(rows * h->fit_w[k] * 4);

@@ -201,7 +201,6 @@ struct FitNetTC {
 struct FitScratchTC {
   int64_t rows;                  // rows per chunk (a multiple of 128)
   int wmax;
-  float* part;                   // [din/256][rows][64] partials of dE/dT (x < 16)
   float* t[DP_MAXFIT];           // [rows][wout[k]] tanh values (table mode: derivatives)
   float* z[DP_MAXFIT];           // [rows][wout[k]] layer outputs (k >= 1)
   __nv_bfloat16* zh[DP_MAXFIT];  // tiled pieces of the layer outputs (next A operand)

@@ -4,23 +4,25 @@
 // epilogues (bias, tanh, shortcut, per-atom energy, gradient of tanh, the
 // descriptor's own backward).
 //
-// One CTA computes a 128-row x NT-column tile of C = A B^T (A: rows x K, B:
-// N x K).  Both operands live in global memory PRE-TILED in the tensor core's
-// no-swizzle K-major shared-memory layout: for each 128-row (A) or NT-row (B)
-// tile and each 16-wide K chunk, one contiguous block holding every BF16
-// piece of the operand, core matrices of 8 rows x 16 bytes, the two K groups
-// 128 bytes apart, 8-row groups 256 bytes apart.  A pipeline stage is then
-// two bulk asynchronous copies (cp.async.bulk, completion counted in bytes on
-// the stage's mbarrier) issued by one thread; the previous GEMM's epilogue
-// writes its output straight into that layout for the next GEMM.
+// C = A B^T (A: rows x K, B: N x K) in 128-row tiles.  The operands live in
+// global memory PRE-TILED in the tensor core's no-swizzle K-major
+// shared-memory layout: for each 128-row (A) or 256-row (B) tile and each
+// 16-wide K chunk, one contiguous block holding every BF16 piece of the
+// operand, core matrices of 8 rows x 16 bytes, the two K groups 128 bytes
+// apart, 8-row groups 256 bytes apart.  A pipeline stage is then a few bulk
+// asynchronous copies (cp.async.bulk, completion counted in bytes on the
+// stage's mbarrier) issued by one thread; each GEMM's epilogue writes its
+// output straight into that layout for the next GEMM.
 //
+// Two kernels.  Layer 0 (K = 2048) runs on a tiled kernel, one output tile
+// per CTA, whose warps 4-7 form the descriptor D from T in the stage's A
+// slot.  The K-short GEMMs (hidden, last, backward, dE/dD) run on a
+// persistent kernel, one CTA per SM with double-buffered TMEM accumulators.
 // Warp roles: warp 0 (one lane) issues the copies up to NS stages ahead,
 // warp 1 (one lane) issues the MMAs and commits each stage back to its
-// "empty" barrier, warps 4-7 (layer 0 only) form the descriptor D from T in
-// the stage's A slot, then all eight warps run the epilogue from TMEM.  Every
-// wait is bounded: on timeout the kernel records an error word, stops issuing
-// work, waits (bounded) for its own copies and MMAs, frees its TMEM and
-// returns.
+// "empty" barrier, the epilogue warps drain TMEM.  Every wait is bounded: on
+// timeout the kernel records an error word, stops issuing work, waits
+// (bounded) for its own copies and MMAs, frees its TMEM and returns.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -66,7 +68,7 @@ __device__ __forceinline__ void store_tiled(__nv_bfloat16* out, int nkc, int row
 // TC_L0: layer 0, its A operand (the descriptor D of Eq. 2) formed from T in
 // the stage; TC_DT: the input gradient dE/dD contracted with T into dE/dT in
 // the epilogue (D and dE/dD never reach global memory)
-enum { TC_PLAIN = 0, TC_L0 = 1, TC_MID = 2, TC_LAST = 3, TC_BWD = 4, TC_DT = 5 };
+enum { TC_L0 = 1, TC_MID = 2, TC_LAST = 3, TC_BWD = 4, TC_DT = 5 };
 
 struct TcEpi {
   const float* bias;       // [N]
@@ -77,7 +79,7 @@ struct TcEpi {
   const float* wout;       // output weights (TC_LAST)
   float bout;
   float* out_a;            // FP32 [rows][ldo]: t, or in the table mode the activation
-                           // derivative (L0, MID); C (PLAIN)
+                           // derivative (L0, MID)
   float* out_b;            // FP32 [rows][ldo]: z (MID) or gz (BWD)
   __nv_bfloat16* out_h;    // the next A operand, pre-tiled, width ldo
   int ldo;
@@ -88,15 +90,16 @@ struct TcEpi {
   float* dT;               // TC_DT: dE/dT rows, same indexing as T
   const int32_t* tidx;
   int Mw;                  // embedding width M
-  float* part;             // TC_DT: per-N-tile partial sums [slot][rows][64]
-  int64_t part_ps;         // elements between slots
   const float4* tab;       // tanh table (L0, MID, LAST), NULL: tanhf
 };
 
+// The tiled kernel (one output tile per CTA) runs layer 0 (K = 2048), its A
+// operand D formed in the stage from T by warps 4-7; the K-short layers run
+// on the persistent kernel below.
 template <int EPI, int PC, bool TAB>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_tc_gemm(int M, int N, int K, int NT, const __nv_bfloat16* __restrict__ A,
-              const __nv_bfloat16* __restrict__ B, TcEpi ep) {
+    k_tc_gemm(int M, int N, int K, int NT, const __nv_bfloat16* __restrict__ B, TcEpi ep) {
+  static_assert(EPI == TC_L0, "the tiled kernel serves layer 0");
   using C = TcCfg<PC>;
   constexpr int NS = C::NS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -107,7 +110,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ __align__(8) uint64_t s_acc;        // accumulator complete
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
-  __shared__ float s_e[2][kBM];
   volatile int* abort_flag = &s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -143,16 +145,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: the A and B blocks of chunk kc land in stage kc % NS
+      // producer: the B block of chunk kc lands in stage kc % NS (its A
+      // block is written there by warps 4-7)
       int kc = 0;
       for (; kc < nk; ++kc) {
         const int s = kc % NS, u = kc / NS;
         if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
         const uint32_t st0 = smem_u32(base + (size_t)s * C::STAGE);
-        mbar_expect_tx(&s_full[s], (EPI == TC_L0 ? 0u : a_bytes) + PC * b_piece);
-        if (EPI != TC_L0)
-          bulk_g2s(st0, A + ((size_t)m_tile * nk + kc) * PC * (kBM * kBK), a_bytes,
-                   &s_full[s]);
+        mbar_expect_tx(&s_full[s], PC * b_piece);
         bulk_g2s(st0 + a_bytes,
                  B + (size_t)n0 * K * PC + (size_t)kc * PC * ((size_t)ntile * kBK),
                  PC * b_piece, &s_full[s]);
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int kc = 0; kc < nk; ++kc) {
         const int s = kc % NS, u = kc / NS;
         if (!mbar_wait(&s_full[s], u & 1, abort_flag)) break;
-        if (EPI == TC_L0 && !mbar_wait(&s_gen[s], u & 1, abort_flag)) break;
+        if (!mbar_wait(&s_gen[s], u & 1, abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n");
         const uint32_t st0 = smem_u32(base + (size_t)s * C::STAGE);
 #pragma unroll
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               smem_u32(&s_acc)));
     }
     __syncwarp();
-  } else if (EPI == TC_L0 && warp >= 4) {
+  } else if (warp >= 4) {
     // layer 0: D[r][16 b + a] = sum_c T[c][b] T[c][a] (Eq. 2, M< = 16), one
     // thread per row; chunk kc is b = kc
     const int r = tid - kTcThreads / 2;
@@ -273,23 +273,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int nch = ntile / 16;
     const int c_beg = half ? (nch + 1) / 2 : 0, c_end = half ? nch : (nch + 1) / 2;
     const int nkc_out = ep.ldo / kBK;
-    float e_acc = 0.0f;
-    // TC_DT: T[row][c][0..15] and the partial sums of the second factor; the
-    // first factor of the tile's 16 b goes through shared memory [row][c][b]
-    // (the idle stage memory after the half-sum area) for row-contiguous stores
-    float tl[4][16], part[4][16];
-    const float* tr = nullptr;
-    float* sf = reinterpret_cast<float*>(base + 33280);
-    if (EPI == TC_DT) {
-      if (rok) tr = ep.T + (size_t)(ep.tidx ? ep.tidx[row] : row) * 4 * ep.Mw;
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int a = 0; a < 16; ++a) {
-          tl[c][a] = tr ? __ldg(tr + c * ep.Mw + a) : 0.0f;
-          part[c][a] = 0.0f;
-        }
-    }
     for (int ch = c_beg; ch < c_end; ++ch) {
       const int c0 = ch * 16;
       float v[16];
@@ -302,138 +285,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       if (!rok) continue;
       const int n = n0 + c0;
-      if (EPI == TC_DT) {
-        // v = dE/dD[b][0..15] with b = n/16 (Eq. 2: D[b][a] = sum_c T[c][b] T[c][a])
-        const int b = n >> 4;
-        float tb[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          tb[c] = __ldg(tr + c * ep.Mw + b);
-          float acc = 0.0f;
-#pragma unroll
-          for (int a = 0; a < 16; ++a) acc = fmaf(v[a], tl[c][a], acc);
-          sf[row_t * 68 + c * 16 + ch] = acc;  // first factor: complete for this b
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int a = 0; a < 16; ++a) part[c][a] = fmaf(v[a], tb[c], part[c][a]);
-        continue;
-      }
       const size_t o = (size_t)row * ep.ldo + n;
-      float r[16], b[16], tt[16], oa[16], ob[16], oh[16];
-      if (EPI == TC_L0 || EPI == TC_MID || EPI == TC_LAST) {
+      float b[16], oa[16], oh[16];
 #pragma unroll
-        for (int k = 0; k < 16; k += 4)
-          *reinterpret_cast<float4*>(b + k) = *reinterpret_cast<const float4*>(ep.bias + n + k);
-      }
-      if (EPI == TC_MID || EPI == TC_LAST || EPI == TC_BWD) {
-        if (ep.R) {
-#pragma unroll
-          for (int k = 0; k < 16; k += 4)
-            *reinterpret_cast<float4*>(r + k) =
-                *reinterpret_cast<const float4*>(ep.R + (size_t)row * ep.ldr + n + k);
-        } else {
-#pragma unroll
-          for (int k = 0; k < 16; ++k) r[k] = 0.0f;
-        }
-      }
-      if (EPI == TC_BWD) {
-#pragma unroll
-        for (int k = 0; k < 16; k += 4)
-          *reinterpret_cast<float4*>(tt + k) =
-              *reinterpret_cast<const float4*>(ep.Tt + (size_t)row * ep.ldt + n + k);
-      }
+      for (int k = 0; k < 16; k += 4)
+        *reinterpret_cast<float4*>(b + k) = *reinterpret_cast<const float4*>(ep.bias + n + k);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        if (EPI == TC_PLAIN) {
-          oa[k] = v[k];
-        } else if (EPI == TC_L0) {
-          float d;
-          const float t = act_tanh_t<TAB>(v[k] + b[k], ep.tab, d);
-          oa[k] = TAB ? d : t;
-          ob[k] = t;  // z_0 = t_0 (layer 0 has no shortcut; table mode only)
-          oh[k] = t;
-        } else if (EPI == TC_MID) {
-          float d;
-          const float t = act_tanh_t<TAB>(v[k] + b[k], ep.tab, d);
-          oa[k] = TAB ? d : t;
-          ob[k] = r[k] + t;
-          oh[k] = ob[k];
-        } else if (EPI == TC_LAST) {
-          float d;
-          const float t = act_tanh_t<TAB>(v[k] + b[k], ep.tab, d);
-          const float w = ep.wout[n + k];
-          e_acc = fmaf(r[k] + t, w, e_acc);
-          oh[k] = w * d;
-        } else {  // TC_BWD
-          const float gz = v[k] + r[k];
-          ob[k] = gz;
-          oh[k] = gz * (TAB ? tt[k] : 1.0f - tt[k] * tt[k]);
-        }
+        float d;
+        const float t = act_tanh_t<TAB>(v[k] + b[k], ep.tab, d);
+        oa[k] = TAB ? d : t;
+        oh[k] = t;  // z_0 = t_0 (layer 0 has no shortcut)
       }
-      if (EPI == TC_PLAIN || EPI == TC_L0 || EPI == TC_MID) {
+#pragma unroll
+      for (int k = 0; k < 16; k += 4)
+        *reinterpret_cast<float4*>(ep.out_a + o + k) = *reinterpret_cast<const float4*>(oa + k);
+      if (TAB) {  // the table mode keeps derivatives in out_a: z_0 separately
 #pragma unroll
         for (int k = 0; k < 16; k += 4)
-          *reinterpret_cast<float4*>(ep.out_a + o + k) = *reinterpret_cast<const float4*>(oa + k);
+          *reinterpret_cast<float4*>(ep.out_b + o + k) = *reinterpret_cast<const float4*>(oh + k);
       }
-      if ((EPI == TC_L0 && TAB) || EPI == TC_MID || EPI == TC_BWD) {
-#pragma unroll
-        for (int k = 0; k < 16; k += 4)
-          *reinterpret_cast<float4*>(ep.out_b + o + k) = *reinterpret_cast<const float4*>(ob + k);
-      }
-      if (EPI != TC_PLAIN) {
-        store_tiled<PC>(ep.out_h, nkc_out, row, n, oh);
-        store_tiled<PC>(ep.out_h, nkc_out, row, n + 8, oh + 8);
-      }
-    }
-    if (EPI == TC_LAST) {
-      s_e[half][row_t] = e_acc;
-    }
-    if (EPI == TC_DT) {
-      // second factor (a < 16): the two halves meet in the (now idle) stage
-      // memory, row stride 65 floats (conflict-free); one partial per N tile
-      float* sp = reinterpret_cast<float*>(base) + row_t * 65;
-      if (half) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int a = 0; a < 16; ++a) sp[c * 16 + a] = part[c][a];
-      }
-      __syncthreads();
-      if (!half && rok) {
-        float* pp = ep.part + (size_t)n_tile * ep.part_ps + (size_t)row * 64;
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int a = 0; a < 16; a += 4)
-            *reinterpret_cast<float4*>(pp + c * 16 + a) =
-                make_float4(part[c][a] + sp[c * 16 + a], part[c][a + 1] + sp[c * 16 + a + 1],
-                            part[c][a + 2] + sp[c * 16 + a + 2], part[c][a + 3] + sp[c * 16 + a + 3]);
-      }
-      // first factor: dE/dT[c][b] for the tile's b = n0/16 .., four threads
-      // per (row, c), 16-byte stores
-      const int nb = ntile / 16, b0 = n0 / 16;
-      for (int q = tid; q < kBM * 16; q += kTcThreads) {
-        const int rt = q >> 4, c = (q >> 2) & 3, f = (q & 3) * 4;
-        const int grow = m0 + rt;
-        if (grow >= M || f >= nb) continue;
-        const float* src = sf + rt * 68 + c * 16 + f;
-        float* dst = ep.dT + (size_t)(ep.tidx ? ep.tidx[grow] : grow) * 4 * ep.Mw +
-                     (size_t)c * ep.Mw + b0 + f;
-        if (f + 4 <= nb && ((b0 + f) & 3) == 0 && (ep.Mw & 3) == 0) {
-          *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
-        } else {
-          for (int k = 0; k < 4 && f + k < nb; ++k) dst[k] = src[k];
-        }
-      }
-    }
-  }
-  if (EPI == TC_LAST) {
-    __syncthreads();
-    if (done && tid < kBM && m0 + tid < M) {
-      const int row = m0 + tid;
-      ep.e_atom[ep.idx ? ep.idx[row] : row] = (double)(s_e[0][tid] + s_e[1][tid] + ep.bout);
+      store_tiled<PC>(ep.out_h, nkc_out, row, n, oh);
+      store_tiled<PC>(ep.out_h, nkc_out, row, n + 8, oh + 8);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -444,10 +317,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // ---------------------------------------------------------------- persistent
-// K-short GEMMs (K <= 240: hidden, last, backward and dE/dD layers): one CTA
-// per SM walks row tiles; a row tile's A (all K chunks, all pieces) stays in
-// shared memory (or, for one or two N tiles, streams with B) while its N
-// tiles of 128 columns stream B through the stages.
+// K-short GEMMs (K <= 256: hidden, last, backward and dE/dD layers): one CTA
+// per SM walks row tiles and, per row tile, its N tiles of 128 columns; each
+// stage holds one K chunk of A and of B (all pieces), up to 8 stages deep.
+// (Keeping the row tile's A resident instead, loaded once for all N tiles,
+// measured slower even for the 16 N tiles of the dE/dD GEMM: its 180 KB
+// leave room for three B stages only, and the MMAs then wait on B.)
 // The accumulators are double-buffered in TMEM (2 x 256 columns), so warps 4-7
 // drain N tile t (the fused epilogue, one thread per row) while warp 1 issues
 // the MMAs of tile t+1 and warp 0 the copies of t+2.  Per-row state across the
@@ -458,42 +333,31 @@ constexpr int kPMaxNS = 8;   // stages at most
 constexpr int kPMaxK = 16;   // K chunks a row tile can hold (K <= 256)
 constexpr size_t kPSmemMax = 225 * 1024;
 
-// Two ways to feed A: resident (the row tile's A loaded once, B streamed;
-// for many N tiles, where re-reading A from L2 per N tile would cost more
-// than the shallow B pipeline) or streamed (A and B chunks share each
-// stage, up to 8 stages deep; for the layers with one or two N tiles)
 template <int PC>
 struct PCfg {
   static constexpr int A_CHUNK = PC * kBM * kBK * 2;   // one K chunk of A, all pieces
-  static constexpr int B_PIECE = kPNT * kBK * 2;       // one piece of a B stage
-  static constexpr int B_STAGE = PC * B_PIECE;
-  __host__ __device__ static int stage_bytes(bool res) { return res ? B_STAGE : A_CHUNK + B_STAGE; }
-  static int stages(int nk, bool res) {
-    const long left = (long)kPSmemMax - 128 - (res ? (long)nk * A_CHUNK : 0L);
-    const long ns = left / stage_bytes(res);
+  static constexpr int B_PIECE = kPNT * kBK * 2;       // one piece of B
+  static constexpr int STAGE = A_CHUNK + PC * B_PIECE;  // [A chunk][B pieces]
+  static int stages() {
+    const long ns = ((long)kPSmemMax - 128) / STAGE;
     return (int)(ns < kPMaxNS ? ns : kPMaxNS);
   }
-  static size_t smem(int nk, bool res) {
-    return 128 + (res ? (size_t)nk * A_CHUNK : 0) + (size_t)stages(nk, res) * stage_bytes(res);
-  }
+  static size_t smem() { return 128 + (size_t)stages() * STAGE; }
 };
 
 // EW epilogue warps: 4 (one thread per row, all columns) or 8 (two column
 // halves; for the layers whose epilogue keeps no per-row state across columns)
 template <int EPI, int PC, bool TAB, int EW>
 __global__ void __launch_bounds__(128 + EW * 32, 1)
-    k_tc_gemm_p(int M, int N, int K, int res, int NS, const __nv_bfloat16* __restrict__ A,
+    k_tc_gemm_p(int M, int N, int K, int NS, const __nv_bfloat16* __restrict__ A,
                 const __nv_bfloat16* __restrict__ B, TcEpi ep) {
   using C = PCfg<PC>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   const int nk = K / kBK;
-  const int sbytes = C::stage_bytes(res != 0);
-  unsigned char* a_smem = base;                                          // resident A
-  unsigned char* st_smem = base + (res ? (size_t)nk * C::A_CHUNK : 0);   // the stages
-  // stage s: [A chunk (streamed mode)][B pieces]
-  const uint32_t st_b = res ? 0u : (uint32_t)C::A_CHUNK;
-  __shared__ __align__(8) uint64_t a_full[kPMaxK], a_empty, b_full[kPMaxNS], b_empty[kPMaxNS];
+  unsigned char* st_smem = base;  // stage s: [A chunk][B pieces]
+  const uint32_t st_b = (uint32_t)C::A_CHUNK;
+  __shared__ __align__(8) uint64_t b_full[kPMaxNS], b_empty[kPMaxNS];
   __shared__ __align__(8) uint64_t t_full[2], t_empty[2], fin;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
@@ -511,8 +375,6 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
   };
 
   if (tid == 0) {
-    for (int k = 0; k < kPMaxK; ++k) mbar_init(&a_full[k], 1);
-    mbar_init(&a_empty, 1);
     for (int s = 0; s < kPMaxNS; ++s) {
       mbar_init(&b_full[s], 1);
       mbar_init(&b_empty[s], 1);
@@ -538,19 +400,10 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: resident mode loads a row tile's A once, then B for every
-      // (N tile, K chunk); streamed mode loads the A chunk with each B chunk
-      uint32_t bi = 0, im = 0;
+      // producer: for every (row tile, N tile, K chunk) the A chunk and the B chunk
+      uint32_t bi = 0;
       bool ok = true;
-      for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x, ++im) {
-        if (res) {
-          if (im > 0 && !mbar_wait(&a_empty, (im - 1) & 1, abort_flag)) break;
-          for (int kc = 0; kc < nk; ++kc) {
-            mbar_expect_tx(&a_full[kc], C::A_CHUNK);
-            bulk_g2s(smem_u32(a_smem + (size_t)kc * C::A_CHUNK),
-                     A + ((size_t)mt * nk + kc) * PC * (kBM * kBK), C::A_CHUNK, &a_full[kc]);
-          }
-        }
+      for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x) {
         for (int n = 0; n < ntn && ok; ++n) {
           const int nt = min(kPNT, N - n * kPNT);
           for (int kc = 0; kc < nk; ++kc, ++bi) {
@@ -560,10 +413,9 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
               ok = false;
               break;
             }
-            const uint32_t st0 = smem_u32(st_smem + (size_t)s * sbytes);
-            mbar_expect_tx(&b_full[s], (res ? 0u : (uint32_t)C::A_CHUNK) + PC * nt * 32);
-            if (!res)
-              bulk_g2s(st0, A + ((size_t)mt * nk + kc) * PC * (kBM * kBK), C::A_CHUNK, &b_full[s]);
+            const uint32_t st0 = smem_u32(st_smem + (size_t)s * C::STAGE);
+            mbar_expect_tx(&b_full[s], (uint32_t)C::A_CHUNK + PC * nt * 32);
+            bulk_g2s(st0, A + ((size_t)mt * nk + kc) * PC * (kBM * kBK), C::A_CHUNK, &b_full[s]);
 #pragma unroll
             for (int p = 0; p < PC; ++p)
               bulk_g2s(st0 + st_b + p * C::B_PIECE, b_src(n, kc, p), nt * 32, &b_full[s]);
@@ -574,16 +426,14 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
         // aborted: wait (bounded) for the copies already issued to land
         for (uint32_t j = bi > (uint32_t)NS ? bi - NS : 0; j < bi; ++j)
           mbar_wait(&b_full[j % NS], (j / NS) & 1, nullptr);
-        if (res && im > 0)
-          for (int kc = 0; kc < nk; ++kc) mbar_wait(&a_full[kc], (im - 1) & 1, nullptr);
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      uint32_t bi = 0, ti = 0, im = 0;
+      uint32_t bi = 0, ti = 0;
       bool ok = true;
-      for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x, ++im) {
+      for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x) {
         for (int n = 0; n < ntn && ok; ++n, ++ti) {
           const int nt = min(kPNT, N - n * kPNT);
           const uint32_t idesc = make_idesc_bf16(kBM, nt);
@@ -594,19 +444,14 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n");
           for (int kc = 0; kc < nk; ++kc, ++bi) {
-            if (res && n == 0 && !mbar_wait(&a_full[kc], im & 1, abort_flag)) {
-              ok = false;
-              break;
-            }
             const int s = bi % NS;
             if (!mbar_wait(&b_full[s], (bi / NS) & 1, abort_flag)) {
               ok = false;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n");
-            const uint32_t st0 = smem_u32(st_smem + (size_t)s * sbytes);
-            const uint32_t a0 = res ? smem_u32(a_smem + (size_t)kc * C::A_CHUNK) : st0;
-            const uint32_t b0 = st0 + st_b;
+            const uint32_t a0 = smem_u32(st_smem + (size_t)s * C::STAGE);
+            const uint32_t b0 = a0 + st_b;
 #pragma unroll
             for (int q = 0; q < (PC == 1 ? 1 : 6); ++q) {
               int pa = 0, pb = 0;
@@ -628,10 +473,6 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
               "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                   smem_u32(&t_full[j])));
         }
-        if (res)
-          asm volatile(
-              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                  smem_u32(&a_empty)));
       }
       // the epilogue may be waiting for a buffer this thread will not fill
       if (!ok) *abort_flag = 1;
@@ -815,7 +656,7 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
 
 int g_tc_sms = 0;
 
-// persistent launch of the K-short GEMMs; -2: the row tile's A does not fit
+// persistent launch of the K-short GEMMs
 template <int EPI, int PC, bool TAB>
 int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
               const __nv_bfloat16* B, const TcEpi& ep) {
@@ -823,12 +664,9 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
   if (M <= 0) return 0;
   if (K <= 0 || K % kBK || K / kBK > kPMaxK || N <= 0 || N % 16) return -1;
   if (EPI != TC_DT && ep.ldo != N) return -1;
-  // A resident for many N tiles (the dE/dD GEMM), streamed for one or two
-  const int nk = K / kBK, ntn = (N + kPNT - 1) / kPNT;
-  const bool res = ntn > 2;
-  const int NS = PCfg<PC>::stages(nk, res);
-  if (NS < 3) return -2;
-  const size_t sm = PCfg<PC>::smem(nk, res);
+  static_assert(PCfg<PC>::STAGE * 3 + 128 <= kPSmemMax, "three stages at least");
+  const int NS = PCfg<PC>::stages();
+  const size_t sm = PCfg<PC>::smem();
   static size_t set = 0;
   if (sm > set) {
     if (cudaFuncSetAttribute(k_tc_gemm_p<EPI, PC, TAB, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -845,18 +683,18 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
   const int mtiles = (M + kBM - 1) / kBM;
   DP_LAUNCHED(1);
   k_tc_gemm_p<EPI, PC, TAB, EW><<<mtiles < g_tc_sms ? mtiles : g_tc_sms, 128 + EW * 32, sm, st>>>(
-      M, N, K, res ? 1 : 0, NS, A, B, ep);
+      M, N, K, NS, A, B, ep);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 // the caller's layouts: A pre-tiled in 128-row tiles, B in tiles of 256 rows
 // (the last one ragged), N % 16 == 0, K % 16 == 0
+// layer 0 on the tiled kernel (A formed from T in the stage)
 template <int EPI, int PC, bool TAB>
-int tc_gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B,
-            const TcEpi& ep) {
+int tc_gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* B, const TcEpi& ep) {
   if (M <= 0) return 0;
   if (K <= 0 || K % kBK || N <= 0 || N % 16) return -1;
-  if (EPI != TC_DT && EPI != TC_PLAIN && ep.ldo != N) return -1;
+  if (ep.ldo != N) return -1;
   const int NT = N <= 256 ? N : 256;
   static bool attr = false;
   if (!attr) {
@@ -867,22 +705,8 @@ int tc_gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A, const 
   }
   dim3 grid((N + NT - 1) / NT, (M + kBM - 1) / kBM);
   DP_LAUNCHED(1);
-  k_tc_gemm<EPI, PC, TAB><<<grid, kTcThreads, TcCfg<PC>::SMEM, st>>>(M, N, K, NT, A, B, ep);
+  k_tc_gemm<EPI, PC, TAB><<<grid, kTcThreads, TcCfg<PC>::SMEM, st>>>(M, N, K, NT, B, ep);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
-}
-
-// dE/dT[c][x] for x < 16 gets the second factor of Eq. 2's derivative,
-// sum_b dE/dD[b][x] T[c][b], as the fixed-order sum of the per-N-tile partials
-__global__ void k_dt_reduce(int64_t rows, const int32_t* __restrict__ idx, int M, int slots,
-                            int64_t part_ps, const float* __restrict__ part, float* __restrict__ dT) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= rows * 64) return;
-  const int64_t r = i >> 6;
-  const int e = (int)(i & 63);  // c * 16 + x
-  float acc = 0.0f;
-  for (int sl = 0; sl < slots; ++sl) acc += part[(size_t)sl * part_ps + (size_t)r * 64 + e];
-  const int64_t a = idx ? idx[r] : r;
-  dT[(size_t)a * 4 * M + (e >> 4) * M + (e & 15)] += acc;
 }
 
 // FP32 B [N][K] -> PC BF16 pieces in the pre-tiled B layout: tile nt (rows
@@ -918,18 +742,6 @@ int launch_tile_operand(cudaStream_t st, int N, int K, int pieces, const float* 
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-// the K-short layers: persistent kernel when the row tile's A fits in shared
-// memory, the tiled kernel otherwise; *fused_dt tells whether the dE/dD GEMM
-// completed dE/dT itself (no partials to reduce)
-template <int EPI, int PC, bool TAB>
-static int gemm_k_short(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
-                        const __nv_bfloat16* B, const TcEpi& ep, bool* persistent) {
-  const int rc = tc_gemm_p<EPI, PC, TAB>(st, M, N, K, A, B, ep);
-  if (persistent) *persistent = rc == 0;
-  if (rc != -2) return rc;
-  return tc_gemm<EPI, PC, TAB>(st, M, N, K, A, B, ep);
-}
-
 template <int PC, bool TAB>
 static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const FitNetTC& net, int M,
                        int m_lt, const float* T, float* dT, double* e_atom, const FitScratchTC& s,
@@ -942,7 +754,7 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
   if (m_lt != 16 || M % 4 || M < 16) return -1;  // the fused descriptor wants M< = 16
   // bulk copies and vector loads want 16-byte aligned operands
   auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
-  if (!al(T) || !al(s.part) || !al(s.gph[0]) || !al(s.gph[1])) return -1;
+  if (!al(T) || !al(s.gph[0]) || !al(s.gph[1])) return -1;
   for (int k = 0; k < nl; ++k)
     if (!al(net.WTh[k]) || !al(net.Wh[k]) || !al(s.zh[k]) || !al(net.b[k])) return -1;
   const int64_t R = s.rows;
@@ -970,7 +782,7 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
         ep.T = Tc;
         ep.tidx = id;
         ep.Mw = M;
-        rc = tc_gemm<TC_L0, PC, TAB>(st, rows, net.wout[0], din, nullptr, net.WTh[0], ep);
+        rc = tc_gemm<TC_L0, PC, TAB>(st, rows, net.wout[0], din, net.WTh[0], ep);
       } else if (k == nl - 1) {
         ep.R = net.shortcut[k] ? zb : nullptr;
         ep.ldr = net.wout[k - 1];
@@ -979,16 +791,16 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
         ep.out_h = s.gph[0];
         ep.e_atom = e_atom + (idx ? 0 : r0);
         ep.idx = id;
-        rc = gemm_k_short<TC_LAST, PC, TAB>(st, rows, net.wout[k], net.win[k], s.zh[k - 1], net.WTh[k],
-                                       ep, nullptr);
+        rc = tc_gemm_p<TC_LAST, PC, TAB>(st, rows, net.wout[k], net.win[k], s.zh[k - 1],
+                                         net.WTh[k], ep);
       } else {
         ep.R = net.shortcut[k] ? zb : nullptr;
         ep.ldr = net.wout[k - 1];
         ep.out_a = s.t[k];
         ep.out_b = s.z[k];
         ep.out_h = s.zh[k];
-        rc = gemm_k_short<TC_MID, PC, TAB>(st, rows, net.wout[k], net.win[k], s.zh[k - 1], net.WTh[k],
-                                      ep, nullptr);
+        rc = tc_gemm_p<TC_MID, PC, TAB>(st, rows, net.wout[k], net.win[k], s.zh[k - 1],
+                                        net.WTh[k], ep);
       }
       if (rc) return rc;
     }
@@ -1007,18 +819,17 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.out_h = s.gph[gi ^ 1];
       ep.ldo = net.win[k];
       ep.err = err;
-      const int rc = gemm_k_short<TC_BWD, PC, TAB>(st, rows, net.win[k], net.wout[k], s.gph[gi],
-                                              net.Wh[k], ep, nullptr);
+      const int rc = tc_gemm_p<TC_BWD, PC, TAB>(st, rows, net.win[k], net.wout[k], s.gph[gi],
+                                                net.Wh[k], ep);
       if (rc) return rc;
       gz_prev = s.gz;
       ldgz = net.win[k];
       gi ^= 1;
     }
-    bool dt_done = false;
     {
       // dE/dD = gp_0 W_0^T never leaves the chip: the epilogue contracts it
-      // with T into dE/dT (the tiled kernel leaves per-N-tile partials of the
-      // x < 16 term, the persistent one completes it in registers)
+      // with T into dE/dT, both factors of Eq. 2's derivative (the x < 16
+      // term completed in the epilogue thread's registers)
       TcEpi ep{};
       ep.ldo = din;
       ep.err = err;
@@ -1026,17 +837,9 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.dT = dTc;
       ep.tidx = id;
       ep.Mw = M;
-      ep.part = s.part;
-      ep.part_ps = R * 64;
-      const int rc = gemm_k_short<TC_DT, PC, TAB>(st, rows, din, net.wout[0], s.gph[gi], net.Wh[0], ep,
-                                             &dt_done);
+      const int rc = tc_gemm_p<TC_DT, PC, TAB>(st, rows, din, net.wout[0], s.gph[gi], net.Wh[0], ep);
       if (rc) return rc;
     }
-    if (dt_done) continue;
-    const int slots = (din + 255) / 256;
-    DP_LAUNCHED(1);
-    k_dt_reduce<<<(int)((rows * 64 + 255) / 256), 256, 0, st>>>(rows, id, M, slots, R * 64, s.part,
-                                                                dTc);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -179,11 +179,9 @@ def test_split_mode_water_two_types(dp, water_model_path):
 
 
 def test_split_mode_wide_fitting_fallback(dp, model_dir):
-    # fitting layers 256 wide: the hidden and backward layers (two N tiles)
-    # stream A with B through the persistent kernel's stages; the dE/dD GEMM
-    # keeps A resident, and 16 K chunks x 3 pieces leave too little shared
-    # memory for three B stages, so it runs on the tiled kernel (dE/dT second
-    # factor through per-N-tile partials)
+    # fitting layers 256 wide: K = 256 is the most the persistent kernel
+    # takes (16 K chunks); every K-short GEMM streams A with B through its
+    # stages, the dE/dD GEMM over 16 N tiles of 128 columns
     spec = inputs.ModelSpec(1, (32, 64, 128), 16, (256, 256, 256))
     path = str(model_dir / "cu_wide256.model")
     inputs.write_seeded_model(path, spec, seed=7, std=1.0)
@@ -202,7 +200,7 @@ def test_split_mode_wide_fitting_fallback(dp, model_dir):
     dei = float(np.abs(Ei - r["atom_energy"]).max())
     fr = rmse(F, r["force"])
     frms = float(np.sqrt((r["force"] ** 2).mean()))
-    PARITY_LOG.append(dict(case="tc split Cu 500, 256-wide fitting (tiled fallback)",
+    PARITY_LOG.append(dict(case="tc split Cu 500, 256-wide fitting",
                            natoms=len(x), max_dEi=dei, force_rmse=fr, force_rms=frms))
     assert dei < 2e-5 * float(np.abs(r["atom_energy"]).max()), dei
     assert fr < max(1e-5, 3e-5 * frms), (fr, frms)
