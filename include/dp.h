@@ -69,6 +69,12 @@ typedef struct {
   int tanh_table;      /* fitting-net activation: 0 tanh [0]; 1 the tanh table
                           of Sec. 3.5 (second order on [0, 8) in intervals of
                           1/128, odd, 1 beyond 8; error < 2.3e-7) */
+  int md_graphs;       /* dp_md_step: 1 [1] replays the launches of a step
+                          without a list rebuild as one CUDA graph (captured
+                          once per system and invalidated when a buffer is
+                          reallocated); 0 launches every kernel.  The results
+                          are bitwise the same; not used while profiling or
+                          when thermo output is requested */
 } dp_options;
 
 /* Thermodynamic record of one MD step (Sec. 4). */

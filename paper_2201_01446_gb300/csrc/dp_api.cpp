@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -23,6 +24,9 @@ constexpr double kEvA3Bar = 1.602176634e6;
 // DP_FAULT=alloc:N makes the N-th device allocation of the process fail
 // (host-side injection; nothing on the GPU is disturbed).
 long g_alloc_count = 0;
+// bumped by every device (re)allocation: a captured CUDA graph holds raw
+// pointers and is valid only while no buffer it uses has moved
+std::atomic<unsigned long long> g_alloc_gen{0};
 long g_alloc_fail_at = -1;
 bool g_fault_parsed = false;
 
@@ -53,6 +57,7 @@ cudaError_t ensure(DevBuf& b, size_t bytes) {
   ++g_alloc_count;
   if (g_alloc_fail_at > 0 && g_alloc_count == g_alloc_fail_at) return cudaErrorMemoryAllocation;
   b.release();
+  g_alloc_gen.fetch_add(1);
   cudaError_t e = cudaMalloc(&b.p, bytes);
   if (e == cudaSuccess) {
     b.bytes = bytes;
@@ -120,7 +125,9 @@ struct dp_handle {
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[DP_NPHASE];
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pool;
+  cudaStream_t cap_st = nullptr;  // private stream for CUDA-graph capture
   ~dp_handle() {
+    if (cap_st) cudaStreamDestroy(cap_st);
     for (auto& v : prof_ev)
       for (auto& e : v) prof_pool.push_back(e);
     for (auto& e : prof_pool) {
@@ -139,6 +146,16 @@ struct dp_system {
   double box[9] = {0};
   int64_t step = 0;
   bool f_valid = false;
+  // a step without a list rebuild, captured as one CUDA graph
+  cudaGraphExec_t gexec = nullptr;
+  unsigned long long ggen = 0;  // g_alloc_gen at capture
+  double gdt = 0.0;
+  unsigned long long glaunches = 0;  // kernel launches the graph replays
+  int gplain = 0;  // plain steps since the last rebuild (lazy set-up done)
+  bool gbroken = false;  // capture failed once: launch normally from now on
+  ~dp_system() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+  }
 };
 
 namespace {
@@ -703,6 +720,7 @@ void dp_options_default(dp_options* o) {
   o->rebuild_every = 10;
   o->embed_precision = 0;
   o->tanh_table = 0;
+  o->md_graphs = 1;
 }
 
 const char* dp_version(void) { return "dp-gb300 0.1 (sm_103a; tabulated FP32 embedding, FP32 SIMT fitting)"; }
@@ -739,7 +757,8 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
     return bail(DP_ERR_ARG);
   if (h->opt.tabulated < 0 || h->opt.tabulated > 1 || h->opt.fit_precision < 0 ||
       h->opt.fit_precision > 2 || (h->opt.embed_precision != 0 && h->opt.embed_precision != 2) ||
-      h->opt.tanh_table < 0 || h->opt.tanh_table > 1)
+      h->opt.tanh_table < 0 || h->opt.tanh_table > 1 || h->opt.md_graphs < 0 ||
+      h->opt.md_graphs > 1)
     return bail(DP_ERR_UNIMPLEMENTED);
   HostModel m;
   std::string why;
@@ -1455,7 +1474,77 @@ dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_th
   const double vol = L[0] * L[1] * L[2];
   if (thermo) CK(ensure(s->thermo, sizeof(double) * 16 * std::max(nsteps, 1)), "alloc thermo");
   CKS(clear_status(h));
+  // the launches of a step without a rebuild (kick + drift, FP32 mirror,
+  // evaluation, kick); no host synchronisation inside
+  auto plain_step = [&]() -> dp_status {
+    launch_kick_drift(h->st, n, P<double>(w.x), P<double>(s->v), P<double>(w.f),
+                      P<int32_t>(w.types), P<double>(s->inv_mass_acc), dt_fs, P<double>(w.xref),
+                      half_skin2, P<int32_t>(h->status));
+    launch_mirror(h->st, n, P<double>(w.x), P<int32_t>(w.cellc), P<int32_t>(w.types), w.geom,
+                  P<float4>(w.off));
+    CKS(evaluate(h, w));
+    launch_kick(h->st, n, P<double>(s->v), P<double>(w.f), P<int32_t>(w.types),
+                P<double>(s->inv_mass_acc), P<double>(s->mass), dt_fs, nullptr);
+    return DP_OK;
+  };
   for (int k = 0; k < nsteps; ++k) {
+    const bool rebuild_now = (s->step + 1) % h->opt.rebuild_every == 0;
+    // graph replay: plain steps, once one plain step since the last rebuild
+    // has run normally (every lazy allocation and attribute set is done)
+    if (!rebuild_now && h->opt.md_graphs && !h->prof && !thermo && !s->gbroken &&
+        s->gplain > 0 && n > 0) {
+      if (s->gexec && (s->ggen != g_alloc_gen.load() || s->gdt != dt_fs)) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+      }
+      if (!s->gexec) {
+        const unsigned long long l0 = g_dp_launches_tl;
+        const unsigned long long gen = g_alloc_gen.load();
+        const bool dead0 = h->dead;
+        cudaGraph_t graph = nullptr;
+        // captured on a private stream (the caller's may be the legacy
+        // default stream, which cannot be captured), replayed on the caller's
+        if (!h->cap_st) cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking);
+        cudaStream_t user_st = h->st;
+        bool ok = h->cap_st &&
+                  cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        dp_status st = DP_ERR_CUDA;
+        if (ok) {
+          h->st = h->cap_st;
+          st = plain_step();
+          h->st = user_st;
+          ok = cudaStreamEndCapture(h->cap_st, &graph) == cudaSuccess;
+        }
+        ok = ok && st == DP_OK && g_alloc_gen.load() == gen;
+        if (ok && cudaGraphInstantiate(&s->gexec, graph, 0) != cudaSuccess) {
+          s->gexec = nullptr;
+          ok = false;
+        }
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();  // a failed capture leaves a non-sticky error
+        // nothing ran during the capture: a capture error poisons nothing
+        h->dead = dead0;
+        const unsigned long long nl = g_dp_launches_tl - l0;
+        g_dp_launches_tl -= nl;  // counted at each replay instead
+        __atomic_fetch_sub(&g_dp_launches, nl, __ATOMIC_RELAXED);
+        if (ok) {
+          s->ggen = gen;
+          s->gdt = dt_fs;
+          s->glaunches = nl;
+        } else {
+          s->gbroken = true;
+          h->err.clear();
+        }
+      }
+      if (s->gexec) {
+        CK(cudaGraphLaunch(s->gexec, h->st), "graph launch");
+        DP_LAUNCHED(s->glaunches);
+        s->step += 1;
+        s->f_valid = true;
+        ++s->gplain;
+        continue;
+      }
+    }
     Phase ph1(h, 4);
     launch_kick_drift(h->st, n, P<double>(w.x), P<double>(s->v), P<double>(w.f),
                       P<int32_t>(w.types), P<double>(s->inv_mass_acc), dt_fs, P<double>(w.xref),
@@ -1466,9 +1555,17 @@ dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_th
       CKS(read_status(h));
       CKS(status_errors(h));
       CKS(rebuild(h, w, L, h->rc + h->opt.skin));
+      // a rebuild may change launch parameters (list capacity, cell grid,
+      // tiles) baked into the graph: capture again after it
+      s->gplain = 0;
+      if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+      }
     } else {
       launch_mirror(h->st, n, P<double>(w.x), P<int32_t>(w.cellc), P<int32_t>(w.types), w.geom,
                     P<float4>(w.off));
+      ++s->gplain;
     }
     ph1.end();
     CKS(evaluate(h, w));

@@ -11,7 +11,10 @@
 
 // Number of kernels this library has launched in the process (all threads).
 extern unsigned long long g_dp_launches;
-#define DP_LAUNCHED(k) __atomic_fetch_add(&g_dp_launches, (unsigned long long)(k), __ATOMIC_RELAXED)
+extern thread_local unsigned long long g_dp_launches_tl;  // this thread's share
+#define DP_LAUNCHED(k)                                                               \
+  (__atomic_fetch_add(&g_dp_launches, (unsigned long long)(k), __ATOMIC_RELAXED),    \
+   g_dp_launches_tl += (unsigned long long)(k))
 
 // Per-call device status words (int32).  Kernels only ever add / max into them.
 enum {

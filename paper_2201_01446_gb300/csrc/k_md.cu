@@ -3,6 +3,7 @@
 #include "dp_internal.h"
 
 unsigned long long g_dp_launches = 0;
+thread_local unsigned long long g_dp_launches_tl = 0;
 
 namespace {
 

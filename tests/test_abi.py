@@ -40,7 +40,7 @@ def test_defaults_and_version():
     assert o.tabulated == 1 and o.fit_precision == 0
     assert abs(o.table_step - 0.01) < 1e-15 and o.s_max == 2.0
     assert o.skin == 2.0 and o.rebuild_every == 10
-    assert o.embed_precision == 0 and o.tanh_table == 0
+    assert o.embed_precision == 0 and o.tanh_table == 0 and o.md_graphs == 1
     assert "sm_103a" in dp.dp_version()
 
 

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_2201_01446_gb300 import inputs
-from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, TABLE_H, rmse
+from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, PARITY_LOG, TABLE_H, rmse
 
 pytestmark = pytest.mark.gpu
 
@@ -104,3 +104,35 @@ def test_skin_violation_reported(dp, stress):
         assert e.value.code == 10
     finally:
         dp.dp_system_destroy(s)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_md_graph_replay_bitwise(dp, cu_stress_path, prec):
+    # plain MD steps replayed as one captured CUDA graph give bitwise the
+    # launches' results, across list rebuilds, and count the same launches
+    import time
+    x, v, t, box = _system(4, seed=16)
+    out = {}
+    for graphs in (0, 1):
+        o = dp.dp_options_default()
+        o.md_graphs = graphs
+        o.fit_precision = prec
+        o.embed_precision = prec
+        h = dp.dp_create(cu_stress_path, 1, CU_RC, CU_RCS, [CU_SEL], options=o, stream=None)
+        try:
+            s = dp.dp_system_create(h, x, v, t, [inputs.MASS_CU], box)
+            dp.dp_md_step(h, s, 3, 1.0)
+            l0 = dp.dp_stats(h, s)["kernel_launches"]
+            t0 = time.perf_counter()
+            dp.dp_md_step(h, s, 22, 1.0)  # rebuilds at steps 10 and 20
+            xg, vg, fg = dp.dp_system_get(h, s, len(x))
+            dt = time.perf_counter() - t0
+            out[graphs] = (xg, vg, fg, dp.dp_stats(h, s)["kernel_launches"] - l0, dt)
+            dp.dp_system_destroy(s)
+        finally:
+            dp.dp_destroy(h)
+    a, b = out[0], out[1]
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    assert a[3] == b[3], (a[3], b[3])
+    PARITY_LOG.append(dict(case=f"md graphs 256 atoms prec {prec}", ms_per_step_launches=a[4] / 22e-3,
+                           ms_per_step_graphs=b[4] / 22e-3))

@@ -196,7 +196,7 @@ def test_set_params_matches_oracle_and_autograd(dp, cu_stress_path):
         Et = autograd.energy_params(h, pf, pt, x, t, box)
         Et.backward()
         E2, gf, gt = dp.dp_param_grad(h, x, t, box)
-        assert float(Et) == E2
+        assert float(Et.detach()) == E2
         assert np.array_equal(pf.grad.numpy(), gf) and np.array_equal(pt.grad.numpy(), gt)
         # a gradient step on the fitting parameters lowers E by eta |g|^2 to
         # first order: E(p - eta g) = E - eta |g|^2 + O(eta^2); two step
