@@ -199,6 +199,22 @@ dp_status dp_descriptor(dp_handle* h, int64_t natoms, const double* coords,
 dp_status dp_fitting(dp_handle* h, int64_t natoms, const int32_t* types, const float* T,
                      double* e_out, float* dT_out);
 
+/* Several independent systems in one evaluation (a serving batch of small
+ * boxes): one neighbor list per system, one launch of each embedding and
+ * fitting kernel over all atoms.  HOST arrays:
+ *   natoms  [nsys] atoms per system; coords [sum natoms][3] and types
+ *           [sum natoms], the systems one after another;
+ *   boxes   [nsys][3][3] orthorhombic boxes (rows);
+ *   energies [nsys] eV; forces [sum natoms][3] eV/A; virials [nsys][9] eV.
+ * Needs tabulated = 1 and embed_precision = 2 (DP_ERR_UNIMPLEMENTED
+ * otherwise).  A system's forces are bitwise those of dp_compute on it
+ * alone; its energy and virial are summed in another order (per atom and
+ * per tile of 32 atoms, in FP64), so they agree to rounding.  An error in
+ * any system (sel overflow, table range, box) fails the call. */
+dp_status dp_compute_batch(dp_handle* h, int nsys, const int64_t* natoms, const double* coords,
+                           const int32_t* types, const double* boxes, double* energies,
+                           double* forces, double* virials);
+
 /* ---------------------------------------------------------------------------
  * Parameter gradients (training use of the same energy, Sec. 2.1 and 3.2):
  * dE/d(fitting-net parameters) and dE/d(table coefficients).

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -84,6 +85,9 @@ struct Work {
   bool have_idx = false;
   TileMap tiles{};  // the same grouping in tiles of 32 (tensor-core embedding)
   DevBuf tc_pairs, tc_hist, tc_range;  // sorted pairs / bin ends the forward leaves
+  // several systems in one evaluation: tile index lists padded per system,
+  // atom -> system, per-system first atom and cell edges, per-tile virial
+  DevBuf bidx, sys_of, sys_base, sys_edge, vir_tile;
 };
 
 }  // namespace
@@ -522,6 +526,77 @@ dp_status rebuild(dp_handle* h, Work& w, const double* L, double rlist) {
                       P<int32_t>(w.cell_start), P<int32_t>(w.cell_atoms), g, rlist, rc2,
                       h->ntypes, P<int32_t>(h->sel_dev), w.cap, P<uint32_t>(w.nlist),
                       P<int32_t>(w.nn), P<int32_t>(h->status));
+    CK(cudaGetLastError(), "neighbor kernels");
+    CKS(read_status(h));
+    if (h->status_host[ST_LISTOVF] == 0) return DP_OK;
+    w.cap = ((int)(h->status_host[ST_MAXLIST] * 1.1) + 8 + 31) / 32 * 32;
+  }
+  return fail(h, DP_ERR_CUDA, "neighbor list capacity did not converge");
+}
+
+// neighbor lists of several systems (atoms [base[s], base[s+1]) in a box of
+// edges L[s]) into one list array: each system is binned and listed on its
+// own (the cell arrays are reused in stream order); entries hold
+// system-local indices
+dp_status rebuild_batch(dp_handle* h, Work& w, const std::vector<int64_t>& base,
+                        const std::vector<std::array<double, 3>>& Ls, double rlist,
+                        std::vector<CellGeom>& gs) {
+  const int nsys = (int)base.size() - 1;
+  const int64_t n = w.n;
+  gs.assign(nsys, CellGeom{});
+  long long maxcell = 1;
+  double est = 0.0;
+  for (int q = 0; q < nsys; ++q) {
+    CellGeom g{};
+    long long ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+      if (Ls[q][a] < rlist)
+        return fail(h, DP_ERR_BOX, "a box edge is shorter than the neighbor-list cutoff");
+      g.L[a] = Ls[q][a];
+      g.nc[a] = std::max(1, (int)std::floor(Ls[q][a] / rlist));
+      g.edge[a] = Ls[q][a] / g.nc[a];
+      g.edgef[a] = (float)g.edge[a];
+      ncell *= g.nc[a];
+    }
+    if (ncell > (1LL << 30)) return fail(h, DP_ERR_BOX, "too many cells");
+    g.ncell = ncell;
+    gs[q] = g;
+    maxcell = std::max(maxcell, ncell);
+    const double vol = Ls[q][0] * Ls[q][1] * Ls[q][2];
+    est = std::max(est, (double)(base[q + 1] - base[q]) / vol * 4.18879020479 * rlist * rlist * rlist);
+  }
+  w.geom = gs.empty() ? CellGeom{} : gs[0];
+  w.rlist = rlist;
+  if (n == 0) return DP_OK;
+  CK(ensure(w.cell_count, (maxcell + 1) * sizeof(int32_t)), "alloc cells");
+  CK(ensure(w.cell_fill, (maxcell + 1) * sizeof(int32_t)), "alloc cells");
+  CK(ensure(w.cell_start, (maxcell + 1) * sizeof(int32_t)), "alloc cells");
+  w.cap = std::max(32, ((int)(1.25 * est + 32) + 31) / 32 * 32);
+  const float rc2 = (float)(h->rc * h->rc);
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    CK(ensure(w.nlist, (size_t)n * w.cap * sizeof(uint32_t)), "alloc neighbor list");
+    CK(cudaMemsetAsync(P<int32_t>(h->status) + ST_MAXLIST, 0, 2 * sizeof(int32_t), h->st), "memset");
+    for (int q = 0; q < nsys; ++q) {
+      const int64_t b = base[q], ns = base[q + 1] - base[q];
+      if (ns == 0) continue;
+      const CellGeom& g = gs[q];
+      CK(cudaMemsetAsync(w.cell_count.p, 0, (g.ncell + 1) * sizeof(int32_t), h->st), "memset");
+      CK(cudaMemsetAsync(w.cell_fill.p, 0, (g.ncell + 1) * sizeof(int32_t), h->st), "memset");
+      double* xb = P<double>(w.x) + 3 * b;
+      int32_t* cb = P<int32_t>(w.cellc) + b;
+      float4* ob = P<float4>(w.off) + b;
+      launch_wrap_bin(h->st, ns, xb, g, cb, P<int32_t>(w.cell_count));
+      launch_scan(h->st, P<int32_t>(w.cell_count), P<int32_t>(w.cell_start), g.ncell);
+      launch_scatter(h->st, ns, cb, P<int32_t>(w.cell_start), P<int32_t>(w.cell_fill),
+                     P<int32_t>(w.cell_tmp));
+      launch_cell_sort(h->st, g.ncell, P<int32_t>(w.cell_start), P<int32_t>(w.cell_tmp),
+                       P<int32_t>(w.cell_atoms));
+      launch_mirror(h->st, ns, xb, cb, P<int32_t>(w.types) + b, g, ob);
+      launch_build_list(h->st, ns, xb, cb, ob, P<int32_t>(w.cell_start), P<int32_t>(w.cell_atoms),
+                        g, rlist, rc2, h->ntypes, P<int32_t>(h->sel_dev), w.cap,
+                        P<uint32_t>(w.nlist) + (size_t)b * w.cap, P<int32_t>(w.nn) + b,
+                        P<int32_t>(h->status));
+    }
     CK(cudaGetLastError(), "neighbor kernels");
     CKS(read_status(h));
     if (h->status_host[ST_LISTOVF] == 0) return DP_OK;
@@ -1034,6 +1109,136 @@ dp_status dp_compute(dp_handle* h, int64_t natoms, const double* coords, const i
       CK(cudaMemcpyAsync(atom_energy, w.e_atom.p, sizeof(double) * n, kind, h->st), "e copy");
   }
   if (!device_ptrs) CK(cudaStreamSynchronize(h->st), "result copy");
+  return DP_OK;
+}
+
+dp_status dp_compute_batch(dp_handle* h, int nsys, const int64_t* natoms, const double* coords,
+                           const int32_t* types, const double* boxes, double* energies,
+                           double* forces, double* virials) {
+  CKS(check_handle(h));
+  if (nsys < 0 || (nsys > 0 && (!natoms || !boxes || !energies || !virials)))
+    return fail(h, DP_ERR_ARG, "bad argument");
+  if (!(h->opt.tabulated && h->opt.embed_precision == 2))
+    return fail(h, DP_ERR_UNIMPLEMENTED,
+                "batched evaluation needs the tabulated tensor-core embedding (embed_precision 2)");
+  std::vector<int64_t> base(nsys + 1, 0);
+  for (int q = 0; q < nsys; ++q) {
+    if (natoms[q] < 0) return fail(h, DP_ERR_ARG, "negative atom count");
+    base[q + 1] = base[q] + natoms[q];
+  }
+  const int64_t n = base[nsys];
+  if (n >= (1LL << 27)) return fail(h, DP_ERR_ARG, "at most 2^27 atoms per call");
+  if (n > 0 && (!coords || !types || !forces)) return fail(h, DP_ERR_ARG, "null pointer");
+  std::vector<std::array<double, 3>> Ls(nsys);
+  for (int q = 0; q < nsys; ++q) CKS(box_lengths(h, boxes + 9 * q, Ls[q].data()));
+  Work& w = h->w;
+  CKS(load_coords(h, w, n, coords, types, 0));
+  CKS(clear_status(h));
+  // tiles: each system's atoms of a type start a new tile (padding entries
+  // -1), so a tile belongs to one system and its virial row to that system
+  std::vector<int32_t> pidx;
+  std::vector<std::vector<int64_t>> sys_tiles(nsys);
+  TileMap tm{};
+  tm.ntypes = h->ntypes;
+  for (int t = 0; t < h->ntypes; ++t) {
+    tm.atom_off[t] = (int64_t)pidx.size();
+    tm.tile_off[t] = (int64_t)pidx.size() / 32;
+    for (int q = 0; q < nsys; ++q) {
+      const int64_t t0 = (int64_t)pidx.size() / 32;
+      for (int64_t i = base[q]; i < base[q + 1]; ++i)
+        if (h->type_map[types[i]] == t) pidx.push_back((int32_t)i);
+      while (pidx.size() % 32) pidx.push_back(-1);
+      for (int64_t k = t0; k < (int64_t)pidx.size() / 32; ++k) sys_tiles[q].push_back(k);
+    }
+    tm.atom_cnt[t] = (int64_t)pidx.size() - tm.atom_off[t];
+  }
+  tm.tile_off[h->ntypes] = (int64_t)pidx.size() / 32;
+  const int64_t ntile = tm.tile_off[h->ntypes];
+  std::vector<int32_t> sys_of(std::max<int64_t>(n, 1)), sys_base(std::max(nsys, 1));
+  std::vector<float4> sys_edge(std::max(nsys, 1));
+  for (int q = 0; q < nsys; ++q) {
+    for (int64_t i = base[q]; i < base[q + 1]; ++i) sys_of[i] = q;
+    sys_base[q] = (int32_t)base[q];
+  }
+  std::vector<CellGeom> geoms;
+  CKS(rebuild_batch(h, w, base, Ls, h->rc, geoms));
+  CKS(status_errors(h));
+  if (n > 0) {
+    const EnvParams ep = env_params(h);
+    for (int q = 0; q < nsys; ++q)
+      sys_edge[q] = make_float4(geoms[q].edgef[0], geoms[q].edgef[1], geoms[q].edgef[2], 0.0f);
+    CK(ensure(w.bidx, std::max<size_t>(pidx.size(), 1) * sizeof(int32_t)), "alloc tiles");
+    CK(ensure(w.sys_of, sys_of.size() * sizeof(int32_t)), "alloc systems");
+    CK(ensure(w.sys_base, sys_base.size() * sizeof(int32_t)), "alloc systems");
+    CK(ensure(w.sys_edge, sys_edge.size() * sizeof(float4)), "alloc systems");
+    CK(ensure(w.vir_tile, (size_t)std::max<int64_t>(ntile, 1) * 9 * sizeof(double)), "alloc virial");
+    CK(ensure(w.tc_pairs, (size_t)std::max<int64_t>(tab_tc_pair_elems(ep, ntile), 1) * 16),
+       "alloc sorted pairs");
+    CK(ensure(w.tc_hist, (size_t)std::max<int64_t>(tab_tc_hist_elems(ep, ntile), 8) * 2),
+       "alloc bin ends");
+    CK(ensure(w.tc_range, (size_t)std::max<int64_t>(ntile, 1) * 8), "alloc bin ranges");
+    CK(cudaMemcpyAsync(w.bidx.p, pidx.data(), pidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                       h->st),
+       "tiles upload");
+    CK(cudaMemcpyAsync(w.sys_of.p, sys_of.data(), sys_of.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, h->st),
+       "systems upload");
+    CK(cudaMemcpyAsync(w.sys_base.p, sys_base.data(), sys_base.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, h->st),
+       "systems upload");
+    CK(cudaMemcpyAsync(w.sys_edge.p, sys_edge.data(), sys_edge.size() * sizeof(float4),
+                       cudaMemcpyHostToDevice, h->st),
+       "systems upload");
+    tm.idx = P<int32_t>(w.bidx);
+    launch_zero_forces(h->st, n, P<unsigned long long>(w.ffix));
+    CK(cudaMemsetAsync(w.pairs.p, 0, sizeof(unsigned long long), h->st), "memset");
+    if (launch_tab_fwd_tc(h->st, tm, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
+                          w.cap, w.geom, ep, P<__nv_bfloat16>(h->tabF), P<float>(h->tc_scratch),
+                          P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist), P<int2>(w.tc_range),
+                          P<float>(w.T), P<int32_t>(h->status), P<unsigned long long>(w.pairs),
+                          P<int32_t>(w.sys_of), P<int32_t>(w.sys_base), P<float4>(w.sys_edge)))
+      return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core embedding cannot run this model shape");
+    for (int t = 0; t < h->ntypes; ++t) {
+      const int64_t cnt = w.have_idx ? w.type_count[t] : n;
+      if (cnt == 0) continue;
+      const int32_t* idx = w.have_idx ? P<int32_t>(w.idx) + w.type_off[t] : nullptr;
+      CKS(run_fitting(h, t, cnt, idx, P<float>(w.T), P<float>(w.dT), P<double>(w.e_atom)));
+      if (!w.have_idx) break;
+    }
+    if (launch_tab_bwd_tc(h->st, tm, P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist),
+                          P<int2>(w.tc_range), ep, P<__nv_bfloat16>(h->tabB), P<float>(w.dT),
+                          P<unsigned long long>(w.ffix), P<double>(w.vir_part),
+                          (int)tab_tc_slots(), P<int32_t>(h->status), P<double>(w.vir_tile)))
+      return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core embedding cannot run this model shape");
+    launch_force_finalize(h->st, n, P<unsigned long long>(w.ffix), P<double>(w.f),
+                          P<int32_t>(h->status));
+    launch_check_energy(h->st, n, P<double>(w.e_atom), P<int32_t>(h->status));
+    CK(cudaGetLastError(), "evaluation kernels");
+  }
+  CKS(read_status(h));
+  CKS(status_errors(h));
+  std::vector<double> e(std::max<int64_t>(n, 1)), vt((size_t)std::max<int64_t>(ntile, 1) * 9);
+  if (n > 0) {
+    CK(cudaMemcpyAsync(e.data(), w.e_atom.p, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st),
+       "energy copy");
+    CK(cudaMemcpyAsync(vt.data(), w.vir_tile.p, sizeof(double) * 9 * ntile, cudaMemcpyDeviceToHost,
+                       h->st),
+       "virial copy");
+    CK(cudaMemcpyAsync(forces, w.f.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->st),
+       "force copy");
+    CK(cudaStreamSynchronize(h->st), "result copy");
+  }
+  // per-system sums in a fixed order (atoms, then the system's tiles)
+  for (int q = 0; q < nsys; ++q) {
+    double E = 0.0;
+    for (int64_t i = base[q]; i < base[q + 1]; ++i) E += e[i];
+    energies[q] = E;
+    for (int a = 0; a < 9; ++a) {
+      double v = 0.0;
+      for (int64_t k : sys_tiles[q]) v += vt[(size_t)k * 9 + a];
+      virials[9 * q + a] = v;
+    }
+  }
   return DP_OK;
 }
 

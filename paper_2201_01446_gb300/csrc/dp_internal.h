@@ -123,15 +123,21 @@ int64_t tab_grad_part_floats(const EnvParams& ep);
 int launch_tab_grad_tc(cudaStream_t st, const TileMap& tm, const float4* pairs,
                        const uint16_t* hist, const int2* range, const EnvParams& ep,
                        const float* dT, float* part, double* grad);
+// Several systems in one launch: sys_of [atoms] -> system, sys_base [systems]
+// first atom, sys_edge [systems] cell edges (x, y, z, 0); the neighbor lists
+// then hold system-local indices.  All NULL: one system.
 int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, const uint32_t* nlist,
                       const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
                       const __nv_bfloat16* tabF, float* scratch, float4* pairs_out,
                       uint16_t* hist_out, int2* range_out, float* T, int32_t* status,
-                      unsigned long long* pair_count);
+                      unsigned long long* pair_count, const int32_t* sys_of = nullptr,
+                      const int32_t* sys_base = nullptr, const float4* sys_edge = nullptr);
+// vir_tile != NULL: the virial as one FP64 row of 9 per tile (several systems
+// in one launch, tiles padded per system) instead of the per-slot partials
 int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs, const uint16_t* hist,
                       const int2* range, const EnvParams& ep, const __nv_bfloat16* tabB,
                       const float* dT, unsigned long long* ffix, double* vir_part, int vir_slots,
-                      int32_t* status);
+                      int32_t* status, double* vir_tile = nullptr);
 
 // plain untabulated embedding (the comparator of the tabulation), FP32
 int plain_kernel_slots(int64_t n);

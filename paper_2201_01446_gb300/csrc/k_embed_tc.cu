@@ -171,7 +171,9 @@ __device__ __forceinline__ int tile_atom(const TileMap& tm, int ti, int64_t tile
 // for the backward.  On return hist holds the end
 // of every bin (all zero when the atom has no slot: padding or overflow).
 // Returns the pairs within rc; lo/hi the occupied bin range of this atom.
-__device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ off,
+// off: the offsets of the atom's system, whose first atom is jb (neighbor
+// entries hold system-local indices; the pair copy gets global ones)
+__device__ __forceinline__ int sort_atom(int atom, int jb, const float4* __restrict__ off,
                                          const uint32_t* __restrict__ nlist,
                                          const int32_t* __restrict__ nn, int cap,
                                          const CellGeom& g, const EnvParams& ep, int scap, int* hist,
@@ -184,7 +186,7 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
   lo = INT_MAX;
   hi = -1;
   if (atom < 0) return 0;
-  const float4 oi = off[atom];
+  const float4 oi = off[atom - jb];
   const int cnt = min(nn[atom], cap);
   const uint32_t* L = nlist + (size_t)atom * cap;
   const unsigned below = (1u << lane) - 1u;
@@ -229,7 +231,7 @@ __device__ __forceinline__ int sort_atom(int atom, const float4* __restrict__ of
     const unsigned bal = __ballot_sync(0xffffffffu, in);
     const int q = np + __popc(bal & below);
     if (in && q < scap) {
-      stg[2 * q] = make_float4(__int_as_float(bin), __int_as_float((int)(e >> 5)), Pk.s, Pk.u);
+      stg[2 * q] = make_float4(__int_as_float(bin), __int_as_float(jb + (int)(e >> 5)), Pk.s, Pk.u);
       stg[2 * q + 1] = make_float4(Pk.dx, Pk.dy, Pk.dz, Pk.ir);
     }
     np += __popc(bal);
@@ -284,7 +286,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                  float* __restrict__ scratch, float4* __restrict__ pairs_out,
                  uint16_t* __restrict__ hist_out, int2* __restrict__ range_out,
                  float* __restrict__ T,
-                 int32_t* __restrict__ status, unsigned long long* __restrict__ pair_count) {
+                 int32_t* __restrict__ status, unsigned long long* __restrict__ pair_count,
+                 const int32_t* __restrict__ sys_of, const int32_t* __restrict__ sys_base,
+                 const float4* __restrict__ sys_edge) {
   const FwdCfg cf = fwd_cfg(ep);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -344,7 +348,19 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int atom = tile_atom(tm, ti, tile, al);
       if (lane == 0) s_atom[al] = atom;
       int lo, hi;
-      const int np = sort_atom(atom, off, nlist, nn, cap, g, ep, scap, whist, nbins,
+      // several systems in one launch: the atom's system gives the base of
+      // its offsets and the cell edges of the stencil shifts
+      int jb = 0;
+      CellGeom gs = g;
+      if (sys_of && atom >= 0) {
+        const int sy = sys_of[atom];
+        jb = sys_base[sy];
+        const float4 e4 = sys_edge[sy];
+        gs.edgef[0] = e4.x;
+        gs.edgef[1] = e4.y;
+        gs.edgef[2] = e4.z;
+      }
+      const int np = sort_atom(atom, jb, off + jb, nlist, nn, cap, gs, ep, scap, whist, nbins,
                                reinterpret_cast<float4*>(sc_cta) + (size_t)al * scap,
                                sc_cta + 4 * (size_t)kAtoms * scap + (size_t)al * scap, wstg,
                                pairs_out + ((size_t)tile * kAtoms + al) * scap, lane, nrange,
@@ -593,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                  EnvParams ep,
                  const __nv_bfloat16* __restrict__ tabB, int scap, const float* __restrict__ dT,
                  unsigned long long* __restrict__ ffix, double* __restrict__ vir_part,
-                 int32_t* __restrict__ status) {
+                 int32_t* __restrict__ status, double* __restrict__ vir_tile) {
   const BwdCfg cf = bwd_cfg(ep);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -606,6 +622,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   __shared__ int s_abort;
   __shared__ int s_atom[kAtoms];
   __shared__ double s_vir[kThreads / 32][9];
+  __shared__ double s_vt[kThreads / 32][9];  // this tile's virial per warp (vir_tile)
   volatile int* abort_flag = &s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -934,9 +951,17 @@ __global__ void __launch_bounds__(kThreads, 2)
       float vv = vl[0];
 #pragma unroll
       for (int a = 1; a < 9; ++a) vv = lane == a ? vl[a] : vv;
-      s_vir[warp][lane] += (double)vv;
+      if (vir_tile) s_vt[warp][lane] = (double)vv;
+      else s_vir[warp][lane] += (double)vv;
     }
     __syncthreads();  // shist and s_atom are refilled by the next tile
+    if (vir_tile && tid < 9) {
+      // one row per tile (several systems in one launch: tiles never span two)
+      double v = 0.0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) v += s_vt[w][tid];
+      vir_tile[(size_t)tile * 9 + tid] = v;
+    }
   }
   if (lane < 9) vir_part[((size_t)blockIdx.x * (kThreads / 32) + warp) * 9 + lane] = s_vir[warp][lane];
   nbad = __reduce_add_sync(0xffffffffu, nbad);
@@ -1122,7 +1147,8 @@ int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, con
                       const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
                       const __nv_bfloat16* tabF, float* scratch, float4* pairs_out,
                       uint16_t* hist_out, int2* range_out, float* T, int32_t* status,
-                      unsigned long long* pair_count) {
+                      unsigned long long* pair_count, const int32_t* sys_of,
+                      const int32_t* sys_base, const float4* sys_edge) {
   if (ep.M > 128 || ep.M % 4 || ep.M < 16) return -1;
   if (tm.ntypes < 1 || tm.ntypes > DP_MAXT || tm.ntypes != ep.ntypes) return -1;
   if (((uintptr_t)tabF & 15) || ((uintptr_t)T & 15)) return -1;
@@ -1142,7 +1168,8 @@ int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, con
   DP_LAUNCHED(1);
   k_tab_fwd_tc<<<grid, kThreads, cf.smem, st>>>(ntile, tm, off, nlist, nn, cap, g, ep, tabF,
                                                 stage_cap_tc(ep), scratch, pairs_out, hist_out,
-                                                range_out, T, status, pair_count);
+                                                range_out, T, status, pair_count, sys_of,
+                                                sys_base, sys_edge);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -1152,7 +1179,7 @@ int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs,
                       const uint16_t* hist,
                       const int2* range, const EnvParams& ep, const __nv_bfloat16* tabB,
                       const float* dT, unsigned long long* ffix, double* vir_part, int vir_slots,
-                      int32_t* status) {
+                      int32_t* status, double* vir_tile) {
   if (ep.M > 128 || ep.M % 4 || ep.M < 16) return -1;
   if (tm.ntypes < 1 || tm.ntypes > DP_MAXT || tm.ntypes != ep.ntypes) return -1;
   if (((uintptr_t)tabB & 15) || ((uintptr_t)dT & 15) || ((uintptr_t)hist & 15)) return -1;
@@ -1171,7 +1198,8 @@ int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs,
   // every slot is written (grid = the full persistent grid, idle CTAs write zeros)
   DP_LAUNCHED(1);
   k_tab_bwd_tc<<<tc_grid(), kThreads, cf.smem, st>>>(ntile, tm, pairs, hist, range, ep, tabB,
-                                                     stage_cap_tc(ep), dT, ffix, vir_part, status);
+                                                     stage_cap_tc(ep), dT, ffix, vir_part, status,
+                                                     vir_tile);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -46,7 +46,7 @@ EXPORTS = ["dp_options_default", "dp_create", "dp_destroy", "dp_last_error", "dp
            "dp_system_step", "dp_md_step", "dp_state_save", "dp_state_load",
            "dp_neighbor_pairs", "dp_table_coeffs", "dp_descriptor", "dp_version",
            "dp_profile", "dp_profile_read", "dp_stats", "dp_neighbor_pairs_static", "dp_fitting",
-           "dp_param_sizes", "dp_param_grad", "dp_get_params", "dp_set_params"]
+           "dp_param_sizes", "dp_param_grad", "dp_get_params", "dp_set_params", "dp_compute_batch"]
 
 DP_NPHASE = 5
 PHASES = ["neighbor_build", "embed_contract_fwd", "fitting", "embed_contract_bwd_forces",
@@ -88,6 +88,7 @@ def _load():
         "dp_param_sizes": (i, [vp, i64p, i64p]),
         "dp_param_grad": (i, [vp, i64, dp_, dp_, dp_, vp, vp, vp]),
         "dp_get_params": (i, [vp, vp, vp]),
+        "dp_compute_batch": (i, [vp, i, vp, vp, vp, vp, vp, vp, vp]),
         "dp_set_params": (i, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -327,6 +328,30 @@ def dp_neighbor_pairs_static(coords, box, rlist, stream=None):
                                         b.ctypes.data_as(C.c_void_p), float(rlist), cnt.value,
                                         C.c_void_p(out.data_ptr()), C.byref(cnt), stream), None)
     return out[:cnt.value]
+
+
+def dp_compute_batch(h, systems):
+    """Several systems [(coords [n, 3], types [n], box [3, 3]), ...] in one
+    evaluation (host arrays): (energies [nsys], [forces [n, 3] per system],
+    virials [nsys, 3, 3])."""
+    nsys = len(systems)
+    counts = np.array([len(np.atleast_2d(x)) if np.size(x) else 0 for x, _, _ in systems], np.int64)
+    n = int(counts.sum())
+    x = np.ascontiguousarray(np.concatenate([np.reshape(x, (-1, 3)) for x, _, _ in systems])
+                             if nsys else np.zeros((0, 3)), np.float64)
+    t = np.ascontiguousarray(np.concatenate([np.ravel(t) for _, t, _ in systems])
+                             if nsys else np.zeros(0), np.int32)
+    boxes = np.ascontiguousarray(np.stack([np.asarray(b, np.float64).reshape(3, 3)
+                                           for _, _, b in systems]) if nsys else np.zeros((1, 3, 3)))
+    e = np.zeros(max(nsys, 1))
+    f = np.zeros((max(n, 1), 3))
+    v = np.zeros((max(nsys, 1), 9))
+    _check(lib.dp_compute_batch(h, nsys, counts.ctypes.data_as(C.c_void_p),
+                                x.ctypes.data_as(C.c_void_p), t.ctypes.data_as(C.c_void_p),
+                                boxes.ctypes.data_as(C.c_void_p), e.ctypes.data_as(C.c_void_p),
+                                f.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p)), h)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    return e[:nsys], [f[off[q]:off[q + 1]] for q in range(nsys)], v[:nsys].reshape(nsys, 3, 3)
 
 
 def dp_param_sizes(h):

@@ -1,0 +1,82 @@
+"""Several systems in one evaluation (dp_compute_batch, the packed launch of
+the serving loop): per system the forces are bitwise those of dp_compute on
+the system alone, energies and virials agree to FP64 summation order; one
+system against the oracle; empty and one-atom systems; copper and two-type
+water; the mode requirement."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_01446_gb300 import inputs
+from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, PARITY_LOG, TABLE_H, rmse
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dp():
+    from paper_2201_01446_gb300 import dp as _dp
+    return _dp
+
+
+def _tc(dp, path, ntypes=1, rc=CU_RC, rcs=CU_RCS, sel=(CU_SEL,), s_max=CU_SMAX):
+    o = dp.dp_options_default()
+    o.embed_precision = 2
+    o.fit_precision = 2
+    o.s_max = s_max
+    return dp.dp_create(path, ntypes, rc, rcs, list(sel), options=o, stream=None)
+
+
+def _check_alone(dp, h, systems, tag):
+    E, F, V = dp.dp_compute_batch(h, systems)
+    worst = 0.0
+    for q, (x, t, box) in enumerate(systems):
+        Ea, Fa, Va, _ = dp.dp_compute(h, x, t, box)
+        assert np.array_equal(F[q], Fa), (tag, q)
+        assert abs(E[q] - Ea) <= 1e-12 * max(1.0, abs(Ea)), (tag, q, E[q], Ea)
+        assert np.abs(V[q] - Va).max() <= 1e-12 * max(1.0, float(np.abs(Va).max())), (tag, q)
+        worst = max(worst, abs(E[q] - Ea) / max(1.0, abs(Ea)))
+    PARITY_LOG.append(dict(case=f"batch vs alone: {tag}", systems=len(systems),
+                           max_rel_energy_diff=worst))
+    return E, F, V
+
+
+def test_batch_copper_matches_alone_and_oracle(dp, cu_stress_path):
+    h = _tc(dp, cu_stress_path)
+    try:
+        systems = [inputs.fcc_copper(5, sigma=0.05, seed=1),
+                   inputs.fcc_copper((3, 4, 5), sigma=0.15, seed=2),
+                   (np.zeros((0, 3)), np.zeros(0, np.int32), np.diag([30.0, 30.0, 30.0])),
+                   (np.array([[1.0, 2.0, 3.0]]), np.zeros(1, np.int32), np.diag([40.0] * 3)),
+                   inputs.fcc_copper(4, sigma=0.1, seed=3)]
+        E, F, V = _check_alone(dp, h, systems, "Cu 500 + 240 + 0 + 1 + 256")
+        assert E[2] == 0.0 and F[2].shape == (0, 3) and not V[2].any()
+        # the 240-atom system (ragged tiles, non-cubic box) against the oracle
+        m = oracle.Model(cu_stress_path)
+        x, t, box = systems[1]
+        r = oracle.evaluate(m, oracle.Table(m, TABLE_H, CU_SMAX), CU_RC, CU_RCS, CU_SEL, x, t, box)
+        frms = float(np.sqrt((r["force"] ** 2).mean()))
+        assert abs(E[1] - r["energy"]) / len(x) < max(1e-6, 5e-6 * np.abs(r["atom_energy"]).mean())
+        assert rmse(F[1], r["force"]) < max(1e-5, 3e-5 * frms)
+        assert np.abs(V[1] - r["virial"]).max() < 1e-4 * np.abs(r["virial"]).max() + 1e-9
+    finally:
+        dp.dp_destroy(h)
+
+
+def test_batch_water_two_types(dp, water_model_path):
+    h = _tc(dp, water_model_path, 2, 6.0, 0.5, (46, 92), 1.25)
+    try:
+        systems = [inputs.water_like(64, L=12.417, seed=s) for s in (3, 4, 5)]
+        _check_alone(dp, h, systems, "3 x water 192")
+    finally:
+        dp.dp_destroy(h)
+
+
+def test_batch_needs_tensor_core_embedding(dp, cu_model_path):
+    h = dp.dp_create(cu_model_path, 1, CU_RC, CU_RCS, [CU_SEL], options=None, stream=None)
+    try:
+        with pytest.raises(dp.DPError) as e:
+            dp.dp_compute_batch(h, [inputs.fcc_copper(3, sigma=0.05, seed=1)])
+        assert e.value.code == 9
+    finally:
+        dp.dp_destroy(h)
