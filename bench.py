@@ -255,8 +255,10 @@ def serve_leg(args, cu_model, pg):
             "requests": len(specs), "errors": st["errors"] + closed["errors"],
             "arrival_rate_per_s": lam, "capacity_req_per_s": capacity,
             "atom_steps_per_s": st["atom_steps_per_s"], "slots": args.serve_slots,
+            "packed_calls": st["packed_calls"], "packed_requests": st["packed_requests"],
             "mix": "Cu 500-500k atoms log-uniform + water 192*2^k (k<8), half eval half MD "
-                   "(Cu 50 steps, water 10), Poisson arrivals at 0.7 x closed-loop capacity"}
+                   "(Cu 50 steps, water 10), Poisson arrivals at 0.7 x closed-loop capacity; "
+                   "queued evaluations of one model packed up to 32768 atoms per call"}
 
 
 def grad_leg(args, model_path, stream):

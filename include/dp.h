@@ -207,10 +207,10 @@ dp_status dp_fitting(dp_handle* h, int64_t natoms, const int32_t* types, const f
  *   boxes   [nsys][3][3] orthorhombic boxes (rows);
  *   energies [nsys] eV; forces [sum natoms][3] eV/A; virials [nsys][9] eV.
  * Needs tabulated = 1 and embed_precision = 2 (DP_ERR_UNIMPLEMENTED
- * otherwise).  A system's forces are bitwise those of dp_compute on it
- * alone; its energy and virial are summed in another order (per atom and
- * per tile of 32 atoms, in FP64), so they agree to rounding.  An error in
- * any system (sel overflow, table range, box) fails the call. */
+ * otherwise).  A system's energy, forces and virial are bitwise those of
+ * dp_compute on it alone (its atoms are grouped in the same tiles of 32 and
+ * every sum runs in the same order).  An error in any system (sel
+ * overflow, table range, box) fails the call. */
 dp_status dp_compute_batch(dp_handle* h, int nsys, const int64_t* natoms, const double* coords,
                            const int32_t* types, const double* boxes, double* energies,
                            double* forces, double* virials);

@@ -87,7 +87,7 @@ struct Work {
   DevBuf tc_pairs, tc_hist, tc_range;  // sorted pairs / bin ends the forward leaves
   // several systems in one evaluation: tile index lists padded per system,
   // atom -> system, per-system first atom and cell edges, per-tile virial
-  DevBuf bidx, sys_of, sys_base, sys_edge, vir_tile;
+  DevBuf bidx, sys_of, sys_base, sys_edge, vir_tile, vir_type, seg, seg_part, seg_out;
 };
 
 }  // namespace
@@ -432,6 +432,8 @@ dp_status set_types(dp_handle* h, Work& w, const int32_t* types_user_host) {
     CK(ensure(w.tc_hist, (size_t)std::max<int64_t>(tab_tc_hist_elems(ep, ntile), 8) * 2),
        "alloc bin ends");
     CK(ensure(w.tc_range, (size_t)std::max<int64_t>(ntile, 1) * 8), "alloc bin ranges");
+    CK(ensure(w.vir_tile, (size_t)std::max<int64_t>(ntile, 1) * 9 * sizeof(double)), "alloc virial");
+    CK(ensure(w.vir_type, DP_MAXT * 9 * sizeof(double)), "alloc virial");
   }
   if (n > 0) {
     CK(cudaMemcpyAsync(w.types.p, mt.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->st),
@@ -705,7 +707,7 @@ dp_status evaluate(dp_handle* h, Work& w) {
       if (launch_tab_bwd_tc(h->st, w.tiles, P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist),
                             P<int2>(w.tc_range), ep, P<__nv_bfloat16>(h->tabB), P<float>(w.dT),
                             P<unsigned long long>(w.ffix), P<double>(w.vir_part),
-                            (int)tab_tc_slots(), P<int32_t>(h->status)))
+                            (int)tab_tc_slots(), P<int32_t>(h->status), P<double>(w.vir_tile)))
         return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core embedding cannot run this model shape");
     } else if (h->opt.tabulated) {
       if (launch_tab_bwd(h->st, n, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
@@ -726,11 +728,23 @@ dp_status evaluate(dp_handle* h, Work& w) {
   launch_force_finalize(h->st, n, P<unsigned long long>(w.ffix), P<double>(w.f),
                         P<int32_t>(h->status));
   launch_sum_rows(h->st, n, 1, P<double>(w.e_atom), P<double>(w.red_part), P<double>(w.red_out));
-  const int64_t vslots = !h->opt.tabulated             ? plain_kernel_slots(n)
-                         : h->opt.embed_precision == 2 ? tab_tc_slots()
-                                                       : tab_kernel_slots(n);
-  launch_sum_rows(h->st, vslots, 9,
-                  P<double>(w.vir_part), P<double>(w.red_part), P<double>(w.red_out) + 1);
+  if (h->opt.tabulated && h->opt.embed_precision == 2) {
+    // the virial from one row per tile: summed per centre type, the types
+    // then added in order (the same sums dp_compute_batch makes per system)
+    int k = 0;
+    for (int t = 0; t < h->ntypes; ++t) {
+      const int64_t nt = w.tiles.tile_off[t + 1] - w.tiles.tile_off[t];
+      if (nt == 0) continue;
+      launch_sum_rows(h->st, nt, 9, P<double>(w.vir_tile) + w.tiles.tile_off[t] * 9,
+                      P<double>(w.red_part), P<double>(w.vir_type) + 9 * k);
+      ++k;
+    }
+    launch_add_rows(h->st, k, 9, P<double>(w.vir_type), P<double>(w.red_out) + 1);
+  } else {
+    const int64_t vslots = !h->opt.tabulated ? plain_kernel_slots(n) : tab_kernel_slots(n);
+    launch_sum_rows(h->st, vslots, 9,
+                    P<double>(w.vir_part), P<double>(w.red_part), P<double>(w.red_out) + 1);
+  }
   launch_check_energy(h->st, n, P<double>(w.e_atom), P<int32_t>(h->status));
   CK(cudaGetLastError(), "evaluation kernels");
   return DP_OK;
@@ -1137,7 +1151,8 @@ dp_status dp_compute_batch(dp_handle* h, int nsys, const int64_t* natoms, const 
   // tiles: each system's atoms of a type start a new tile (padding entries
   // -1), so a tile belongs to one system and its virial row to that system
   std::vector<int32_t> pidx;
-  std::vector<std::vector<int64_t>> sys_tiles(nsys);
+  // per system, the tile range of each centre type that has atoms there
+  std::vector<std::vector<std::pair<int64_t, int64_t>>> sys_tiles(nsys);
   TileMap tm{};
   tm.ntypes = h->ntypes;
   for (int t = 0; t < h->ntypes; ++t) {
@@ -1148,7 +1163,8 @@ dp_status dp_compute_batch(dp_handle* h, int nsys, const int64_t* natoms, const 
       for (int64_t i = base[q]; i < base[q + 1]; ++i)
         if (h->type_map[types[i]] == t) pidx.push_back((int32_t)i);
       while (pidx.size() % 32) pidx.push_back(-1);
-      for (int64_t k = t0; k < (int64_t)pidx.size() / 32; ++k) sys_tiles[q].push_back(k);
+      const int64_t t1 = (int64_t)pidx.size() / 32;
+      if (t1 > t0) sys_tiles[q].push_back({t0, t1 - t0});
     }
     tm.atom_cnt[t] = (int64_t)pidx.size() - tm.atom_off[t];
   }
@@ -1217,27 +1233,50 @@ dp_status dp_compute_batch(dp_handle* h, int nsys, const int64_t* natoms, const 
   }
   CKS(read_status(h));
   CKS(status_errors(h));
-  std::vector<double> e(std::max<int64_t>(n, 1)), vt((size_t)std::max<int64_t>(ntile, 1) * 9);
+  // per-system sums, each bitwise the one dp_compute makes for the system
+  // alone: its atoms' energies (segments of e_atom) and, per centre type,
+  // its tiles' virial rows (segments of vir_tile), added in type order
+  std::vector<int64_t> seg;  // [rows..., offsets...]: systems, then (system, type) ranges
+  int nvseg = 0;
+  for (int q = 0; q < nsys; ++q) seg.push_back(base[q + 1] - base[q]);
+  for (int q = 0; q < nsys; ++q)
+    for (auto& r : sys_tiles[q]) seg.push_back(r.second), ++nvseg;
+  for (int q = 0; q < nsys; ++q) seg.push_back(base[q]);
+  for (int q = 0; q < nsys; ++q)
+    for (auto& r : sys_tiles[q]) seg.push_back(r.first);
+  const int nseg = nsys + nvseg;
+  std::vector<double> out((size_t)nsys + 9 * (size_t)nvseg);
   if (n > 0) {
-    CK(cudaMemcpyAsync(e.data(), w.e_atom.p, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st),
-       "energy copy");
-    CK(cudaMemcpyAsync(vt.data(), w.vir_tile.p, sizeof(double) * 9 * ntile, cudaMemcpyDeviceToHost,
+    CK(ensure(w.seg, seg.size() * sizeof(int64_t)), "alloc sums");
+    CK(ensure(w.seg_part, (size_t)std::max<int64_t>(sum_rows_seg_part_size(nsys, 1),
+                                                     sum_rows_seg_part_size(nvseg, 9)) *
+                              sizeof(double)),
+       "alloc sums");
+    CK(ensure(w.seg_out, out.size() * sizeof(double)), "alloc sums");
+    CK(cudaMemcpyAsync(w.seg.p, seg.data(), seg.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                        h->st),
-       "virial copy");
+       "sums upload");
+    const int64_t* rows = P<int64_t>(w.seg);
+    const int64_t* offs = rows + nseg;
+    launch_sum_rows_seg(h->st, nsys, rows, offs, 1, P<double>(w.e_atom), P<double>(w.seg_part),
+                        P<double>(w.seg_out));
+    launch_sum_rows_seg(h->st, nvseg, rows + nsys, offs + nsys, 9, P<double>(w.vir_tile),
+                        P<double>(w.seg_part), P<double>(w.seg_out) + nsys);
+    CK(cudaGetLastError(), "sum kernels");
+    CK(cudaMemcpyAsync(out.data(), w.seg_out.p, out.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, h->st),
+       "energy copy");
     CK(cudaMemcpyAsync(forces, w.f.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->st),
        "force copy");
     CK(cudaStreamSynchronize(h->st), "result copy");
   }
-  // per-system sums in a fixed order (atoms, then the system's tiles)
+  int vk = 0;
   for (int q = 0; q < nsys; ++q) {
-    double E = 0.0;
-    for (int64_t i = base[q]; i < base[q + 1]; ++i) E += e[i];
-    energies[q] = E;
-    for (int a = 0; a < 9; ++a) {
-      double v = 0.0;
-      for (int64_t k : sys_tiles[q]) v += vt[(size_t)k * 9 + a];
-      virials[9 * q + a] = v;
-    }
+    energies[q] = n > 0 ? out[q] : 0.0;
+    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // the order of launch_add_rows
+    for (size_t r = 0; r < sys_tiles[q].size(); ++r, ++vk)
+      for (int a = 0; a < 9; ++a) v[a] += out[nsys + 9 * (size_t)vk + a];
+    for (int a = 0; a < 9; ++a) virials[9 * q + a] = v[a];
   }
   return DP_OK;
 }

@@ -231,6 +231,14 @@ void launch_force_finalize(cudaStream_t st, int64_t n, const unsigned long long*
 void launch_sum_rows(cudaStream_t st, int64_t rows, int width, const double* in, double* part,
                      double* out);
 int sum_rows_part_size(int64_t rows, int width);
+// launch_sum_rows on nseg segments in one pass (seg_rows, seg_off: device
+// arrays; out [nseg][width]); each segment's sum is bitwise the one
+// launch_sum_rows gives on it alone
+int64_t sum_rows_seg_part_size(int nseg, int width);
+void launch_sum_rows_seg(cudaStream_t st, int nseg, const int64_t* seg_rows, const int64_t* seg_off,
+                         int width, const double* in, double* part, double* out);
+// out[c] = sum over r (in order, from 0) of in[r][c]; width <= 32
+void launch_add_rows(cudaStream_t st, int nrows, int width, const double* in, double* out);
 void launch_kick_drift(cudaStream_t st, int64_t n, double* x, double* v, const double* f,
                        const int32_t* types, const double* inv_mass_acc, double dt,
                        const double* xref, double half_skin2, int32_t* status);

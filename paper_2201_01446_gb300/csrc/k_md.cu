@@ -45,6 +45,54 @@ __global__ void k_sum_stage2(int nblk, int width, const double* __restrict__ par
 
 constexpr int kSumBlocks = 512;
 
+// the same two stages for several segments at once (segment q: rows
+// [off[q], off[q] + rows[q]) of in): every segment gets exactly the
+// additions launch_sum_rows would make on it alone
+__global__ void k_sum_stage1_seg(const int64_t* __restrict__ seg_rows,
+                                 const int64_t* __restrict__ seg_off, int width,
+                                 const double* __restrict__ in, double* __restrict__ part) {
+  __shared__ double sm[256];
+  const int q = blockIdx.y;
+  const int64_t rows = seg_rows[q];
+  int64_t chunk = (rows + kSumBlocks - 1) / kSumBlocks;
+  if (chunk < 1) chunk = 1;
+  const double* src = in + seg_off[q] * width;
+  const int64_t r0 = blockIdx.x * chunk;
+  const int64_t r1 = min(rows, r0 + chunk);
+  for (int c = 0; c < width; ++c) {
+    double s = 0.0;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) s += src[r * width + c];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o >= 1; o >>= 1) {
+      if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[((int64_t)q * kSumBlocks + blockIdx.x) * width + c] = sm[0];
+    __syncthreads();
+  }
+}
+
+__global__ void k_sum_stage2_seg(int nseg, int width, const double* __restrict__ part,
+                                 double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nseg * width) return;
+  const int q = i / width, c = i - q * width;
+  double s = 0.0;
+  for (int b = 0; b < kSumBlocks; ++b) s += part[((int64_t)q * kSumBlocks + b) * width + c];
+  out[i] = s;
+}
+
+// out[c] = in[0][c] + in[1][c] + ... (sequential from 0)
+__global__ void k_add_rows(int nrows, int width, const double* __restrict__ in,
+                           double* __restrict__ out) {
+  const int c = threadIdx.x;
+  if (c >= width) return;
+  double s = 0.0;
+  for (int r = 0; r < nrows; ++r) s += in[r * width + c];
+  out[c] = s;
+}
+
 __global__ void k_kick_drift(int64_t n, double* __restrict__ x, double* __restrict__ v,
                              const double* __restrict__ f, const int32_t* __restrict__ types,
                              const double* __restrict__ inv_mass_acc, double dt,
@@ -123,6 +171,21 @@ void launch_sum_rows(cudaStream_t st, int64_t rows, int width, const double* in,
   DP_LAUNCHED(2);
   k_sum_stage1<<<kSumBlocks, 256, 0, st>>>(rows, width, chunk, in, part);
   k_sum_stage2<<<1, 32, 0, st>>>(kSumBlocks, width, part, out);
+}
+
+int64_t sum_rows_seg_part_size(int nseg, int width) { return (int64_t)nseg * kSumBlocks * width; }
+
+void launch_sum_rows_seg(cudaStream_t st, int nseg, const int64_t* seg_rows, const int64_t* seg_off,
+                         int width, const double* in, double* part, double* out) {
+  if (nseg <= 0) return;
+  DP_LAUNCHED(2);
+  k_sum_stage1_seg<<<dim3(kSumBlocks, nseg), 256, 0, st>>>(seg_rows, seg_off, width, in, part);
+  k_sum_stage2_seg<<<(nseg * width + 127) / 128, 128, 0, st>>>(nseg, width, part, out);
+}
+
+void launch_add_rows(cudaStream_t st, int nrows, int width, const double* in, double* out) {
+  DP_LAUNCHED(1);
+  k_add_rows<<<1, 32, 0, st>>>(nrows, width, in, out);
 }
 
 void launch_kick_drift(cudaStream_t st, int64_t n, double* x, double* v, const double* f,

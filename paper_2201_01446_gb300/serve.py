@@ -5,10 +5,15 @@ per model), so requests from different slots overlap on the GPU.  Results are
 computed by the same deterministic kernels whatever runs beside them, so a
 request's result is bitwise the one it has alone.
 
+Small evaluation requests of one model are packed: a slot that takes an
+evaluation from the head of the queue also takes the queued evaluations of
+the same model behind it, up to `pack_atoms` atoms in all, and runs them as
+one dp_compute_batch call (one launch of each kernel for all of them; each
+result still bitwise the one it has alone).  MD requests replay their steps
+without a list rebuild as a CUDA graph inside the library.
+
 Host orchestration only (queueing, admission, timing): every step of every
-request runs in the library's kernels.  Packing several small systems into
-one ragged launch and CUDA graphs per size bucket are not built: small
-requests overlap through the slots' streams instead.
+request runs in the library's kernels.
 """
 from __future__ import annotations
 
@@ -68,10 +73,14 @@ def estimate_bytes(natoms: int, cfg: ModelCfg, M: int = 128) -> int:
 
 
 class Server:
-    def __init__(self, models: dict, slots: int = 4, budget_bytes: float = 150e9):
+    def __init__(self, models: dict, slots: int = 4, budget_bytes: float = 150e9,
+                 pack_atoms: int = 32768):
         self.models = models
         self.slots = slots
         self.budget = float(budget_bytes)
+        self.pack_atoms = int(pack_atoms)
+        self.packed_calls = 0
+        self.packed_requests = 0
         self._cond = threading.Condition()
         self._ready = []       # arrived, not yet admitted (FIFO)
         self._in_use = 0.0
@@ -85,9 +94,11 @@ class Server:
             self._ready.append(req)
             self._cond.notify_all()
 
-    def _take(self):
-        """Head of the queue once it fits the budget (FIFO admission); None
-        when the server closes with nothing left."""
+    def _take(self, can_pack: bool):
+        """The head of the queue once it fits the budget (FIFO admission),
+        with, when the head is a small evaluation and the slot can pack, the
+        queued evaluations of the same model that fit behind it; None when
+        the server closes with nothing left."""
         with self._cond:
             while True:
                 if self._ready:
@@ -95,8 +106,19 @@ class Server:
                     if self._in_use + head.nbytes <= self.budget or self._in_use == 0.0:
                         self._ready.pop(0)
                         self._in_use += head.nbytes
+                        batch = [head]
+                        if can_pack and head.kind == "eval" and len(head.x) <= self.pack_atoms:
+                            atoms = len(head.x)
+                            for r in list(self._ready):
+                                if (r.kind == "eval" and r.model == head.model
+                                        and atoms + len(r.x) <= self.pack_atoms
+                                        and self._in_use + r.nbytes <= self.budget):
+                                    self._ready.remove(r)
+                                    self._in_use += r.nbytes
+                                    atoms += len(r.x)
+                                    batch.append(r)
                         self.peak_in_use = max(self.peak_in_use, self._in_use)
-                        return head
+                        return batch
                 elif self._closing:
                     return None
                 self._cond.wait(0.05)
@@ -118,20 +140,32 @@ class Server:
         execs = [make(i) for i in range(self.slots)]
         self._done = []
         self._closing = False
+        self.packed_calls = self.packed_requests = 0
         t0 = time.perf_counter()
 
         def worker(ex):
+            can_pack = self.pack_atoms > 0 and hasattr(ex, "batch")
             while True:
-                req = self._take()
-                if req is None:
+                reqs = self._take(can_pack)
+                if reqs is None:
                     return
-                req.t_start = time.perf_counter() - t0
+                for r in reqs:
+                    r.t_start = time.perf_counter() - t0
                 try:
-                    req.result = ex(req)
+                    if len(reqs) == 1:
+                        reqs[0].result = ex(reqs[0])
+                    else:
+                        for r, res in zip(reqs, ex.batch(reqs)):
+                            r.result = res
+                        with self._cond:
+                            self.packed_calls += 1
+                            self.packed_requests += len(reqs)
                 except Exception as e:  # recorded, the loop goes on
-                    req.error = str(e)
-                req.t_done = time.perf_counter() - t0
-                self._finish(req)
+                    for r in reqs:
+                        r.error = str(e)
+                for r in reqs:
+                    r.t_done = time.perf_counter() - t0
+                    self._finish(r)
 
         threads = [threading.Thread(target=worker, args=(ex,), daemon=True) for ex in execs]
         for th in threads:
@@ -160,7 +194,8 @@ class Server:
                 "p50_ms": float(np.percentile(lat, 50)) if len(lat) else 0.0,
                 "p99_ms": float(np.percentile(lat, 99)) if len(lat) else 0.0,
                 "atom_steps_per_s": sum(r.atom_steps for r in requests) / max(makespan, 1e-9),
-                "slots": self.slots, "peak_budget_bytes": self.peak_in_use}
+                "slots": self.slots, "peak_budget_bytes": self.peak_in_use,
+                "packed_calls": self.packed_calls, "packed_requests": self.packed_requests}
 
     def _dp_executor(self, slot: int):
         return _DpSlot(self.models)
@@ -174,9 +209,20 @@ class _DpSlot:
         import torch
         self._stream = torch.cuda.Stream()
         self._sp = ctypes.c_void_p(self._stream.cuda_stream)
+        self.models = models
         self.handles = {name: dp.dp_create(c.path, c.ntypes, c.rc, c.rcs, c.sel,
                                            options=c.options, stream=self._sp)
                         for name, c in models.items()}
+
+    def batch(self, reqs: list):
+        """Evaluations of one model as one dp_compute_batch call (models
+        without the tensor-core tabulated embedding run them one by one)."""
+        h = self.handles[reqs[0].model]
+        o = self.models[reqs[0].model].options
+        if o is None or not (o.tabulated and o.embed_precision == 2):
+            return [self(r) for r in reqs]
+        E, F, V = dp.dp_compute_batch(h, [(r.x, r.types, r.box) for r in reqs])
+        return [(float(E[q]), F[q], V[q]) for q in range(len(reqs))]
 
     def __call__(self, req: Request):
         h = self.handles[req.model]

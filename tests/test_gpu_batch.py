@@ -1,8 +1,8 @@
 """Several systems in one evaluation (dp_compute_batch, the packed launch of
-the serving loop): per system the forces are bitwise those of dp_compute on
-the system alone, energies and virials agree to FP64 summation order; one
-system against the oracle; empty and one-atom systems; copper and two-type
-water; the mode requirement."""
+the serving loop): per system the energy, forces and virial are bitwise
+those of dp_compute on the system alone; one system against the oracle;
+empty and one-atom systems; copper and two-type water; the mode
+requirement."""
 import numpy as np
 import pytest
 
@@ -29,15 +29,13 @@ def _tc(dp, path, ntypes=1, rc=CU_RC, rcs=CU_RCS, sel=(CU_SEL,), s_max=CU_SMAX):
 
 def _check_alone(dp, h, systems, tag):
     E, F, V = dp.dp_compute_batch(h, systems)
-    worst = 0.0
     for q, (x, t, box) in enumerate(systems):
         Ea, Fa, Va, _ = dp.dp_compute(h, x, t, box)
+        # bitwise: the same per-atom and per-tile values, summed in the same order
         assert np.array_equal(F[q], Fa), (tag, q)
-        assert abs(E[q] - Ea) <= 1e-12 * max(1.0, abs(Ea)), (tag, q, E[q], Ea)
-        assert np.abs(V[q] - Va).max() <= 1e-12 * max(1.0, float(np.abs(Va).max())), (tag, q)
-        worst = max(worst, abs(E[q] - Ea) / max(1.0, abs(Ea)))
-    PARITY_LOG.append(dict(case=f"batch vs alone: {tag}", systems=len(systems),
-                           max_rel_energy_diff=worst))
+        assert E[q] == Ea, (tag, q, E[q], Ea)
+        assert np.array_equal(V[q], Va), (tag, q)
+    PARITY_LOG.append(dict(case=f"batch vs alone (bitwise): {tag}", systems=len(systems)))
     return E, F, V
 
 

@@ -73,3 +73,43 @@ def test_request_mix_is_seeded():
         assert 192 <= len(p["x"]) <= 500000
     x, t, box = inputs.water_tiled(4)
     assert len(x) == 768 and np.count_nonzero(t == 0) == 256
+
+
+class _Packer(_Sleep):
+    """Stand-in slot that also takes packed batches."""
+
+    def __init__(self, log, slot, batches):
+        super().__init__(log, slot)
+        self.batches = batches
+
+    def batch(self, reqs):
+        self.batches.append([r.rid for r in reqs])
+        time.sleep(0.002)
+        return [("ok", r.rid) for r in reqs]
+
+
+def test_small_evaluations_are_packed():
+    # one slot, everything queued at once: the head evaluation takes the
+    # queued evaluations of the same model behind it up to pack_atoms atoms;
+    # MD requests and the other model's requests are never packed with it
+    models = {"cu": serve.ModelCfg("unused", 1, 8.0, 0.5, [256]),
+              "water": serve.ModelCfg("unused", 2, 6.0, 0.5, [46, 92])}
+    reqs = _reqs([1000, 2000, 500, 3000, 9000, 800, 700], ["eval", "md", "eval", "eval", "eval",
+                                                           "eval", "eval"])
+    reqs[5].model = "water"
+    for r in reqs:
+        r.nbytes = 10
+    srv = serve.Server(models, slots=1, budget_bytes=1000, pack_atoms=6000)
+    log, batches = [], []
+    st = srv.run(reqs, np.zeros(len(reqs)), executor_factory=lambda s: _Packer(log, s, batches))
+    assert st["errors"] == 0 and all(r.result == ("ok", r.rid) for r in reqs)
+    assert st["packed_calls"] == len(batches) and st["packed_requests"] == sum(map(len, batches))
+    for b in batches:
+        kinds = {reqs[i].kind for i in b}
+        names = {reqs[i].model for i in b}
+        assert kinds == {"eval"} and len(names) == 1
+        assert sum(len(reqs[i].x) for i in b) <= 6000
+    # the single slot is busy while the rest queue up, so packing happens;
+    # the 9000-atom evaluation exceeds pack_atoms and always runs alone
+    assert st["packed_calls"] >= 1
+    assert all(4 not in b for b in batches)
