@@ -145,6 +145,11 @@ dp_status dp_compute(dp_handle* h, int64_t natoms, const double* coords, const i
 dp_status dp_system_create(dp_handle* h, int64_t natoms, const double* x, const double* v,
                            const int32_t* types, const double* mass_of_type, const double* box,
                            int device_ptrs, dp_system** out);
+/* Frees the system.  The handle keeps the device buffers of the last
+ * destroyed system (lists, T, dT, sorted pairs ...) and gives them to its
+ * next dp_system_create, so a stream of systems does not allocate and free
+ * gigabytes each time; dp_destroy releases them.  Destroy every system
+ * before its handle. */
 void dp_system_destroy(dp_system* s);
 
 /* Copy x, v, f (any may be NULL) out of the system; device_ptrs as above.

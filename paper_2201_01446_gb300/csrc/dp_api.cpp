@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <array>
+#include <memory>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -41,6 +42,23 @@ void parse_fault() {
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) {
+    o.p = nullptr;
+    o.bytes = 0;
+  }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      if (p) cudaFree(p);
+      p = o.p;
+      bytes = o.bytes;
+      o.p = nullptr;
+      o.bytes = 0;
+    }
+    return *this;
+  }
   ~DevBuf() {
     if (p) cudaFree(p);
   }
@@ -130,6 +148,10 @@ struct dp_handle {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[DP_NPHASE];
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pool;
   cudaStream_t cap_st = nullptr;  // private stream for CUDA-graph capture
+  // the device buffers of the last destroyed system, reused by the next
+  // dp_system_create (no cudaMalloc/cudaFree of the multi-GB lists per system)
+  std::unique_ptr<Work> spare_work;
+  DevBuf spare_v;
   ~dp_handle() {
     if (cap_st) cudaStreamDestroy(cap_st);
     for (auto& v : prof_ev)
@@ -1643,6 +1665,11 @@ dp_status dp_system_create(dp_handle* h, int64_t natoms, const double* x, const 
     if (!(mm > 0)) return bail(fail(h, DP_ERR_ARG, "masses must be > 0"));
   std::memcpy(s->box, box_h, sizeof box_h);
   s->mass_user = mass_h;
+  if (h->spare_work) {
+    s->w = std::move(*h->spare_work);
+    h->spare_work.reset();
+    s->v = std::move(h->spare_v);
+  }
   st = load_coords(h, s->w, natoms, x, types, device_ptrs);
   if (st) return bail(st);
   s->types_user.resize(natoms);
@@ -1687,6 +1714,11 @@ dp_status dp_system_create(dp_handle* h, int64_t natoms, const double* x, const 
 void dp_system_destroy(dp_system* s) {
   if (!s) return;
   if (s->h && s->h->st) cudaStreamSynchronize(s->h->st);
+  if (s->h && !s->h->dead && !s->h->spare_work) {
+    // keep the buffers for the handle's next system
+    s->h->spare_work.reset(new Work(std::move(s->w)));
+    s->h->spare_v = std::move(s->v);
+  }
   delete s;
 }
 
