@@ -228,11 +228,14 @@ def dp_system_step(s) -> int:
 
 
 def dp_system_get(h, s, n, x=True, v=True, f=True, out=None):
-    """Host copies (numpy) of x, v, f; or, with out=(x, v, f) CUDA tensors,
-    device-to-device copies into them."""
+    """Host copies (numpy) of x, v, f; or, with out=(x, v, f) of CUDA tensors,
+    device-to-device copies into them; or, with out of host arrays (numpy or
+    CPU tensors, e.g. pinned), host copies into them."""
     if out is not None:
-        ptrs = [C.c_void_p(t.data_ptr()) if t is not None else None for t in out]
-        _check(lib.dp_system_get(s, *ptrs, 1), h)
+        dev = any(_is_torch(t) and t.is_cuda for t in out if t is not None)
+        ptrs = [(C.c_void_p(t.data_ptr()) if _is_torch(t) else t.ctypes.data_as(C.c_void_p))
+                if t is not None else None for t in out]
+        _check(lib.dp_system_get(s, *ptrs, 1 if dev else 0), h)
         return out
     arrs = [np.zeros((max(n, 1), 3)) if want else None for want in (x, v, f)]
     _check(lib.dp_system_get(s, *[a.ctypes.data_as(C.c_void_p) if a is not None else None
