@@ -1828,6 +1828,7 @@ dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_th
     s->step += 1;
     s->f_valid = false;
     if (s->step % h->opt.rebuild_every == 0) {
+      ph1.end();  // the rebuild is timed as its own phase
       CKS(read_status(h));
       CKS(status_errors(h));
       CKS(rebuild(h, w, L, h->rc + h->opt.skin));

@@ -134,7 +134,11 @@ __global__ void k_mirror(int64_t n, const double* __restrict__ x, const int32_t*
 }
 
 // one warp per atom, atoms visited in cell order so that the warps of a CTA
-// share their candidate cells in L1
+// share their candidate cells in L1.  Lane l < 27 first looks up stencil
+// slot l's cell (its atom range and image shift); the warp then walks the
+// 27 ranges as one sequence of rounds of 32 candidates, with the next
+// round's candidate indices and offsets loaded while the current round is
+// tested (the slot order, hence the list order, is unchanged)
 __global__ void __launch_bounds__(128) k_build_list(
     int64_t n, const double* __restrict__ x, const int32_t* __restrict__ cellc,
     const float4* __restrict__ off, const int32_t* __restrict__ cell_start,
@@ -152,59 +156,104 @@ __global__ void __launch_bounds__(128) k_build_list(
   const float rl2f = (float)rl2;
   const float lo = rl2f * (1.0f - 1e-4f), hi = rl2f * (1.0f + 1e-4f);
   uint32_t* L = nlist + (size_t)i * cap;
+  // lane l < 27: stencil slot l's atom range [my_s, my_e) and image code
+  int my_s = 0, my_e = 0, my_img = 0;
+  if (lane < 27) {
+    const int o[3] = {lane / 9 - 1, (lane / 3) % 3 - 1, lane % 3 - 1};
+    int cc[3], im[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int v = ci[a] + o[a];
+      im[a] = v < 0 ? -1 : (v >= g.nc[a] ? 1 : 0);
+      cc[a] = v - im[a] * g.nc[a];
+    }
+    const int cid = (cc[0] * g.nc[1] + cc[1]) * g.nc[2] + cc[2];
+    my_s = cell_start[cid];
+    my_e = cell_start[cid + 1];
+    my_img = (im[0] + 1) * 9 + (im[1] + 1) * 3 + (im[2] + 1);
+  }
   int cnt = 0;
   int cnt_t[DP_MAXT];
 #pragma unroll
   for (int t = 0; t < DP_MAXT; ++t) cnt_t[t] = 0;
   const unsigned below = (1u << lane) - 1u;
-  for (int slot = 0; slot < 27; ++slot) {
-    const int o[3] = {slot / 9 - 1, (slot / 3) % 3 - 1, slot % 3 - 1};
-    int cc[3], img[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      int v = ci[a] + o[a];
-      img[a] = v < 0 ? -1 : (v >= g.nc[a] ? 1 : 0);
-      cc[a] = v - img[a] * g.nc[a];
+  // the round sequence: (slot, base) with base stepping by 32 through the
+  // slot's range; advance() moves to the next non-empty round
+  int slot = 0, base = __shfl_sync(0xffffffffu, my_s, 0), e = __shfl_sync(0xffffffffu, my_e, 0);
+  auto advance = [&](int& sl, int& b, int& en) {
+    b += 32;
+    while (b >= en && sl < 27) {
+      ++sl;
+      if (sl < 27) {
+        b = __shfl_sync(0xffffffffu, my_s, sl);
+        en = __shfl_sync(0xffffffffu, my_e, sl);
+      }
     }
-    const int cid = (cc[0] * g.nc[1] + cc[1]) * g.nc[2] + cc[2];
-    const int s = cell_start[cid], e = cell_start[cid + 1];
-    const float sx = o[0] * g.edgef[0], sy = o[1] * g.edgef[1], sz = o[2] * g.edgef[2];
-    for (int base = s; base < e; base += 32) {
-      const int k = base + lane;
-      bool in = false, inrc = false;
-      int j = 0, tj = 0;
-      if (k < e) {
-        j = cell_atoms[k];
-        const float4 oj = off[j];
-        tj = __float_as_int(oj.w);
-        const float dx = (oj.x - oi.x) + sx, dy = (oj.y - oi.y) + sy, dz = (oj.z - oi.z) + sz;
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        const bool self = (j == i) && slot == 13;
-        if (!self) {
-          if (r2 < lo) {
-            in = true;
-          } else if (r2 <= hi) {
-            // boundary band: decide exactly as the FP64 definition does
-            double r2d = 0.0;
+  };
+  if (base >= e) {  // the first slot's cell is empty: find the first round
+    base -= 32;
+    advance(slot, base, e);
+  }
+  // prefetched candidate of the current round
+  int j_c = 0;
+  float4 o_c = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (slot < 27 && base + lane < e) {
+    j_c = cell_atoms[base + lane];
+    o_c = off[j_c];
+  }
+  while (slot < 27) {
+    // the next round and its candidate, loaded before this round is tested
+    int nslot = slot, nbase = base, ne = e;
+    advance(nslot, nbase, ne);
+    int j_n = 0;
+    float4 o_n = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (nslot < 27 && nbase + lane < ne) {
+      j_n = cell_atoms[nbase + lane];
+      o_n = off[j_n];
+    }
+    const int img_code = __shfl_sync(0xffffffffu, my_img, slot);
+    const int o0 = slot / 9 - 1, o1 = (slot / 3) % 3 - 1, o2 = slot % 3 - 1;
+    const float sx = o0 * g.edgef[0], sy = o1 * g.edgef[1], sz = o2 * g.edgef[2];
+    const int k = base + lane;
+    bool in = false, inrc = false;
+    const int j = j_c;
+    int tj = 0;
+    if (k < e) {
+      const float4 oj = o_c;
+      tj = __float_as_int(oj.w);
+      const float dx = (oj.x - oi.x) + sx, dy = (oj.y - oi.y) + sy, dz = (oj.z - oi.z) + sz;
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const bool self = (j == i) && slot == 13;
+      if (!self) {
+        if (r2 < lo) {
+          in = true;
+        } else if (r2 <= hi) {
+          // boundary band: decide exactly as the FP64 definition does
+          const int img[3] = {img_code / 9 - 1, (img_code / 3) % 3 - 1, img_code % 3 - 1};
+          double r2d = 0.0;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              double d = __dadd_rn(__dsub_rn(x[(size_t)j * 3 + a], x[(size_t)i * 3 + a]),
-                                   __dmul_rn((double)img[a], g.L[a]));
-              r2d = __dadd_rn(r2d, __dmul_rn(d, d));
-            }
-            in = r2d < rl2;
+          for (int a = 0; a < 3; ++a) {
+            double d = __dadd_rn(__dsub_rn(x[(size_t)j * 3 + a], x[(size_t)i * 3 + a]),
+                                 __dmul_rn((double)img[a], g.L[a]));
+            r2d = __dadd_rn(r2d, __dmul_rn(d, d));
           }
-          inrc = r2 < rc2;
+          in = r2d < rl2;
         }
+        inrc = r2 < rc2;
       }
-      const unsigned m = __ballot_sync(0xffffffffu, in);
-      if (in) {
-        const int p = cnt + __popc(m & below);
-        if (p < cap) L[p] = ((uint32_t)j << 5) | (uint32_t)slot;
-      }
-      cnt += __popc(m);
-      for (int t = 0; t < ntypes; ++t) cnt_t[t] += __popc(__ballot_sync(0xffffffffu, inrc && tj == t));
     }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (in) {
+      const int p = cnt + __popc(m & below);
+      if (p < cap) L[p] = ((uint32_t)j << 5) | (uint32_t)slot;
+    }
+    cnt += __popc(m);
+    for (int t = 0; t < ntypes; ++t) cnt_t[t] += __popc(__ballot_sync(0xffffffffu, inrc && tj == t));
+    slot = nslot;
+    base = nbase;
+    e = ne;
+    j_c = j_n;
+    o_c = o_n;
   }
   if (lane == 0) {
     nn[i] = cnt;
