@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <array>
 #include <memory>
+#include <mutex>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -25,18 +26,18 @@ constexpr double kEvA3Bar = 1.602176634e6;
 // ------------------------------------------------------------------ fault injection
 // DP_FAULT=alloc:N makes the N-th device allocation of the process fail
 // (host-side injection; nothing on the GPU is disturbed).
-long g_alloc_count = 0;
+std::atomic<long> g_alloc_count{0};  // allocations from several host threads
 // bumped by every device (re)allocation: a captured CUDA graph holds raw
 // pointers and is valid only while no buffer it uses has moved
 std::atomic<unsigned long long> g_alloc_gen{0};
-long g_alloc_fail_at = -1;
-bool g_fault_parsed = false;
+std::atomic<long> g_alloc_fail_at{-1};
+std::once_flag g_fault_once;
 
 void parse_fault() {
-  if (g_fault_parsed) return;
-  g_fault_parsed = true;
-  const char* s = std::getenv("DP_FAULT");
-  if (s && std::strncmp(s, "alloc:", 6) == 0) g_alloc_fail_at = std::atol(s + 6);
+  std::call_once(g_fault_once, [] {
+    const char* s = std::getenv("DP_FAULT");
+    if (s && std::strncmp(s, "alloc:", 6) == 0) g_alloc_fail_at = std::atol(s + 6);
+  });
 }
 
 struct DevBuf {
@@ -73,8 +74,8 @@ cudaError_t ensure(DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (bytes <= b.bytes) return cudaSuccess;
   parse_fault();
-  ++g_alloc_count;
-  if (g_alloc_fail_at > 0 && g_alloc_count == g_alloc_fail_at) return cudaErrorMemoryAllocation;
+  const long na = ++g_alloc_count;
+  if (g_alloc_fail_at > 0 && na == g_alloc_fail_at) return cudaErrorMemoryAllocation;
   b.release();
   g_alloc_gen.fetch_add(1);
   cudaError_t e = cudaMalloc(&b.p, bytes);

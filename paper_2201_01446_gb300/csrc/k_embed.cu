@@ -20,6 +20,7 @@
 //   F_i += g_ij, F_j -= g_ij, virial -= r_ij (x) g_ij.
 // Forces go to int64 fixed-point accumulators (associative, deterministic);
 // the virial to per-warp FP64 partials summed later in a fixed order.
+#include <atomic>
 #include <math.h>
 
 #include "dp_internal.h"
@@ -571,7 +572,7 @@ int launch_tab_fwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t
   if (ep.M > 128 || ep.M % 4 || ep.ntypes * ep.n_int > 32768) return -1;
   size_t sm = fwd_smem(ep);
   if (sm > 200 * 1024) return -1;
-  static size_t set_fwd = 0;
+  static std::atomic<size_t> set_fwd{0};  // launches from several host threads
   if (sm > 48 * 1024 && sm > set_fwd) {
     cudaFuncSetAttribute(k_tab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set_fwd = sm;
@@ -591,7 +592,7 @@ int launch_tab_bwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t
   if (vir_slots < tab_kernel_slots(n)) return -1;
   size_t sm = bwd_smem(ep);
   if (sm > 200 * 1024) return -1;
-  static size_t set_bwd = 0;
+  static std::atomic<size_t> set_bwd{0};
   if (sm > 48 * 1024 && sm > set_bwd) {
     cudaFuncSetAttribute(k_tab_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set_bwd = sm;

@@ -18,6 +18,7 @@
 // so the per-CTA scratch stays small.  Operands are FP32-accurate: each value
 // is h + m + l in BF16 and six piece products accumulate in FP32 (the h*h sum
 // and the small products in separate TMEM accumulators).
+#include <atomic>
 #include <cuda_bf16.h>
 #include <limits.h>
 #include <math.h>
@@ -1104,13 +1105,14 @@ __global__ void k_tab_grad_reduce(int nct, int64_t n, const float* __restrict__ 
   out[e] = s * (double)inv_nm;
 }
 
-int g_sms = 0;
+std::atomic<int> g_sms{0};
 int sm_count() {
   if (!g_sms) {
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 1;
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    g_sms = v > 0 ? v : 1;
   }
   return g_sms;
 }
@@ -1157,7 +1159,7 @@ int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, con
   if (ntile <= 0) return 0;
   const FwdCfg cf = fwd_cfg(ep);
   if (cf.smem > 113 * 1024) return -1;  // two CTAs per SM
-  static size_t set = 0;
+  static std::atomic<size_t> set{0};  // launches from several host threads
   if (cf.smem > 48 * 1024 && cf.smem > set) {
     if (cudaFuncSetAttribute(k_tab_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)cf.smem) != cudaSuccess)
@@ -1188,7 +1190,7 @@ int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs,
   if (ntile <= 0) return 0;
   const BwdCfg cf = bwd_cfg(ep);
   if (cf.smem > 113 * 1024) return -1;  // two CTAs per SM
-  static size_t set = 0;
+  static std::atomic<size_t> set{0};  // launches from several host threads
   if (cf.smem > 48 * 1024 && cf.smem > set) {
     if (cudaFuncSetAttribute(k_tab_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)cf.smem) != cudaSuccess)
@@ -1218,7 +1220,7 @@ int launch_tab_grad_tc(cudaStream_t st, const TileMap& tm, const float4* pairs,
   const int64_t ntile = tm.tile_off[tm.ntypes];
   const size_t smem = grad_smem(ep);
   if (smem > 225 * 1024) return -1;
-  static size_t set = 0;
+  static std::atomic<size_t> set{0};  // launches from several host threads
   if (smem > 48 * 1024 && smem > set) {
     if (cudaFuncSetAttribute(k_tab_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)

@@ -23,6 +23,7 @@
 // "empty" barrier, the epilogue warps drain TMEM.  Every wait is bounded: on
 // timeout the kernel records an error word, stops issuing work, waits
 // (bounded) for its own copies and MMAs, frees its TMEM and returns.
+#include <atomic>
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -654,7 +655,7 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512));
 }
 
-int g_tc_sms = 0;
+std::atomic<int> g_tc_sms{0};
 
 // persistent launch of the K-short GEMMs
 template <int EPI, int PC, bool TAB>
@@ -667,7 +668,7 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
   static_assert(PCfg<PC>::STAGE * 3 + 128 <= kPSmemMax, "three stages at least");
   const int NS = PCfg<PC>::stages();
   const size_t sm = PCfg<PC>::smem();
-  static size_t set = 0;
+  static std::atomic<size_t> set{0};  // launches from several host threads
   if (sm > set) {
     if (cudaFuncSetAttribute(k_tc_gemm_p<EPI, PC, TAB, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm) != cudaSuccess)
@@ -677,12 +678,13 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
   if (!g_tc_sms) {
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_tc_sms <= 0) g_tc_sms = 1;
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    g_tc_sms = v > 0 ? v : 1;
   }
-  const int mtiles = (M + kBM - 1) / kBM;
+  const int mtiles = (M + kBM - 1) / kBM, nsm = g_tc_sms;
   DP_LAUNCHED(1);
-  k_tc_gemm_p<EPI, PC, TAB, EW><<<mtiles < g_tc_sms ? mtiles : g_tc_sms, 128 + EW * 32, sm, st>>>(
+  k_tc_gemm_p<EPI, PC, TAB, EW><<<mtiles < nsm ? mtiles : nsm, 128 + EW * 32, sm, st>>>(
       M, N, K, NS, A, B, ep);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -696,7 +698,7 @@ int tc_gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* B, const 
   if (K <= 0 || K % kBK || N <= 0 || N % 16) return -1;
   if (ep.ldo != N) return -1;
   const int NT = N <= 256 ? N : 256;
-  static bool attr = false;
+  static std::atomic<bool> attr{false};  // launches from several host threads
   if (!attr) {
     if (cudaFuncSetAttribute(k_tc_gemm<EPI, PC, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TcCfg<PC>::SMEM) != cudaSuccess)

@@ -12,6 +12,7 @@
 // weight load feeds 8 multiply-adds.  Lanes own layer outputs: h0[k] for
 // k = lane, h1[m] for m = lane, lane + 32, and embedding columns 4*lane.. .
 // Requires the doubling widths of Eq. 5 with d1 <= 32 (M <= 128).
+#include <atomic>
 #include <math.h>
 
 #include "dp_internal.h"
@@ -537,7 +538,7 @@ int launch_plain_fwd(cudaStream_t st, int64_t n, const float4* off, const uint32
   if (n <= 0) return 0;
   if (!plain_shape_ok(ep, d1)) return -1;
   const size_t sm = sizeof(PlainSmem) * kWpb;
-  static bool attr = false;
+  static std::atomic<bool> attr{false};  // launches from several host threads
   if (!attr) {
     cudaFuncSetAttribute(k_plain_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
@@ -556,7 +557,7 @@ int launch_plain_bwd(cudaStream_t st, int64_t n, const float4* off, const uint32
   if (!plain_shape_ok(ep, d1)) return -1;
   if (vir_slots < plain_kernel_slots(n)) return -1;
   const size_t sm = sizeof(PlainSmem) * kWpb;
-  static bool attr = false;
+  static std::atomic<bool> attr{false};  // launches from several host threads
   if (!attr) {
     cudaFuncSetAttribute(k_plain_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
