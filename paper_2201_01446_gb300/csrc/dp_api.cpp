@@ -1585,6 +1585,8 @@ dp_status dp_get_params(dp_handle* h, double* fit, double* table) {
 dp_status dp_set_params(dp_handle* h, const double* fit, const double* table) {
   CKS(check_handle(h));
   if (table && !h->opt.tabulated) return fail(h, DP_ERR_ARG, "the untabulated path has no table");
+  // captured MD graphs hold the output bias by value: capture them again
+  g_alloc_gen.fetch_add(1);
   if (fit) {
     std::vector<float> fb(h->fit_floats);
     CK(cudaMemcpyAsync(fb.data(), h->fit32.p, sizeof(float) * fb.size(), cudaMemcpyDeviceToHost,
