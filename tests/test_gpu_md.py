@@ -136,3 +136,33 @@ def test_md_graph_replay_bitwise(dp, cu_stress_path, prec):
     assert a[3] == b[3], (a[3], b[3])
     PARITY_LOG.append(dict(case=f"md graphs 256 atoms prec {prec}", ms_per_step_launches=a[4] / 22e-3,
                            ms_per_step_graphs=b[4] / 22e-3))
+
+
+def test_md_graph_replay_after_set_params(dp, cu_stress_path):
+    # new parameters between MD calls: replayed graphs must see them (the
+    # output bias is a launch parameter), so graphs and launches still agree
+    x, v, t, box = _system(4, seed=17)
+    out = {}
+    for graphs in (0, 1):
+        o = dp.dp_options_default()
+        o.md_graphs = graphs
+        o.fit_precision = 2
+        o.embed_precision = 2
+        h = dp.dp_create(cu_stress_path, 1, CU_RC, CU_RCS, [CU_SEL], options=o, stream=None)
+        try:
+            s = dp.dp_system_create(h, x, v, t, [inputs.MASS_CU], box)
+            dp.dp_md_step(h, s, 5, 1.0)
+            fit, tab = dp.dp_get_params(h)
+            fit[-1] += 0.25  # output bias: shifts every E_i, not the forces
+            fit[:-1] *= 1.01
+            dp.dp_set_params(h, fit, None)
+            th = dp.dp_md_step(h, s, 3, 1.0, thermo=True)
+            dp.dp_md_step(h, s, 4, 1.0)
+            xg, vg, fg = dp.dp_system_get(h, s, len(x))
+            E, F, V, _ = dp.dp_compute(h, xg, t, box)
+            out[graphs] = (xg, vg, fg, th, E)
+            dp.dp_system_destroy(s)
+        finally:
+            dp.dp_destroy(h)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
