@@ -145,6 +145,19 @@ dp_status dp_compute(dp_handle* h, int64_t natoms, const double* coords, const i
 dp_status dp_system_create(dp_handle* h, int64_t natoms, const double* x, const double* v,
                            const int32_t* types, const double* mass_of_type, const double* box,
                            int device_ptrs, dp_system** out);
+/* Several independent systems as one MD system (a serving batch of small MD
+ * requests): natoms [nsys], x, v [sum natoms][3] and types [sum natoms] the
+ * systems one after another, boxes [nsys][3][3], mass_of_type as above (HOST
+ * arrays).  dp_md_step then advances all of them (one launch of each kernel;
+ * each system keeps its own box, cells and neighbor list, rebuilt on the
+ * common schedule), dp_system_get returns the concatenated arrays.  Each
+ * system's trajectory is bitwise the one it has alone.  Needs tabulated = 1
+ * and embed_precision = 2; no thermo output and no state file (both
+ * DP_ERR_UNIMPLEMENTED). */
+dp_status dp_system_create_batch(dp_handle* h, int nsys, const int64_t* natoms, const double* x,
+                                 const double* v, const int32_t* types,
+                                 const double* mass_of_type, const double* boxes,
+                                 dp_system** out);
 /* Frees the system.  The handle keeps the device buffers of the last
  * destroyed system (lists, T, dT, sorted pairs ...) and gives them to its
  * next dp_system_create, so a stream of systems does not allocate and free

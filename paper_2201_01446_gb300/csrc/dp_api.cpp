@@ -109,6 +109,18 @@ struct Work {
   DevBuf bidx, sys_of, sys_base, sys_edge, vir_tile, vir_type, seg, seg_part, seg_out;
 };
 
+// several independent systems in one atom array (host bookkeeping)
+struct Batch {
+  int nsys = 0;
+  std::vector<int64_t> base;             // [nsys + 1] first atom of each system
+  std::vector<std::array<double, 3>> L;  // box edges
+  std::vector<CellGeom> geoms;           // cell grids of the last list build
+  TileMap tm{};                          // tiles padded per system (index list in Work::bidx)
+  // per system: (first tile, tiles) of each centre type present in it
+  std::vector<std::vector<std::pair<int64_t, int64_t>>> sys_tiles;
+  DevBuf geoms_dev;                      // CellGeom [nsys] for the batched mirror
+};
+
 }  // namespace
 
 struct dp_handle {
@@ -167,6 +179,7 @@ struct dp_handle {
 struct dp_system {
   dp_handle* h = nullptr;
   Work w;
+  std::unique_ptr<Batch> batch;  // several systems (dp_system_create_batch)
   DevBuf v, mass, inv_mass_acc, thermo;
   std::vector<int32_t> types_user;
   std::vector<double> mass_user;
@@ -773,6 +786,194 @@ dp_status evaluate(dp_handle* h, Work& w) {
   return DP_OK;
 }
 
+// ------------------------------------------------------------------ several systems
+dp_status batch_init(dp_handle* h, Batch& b, int nsys, const int64_t* natoms,
+                     const double* boxes) {
+  if (nsys < 0 || (nsys > 0 && (!natoms || !boxes))) return fail(h, DP_ERR_ARG, "bad argument");
+  if (!(h->opt.tabulated && h->opt.embed_precision == 2))
+    return fail(h, DP_ERR_UNIMPLEMENTED,
+                "several systems at once need the tabulated tensor-core embedding "
+                "(embed_precision 2)");
+  b.nsys = nsys;
+  b.base.assign(nsys + 1, 0);
+  for (int q = 0; q < nsys; ++q) {
+    if (natoms[q] < 0) return fail(h, DP_ERR_ARG, "negative atom count");
+    b.base[q + 1] = b.base[q] + natoms[q];
+  }
+  if (b.base[nsys] >= (1LL << 27)) return fail(h, DP_ERR_ARG, "at most 2^27 atoms per call");
+  b.L.assign(nsys, {0.0, 0.0, 0.0});
+  for (int q = 0; q < nsys; ++q) CKS(box_lengths(h, boxes + 9 * q, b.L[q].data()));
+  return DP_OK;
+}
+
+// tiles of 32 padded per system (a tile belongs to one system, its virial row
+// to that system) and the atom -> system tables; after load_coords
+dp_status batch_tiles(dp_handle* h, Work& w, Batch& b, const int32_t* types_user) {
+  const int nsys = b.nsys;
+  const int64_t n = b.base[nsys];
+  std::vector<int32_t> pidx;
+  b.sys_tiles.assign(nsys, {});
+  TileMap tm{};
+  tm.ntypes = h->ntypes;
+  for (int t = 0; t < h->ntypes; ++t) {
+    tm.atom_off[t] = (int64_t)pidx.size();
+    tm.tile_off[t] = (int64_t)pidx.size() / 32;
+    for (int q = 0; q < nsys; ++q) {
+      const int64_t t0 = (int64_t)pidx.size() / 32;
+      for (int64_t i = b.base[q]; i < b.base[q + 1]; ++i)
+        if (h->type_map[types_user[i]] == t) pidx.push_back((int32_t)i);
+      while (pidx.size() % 32) pidx.push_back(-1);
+      const int64_t t1 = (int64_t)pidx.size() / 32;
+      if (t1 > t0) b.sys_tiles[q].push_back({t0, t1 - t0});
+    }
+    tm.atom_cnt[t] = (int64_t)pidx.size() - tm.atom_off[t];
+  }
+  tm.tile_off[h->ntypes] = (int64_t)pidx.size() / 32;
+  const int64_t ntile = tm.tile_off[h->ntypes];
+  std::vector<int32_t> sys_of(std::max<int64_t>(n, 1), 0), sys_base(std::max(nsys, 1), 0);
+  for (int q = 0; q < nsys; ++q) {
+    for (int64_t i = b.base[q]; i < b.base[q + 1]; ++i) sys_of[i] = q;
+    sys_base[q] = (int32_t)b.base[q];
+  }
+  const EnvParams ep = env_params(h);
+  CK(ensure(w.bidx, std::max<size_t>(pidx.size(), 1) * sizeof(int32_t)), "alloc tiles");
+  CK(ensure(w.sys_of, sys_of.size() * sizeof(int32_t)), "alloc systems");
+  CK(ensure(w.sys_base, sys_base.size() * sizeof(int32_t)), "alloc systems");
+  CK(ensure(w.sys_edge, (size_t)std::max(nsys, 1) * sizeof(float4)), "alloc systems");
+  CK(ensure(b.geoms_dev, (size_t)std::max(nsys, 1) * sizeof(CellGeom)), "alloc systems");
+  CK(ensure(w.vir_tile, (size_t)std::max<int64_t>(ntile, 1) * 9 * sizeof(double)), "alloc virial");
+  CK(ensure(w.tc_pairs, (size_t)std::max<int64_t>(tab_tc_pair_elems(ep, ntile), 1) * 16),
+     "alloc sorted pairs");
+  CK(ensure(w.tc_hist, (size_t)std::max<int64_t>(tab_tc_hist_elems(ep, ntile), 8) * 2),
+     "alloc bin ends");
+  CK(ensure(w.tc_range, (size_t)std::max<int64_t>(ntile, 1) * 8), "alloc bin ranges");
+  if (!pidx.empty())
+    CK(cudaMemcpyAsync(w.bidx.p, pidx.data(), pidx.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, h->st),
+       "tiles upload");
+  CK(cudaMemcpyAsync(w.sys_of.p, sys_of.data(), sys_of.size() * sizeof(int32_t),
+                     cudaMemcpyHostToDevice, h->st),
+     "systems upload");
+  CK(cudaMemcpyAsync(w.sys_base.p, sys_base.data(), sys_base.size() * sizeof(int32_t),
+                     cudaMemcpyHostToDevice, h->st),
+     "systems upload");
+  // the host vectors are freed on return: wait for the copies
+  CK(cudaStreamSynchronize(h->st), "systems upload");
+  tm.idx = P<int32_t>(w.bidx);
+  b.tm = tm;
+  return DP_OK;
+}
+
+// the systems' neighbor lists and, for the kernels, their cell grids and edges
+dp_status batch_rebuild(dp_handle* h, Work& w, Batch& b, double rlist) {
+  CKS(rebuild_batch(h, w, b.base, b.L, rlist, b.geoms));
+  const int nsys = b.nsys;
+  if (nsys == 0 || w.n == 0) return DP_OK;
+  std::vector<float4> edge(nsys);
+  for (int q = 0; q < nsys; ++q)
+    edge[q] = make_float4(b.geoms[q].edgef[0], b.geoms[q].edgef[1], b.geoms[q].edgef[2], 0.0f);
+  CK(cudaMemcpyAsync(w.sys_edge.p, edge.data(), nsys * sizeof(float4), cudaMemcpyHostToDevice,
+                     h->st),
+     "systems upload");
+  CK(cudaMemcpyAsync(b.geoms_dev.p, b.geoms.data(), nsys * sizeof(CellGeom),
+                     cudaMemcpyHostToDevice, h->st),
+     "systems upload");
+  CK(cudaMemcpyAsync(w.xref.p, w.x.p, sizeof(double) * 3 * w.n, cudaMemcpyDeviceToDevice, h->st),
+     "xref");
+  CK(cudaStreamSynchronize(h->st), "systems upload");
+  return DP_OK;
+}
+
+// forces, per-atom energies and per-tile virial rows of all the systems
+dp_status evaluate_batch(dp_handle* h, Work& w, Batch& b) {
+  const int64_t n = w.n;
+  if (n == 0) return DP_OK;
+  const EnvParams ep = env_params(h);
+  launch_zero_forces(h->st, n, P<unsigned long long>(w.ffix));
+  CK(cudaMemsetAsync(w.pairs.p, 0, sizeof(unsigned long long), h->st), "memset");
+  {
+    Phase ph(h, 1);
+    if (launch_tab_fwd_tc(h->st, b.tm, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
+                          w.cap, w.geom, ep, P<__nv_bfloat16>(h->tabF), P<float>(h->tc_scratch),
+                          P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist), P<int2>(w.tc_range),
+                          P<float>(w.T), P<int32_t>(h->status), P<unsigned long long>(w.pairs),
+                          P<int32_t>(w.sys_of), P<int32_t>(w.sys_base), P<float4>(w.sys_edge)))
+      return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core embedding cannot run this model shape");
+  }
+  {
+    Phase ph(h, 2);
+    for (int t = 0; t < h->ntypes; ++t) {
+      const int64_t cnt = w.have_idx ? w.type_count[t] : n;
+      if (cnt == 0) continue;
+      const int32_t* idx = w.have_idx ? P<int32_t>(w.idx) + w.type_off[t] : nullptr;
+      CKS(run_fitting(h, t, cnt, idx, P<float>(w.T), P<float>(w.dT), P<double>(w.e_atom)));
+      if (!w.have_idx) break;
+    }
+  }
+  {
+    Phase ph(h, 3);
+    if (launch_tab_bwd_tc(h->st, b.tm, P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist),
+                          P<int2>(w.tc_range), ep, P<__nv_bfloat16>(h->tabB), P<float>(w.dT),
+                          P<unsigned long long>(w.ffix), P<double>(w.vir_part),
+                          (int)tab_tc_slots(), P<int32_t>(h->status), P<double>(w.vir_tile)))
+      return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core embedding cannot run this model shape");
+  }
+  launch_force_finalize(h->st, n, P<unsigned long long>(w.ffix), P<double>(w.f),
+                        P<int32_t>(h->status));
+  launch_check_energy(h->st, n, P<double>(w.e_atom), P<int32_t>(h->status));
+  CK(cudaGetLastError(), "evaluation kernels");
+  return DP_OK;
+}
+
+// per-system energies and virials, each bitwise the one dp_compute makes for
+// the system alone: its atoms' energies (segments of e_atom) and, per centre
+// type, its tiles' virial rows (segments of vir_tile), added in type order
+dp_status batch_sums(dp_handle* h, Work& w, Batch& b, double* energies, double* virials) {
+  const int nsys = b.nsys;
+  const int64_t n = w.n;
+  std::vector<int64_t> seg;  // [rows..., offsets...]: systems, then (system, type) ranges
+  int nvseg = 0;
+  for (int q = 0; q < nsys; ++q) seg.push_back(b.base[q + 1] - b.base[q]);
+  for (int q = 0; q < nsys; ++q)
+    for (auto& r : b.sys_tiles[q]) seg.push_back(r.second), ++nvseg;
+  for (int q = 0; q < nsys; ++q) seg.push_back(b.base[q]);
+  for (int q = 0; q < nsys; ++q)
+    for (auto& r : b.sys_tiles[q]) seg.push_back(r.first);
+  const int nseg = nsys + nvseg;
+  std::vector<double> out((size_t)nsys + 9 * (size_t)nvseg, 0.0);
+  if (n > 0) {
+    CK(ensure(w.seg, seg.size() * sizeof(int64_t)), "alloc sums");
+    CK(ensure(w.seg_part, (size_t)std::max<int64_t>(sum_rows_seg_part_size(nsys, 1),
+                                                     sum_rows_seg_part_size(nvseg, 9)) *
+                              sizeof(double)),
+       "alloc sums");
+    CK(ensure(w.seg_out, out.size() * sizeof(double)), "alloc sums");
+    CK(cudaMemcpyAsync(w.seg.p, seg.data(), seg.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                       h->st),
+       "sums upload");
+    const int64_t* rows = P<int64_t>(w.seg);
+    const int64_t* offs = rows + nseg;
+    launch_sum_rows_seg(h->st, nsys, rows, offs, 1, P<double>(w.e_atom), P<double>(w.seg_part),
+                        P<double>(w.seg_out));
+    launch_sum_rows_seg(h->st, nvseg, rows + nsys, offs + nsys, 9, P<double>(w.vir_tile),
+                        P<double>(w.seg_part), P<double>(w.seg_out) + nsys);
+    CK(cudaGetLastError(), "sum kernels");
+    CK(cudaMemcpyAsync(out.data(), w.seg_out.p, out.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, h->st),
+       "energy copy");
+    CK(cudaStreamSynchronize(h->st), "energy copy");
+  }
+  int vk = 0;
+  for (int q = 0; q < nsys; ++q) {
+    energies[q] = out[q];
+    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // the order of launch_add_rows
+    for (size_t r = 0; r < b.sys_tiles[q].size(); ++r, ++vk)
+      for (int a = 0; a < 9; ++a) v[a] += out[nsys + 9 * (size_t)vk + a];
+    for (int a = 0; a < 9; ++a) virials[9 * q + a] = v[a];
+  }
+  return DP_OK;
+}
+
 dp_status check_handle(dp_handle* h) {
   if (!h) return DP_ERR_ARG;
   if (h->dead) return fail(h, DP_ERR_CUDA, "handle unusable after an earlier CUDA error");
@@ -1153,153 +1354,25 @@ dp_status dp_compute_batch(dp_handle* h, int nsys, const int64_t* natoms, const 
                            const int32_t* types, const double* boxes, double* energies,
                            double* forces, double* virials) {
   CKS(check_handle(h));
-  if (nsys < 0 || (nsys > 0 && (!natoms || !boxes || !energies || !virials)))
-    return fail(h, DP_ERR_ARG, "bad argument");
-  if (!(h->opt.tabulated && h->opt.embed_precision == 2))
-    return fail(h, DP_ERR_UNIMPLEMENTED,
-                "batched evaluation needs the tabulated tensor-core embedding (embed_precision 2)");
-  std::vector<int64_t> base(nsys + 1, 0);
-  for (int q = 0; q < nsys; ++q) {
-    if (natoms[q] < 0) return fail(h, DP_ERR_ARG, "negative atom count");
-    base[q + 1] = base[q] + natoms[q];
-  }
-  const int64_t n = base[nsys];
-  if (n >= (1LL << 27)) return fail(h, DP_ERR_ARG, "at most 2^27 atoms per call");
+  if (nsys > 0 && (!energies || !virials)) return fail(h, DP_ERR_ARG, "bad argument");
+  Batch b;
+  CKS(batch_init(h, b, nsys, natoms, boxes));
+  const int64_t n = b.base[nsys];
   if (n > 0 && (!coords || !types || !forces)) return fail(h, DP_ERR_ARG, "null pointer");
-  std::vector<std::array<double, 3>> Ls(nsys);
-  for (int q = 0; q < nsys; ++q) CKS(box_lengths(h, boxes + 9 * q, Ls[q].data()));
   Work& w = h->w;
   CKS(load_coords(h, w, n, coords, types, 0));
   CKS(clear_status(h));
-  // tiles: each system's atoms of a type start a new tile (padding entries
-  // -1), so a tile belongs to one system and its virial row to that system
-  std::vector<int32_t> pidx;
-  // per system, the tile range of each centre type that has atoms there
-  std::vector<std::vector<std::pair<int64_t, int64_t>>> sys_tiles(nsys);
-  TileMap tm{};
-  tm.ntypes = h->ntypes;
-  for (int t = 0; t < h->ntypes; ++t) {
-    tm.atom_off[t] = (int64_t)pidx.size();
-    tm.tile_off[t] = (int64_t)pidx.size() / 32;
-    for (int q = 0; q < nsys; ++q) {
-      const int64_t t0 = (int64_t)pidx.size() / 32;
-      for (int64_t i = base[q]; i < base[q + 1]; ++i)
-        if (h->type_map[types[i]] == t) pidx.push_back((int32_t)i);
-      while (pidx.size() % 32) pidx.push_back(-1);
-      const int64_t t1 = (int64_t)pidx.size() / 32;
-      if (t1 > t0) sys_tiles[q].push_back({t0, t1 - t0});
-    }
-    tm.atom_cnt[t] = (int64_t)pidx.size() - tm.atom_off[t];
-  }
-  tm.tile_off[h->ntypes] = (int64_t)pidx.size() / 32;
-  const int64_t ntile = tm.tile_off[h->ntypes];
-  std::vector<int32_t> sys_of(std::max<int64_t>(n, 1)), sys_base(std::max(nsys, 1));
-  std::vector<float4> sys_edge(std::max(nsys, 1));
-  for (int q = 0; q < nsys; ++q) {
-    for (int64_t i = base[q]; i < base[q + 1]; ++i) sys_of[i] = q;
-    sys_base[q] = (int32_t)base[q];
-  }
-  std::vector<CellGeom> geoms;
-  CKS(rebuild_batch(h, w, base, Ls, h->rc, geoms));
+  CKS(batch_tiles(h, w, b, types));
+  CKS(batch_rebuild(h, w, b, h->rc));
   CKS(status_errors(h));
-  if (n > 0) {
-    const EnvParams ep = env_params(h);
-    for (int q = 0; q < nsys; ++q)
-      sys_edge[q] = make_float4(geoms[q].edgef[0], geoms[q].edgef[1], geoms[q].edgef[2], 0.0f);
-    CK(ensure(w.bidx, std::max<size_t>(pidx.size(), 1) * sizeof(int32_t)), "alloc tiles");
-    CK(ensure(w.sys_of, sys_of.size() * sizeof(int32_t)), "alloc systems");
-    CK(ensure(w.sys_base, sys_base.size() * sizeof(int32_t)), "alloc systems");
-    CK(ensure(w.sys_edge, sys_edge.size() * sizeof(float4)), "alloc systems");
-    CK(ensure(w.vir_tile, (size_t)std::max<int64_t>(ntile, 1) * 9 * sizeof(double)), "alloc virial");
-    CK(ensure(w.tc_pairs, (size_t)std::max<int64_t>(tab_tc_pair_elems(ep, ntile), 1) * 16),
-       "alloc sorted pairs");
-    CK(ensure(w.tc_hist, (size_t)std::max<int64_t>(tab_tc_hist_elems(ep, ntile), 8) * 2),
-       "alloc bin ends");
-    CK(ensure(w.tc_range, (size_t)std::max<int64_t>(ntile, 1) * 8), "alloc bin ranges");
-    CK(cudaMemcpyAsync(w.bidx.p, pidx.data(), pidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
-                       h->st),
-       "tiles upload");
-    CK(cudaMemcpyAsync(w.sys_of.p, sys_of.data(), sys_of.size() * sizeof(int32_t),
-                       cudaMemcpyHostToDevice, h->st),
-       "systems upload");
-    CK(cudaMemcpyAsync(w.sys_base.p, sys_base.data(), sys_base.size() * sizeof(int32_t),
-                       cudaMemcpyHostToDevice, h->st),
-       "systems upload");
-    CK(cudaMemcpyAsync(w.sys_edge.p, sys_edge.data(), sys_edge.size() * sizeof(float4),
-                       cudaMemcpyHostToDevice, h->st),
-       "systems upload");
-    tm.idx = P<int32_t>(w.bidx);
-    launch_zero_forces(h->st, n, P<unsigned long long>(w.ffix));
-    CK(cudaMemsetAsync(w.pairs.p, 0, sizeof(unsigned long long), h->st), "memset");
-    if (launch_tab_fwd_tc(h->st, tm, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
-                          w.cap, w.geom, ep, P<__nv_bfloat16>(h->tabF), P<float>(h->tc_scratch),
-                          P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist), P<int2>(w.tc_range),
-                          P<float>(w.T), P<int32_t>(h->status), P<unsigned long long>(w.pairs),
-                          P<int32_t>(w.sys_of), P<int32_t>(w.sys_base), P<float4>(w.sys_edge)))
-      return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core embedding cannot run this model shape");
-    for (int t = 0; t < h->ntypes; ++t) {
-      const int64_t cnt = w.have_idx ? w.type_count[t] : n;
-      if (cnt == 0) continue;
-      const int32_t* idx = w.have_idx ? P<int32_t>(w.idx) + w.type_off[t] : nullptr;
-      CKS(run_fitting(h, t, cnt, idx, P<float>(w.T), P<float>(w.dT), P<double>(w.e_atom)));
-      if (!w.have_idx) break;
-    }
-    if (launch_tab_bwd_tc(h->st, tm, P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist),
-                          P<int2>(w.tc_range), ep, P<__nv_bfloat16>(h->tabB), P<float>(w.dT),
-                          P<unsigned long long>(w.ffix), P<double>(w.vir_part),
-                          (int)tab_tc_slots(), P<int32_t>(h->status), P<double>(w.vir_tile)))
-      return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core embedding cannot run this model shape");
-    launch_force_finalize(h->st, n, P<unsigned long long>(w.ffix), P<double>(w.f),
-                          P<int32_t>(h->status));
-    launch_check_energy(h->st, n, P<double>(w.e_atom), P<int32_t>(h->status));
-    CK(cudaGetLastError(), "evaluation kernels");
-  }
+  CKS(evaluate_batch(h, w, b));
   CKS(read_status(h));
   CKS(status_errors(h));
-  // per-system sums, each bitwise the one dp_compute makes for the system
-  // alone: its atoms' energies (segments of e_atom) and, per centre type,
-  // its tiles' virial rows (segments of vir_tile), added in type order
-  std::vector<int64_t> seg;  // [rows..., offsets...]: systems, then (system, type) ranges
-  int nvseg = 0;
-  for (int q = 0; q < nsys; ++q) seg.push_back(base[q + 1] - base[q]);
-  for (int q = 0; q < nsys; ++q)
-    for (auto& r : sys_tiles[q]) seg.push_back(r.second), ++nvseg;
-  for (int q = 0; q < nsys; ++q) seg.push_back(base[q]);
-  for (int q = 0; q < nsys; ++q)
-    for (auto& r : sys_tiles[q]) seg.push_back(r.first);
-  const int nseg = nsys + nvseg;
-  std::vector<double> out((size_t)nsys + 9 * (size_t)nvseg);
+  CKS(batch_sums(h, w, b, energies, virials));
   if (n > 0) {
-    CK(ensure(w.seg, seg.size() * sizeof(int64_t)), "alloc sums");
-    CK(ensure(w.seg_part, (size_t)std::max<int64_t>(sum_rows_seg_part_size(nsys, 1),
-                                                     sum_rows_seg_part_size(nvseg, 9)) *
-                              sizeof(double)),
-       "alloc sums");
-    CK(ensure(w.seg_out, out.size() * sizeof(double)), "alloc sums");
-    CK(cudaMemcpyAsync(w.seg.p, seg.data(), seg.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
-                       h->st),
-       "sums upload");
-    const int64_t* rows = P<int64_t>(w.seg);
-    const int64_t* offs = rows + nseg;
-    launch_sum_rows_seg(h->st, nsys, rows, offs, 1, P<double>(w.e_atom), P<double>(w.seg_part),
-                        P<double>(w.seg_out));
-    launch_sum_rows_seg(h->st, nvseg, rows + nsys, offs + nsys, 9, P<double>(w.vir_tile),
-                        P<double>(w.seg_part), P<double>(w.seg_out) + nsys);
-    CK(cudaGetLastError(), "sum kernels");
-    CK(cudaMemcpyAsync(out.data(), w.seg_out.p, out.size() * sizeof(double),
-                       cudaMemcpyDeviceToHost, h->st),
-       "energy copy");
     CK(cudaMemcpyAsync(forces, w.f.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->st),
        "force copy");
-    CK(cudaStreamSynchronize(h->st), "result copy");
-  }
-  int vk = 0;
-  for (int q = 0; q < nsys; ++q) {
-    energies[q] = n > 0 ? out[q] : 0.0;
-    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // the order of launch_add_rows
-    for (size_t r = 0; r < sys_tiles[q].size(); ++r, ++vk)
-      for (int a = 0; a < 9; ++a) v[a] += out[nsys + 9 * (size_t)vk + a];
-    for (int a = 0; a < 9; ++a) virials[9 * q + a] = v[a];
+    CK(cudaStreamSynchronize(h->st), "force copy");
   }
   return DP_OK;
 }
@@ -1714,6 +1787,64 @@ dp_status dp_system_create(dp_handle* h, int64_t natoms, const double* x, const 
   return DP_OK;
 }
 
+dp_status dp_system_create_batch(dp_handle* h, int nsys, const int64_t* natoms, const double* x,
+                                 const double* v, const int32_t* types,
+                                 const double* mass_of_type, const double* boxes,
+                                 dp_system** out) {
+  CKS(check_handle(h));
+  if (!out || !mass_of_type) return fail(h, DP_ERR_ARG, "bad argument");
+  *out = nullptr;
+  std::unique_ptr<Batch> b(new Batch());
+  CKS(batch_init(h, *b, nsys, natoms, boxes));
+  const int64_t n = b->base[nsys];
+  if (n > 0 && (!x || !v || !types)) return fail(h, DP_ERR_ARG, "null pointer");
+  // the system's own fields as dp_system_create sets them (the first box
+  // stands in for the batch's: dp_md_step uses the per-system boxes)
+  std::vector<double> mass_h(mass_of_type, mass_of_type + h->ntypes_user);
+  for (double mm : mass_h)
+    if (!(mm > 0)) return fail(h, DP_ERR_ARG, "masses must be > 0");
+  std::vector<double> mass_model(DP_MAXT, 0.0), inv_acc(DP_MAXT, 0.0);
+  for (int t = 0; t < h->ntypes_user; ++t) {
+    const int mt = h->type_map[t];
+    if (mass_model[mt] != 0.0 && mass_model[mt] != mass_h[t])
+      return fail(h, DP_ERR_UNIMPLEMENTED, "caller types sharing a model type need equal masses");
+    mass_model[mt] = mass_h[t];
+  }
+  for (int t = 0; t < DP_MAXT; ++t) inv_acc[t] = mass_model[t] > 0 ? kAcc / mass_model[t] : 0.0;
+  std::unique_ptr<dp_system> s(new dp_system());
+  s->h = h;
+  if (nsys > 0) std::memcpy(s->box, boxes, sizeof s->box);
+  s->mass_user = mass_h;
+  if (h->spare_work) {
+    s->w = std::move(*h->spare_work);
+    h->spare_work.reset();
+    s->v = std::move(h->spare_v);
+  }
+  CKS(load_coords(h, s->w, n, x, types, 0));
+  s->types_user.assign(types, types + n);
+  CK(ensure(s->v, sizeof(double) * 3 * std::max<int64_t>(n, 1)), "alloc velocities");
+  CK(ensure(s->mass, sizeof(double) * DP_MAXT), "alloc masses");
+  CK(ensure(s->inv_mass_acc, sizeof(double) * DP_MAXT), "alloc masses");
+  if (n) CK(cudaMemcpyAsync(s->v.p, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->st), "v");
+  CK(cudaMemcpyAsync(s->mass.p, mass_model.data(), sizeof(double) * DP_MAXT,
+                     cudaMemcpyHostToDevice, h->st),
+     "masses");
+  CK(cudaMemcpyAsync(s->inv_mass_acc.p, inv_acc.data(), sizeof(double) * DP_MAXT,
+                     cudaMemcpyHostToDevice, h->st),
+     "masses");
+  CKS(clear_status(h));
+  CKS(batch_tiles(h, s->w, *b, types));
+  CKS(batch_rebuild(h, s->w, *b, h->rc + h->opt.skin));
+  CKS(status_errors(h));
+  CKS(evaluate_batch(h, s->w, *b));
+  CKS(read_status(h));
+  CKS(status_errors(h));
+  s->batch = std::move(b);
+  s->f_valid = true;
+  *out = s.release();
+  return DP_OK;
+}
+
 void dp_system_destroy(dp_system* s) {
   if (!s) return;
   if (s->h && s->h->st) cudaStreamSynchronize(s->h->st);
@@ -1747,8 +1878,10 @@ dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_th
   if (!s || s->h != h || nsteps < 0 || !(dt_fs > 0)) return fail(h, DP_ERR_ARG, "bad argument");
   Work& w = s->w;
   const int64_t n = w.n;
-  double L[3];
-  CKS(box_lengths(h, s->box, L));
+  Batch* bt = s->batch.get();  // several systems: their own boxes and lists
+  if (bt && thermo) return fail(h, DP_ERR_UNIMPLEMENTED, "thermo output of several systems");
+  double L[3] = {0.0, 0.0, 0.0};
+  if (!bt) CKS(box_lengths(h, s->box, L));
   const double half_skin2 = 0.25 * h->opt.skin * h->opt.skin;
   const double vol = L[0] * L[1] * L[2];
   if (thermo) CK(ensure(s->thermo, sizeof(double) * 16 * std::max(nsteps, 1)), "alloc thermo");
@@ -1759,9 +1892,15 @@ dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_th
     launch_kick_drift(h->st, n, P<double>(w.x), P<double>(s->v), P<double>(w.f),
                       P<int32_t>(w.types), P<double>(s->inv_mass_acc), dt_fs, P<double>(w.xref),
                       half_skin2, P<int32_t>(h->status));
-    launch_mirror(h->st, n, P<double>(w.x), P<int32_t>(w.cellc), P<int32_t>(w.types), w.geom,
-                  P<float4>(w.off));
-    CKS(evaluate(h, w));
+    if (bt) {
+      launch_mirror_batch(h->st, n, P<double>(w.x), P<int32_t>(w.cellc), P<int32_t>(w.types),
+                          P<int32_t>(w.sys_of), P<CellGeom>(bt->geoms_dev), P<float4>(w.off));
+      CKS(evaluate_batch(h, w, *bt));
+    } else {
+      launch_mirror(h->st, n, P<double>(w.x), P<int32_t>(w.cellc), P<int32_t>(w.types), w.geom,
+                    P<float4>(w.off));
+      CKS(evaluate(h, w));
+    }
     launch_kick(h->st, n, P<double>(s->v), P<double>(w.f), P<int32_t>(w.types),
                 P<double>(s->inv_mass_acc), P<double>(s->mass), dt_fs, nullptr);
     return DP_OK;
@@ -1834,7 +1973,8 @@ dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_th
       ph1.end();  // the rebuild is timed as its own phase
       CKS(read_status(h));
       CKS(status_errors(h));
-      CKS(rebuild(h, w, L, h->rc + h->opt.skin));
+      if (bt) CKS(batch_rebuild(h, w, *bt, h->rc + h->opt.skin));
+      else CKS(rebuild(h, w, L, h->rc + h->opt.skin));
       // a rebuild may change launch parameters (list capacity, cell grid,
       // tiles) baked into the graph: capture again after it
       s->gplain = 0;
@@ -1843,12 +1983,17 @@ dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_th
         s->gexec = nullptr;
       }
     } else {
-      launch_mirror(h->st, n, P<double>(w.x), P<int32_t>(w.cellc), P<int32_t>(w.types), w.geom,
-                    P<float4>(w.off));
+      if (bt)
+        launch_mirror_batch(h->st, n, P<double>(w.x), P<int32_t>(w.cellc), P<int32_t>(w.types),
+                            P<int32_t>(w.sys_of), P<CellGeom>(bt->geoms_dev), P<float4>(w.off));
+      else
+        launch_mirror(h->st, n, P<double>(w.x), P<int32_t>(w.cellc), P<int32_t>(w.types), w.geom,
+                      P<float4>(w.off));
       ++s->gplain;
     }
     ph1.end();
-    CKS(evaluate(h, w));
+    if (bt) CKS(evaluate_batch(h, w, *bt));
+    else CKS(evaluate(h, w));
     Phase ph2(h, 4);
     launch_kick(h->st, n, P<double>(s->v), P<double>(w.f), P<int32_t>(w.types),
                 P<double>(s->inv_mass_acc), P<double>(s->mass), dt_fs,
@@ -1890,6 +2035,7 @@ dp_status dp_state_save(dp_system* s, const char* path) {
   if (!s || !path) return DP_ERR_ARG;
   dp_handle* h = s->h;
   CKS(check_handle(h));
+  if (s->batch) return fail(h, DP_ERR_UNIMPLEMENTED, "state files hold one system");
   const int64_t n = s->w.n;
   std::vector<double> x(3 * n), v(3 * n), f(3 * n), xr(3 * n);
   if (n) {

@@ -67,6 +67,10 @@ void launch_cell_sort(cudaStream_t st, long long ncell, const int32_t* start,
                       const int32_t* unsorted, int32_t* sorted);
 void launch_mirror(cudaStream_t st, int64_t n, const double* x, const int32_t* cellc,
                    const int32_t* types, const CellGeom& g, float4* off);
+// several systems: atom i uses the cell grid geoms[sys_of[i]] (device array)
+void launch_mirror_batch(cudaStream_t st, int64_t n, const double* x, const int32_t* cellc,
+                         const int32_t* types, const int32_t* sys_of, const CellGeom* geoms,
+                         float4* off);
 void launch_build_list(cudaStream_t st, int64_t n, const double* x, const int32_t* cellc,
                        const float4* off, const int32_t* cell_start, const int32_t* cell_atoms,
                        const CellGeom& g, double rlist, float rc2, int ntypes, const int32_t* sel,

@@ -133,6 +133,27 @@ __global__ void k_mirror(int64_t n, const double* __restrict__ x, const int32_t*
   off[i] = o;
 }
 
+// the same for several systems in one array: atom i uses the cell grid of
+// its system sys_of[i] (cellc holds system-local cell indices)
+__global__ void k_mirror_batch(int64_t n, const double* __restrict__ x,
+                               const int32_t* __restrict__ cellc, const int32_t* __restrict__ types,
+                               const int32_t* __restrict__ sys_of, const CellGeom* __restrict__ geoms,
+                               float4* __restrict__ off) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const CellGeom& g = geoms[sys_of[i]];
+  int id = cellc[i];
+  int c2 = id % g.nc[2];
+  int c1 = (id / g.nc[2]) % g.nc[1];
+  int c0 = id / (g.nc[2] * g.nc[1]);
+  float4 o;
+  o.x = (float)(x[i * 3 + 0] - (c0 + 0.5) * g.edge[0]);
+  o.y = (float)(x[i * 3 + 1] - (c1 + 0.5) * g.edge[1]);
+  o.z = (float)(x[i * 3 + 2] - (c2 + 0.5) * g.edge[2]);
+  o.w = __int_as_float(types[i]);
+  off[i] = o;
+}
+
 // one warp per atom, atoms visited in cell order so that the warps of a CTA
 // share their candidate cells in L1.  Lane l < 27 first looks up stencil
 // slot l's cell (its atom range and image shift); the warp then walks the
@@ -293,6 +314,14 @@ void launch_cell_sort(cudaStream_t st, long long ncell, const int32_t* start, co
 void launch_mirror(cudaStream_t st, int64_t n, const double* x, const int32_t* cellc,
                    const int32_t* types, const CellGeom& g, float4* off) {
   if (n > 0) DP_LAUNCHED(1), k_mirror<<<nblk(n, 256), 256, 0, st>>>(n, x, cellc, types, g, off);
+}
+
+void launch_mirror_batch(cudaStream_t st, int64_t n, const double* x, const int32_t* cellc,
+                         const int32_t* types, const int32_t* sys_of, const CellGeom* geoms,
+                         float4* off) {
+  if (n > 0)
+    DP_LAUNCHED(1), k_mirror_batch<<<nblk(n, 256), 256, 0, st>>>(n, x, cellc, types, sys_of, geoms,
+                                                               off);
 }
 
 void launch_build_list(cudaStream_t st, int64_t n, const double* x, const int32_t* cellc,

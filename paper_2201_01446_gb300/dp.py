@@ -46,7 +46,8 @@ EXPORTS = ["dp_options_default", "dp_create", "dp_destroy", "dp_last_error", "dp
            "dp_system_step", "dp_md_step", "dp_state_save", "dp_state_load",
            "dp_neighbor_pairs", "dp_table_coeffs", "dp_descriptor", "dp_version",
            "dp_profile", "dp_profile_read", "dp_stats", "dp_neighbor_pairs_static", "dp_fitting",
-           "dp_param_sizes", "dp_param_grad", "dp_get_params", "dp_set_params", "dp_compute_batch"]
+           "dp_param_sizes", "dp_param_grad", "dp_get_params", "dp_set_params", "dp_compute_batch",
+           "dp_system_create_batch"]
 
 DP_NPHASE = 5
 PHASES = ["neighbor_build", "embed_contract_fwd", "fitting", "embed_contract_bwd_forces",
@@ -89,6 +90,7 @@ def _load():
         "dp_param_grad": (i, [vp, i64, dp_, dp_, dp_, vp, vp, vp]),
         "dp_get_params": (i, [vp, vp, vp]),
         "dp_compute_batch": (i, [vp, i, vp, vp, vp, vp, vp, vp, vp]),
+        "dp_system_create_batch": (i, [vp, i, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]),
         "dp_set_params": (i, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -216,6 +218,26 @@ def dp_system_create(h, x, v, types, masses, box):
         ptrs = [_ptr(a, dt) for a, dt in ((x, np.float64), (v, np.float64), (types, np.int32),
                                            (masses, np.float64), (box, np.float64))]
         _check(lib.dp_system_create(h, n, *[p[0] for p in ptrs], 0, C.byref(out)), h)
+    return out
+
+
+def dp_system_create_batch(h, systems, masses):
+    """Several systems [(x [n, 3], v [n, 3], types [n], box [3, 3]), ...] as
+    one MD system (host arrays); dp_system_get returns them concatenated."""
+    nsys = len(systems)
+    counts = np.array([len(np.reshape(x, (-1, 3))) for x, _, _, _ in systems], np.int64)
+    cat = lambda k, shape, dt: np.ascontiguousarray(  # noqa: E731
+        np.concatenate([np.reshape(sy[k], shape) for sy in systems]) if nsys else np.zeros(0), dt)
+    x, v = cat(0, (-1, 3), np.float64), cat(1, (-1, 3), np.float64)
+    t = cat(2, (-1,), np.int32)
+    boxes = np.ascontiguousarray(np.stack([np.asarray(sy[3], np.float64).reshape(3, 3)
+                                           for sy in systems]) if nsys else np.zeros((1, 3, 3)))
+    m = np.ascontiguousarray(masses, np.float64)
+    out = C.c_void_p()
+    _check(lib.dp_system_create_batch(h, nsys, counts.ctypes.data_as(C.c_void_p),
+                                      x.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p),
+                                      t.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p),
+                                      boxes.ctypes.data_as(C.c_void_p), C.byref(out)), h)
     return out
 
 

@@ -78,3 +78,39 @@ def test_batch_needs_tensor_core_embedding(dp, cu_model_path):
         assert e.value.code == 9
     finally:
         dp.dp_destroy(h)
+
+
+def test_batch_md_matches_alone(dp, cu_stress_path):
+    # several systems advanced as one (list rebuilds at steps 10 and 20, plain
+    # steps replayed as a graph): each trajectory bitwise the one it has alone
+    h = _tc(dp, cu_stress_path)
+    try:
+        sys3 = []
+        for k, (cells, sig) in enumerate([(4, 0.05), ((3, 4, 5), 0.1), (5, 0.05)]):
+            x, t, box = inputs.fcc_copper(cells, sigma=sig, seed=20 + k)
+            v = inputs.maxwell_velocities(np.full(len(x), inputs.MASS_CU), 330.0, seed=30 + k)
+            sys3.append((x, v, t, box))
+        sb = dp.dp_system_create_batch(h, sys3, [inputs.MASS_CU])
+        try:
+            dp.dp_md_step(h, sb, 23, 1.0)
+            n = sum(len(s[0]) for s in sys3)
+            xb, vb, fb = dp.dp_system_get(h, sb, n)
+            with pytest.raises(dp.DPError) as e:
+                dp.dp_md_step(h, sb, 1, 1.0, thermo=True)
+            assert e.value.code == 9
+        finally:
+            dp.dp_system_destroy(sb)
+        o = 0
+        for x, v, t, box in sys3:
+            s = dp.dp_system_create(h, x, v, t, [inputs.MASS_CU], box)
+            try:
+                dp.dp_md_step(h, s, 23, 1.0)
+                xa, va, fa = dp.dp_system_get(h, s, len(x))
+            finally:
+                dp.dp_system_destroy(s)
+            m = len(x)
+            assert np.array_equal(xb[o:o + m], xa) and np.array_equal(vb[o:o + m], va)
+            assert np.array_equal(fb[o:o + m], fa)
+            o += m
+    finally:
+        dp.dp_destroy(h)
