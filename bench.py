@@ -258,7 +258,8 @@ def serve_leg(args, cu_model, pg):
             "packed_calls": st["packed_calls"], "packed_requests": st["packed_requests"],
             "mix": "Cu 500-500k atoms log-uniform + water 192*2^k (k<8), half eval half MD "
                    "(Cu 50 steps, water 10), Poisson arrivals at 0.7 x closed-loop capacity; "
-                   "queued evaluations of one model packed up to 32768 atoms per call"}
+                   "queued requests of one model and kind (MD: same steps) packed up to 32768 atoms "
+                   "per call"}
 
 
 def grad_leg(args, model_path, stream):

@@ -5,12 +5,13 @@ per model), so requests from different slots overlap on the GPU.  Results are
 computed by the same deterministic kernels whatever runs beside them, so a
 request's result is bitwise the one it has alone.
 
-Small evaluation requests of one model are packed: a slot that takes an
-evaluation from the head of the queue also takes the queued evaluations of
-the same model behind it, up to `pack_atoms` atoms in all, and runs them as
-one dp_compute_batch call (one launch of each kernel for all of them; each
-result still bitwise the one it has alone).  MD requests replay their steps
-without a list rebuild as a CUDA graph inside the library.
+Small requests of one model are packed: a slot that takes a request from
+the head of the queue also takes the queued requests of the same model and
+kind behind it (MD requests: also the same number of steps), up to
+`pack_atoms` atoms in all, and runs them as one dp_compute_batch call or one
+batched MD system (one launch of each kernel for all of them; each result
+still bitwise the one it has alone).  MD steps without a list rebuild replay
+as a CUDA graph inside the library.
 
 Host orchestration only (queueing, admission, timing): every step of every
 request runs in the library's kernels.
@@ -107,10 +108,11 @@ class Server:
                         self._ready.pop(0)
                         self._in_use += head.nbytes
                         batch = [head]
-                        if can_pack and head.kind == "eval" and len(head.x) <= self.pack_atoms:
+                        if can_pack and len(head.x) <= self.pack_atoms:
                             atoms = len(head.x)
                             for r in list(self._ready):
-                                if (r.kind == "eval" and r.model == head.model
+                                if (r.kind == head.kind and r.model == head.model
+                                        and (r.kind == "eval" or r.steps == head.steps)
                                         and atoms + len(r.x) <= self.pack_atoms
                                         and self._in_use + r.nbytes <= self.budget):
                                     self._ready.remove(r)
@@ -215,14 +217,31 @@ class _DpSlot:
                         for name, c in models.items()}
 
     def batch(self, reqs: list):
-        """Evaluations of one model as one dp_compute_batch call (models
+        """Requests of one model and kind as one call: evaluations through
+        dp_compute_batch, MD runs (same steps) as one batched system (models
         without the tensor-core tabulated embedding run them one by one)."""
         h = self.handles[reqs[0].model]
         o = self.models[reqs[0].model].options
-        if o is None or not (o.tabulated and o.embed_precision == 2):
+        same_mass = all(list(r.masses) == list(reqs[0].masses) for r in reqs)
+        if o is None or not (o.tabulated and o.embed_precision == 2) or not same_mass:
             return [self(r) for r in reqs]
-        E, F, V = dp.dp_compute_batch(h, [(r.x, r.types, r.box) for r in reqs])
-        return [(float(E[q]), F[q], V[q]) for q in range(len(reqs))]
+        if reqs[0].kind == "eval":
+            E, F, V = dp.dp_compute_batch(h, [(r.x, r.types, r.box) for r in reqs])
+            return [(float(E[q]), F[q], V[q]) for q in range(len(reqs))]
+        s = dp.dp_system_create_batch(h, [(r.x, r.v, r.types, r.box) for r in reqs],
+                                      reqs[0].masses)
+        try:
+            dp.dp_md_step(h, s, reqs[0].steps, DT_FS[reqs[0].model])
+            n = sum(len(r.x) for r in reqs)
+            X, Vv, F = dp.dp_system_get(h, s, n)
+        finally:
+            dp.dp_system_destroy(s)
+        out, o0 = [], 0
+        for r in reqs:
+            m = len(r.x)
+            out.append((X[o0:o0 + m], Vv[o0:o0 + m], F[o0:o0 + m]))
+            o0 += m
+        return out
 
     def __call__(self, req: Request):
         h = self.handles[req.model]

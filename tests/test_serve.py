@@ -89,9 +89,9 @@ class _Packer(_Sleep):
 
 
 def test_small_evaluations_are_packed():
-    # one slot, everything queued at once: the head evaluation takes the
-    # queued evaluations of the same model behind it up to pack_atoms atoms;
-    # MD requests and the other model's requests are never packed with it
+    # one slot, everything queued at once: the head request takes the queued
+    # requests of the same model and kind (MD: same steps) behind it up to
+    # pack_atoms atoms; other kinds and models are never packed with it
     models = {"cu": serve.ModelCfg("unused", 1, 8.0, 0.5, [256]),
               "water": serve.ModelCfg("unused", 2, 6.0, 0.5, [46, 92])}
     reqs = _reqs([1000, 2000, 500, 3000, 9000, 800, 700], ["eval", "md", "eval", "eval", "eval",
@@ -107,7 +107,8 @@ def test_small_evaluations_are_packed():
     for b in batches:
         kinds = {reqs[i].kind for i in b}
         names = {reqs[i].model for i in b}
-        assert kinds == {"eval"} and len(names) == 1
+        steps = {reqs[i].steps for i in b}
+        assert len(kinds) == 1 and len(names) == 1 and len(steps) == 1
         assert sum(len(reqs[i].x) for i in b) <= 6000
     # the single slot is busy while the rest queue up, so packing happens;
     # the 9000-atom evaluation exceeds pack_atoms and always runs alone
