@@ -21,8 +21,9 @@ __device__ __forceinline__ void pair_geom(const EnvParams& ep, float dx, float d
   P.dy = dy;
   P.dz = dz;
   P.tj = tj;
-  const float r = sqrtf(r2);
-  const float ir = 1.0f / r;
+  // 1/r from the hardware reciprocal square root (a few ulp), r = r2 / r
+  const float ir = rsqrtf(r2);
+  const float r = r2 * ir;
   float sw, dsw;
   if (r < ep.rcs) {
     sw = 1.0f;
