@@ -114,3 +114,29 @@ def test_batch_md_matches_alone(dp, cu_stress_path):
             o += m
     finally:
         dp.dp_destroy(h)
+
+
+def test_batch_errors_and_type_map(dp, cu_stress_path, water_model_path):
+    # an over-full system fails the whole call with the sel error; caller
+    # types reach the model through the handle's type map, as in dp_compute
+    h = _tc(dp, cu_stress_path, sel=(100,))
+    try:
+        with pytest.raises(dp.DPError) as e:
+            dp.dp_compute_batch(h, [inputs.fcc_copper(3, sigma=0.05, seed=1),
+                                    inputs.fcc_copper(4, sigma=0.0)])
+        assert e.value.code == 5
+    finally:
+        dp.dp_destroy(h)
+    o = dp.dp_options_default()
+    o.embed_precision = 2
+    o.fit_precision = 2
+    o.s_max = 1.25
+    # caller types 0 = H, 1 = O mapped onto model types 1, 0
+    hm = dp.dp_create(water_model_path, 2, 6.0, 0.5, [46, 92], type_map=[1, 0], options=o,
+                      stream=None)
+    try:
+        sys2 = [inputs.water_like(64, L=12.417, seed=s) for s in (3, 6)]
+        swapped = [(x, 1 - t, box) for x, t, box in sys2]
+        _check_alone(dp, hm, swapped, "2 x water 192, mapped types")
+    finally:
+        dp.dp_destroy(hm)

@@ -213,3 +213,30 @@ def test_set_params_matches_oracle_and_autograd(dp, cu_stress_path):
         assert ratios[0] > 0 and abs(r_ex - 1.0) < 0.05, ratios
     finally:
         dp.dp_destroy(h)
+
+
+def test_param_grad_tanh_table(dp, cu_stress_path):
+    # the fitting net on the Sec. 3.5 tanh table: the gradients use the
+    # table's own derivative on both sides
+    m = oracle.Model(cu_stress_path)
+    tab = oracle.Table(m, TABLE_H, CU_SMAX)
+    x, t, box = inputs.fcc_copper(4, sigma=0.05, seed=8)
+    oracle.set_tanh_table(True)
+    try:
+        E0, gf0, gt0 = oracle.param_grad(m, tab, CU_RC, CU_RCS, CU_SEL, x, t, box)
+    finally:
+        oracle.set_tanh_table(False)
+    o = dp.dp_options_default()
+    o.embed_precision = 2
+    o.tanh_table = 1
+    h = dp.dp_create(cu_stress_path, 1, CU_RC, CU_RCS, [CU_SEL], options=o, stream=None)
+    try:
+        E, gf, gt = dp.dp_param_grad(h, x, t, box)
+    finally:
+        dp.dp_destroy(h)
+    skip = _node_intervals(x, t, box, CU_RC, CU_RCS, TABLE_H)
+    wf = _compare_fit(gf, gf0, m, inputs.COPPER_SPEC.fit_w, "Cu tanh table", 2e-5)
+    wt = _compare_table(gt, gt0, "Cu tanh table", 2e-5, skip)
+    PARITY_LOG.append(dict(case="param grad Cu 256 tanh table", dE=abs(E - E0),
+                           fit_max_err_over_block_max=max(wf.values()),
+                           table_max_err_over_max=max(wt.values())))
