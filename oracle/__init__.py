@@ -72,6 +72,8 @@ def lib():
             "orc_model_fit_params": (i, [p, i, dp, dp]),
             "orc_table_set_coeffs": (i, [p, i, i, dp]),
             "orc_param_grad": (i, [p, p, d, d, i32p, i64, dp, i32p, dp, dp, dp, dp]),
+            "orc_emb_param_count": (i64, [p]),
+            "orc_model_emb_params": (i, [p, i, i, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -165,6 +167,25 @@ class Model:
         v = _f64(values)
         assert v.size == self.n_fit_params
         e = lib().orc_model_fit_params(self.h, ti, None, _d(v))
+        if e:
+            raise OracleError(e)
+
+    @property
+    def n_emb_params(self) -> int:
+        """Length of one type pair's embedding-net parameter layout."""
+        return int(lib().orc_emb_param_count(self.h))
+
+    def emb_params(self, ti, tj):
+        out = np.zeros(self.n_emb_params)
+        e = lib().orc_model_emb_params(self.h, ti, tj, _d(out), None)
+        if e:
+            raise OracleError(e)
+        return out
+
+    def set_emb_params(self, ti, tj, values):
+        v = _f64(values)
+        assert v.size == self.n_emb_params
+        e = lib().orc_model_emb_params(self.h, ti, tj, None, _d(v))
         if e:
             raise OracleError(e)
 
@@ -331,10 +352,12 @@ def md(model: Model, table, rc, rcs, sel, x, v, types, masses, box, dt, nsteps, 
 
 
 def param_grad(model: Model, table, rc, rcs, sel, x, types, box, with_table=True):
-    """(E, grad_fit [ntypes, n_fit_params], grad_table [ntypes, ntypes, n, 6, M]
-    or None): the energy's gradient with respect to the fitting parameters and
-    (tabulated model) the table coefficients of the normalised local variable
-    (s - k h)/h, i.e. c_q = a_q h^q."""
+    """(E, grad_fit [ntypes, n_fit_params], grad_table or None): the energy's
+    gradient with respect to the fitting parameters and the embedding
+    representation: for a tabulated model the table coefficients
+    [ntypes, ntypes, n, 6, M] of the normalised local variable (s - k h)/h,
+    i.e. c_q = a_q h^q; for the original net (table None) its weights and
+    biases [ntypes, ntypes, n_emb_params]."""
     x, box = _f64(x), _f64(box)
     types = np.ascontiguousarray(types, np.int32)
     sel = _sel(sel, model.ntypes)
@@ -343,6 +366,8 @@ def param_grad(model: Model, table, rc, rcs, sel, x, types, box, with_table=True
     gt = None
     if with_table and table is not None:
         gt = np.zeros((model.ntypes, model.ntypes, table.n, 6, model.M))
+    elif with_table:
+        gt = np.zeros((model.ntypes, model.ntypes, model.n_emb_params))
     code = lib().orc_param_grad(model.h, table.handle if table is not None else None,
                                 float(rc), float(rcs), _i32(sel), len(x), _d(x), _i32(types),
                                 _d(box), _d(E), _d(gf), _d(gt) if gt is not None else None)

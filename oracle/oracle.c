@@ -1294,6 +1294,114 @@ static int fit_grad(const orc_model* m, int ti, const double* D, double* E, doub
   return ORC_OK;
 }
 
+/* per (centre type, neighbor type) embedding net: layer k as a
+ * [(win_k + 1)][wout_k] block (W_k rows, then b_k), win_0 = 1 */
+int64_t orc_emb_param_count(const orc_model* m) {
+  if (!m) return -ORC_ERR_ARG;
+  int64_t c = 0;
+  int win = 1;
+  for (int k = 0; k < m->n_emb; ++k) {
+    c += (int64_t)(win + 1) * m->emb_w[k];
+    win = m->emb_w[k];
+  }
+  return c;
+}
+
+int orc_model_emb_params(orc_model* m, int ti, int tj, double* get, const double* set) {
+  if (!m || ti < 0 || tj < 0 || ti >= m->ntypes || tj >= m->ntypes) return ORC_ERR_ARG;
+  const int p = ti * m->ntypes + tj;
+  int64_t o = 0;
+  int win = 1;
+  for (int k = 0; k < m->n_emb; ++k) {
+    const int wo = m->emb_w[k];
+    double* W = (double*)m->emb_W[p][k];
+    double* b = (double*)m->emb_b[p][k];
+    const size_t nw = (size_t)win * wo;
+    if (get) {
+      memcpy(get + o, W, sizeof(double) * nw);
+      memcpy(get + o + nw, b, sizeof(double) * wo);
+    }
+    if (set) {
+      memcpy(W, set + o, sizeof(double) * nw);
+      memcpy(b, set + o + nw, sizeof(double) * wo);
+    }
+    o += (int64_t)nw + wo;
+    win = wo;
+  }
+  return ORC_OK;
+}
+
+/* dE/d(embedding-net parameters of pair type p) added into g, given
+ * dE/dG at s.  Reverse mode through Eq. 4-5: with out_L = (in,in) + t_L,
+ * t_L = tanh(in W_L + b_L) and dz = dE/dout_L (1 - t_L^2):
+ *   dE/dW_L[k][c] = in[k] dz[c],  dE/db_L = dz,
+ *   dE/din[k] = sum_c W_L[k][c] dz[c] + sum_{c : c mod win = k} dE/dout_L[c]. */
+static int emb_grad(const orc_model* m, int p, double s, const double* dEdG, double* g) {
+  const int nl = m->n_emb;
+  size_t tot = 0;
+  for (int k = 0; k < nl; ++k) tot += (size_t)m->emb_w[k];
+  double* buf = (double*)malloc(sizeof(double) * (2 * tot + 3 * (size_t)m->M));
+  if (!buf) return ORC_ERR_NOMEM;
+  double* t = buf;         /* tanh values, layer by layer */
+  double* out = buf + tot; /* layer outputs */
+  double* d = out + tot;
+  double* dn = d + m->M;
+  double* dz = dn + m->M;
+  size_t off[MAXL + 1];
+  off[0] = 0;
+  for (int k = 0; k < nl; ++k) off[k + 1] = off[k] + (size_t)m->emb_w[k];
+  for (int c = 0; c < m->emb_w[0]; ++c) {
+    t[c] = tanh(s * m->emb_W[p][0][c] + m->emb_b[p][0][c]);
+    out[c] = t[c];
+  }
+  for (int L = 1; L < nl; ++L) {
+    const int win = m->emb_w[L - 1], wo = m->emb_w[L];
+    const double* in = out + off[L - 1];
+    for (int c = 0; c < wo; ++c) {
+      double z = m->emb_b[p][L][c];
+      for (int k = 0; k < win; ++k) z += in[k] * m->emb_W[p][L][(size_t)k * wo + c];
+      t[off[L] + c] = tanh(z);
+      out[off[L] + c] = in[c % win] + t[off[L] + c];
+    }
+  }
+  size_t goff[MAXL + 1];
+  goff[0] = 0;
+  for (int k = 0, win = 1; k < nl; ++k) {
+    goff[k + 1] = goff[k] + (size_t)(win + 1) * m->emb_w[k];
+    win = m->emb_w[k];
+  }
+  memcpy(d, dEdG, sizeof(double) * m->M);
+  for (int L = nl - 1; L >= 1; --L) {
+    const int win = m->emb_w[L - 1], wo = m->emb_w[L];
+    const double* in = out + off[L - 1];
+    double* gW = g + goff[L];
+    double* gb = gW + (size_t)win * wo;
+    for (int c = 0; c < wo; ++c) {
+      const double tt = t[off[L] + c];
+      dz[c] = d[c] * (1.0 - tt * tt);
+      gb[c] += dz[c];
+    }
+    for (int k = 0; k < win; ++k) {
+      double v = 0.0;
+      for (int c = 0; c < wo; ++c) {
+        gW[(size_t)k * wo + c] += in[k] * dz[c];
+        v += m->emb_W[p][L][(size_t)k * wo + c] * dz[c];
+      }
+      for (int c = k; c < wo; c += win) v += d[c];
+      dn[k] = v;
+    }
+    memcpy(d, dn, sizeof(double) * win);
+  }
+  const int w0 = m->emb_w[0];
+  for (int c = 0; c < w0; ++c) {
+    const double dz0 = d[c] * (1.0 - t[c] * t[c]);
+    g[c] += s * dz0;       /* W_0 [1][w0] */
+    g[w0 + c] += dz0;      /* b_0 */
+  }
+  free(buf);
+  return ORC_OK;
+}
+
 /* E and the parameter gradients of the whole system.  grad_fit: the blocks
  * of every centre type in type order (orc_fit_param_count each).
  * grad_table (tabulated model only, may be NULL): [ntypes*ntypes][n][6][M]
@@ -1306,7 +1414,6 @@ int orc_param_grad(const orc_model* m, const orc_table* table, double rc, double
                    const int32_t* sel, int64_t n, const double* x, const int32_t* types,
                    const double* box, double* energy, double* grad_fit, double* grad_table) {
   if (!grad_fit || !energy) return ORC_ERR_ARG;
-  if (grad_table && !table) return ORC_ERR_ARG;
   ctx_t C;
   cells_t cells;
   int e = ctx_setup(&C, &cells, m, table, rc, rcs, sel, n, x, types, box);
@@ -1314,8 +1421,11 @@ int orc_param_grad(const orc_model* m, const orc_table* table, double rc, double
   const int64_t per = orc_fit_param_count(m);
   const int M = m->M, mlt = m->m_lt;
   memset(grad_fit, 0, sizeof(double) * (size_t)per * m->ntypes);
+  const int64_t per_emb = orc_emb_param_count(m);
   if (grad_table)
-    memset(grad_table, 0, sizeof(double) * (size_t)m->ntypes * m->ntypes * table->n * 6 * M);
+    memset(grad_table, 0,
+           sizeof(double) * (size_t)m->ntypes * m->ntypes *
+               (table ? (size_t)table->n * 6 * M : (size_t)per_emb));
   const double inv_nm = 1.0 / (double)C.Nm;
   work_t w;
   double* Ei = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -1366,21 +1476,27 @@ int orc_param_grad(const orc_model* m, const orc_table* table, double rc, double
           for (int b = 0; b < M; ++b) s += w.dD[b * mlt + a] * w.T[c * M + b];
         w.dT[c * M + a] = s;
       }
-    for (int64_t q = 0; q < k; ++q) {
+    for (int64_t q = 0; q < k && !e; ++q) {
       const int tj = types[w.nb[q].j];
       const double* R = w.R + q * 4;
-      /* the interval and local variable of orc_table_eval */
       const double s = R[0];
-      const double fk = floor(s / table->h);
-      int kk = (int)fk;
-      if (fk < 0) kk = 0;
-      if (fk > table->n - 1) kk = table->n - 1;
-      const double v = (s - kk * table->h) / table->h;
       for (int a = 0; a < M; ++a) {
         double g = 0.0;
         for (int c = 0; c < 4; ++c) g += w.dT[c * M + a] * R[c];
         dEdg[a] = g * inv_nm;
       }
+      if (!table) {
+        /* the original embedding net: its weights and biases */
+        e = emb_grad(m, ti * m->ntypes + tj, s, dEdg,
+                     grad_table + (size_t)(ti * m->ntypes + tj) * per_emb);
+        continue;
+      }
+      /* the interval and local variable of orc_table_eval */
+      const double fk = floor(s / table->h);
+      int kk = (int)fk;
+      if (fk < 0) kk = 0;
+      if (fk > table->n - 1) kk = table->n - 1;
+      const double v = (s - kk * table->h) / table->h;
       double* out = grad_table + ((size_t)(ti * m->ntypes + tj) * table->n + kk) * 6 * M;
       double vp = 1.0;
       for (int p = 0; p < 6; ++p) {

@@ -130,11 +130,16 @@ int64_t orc_fit_param_count(const orc_model* m);
 int orc_model_fit_params(orc_model* m, int ti, double* get, const double* set);
 /* replace the coefficients of pair (ti,tj) ([n][6][M], local variable s - k*h) */
 int orc_table_set_coeffs(orc_table* t, int ti, int tj, const double* in);
+/* per (centre, neighbor) type pair: the embedding net's parameters, layer k
+ * as a [(win_k + 1)][wout_k] block (W_k rows, then b_k), win_0 = 1 */
+int64_t orc_emb_param_count(const orc_model* m);
+int orc_model_emb_params(orc_model* m, int ti, int tj, double* get, const double* set);
 /* energy and dE/d(fitting parameters) of all centre types (grad_fit:
- * ntypes x orc_fit_param_count) and, for a tabulated model, dE/d(table
- * coefficients) grad_table [ntypes*ntypes][n][6][M] (may be NULL) with
- * respect to c_q = a_q h^q, the coefficients of the normalised local
- * variable (s - k*h)/h */
+ * ntypes x orc_fit_param_count) and dE/d(embedding representation) in
+ * grad_table (may be NULL): for a tabulated model the table coefficients
+ * [ntypes*ntypes][n][6][M] with respect to c_q = a_q h^q, the coefficients of
+ * the normalised local variable (s - k*h)/h; for the original net
+ * (table == NULL) its weights and biases [ntypes*ntypes][orc_emb_param_count] */
 int orc_param_grad(const orc_model* m, const orc_table* table, double rc, double rcs,
                    const int32_t* sel, int64_t n, const double* x, const int32_t* types,
                    const double* box, double* energy, double* grad_fit, double* grad_table);

@@ -1,6 +1,7 @@
 """Pins of the oracle's parameter gradients (dE/d fitting weights and biases,
-dE/d table coefficients) to central differences of the oracle's energy, to
-the exact bias gradient and to the table's homogeneity (T is linear in the
+dE/d table coefficients, dE/d embedding-net weights and biases of the
+original model) to central differences of the oracle's energy, to the exact
+bias gradient and to the table's homogeneity (T is linear in the
 coefficients, so sum_c c dE/dc = d/dlambda E(lambda c) at lambda = 1)."""
 import numpy as np
 import pytest
@@ -116,7 +117,7 @@ def test_table_gradient_homogeneity(small):
 def test_untabulated_fitting_gradient(small):
     # the original embedding net: fitting gradients only, same central-difference pin
     m, _, x, t, box = small
-    E, gf, gt = oracle.param_grad(m, None, RC, RCS, SEL, x, t, box)
+    E, gf, gt = oracle.param_grad(m, None, RC, RCS, SEL, x, t, box, with_table=False)
     assert gt is None and E == _energy(m, None, x, t, box)
     p0 = m.fit_params(1)
     k = len(p0) // 3
@@ -132,3 +133,30 @@ def test_untabulated_fitting_gradient(small):
     finally:
         m.set_fit_params(1, p0)
     assert abs((ep - em) / (2 * eps) - gf[1, k]) < 1e-7 + 1e-6 * abs(gf[1, k])
+
+
+@pytest.mark.parametrize("pair", [(0, 0), (0, 1), (1, 1)])
+def test_embedding_net_gradient_matches_central_differences(small, pair):
+    # the original (untabulated) model: dE/d(embedding-net weights, biases)
+    m, _, x, t, box = small
+    ti, tj = pair
+    _, _, ge = oracle.param_grad(m, None, RC, RCS, SEL, x, t, box)
+    assert ge.shape == (2, 2, m.n_emb_params)
+    p0 = m.emb_params(ti, tj)
+    rng = np.random.default_rng(3 + ti + 2 * tj)
+    # W_0, b_0, a hidden W and b, the last layer's W and b
+    idx = [0, 9, 20] + list(rng.choice(len(p0), 9, replace=False)) + [len(p0) - 1]
+    try:
+        for k in idx:
+            eps = 1e-5 * max(1.0, abs(p0[k]))
+            p = p0.copy()
+            p[k] += eps
+            m.set_emb_params(ti, tj, p)
+            ep = _energy(m, None, x, t, box)
+            p[k] -= 2 * eps
+            m.set_emb_params(ti, tj, p)
+            em = _energy(m, None, x, t, box)
+            fd = (ep - em) / (2 * eps)
+            assert abs(fd - ge[ti, tj, k]) < 1e-8 + 1e-6 * abs(fd), (k, fd, ge[ti, tj, k])
+    finally:
+        m.set_emb_params(ti, tj, p0)
