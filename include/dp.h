@@ -239,9 +239,12 @@ dp_status dp_compute_batch(dp_handle* h, int nsys, const int64_t* natoms, const 
  *
  * Fitting layout, per model type in type order, per hidden layer k a block of
  * [(win_k + 1)][wout_k] doubles (W_k row-major, then b_k), then [(w_last + 1)]
- * (w_out, then b_out).  Table layout: [ntypes][ntypes][n][6][M], the layout
- * of dp_table_coeffs: the derivative with respect to c[k][q][:], the
- * coefficient of u^q with u = s/h - k.
+ * (w_out, then b_out).  The embedding representation ("table" arrays): for
+ * a tabulated handle the table, [ntypes][ntypes][n][6][M] in the layout of
+ * dp_table_coeffs (the derivative with respect to c[k][q][:], the
+ * coefficient of u^q with u = s/h - k); for an untabulated handle
+ * (tabulated = 0) the embedding nets' weights and biases, per (centre,
+ * neighbor) type pair per layer a [(win_k + 1)][wout_k] block, win_0 = 1.
  * ------------------------------------------------------------------------- */
 /* *n_fit: doubles of the fitting gradient (all types); *n_table: doubles of
  * the table gradient.  Either pointer may be NULL. */
@@ -252,7 +255,7 @@ dp_status dp_param_sizes(dp_handle* h, int64_t* n_fit, int64_t* n_table);
  * cores whatever fit_precision says; the gradients are summed per chunk in
  * FP32 and across chunks in FP64 (deterministic).
  *   grad_fit   HOST [n_fit] (required, overwritten);
- *   grad_table HOST [n_table] or NULL.  Needs tabulated = 1 and
+ *   grad_table HOST [n_table] or NULL.  A tabulated handle needs
  *              embed_precision = 2 (DP_ERR_UNIMPLEMENTED otherwise).
  * Errors as dp_compute (DP_ERR_SEL_OVERFLOW, DP_ERR_TABLE_RANGE, ...). */
 dp_status dp_param_grad(dp_handle* h, int64_t natoms, const double* coords,
@@ -261,14 +264,15 @@ dp_status dp_param_grad(dp_handle* h, int64_t natoms, const double* coords,
 
 /* The model's current parameters in the same two layouts (HOST arrays of
  * n_fit and n_table doubles; either may be NULL).  The device keeps FP32
- * copies, so a get returns FP32 values. */
+ * copies of the fitting nets and the table, so those come back as FP32
+ * values; an untabulated handle's embedding nets come back as loaded. */
 dp_status dp_get_params(dp_handle* h, double* fit, double* table);
 
 /* Replace the fitting parameters and/or the table coefficients (either
  * pointer may be NULL), e.g. after a gradient step; they are rounded to FP32
  * and every derived device copy (transposes, BF16 pieces, tiled table
- * operands) is rebuilt.  Synchronous.  A table on an untabulated handle is
- * DP_ERR_ARG. */
+ * operands) is rebuilt.  Synchronous.  A table on an untabulated handle (its
+ * embedding nets cannot be replaced) is DP_ERR_ARG. */
 dp_status dp_set_params(dp_handle* h, const double* fit, const double* table);
 
 /* ---------------------------------------------------------------------------

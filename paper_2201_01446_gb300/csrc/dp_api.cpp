@@ -1546,10 +1546,18 @@ static int64_t fit_params_per_type(const dp_handle* h) {
   return c + win + 1;
 }
 
+// doubles of the embedding representation's gradient: the table
+// coefficients (tabulated) or the embedding nets' weights and biases
+static int64_t emb_repr_params(const dp_handle* h) {
+  const int64_t np = (int64_t)h->ntypes * h->ntypes;
+  if (h->opt.tabulated) return np * h->n_int * 6 * h->M;
+  return np * plain_wgrad_params(h->emb_w[0], h->M);
+}
+
 dp_status dp_param_sizes(dp_handle* h, int64_t* n_fit, int64_t* n_table) {
   CKS(check_handle(h));
   if (n_fit) *n_fit = fit_params_per_type(h) * h->ntypes;
-  if (n_table) *n_table = (int64_t)h->ntypes * h->ntypes * h->n_int * 6 * h->M;
+  if (n_table) *n_table = emb_repr_params(h);
   return DP_OK;
 }
 
@@ -1560,7 +1568,7 @@ dp_status dp_param_grad(dp_handle* h, int64_t natoms, const double* coords, cons
   if (natoms < 0 || !box || !energy || !grad_fit || (natoms > 0 && (!coords || !types)))
     return fail(h, DP_ERR_ARG, "null pointer or negative atom count");
   if (natoms >= (1LL << 27)) return fail(h, DP_ERR_ARG, "at most 2^27 atoms per call");
-  if (grad_table && !(h->opt.tabulated && h->opt.embed_precision == 2))
+  if (grad_table && h->opt.tabulated && h->opt.embed_precision != 2)
     return fail(h, DP_ERR_UNIMPLEMENTED,
                 "table gradients need the tabulated tensor-core embedding (embed_precision 2)");
   double L[3];
@@ -1572,7 +1580,7 @@ dp_status dp_param_grad(dp_handle* h, int64_t natoms, const double* coords, cons
   CKS(status_errors(h));
   const int64_t per = fit_params_per_type(h);
   const int64_t nfit = per * h->ntypes;
-  const int64_t ntab = (int64_t)h->ntypes * h->ntypes * h->n_int * 6 * h->M;
+  const int64_t ntab = emb_repr_params(h);
   CK(ensure(h->pg, sizeof(double) * (size_t)(nfit + ntab)), "alloc gradients");
   CK(cudaMemsetAsync(h->pg.p, 0, sizeof(double) * (size_t)(nfit + ntab), h->st), "memset");
   const int64_t n = natoms;
@@ -1595,13 +1603,25 @@ dp_status dp_param_grad(dp_handle* h, int64_t natoms, const double* coords, cons
         return fail(h, DP_ERR_CUDA, "fitting kernels failed to launch");
       if (!w.have_idx) break;
     }
-    if (grad_table) {
+    if (grad_table && h->opt.tabulated) {
       const int64_t tp = tab_grad_part_floats(ep);
       CK(ensure(h->pg_tab_part, sizeof(float) * (size_t)tp), "alloc gradient partials");
       if (launch_tab_grad_tc(h->st, w.tiles, P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist),
                              P<int2>(w.tc_range), ep, P<float>(w.dT), P<float>(h->pg_tab_part),
                              P<double>(h->pg) + nfit))
         return fail(h, DP_ERR_UNIMPLEMENTED, "table gradient cannot run this model shape");
+    } else if (grad_table) {
+      // the original embedding nets: one launch per (centre, neighbor) type pair
+      const int npar = plain_wgrad_params(h->emb_w[0], h->M);
+      CK(ensure(h->pg_tab_part, sizeof(float) * (size_t)plain_wgrad_ctas() * npar),
+         "alloc gradient partials");
+      for (int ti = 0; ti < h->ntypes; ++ti)
+        for (int tj = 0; tj < h->ntypes; ++tj)
+          if (launch_plain_wgrad(h->st, n, P<float4>(w.off), P<uint32_t>(w.nlist),
+                                 P<int32_t>(w.nn), w.cap, w.geom, ep, h->plain_nets.p, h->emb_w[0],
+                                 P<float>(w.dT), ti, tj, P<float>(h->pg_tab_part),
+                                 P<double>(h->pg) + nfit + (size_t)(ti * h->ntypes + tj) * npar))
+            return fail(h, DP_ERR_UNIMPLEMENTED, "embedding-net gradient cannot run this model");
     }
     launch_sum_rows(h->st, n, 1, P<double>(w.e_atom), P<double>(w.red_part), P<double>(w.red_out));
     launch_check_energy(h->st, n, P<double>(w.e_atom), P<int32_t>(h->status));
@@ -1645,7 +1665,13 @@ dp_status dp_get_params(dp_handle* h, double* fit, double* table) {
       *o++ = h->b_out[t];
     }
   }
-  if (table) {
+  if (table && !h->opt.tabulated) {
+    // the embedding nets' FP64 weights and biases, in the file's (and the
+    // gradient's) layout
+    CK(cudaMemcpy(table, h->emb64.p, sizeof(double) * (size_t)emb_repr_params(h),
+                  cudaMemcpyDeviceToHost),
+       "embedding copy");
+  } else if (table) {
     const size_t n = (size_t)h->ntypes * h->ntypes * h->n_int * 6 * h->M;
     std::vector<float> tb(n);
     CK(cudaMemcpy(tb.data(), h->table.p, sizeof(float) * n, cudaMemcpyDeviceToHost),

@@ -155,6 +155,15 @@ int launch_plain_bwd(cudaStream_t st, int64_t n, const float4* off, const uint32
                      const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
                      const void* nets, int d1, const float* dT, unsigned long long* ffix,
                      double* vir_part, int vir_slots, int32_t* status);
+// dE/d(embedding-net parameters) of type pair (ti, tj) added into grad (FP64,
+// per layer a [(win + 1)][wout] block: W rows then b; win_0 = 1) from dE/dT;
+// part: plain_wgrad_ctas() x plain_wgrad_params() floats
+int plain_wgrad_params(int d1, int M);
+int plain_wgrad_ctas();
+int launch_plain_wgrad(cudaStream_t st, int64_t n, const float4* off, const uint32_t* nlist,
+                       const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
+                       const void* nets, int d1, const float* dT, int ti, int tj, float* part,
+                       double* grad);
 
 // ---------------------------------------------------------------- fitting
 struct FitNet {           // one centre type, FP32 device pointers

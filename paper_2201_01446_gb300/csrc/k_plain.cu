@@ -528,6 +528,242 @@ bool plain_shape_ok(const EnvParams& ep, int d1) {
 }
 
 
+// ------------------------------------------------------------------ parameter gradients
+// dE/d(embedding-net weights and biases) of one (centre, neighbor) type pair,
+// reverse mode through Eq. 4-5 per pair: with dE/dG = (1/N_m) R^T dE/dT,
+//   layer 2: dp2 = dE/dG (1 - t2^2), dW2[l][q] += h1[l] dp2[q], db2 += dp2,
+//   layer 1: dp1 = dE/dh1 (1 - t1^2), dW1[k][m] += h0[k] dp1[m], db1 += dp1,
+//   layer 0: dp0 = dE/dh0 (1 - h0^2), dW0[k] += s dp0[k], db0 += dp0,
+// where dE/dh1 and dE/dh0 carry the (x,x) shortcuts.  One warp per CTA; the
+// CTA's sums (one layout block per layer: W rows, then b) stay in its
+// shared memory, every element owned by one lane (no atomics), and go to the
+// CTA's row of part at the end; a second kernel adds the rows in order.
+__global__ void __launch_bounds__(32) k_plain_wgrad(int64_t n, const float4* __restrict__ off,
+                                                    const uint32_t* __restrict__ nlist,
+                                                    const int32_t* __restrict__ nn, int cap,
+                                                    CellGeom g, EnvParams ep,
+                                                    const PlainNet* __restrict__ nets, int d1,
+                                                    const float* __restrict__ dT, int ti, int tj,
+                                                    int npar, float* __restrict__ part) {
+  extern __shared__ float4 smem4[];
+  PlainSmem& S = *reinterpret_cast<PlainSmem*>(smem4);
+  float* acc = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(smem4) +
+                                        (sizeof(PlainSmem) + 15) / 16 * 16);
+  const int lane = threadIdx.x;
+  const int M = ep.M, nt = ep.ntypes, d2 = 2 * d1;
+  const int cl = lane * 4;
+  const unsigned below = (1u << lane) - 1u;
+  // the layer blocks: W0 [1][d1], b0; W1 [d1][d2], b1; W2 [d2][M], b2
+  float* gW0 = acc;
+  float* gb0 = gW0 + d1;
+  float* gW1 = gb0 + d1;
+  float* gb1 = gW1 + d1 * d2;
+  float* gW2 = gb1 + d2;
+  float* gb2 = gW2 + d2 * M;
+  for (int e = lane; e < npar; e += 32) acc[e] = 0.0f;
+  __syncwarp();
+  const PlainNet w = nets[ti * nt + tj];
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const float4 oi = off[i];
+    if (__float_as_int(oi.w) != ti) continue;
+    const int cnt = min(nn[i], cap);
+    const uint32_t* L = nlist + (size_t)i * cap;
+    float dTv[4][4];  // dT[c][cl + q]
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float4 t4 = cl < M ? *reinterpret_cast<const float4*>(dT + (size_t)i * 4 * M + c * M + cl)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+      dTv[c][0] = t4.x;
+      dTv[c][1] = t4.y;
+      dTv[c][2] = t4.z;
+      dTv[c][3] = t4.w;
+    }
+    for (int b0 = 0; b0 < cnt; b0 += 32) {
+      const int k = b0 + lane;
+      bool in = false;
+      float s = 0.f, dsdr = 0.f, ir = 0.f, dx = 0.f, dy = 0.f, dz = 0.f;
+      if (k < cnt) {
+        int t;
+        load_pair_p(oi, off, g, L[k], dx, dy, dz, t);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < ep.rc2 && t == tj) {
+          in = true;
+          plain_pair(ep, dx, dy, dz, r2, s, dsdr, ir);
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int slot = __popc(m & below);
+        S.s[slot] = s;
+        S.R[slot][0] = s;
+        S.R[slot][1] = s * dx * ir;
+        S.R[slot][2] = s * dy * ir;
+        S.R[slot][3] = s * dz * ir;
+      }
+      __syncwarp();
+      const int c = __popc(m);
+      for (int p0 = 0; p0 < c; p0 += kP) {
+        float sv[kP];
+#pragma unroll
+        for (int p = 0; p < kP; ++p) sv[p] = p0 + p < c ? S.s[p0 + p] : 0.0f;
+        plain_layers01(w, d1, S, sv, lane);
+        float G[kP][4], t2[kP][4];
+        plain_layer2(w, d1, M, S, lane, G, t2);
+        // dE/dG and dp2 for the lane's columns (zero for padding pairs)
+        float dp2[kP][4];
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+          float4 R = *reinterpret_cast<const float4*>(S.R[p0 + p < c ? p0 + p : p0]);
+          if (p0 + p >= c) R = make_float4(0.f, 0.f, 0.f, 0.f);
+          const float rv[4] = {R.x, R.y, R.z, R.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float dg = 0.0f;
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) dg = fmaf(dTv[cc][q], rv[cc], dg);
+            dg *= ep.inv_nm;
+            dp2[p][q] = dg * (1.0f - t2[p][q] * t2[p][q]);
+            if (cl < M) {
+              S.dg[cl + q][p] = dg;
+              S.dp2[cl + q][p] = dp2[p][q];
+            }
+          }
+        }
+        // layer 2: the lane's four columns of W2 and b2
+        if (cl < M) {
+          for (int l = 0; l < d2; ++l) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&S.h1[l][0]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&S.h1[l][4]);
+            const float hv[kP] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            // scalar accesses: the block's offset need not be a multiple of 4
+            float* gr = gW2 + l * M + cl;
+            float gw[4] = {gr[0], gr[1], gr[2], gr[3]};
+#pragma unroll
+            for (int p = 0; p < kP; ++p)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) gw[q] = fmaf(hv[p], dp2[p][q], gw[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) gr[q] = gw[q];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float sb = gb2[cl + q];
+#pragma unroll
+            for (int p = 0; p < kP; ++p) sb += dp2[p][q];
+            gb2[cl + q] = sb;
+          }
+        }
+        __syncwarp();
+        // back to h1 (lanes own l = lane, lane + 32), then dp1
+        float dh1[2][kP], dp1[2][kP];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int l = lane + 32 * h;
+#pragma unroll
+          for (int p = 0; p < kP; ++p) dh1[h][p] = dp1[h][p] = 0.0f;
+          if (l < d2) {
+#pragma unroll
+            for (int p = 0; p < kP; ++p) dh1[h][p] = S.dg[l][p] + S.dg[l + d2][p];
+            for (int q = 0; q < M; ++q) {
+              const float W = __ldg(w.W2T + q * d2 + l);
+              const float4 a0 = *reinterpret_cast<const float4*>(&S.dp2[q][0]);
+              const float4 a1 = *reinterpret_cast<const float4*>(&S.dp2[q][4]);
+              dh1[h][0] = fmaf(a0.x, W, dh1[h][0]);
+              dh1[h][1] = fmaf(a0.y, W, dh1[h][1]);
+              dh1[h][2] = fmaf(a0.z, W, dh1[h][2]);
+              dh1[h][3] = fmaf(a0.w, W, dh1[h][3]);
+              dh1[h][4] = fmaf(a1.x, W, dh1[h][4]);
+              dh1[h][5] = fmaf(a1.y, W, dh1[h][5]);
+              dh1[h][6] = fmaf(a1.z, W, dh1[h][6]);
+              dh1[h][7] = fmaf(a1.w, W, dh1[h][7]);
+            }
+#pragma unroll
+            for (int p = 0; p < kP; ++p) {
+              const float t = S.t1[l][p];
+              dp1[h][p] = dh1[h][p] * (1.0f - t * t);
+            }
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int l = lane + 32 * h;
+          if (l < d2) {
+#pragma unroll
+            for (int p = 0; p < kP; ++p) {
+              S.dp1[l][p] = dp1[h][p];
+              S.h1[l][p] = dh1[h][p];  // h1 is no longer needed: keep dE/dh1 there
+            }
+            // layer 1: column l of W1 and b1
+            float sb = gb1[l];
+#pragma unroll
+            for (int p = 0; p < kP; ++p) sb += dp1[h][p];
+            gb1[l] = sb;
+            for (int kk = 0; kk < d1; ++kk) {
+              const float4 a0 = *reinterpret_cast<const float4*>(&S.h0[kk][0]);
+              const float4 a1 = *reinterpret_cast<const float4*>(&S.h0[kk][4]);
+              float gw = gW1[kk * d2 + l];
+              gw = fmaf(a0.x, dp1[h][0], gw);
+              gw = fmaf(a0.y, dp1[h][1], gw);
+              gw = fmaf(a0.z, dp1[h][2], gw);
+              gw = fmaf(a0.w, dp1[h][3], gw);
+              gw = fmaf(a1.x, dp1[h][4], gw);
+              gw = fmaf(a1.y, dp1[h][5], gw);
+              gw = fmaf(a1.z, dp1[h][6], gw);
+              gw = fmaf(a1.w, dp1[h][7], gw);
+              gW1[kk * d2 + l] = gw;
+            }
+          }
+        }
+        __syncwarp();
+        // back to h0 (lane = k), then layer 0
+        if (lane < d1) {
+          float dh0[kP];
+#pragma unroll
+          for (int p = 0; p < kP; ++p) dh0[p] = S.h1[lane][p] + S.h1[lane + d1][p];
+          for (int mm = 0; mm < d2; ++mm) {
+            const float W = __ldg(w.W1T + mm * d1 + lane);
+            const float4 a0 = *reinterpret_cast<const float4*>(&S.dp1[mm][0]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&S.dp1[mm][4]);
+            dh0[0] = fmaf(a0.x, W, dh0[0]);
+            dh0[1] = fmaf(a0.y, W, dh0[1]);
+            dh0[2] = fmaf(a0.z, W, dh0[2]);
+            dh0[3] = fmaf(a0.w, W, dh0[3]);
+            dh0[4] = fmaf(a1.x, W, dh0[4]);
+            dh0[5] = fmaf(a1.y, W, dh0[5]);
+            dh0[6] = fmaf(a1.z, W, dh0[6]);
+            dh0[7] = fmaf(a1.w, W, dh0[7]);
+          }
+          float sw = gW0[lane], sb = gb0[lane];
+#pragma unroll
+          for (int p = 0; p < kP; ++p) {
+            const float h0 = S.h0[lane][p];
+            const float dp0 = dh0[p] * (1.0f - h0 * h0);
+            sw = fmaf(sv[p], dp0, sw);
+            sb += dp0;
+          }
+          gW0[lane] = sw;
+          gb0[lane] = sb;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncwarp();
+  float* dst = part + (size_t)blockIdx.x * npar;
+  for (int e = lane; e < npar; e += 32) dst[e] = acc[e];
+}
+
+// g[e] += sum over the CTAs (in order) of part[cta][e], in FP64
+__global__ void k_plain_wgrad_add(int nct, int npar, const float* __restrict__ part,
+                                  double* __restrict__ g) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= npar) return;
+  double s = 0.0;
+  for (int k = 0; k < nct; ++k) s += (double)part[(size_t)k * npar + e];
+  g[e] += s;
+}
+
 }  // namespace
 
 int plain_kernel_slots(int64_t n) { return plain_blocks(n) * kWpb; }
@@ -566,6 +802,37 @@ int launch_plain_bwd(cudaStream_t st, int64_t n, const float4* off, const uint32
   k_plain_bwd<<<plain_blocks(n), kWpb * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep,
                                                       (const PlainNet*)nets, d1, dT, ffix,
                                                       vir_part, status);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int plain_wgrad_params(int d1, int M) { return 2 * d1 + (d1 + 1) * 2 * d1 + (2 * d1 + 1) * M; }
+int plain_wgrad_ctas() {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return 4 * (sms > 0 ? sms : 1);
+}
+
+int launch_plain_wgrad(cudaStream_t st, int64_t n, const float4* off, const uint32_t* nlist,
+                       const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
+                       const void* nets, int d1, const float* dT, int ti, int tj, float* part,
+                       double* grad) {
+  if (n <= 0) return 0;
+  if (!plain_shape_ok(ep, d1)) return -1;
+  const int npar = plain_wgrad_params(d1, ep.M);
+  const size_t sm = (sizeof(PlainSmem) + 15) / 16 * 16 + sizeof(float) * (size_t)npar;
+  static std::atomic<size_t> set{0};  // launches from several host threads
+  if (sm > set) {
+    if (cudaFuncSetAttribute(k_plain_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        cudaSuccess)
+      return -3;
+    set = sm;
+  }
+  const int grid = plain_wgrad_ctas();
+  DP_LAUNCHED(2);
+  k_plain_wgrad<<<grid, 32, sm, st>>>(n, off, nlist, nn, cap, g, ep, (const PlainNet*)nets, d1, dT,
+                                      ti, tj, npar, part);
+  k_plain_wgrad_add<<<(npar + 255) / 256, 256, 0, st>>>(grid, npar, part, grad);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

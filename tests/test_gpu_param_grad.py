@@ -240,3 +240,51 @@ def test_param_grad_tanh_table(dp, cu_stress_path):
     PARITY_LOG.append(dict(case="param grad Cu 256 tanh table", dE=abs(E - E0),
                            fit_max_err_over_block_max=max(wf.values()),
                            table_max_err_over_max=max(wt.values())))
+
+
+def _emb_blocks(d1, M):
+    d2 = 2 * d1
+    return [("W0", 0, d1), ("b0", d1, d1), ("W1", 2 * d1, d1 * d2), ("b1", 2 * d1 + d1 * d2, d2),
+            ("W2", 2 * d1 + d1 * d2 + d2, d2 * M), ("b2", 2 * d1 + d1 * d2 + d2 + d2 * M, M)]
+
+
+@pytest.mark.parametrize("case", ["cu", "water"])
+def test_param_grad_untabulated(dp, cu_stress_path, water_model_path, case):
+    # the original embedding nets (tabulated = 0): dE/d(embedding weights and
+    # biases) per type pair on the plain path, and the fitting gradients
+    if case == "cu":
+        path, nt, rc, rcs, sel, spec = cu_stress_path, 1, CU_RC, CU_RCS, [CU_SEL], inputs.COPPER_SPEC
+        x, t, box = inputs.fcc_copper(4, sigma=0.05, seed=9)
+    else:
+        path, nt, rc, rcs, sel, spec = water_model_path, 2, 6.0, 0.5, [46, 92], inputs.WATER_SPEC
+        x, t, box = inputs.water_like(64, L=12.417, seed=3)
+    m = oracle.Model(path)
+    E0, gf0, ge0 = oracle.param_grad(m, None, rc, rcs, sel, x, t, box)
+    o = dp.dp_options_default()
+    o.tabulated = 0
+    h = dp.dp_create(path, nt, rc, rcs, sel, options=o, stream=None)
+    try:
+        E, gf, ge = dp.dp_param_grad(h, x, t, box)
+        fit, emb = dp.dp_get_params(h)
+    finally:
+        dp.dp_destroy(h)
+    npar = m.n_emb_params
+    assert ge.size == nt * nt * npar
+    # the handle's embedding parameters are the model's, in the same layout
+    for a in range(nt):
+        for b in range(nt):
+            assert np.array_equal(emb[(a * nt + b) * npar:(a * nt + b + 1) * npar], m.emb_params(a, b))
+    wf = _compare_fit(gf, gf0, m, spec.fit_w, f"{case} plain", 2e-5)
+    worst = 0.0
+    ge = ge.reshape(nt, nt, npar)
+    for a in range(nt):
+        for b in range(nt):
+            for name, o0, cnt in _emb_blocks(spec.emb_w[0], spec.emb_w[-1]):
+                u, v = ge[a, b, o0:o0 + cnt], ge0[a, b, o0:o0 + cnt]
+                scale = float(np.abs(v).max())
+                err = float(np.abs(u - v).max())
+                worst = max(worst, err / max(scale, 1e-300))
+                assert err <= 2e-5 * scale + 1e-12, (case, a, b, name, err, scale)
+    PARITY_LOG.append(dict(case=f"param grad {case} untabulated", dE=abs(E - E0),
+                           fit_max_err_over_block_max=max(wf.values()),
+                           emb_max_err_over_block_max=worst))
