@@ -151,9 +151,9 @@ dp_status dp_system_create(dp_handle* h, int64_t natoms, const double* x, const 
  * arrays).  dp_md_step then advances all of them (one launch of each kernel;
  * each system keeps its own box, cells and neighbor list, rebuilt on the
  * common schedule), dp_system_get returns the concatenated arrays.  Each
- * system's trajectory is bitwise the one it has alone.  Needs tabulated = 1
- * and embed_precision = 2; no thermo output and no state file (both
- * DP_ERR_UNIMPLEMENTED). */
+ * system's trajectory is bitwise the one it has alone, and so are its thermo
+ * records (dp_md_step writes [nsteps][nsys] of them).  Needs tabulated = 1
+ * and embed_precision = 2; no state file (DP_ERR_UNIMPLEMENTED). */
 dp_status dp_system_create_batch(dp_handle* h, int nsys, const int64_t* natoms, const double* x,
                                  const double* v, const int32_t* types,
                                  const double* mass_of_type, const double* boxes,
@@ -172,13 +172,19 @@ dp_status dp_system_get(dp_system* s, double* x, double* v, double* f, int devic
 /* Current step count of the system. */
 int64_t dp_system_step(const dp_system* s);
 
+/* Number of systems of a system made by dp_system_create_batch; 0 for one
+ * made by dp_system_create or dp_state_load. */
+int dp_system_batch_size(const dp_system* s);
+
 /*
  * dp_md_step -- nsteps velocity-Verlet steps of dt_fs (Sec. 4):
  *   v += dt/2 F/m;  x += dt v;  (list rebuild when step % rebuild_every == 0);
  *   F = -grad E;  v += dt/2 F/m.
  * The rebuild schedule is keyed to the absolute step count, so a run split
  * into several calls (or saved and loaded) follows the same schedule.
- * thermo_out: NULL, or [nsteps] records (one per step, after the step).
+ * thermo_out: NULL, or [nsteps] records (one per step, after the step);
+ *   for a batch system [nsteps][nsys], one per system (its own atoms, 3N-3
+ *   degrees of freedom, box volume and virial).
  * Errors: as dp_compute, plus DP_ERR_SKIN.
  */
 dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_thermo* thermo_out);
@@ -268,11 +274,14 @@ dp_status dp_param_grad(dp_handle* h, int64_t natoms, const double* coords,
  * values; an untabulated handle's embedding nets come back as loaded. */
 dp_status dp_get_params(dp_handle* h, double* fit, double* table);
 
-/* Replace the fitting parameters and/or the table coefficients (either
- * pointer may be NULL), e.g. after a gradient step; they are rounded to FP32
- * and every derived device copy (transposes, BF16 pieces, tiled table
- * operands) is rebuilt.  Synchronous.  A table on an untabulated handle (its
- * embedding nets cannot be replaced) is DP_ERR_ARG. */
+/* Replace the fitting parameters and/or the embedding representation
+ * (either pointer may be NULL), e.g. after a gradient step, in the layouts of
+ * dp_param_grad: the table coefficients of a tabulated handle, the embedding
+ * nets' weights and biases of an untabulated one.  Values are rounded to FP32
+ * for the device copies and every derived copy (transposes, BF16 pieces,
+ * tiled table operands; for new embedding nets the FP32 nets and the
+ * handle's table, which dp_table_coeffs then returns) is rebuilt.
+ * Synchronous. */
 dp_status dp_set_params(dp_handle* h, const double* fit, const double* table);
 
 /* ---------------------------------------------------------------------------

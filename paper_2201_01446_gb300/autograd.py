@@ -73,11 +73,12 @@ def _host(a, dtype):
 
 def energy_params(handle, fit: torch.Tensor, table, x, types, box):
     """E (0-dim FP64 CPU tensor) as a differentiable function of the fitting
-    parameters fit [n_fit] and (tabulated tensor-core embedding only) the
-    table coefficients table [n_table] or None; both CPU float64 tensors in
-    the layouts of dp_param_grad.  x [N, 3], types [N], box [3, 3]: host
-    arrays or tensors (copied to the host).  The handle keeps the given
-    parameters afterwards."""
+    parameters fit [n_fit] and the embedding representation table [n_table]
+    or None (the table coefficients of a tabulated tensor-core handle, the
+    embedding nets' weights and biases of an untabulated one); both CPU
+    float64 tensors in the layouts of dp_param_grad.  x [N, 3], types [N],
+    box [3, 3]: host arrays or tensors (copied to the host).  The handle
+    keeps the given parameters afterwards."""
     if fit.dtype != torch.float64 or (table is not None and table.dtype != torch.float64):
         raise ValueError("parameters must be float64 tensors")
     return _EnergyParams.apply(fit, table, handle, _host(x, np.float64), _host(types, np.int32),

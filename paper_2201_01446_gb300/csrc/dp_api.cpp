@@ -925,51 +925,85 @@ dp_status evaluate_batch(dp_handle* h, Work& w, Batch& b) {
   return DP_OK;
 }
 
-// per-system energies and virials, each bitwise the one dp_compute makes for
-// the system alone: its atoms' energies (segments of e_atom) and, per centre
-// type, its tiles' virial rows (segments of vir_tile), added in type order
-dp_status batch_sums(dp_handle* h, Work& w, Batch& b, double* energies, double* virials) {
+// Per-system sums of a batch, each bitwise the one the system has alone: its
+// atoms' energies (segments of e_atom; of the kinetic terms likewise) and,
+// per centre type, its tiles' virial rows (segments of vir_tile), added in
+// type order.  The segment table (rows of each segment, then its first row:
+// systems, then (system, type) tile ranges) goes to w.seg; *nvseg is the
+// number of tile ranges.
+static dp_status batch_seg_upload(dp_handle* h, Work& w, const Batch& b, int* nvseg) {
   const int nsys = b.nsys;
-  const int64_t n = w.n;
-  std::vector<int64_t> seg;  // [rows..., offsets...]: systems, then (system, type) ranges
-  int nvseg = 0;
+  std::vector<int64_t> seg;
+  int nv = 0;
   for (int q = 0; q < nsys; ++q) seg.push_back(b.base[q + 1] - b.base[q]);
   for (int q = 0; q < nsys; ++q)
-    for (auto& r : b.sys_tiles[q]) seg.push_back(r.second), ++nvseg;
+    for (auto& r : b.sys_tiles[q]) seg.push_back(r.second), ++nv;
   for (int q = 0; q < nsys; ++q) seg.push_back(b.base[q]);
   for (int q = 0; q < nsys; ++q)
     for (auto& r : b.sys_tiles[q]) seg.push_back(r.first);
-  const int nseg = nsys + nvseg;
-  std::vector<double> out((size_t)nsys + 9 * (size_t)nvseg, 0.0);
-  if (n > 0) {
-    CK(ensure(w.seg, seg.size() * sizeof(int64_t)), "alloc sums");
-    CK(ensure(w.seg_part, (size_t)std::max<int64_t>(sum_rows_seg_part_size(nsys, 1),
-                                                     sum_rows_seg_part_size(nvseg, 9)) *
-                              sizeof(double)),
-       "alloc sums");
-    CK(ensure(w.seg_out, out.size() * sizeof(double)), "alloc sums");
+  *nvseg = nv;
+  CK(ensure(w.seg, std::max<size_t>(seg.size(), 1) * sizeof(int64_t)), "alloc sums");
+  CK(ensure(w.seg_part, (size_t)std::max<int64_t>(sum_rows_seg_part_size(nsys, 1),
+                                                   sum_rows_seg_part_size(nv, 9)) *
+                            sizeof(double)),
+     "alloc sums");
+  if (!seg.empty())
     CK(cudaMemcpyAsync(w.seg.p, seg.data(), seg.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                        h->st),
        "sums upload");
-    const int64_t* rows = P<int64_t>(w.seg);
-    const int64_t* offs = rows + nseg;
-    launch_sum_rows_seg(h->st, nsys, rows, offs, 1, P<double>(w.e_atom), P<double>(w.seg_part),
-                        P<double>(w.seg_out));
-    launch_sum_rows_seg(h->st, nvseg, rows + nsys, offs + nsys, 9, P<double>(w.vir_tile),
-                        P<double>(w.seg_part), P<double>(w.seg_out) + nsys);
+  return DP_OK;
+}
+
+// doubles of one record of batch_seg_launch: [nsys] energies, [nvseg][9]
+// virial rows, then (with kinetic terms) [nsys] kinetic sums
+static size_t batch_seg_len(const Batch& b, int nvseg, bool ke) {
+  return (size_t)b.nsys * (ke ? 2 : 1) + 9 * (size_t)nvseg;
+}
+
+// the sums of batch_seg_upload's table into out (device, batch_seg_len)
+static void batch_seg_launch(dp_handle* h, Work& w, const Batch& b, int nvseg,
+                             const double* ke, double* out) {
+  const int nsys = b.nsys;
+  const int64_t* rows = P<int64_t>(w.seg);
+  const int64_t* offs = rows + nsys + nvseg;
+  launch_sum_rows_seg(h->st, nsys, rows, offs, 1, P<double>(w.e_atom), P<double>(w.seg_part),
+                      out);
+  launch_sum_rows_seg(h->st, nvseg, rows + nsys, offs + nsys, 9, P<double>(w.vir_tile),
+                      P<double>(w.seg_part), out + nsys);
+  if (ke)
+    launch_sum_rows_seg(h->st, nsys, rows, offs, 1, ke, P<double>(w.seg_part),
+                        out + nsys + 9 * (size_t)nvseg);
+}
+
+// system q's virial from a record of batch_seg_launch: its tile ranges'
+// rows added in order from zero (the order of launch_add_rows)
+static void batch_seg_virial(const Batch& b, const double* rec, int q, double* v) {
+  size_t vk = 0;
+  for (int p = 0; p < q; ++p) vk += b.sys_tiles[p].size();
+  for (int a = 0; a < 9; ++a) v[a] = 0.0;
+  for (size_t r = 0; r < b.sys_tiles[q].size(); ++r, ++vk)
+    for (int a = 0; a < 9; ++a) v[a] += rec[b.nsys + 9 * vk + a];
+}
+
+dp_status batch_sums(dp_handle* h, Work& w, Batch& b, double* energies, double* virials) {
+  const int nsys = b.nsys;
+  int nvseg = 0;
+  std::vector<double> out(batch_seg_len(b, 0, false), 0.0);
+  if (w.n > 0) {
+    CKS(batch_seg_upload(h, w, b, &nvseg));
+    out.assign(batch_seg_len(b, nvseg, false), 0.0);
+    CK(ensure(w.seg_out, out.size() * sizeof(double)), "alloc sums");
+    batch_seg_launch(h, w, b, nvseg, nullptr, P<double>(w.seg_out));
     CK(cudaGetLastError(), "sum kernels");
     CK(cudaMemcpyAsync(out.data(), w.seg_out.p, out.size() * sizeof(double),
                        cudaMemcpyDeviceToHost, h->st),
        "energy copy");
     CK(cudaStreamSynchronize(h->st), "energy copy");
   }
-  int vk = 0;
   for (int q = 0; q < nsys; ++q) {
     energies[q] = out[q];
-    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // the order of launch_add_rows
-    for (size_t r = 0; r < b.sys_tiles[q].size(); ++r, ++vk)
-      for (int a = 0; a < 9; ++a) v[a] += out[nsys + 9 * (size_t)vk + a];
-    for (int a = 0; a < 9; ++a) virials[9 * q + a] = v[a];
+    if (w.n > 0) batch_seg_virial(b, out.data(), q, virials + 9 * q);
+    else for (int a = 0; a < 9; ++a) virials[9 * q + a] = 0.0;
   }
   return DP_OK;
 }
@@ -983,6 +1017,69 @@ dp_status check_handle(dp_handle* h) {
 
 // BF16 pieces of every fitting weight (W^T and W, pre-tiled B operands of the
 // tensor-core fitting) from the FP32 copies in fit32
+// The plain path's FP32 embedding weights, from the embedding nets' FP64
+// parameters in the model file's layout (per (centre, neighbor) type pair,
+// per layer W then b, contiguous): every sub-array padded to a 16-byte
+// boundary (the kernels read float4), plus the transposes the backward
+// reads, and one device record per pair pointing into them.
+static dp_status upload_plain_nets(dp_handle* h, const double* emb) {
+  const int d1 = h->emb_w[0], d2 = h->emb_w[1], Me = h->emb_w[2];
+  const int np = h->ntypes * h->ntypes;
+  auto pad4 = [](size_t v) { return (v + 3) & ~(size_t)3; };
+  const size_t oW0 = 0, ob0 = pad4(d1), oW1 = ob0 + pad4(d1), ob1 = oW1 + pad4((size_t)d1 * d2),
+               oW2 = ob1 + pad4(d2), ob2 = oW2 + pad4((size_t)d2 * Me),
+               oW1T = ob2 + pad4(Me), oW2T = oW1T + pad4((size_t)d1 * d2),
+               per = oW2T + pad4((size_t)d2 * Me);
+  const size_t pair_doubles = (size_t)plain_wgrad_params(d1, Me);
+  std::vector<float> pw((size_t)np * per, 0.0f);
+  for (int p = 0; p < np; ++p) {
+    float* q = pw.data() + (size_t)p * per;
+    const double* W0 = emb + (size_t)p * pair_doubles;  // W0[d1], b0[d1]
+    const double* W1 = W0 + 2 * d1;                     // W1[d1][d2], b1[d2]
+    const double* W2 = W1 + (size_t)(d1 + 1) * d2;      // W2[d2][Me], b2[Me]
+    for (int k = 0; k < d1; ++k) {
+      q[oW0 + k] = (float)W0[k];
+      q[ob0 + k] = (float)W0[d1 + k];
+    }
+    for (size_t k = 0; k < (size_t)d1 * d2; ++k) q[oW1 + k] = (float)W1[k];
+    for (int k = 0; k < d2; ++k) q[ob1 + k] = (float)W1[(size_t)d1 * d2 + k];
+    for (size_t k = 0; k < (size_t)d2 * Me; ++k) q[oW2 + k] = (float)W2[k];
+    for (int k = 0; k < Me; ++k) q[ob2 + k] = (float)W2[(size_t)d2 * Me + k];
+    for (int mm = 0; mm < d2; ++mm)
+      for (int k = 0; k < d1; ++k) q[oW1T + (size_t)mm * d1 + k] = (float)W1[(size_t)k * d2 + mm];
+    for (int c = 0; c < Me; ++c)
+      for (int l = 0; l < d2; ++l) q[oW2T + (size_t)c * d2 + l] = (float)W2[(size_t)l * Me + c];
+  }
+  const size_t rb = plain_net_bytes();
+  std::vector<unsigned char> recs((size_t)np * rb);
+  if (ensure(h->plain_w, sizeof(float) * pw.size()) != cudaSuccess ||
+      cudaMemcpyAsync(h->plain_w.p, pw.data(), sizeof(float) * pw.size(), cudaMemcpyHostToDevice,
+                      h->st) != cudaSuccess) {
+    h->err = "device allocation failed";
+    cudaGetLastError();
+    return DP_ERR_OOM;
+  }
+  const float* dpw = P<float>(h->plain_w);
+  for (int p = 0; p < np; ++p) {
+    const float* b = dpw + (size_t)p * per;
+    if (!plain_net_fill(recs.data() + (size_t)p * rb, b + oW0, b + ob0, b + oW1, b + ob1,
+                        b + oW2, b + ob2, b + oW1T, b + oW2T) ||
+        Me % 4) {
+      h->err = "plain embedding weights are not 16-byte aligned";
+      return DP_ERR_UNIMPLEMENTED;
+    }
+  }
+  if (ensure(h->plain_nets, recs.size()) != cudaSuccess ||
+      cudaMemcpyAsync(h->plain_nets.p, recs.data(), recs.size(), cudaMemcpyHostToDevice,
+                      h->st) != cudaSuccess ||
+      cudaStreamSynchronize(h->st) != cudaSuccess) {
+    h->err = "device allocation failed";
+    cudaGetLastError();
+    return DP_ERR_OOM;
+  }
+  return DP_OK;
+}
+
 void tile_fit_weights(dp_handle* h) {
   const float* fb = P<float>(h->fit32);
   __nv_bfloat16* hb = P<__nv_bfloat16>(h->fit_bf16);
@@ -1219,54 +1316,8 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
   }
   // FP32 embedding weights (and transposes) for the plain untabulated path
   if (m.n_emb == 3 && m.emb_w[0] <= 32) {
-    const int d1 = m.emb_w[0], d2 = m.emb_w[1], Me = m.emb_w[2];
-    // every sub-array starts on a 16-byte boundary (the kernels read float4)
-    auto pad4 = [](size_t v) { return (v + 3) & ~(size_t)3; };
-    const size_t oW0 = 0, ob0 = pad4(d1), oW1 = ob0 + pad4(d1), ob1 = oW1 + pad4((size_t)d1 * d2),
-                 oW2 = ob1 + pad4(d2), ob2 = oW2 + pad4((size_t)d2 * Me),
-                 oW1T = ob2 + pad4(Me), oW2T = oW1T + pad4((size_t)d1 * d2),
-                 per = oW2T + pad4((size_t)d2 * Me);
-    std::vector<float> pw((size_t)np * per, 0.0f);
-    for (int p = 0; p < np; ++p) {
-      float* q = pw.data() + (size_t)p * per;
-      const double* W0 = m.data.data() + m.emb_off[p * 3 + 0];  // W0[d1], b0[d1]
-      const double* W1 = m.data.data() + m.emb_off[p * 3 + 1];  // W1[d1][d2], b1[d2]
-      const double* W2 = m.data.data() + m.emb_off[p * 3 + 2];  // W2[d2][Me], b2[Me]
-      for (int k = 0; k < d1; ++k) {
-        q[oW0 + k] = (float)W0[k];
-        q[ob0 + k] = (float)W0[d1 + k];
-      }
-      for (size_t k = 0; k < (size_t)d1 * d2; ++k) q[oW1 + k] = (float)W1[k];
-      for (int k = 0; k < d2; ++k) q[ob1 + k] = (float)W1[(size_t)d1 * d2 + k];
-      for (size_t k = 0; k < (size_t)d2 * Me; ++k) q[oW2 + k] = (float)W2[k];
-      for (int k = 0; k < Me; ++k) q[ob2 + k] = (float)W2[(size_t)d2 * Me + k];
-      for (int mm = 0; mm < d2; ++mm)
-        for (int k = 0; k < d1; ++k) q[oW1T + (size_t)mm * d1 + k] = (float)W1[(size_t)k * d2 + mm];
-      for (int c = 0; c < Me; ++c)
-        for (int l = 0; l < d2; ++l) q[oW2T + (size_t)c * d2 + l] = (float)W2[(size_t)l * Me + c];
-    }
-    const size_t rb = plain_net_bytes();
-    std::vector<unsigned char> recs((size_t)np * rb);
-    if (!up(h->plain_w, pw.data(), sizeof(float) * pw.size())) {
-      h->err = "device allocation failed";
-      cudaGetLastError();
-      return bail(DP_ERR_OOM);
-    }
-    const float* dpw = P<float>(h->plain_w);
-    for (int p = 0; p < np; ++p) {
-      const float* b = dpw + (size_t)p * per;
-      if (!plain_net_fill(recs.data() + (size_t)p * rb, b + oW0, b + ob0, b + oW1, b + ob1,
-                          b + oW2, b + ob2, b + oW1T, b + oW2T) ||
-          Me % 4) {
-        h->err = "plain embedding weights are not 16-byte aligned";
-        return bail(DP_ERR_UNIMPLEMENTED);
-      }
-    }
-    if (!up(h->plain_nets, recs.data(), recs.size())) {
-      h->err = "device allocation failed";
-      cudaGetLastError();
-      return bail(DP_ERR_OOM);
-    }
+    const dp_status st = upload_plain_nets(h, m.data.data());
+    if (st != DP_OK) return bail(st);
   } else if (h->opt.tabulated == 0) {
     h->err = "the plain path needs three doubling embedding layers with d1 <= 32";
     return bail(DP_ERR_UNIMPLEMENTED);
@@ -1683,7 +1734,6 @@ dp_status dp_get_params(dp_handle* h, double* fit, double* table) {
 
 dp_status dp_set_params(dp_handle* h, const double* fit, const double* table) {
   CKS(check_handle(h));
-  if (table && !h->opt.tabulated) return fail(h, DP_ERR_ARG, "the untabulated path has no table");
   // captured MD graphs hold the output bias by value: capture them again
   g_alloc_gen.fetch_add(1);
   if (fit) {
@@ -1721,7 +1771,18 @@ dp_status dp_set_params(dp_handle* h, const double* fit, const double* table) {
     tile_fit_weights(h);
     CK(cudaStreamSynchronize(h->st), "parameter upload");
   }
-  if (table) {
+  if (table && !h->opt.tabulated) {
+    // the embedding nets (FP64, the file's layout): the plain path's FP32
+    // weights, and the handle's table built from them, follow
+    CK(cudaMemcpyAsync(h->emb64.p, table, sizeof(double) * (size_t)emb_repr_params(h),
+                       cudaMemcpyHostToDevice, h->st),
+       "embedding upload");
+    CKS(upload_plain_nets(h, table));
+    if (table_build(h->st, P<double>(h->emb64), P<int64_t>(h->emb_off), h->n_emb, h->emb_w,
+                    h->ntypes * h->ntypes, h->h, h->n_int, P<float>(h->table)) != 0)
+      return fail(h, DP_ERR_CUDA, "table build failed");
+    CK(cudaStreamSynchronize(h->st), "embedding upload");
+  } else if (table) {
     const size_t n = (size_t)h->ntypes * h->ntypes * h->n_int * 6 * h->M;
     std::vector<float> tb(n);
     for (size_t q = 0; q < n; ++q) tb[q] = (float)table[q];
@@ -1884,6 +1945,8 @@ void dp_system_destroy(dp_system* s) {
 
 int64_t dp_system_step(const dp_system* s) { return s ? s->step : -1; }
 
+int dp_system_batch_size(const dp_system* s) { return s && s->batch ? s->batch->nsys : 0; }
+
 dp_status dp_system_get(dp_system* s, double* x, double* v, double* f, int device_ptrs) {
   if (!s) return DP_ERR_ARG;
   dp_handle* h = s->h;
@@ -1905,12 +1968,17 @@ dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_th
   Work& w = s->w;
   const int64_t n = w.n;
   Batch* bt = s->batch.get();  // several systems: their own boxes and lists
-  if (bt && thermo) return fail(h, DP_ERR_UNIMPLEMENTED, "thermo output of several systems");
   double L[3] = {0.0, 0.0, 0.0};
   if (!bt) CKS(box_lengths(h, s->box, L));
   const double half_skin2 = 0.25 * h->opt.skin * h->opt.skin;
   const double vol = L[0] * L[1] * L[2];
-  if (thermo) CK(ensure(s->thermo, sizeof(double) * 16 * std::max(nsteps, 1)), "alloc thermo");
+  // one thermo record per step: [KE, PE, virial] of the system, or the
+  // per-system sums of batch_seg_launch
+  int nvseg = 0;
+  if (thermo && bt && n > 0) CKS(batch_seg_upload(h, w, *bt, &nvseg));
+  const size_t rec_len = bt ? batch_seg_len(*bt, nvseg, true) : 16;
+  if (thermo)
+    CK(ensure(s->thermo, sizeof(double) * rec_len * std::max(nsteps, 1)), "alloc thermo");
   CKS(clear_status(h));
   // the launches of a step without a rebuild (kick + drift, FP32 mirror,
   // evaluation, kick); no host synchronisation inside
@@ -2024,7 +2092,10 @@ dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_th
     launch_kick(h->st, n, P<double>(s->v), P<double>(w.f), P<int32_t>(w.types),
                 P<double>(s->inv_mass_acc), P<double>(s->mass), dt_fs,
                 thermo ? P<double>(w.ke) : nullptr);
-    if (thermo) {
+    if (thermo && bt) {
+      if (n > 0)
+        batch_seg_launch(h, w, *bt, nvseg, P<double>(w.ke), P<double>(s->thermo) + rec_len * k);
+    } else if (thermo) {
       double* rec = P<double>(s->thermo) + 16 * k;
       launch_sum_rows(h->st, n, 1, P<double>(w.ke), P<double>(w.red_part), rec);
       CK(cudaMemcpyAsync(rec + 1, w.red_out.p, sizeof(double) * 10, cudaMemcpyDeviceToDevice,
@@ -2036,7 +2107,30 @@ dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_th
   CK(cudaGetLastError(), "md kernels");
   CKS(read_status(h));
   CKS(status_errors(h));
-  if (thermo && nsteps > 0) {
+  if (thermo && bt && nsteps > 0) {
+    const int nsys = bt->nsys;
+    std::vector<double> rec(rec_len * nsteps, 0.0);
+    if (n > 0)
+      CK(cudaMemcpy(rec.data(), s->thermo.p, sizeof(double) * rec.size(),
+                    cudaMemcpyDeviceToHost),
+         "thermo copy");
+    for (int k = 0; k < nsteps; ++k) {
+      const double* r = rec.data() + rec_len * k;
+      for (int q = 0; q < nsys; ++q) {
+        dp_thermo& t = thermo[(size_t)k * nsys + q];
+        const int64_t dof = 3 * (bt->base[q + 1] - bt->base[q]) - 3;
+        const double vq = bt->L[q][0] * bt->L[q][1] * bt->L[q][2];
+        t.step = s->step - nsteps + k + 1;
+        t.kinetic = r[nsys + 9 * (size_t)nvseg + q] / kAcc;
+        t.potential = r[q];
+        if (n > 0) batch_seg_virial(*bt, r, q, t.virial);
+        else for (int a = 0; a < 9; ++a) t.virial[a] = 0.0;
+        t.temperature = dof > 0 ? 2.0 * t.kinetic / (dof * kKb) : 0.0;
+        t.pressure =
+            (2.0 * t.kinetic + t.virial[0] + t.virial[4] + t.virial[8]) / (3.0 * vq) * kEvA3Bar;
+      }
+    }
+  } else if (thermo && nsteps > 0) {
     std::vector<double> rec((size_t)16 * nsteps);
     CK(cudaMemcpy(rec.data(), s->thermo.p, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost),
        "thermo copy");

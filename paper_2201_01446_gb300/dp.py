@@ -47,7 +47,7 @@ EXPORTS = ["dp_options_default", "dp_create", "dp_destroy", "dp_last_error", "dp
            "dp_neighbor_pairs", "dp_table_coeffs", "dp_descriptor", "dp_version",
            "dp_profile", "dp_profile_read", "dp_stats", "dp_neighbor_pairs_static", "dp_fitting",
            "dp_param_sizes", "dp_param_grad", "dp_get_params", "dp_set_params", "dp_compute_batch",
-           "dp_system_create_batch"]
+           "dp_system_create_batch", "dp_system_batch_size"]
 
 DP_NPHASE = 5
 PHASES = ["neighbor_build", "embed_contract_fwd", "fitting", "embed_contract_bwd_forces",
@@ -92,6 +92,7 @@ def _load():
         "dp_compute_batch": (i, [vp, i, vp, vp, vp, vp, vp, vp, vp]),
         "dp_system_create_batch": (i, [vp, i, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]),
         "dp_set_params": (i, [vp, vp, vp]),
+        "dp_system_batch_size": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -266,12 +267,16 @@ def dp_system_get(h, s, n, x=True, v=True, f=True, out=None):
 
 
 def dp_md_step(h, s, nsteps, dt_fs, thermo=False):
-    th = (dp_thermo * max(nsteps, 1))() if thermo else None
+    """nsteps velocity-Verlet steps; with thermo, the records (step, KE, PE,
+    T, P) as [nsteps, 5], or [nsteps, nsys, 5] for a batch system."""
+    nsys = int(lib.dp_system_batch_size(s))
+    th = (dp_thermo * (max(nsteps, 1) * max(nsys, 1)))() if thermo else None
     _check(lib.dp_md_step(h, s, int(nsteps), float(dt_fs), th), h)
     if not thermo:
         return None
-    return np.array([(t.step, t.kinetic, t.potential, t.temperature, t.pressure)
-                     for t in th[:nsteps]])
+    rec = np.array([(t.step, t.kinetic, t.potential, t.temperature, t.pressure)
+                    for t in th[:nsteps * max(nsys, 1)]]).reshape(-1, 5)
+    return rec.reshape(nsteps, nsys, 5) if nsys else rec
 
 
 def dp_state_save(h, s, path):
@@ -415,7 +420,8 @@ def dp_get_params(h):
 
 
 def dp_set_params(h, fit=None, table=None):
-    """Replace the fitting parameters and/or the table coefficients."""
+    """Replace the fitting parameters and/or the embedding representation
+    (table coefficients, or an untabulated handle's embedding nets)."""
     nf, nt = dp_param_sizes(h)
     f = np.ascontiguousarray(fit, np.float64).ravel() if fit is not None else None
     t = np.ascontiguousarray(table, np.float64).ravel() if table is not None else None

@@ -82,7 +82,8 @@ def test_batch_needs_tensor_core_embedding(dp, cu_model_path):
 
 def test_batch_md_matches_alone(dp, cu_stress_path):
     # several systems advanced as one (list rebuilds at steps 10 and 20, plain
-    # steps replayed as a graph): each trajectory bitwise the one it has alone
+    # steps replayed as a graph, then steps with thermo records): each
+    # trajectory and each system's records bitwise those it has alone
     h = _tc(dp, cu_stress_path)
     try:
         sys3 = []
@@ -92,25 +93,28 @@ def test_batch_md_matches_alone(dp, cu_stress_path):
             sys3.append((x, v, t, box))
         sb = dp.dp_system_create_batch(h, sys3, [inputs.MASS_CU])
         try:
-            dp.dp_md_step(h, sb, 23, 1.0)
+            assert dp.lib.dp_system_batch_size(sb) == 3
+            dp.dp_md_step(h, sb, 20, 1.0)
+            thb = dp.dp_md_step(h, sb, 3, 1.0, thermo=True)
             n = sum(len(s[0]) for s in sys3)
             xb, vb, fb = dp.dp_system_get(h, sb, n)
-            with pytest.raises(dp.DPError) as e:
-                dp.dp_md_step(h, sb, 1, 1.0, thermo=True)
-            assert e.value.code == 9
         finally:
             dp.dp_system_destroy(sb)
+        assert thb.shape == (3, 3, 5)
         o = 0
-        for x, v, t, box in sys3:
+        for q, (x, v, t, box) in enumerate(sys3):
             s = dp.dp_system_create(h, x, v, t, [inputs.MASS_CU], box)
             try:
-                dp.dp_md_step(h, s, 23, 1.0)
+                assert dp.lib.dp_system_batch_size(s) == 0
+                dp.dp_md_step(h, s, 20, 1.0)
+                tha = dp.dp_md_step(h, s, 3, 1.0, thermo=True)
                 xa, va, fa = dp.dp_system_get(h, s, len(x))
             finally:
                 dp.dp_system_destroy(s)
             m = len(x)
             assert np.array_equal(xb[o:o + m], xa) and np.array_equal(vb[o:o + m], va)
             assert np.array_equal(fb[o:o + m], fa)
+            assert np.array_equal(thb[:, q], tha), (q, thb[:, q], tha)
             o += m
     finally:
         dp.dp_destroy(h)

@@ -288,3 +288,44 @@ def test_param_grad_untabulated(dp, cu_stress_path, water_model_path, case):
     PARITY_LOG.append(dict(case=f"param grad {case} untabulated", dE=abs(E - E0),
                            fit_max_err_over_block_max=max(wf.values()),
                            emb_max_err_over_block_max=worst))
+
+
+def test_set_params_untabulated_embedding_nets(dp, water_model_path):
+    # new embedding nets on an untabulated handle: energy and forces follow
+    # the oracle's original model with the same nets; the handle returns
+    # them as given; a torch step on them matches dp_param_grad
+    torch = pytest.importorskip("torch")
+    from paper_2201_01446_gb300 import autograd
+    m = oracle.Model(water_model_path)
+    x, t, box = inputs.water_like(64, L=12.417, seed=7)
+    o = dp.dp_options_default()
+    o.tabulated = 0
+    h = dp.dp_create(water_model_path, 2, 6.0, 0.5, [46, 92], options=o, stream=None)
+    npar = m.n_emb_params
+    try:
+        fit0, emb0 = dp.dp_get_params(h)
+        rng = np.random.default_rng(4)
+        emb = emb0 * (1.0 + 0.05 * rng.standard_normal(emb0.size))
+        dp.dp_set_params(h, None, emb)
+        _, emb1 = dp.dp_get_params(h)
+        assert np.array_equal(emb1, emb)
+        E, F, V, _ = dp.dp_compute(h, x, t, box)
+        for a in range(2):
+            for b in range(2):
+                q = a * 2 + b
+                m.set_emb_params(a, b, emb[q * npar:(q + 1) * npar])
+        r = oracle.evaluate(m, None, 6.0, 0.5, [46, 92], x, t, box)
+        frms = float(np.sqrt((r["force"] ** 2).mean()))
+        assert abs(E - r["energy"]) / len(x) < max(1e-6, 2e-6 * float(np.abs(r["atom_energy"]).mean()))
+        assert float(np.sqrt(((F - r["force"]) ** 2).mean())) < max(1e-5, 3e-5 * frms)
+        assert np.abs(V - r["virial"]).max() < 1e-4 * np.abs(r["virial"]).max() + 1e-9
+        # the energy as a torch function of the embedding nets
+        pe = torch.tensor(emb, requires_grad=True)
+        Et = autograd.energy_params(h, torch.tensor(fit0), pe, x, t, box)
+        Et.backward()
+        E2, _, ge = dp.dp_param_grad(h, x, t, box)
+        assert float(Et.detach()) == E2 and np.array_equal(pe.grad.numpy(), ge)
+        PARITY_LOG.append(dict(case="set embedding nets, water 192 untabulated",
+                               dE_per_atom=abs(E - r["energy"]) / len(x)))
+    finally:
+        dp.dp_destroy(h)
