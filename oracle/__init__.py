@@ -56,6 +56,8 @@ def lib():
             "orc_set_tanh_table": (None, [i]),
             "orc_act": (d, [d, dp]),
             "orc_table_build": (p, [p, d, d]),
+            "orc_table_build_ext": (p, [p, d, d, d, i]),
+            "orc_table_ext": (i, [p, i32p, dp]),
             "orc_table_free": (None, [p]),
             "orc_table_dims": (i, [p, i32p, dp]),
             "orc_table_coeffs": (i, [p, i, i, dp]),
@@ -200,15 +202,32 @@ class Model:
 
 
 class Table:
-    def __init__(self, model: Model, h: float, s_max: float):
+    """Sec. 3.2 table of the model's embedding nets: intervals of width h up
+    to s_max, and (s_ext > s_max) an extrapolation region of intervals of
+    width ext_stride * h up to s_ext."""
+
+    def __init__(self, model: Model, h: float, s_max: float, s_ext: float = 0.0,
+                 ext_stride: int = 10):
         self.model = model
-        self.h_ptr = lib().orc_table_build(model.h, float(h), float(s_max))
+        self.h_ptr = lib().orc_table_build_ext(model.h, float(h), float(s_max), float(s_ext),
+                                               int(ext_stride))
         if not self.h_ptr:
             raise OracleError(1, "table build")
         n = np.zeros(1, np.int32)
         hh = np.zeros(1)
         lib().orc_table_dims(self.h_ptr, _i32(n), _d(hh))
         self.n, self.h = int(n[0]), float(hh[0])
+        lib().orc_table_ext(self.h_ptr, _i32(n), _d(hh))
+        self.n_fine, self.H = int(n[0]), float(hh[0])
+
+    def widths(self):
+        """[n] interval widths (h, then H in the extrapolation region)."""
+        return np.where(np.arange(self.n) < self.n_fine, self.h, self.H)
+
+    def nodes(self):
+        """[n + 1] node positions."""
+        k = np.arange(self.n + 1)
+        return np.where(k <= self.n_fine, k * self.h, self.n_fine * self.h + (k - self.n_fine) * self.H)
 
     @property
     def handle(self):

@@ -33,8 +33,36 @@ struct orc_model {
 struct orc_table {
   int ntypes, M, n;
   double h;
-  double* a; /* [ntypes*ntypes][n][6][M] */
+  int n_fine; /* intervals of width h on [0, n_fine h]; the rest, up to n, */
+  double H;   /* of width H (the extrapolation region; n_fine = n without) */
+  double* a;  /* [ntypes*ntypes][n][6][M] */
 };
+
+/* node k of the table: k h in the first region, n_fine h + (k - n_fine) H
+ * beyond it */
+static double tab_node(const orc_table* t, int k) {
+  return k <= t->n_fine ? k * t->h : t->n_fine * t->h + (k - t->n_fine) * t->H;
+}
+
+static double tab_width(const orc_table* t, int k) { return k < t->n_fine ? t->h : t->H; }
+
+/* interval k owning s (interval k is [x_k, x_{k+1}), clamped to the table)
+ * and the local variable s - x_k */
+static double tab_locate(const orc_table* t, double s, int* k_out) {
+  const double s_fine = t->n_fine * t->h;
+  double fk;
+  int k;
+  if (s < s_fine || t->n == t->n_fine) {
+    fk = floor(s / t->h);
+    k = fk < 0 ? 0 : (fk > t->n_fine - 1 ? t->n_fine - 1 : (int)fk);
+  } else {
+    fk = floor((s - s_fine) / t->H);
+    const int last = t->n - t->n_fine - 1;
+    k = t->n_fine + (fk < 0 ? 0 : (fk > last ? last : (int)fk));
+  }
+  *k_out = k;
+  return s - tab_node(t, k);
+}
 
 void orc_set_threads(int nthreads) {
 #ifdef _OPENMP
@@ -393,15 +421,26 @@ void orc_hermite5(const double* y0, const double* y1, double h, double* a) {
 }
 
 orc_table* orc_table_build(const orc_model* m, double h, double s_max) {
-  if (!m || !(h > 0) || !(s_max > 0)) return NULL;
-  int n = (int)ceil(s_max / h - 1e-9);
-  if (n < 1) n = 1;
+  return orc_table_build_ext(m, h, s_max, 0.0, 1);
+}
+
+orc_table* orc_table_build_ext(const orc_model* m, double h, double s_max, double s_ext,
+                               int stride) {
+  if (!m || !(h > 0) || !(s_max > 0) || stride < 1) return NULL;
+  int n_fine = (int)ceil(s_max / h - 1e-9);
+  if (n_fine < 1) n_fine = 1;
+  const double H = stride * h;
+  const double rest = s_ext - n_fine * h;
+  const int n_ext = rest > 0 ? (int)ceil(rest / H - 1e-9) : 0;
+  const int n = n_fine + (n_ext > 0 ? n_ext : 0);
   orc_table* t = (orc_table*)calloc(1, sizeof(orc_table));
   if (!t) return NULL;
   t->ntypes = m->ntypes;
   t->M = m->M;
   t->n = n;
   t->h = h;
+  t->n_fine = n_fine;
+  t->H = H;
   int np = m->ntypes * m->ntypes, M = m->M;
   t->a = (double*)malloc(sizeof(double) * (size_t)np * n * 6 * M);
   double* node = (double*)malloc(sizeof(double) * (size_t)np * (n + 1) * 3 * M);
@@ -416,7 +455,7 @@ orc_table* orc_table_build(const orc_model* m, double h, double s_max) {
   for (int idx = 0; idx < np * (n + 1); ++idx) {
     int p = idx / (n + 1), k = idx % (n + 1);
     double* nd = node + (size_t)idx * 3 * M;
-    err |= orc_embed(m, p / m->ntypes, p % m->ntypes, k * h, nd, nd + M, nd + 2 * M);
+    err |= orc_embed(m, p / m->ntypes, p % m->ntypes, tab_node(t, k), nd, nd + M, nd + 2 * M);
   }
   if (err) {
     free(node);
@@ -431,7 +470,7 @@ orc_table* orc_table_build(const orc_model* m, double h, double s_max) {
         double y0[3] = {n0[c], n0[M + c], n0[2 * M + c]};
         double y1[3] = {n1[c], n1[M + c], n1[2 * M + c]};
         double a[6];
-        orc_hermite5(y0, y1, h, a);
+        orc_hermite5(y0, y1, tab_width(t, k), a);
         for (int q = 0; q < 6; ++q) t->a[(((size_t)p * n + k) * 6 + q) * M + c] = a[q];
       }
     }
@@ -452,6 +491,13 @@ int orc_table_dims(const orc_table* t, int32_t* n, double* h) {
   return ORC_OK;
 }
 
+int orc_table_ext(const orc_table* t, int32_t* n_fine, double* H) {
+  if (!t) return ORC_ERR_ARG;
+  if (n_fine) *n_fine = t->n_fine;
+  if (H) *H = t->H;
+  return ORC_OK;
+}
+
 int orc_table_coeffs(const orc_table* t, int ti, int tj, double* out) {
   if (!t || ti < 0 || tj < 0 || ti >= t->ntypes || tj >= t->ntypes) return ORC_ERR_ARG;
   size_t sz = (size_t)t->n * 6 * t->M;
@@ -464,12 +510,9 @@ int orc_table_eval(const orc_table* t, int ti, int tj, double s, double* g, doub
    * the paper writes global powers of x, which is the same polynomial).
    * s = sw(r)/r >= 0; a rounding-level negative s next to rc evaluates the
    * first interval, so only s beyond the last node is out of range */
-  int out = (s > t->n * t->h) ? 1 : 0;
-  double fk = floor(s / t->h);
-  int k = (int)fk;
-  if (fk < 0) k = 0;
-  if (fk > t->n - 1) k = t->n - 1;
-  double u = s - k * t->h;
+  int out = (s > tab_node(t, t->n)) ? 1 : 0;
+  int k;
+  double u = tab_locate(t, s, &k);
   int M = t->M;
   const double* a = t->a + ((size_t)(ti * t->ntypes + tj) * t->n + k) * 6 * M;
   for (int c = 0; c < M; ++c) {
@@ -1491,12 +1534,10 @@ int orc_param_grad(const orc_model* m, const orc_table* table, double rc, double
                      grad_table + (size_t)(ti * m->ntypes + tj) * per_emb);
         continue;
       }
-      /* the interval and local variable of orc_table_eval */
-      const double fk = floor(s / table->h);
-      int kk = (int)fk;
-      if (fk < 0) kk = 0;
-      if (fk > table->n - 1) kk = table->n - 1;
-      const double v = (s - kk * table->h) / table->h;
+      /* the interval and local variable of orc_table_eval, the latter
+       * normalised by the interval's width */
+      int kk;
+      const double v = tab_locate(table, s, &kk) / tab_width(table, kk);
       double* out = grad_table + ((size_t)(ti * m->ntypes + tj) * table->n + kk) * 6 * M;
       double vp = 1.0;
       for (int p = 0; p < 6; ++p) {

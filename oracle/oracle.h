@@ -71,11 +71,21 @@ int orc_fit(const orc_model* m, int ti, const double* D, double* E, double* dD);
 
 /* Sec. 3.2 tabulation: nodes x_k = k*h, k=0..n with n=ceil(s_max/h) */
 orc_table* orc_table_build(const orc_model* m, double h, double s_max);
+/* The same with an extrapolation region: intervals of width h up to
+ * n_fine h >= s_max, then of width stride*h up to the first node >= s_ext
+ * (none when s_ext <= n_fine h).  Each interval is the quintic matching the
+ * net's value and first two derivatives at its two nodes (Sec. 3.2); the
+ * coarser second region is an extension of the paper's equal division. */
+orc_table* orc_table_build_ext(const orc_model* m, double h, double s_max, double s_ext,
+                               int stride);
+/* the extrapolation layout: intervals of width h, width of the others */
+int orc_table_ext(const orc_table* t, int32_t* n_fine, double* H);
 void orc_table_free(orc_table* t);
 int orc_table_dims(const orc_table* t, int32_t* n, double* h);
-/* coefficients of pair (ti,tj): out[n][6][M], local variable t = s - k*h */
+/* coefficients of pair (ti,tj): out[n][6][M], local variable t = s - x_k
+ * (x_k = k h in the first region) */
 int orc_table_coeffs(const orc_table* t, int ti, int tj, double* out);
-/* evaluate the table: g[M], dg[M]; returns 1 when s > n*h */
+/* evaluate the table: g[M], dg[M]; returns 1 when s is beyond the last node */
 int orc_table_eval(const orc_table* t, int ti, int tj, double s, double* g, double* dg);
 /* quintic on [0,h] matching (y,y',y'') at both ends: a[0..5] */
 void orc_hermite5(const double* y0, const double* y1, double h, double* a);

@@ -192,6 +192,63 @@ def test_table_converges_sixth_order(tmp_path):
     assert 40 < ratios[0] < 90 and 55 < ratios[1] < 73, (errs, ratios)
 
 
+def test_extrapolation_region_pins(tmp_path):
+    # intervals of width h up to s_max, then of width H = 10 h up to s_ext:
+    # the first region is the plain table's, bit for bit; the table equals
+    # the net at every node of both regions (both sides of the boundary);
+    # the coarse region converges at sixth order in H
+    p = tmp_path / "std2.model"
+    inputs.write_seeded_model(p, inputs.COPPER_SPEC, seed=0, std=2.0)
+    m = oracle.Model(p)
+    plain = oracle.Table(m, 0.01, 0.3)
+    ext = oracle.Table(m, 0.01, 0.3, s_ext=0.75, ext_stride=10)
+    assert (plain.n, ext.n_fine, ext.n, ext.H) == (30, 30, 35, 0.1)
+    assert np.array_equal(ext.coeffs()[:30], plain.coeffs())
+    nodes = ext.nodes()
+    assert np.allclose(nodes[-1], 0.8) and np.allclose(np.diff(nodes), ext.widths())
+    for k, x in enumerate(nodes):
+        g, dg, _ = m.embed(0, 0, x)
+        for side in ([-1e-12] if k else []) + [0.0] + ([1e-12] if k < ext.n else []):
+            tg, tdg, out = ext.eval(0, 0, x + side)
+            assert not out
+            assert np.allclose(tg, g, atol=1e-10) and np.allclose(tdg, dg, atol=1e-6), (k, side)
+    assert ext.eval(0, 0, 0.81)[2] and not ext.eval(0, 0, 0.79)[2]
+    # coarse region error at interval midpoints: O(H^6) (64 per halving)
+    errs = []
+    for stride in (8, 4, 2):
+        t = oracle.Table(m, 0.0025, 0.3, s_ext=0.62, ext_stride=stride)
+        mid = (t.nodes()[t.n_fine:-1] + t.nodes()[t.n_fine + 1:]) / 2
+        errs.append(max(np.abs(t.eval(0, 0, v)[0] - m.embed(0, 0, v)[0]).max() for v in mid))
+    ratios = [errs[0] / errs[1], errs[1] / errs[2]]
+    assert 45 < ratios[0] < 80 and 55 < ratios[1] < 73, (errs, ratios)
+
+
+def test_extrapolation_region_evaluation(stress):
+    # a table whose fine region ends below the nearest-neighbor s of copper
+    # (s ~ 0.34): those pairs use the coarse intervals.  Forces stay the
+    # exact negative gradient of that table's energy, and the energy is
+    # close to the untabulated model's within the coarse interpolation error
+    m, _ = stress
+    tab = oracle.Table(m, TABLE_H, 0.3, s_ext=2.0, ext_stride=10)
+    assert tab.n == 30 + 17
+    x, t, box = inputs.fcc_copper(3, sigma=0.1, seed=13)
+    a = _ev(m, tab, x, t, box)
+    b = _ev(m, None, x, t, box)
+    assert a["status"] == 0
+    d = np.zeros_like(x)
+    for i, c in [(0, 0), (5, 1), (33, 2)]:
+        for sgn in (1, -1):
+            d[i, c] = sgn * 1e-5
+            e = _ev(m, tab, x + d, t, box)["energy"]
+            d[i, c] = 0.0
+            if sgn > 0:
+                ep = e
+            else:
+                fd = -(ep - e) / 2e-5
+        assert abs(fd - a["force"][i, c]) < 1e-6 * max(1.0, abs(fd)), (i, c, fd)
+    assert abs(a["energy"] - b["energy"]) / len(x) < 1e-3 * np.abs(b["atom_energy"]).mean()
+
+
 # ------------------------------------------------------------ neighbors
 def test_fcc_shell_counts_golden():
     rows = np.loadtxt(os.path.join(HERE, "golden", "fcc_shells.txt"), dtype=int)

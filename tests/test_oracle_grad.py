@@ -160,3 +160,35 @@ def test_embedding_net_gradient_matches_central_differences(small, pair):
             assert abs(fd - ge[ti, tj, k]) < 1e-8 + 1e-6 * abs(fd), (k, fd, ge[ti, tj, k])
     finally:
         m.set_emb_params(ti, tj, p0)
+
+
+def test_table_gradient_with_extrapolation_region(small):
+    # coarse intervals (width H = 10 h beyond s = 0.4): the gradient is with
+    # respect to c_q = a_q w^q, w the interval's own width
+    m, _, x, t, box = small
+    tab = oracle.Table(m, 0.01, 0.4, s_ext=1.25, ext_stride=10)
+    assert tab.n_fine == 40 and tab.n == 49
+    _, _, gt = oracle.param_grad(m, tab, RC, RCS, SEL, x, t, box)
+    w = tab.widths()
+    big = np.argwhere(np.abs(gt) > 1e-3 * np.abs(gt).max())
+    coarse = big[big[:, 2] >= tab.n_fine]
+    fine = big[big[:, 2] < tab.n_fine]
+    assert len(coarse) >= 6 and len(fine) >= 6
+    rng = np.random.default_rng(2)
+    picks = list(coarse[rng.choice(len(coarse), 6, replace=False)]) + \
+        list(fine[rng.choice(len(fine), 3, replace=False)])
+    for ti, tj, kk, q, a in (tuple(int(v) for v in p) for p in picks):
+        c0 = tab.coeffs(ti, tj)
+        eps = 1e-4
+        try:
+            c = c0.copy()
+            c[kk, q, a] += eps / w[kk] ** q
+            tab.set_coeffs(ti, tj, c)
+            ep = _energy(m, tab, x, t, box)
+            c[kk, q, a] -= 2 * eps / w[kk] ** q
+            tab.set_coeffs(ti, tj, c)
+            em = _energy(m, tab, x, t, box)
+        finally:
+            tab.set_coeffs(ti, tj, c0)
+        fd = (ep - em) / (2 * eps)
+        assert abs(fd - gt[ti, tj, kk, q, a]) < 1e-9 + 1e-6 * abs(fd), ((ti, tj, kk, q, a), fd)
