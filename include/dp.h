@@ -39,7 +39,7 @@ typedef enum {
   DP_ERR_CUDA = 3,          /* CUDA runtime/kernel failure (sticky) */
   DP_ERR_OOM = 4,           /* device allocation failed */
   DP_ERR_SEL_OVERFLOW = 5,  /* more neighbors of one type within rc than sel[t] */
-  DP_ERR_TABLE_RANGE = 6,   /* an s(r) outside the tabulated domain [0, n*h] */
+  DP_ERR_TABLE_RANGE = 6,   /* an s(r) beyond the table's last node */
   DP_ERR_BOX = 7,           /* box not orthorhombic, or an edge shorter than the list cutoff */
   DP_ERR_TIMEOUT = 8,       /* a bounded wait gave up */
   DP_ERR_UNIMPLEMENTED = 9, /* option combination not built */
@@ -75,6 +75,12 @@ typedef struct {
                           reallocated); 0 launches every kernel.  The results
                           are bitwise the same; not used while profiling or
                           when thermo output is requested */
+  double s_ext;        /* table extrapolation region: beyond the first region
+                          [0, n_fine*h], n_fine = ceil(s_max/h), intervals of
+                          width ext_stride*h up to the first node >= s_ext;
+                          [0.0] none (s_ext <= n_fine*h) */
+  int ext_stride;      /* width of the extrapolation intervals in units of h
+                          (>= 1) [10] */
 } dp_options;
 
 /* Thermodynamic record of one MD step (Sec. 4). */
@@ -206,9 +212,11 @@ dp_status dp_neighbor_pairs(dp_handle* h, int64_t natoms, const double* coords,
                             int64_t* count);
 
 /* The device table of model type pair (ti, tj) as FP32 [n][6][M]: on
- * interval k the embedding row is sum_q c[k][q][:] u^q with the normalised
- * local variable u = s/h - k in [0, 1), i.e. c[k][q] = a_q h^q for the
- * paper's coefficients a_q of the local variable s - k*h (Sec. 3.2).
+ * interval k, [x_k, x_k + w_k), the embedding row is sum_q c[k][q][:] u^q
+ * with the normalised local variable u = (s - x_k)/w_k in [0, 1), i.e.
+ * c[k][q] = a_q w_k^q for the paper's coefficients a_q of the local variable
+ * s - x_k (Sec. 3.2).  x_k = k h and w_k = h in the first region (k <
+ * n_fine); beyond it w_k = ext_stride*h (see dp_options.s_ext).
  * *n receives the interval count (call with out == NULL to query it). */
 dp_status dp_table_coeffs(dp_handle* h, int ti, int tj, float* out, int32_t* n);
 
@@ -248,7 +256,7 @@ dp_status dp_compute_batch(dp_handle* h, int nsys, const int64_t* natoms, const 
  * (w_out, then b_out).  The embedding representation ("table" arrays): for
  * a tabulated handle the table, [ntypes][ntypes][n][6][M] in the layout of
  * dp_table_coeffs (the derivative with respect to c[k][q][:], the
- * coefficient of u^q with u = s/h - k); for an untabulated handle
+ * coefficient of u^q with u = (s - x_k)/w_k); for an untabulated handle
  * (tabulated = 0) the embedding nets' weights and biases, per (centre,
  * neighbor) type pair per layer a [(win_k + 1)][wout_k] block, win_0 = 1.
  * ------------------------------------------------------------------------- */

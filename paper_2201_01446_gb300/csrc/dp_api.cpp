@@ -146,8 +146,9 @@ struct dp_handle {
   };
   std::vector<FitOfs> fit_ofs;
   size_t fit_floats = 0;
-  int n_int = 0;
-  double h = 0.0;
+  int n_int = 0;     // table intervals: n_fine of width h, then of width H
+  int n_fine = 0;
+  double h = 0.0, H = 0.0;
   FitNet nets[DP_MAXT];
   FitNetTC nets_tc[DP_MAXT];
   float b_out[DP_MAXT] = {0};
@@ -353,9 +354,12 @@ EnvParams env_params(const dp_handle* h) {
   ep.inv_w = (float)(1.0 / (h->rc - h->rcs));
   ep.inv_h = (float)(1.0 / h->h);
   ep.h = (float)h->h;
-  ep.smax = (float)(h->n_int * h->h);
+  ep.s_fine = (float)(h->n_fine * h->h);
+  ep.inv_H = (float)(1.0 / h->H);
+  ep.smax = (float)(h->n_fine * h->h + (h->n_int - h->n_fine) * h->H);
   ep.inv_nm = (float)(1.0 / h->Nm);
   ep.n_int = h->n_int;
+  ep.n_fine = h->n_fine;
   ep.M = h->M;
   ep.ntypes = h->ntypes;
   return ep;
@@ -393,7 +397,7 @@ dp_status status_errors(dp_handle* h) {
   }
   if (s[ST_RANGE]) {
     std::snprintf(buf, sizeof buf, "%d pairs have s outside the table domain [0, %g]", s[ST_RANGE],
-                  h->n_int * h->h);
+                  h->n_fine * h->h + (h->n_int - h->n_fine) * h->H);
     return fail(h, DP_ERR_TABLE_RANGE, buf);
   }
   if (s[ST_TIMEOUT]) {
@@ -1131,6 +1135,8 @@ void dp_options_default(dp_options* o) {
   o->embed_precision = 0;
   o->tanh_table = 0;
   o->md_graphs = 1;
+  o->s_ext = 0.0;
+  o->ext_stride = 10;
 }
 
 const char* dp_version(void) { return "dp-gb300 0.1 (sm_103a; tabulated FP32 embedding, FP32 SIMT fitting)"; }
@@ -1170,6 +1176,8 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
       h->opt.tanh_table < 0 || h->opt.tanh_table > 1 || h->opt.md_graphs < 0 ||
       h->opt.md_graphs > 1)
     return bail(DP_ERR_UNIMPLEMENTED);
+  if (h->opt.ext_stride < 1 || h->opt.ext_stride > 1000 || !(h->opt.s_ext >= 0.0))
+    return bail(DP_ERR_ARG);
   HostModel m;
   std::string why;
   if (!read_model(model_path, m, why)) {
@@ -1202,7 +1210,14 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
   }
   if (h->Nm <= 0) return bail(DP_ERR_ARG);
   h->h = h->opt.table_step;
-  h->n_int = std::max(1, (int)std::ceil(h->opt.s_max / h->h - 1e-9));
+  h->n_fine = std::max(1, (int)std::ceil(h->opt.s_max / h->h - 1e-9));
+  h->H = h->opt.ext_stride * h->h;
+  {
+    const double rest = h->opt.s_ext - h->n_fine * h->h;
+    const double n_ext = rest > 0.0 ? std::ceil(rest / h->H - 1e-9) : 0.0;
+    if (n_ext > 4096) return bail(DP_ERR_ARG);
+    h->n_int = h->n_fine + (int)n_ext;
+  }
   if (h->n_int > 4096) return bail(DP_ERR_ARG);
   if (cudaMallocHost(&h->status_host, sizeof(int32_t) * ST_NWORDS) != cudaSuccess) {
     cudaGetLastError();
@@ -1323,7 +1338,7 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
     return bail(DP_ERR_UNIMPLEMENTED);
   }
   if (table_build(h->st, P<double>(h->emb64), P<int64_t>(h->emb_off), m.n_emb, m.emb_w, np, h->h,
-                  h->n_int, P<float>(h->table)) != 0) {
+                  h->n_int, h->n_fine, h->H, P<float>(h->table)) != 0) {
     h->err = "table build failed";
     return bail(DP_ERR_CUDA);
   }
@@ -1779,7 +1794,7 @@ dp_status dp_set_params(dp_handle* h, const double* fit, const double* table) {
        "embedding upload");
     CKS(upload_plain_nets(h, table));
     if (table_build(h->st, P<double>(h->emb64), P<int64_t>(h->emb_off), h->n_emb, h->emb_w,
-                    h->ntypes * h->ntypes, h->h, h->n_int, P<float>(h->table)) != 0)
+                    h->ntypes * h->ntypes, h->h, h->n_int, h->n_fine, h->H, P<float>(h->table)) != 0)
       return fail(h, DP_ERR_CUDA, "table build failed");
     CK(cudaStreamSynchronize(h->st), "embedding upload");
   } else if (table) {

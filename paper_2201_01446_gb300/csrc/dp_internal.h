@@ -50,9 +50,11 @@ struct CellGeom {
 // Smooth-switch / table parameters in FP32 for the pair kernels.
 struct EnvParams {
   float rc2, rc, rcs, inv_w;  // inv_w = 1/(rc - rcs)
-  float inv_h, h, smax;       // table step and domain end n*h
+  float inv_h, h, smax;       // table step and domain end (the last node)
+  float s_fine, inv_H;        // end of the step-h region; 1/width beyond it
   float inv_nm;               // 1/N_m (N_m = sum of sel)
   int n_int;                  // table intervals
+  int n_fine;                 // of them of width h (the rest, of width H)
   int M;                      // embedding width
   int ntypes;                 // model types
 };
@@ -77,11 +79,13 @@ void launch_build_list(cudaStream_t st, int64_t n, const double* x, const int32_
                        int cap, uint32_t* nlist, int32_t* nn, int32_t* status);
 
 // ---------------------------------------------------------------- embedding
-// FP64 forward-mode evaluation of every embedding net at the nodes k*h and
-// the quintic fit per interval; writes FP32 [npair][n_int][6][M] with the
-// coefficients of the normalised local variable u = s/h - k.
+// FP64 forward-mode evaluation of every embedding net at the nodes (k*h for
+// k <= n_fine, then steps of H) and the quintic fit per interval; writes FP32
+// [npair][n_int][6][M] with the coefficients of the normalised local
+// variable u = (s - x_k)/w_k.
 int table_build(cudaStream_t st, const double* emb64, const int64_t* emb_off, int n_emb,
-                const int* emb_w, int npair, double h, int n_int, float* table_out);
+                const int* emb_w, int npair, double h, int n_int, int n_fine, double H,
+                float* table_out);
 int launch_tab_fwd(cudaStream_t st, int64_t n, const float4* off, const uint32_t* nlist,
                    const int32_t* nn, int cap, const CellGeom& g, const EnvParams& ep,
                    const float* table, float* T, int32_t* status,

@@ -15,6 +15,29 @@ struct Pair {
   bool out_of_range;
 };
 
+// The table interval of s: floor(s/h) in the first region (intervals of
+// width h up to s_fine), n_fine + floor((s - s_fine)/H) beyond it, clamped to
+// the table (s beyond the last node is flagged by the caller).
+__device__ __forceinline__ int interval_of(const EnvParams& ep, float s) {
+  const float q = floorf(s * ep.inv_h);
+  if (q < (float)ep.n_fine) return q < 0.0f ? 0 : (int)q;
+  if (ep.n_int == ep.n_fine) return ep.n_fine - 1;
+  // clamped in floating point first (fmaxf maps a NaN to 0)
+  const float j = fminf(fmaxf(floorf((s - ep.s_fine) * ep.inv_H), 0.0f),
+                        (float)(ep.n_int - ep.n_fine - 1));
+  return ep.n_fine + (int)j;
+}
+
+// The normalised local variable of s on interval th, u = (s - x_th) / w_th,
+// and the width's reciprocal du/ds.
+__device__ __forceinline__ float interval_u(const EnvParams& ep, float s, int th) {
+  return th < ep.n_fine ? s * ep.inv_h - (float)th
+                        : (s - ep.s_fine) * ep.inv_H - (float)(th - ep.n_fine);
+}
+__device__ __forceinline__ float interval_du_ds(const EnvParams& ep, int th) {
+  return th < ep.n_fine ? ep.inv_h : ep.inv_H;
+}
+
 __device__ __forceinline__ void pair_geom(const EnvParams& ep, float dx, float dy, float dz,
                                           float r2, int tj, Pair& P) {
   P.dx = dx;
@@ -41,11 +64,9 @@ __device__ __forceinline__ void pair_geom(const EnvParams& ep, float dx, float d
   P.ir = ir;
   P.s = s;
   P.dsdr = (dsw - s) * ir;
-  const float q = s * ep.inv_h;
-  int th = (int)floorf(q);
-  th = th < 0 ? 0 : (th > ep.n_int - 1 ? ep.n_int - 1 : th);
+  const int th = interval_of(ep, s);
   P.th = th;
-  P.u = q - (float)th;
+  P.u = interval_u(ep, s, th);
   P.out_of_range = s > ep.smax;
 }
 

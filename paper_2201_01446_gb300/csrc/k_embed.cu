@@ -34,7 +34,7 @@ using namespace dp_embed;
 // and second derivative in s, by forward-mode propagation in FP64.
 __global__ void k_table_nodes(const double* __restrict__ emb, const int64_t* __restrict__ emb_off,
                               int n_emb, int w0, int w1, int w2, int w3, int w4, int w5, double h,
-                              int n_nodes, double* __restrict__ node) {
+                              int n_fine, double H, int n_nodes, double* __restrict__ node) {
   extern __shared__ double sm[];
   const int p = blockIdx.x / n_nodes, k = blockIdx.x % n_nodes;
   const int widths[6] = {w0, w1, w2, w3, w4, w5};
@@ -42,7 +42,8 @@ __global__ void k_table_nodes(const double* __restrict__ emb, const int64_t* __r
   for (int l = 0; l < n_emb; ++l) wmax = max(wmax, widths[l]);
   double* cur = sm;                 // [3][wmax]
   double* nxt = sm + 3 * wmax;      // [3][wmax]
-  const double s = k * h;
+  // node k: k h up to n_fine, then steps of H (the extrapolation region)
+  const double s = k <= n_fine ? k * h : n_fine * h + (k - n_fine) * H;
   const int c = threadIdx.x;
   {
     const double* W = emb + emb_off[p * n_emb + 0];
@@ -90,16 +91,18 @@ __global__ void k_table_nodes(const double* __restrict__ emb, const int64_t* __r
 }
 
 // Quintic on u in [0,1] with f, f', f'' given at both ends (derivatives in u,
-// i.e. the s-derivatives times h and h^2).  With A, B, C the residuals of the
-// value, slope and curvature left at u = 1 by the first three coefficients,
-// the last three solve  p+q+w = A, 3p+4q+5w = B, 6p+12q+20w = C.
-__global__ void k_table_coef(const double* __restrict__ node, int npair, int n_int, int M, double h,
-                             float* __restrict__ table) {
+// i.e. the s-derivatives times the interval width w and w^2; w = h, or H
+// in the extrapolation region).  With A, B, C the residuals of the value,
+// slope and curvature left at u = 1 by the first three coefficients, the
+// last three solve  p+q+w = A, 3p+4q+5w = B, 6p+12q+20w = C.
+__global__ void k_table_coef(const double* __restrict__ node, int npair, int n_int, int M,
+                             double h_fine, int n_fine, double H, float* __restrict__ table) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)npair * n_int * M) return;
   const int c = idx % M;
   const int k = (idx / M) % n_int;
   const int p = idx / ((int64_t)M * n_int);
+  const double h = k < n_fine ? h_fine : H;
   const double* n0 = node + ((size_t)p * (n_int + 1) + k) * 3 * M;
   const double* n1 = n0 + 3 * M;
   const double f0 = n0[c], d0 = n0[M + c] * h, e0 = n0[2 * M + c] * h * h;
@@ -440,7 +443,8 @@ __global__ void __launch_bounds__(256, 3) k_tab_bwd(int64_t n, const float4* __r
             }
             const float ux = P.dx * P.ir, uy = P.dy * P.ir, uz = P.dz * P.ir;
             const float s = P.s;
-            const float gs = ep.inv_h * s * (dgu[0] + ux * dgu[1] + uy * dgu[2] + uz * dgu[3]);
+            const float gs =
+                interval_du_ds(ep, P.th) * s * (dgu[0] + ux * dgu[1] + uy * dgu[2] + uz * dgu[3]);
             const float a0 = gR[0] + gs;
             const float dot = gR[1] * ux + gR[2] * uy + gR[3] * uz;
             const float sor = s * P.ir;
@@ -540,7 +544,8 @@ size_t bwd_smem(const EnvParams& ep) {
 int tab_kernel_slots(int64_t n) { return tab_blocks(n) * kWarpsPerBlock; }
 
 int table_build(cudaStream_t st, const double* emb64, const int64_t* emb_off, int n_emb,
-                const int* emb_w, int npair, double h, int n_int, float* table_out) {
+                const int* emb_w, int npair, double h, int n_int, int n_fine, double H,
+                float* table_out) {
   if (n_emb < 1 || n_emb > 6) return -1;
   int w[6] = {0, 0, 0, 0, 0, 0};
   int wmax = 0;
@@ -557,9 +562,10 @@ int table_build(cudaStream_t st, const double* emb64, const int64_t* emb_off, in
   int threads = ((wmax + 31) / 32) * 32;
   DP_LAUNCHED(2);
   k_table_nodes<<<npair * n_nodes, threads, sizeof(double) * 6 * wmax, st>>>(
-      emb64, emb_off, n_emb, w[0], w[1], w[2], w[3], w[4], w[5], h, n_nodes, node);
+      emb64, emb_off, n_emb, w[0], w[1], w[2], w[3], w[4], w[5], h, n_fine, H, n_nodes, node);
   int64_t tot = (int64_t)npair * n_int * M;
-  k_table_coef<<<(int)((tot + 255) / 256), 256, 0, st>>>(node, npair, n_int, M, h, table_out);
+  k_table_coef<<<(int)((tot + 255) / 256), 256, 0, st>>>(node, npair, n_int, M, h, n_fine, H,
+                                                         table_out);
   cudaFreeAsync(node, st);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -867,7 +867,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const float r2 = dx * dx + dy * dy + dz * dz;
         Pair P;
         pair_geom(ep, dx, dy, dz, r2, tj, P);
-        const float u = P.s * ep.inv_h - (float)th;  // the sort's interval
+        const float u = interval_u(ep, P.s, th);  // the sort's interval
         const float* Bk = Bsm + al * kBsmAtom + (b - w0) * 24;
         float Bv[24];
 #pragma unroll
@@ -889,7 +889,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         const float ux = P.dx * P.ir, uy = P.dy * P.ir, uz = P.dz * P.ir;
         const float s = P.s;
-        const float gs = ep.inv_h * s * (dgu[0] + ux * dgu[1] + uy * dgu[2] + uz * dgu[3]);
+        const float gs =
+            interval_du_ds(ep, th) * s * (dgu[0] + ux * dgu[1] + uy * dgu[2] + uz * dgu[3]);
         const float a0 = gR[0] + gs;
         const float dot = gR[1] * ux + gR[2] * uy + gR[3] * uz;
         const float sor = s * P.ir;

@@ -32,7 +32,8 @@ class DPError(RuntimeError):
 class dp_options(C.Structure):
     _fields_ = [("tabulated", C.c_int), ("fit_precision", C.c_int), ("table_step", C.c_double),
                 ("s_max", C.c_double), ("skin", C.c_double), ("rebuild_every", C.c_int),
-                ("embed_precision", C.c_int), ("tanh_table", C.c_int), ("md_graphs", C.c_int)]
+                ("embed_precision", C.c_int), ("tanh_table", C.c_int), ("md_graphs", C.c_int),
+                ("s_ext", C.c_double), ("ext_stride", C.c_int)]
 
 
 class dp_thermo(C.Structure):
