@@ -158,8 +158,9 @@ dp_status dp_system_create(dp_handle* h, int64_t natoms, const double* x, const 
  * each system keeps its own box, cells and neighbor list, rebuilt on the
  * common schedule), dp_system_get returns the concatenated arrays.  Each
  * system's trajectory is bitwise the one it has alone, and so are its thermo
- * records (dp_md_step writes [nsteps][nsys] of them).  Needs tabulated = 1
- * and embed_precision = 2; no state file (DP_ERR_UNIMPLEMENTED). */
+ * records (dp_md_step writes [nsteps][nsys] of them); dp_state_save and
+ * dp_state_load keep all the systems.  Needs tabulated = 1 and
+ * embed_precision = 2. */
 dp_status dp_system_create_batch(dp_handle* h, int nsys, const int64_t* natoms, const double* x,
                                  const double* v, const int32_t* types,
                                  const double* mass_of_type, const double* boxes,
@@ -195,7 +196,10 @@ int dp_system_batch_size(const dp_system* s);
  */
 dp_status dp_md_step(dp_handle* h, dp_system* s, int nsteps, double dt_fs, dp_thermo* thermo_out);
 
-/* Save / load the MD state (x, v, types, masses, box, step) to a file. */
+/* Save / load the MD state (x, v, f, types, masses, box, step and the
+ * list's reference positions) to a file; a batch system's file holds every
+ * system (atom counts and boxes) and loads as a batch system.  A loaded
+ * system continues bitwise as the saved one would have. */
 dp_status dp_state_save(dp_system* s, const char* path);
 dp_status dp_state_load(dp_handle* h, const char* path, dp_system** out);
 

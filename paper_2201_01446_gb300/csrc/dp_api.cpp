@@ -114,6 +114,7 @@ struct Batch {
   int nsys = 0;
   std::vector<int64_t> base;             // [nsys + 1] first atom of each system
   std::vector<std::array<double, 3>> L;  // box edges
+  std::vector<double> boxes;             // [nsys][9] as given (state files)
   std::vector<CellGeom> geoms;           // cell grids of the last list build
   TileMap tm{};                          // tiles padded per system (index list in Work::bidx)
   // per system: (first tile, tiles) of each centre type present in it
@@ -807,6 +808,7 @@ dp_status batch_init(dp_handle* h, Batch& b, int nsys, const int64_t* natoms,
   if (b.base[nsys] >= (1LL << 27)) return fail(h, DP_ERR_ARG, "at most 2^27 atoms per call");
   b.L.assign(nsys, {0.0, 0.0, 0.0});
   for (int q = 0; q < nsys; ++q) CKS(box_lengths(h, boxes + 9 * q, b.L[q].data()));
+  b.boxes.assign(boxes, boxes + 9 * (size_t)nsys);
   return DP_OK;
 }
 
@@ -2170,8 +2172,8 @@ dp_status dp_state_save(dp_system* s, const char* path) {
   if (!s || !path) return DP_ERR_ARG;
   dp_handle* h = s->h;
   CKS(check_handle(h));
-  if (s->batch) return fail(h, DP_ERR_UNIMPLEMENTED, "state files hold one system");
   const int64_t n = s->w.n;
+  const Batch* bt = s->batch.get();
   std::vector<double> x(3 * n), v(3 * n), f(3 * n), xr(3 * n);
   if (n) {
     CK(cudaStreamSynchronize(h->st), "sync");
@@ -2183,8 +2185,21 @@ dp_status dp_state_save(dp_system* s, const char* path) {
   FILE* fp = std::fopen(path, "wb");
   if (!fp) return fail(h, DP_ERR_ARG, "cannot open state file for writing");
   int64_t hdr[3] = {n, (int64_t)s->mass_user.size(), s->step};
-  bool ok = std::fwrite("DPSTATE1", 1, 8, fp) == 8 && std::fwrite(hdr, 8, 3, fp) == 3 &&
-            std::fwrite(s->box, 8, 9, fp) == 9 &&
+  bool ok;
+  if (bt) {
+    // several systems: their count, atom counts and boxes after the header
+    const int64_t nsys = bt->nsys;
+    std::vector<int64_t> counts(nsys);
+    for (int q = 0; q < bt->nsys; ++q) counts[q] = bt->base[q + 1] - bt->base[q];
+    ok = std::fwrite("DPSTATE2", 1, 8, fp) == 8 && std::fwrite(hdr, 8, 3, fp) == 3 &&
+         std::fwrite(&nsys, 8, 1, fp) == 1 &&
+         std::fwrite(counts.data(), 8, counts.size(), fp) == counts.size() &&
+         std::fwrite(bt->boxes.data(), 8, bt->boxes.size(), fp) == bt->boxes.size();
+  } else {
+    ok = std::fwrite("DPSTATE1", 1, 8, fp) == 8 && std::fwrite(hdr, 8, 3, fp) == 3 &&
+         std::fwrite(s->box, 8, 9, fp) == 9;
+  }
+  ok = ok &&
             std::fwrite(s->mass_user.data(), 8, s->mass_user.size(), fp) == s->mass_user.size() &&
             std::fwrite(s->types_user.data(), 4, n, fp) == (size_t)n &&
             std::fwrite(x.data(), 8, 3 * n, fp) == (size_t)(3 * n) &&
@@ -2203,9 +2218,32 @@ dp_status dp_state_load(dp_handle* h, const char* path, dp_system** out) {
   char magic[8];
   int64_t hdr[3];
   double box[9];
-  bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "DPSTATE1", 8) == 0 &&
-            std::fread(hdr, 8, 3, fp) == 3 && std::fread(box, 8, 9, fp) == 9 && hdr[0] >= 0 &&
-            hdr[1] == h->ntypes_user;
+  bool ok = std::fread(magic, 1, 8, fp) == 8;
+  const bool several = ok && std::memcmp(magic, "DPSTATE2", 8) == 0;
+  ok = ok && (several || std::memcmp(magic, "DPSTATE1", 8) == 0) &&
+       std::fread(hdr, 8, 3, fp) == 3 && hdr[0] >= 0 && hdr[0] < (1LL << 40) &&
+       hdr[1] == h->ntypes_user;
+  // several systems: their count, atom counts (summing to n) and boxes
+  int64_t nsys = 0;
+  std::vector<int64_t> counts;
+  std::vector<double> boxes;
+  if (ok && several) {
+    ok = std::fread(&nsys, 8, 1, fp) == 1 && nsys >= 0 && nsys < (1 << 24);
+    if (ok) {
+      counts.resize(nsys);
+      boxes.resize(9 * (size_t)nsys);
+      ok = std::fread(counts.data(), 8, nsys, fp) == (size_t)nsys &&
+           std::fread(boxes.data(), 8, boxes.size(), fp) == boxes.size();
+      int64_t tot = 0;
+      for (int64_t c : counts) {
+        ok = ok && c >= 0;
+        tot += c;
+      }
+      ok = ok && tot == hdr[0];
+    }
+  } else if (ok) {
+    ok = std::fread(box, 8, 9, fp) == 9;
+  }
   const int64_t n = ok ? hdr[0] : 0;
   std::vector<double> mass(ok ? hdr[1] : 0), x(3 * n), v(3 * n), f(3 * n), xr(3 * n);
   std::vector<int32_t> types(n);
@@ -2221,7 +2259,11 @@ dp_status dp_state_load(dp_handle* h, const char* path, dp_system** out) {
   // restore the current positions and forces: the continued run then sees
   // the same list, cells and forces as the run that was saved
   dp_system* s = nullptr;
-  CKS(dp_system_create(h, n, xr.data(), v.data(), types.data(), mass.data(), box, 0, &s));
+  if (several)
+    CKS(dp_system_create_batch(h, (int)nsys, counts.data(), xr.data(), v.data(), types.data(),
+                               mass.data(), boxes.data(), &s));
+  else
+    CKS(dp_system_create(h, n, xr.data(), v.data(), types.data(), mass.data(), box, 0, &s));
   s->step = hdr[2];
   if (n) {
     if (cudaMemcpy(s->w.x.p, x.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice) ||
@@ -2229,8 +2271,13 @@ dp_status dp_state_load(dp_handle* h, const char* path, dp_system** out) {
       dp_system_destroy(s);
       return fail(h, DP_ERR_CUDA, "state upload failed");
     }
-    launch_mirror(h->st, n, P<double>(s->w.x), P<int32_t>(s->w.cellc), P<int32_t>(s->w.types),
-                  s->w.geom, P<float4>(s->w.off));
+    if (s->batch)
+      launch_mirror_batch(h->st, n, P<double>(s->w.x), P<int32_t>(s->w.cellc),
+                          P<int32_t>(s->w.types), P<int32_t>(s->w.sys_of),
+                          P<CellGeom>(s->batch->geoms_dev), P<float4>(s->w.off));
+    else
+      launch_mirror(h->st, n, P<double>(s->w.x), P<int32_t>(s->w.cellc),
+                    P<int32_t>(s->w.types), s->w.geom, P<float4>(s->w.off));
   }
   s->f_valid = true;
   *out = s;

@@ -144,3 +144,38 @@ def test_batch_errors_and_type_map(dp, cu_stress_path, water_model_path):
         _check_alone(dp, hm, swapped, "2 x water 192, mapped types")
     finally:
         dp.dp_destroy(hm)
+
+
+def test_batch_state_file_resume_bitwise(dp, cu_stress_path, tmp_path):
+    # a batch system saved between list rebuilds (step 13) and loaded again
+    # continues bitwise as the uninterrupted run; the file keeps every system
+    h = _tc(dp, cu_stress_path)
+    try:
+        sys2 = []
+        for k, (cells, sig) in enumerate([((3, 4, 5), 0.1), (4, 0.05)]):
+            x, t, box = inputs.fcc_copper(cells, sigma=sig, seed=40 + k)
+            v = inputs.maxwell_velocities(np.full(len(x), inputs.MASS_CU), 330.0, seed=50 + k)
+            sys2.append((x, v, t, box))
+        n = sum(len(s[0]) for s in sys2)
+        a = dp.dp_system_create_batch(h, sys2, [inputs.MASS_CU])
+        try:
+            dp.dp_md_step(h, a, 23, 1.0)
+            xa, va, fa = dp.dp_system_get(h, a, n)
+        finally:
+            dp.dp_system_destroy(a)
+        b = dp.dp_system_create_batch(h, sys2, [inputs.MASS_CU])
+        try:
+            dp.dp_md_step(h, b, 13, 1.0)
+            dp.dp_state_save(h, b, tmp_path / "batch.bin")
+        finally:
+            dp.dp_system_destroy(b)
+        c = dp.dp_state_load(h, tmp_path / "batch.bin")
+        try:
+            assert dp.dp_system_step(c) == 13 and dp.lib.dp_system_batch_size(c) == 2
+            dp.dp_md_step(h, c, 10, 1.0)
+            xc, vc, fc = dp.dp_system_get(h, c, n)
+        finally:
+            dp.dp_system_destroy(c)
+        assert np.array_equal(xa, xc) and np.array_equal(va, vc) and np.array_equal(fa, fc)
+    finally:
+        dp.dp_destroy(h)
