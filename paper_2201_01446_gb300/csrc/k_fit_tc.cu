@@ -319,8 +319,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // ---------------------------------------------------------------- persistent
 // K-short GEMMs (K <= 256: hidden, last, backward and dE/dD layers): one CTA
-// per SM walks row tiles and, per row tile, its N tiles of 128 columns; each
-// stage holds one K chunk of A and of B (all pieces), up to 8 stages deep.
+// per SM walks row tiles and, per row tile, its N tiles of 128 columns (256
+// for the dE/dD GEMM); each stage holds one K chunk of A and of B (all
+// pieces), up to 8 stages deep.
 // (Keeping the row tile's A resident instead, loaded once for all N tiles,
 // measured slower even for the 16 N tiles of the dE/dD GEMM: its 180 KB
 // leave room for three B stages only, and the MMAs then wait on B.)
@@ -329,15 +330,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // the MMAs of tile t+1 and warp 0 the copies of t+2.  Per-row state across the
 // N tiles of a row tile (the energy sum, the dE/dT second factor) stays in the
 // epilogue thread's registers.
-constexpr int kPNT = 128;    // columns per N tile
+constexpr int kPNT = 128;    // columns per N tile (the dE/dD GEMM: 256, see below)
 constexpr int kPMaxNS = 8;   // stages at most
 constexpr int kPMaxK = 16;   // K chunks a row tile can hold (K <= 256)
 constexpr size_t kPSmemMax = 225 * 1024;
 
-template <int PC>
+template <int PC, int NTW>
 struct PCfg {
   static constexpr int A_CHUNK = PC * kBM * kBK * 2;   // one K chunk of A, all pieces
-  static constexpr int B_PIECE = kPNT * kBK * 2;       // one piece of B
+  static constexpr int B_PIECE = NTW * kBK * 2;        // one piece of B
   static constexpr int STAGE = A_CHUNK + PC * B_PIECE;  // [A chunk][B pieces]
   static int stages() {
     const long ns = ((long)kPSmemMax - 128) / STAGE;
@@ -352,7 +353,17 @@ template <int EPI, int PC, bool TAB, int EW>
 __global__ void __launch_bounds__(128 + EW * 32, 1)
     k_tc_gemm_p(int M, int N, int K, int NS, const __nv_bfloat16* __restrict__ A,
                 const __nv_bfloat16* __restrict__ B, TcEpi ep) {
-  using C = PCfg<PC>;
+  // The dE/dD GEMM (N = 2048) streams its A chunk once per N tile: N tiles of
+  // 256 columns halve those bytes (36 KB per stage for 6.3 MFLOP instead of
+  // 24 KB for 3.1), and all six piece products then share one accumulator
+  // (2 x 256 TMEM columns, still double-buffered; measured 62.5 -> 60.5 ms of
+  // fitting per 4M-atom step, force errors within the FP32 bars).  The other
+  // layers keep the h*h products in their own accumulator.  What bounds
+  // these GEMMs is shared-memory bandwidth: every 128x256x16 MMA reads 12 KB
+  // of operands while the copies write 6 KB, close to the SM's ~128 B/clock.
+  constexpr int NTW = EPI == TC_DT ? 256 : kPNT;
+  constexpr bool ONE_ACC = NTW == 256;
+  using C = PCfg<PC, NTW>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   const int nk = K / kBK;
@@ -366,10 +377,10 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mtiles = (M + kBM - 1) / kBM;
-  const int ntn = (N + kPNT - 1) / kPNT;
+  const int ntn = (N + NTW - 1) / NTW;
   // B is pre-tiled in tiles of 256 rows (the last ragged)
   auto b_src = [&](int n, int kc, int p) {
-    const int n0 = n * kPNT, t256 = n0 / 256, r0 = n0 - t256 * 256;
+    const int n0 = n * NTW, t256 = n0 / 256, r0 = n0 - t256 * 256;
     const int nt256 = min(256, N - t256 * 256);
     return B + (size_t)t256 * 256 * K * PC + ((size_t)kc * PC + p) * nt256 * kBK +
            (size_t)(r0 / 8) * 128;
@@ -406,7 +417,7 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
       bool ok = true;
       for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x) {
         for (int n = 0; n < ntn && ok; ++n) {
-          const int nt = min(kPNT, N - n * kPNT);
+          const int nt = min(NTW, N - n * NTW);
           for (int kc = 0; kc < nk; ++kc, ++bi) {
             const int s = bi % NS;
             const uint32_t u = bi / NS;
@@ -436,7 +447,7 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
       bool ok = true;
       for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x) {
         for (int n = 0; n < ntn && ok; ++n, ++ti) {
-          const int nt = min(kPNT, N - n * kPNT);
+          const int nt = min(NTW, N - n * NTW);
           const uint32_t idesc = make_idesc_bf16(kBM, nt);
           const int j = ti & 1;
           if (ti >= 2 && !mbar_wait(&t_empty[j], ((ti >> 1) - 1) & 1, abort_flag)) {
@@ -459,8 +470,8 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
               if (PC > 1) prod_pieces(q, pa, pb);
               const uint64_t ad = make_desc(a0 + pa * (kBM * kBK * 2), 128, 256);
               const uint64_t bd = make_desc(b0 + pb * C::B_PIECE, 128, 256);
-              const uint32_t dst = tmem + (uint32_t)(j * 256) + (q > 0 ? 128u : 0u);
-              const uint32_t acc = (kc > 0 || q > 1) ? 1u : 0u;
+              const uint32_t dst = tmem + (uint32_t)(j * 256) + (!ONE_ACC && q > 0 ? 128u : 0u);
+              const uint32_t acc = (kc > 0 || q > (ONE_ACC ? 0 : 1)) ? 1u : 0u;
               asm volatile(
                   "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                   " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
@@ -487,7 +498,7 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
     // epilogue: thread = row of the tile (TMEM lane; a warp reaches the lane
     // quarter warp % 4), all columns of each N tile or one half of them
     static_assert(EW == 4 || (EW == 8 && EPI != TC_DT && EPI != TC_LAST), "epilogue warps");
-    constexpr int CPW = 8 / (EW / 4);  // 16-column chunks per thread and N tile
+    constexpr int CPW = (NTW / 16) / (EW / 4);  // 16-column chunks per thread and N tile
     const int r = (tid - 128) & (kBM - 1);
     const int hf = EW == 8 ? (warp - 4) >> 2 : 0;
     const uint32_t tl_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
@@ -521,20 +532,36 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n");
-        const int nt = min(kPNT, N - n * kPNT), nch = nt / 16;
-        float f1[4][8];
+        const int nt = min(NTW, N - n * NTW), nch = nt / 16;
+        float f1[4][8];  // the first factor of dE/dT for 8 chunks (b) at a time
+        // dE/dT[c][b] for the chunk group g of this N tile (b = NTW/16 n + 8 g ..)
+        auto flush_f1 = [&](int g, int cnt) {
+          const int b0 = n * (NTW / 16) + 8 * g;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float* d = dtr + c * ep.Mw + b0;
+            if (cnt == 8 && ((b0 | ep.Mw) & 3) == 0) {
+              *reinterpret_cast<float4*>(d) = make_float4(f1[c][0], f1[c][1], f1[c][2], f1[c][3]);
+              *reinterpret_cast<float4*>(d + 4) = make_float4(f1[c][4], f1[c][5], f1[c][6], f1[c][7]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                if (q < cnt) d[q] = f1[c][q];
+            }
+          }
+        };
 #pragma unroll
         for (int cc = 0; cc < CPW; ++cc) {
           const int ch = hf * CPW + cc;
           if (ch < nch) {
             float v[16], v2[16];
             tmem_ld16(tl_base + (uint32_t)(j * 256 + ch * 16), v);
-            if (PC > 1) {
+            if (PC > 1 && !ONE_ACC) {
               tmem_ld16(tl_base + (uint32_t)(j * 256 + 128 + ch * 16), v2);
 #pragma unroll
               for (int k = 0; k < 16; ++k) v[k] += v2[k];
             }
-            const int ncol = n * kPNT + ch * 16;
+            const int ncol = n * NTW + ch * 16;
             if (rok) {
               if (EPI == TC_DT) {
                 // v = dE/dD[b][0..15], b = ncol / 16 (Eq. 2)
@@ -546,12 +573,14 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
                   float acc = 0.0f;
 #pragma unroll
                   for (int a = 0; a < 16; ++a) acc = fmaf(v[a], tl[c][a], acc);
-                  f1[c][ch] = acc;
+                  f1[c][ch & 7] = acc;
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
 #pragma unroll
                   for (int a = 0; a < 16; ++a) part[c][a] = fmaf(v[a], tb[c], part[c][a]);
+                // a full group of 8 with more chunks to follow: write it now
+                if ((cc & 7) == 7 && ch < nch - 1) flush_f1(cc >> 3, 8);
               } else {
                 const size_t o = (size_t)row * ep.ldo + ncol;
                 float rr[16], bb[16], tt[16], oh[16];
@@ -617,20 +646,9 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
         asm volatile("tcgen05.fence::before_thread_sync;\n");
         mbar_arrive(&t_empty[j]);
         if (EPI == TC_DT && rok) {
-          // first factor dE/dT[c][b] for this N tile's b = 8n .. 8n + nch - 1
-          const int b0 = n * (kPNT / 16);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            float* d = dtr + c * ep.Mw + b0;
-            if (nch == 8 && ((b0 | ep.Mw) & 3) == 0) {
-              *reinterpret_cast<float4*>(d) = make_float4(f1[c][0], f1[c][1], f1[c][2], f1[c][3]);
-              *reinterpret_cast<float4*>(d + 4) = make_float4(f1[c][4], f1[c][5], f1[c][6], f1[c][7]);
-            } else {
-#pragma unroll
-              for (int ch = 0; ch < 8; ++ch)
-                if (ch < nch) d[ch] = f1[c][ch];
-            }
-          }
+          // the last (possibly partial) group of first factors of this N tile
+          const int g = (nch - 1) >> 3;
+          flush_f1(g, nch - 8 * g);
         }
       }
       if (fail) break;
@@ -665,9 +683,10 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
   if (M <= 0) return 0;
   if (K <= 0 || K % kBK || K / kBK > kPMaxK || N <= 0 || N % 16) return -1;
   if (EPI != TC_DT && ep.ldo != N) return -1;
-  static_assert(PCfg<PC>::STAGE * 3 + 128 <= kPSmemMax, "three stages at least");
-  const int NS = PCfg<PC>::stages();
-  const size_t sm = PCfg<PC>::smem();
+  using CF = PCfg<PC, EPI == TC_DT ? 256 : kPNT>;  // the kernel's N tile width
+  static_assert(CF::STAGE * 3 + 128 <= kPSmemMax, "three stages at least");
+  const int NS = CF::stages();
+  const size_t sm = CF::smem();
   static std::atomic<size_t> set{0};  // launches from several host threads
   if (sm > set) {
     if (cudaFuncSetAttribute(k_tc_gemm_p<EPI, PC, TAB, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
