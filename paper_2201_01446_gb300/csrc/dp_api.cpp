@@ -2221,7 +2221,7 @@ dp_status dp_state_load(dp_handle* h, const char* path, dp_system** out) {
   bool ok = std::fread(magic, 1, 8, fp) == 8;
   const bool several = ok && std::memcmp(magic, "DPSTATE2", 8) == 0;
   ok = ok && (several || std::memcmp(magic, "DPSTATE1", 8) == 0) &&
-       std::fread(hdr, 8, 3, fp) == 3 && hdr[0] >= 0 && hdr[0] < (1LL << 40) &&
+       std::fread(hdr, 8, 3, fp) == 3 && hdr[0] >= 0 && hdr[0] < (1LL << 31) &&
        hdr[1] == h->ntypes_user;
   // several systems: their count, atom counts (summing to n) and boxes
   int64_t nsys = 0;
