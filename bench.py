@@ -16,7 +16,9 @@ JSON line fields beyond the base contract: roofline (dominant phase, live
 CUDA-event time), cpu_baseline (the FP64 oracle on a bounded sample of the
 same configuration, also giving the sampled force/energy error), e2e
 (through dp_system_create / dp_md_step / dp_system_get with host buffers),
-clocks (nvidia-smi sampled during the timed region).
+clocks (nvidia-smi sampled during the timed region); beside the headline:
+plain (the untabulated comparator), serve (the request loop), param_grad,
+water (MD of a replicated two-type water-like box).
 
 --impl reference runs the FP64 oracle (the correctness reference; there is
 no reference code to install) on a bounded sample of the same workload: MD
@@ -70,6 +72,10 @@ def parse():
                     help="copper cells per edge of the parameter-gradient leg (0: skip)")
     ap.add_argument("--ref-cells", type=int, default=20,
                     help="FCC cells per edge of the reference arm's oracle sample")
+    ap.add_argument("--water-reps", type=int, default=16,
+                    help="copies per edge of the 192-atom water box in the water leg (0: skip)")
+    ap.add_argument("--water-steps", type=int, default=3,
+                    help="timed 10-MD-step blocks of the water leg")
     ap.add_argument("--embed-precision", type=int, default=2,
                     help="tabulated contraction: 0 FP32 CUDA cores, 2 FP32-accurate tensor cores")
     return ap.parse_args()
@@ -223,6 +229,71 @@ def cpu_baseline_leg(model_path, xg, t, box, F_gpu, Ei_gpu, n_force=64, n_energy
             "sample": f"FP64 oracle on {n_force} force atoms (+{n_energy} energies) of the final "
                       f"{len(xg)}-atom configuration: ~{centres} atom evaluations in {dt:.1f} s"}
     return base, err
+
+
+def water_leg(args, stream, pg, world):
+    """MD of a two-type water-like box: the seeded 64-molecule box (192 atoms,
+    L = 12.417 A) replicated reps^3 times, rc 6 A, sel [46, 92], embedding
+    1-25-50-100, fitting 1600-240-240-240-1, dt 0.5 fs, rebuild every 10 steps.
+    Atom-steps/s and ns/day with the per-phase times and their fractions of
+    the FP32-lane and tensor peaks (the copper figures' definitions)."""
+    import torch
+    from paper_2201_01446_gb300 import dp
+    tmpdir = tempfile.mkdtemp()
+    wpath = os.path.join(tmpdir, "water.model")
+    inputs.write_seeded_model(wpath, inputs.WATER_SPEC, seed=4, std=0.1)
+    x0, t0, box0 = inputs.water_like(64, L=12.417, seed=3)
+    L0 = float(box0[0, 0])
+    r = args.water_reps
+    shifts = np.array([(i, j, k) for i in range(r) for j in range(r) for k in range(r)], float) * L0
+    x = (x0[None, :, :] + shifts[:, None, :]).reshape(-1, 3)
+    t = np.tile(t0, len(shifts)).astype(np.int32)
+    box = np.diag([r * L0] * 3)
+    n = len(x)
+    # zero initial velocities: the seeded model holds no molecule together,
+    # so thermal motion would carry atoms straight into one another (hundreds
+    # of pairs of the 786k atoms within 0.05 A in 20 fs); the work of a step
+    # (lists, pairs, table, fitting) is the same
+    v = np.zeros_like(x)
+    o = dp.dp_options_default()
+    o.fit_precision = args.fit_precision
+    o.embed_precision = args.embed_precision
+    h = dp.dp_create(wpath, 2, 6.0, 0.5, [46, 92], options=o, stream=C_stream(stream))
+    s = dp.dp_system_create(h, x, v, t, [inputs.MASS_O, inputs.MASS_H], box)
+    dt = 0.5
+    dp.dp_md_step(h, s, MD_PER_STEP, dt)
+    torch.cuda.synchronize()
+    barrier(pg)
+    dp.dp_profile(h, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.water_steps):
+        dp.dp_md_step(h, s, MD_PER_STEP, dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(pg, e0.elapsed_time(e1))
+    prof = dp.dp_profile_read(h)
+    stats = dp.dp_stats(h, s)
+    dp.dp_system_destroy(s)
+    dp.dp_destroy(h)
+    steps = MD_PER_STEP * args.water_steps
+    value = world * n * steps / (ms / 1e3)
+    units = flops_per_unit(M=100, din=1600)
+    ach = {k: units[k][1] * (stats["pairs_within_rc"] if units[k][0] == "pair" else n)
+           / (prof[k][0] / max(prof[k][1], 1) / 1e3) / 1e12 for k in units if prof[k][1]}
+    nprod = 6 if args.fit_precision == 2 else 1
+    bf16 = measured_peaks().get("bf16_tflops_sustained") or 1700.0
+    return {"value": value, "unit": UNIT, "natoms": n, "md_steps": steps, "dt_fs": dt,
+            "ns_per_day": value / world / n * dt * 86400 * 1e-6,
+            "ms_per_md_step": ms / steps,
+            "phases_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
+            "phases_achieved_tflops": ach,
+            "embed_fwd_frac_of_fp32_peak": ach.get("embed_contract_fwd", 0.0) / FP32_PEAK_TFLOPS,
+            "fitting_frac_of_tensor_peak": ach.get("fitting", 0.0) / (bf16 / nprod),
+            "pairs_within_rc": stats["pairs_within_rc"],
+            "workload": f"water-like 64-molecule box replicated {r}^3 ({n} atoms), rc 6 A, "
+                        "sel [46, 92], 1-25-50-100 / 1600-240-240-240-1, tabulated h=0.01 s<=2, "
+                        "zero initial velocities, dt 0.5 fs, rebuild every 10, skin 2 A"}
 
 
 def serve_leg(args, cu_model, pg):
@@ -465,6 +536,12 @@ def main():
         cpu, accuracy = cpu_baseline_leg(model, xg, t, box, F, Ei)
     dp.dp_destroy(h)
     grad_info = grad_leg(args, model, stream) if args.grad_cells > 0 else None
+    water_info = None
+    if args.water_reps > 0:
+        try:
+            water_info = water_leg(args, stream, pg, world)
+        except dp.DPError as e:  # a library error of this leg is reported, not fatal
+            water_info = {"error": str(e)}
     serve_info = serve_leg(args, model, pg) if args.serve_requests > 0 else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -481,7 +558,8 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": ck, "accuracy_vs_oracle": accuracy, "plain": plain,
-                "serve": serve_info, "param_grad": grad_info, "stats": stats}
+                "serve": serve_info, "param_grad": grad_info, "water": water_info,
+                "stats": stats}
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()
