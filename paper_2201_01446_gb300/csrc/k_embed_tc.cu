@@ -151,6 +151,40 @@ __device__ __forceinline__ int bin_begin16(const uint16_t* hist, int b) {
   return b ? hist[b - 1] : 0;
 }
 
+// A tile's occupied units (chunks of two bins, or windows of bins) as a
+// bitmask: the first set bit at or after c, or n when there is none.
+constexpr int kMaxOccWords = 64;  // 2048 units
+__device__ __forceinline__ int next_occ(const uint32_t* occ, int c, int n) {
+  for (int w = c >> 5; w * 32 < n; ++w) {
+    const uint32_t m = occ[w] & (w == (c >> 5) ? (0xffffffffu << (c & 31)) : 0xffffffffu);
+    if (m) {
+      const int k = w * 32 + __ffs(m) - 1;
+      return k < n ? k : n;
+    }
+  }
+  return n;
+}
+
+// bit u of occ: does any atom of the tile have a pair in bins [b0, b1) (of
+// the bin ends in shist)?  Units u = 0 .. n - 1 start at bin bs + width * u.
+__device__ __forceinline__ void mark_occupied(const uint16_t* shist, int nbp, int nbins, int bs,
+                                              int width, int n, uint32_t* occ, int warp,
+                                              int lane, int nwarps) {
+  for (int w = warp; w * 32 < n; w += nwarps) {
+    const int u = w * 32 + lane;
+    bool any = false;
+    if (u < n) {
+      const int b0 = min(bs + width * u, nbins), b1 = min(b0 + width, nbins);
+      for (int al = 0; al < kAtoms && !any && b1 > b0; ++al) {
+        const uint16_t* hist = shist + al * nbp;
+        any = hist[b1 - 1] > bin_begin16(hist, b0);
+      }
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, any);
+    if (lane == 0) occ[w] = m;
+  }
+}
+
 __device__ __forceinline__ int tile_type(const TileMap& tm, int64_t tile) {
   int ti = 0;
   while (ti + 1 < tm.ntypes && tile >= tm.tile_off[ti + 1]) ++ti;
@@ -300,6 +334,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort, s_lo, s_hi;
   __shared__ int s_atom[kAtoms];
+  __shared__ uint32_t s_occ[kMaxOccWords];  // occupied chunks of the tile's range
   volatile int* abort_flag = &s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -389,14 +424,21 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int q = tid; q < kAtoms * cf.nbp / 8; q += kThreads) __stcs(ho + q, hs[q]);
       if (tid == 0) range_out[tile] = make_int2(kb0, nk);
     }
+    // the chunks of the range with a pair: with several neighbor types (or
+    // gaps between neighbor shells) much of the range is empty, and the
+    // contraction skips those chunks (every role walks the same list)
+    mark_occupied(shist, cf.nbp, nbins, kb0, 2, nk, s_occ, warp, lane, kThreads / 32);
+    __syncthreads();
+    int nocc = 0;
+    for (int w = 0; w * 32 < nk; ++w) nocc += __popc(s_occ[w]);
     // ---- phase 2: T rows of the tile = C . table over the occupied bins
     if (nk > 0) {
       if (warp == 0) {
         if (lane == 0) {
           const __nv_bfloat16* Bt = tabF + (size_t)ti * tabF_ti + (size_t)(kb0 / 2) * kPC * NP * 16;
           uint32_t i = it;
-          int kc = 0;
-          for (; kc < nk; ++kc, ++i) {
+          int kc = next_occ(s_occ, 0, nk);
+          for (; kc < nk; kc = next_occ(s_occ, kc + 1, nk), ++i) {
             const int s = i % kNS;
             const uint32_t u = i / kNS;
             if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
@@ -415,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (lane == 0) {
           const uint32_t idesc = make_idesc_bf16(kRows, NP);
           uint32_t i = it;
-          for (int kc = 0; kc < nk; ++kc, ++i) {
+          for (int kc = 0; kc < nocc; ++kc, ++i) {  // kc: the index among the occupied
             const int s = i % kNS;
             const uint32_t u = i / kNS;
             if (!mbar_wait(&s_full[s], u & 1, abort_flag)) break;
@@ -470,14 +512,16 @@ __global__ void __launch_bounds__(kThreads, 2)
           }
         };
         int kbeg, kmid, kend;
-        bounds(0, kbeg, kmid, kend);
+        int kc = next_occ(s_occ, 0, nk);
+        bounds(kc, kbeg, kmid, kend);
         load4(kbeg, kend);
         uint32_t i = it;
-        for (int kc = 0; kc < nk; ++kc, ++i) {
+        for (; kc < nk; ++i) {
           const int s = i % kNS;
           const uint32_t u = i / kNS;
+          const int kn = next_occ(s_occ, kc + 1, nk);
           int nbeg = 0, nmid = 0, nend = 0;
-          if (kc + 1 < nk) bounds(kc + 1, nbeg, nmid, nend);
+          if (kn < nk) bounds(kn, nbeg, nmid, nend);
           float x[16];
 #pragma unroll
           for (int q = 0; q < 16; ++q) x[q] = 0.0f;
@@ -507,6 +551,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           kbeg = nbeg;
           kmid = nmid;
           kend = nend;
+          kc = kn;
           if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
           unsigned char* sa = base + (size_t)s * cf.stage;
 #pragma unroll
@@ -522,7 +567,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           mbar_arrive(&s_gen[s]);
         }
       }
-      it += nk;
+      it += nocc;
       if (!mbar_wait(&s_acc, acc_n & 1, nullptr)) *abort_flag = 1;
       ++acc_n;
       asm volatile("tcgen05.fence::after_thread_sync;\n");
@@ -624,6 +669,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   __shared__ int s_atom[kAtoms];
   __shared__ double s_vir[kThreads / 32][9];
   __shared__ double s_vt[kThreads / 32][9];  // this tile's virial per warp (vir_tile)
+  __shared__ uint32_t s_wocc[kMaxOccWords];  // windows of the range with a pair
   volatile int* abort_flag = &s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -668,6 +714,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int2 rg = range_in[tile];
     const int kb0 = rg.x, nbt = 2 * rg.y;  // bins kb0 .. kb0 + nbt - 1 (even count)
     __syncthreads();
+    // windows without a pair of any atom of the tile are skipped (by every
+    // warp alike: nothing of them is pipelined)
+    const int nwin = (nbt + kWin - 1) / kWin;
+    mark_occupied(shist, cf.nbp, nbins, kb0, kWin, nwin, s_wocc, warp, lane, kThreads / 32);
+    __syncthreads();
     float fxa[kAtoms / 8], fya[kAtoms / 8], fza[kAtoms / 8];
 #pragma unroll
     for (int j = 0; j < kAtoms / 8; ++j) fxa[j] = fya[j] = fza[j] = 0.0f;
@@ -675,6 +726,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
     for (int a = 0; a < 9; ++a) vl[a] = 0.0f;
     for (int w0 = kb0; w0 < kb0 + nbt; w0 += kWin) {
+      const int wi = (w0 - kb0) / kWin;
+      if (!((s_wocc[wi >> 5] >> (wi & 31)) & 1u)) continue;
       const int wb = min(kWin, kb0 + nbt - w0);  // even
       const int Wr = wb * 8;                     // MMA N (a multiple of 16)
       // ---- B window = dT . table^T on the tensor cores
@@ -1247,6 +1300,8 @@ int64_t tab_tc_hist_elems(const EnvParams& ep, int64_t ntile) {
 
 int tab_tc_supported(const EnvParams& ep) {
   if (ep.M > 128 || ep.M % 4 || ep.M < 16) return -1;
+  // the occupancy masks: at most 32 * kMaxOccWords chunks of two bins
+  if (ep.ntypes * ep.n_int + 2 > 2 * 32 * kMaxOccWords) return -2;
   if (fwd_cfg(ep).smem > 113 * 1024 || bwd_cfg(ep).smem > 113 * 1024) return -2;
 
   return 0;
