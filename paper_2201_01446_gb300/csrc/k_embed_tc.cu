@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       s_lo = INT_MAX;
       s_hi = -1;
     }
+    if (tid < kMaxOccWords) s_occ[tid] = 0;
     // the stage memory turns from the async proxy's (copies, MMAs) to phase 1's
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
@@ -401,9 +402,21 @@ __global__ void __launch_bounds__(kThreads, 2)
                                sc_cta + 4 * (size_t)kAtoms * scap + (size_t)al * scap, wstg,
                                pairs_out + ((size_t)tile * kAtoms + al) * scap, lane, nrange,
                                nover, lo, hi);
-      // bin ends of this atom (<= N_m + 32 < 2^16)
-      for (int b = lane; b < cf.nbp; b += 32)
-        shist[al * cf.nbp + b] = (uint16_t)(b < nbins ? whist[b] : 0);
+      // bin ends of this atom (<= N_m + 32 < 2^16), and the chunks (two bins,
+      // absolute index b / 2) in which it has a pair into the tile's mask
+      for (int b0 = 0; b0 < cf.nbp; b0 += 32) {
+        const int b = b0 + lane;
+        const int end = b < nbins ? whist[b] : 0;
+        if (b < cf.nbp) shist[al * cf.nbp + b] = (uint16_t)end;
+        const bool any = b < nbins && end > (b ? whist[b - 1] : 0);
+        uint32_t m = __ballot_sync(0xffffffffu, any);
+        m = (m | (m >> 1)) & 0x55555555u;  // chunk k's bit at 2k; compress to k
+        m = (m | (m >> 1)) & 0x33333333u;
+        m = (m | (m >> 2)) & 0x0f0f0f0fu;
+        m = (m | (m >> 4)) & 0x00ff00ffu;
+        m = (m | (m >> 8)) & 0x0000ffffu;
+        if (lane == 0 && m) atomicOr(&s_occ[b0 >> 6], m << ((b0 >> 1) & 31));
+      }
       npairs += (unsigned long long)np;
       lo = __reduce_min_sync(0xffffffffu, lo);
       hi = __reduce_max_sync(0xffffffffu, hi);
@@ -424,21 +437,22 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int q = tid; q < kAtoms * cf.nbp / 8; q += kThreads) __stcs(ho + q, hs[q]);
       if (tid == 0) range_out[tile] = make_int2(kb0, nk);
     }
-    // the chunks of the range with a pair: with several neighbor types (or
-    // gaps between neighbor shells) much of the range is empty, and the
-    // contraction skips those chunks (every role walks the same list)
-    mark_occupied(shist, cf.nbp, nbins, kb0, 2, nk, s_occ, warp, lane, kThreads / 32);
-    __syncthreads();
+    // the chunks of the range with a pair (s_occ, absolute chunk indices c0 +
+    // kc): with several neighbor types (or gaps between neighbor shells) much
+    // of the range is empty, and the contraction skips those chunks (every
+    // role walks the same list)
+    const int c0 = kb0 >> 1;
+    auto next_kc = [&](int kc) { return next_occ(s_occ, c0 + kc, c0 + nk) - c0; };
     int nocc = 0;
-    for (int w = 0; w * 32 < nk; ++w) nocc += __popc(s_occ[w]);
+    for (int kc = next_kc(0); kc < nk; kc = next_kc(kc + 1)) ++nocc;
     // ---- phase 2: T rows of the tile = C . table over the occupied bins
     if (nk > 0) {
       if (warp == 0) {
         if (lane == 0) {
           const __nv_bfloat16* Bt = tabF + (size_t)ti * tabF_ti + (size_t)(kb0 / 2) * kPC * NP * 16;
           uint32_t i = it;
-          int kc = next_occ(s_occ, 0, nk);
-          for (; kc < nk; kc = next_occ(s_occ, kc + 1, nk), ++i) {
+          int kc = next_kc(0);
+          for (; kc < nk; kc = next_kc(kc + 1), ++i) {
             const int s = i % kNS;
             const uint32_t u = i / kNS;
             if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
@@ -512,14 +526,14 @@ __global__ void __launch_bounds__(kThreads, 2)
           }
         };
         int kbeg, kmid, kend;
-        int kc = next_occ(s_occ, 0, nk);
+        int kc = next_kc(0);
         bounds(kc, kbeg, kmid, kend);
         load4(kbeg, kend);
         uint32_t i = it;
         for (; kc < nk; ++i) {
           const int s = i % kNS;
           const uint32_t u = i / kNS;
-          const int kn = next_occ(s_occ, kc + 1, nk);
+          const int kn = next_kc(kc + 1);
           int nbeg = 0, nmid = 0, nend = 0;
           if (kn < nk) bounds(kn, nbeg, nmid, nend);
           float x[16];
