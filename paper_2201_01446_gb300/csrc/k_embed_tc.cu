@@ -443,8 +443,13 @@ __global__ void __launch_bounds__(kThreads, 2)
     // role walks the same list)
     const int c0 = kb0 >> 1;
     auto next_kc = [&](int kc) { return next_occ(s_occ, c0 + kc, c0 + nk) - c0; };
-    int nocc = 0;
-    for (int kc = next_kc(0); kc < nk; kc = next_kc(kc + 1)) ++nocc;
+    int nocc = 0;  // popcount of the mask over [c0, c0 + nk)
+    for (int w = c0 >> 5; nk > 0 && w <= (c0 + nk - 1) >> 5; ++w) {
+      uint32_t m = s_occ[w];
+      if (w == c0 >> 5) m &= 0xffffffffu << (c0 & 31);
+      if (w == (c0 + nk - 1) >> 5) m &= 0xffffffffu >> (31 - ((c0 + nk - 1) & 31));
+      nocc += __popc(m);
+    }
     // ---- phase 2: T rows of the tile = C . table over the occupied bins
     if (nk > 0) {
       if (warp == 0) {
