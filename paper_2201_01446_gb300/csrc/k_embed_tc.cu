@@ -375,7 +375,6 @@ __global__ void __launch_bounds__(kThreads, 2)
       s_lo = INT_MAX;
       s_hi = -1;
     }
-    if (tid < kMaxOccWords) s_occ[tid] = 0;
     // the stage memory turns from the async proxy's (copies, MMAs) to phase 1's
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
@@ -402,21 +401,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                                sc_cta + 4 * (size_t)kAtoms * scap + (size_t)al * scap, wstg,
                                pairs_out + ((size_t)tile * kAtoms + al) * scap, lane, nrange,
                                nover, lo, hi);
-      // bin ends of this atom (<= N_m + 32 < 2^16), and the chunks (two bins,
-      // absolute index b / 2) in which it has a pair into the tile's mask
-      for (int b0 = 0; b0 < cf.nbp; b0 += 32) {
-        const int b = b0 + lane;
-        const int end = b < nbins ? whist[b] : 0;
-        if (b < cf.nbp) shist[al * cf.nbp + b] = (uint16_t)end;
-        const bool any = b < nbins && end > (b ? whist[b - 1] : 0);
-        uint32_t m = __ballot_sync(0xffffffffu, any);
-        m = (m | (m >> 1)) & 0x55555555u;  // chunk k's bit at 2k; compress to k
-        m = (m | (m >> 1)) & 0x33333333u;
-        m = (m | (m >> 2)) & 0x0f0f0f0fu;
-        m = (m | (m >> 4)) & 0x00ff00ffu;
-        m = (m | (m >> 8)) & 0x0000ffffu;
-        if (lane == 0 && m) atomicOr(&s_occ[b0 >> 6], m << ((b0 >> 1) & 31));
-      }
+      // bin ends of this atom (<= N_m + 32 < 2^16)
+      for (int b = lane; b < cf.nbp; b += 32)
+        shist[al * cf.nbp + b] = (uint16_t)(b < nbins ? whist[b] : 0);
       npairs += (unsigned long long)np;
       lo = __reduce_min_sync(0xffffffffu, lo);
       hi = __reduce_max_sync(0xffffffffu, hi);
@@ -437,19 +424,21 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int q = tid; q < kAtoms * cf.nbp / 8; q += kThreads) __stcs(ho + q, hs[q]);
       if (tid == 0) range_out[tile] = make_int2(kb0, nk);
     }
-    // the chunks of the range with a pair (s_occ, absolute chunk indices c0 +
-    // kc): with several neighbor types (or gaps between neighbor shells) much
-    // of the range is empty, and the contraction skips those chunks (every
-    // role walks the same list)
-    const int c0 = kb0 >> 1;
-    auto next_kc = [&](int kc) { return next_occ(s_occ, c0 + kc, c0 + nk) - c0; };
-    int nocc = 0;  // popcount of the mask over [c0, c0 + nk)
-    for (int w = c0 >> 5; nk > 0 && w <= (c0 + nk - 1) >> 5; ++w) {
-      uint32_t m = s_occ[w];
-      if (w == c0 >> 5) m &= 0xffffffffu << (c0 & 31);
-      if (w == (c0 + nk - 1) >> 5) m &= 0xffffffffu >> (31 - ((c0 + nk - 1) & 31));
-      nocc += __popc(m);
-    }
+    // the chunks of the range with a pair (bit kc of s_occ): with several
+    // neighbor types the range spans every type's section of the bins and
+    // much of it is empty, and the contraction skips those chunks (every role
+    // walks the same list).  With one neighbor type the occupied bins form
+    // one thermally broadened band; there the pass costs more than it saves
+    // (measured on 4M-atom copper) and every chunk of the range is taken.
+    if (ep.ntypes > 1)
+      mark_occupied(shist, cf.nbp, nbins, kb0, 2, nk, s_occ, warp, lane, kThreads / 32);
+    else if (tid < kMaxOccWords)
+      s_occ[tid] = 0xffffffffu;
+    __syncthreads();
+    auto next_kc = [&](int kc) { return next_occ(s_occ, kc, nk); };
+    int nocc = 0;  // popcount of the mask over [0, nk)
+    for (int w = 0; w * 32 < nk; ++w)
+      nocc += __popc(s_occ[w] & (nk - w * 32 >= 32 ? 0xffffffffu : (1u << (nk - w * 32)) - 1u));
     // ---- phase 2: T rows of the tile = C . table over the occupied bins
     if (nk > 0) {
       if (warp == 0) {
@@ -736,7 +725,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     // windows without a pair of any atom of the tile are skipped (by every
     // warp alike: nothing of them is pipelined)
     const int nwin = (nbt + kWin - 1) / kWin;
-    mark_occupied(shist, cf.nbp, nbins, kb0, kWin, nwin, s_wocc, warp, lane, kThreads / 32);
+    if (ep.ntypes > 1)
+      mark_occupied(shist, cf.nbp, nbins, kb0, kWin, nwin, s_wocc, warp, lane, kThreads / 32);
+    else if (tid < kMaxOccWords)
+      s_wocc[tid] = 0xffffffffu;  // one neighbor type: one band (see the forward)
     __syncthreads();
     float fxa[kAtoms / 8], fya[kAtoms / 8], fza[kAtoms / 8];
 #pragma unroll
