@@ -314,6 +314,9 @@ __device__ __forceinline__ int sort_atom(int atom, int jb, const float4* __restr
   return np;
 }
 
+// COMPACT: contract only the occupied chunks of a tile's range (several
+// neighbor types); otherwise every chunk of the range
+template <bool COMPACT>
 __global__ void __launch_bounds__(kThreads, 2)
     k_tab_fwd_tc(int64_t ntile, TileMap tm, const float4* __restrict__ off,
                  const uint32_t* __restrict__ nlist, const int32_t* __restrict__ nn, int cap,
@@ -430,15 +433,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     // walks the same list).  With one neighbor type the occupied bins form
     // one thermally broadened band; there the pass costs more than it saves
     // (measured on 4M-atom copper) and every chunk of the range is taken.
-    if (ep.ntypes > 1)
+    int nocc = nk;
+    if (COMPACT) {
       mark_occupied(shist, cf.nbp, nbins, kb0, 2, nk, s_occ, warp, lane, kThreads / 32);
-    else if (tid < kMaxOccWords)
-      s_occ[tid] = 0xffffffffu;
-    __syncthreads();
-    auto next_kc = [&](int kc) { return next_occ(s_occ, kc, nk); };
-    int nocc = 0;  // popcount of the mask over [0, nk)
-    for (int w = 0; w * 32 < nk; ++w)
-      nocc += __popc(s_occ[w] & (nk - w * 32 >= 32 ? 0xffffffffu : (1u << (nk - w * 32)) - 1u));
+      __syncthreads();
+      nocc = 0;  // popcount of the mask over [0, nk)
+      for (int w = 0; w * 32 < nk; ++w)
+        nocc += __popc(s_occ[w] & (nk - w * 32 >= 32 ? 0xffffffffu : (1u << (nk - w * 32)) - 1u));
+    }
+    auto next_kc = [&](int kc) { return COMPACT ? next_occ(s_occ, kc, nk) : kc; };
     // ---- phase 2: T rows of the tile = C . table over the occupied bins
     if (nk > 0) {
       if (warp == 0) {
@@ -657,6 +660,7 @@ __host__ __device__ inline BwdCfg bwd_cfg(const EnvParams& ep) {
   return c;
 }
 
+template <bool COMPACT>  // skip windows without a pair (several neighbor types)
 __global__ void __launch_bounds__(kThreads, 2)
     k_tab_bwd_tc(int64_t ntile, TileMap tm, const float4* __restrict__ pairs,
                  const uint16_t* __restrict__ hist_in, const int2* __restrict__ range_in,
@@ -724,12 +728,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     // windows without a pair of any atom of the tile are skipped (by every
     // warp alike: nothing of them is pipelined)
-    const int nwin = (nbt + kWin - 1) / kWin;
-    if (ep.ntypes > 1)
+    if (COMPACT) {
+      const int nwin = (nbt + kWin - 1) / kWin;
       mark_occupied(shist, cf.nbp, nbins, kb0, kWin, nwin, s_wocc, warp, lane, kThreads / 32);
-    else if (tid < kMaxOccWords)
-      s_wocc[tid] = 0xffffffffu;  // one neighbor type: one band (see the forward)
-    __syncthreads();
+      __syncthreads();
+    }
     float fxa[kAtoms / 8], fya[kAtoms / 8], fza[kAtoms / 8];
 #pragma unroll
     for (int j = 0; j < kAtoms / 8; ++j) fxa[j] = fya[j] = fza[j] = 0.0f;
@@ -738,7 +741,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int a = 0; a < 9; ++a) vl[a] = 0.0f;
     for (int w0 = kb0; w0 < kb0 + nbt; w0 += kWin) {
       const int wi = (w0 - kb0) / kWin;
-      if (!((s_wocc[wi >> 5] >> (wi & 31)) & 1u)) continue;
+      if (COMPACT && !((s_wocc[wi >> 5] >> (wi & 31)) & 1u)) continue;
       const int wb = min(kWin, kb0 + nbt - w0);  // even
       const int Wr = wb * 8;                     // MMA N (a multiple of 16)
       // ---- B window = dT . table^T on the tensor cores
@@ -1224,19 +1227,21 @@ int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, con
   if (ntile <= 0) return 0;
   const FwdCfg cf = fwd_cfg(ep);
   if (cf.smem > 113 * 1024) return -1;  // two CTAs per SM
-  static std::atomic<size_t> set{0};  // launches from several host threads
-  if (cf.smem > 48 * 1024 && cf.smem > set) {
-    if (cudaFuncSetAttribute(k_tab_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const bool compact = ep.ntypes > 1;
+  auto kern = compact ? k_tab_fwd_tc<true> : k_tab_fwd_tc<false>;
+  static std::atomic<size_t> set[2] = {{0}, {0}};  // launches from several host threads
+  if (cf.smem > 48 * 1024 && cf.smem > set[compact]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)cf.smem) != cudaSuccess)
       return -3;
-    set = cf.smem;
+    set[compact] = cf.smem;
   }
   const int grid = (int)(ntile < tc_grid() ? ntile : tc_grid());
   DP_LAUNCHED(1);
-  k_tab_fwd_tc<<<grid, kThreads, cf.smem, st>>>(ntile, tm, off, nlist, nn, cap, g, ep, tabF,
-                                                stage_cap_tc(ep), scratch, pairs_out, hist_out,
-                                                range_out, T, status, pair_count, sys_of,
-                                                sys_base, sys_edge);
+  kern<<<grid, kThreads, cf.smem, st>>>(ntile, tm, off, nlist, nn, cap, g, ep, tabF,
+                                        stage_cap_tc(ep), scratch, pairs_out, hist_out,
+                                        range_out, T, status, pair_count, sys_of, sys_base,
+                                        sys_edge);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -1255,18 +1260,20 @@ int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs,
   if (ntile <= 0) return 0;
   const BwdCfg cf = bwd_cfg(ep);
   if (cf.smem > 113 * 1024) return -1;  // two CTAs per SM
-  static std::atomic<size_t> set{0};  // launches from several host threads
-  if (cf.smem > 48 * 1024 && cf.smem > set) {
-    if (cudaFuncSetAttribute(k_tab_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const bool compact = ep.ntypes > 1;
+  auto kern = compact ? k_tab_bwd_tc<true> : k_tab_bwd_tc<false>;
+  static std::atomic<size_t> set[2] = {{0}, {0}};  // launches from several host threads
+  if (cf.smem > 48 * 1024 && cf.smem > set[compact]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)cf.smem) != cudaSuccess)
       return -3;
-    set = cf.smem;
+    set[compact] = cf.smem;
   }
   // every slot is written (grid = the full persistent grid, idle CTAs write zeros)
   DP_LAUNCHED(1);
-  k_tab_bwd_tc<<<tc_grid(), kThreads, cf.smem, st>>>(ntile, tm, pairs, hist, range, ep, tabB,
-                                                     stage_cap_tc(ep), dT, ffix, vir_part, status,
-                                                     vir_tile);
+  kern<<<tc_grid(), kThreads, cf.smem, st>>>(ntile, tm, pairs, hist, range, ep, tabB,
+                                             stage_cap_tc(ep), dT, ffix, vir_part, status,
+                                             vir_tile);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
