@@ -358,9 +358,7 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
   // 24 KB for 3.1), and all six piece products then share one accumulator
   // (2 x 256 TMEM columns, still double-buffered; measured 62.5 -> 60.5 ms of
   // fitting per 4M-atom step, force errors within the FP32 bars).  The other
-  // layers keep the h*h products in their own accumulator.  What bounds
-  // these GEMMs is shared-memory bandwidth: every 128x256x16 MMA reads 12 KB
-  // of operands while the copies write 6 KB, close to the SM's ~128 B/clock.
+  // layers keep the h*h products in their own accumulator.
   constexpr int NTW = EPI == TC_DT ? 256 : kPNT;
   constexpr bool ONE_ACC = NTW == 256;
   using C = PCfg<PC, NTW>;
