@@ -525,12 +525,24 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
       bool fail = false;
       for (int n = 0; n < ntn; ++n, ++ti) {
         const int j = ti & 1;
+        const int nt = min(NTW, N - n * NTW), nch = nt / 16;
+        // TC_DT: T[c][b] of the row for chunk b - NTW/16 n, two chunks ahead in
+        // a ring of three (the first two issued before the accumulator wait)
+        float tq[3][4];
+        auto load_tb = [&](int slot, int chn) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            tq[slot][c] = chn < nch ? __ldg(tr + c * ep.Mw + n * (NTW / 16) + chn) : 0.0f;
+        };
+        if (EPI == TC_DT && rok) {
+          load_tb(0, hf * CPW);
+          load_tb(1, hf * CPW + 1);
+        }
         if (!mbar_wait(&t_full[j], (ti >> 1) & 1, abort_flag)) {
           fail = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n");
-        const int nt = min(NTW, N - n * NTW), nch = nt / 16;
         float f1[4][8];  // the first factor of dE/dT for 8 chunks (b) at a time
         // dE/dT[c][b] for the chunk group g of this N tile (b = NTW/16 n + 8 g ..)
         auto flush_f1 = [&](int g, int cnt) {
@@ -563,11 +575,11 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
             if (rok) {
               if (EPI == TC_DT) {
                 // v = dE/dD[b][0..15], b = ncol / 16 (Eq. 2)
-                const int b = ncol >> 4;
+                if (cc + 2 < CPW) load_tb((cc + 2) % 3, ch + 2);
                 float tb[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                  tb[c] = __ldg(tr + c * ep.Mw + b);
+                  tb[c] = tq[cc % 3][c];  // T[c][b], b = ncol / 16
                   float acc = 0.0f;
 #pragma unroll
                   for (int a = 0; a < 16; ++a) acc = fmaf(v[a], tl[c][a], acc);
