@@ -78,9 +78,10 @@ typedef struct {
   double s_ext;        /* table extrapolation region: beyond the first region
                           [0, n_fine*h], n_fine = ceil(s_max/h), intervals of
                           width ext_stride*h up to the first node >= s_ext;
-                          [0.0] none (s_ext <= n_fine*h) */
-  int ext_stride;      /* width of the extrapolation intervals in units of h
-                          (>= 1) [10] */
+                          [0.0] none (s_ext <= n_fine*h); negative is
+                          DP_ERR_ARG */
+  int ext_stride;      /* width of the extrapolation intervals in units of h,
+                          1 .. 1000 (DP_ERR_ARG otherwise) [10] */
 } dp_options;
 
 /* Thermodynamic record of one MD step (Sec. 4). */
