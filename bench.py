@@ -242,13 +242,8 @@ def water_leg(args, stream, pg, world):
     tmpdir = tempfile.mkdtemp()
     wpath = os.path.join(tmpdir, "water.model")
     inputs.write_seeded_model(wpath, inputs.WATER_SPEC, seed=4, std=0.1)
-    x0, t0, box0 = inputs.water_like(64, L=12.417, seed=3)
-    L0 = float(box0[0, 0])
     r = args.water_reps
-    shifts = np.array([(i, j, k) for i in range(r) for j in range(r) for k in range(r)], float) * L0
-    x = (x0[None, :, :] + shifts[:, None, :]).reshape(-1, 3)
-    t = np.tile(t0, len(shifts)).astype(np.int32)
-    box = np.diag([r * L0] * 3)
+    x, t, box = inputs.replicate(*inputs.water_like(64, L=12.417, seed=3), r)
     n = len(x)
     # zero initial velocities: the seeded model holds no molecule together,
     # so thermal motion would carry atoms straight into one another (hundreds

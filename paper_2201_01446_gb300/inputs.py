@@ -159,6 +159,19 @@ def _random_rotation(rng):
         [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
 
 
+def replicate(x, types, box, reps: int):
+    """The periodic system (x [n, 3], types [n], orthorhombic box) repeated
+    reps times along each axis: copy (i, j, k) is x shifted by (i, j, k) box
+    edges, one copy after another; the box grows reps-fold per edge.  Every
+    atom keeps the environment it has in the original periodic system."""
+    L = np.diag(np.asarray(box, np.float64))
+    shifts = np.array([(i, j, k) for i in range(reps) for j in range(reps)
+                       for k in range(reps)], np.float64) * L
+    xr = (np.asarray(x, np.float64)[None, :, :] + shifts[:, None, :]).reshape(-1, 3)
+    tr = np.tile(np.asarray(types, np.int32), len(shifts))
+    return np.ascontiguousarray(xr), tr, np.diag(L * reps)
+
+
 def water_like(nmol: int = 64, L: float = 12.417, seed: int = 3,
                d_oh: float = 0.96, angle_deg: float = 104.5,
                min_oo: float = 2.5, min_inter: float = 1.4, max_tries: int = 200000):
