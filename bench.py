@@ -246,9 +246,9 @@ def water_leg(args, stream, pg, world):
     x, t, box = inputs.replicate(*inputs.water_like(64, L=12.417, seed=3), r)
     n = len(x)
     # zero initial velocities: the seeded model holds no molecule together,
-    # so thermal motion would carry atoms straight into one another (hundreds
-    # of pairs of the 786k atoms within 0.05 A in 20 fs); the work of a step
-    # (lists, pairs, table, fitting) is the same
+    # so thermal motion carries atoms straight into one another (at 330 K a
+    # dozen pairs of the 786k atoms came within 0.05 A in 20 fs); the work of
+    # a step (lists, pairs, table, fitting) is the same
     v = np.zeros_like(x)
     o = dp.dp_options_default()
     o.fit_precision = args.fit_precision
