@@ -334,7 +334,8 @@ dp_status dp_stats(dp_handle* h, const dp_system* s, int64_t* out);
  *               DP_ERR_CAPACITY).
  *   cap, out5   DEVICE [cap][5] int32 rows (i, j, n0, n1, n2) as in
  *               dp_neighbor_pairs; rows past cap are not written.
- *   count       HOST: receives the total number of pairs.
+ *   count       HOST: receives the total number of pairs (64-bit; it
+ *               may exceed 2^31, e.g. for a box of edge close to rlist).
  *   stream      cudaStream_t (NULL = legacy default); the call returns after
  *               the stream has finished its work.
  * All intermediates live in one fixed device array of about 5 MB that every

@@ -1141,7 +1141,10 @@ void dp_options_default(dp_options* o) {
   o->ext_stride = 10;
 }
 
-const char* dp_version(void) { return "dp-gb300 0.1 (sm_103a; tabulated FP32 embedding, FP32 SIMT fitting)"; }
+const char* dp_version(void) {
+  return "dp-gb300 0.2 (sm_103a; tabulated embedding and fitting net on FP32 CUDA cores or "
+         "tcgen05 tensor cores)";
+}
 
 const char* dp_last_error(const dp_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 

@@ -15,6 +15,7 @@
 // threads without ordering) race on it.  The first call on a device looks
 // up the array's device address (cudaGetSymbolAddress) with that device
 // current; make that first call before any stream capture.
+#include <cmath>
 #include <mutex>
 
 #include "dp_internal.h"
@@ -33,8 +34,8 @@ constexpr size_t kOffAtoms = align256(kOffTmp + sizeof(int) * kStaticMaxAtoms);
 constexpr size_t kOffOff = align256(kOffAtoms + sizeof(int) * kStaticMaxAtoms);  // float4 [N]
 constexpr size_t kOffTypes = align256(kOffOff + sizeof(float4) * kStaticMaxAtoms);
 constexpr size_t kOffCnt = align256(kOffTypes + sizeof(int) * kStaticMaxAtoms);
-constexpr size_t kOffRow = align256(kOffCnt + sizeof(int) * kStaticMaxAtoms);  // [N+1]
-constexpr size_t kOffCellCount = align256(kOffRow + sizeof(int) * (kStaticMaxAtoms + 1));
+constexpr size_t kOffRow = align256(kOffCnt + sizeof(int) * kStaticMaxAtoms);  // int64 [N+1]
+constexpr size_t kOffCellCount = align256(kOffRow + sizeof(int64_t) * (kStaticMaxAtoms + 1));
 constexpr size_t kOffCellFill = align256(kOffCellCount + sizeof(int) * (kStaticMaxCells + 1));
 constexpr size_t kOffCellStart = align256(kOffCellFill + sizeof(int) * (kStaticMaxCells + 1));
 constexpr size_t kStaticBytes = align256(kOffCellStart + sizeof(int) * (kStaticMaxCells + 1));
@@ -59,6 +60,48 @@ dp_status static_scratch(unsigned char** out) {
   return DP_OK;
 }
 
+// row offsets of the atoms' pair rows: start[i] = sum of cnt[k < i] and
+// start[n] = the total, in 64-bit integers (65536 atoms in a box of edge
+// rlist see 27 images of every atom: ~1.2e11 rows, past any 32-bit offset).
+// One block; thread t scans its contiguous run of atoms, the runs' totals
+// are scanned across the block, then each run is written.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_static_scan64(const int32_t* __restrict__ cnt,
+                                                                int n,
+                                                                int64_t* __restrict__ start) {
+  __shared__ int64_t warp_tot[kScanThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int per = (n + kScanThreads - 1) / kScanThreads;
+  const int b = min(n, t * per), e = min(n, b + per);
+  int64_t run = 0;
+  for (int k = b; k < e; ++k) run += cnt[k];
+  // inclusive scan of the runs within the warp, then across the warps
+  int64_t inc = run;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int64_t v = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += v;
+  }
+  if (lane == 31) warp_tot[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t w = warp_tot[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int64_t v = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += v;
+    }
+    warp_tot[lane] = w;  // inclusive totals of warps 0..lane
+  }
+  __syncthreads();
+  int64_t acc = inc - run + (wid > 0 ? warp_tot[wid - 1] : 0);
+  for (int k = b; k < e; ++k) {
+    start[k] = acc;
+    acc += cnt[k];
+  }
+  if (t == kScanThreads - 1) start[n] = warp_tot[kScanThreads / 32 - 1];
+}
+
 // pairs of atom i within rlist, counted (rows == nullptr) or written as
 // (i, j, n0, n1, n2) rows from row_start[i] on (rows past cap are dropped);
 // one warp per atom in cell order, the same tests as the list build
@@ -66,7 +109,7 @@ __global__ void __launch_bounds__(128) k_static_pairs(
     int n, const double* __restrict__ x, const int32_t* __restrict__ cellc,
     const float4* __restrict__ off, const int32_t* __restrict__ cell_start,
     const int32_t* __restrict__ cell_atoms, CellGeom g, double rlist, int32_t* __restrict__ cnt,
-    const int32_t* __restrict__ row_start, int64_t cap, int32_t* __restrict__ rows) {
+    const int64_t* __restrict__ row_start, int64_t cap, int32_t* __restrict__ rows) {
   const int lane = threadIdx.x & 31;
   const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (w >= n) return;
@@ -117,8 +160,8 @@ __global__ void __launch_bounds__(128) k_static_pairs(
       }
       const unsigned m = __ballot_sync(0xffffffffu, in);
       if (in && rows) {
-        const int64_t r = (int64_t)row_start[i] + c + __popc(m & below);
-        if (r < cap) {
+        const int64_t r = row_start[i] + c + __popc(m & below);
+        if (r >= 0 && r < cap) {
           int32_t* q = rows + r * 5;
           q[0] = i;
           q[1] = j;
@@ -151,9 +194,11 @@ extern "C" dp_status dp_neighbor_pairs_static(int64_t natoms, const double* coor
     const double L = box[a * 4];
     if (!(L > 0.0) || L < rlist) return DP_ERR_BOX;
     g.L[a] = L;
-    int nc = (int)(L / rlist);
+    // compared as a double first: a huge L / rlist must not reach the int
+    const double ncd = std::floor(L / rlist);
+    if (!(ncd <= (double)kStaticMaxCells)) return DP_ERR_CAPACITY;
+    const int nc = (int)ncd;
     g.nc[a] = nc < 1 ? 1 : nc;
-    if (g.nc[a] > kStaticMaxCells) return DP_ERR_CAPACITY;
     g.edge[a] = L / g.nc[a];
     g.edgef[a] = (float)g.edge[a];
     ncell *= g.nc[a];
@@ -174,7 +219,7 @@ extern "C" dp_status dp_neighbor_pairs_static(int64_t natoms, const double* coor
   float4* off = reinterpret_cast<float4*>(sc + kOffOff);
   int32_t* types = reinterpret_cast<int32_t*>(sc + kOffTypes);
   int32_t* cnt = reinterpret_cast<int32_t*>(sc + kOffCnt);
-  int32_t* row = reinterpret_cast<int32_t*>(sc + kOffRow);
+  int64_t* row = reinterpret_cast<int64_t*>(sc + kOffRow);
   int32_t* ccount = reinterpret_cast<int32_t*>(sc + kOffCellCount);
   int32_t* cfill = reinterpret_cast<int32_t*>(sc + kOffCellFill);
   int32_t* cstart = reinterpret_cast<int32_t*>(sc + kOffCellStart);
@@ -193,13 +238,13 @@ extern "C" dp_status dp_neighbor_pairs_static(int64_t natoms, const double* coor
   const int blocks = (int)(((int64_t)n * 32 + 127) / 128);
   k_static_pairs<<<blocks, 128, 0, s>>>(n, xw, cellc, off, cstart, atoms, g, rlist, cnt, nullptr, 0,
                                        nullptr);
-  launch_scan(s, cnt, row, n);
+  k_static_scan64<<<1, kScanThreads, 0, s>>>(cnt, n, row);
   k_static_pairs<<<blocks, 128, 0, s>>>(n, xw, cellc, off, cstart, atoms, g, rlist, cnt, row, cap,
                                        out5);
-  DP_LAUNCHED(2);
-  int32_t total = 0;
+  DP_LAUNCHED(3);
+  int64_t total = 0;
   if (cudaGetLastError() != cudaSuccess ||
-      cudaMemcpyAsync(&total, row + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&total, row + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return DP_ERR_CUDA;
   *count = total;

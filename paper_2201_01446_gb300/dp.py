@@ -341,16 +341,27 @@ def dp_stats(h, s=None):
                 pairs_within_rc=int(out[3]), cells=int(out[4]), kernel_launches=int(out[5]))
 
 
-def dp_neighbor_pairs_static(coords, box, rlist, stream=None):
+def dp_neighbor_pairs_static(coords, box, rlist, stream=None, out=None):
     """Pair rows (i, j, n0, n1, n2) of a CUDA float64 tensor of positions,
     computed by the library without allocating device memory (its scratch
-    is a fixed array).  The output tensor is allocated here by torch, on
-    the caller's side of the call; the first call returns only the count."""
+    is a fixed array).  Without out, the output tensor is allocated here by
+    torch, on the caller's side of the call (a first call returns only the
+    count) and the rows are returned.  With out (a CUDA int32 tensor [cap][5],
+    cap >= 0), one call writes at most cap rows into it and (out, total
+    count) is returned."""
     import torch
     assert coords.is_cuda and coords.dtype == torch.float64 and coords.is_contiguous()
     n = int(coords.shape[0])
     b = np.ascontiguousarray(box, np.float64)
     cnt = C.c_int64()
+    if out is not None:
+        assert out.is_cuda and out.dtype == torch.int32 and out.is_contiguous()
+        cap = int(out.shape[0])
+        _check(lib.dp_neighbor_pairs_static(n, C.c_void_p(coords.data_ptr()),
+                                            b.ctypes.data_as(C.c_void_p), float(rlist), cap,
+                                            C.c_void_p(out.data_ptr()) if cap else None,
+                                            C.byref(cnt), stream), None)
+        return out, cnt.value
     _check(lib.dp_neighbor_pairs_static(n, C.c_void_p(coords.data_ptr()),
                                         b.ctypes.data_as(C.c_void_p), float(rlist), 0, None,
                                         C.byref(cnt), stream), None)

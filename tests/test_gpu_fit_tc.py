@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_2201_01446_gb300 import inputs
-from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, PARITY_LOG, TABLE_H, rmse
+from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, PARITY_LOG, TABLE_H, force_bar, rmse
 
 pytestmark = pytest.mark.gpu
 
@@ -134,7 +134,7 @@ def test_split_mode_end_to_end(dp, cu_model_path, cu_stress_path):
                                dE_per_atom=de, force_rmse=fr, force_rms=frms))
         # the FP32 path's bars (configured: absolute; stress: FP32-relative)
         if not stress:
-            assert de < 1e-6 and fr < 1e-5, (de, fr)
+            assert de < 1e-6 and fr <= force_bar(frms), (de, fr, frms)
         else:
             assert de < max(1e-6, 2e-6 * float(np.abs(r["atom_energy"]).mean())), de
             assert fr < max(1e-5, 3e-5 * frms), (fr, frms)

@@ -8,19 +8,21 @@ import pytest
 
 import oracle
 from paper_2201_01446_gb300 import inputs
-from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, PARITY_LOG, TABLE_H
+from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, PARITY_LOG, TABLE_H, force_bar
 
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [0, 2])
-def test_fullsize_4m_copper_sampled(cu_model_path, prec):
-    # fit_precision 0: FP32 CUDA cores; 2: FP32-accurate tensor cores (the bench's mode)
+@pytest.mark.parametrize("prec,embed", [(0, 0), (2, 2)])
+def test_fullsize_4m_copper_sampled(cu_model_path, prec, embed):
+    # (0, 0): FP32 CUDA cores; (2, 2): FP32-accurate tensor cores for the
+    # fitting net and the tabulated contraction (the bench's modes)
     from paper_2201_01446_gb300 import dp
     x, t, box = inputs.fcc_copper(100, sigma=0.0)
     v = inputs.maxwell_velocities(np.full(len(x), inputs.MASS_CU), 330.0, seed=2)
     o = dp.dp_options_default()
     o.fit_precision = prec
+    o.embed_precision = embed
     h = dp.dp_create(cu_model_path, 1, CU_RC, CU_RCS, [CU_SEL], options=o, stream=None)
     try:
         s = dp.dp_system_create(h, x, v, t, [inputs.MASS_CU], box)
@@ -40,12 +42,12 @@ def test_fullsize_4m_copper_sampled(cu_model_path, prec):
     e_ref, f_ref = oracle.eval_subset(m, tab, CU_RC, CU_RCS, CU_SEL, xg, t, box, ie, jf)
     de = np.abs(Ei[ie] - e_ref)
     df = np.sqrt(((F[jf] - f_ref) ** 2).mean())
-    PARITY_LOG.append(dict(case=f"fullsize Cu 4M (sampled) fit_precision {prec}", natoms=len(x),
+    PARITY_LOG.append(dict(case=f"fullsize Cu 4M (sampled) fit {prec} embed {embed}", natoms=len(x),
                            stress=False,
                            max_dEi=float(de.max()), force_rmse=float(df),
                            force_rms=float(np.sqrt((f_ref ** 2).mean()))))
     assert de.max() < 1e-6
-    assert df < 1e-5
+    assert df <= force_bar(float(np.sqrt((f_ref ** 2).mean()))), df
 
 
 @pytest.mark.parametrize("which", ["configured", "stress"])
@@ -82,3 +84,57 @@ def test_config3_bf16_fitting_stated(cu_model_path, cu_stress_path, which):
     # epilogue would exceed by far
     assert rmse_e < 3e-2 * max(1.0, float(np.abs(e_ref).mean()))
     assert rmse_f < 0.5 * frms + 1e-9
+
+
+def test_fullsize_4m_stress_every_atom_benchmarked_mode(cu_stress_path):
+    """The bench's modes (tensor-core contraction and fitting, FP32-accurate
+    split operands) on the stress model at the bench's size: 4,000,000 atoms
+    as 5^3 copies of a displaced 20^3-cell copper box (32,000 atoms).  Every
+    copy keeps its periodic environment, so the oracle's full evaluation of the
+    32,000-atom box gives the expected E_i and force of every one of the 4M
+    atoms, and 125 times its energy and virial.  At 125,000 tiles of 32 atoms
+    each CTA of the persistent embedding kernels walks hundreds of tiles.  The
+    MD launch configuration (system creation: skin list, one force
+    evaluation) is checked on every force as well."""
+    from paper_2201_01446_gb300 import dp
+    x0, t0, box0 = inputs.fcc_copper(20, sigma=0.1, seed=41)
+    reps = 5
+    x, t, box = inputs.replicate(x0, t0, box0, reps)
+    m = oracle.Model(cu_stress_path)
+    tab = oracle.Table(m, TABLE_H, CU_SMAX)
+    r = oracle.evaluate(m, tab, CU_RC, CU_RCS, CU_SEL, x0, t0, box0)
+    ncopy = reps ** 3
+    e_ref = np.tile(r["atom_energy"], ncopy)
+    f_ref = np.tile(r["force"], (ncopy, 1))
+    o = dp.dp_options_default()
+    o.fit_precision = 2
+    o.embed_precision = 2
+    h = dp.dp_create(cu_stress_path, 1, CU_RC, CU_RCS, [CU_SEL], options=o, stream=None)
+    try:
+        E, F, V, Ei = dp.dp_compute(h, x, t, box, atom_energy=True)
+        s = dp.dp_system_create(h, x, np.zeros_like(x), t, [inputs.MASS_CU], box)
+        _, _, fmd = dp.dp_system_get(h, s, len(x), x=False, v=False)
+        dp.dp_system_destroy(s)
+    finally:
+        dp.dp_destroy(h)
+    n = len(x)
+    emean = float(np.abs(e_ref).mean())
+    emax = float(np.abs(e_ref).max())
+    frms = float(np.sqrt((f_ref ** 2).mean()))
+    de = abs(E - ncopy * r["energy"]) / n
+    dei = float(np.abs(Ei - e_ref).max())
+    fr = float(np.sqrt(((F - f_ref) ** 2).mean()))
+    frmd = float(np.sqrt(((fmd - f_ref) ** 2).mean()))
+    dv = float(np.abs(V - ncopy * r["virial"]).max())
+    vmax = float(np.abs(ncopy * r["virial"]).max())
+    PARITY_LOG.append(dict(case="fullsize Cu 4M stress, every atom, fit 2 embed 2", natoms=n,
+                           stress=True, dE_per_atom=de, max_dEi=dei, force_rmse=fr,
+                           force_rmse_md=frmd, force_rms=frms, max_dvirial=dv, max_virial=vmax,
+                           mean_abs_Ei=emean))
+    # the stress bars of the small cases (FP32-relative; the total energy
+    # with the tensor-core allowance of 5e-6 mean|E_i|)
+    assert de < max(1e-6, 5e-6 * emean), (de, emean)
+    assert dei < 2e-5 * emax, (dei, emax)
+    assert fr < max(1e-5, 3e-5 * frms), (fr, frms)
+    assert frmd < max(1e-5, 3e-5 * frms), (frmd, frms)
+    assert dv < 1e-4 * vmax, (dv, vmax)

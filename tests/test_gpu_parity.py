@@ -4,7 +4,9 @@ Bars:
   * neighbor sets bit-exact (as sorted (i, j, image) rows);
   * configured models (weights N(0, 0.1)): energy within 1e-6 eV/atom
     (|dE|/N), force RMSE within 1e-5 eV/A -- the FP32 path's stated
-    tolerance -- and per-atom energies within 1e-6 eV;
+    tolerance -- and within 1e-3 of the reference RMS force (these models
+    exert only ~1e-6 eV/A, so F = 0 must fail too), per-atom energies within
+    1e-6 eV;
   * stress models (weights N(0, 1)): forces of 0.2-4 eV/A and per-atom
     energies of 7-40 eV, where FP32 rounding of the 2048-wide fitting net is
     ~1e-6 relative and does not average out over a near-perfect lattice.
@@ -17,12 +19,11 @@ import pytest
 
 import oracle
 from paper_2201_01446_gb300 import inputs
-from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, PARITY_LOG, TABLE_H, rmse
+from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, F_ABS, PARITY_LOG, TABLE_H, force_bar, rmse
 
 pytestmark = pytest.mark.gpu
 
 E_TOL = 1e-6   # eV/atom
-F_TOL = 1e-5   # eV/A RMSE
 
 
 @pytest.fixture(scope="module")
@@ -126,14 +127,14 @@ def _parity(dp, h, m, tab, x, t, box, sel=CU_SEL, rc=CU_RC, rcs=CU_RCS, stress=F
     if not stress:
         assert de < E_TOL, de
         assert dei < E_TOL, dei
-        assert fr < F_TOL, fr
+        assert fr <= force_bar(frms), (fr, frms)
         assert dv < 1e-4 * max(vmax, 1e-3), (dv, vmax)
     else:
         emean = float(np.abs(r["atom_energy"]).mean())
         emax = float(np.abs(r["atom_energy"]).max())
         assert de < max(E_TOL, e_rel * emean), (de, emean)
         assert dei < 2e-5 * emax, (dei, emax)
-        assert fr < max(F_TOL, 3e-5 * frms), (fr, frms)
+        assert fr < max(F_ABS, 3e-5 * frms), (fr, frms)
         assert dv < 1e-4 * vmax + 1e-9, (dv, vmax)
     return E, F, V, r
 
