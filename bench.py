@@ -50,8 +50,9 @@ MD_PER_STEP = 10
 DT_FS = 1.0
 METRIC = "DP copper atom-steps/s/GPU (fused tabulated vs plain, force err); serve p99 ms"
 UNIT = "atom-steps/s"
-# FP32 CUDA-core peak of GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# nominal FP32 CUDA-core peak of GB300: 152 SMs x 128 FP32 lanes x 2 flop x
+# 2.070 GHz; the rooflines use the FMA probe measured in the run itself
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 def parse():
@@ -233,6 +234,32 @@ TRAFFIC_PER_ATOM = {"embed_contract_fwd": (400625920 + 1347540736) / 256000,
 KERNEL_OF_PHASE = {"embed_contract_fwd": "k_tab_fwd_tc", "embed_contract_bwd_forces": "k_tab_bwd_tc"}
 
 
+def fp32_peak_probe(stream, local, launches=7, outer=12000):
+    """The FP32 FMA probe of the library (every resident thread runs
+    independent FMA chains, ~50 ms a launch), timed with CUDA events on the
+    stream: median and best TFLOP/s over the launches, and the SM clock
+    sampled meanwhile.  This is the FP32 CUDA-core peak the rooflines use."""
+    import torch
+    from paper_2201_01446_gb300 import dp
+    dp.dp_fma_peak_run(outer // 10, C_stream(stream))
+    torch.cuda.synchronize()
+    ck = Clocks(gpu_uuid(local))
+    ck.start()
+    res = []
+    for _ in range(launches):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fl = dp.dp_fma_peak_run(outer, C_stream(stream))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res.append(fl / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    clk = ck.stop()
+    return {"tflops": statistics.median(res), "best_tflops": max(res), "launches": launches,
+            "nominal_tflops": FP32_NOMINAL_TFLOPS, "clocks": clk,
+            "how": "dp_fma_peak_run: 152 x 8 CTAs of 256 threads, 8 independent FMA chains "
+                   "each, CUDA events on the bench stream, median of the launches"}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -274,7 +301,7 @@ def cpu_baseline_leg(model_path, xg, t, box, F_gpu, Ei_gpu, n_force=64, n_energy
     return base, err
 
 
-def water_leg(args, stream, pg, world):
+def water_leg(args, stream, pg, world, fp32_peak):
     """MD of a two-type water-like box: the seeded 64-molecule box (192 atoms,
     L = 12.417 A) replicated reps^3 times, rc 6 A, sel [46, 92], embedding
     1-25-50-100, fitting 1600-240-240-240-1, dt 0.5 fs, rebuild every 10 steps.
@@ -326,7 +353,7 @@ def water_leg(args, stream, pg, world):
             "ms_per_md_step": ms / steps,
             "phases_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
             "phases_achieved_tflops": ach,
-            "embed_fwd_frac_of_fp32_peak": ach.get("embed_contract_fwd", 0.0) / FP32_PEAK_TFLOPS,
+            "embed_fwd_frac_of_fp32_peak": ach.get("embed_contract_fwd", 0.0) / fp32_peak,
             "fitting_frac_of_tensor_peak": ach.get("fitting", 0.0) / (bf16 / nprod),
             "pairs_within_rc": stats["pairs_within_rc"],
             "workload": f"water-like 64-molecule box replicated {r}^3 ({n} atoms), rc 6 A, "
@@ -461,6 +488,7 @@ def main():
     run_schedule(lambda: dp.dp_system_create(h, x, v, t, masses, box),
                  lambda s, nb: dp.dp_md_step(h, s, MD_PER_STEP * nb, DT_FS),
                  dp.dp_system_destroy, args.warmup)
+    fp32 = fp32_peak_probe(stream, local)
     torch.cuda.synchronize()
     barrier(pg)
     torch.cuda.synchronize()
@@ -514,10 +542,11 @@ def main():
     dom = max(single, key=lambda k: per_launch[k])
     achieved = phase_achieved(dom)
     traffic = TRAFFIC_PER_ATOM[dom] * n if args.embed_precision == 2 else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32["tflops"],
+                "unit": "TFLOP/s", "frac": achieved / fp32["tflops"], "traffic": traffic,
                 "kernel": KERNEL_OF_PHASE[dom] if args.embed_precision == 2 else dom,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (FP32 CUDA cores)",
+                "peak_source": "FP32 FMA probe measured in this run (fp32_peak); nominal "
+                               "152 SMs x 128 lanes x 2 x 2.070 GHz = %.1f" % FP32_NOMINAL_TFLOPS,
                 "note": "achieved counts the method's per-pair FLOPs (2304 per pair within rc); "
                         "the interval contraction inside runs on tcgen05"}
     if args.fit_precision > 0 and prof.get("fitting", (0, 0))[1]:
@@ -597,7 +626,7 @@ def main():
     water_info = None
     if args.water_reps > 0:
         try:
-            water_info = water_leg(args, stream, pg, world)
+            water_info = water_leg(args, stream, pg, world, fp32["tflops"])
         except dp.DPError as e:  # a library error of this leg is reported, not fatal
             water_info = {"error": str(e)}
     serve_info = serve_leg(args, model, pg) if args.serve_requests > 0 else None
@@ -620,7 +649,7 @@ def main():
                                      "initial state), summed; system creation (list build and "
                                      "first force evaluation) excluded from value, included in "
                                      "e2e"},
-                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "roofline": roofline, "fp32_peak": fp32, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": ck, "accuracy_vs_oracle": accuracy, "plain": plain,
                 "serve": serve_info, "param_grad": grad_info, "water": water_info,
                 "stats": stats}

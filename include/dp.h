@@ -348,6 +348,15 @@ dp_status dp_neighbor_pairs_static(int64_t natoms, const double* coords, const d
                                    double rlist, int64_t cap, int32_t* out5, int64_t* count,
                                    void* stream);
 
+/* FP32 FMA throughput probe (measurement only; the paper has no
+ * counterpart): one launch on `stream` of a kernel in which every resident
+ * thread of every SM runs independent FMA chains, `outer` x 512 FMAs per
+ * thread; *flops receives the FLOPs it performs (2 per FMA).  Timing the
+ * launch with CUDA events on that stream gives the FP32 CUDA-core peak at the
+ * clock the GPU runs at.  Errors: DP_ERR_ARG (outer < 1, flops NULL),
+ * DP_ERR_CUDA. */
+dp_status dp_fma_peak_run(int64_t outer, void* stream, double* flops);
+
 /* Library build string (architecture, options compiled in). */
 const char* dp_version(void);
 

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libdp.so")
 OBJDIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["dp_api.cpp", "k_nbr.cu", "k_embed.cu", "k_fit.cu", "k_md.cu", "k_static_nbr.cu", "k_fit_tc.cu", "k_plain.cu", "k_embed_tc.cu"]
+SOURCES = ["dp_api.cpp", "k_nbr.cu", "k_embed.cu", "k_fit.cu", "k_md.cu", "k_static_nbr.cu", "k_fit_tc.cu", "k_plain.cu", "k_embed_tc.cu", "k_peak.cu"]
 
 
 def _nvcc():

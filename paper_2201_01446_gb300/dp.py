@@ -48,7 +48,7 @@ EXPORTS = ["dp_options_default", "dp_create", "dp_destroy", "dp_last_error", "dp
            "dp_neighbor_pairs", "dp_table_coeffs", "dp_descriptor", "dp_version",
            "dp_profile", "dp_profile_read", "dp_stats", "dp_neighbor_pairs_static", "dp_fitting",
            "dp_param_sizes", "dp_param_grad", "dp_get_params", "dp_set_params", "dp_compute_batch",
-           "dp_system_create_batch", "dp_system_batch_size"]
+           "dp_system_create_batch", "dp_system_batch_size", "dp_fma_peak_run"]
 
 DP_NPHASE = 5
 PHASES = ["neighbor_build", "embed_contract_fwd", "fitting", "embed_contract_bwd_forces",
@@ -94,6 +94,7 @@ def _load():
         "dp_system_create_batch": (i, [vp, i, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]),
         "dp_set_params": (i, [vp, vp, vp]),
         "dp_system_batch_size": (i, [vp]),
+        "dp_fma_peak_run": (i, [i64, vp, C.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -370,6 +371,15 @@ def dp_neighbor_pairs_static(coords, box, rlist, stream=None, out=None):
                                         b.ctypes.data_as(C.c_void_p), float(rlist), cnt.value,
                                         C.c_void_p(out.data_ptr()), C.byref(cnt), stream), None)
     return out[:cnt.value]
+
+
+def dp_fma_peak_run(outer, stream=None):
+    """Launch the FP32 FMA probe once on the stream (default: torch's
+    current one); returns the FLOPs of the launch."""
+    fl = C.c_double()
+    _check(lib.dp_fma_peak_run(int(outer), stream if stream is not None else _torch_stream(),
+                               C.byref(fl)), None)
+    return fl.value
 
 
 def dp_compute_batch(h, systems):
