@@ -69,8 +69,10 @@ def parse():
                     help="MD steps of the plain untabulated comparator (0: skip)")
     ap.add_argument("--fit-precision", type=int, default=2,
                     help="0 FP32 CUDA cores, 1 BF16 tensor cores, 2 FP32-accurate tensor cores")
-    ap.add_argument("--serve-requests", type=int, default=120,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving leg (0: skip)")
+    ap.add_argument("--serve-capacity-requests", type=int, default=400,
+                    help="requests of the closed-loop capacity pass of the serving leg")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--grad-cells", type=int, default=40,
                     help="copper cells per edge of the parameter-gradient leg (0: skip)")
@@ -362,11 +364,13 @@ def water_leg(args, stream, pg, world, fp32_peak):
 
 
 def serve_leg(args, cu_model, pg):
-    """The serving loop (request stream with admission, several slots): a
+    """The serving loop (request stream with admission, several slots): the
     seeded mix of copper (500-500,000 atoms, log-uniform) and water-like
-    (192-24,576 atoms) boxes, half energy/force evaluations and half MD runs
-    (50 steps copper, 10 steps water).  A closed-loop pass measures capacity; the open-loop pass then
-    offers a Poisson stream at 70% of it and reports latency from arrival."""
+    (192-24,576 atoms) boxes, half energy/force evaluations and half 50-step
+    MD runs, under the 150 GB device budget.  A closed-loop pass over the
+    first requests of the stream measures capacity; the open-loop pass then
+    offers the whole Poisson stream at 70% of it and reports latency from
+    arrival, and the most device memory the library held meanwhile."""
     from paper_2201_01446_gb300 import dp, serve
     wpath = os.path.join(os.path.dirname(cu_model), "water.model")
     inputs.write_seeded_model(wpath, inputs.WATER_SPEC, seed=4, std=0.1)
@@ -380,22 +384,30 @@ def serve_leg(args, cu_model, pg):
 
     # table domain s <= 2.0 (r >= 0.5 A) for both models
     models = {"cu": serve.ModelCfg(cu_model, 1, RC, RCS, [SEL], opts(2.0)),
-              "water": serve.ModelCfg(wpath, 2, 6.0, 0.5, [46, 92], opts(2.0))}
+              "water": serve.ModelCfg(wpath, 2, 6.0, 0.5, [46, 92], opts(2.0), {"M": 100})}
     specs = inputs.serve_requests(args.serve_requests, seed=5)
-    srv = serve.Server(models, slots=args.serve_slots)
-    closed = srv.run(serve.make_requests(specs), np.zeros(len(specs)))
-    capacity = len(specs) / closed["makespan_s"]
+    budget = 150e9
+    srv = serve.Server(models, slots=args.serve_slots, budget_bytes=budget)
+    ncap = min(len(specs), args.serve_capacity_requests)
+    closed = srv.run(serve.make_requests(specs[:ncap]), np.zeros(ncap))
+    capacity = ncap / closed["makespan_s"]
     lam = 0.7 * capacity
+    base = dp.dp_memory(reset_peak=True)["process"]
     st = srv.run(serve.make_requests(specs), inputs.poisson_arrivals(len(specs), lam, seed=6))
+    mem = dp.dp_memory()
     return {"p50_ms": st["p50_ms"], "p99_ms": max_over_ranks(pg, st["p99_ms"]), "unit": "ms",
             "requests": len(specs), "errors": st["errors"] + closed["errors"],
             "arrival_rate_per_s": lam, "capacity_req_per_s": capacity,
+            "capacity_sample": f"closed loop over the first {ncap} requests",
             "atom_steps_per_s": st["atom_steps_per_s"], "slots": args.serve_slots,
+            "makespan_s": st["makespan_s"],
             "packed_calls": st["packed_calls"], "packed_requests": st["packed_requests"],
+            "budget_bytes": budget, "admission_peak_bytes": st["peak_budget_bytes"],
+            "device_peak_bytes": mem["peak"] - base, "trims": st["trims"],
             "mix": "Cu 500-500k atoms log-uniform + water 192*2^k (k<8), half eval half MD "
-                   "(Cu 50 steps, water 10), Poisson arrivals at 0.7 x closed-loop capacity; "
-                   "queued requests of one model and kind (MD: same steps) packed up to 32768 atoms "
-                   "per call"}
+                   "(50 steps; water MD from rest), Poisson arrivals at 0.7 x closed-loop "
+                   "capacity; queued requests of one model and kind (MD: same steps) packed up "
+                   "to 32768 atoms per call"}
 
 
 def grad_leg(args, model_path, stream):

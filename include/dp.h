@@ -348,6 +348,24 @@ dp_status dp_neighbor_pairs_static(int64_t natoms, const double* coords, const d
                                    double rlist, int64_t cap, int32_t* out5, int64_t* count,
                                    void* stream);
 
+/* Device memory held by the library (every buffer it allocated with
+ * cudaMalloc and has not freed).  Any pointer may be NULL.
+ *   handle_bytes   bytes held by the handle h (model, tables, work areas,
+ *                  scratch, buffers kept from destroyed systems; not those
+ *                  of live systems); needs h != NULL (else DP_ERR_ARG).
+ *   process_bytes  bytes held by all handles and systems of the process.
+ *   process_peak   the most process_bytes has been since the last reset.
+ *   reset_peak     non-zero: restart the peak at the current value.
+ * Host-side counters: no device work, no synchronisation. */
+dp_status dp_memory(const dp_handle* h, int64_t* handle_bytes, int64_t* process_bytes,
+                    int64_t* process_peak, int reset_peak);
+
+/* Release the handle's work area, the buffers kept from its destroyed
+ * systems and its fitting / gradient scratch (all are allocated again on
+ * demand, so a memory budget can reclaim an idle handle's cache).  The model,
+ * tables and live systems stay.  Synchronises the handle's stream. */
+dp_status dp_trim(dp_handle* h);
+
 /* FP32 FMA throughput probe (measurement only; the paper has no
  * counterpart): one launch on `stream` of a kernel in which every resident
  * thread of every SM runs independent FMA chains, `outer` x 512 FMAs per

@@ -32,6 +32,17 @@ std::atomic<long> g_alloc_count{0};  // allocations from several host threads
 std::atomic<unsigned long long> g_alloc_gen{0};
 std::atomic<long> g_alloc_fail_at{-1};
 std::once_flag g_fault_once;
+// device bytes the library holds (every DevBuf), and the most it held since
+// the last reset (dp_memory)
+std::atomic<long long> g_dev_bytes{0};
+std::atomic<long long> g_dev_peak{0};
+
+void dev_bytes_add(long long b) {
+  const long long now = g_dev_bytes.fetch_add(b) + b;
+  long long pk = g_dev_peak.load();
+  while (now > pk && !g_dev_peak.compare_exchange_weak(pk, now)) {
+  }
+}
 
 void parse_fault() {
   std::call_once(g_fault_once, [] {
@@ -52,7 +63,10 @@ struct DevBuf {
   }
   DevBuf& operator=(DevBuf&& o) noexcept {
     if (this != &o) {
-      if (p) cudaFree(p);
+      if (p) {
+        cudaFree(p);
+        dev_bytes_add(-(long long)bytes);
+      }
       p = o.p;
       bytes = o.bytes;
       o.p = nullptr;
@@ -61,10 +75,16 @@ struct DevBuf {
     return *this;
   }
   ~DevBuf() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      dev_bytes_add(-(long long)bytes);
+    }
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      dev_bytes_add(-(long long)bytes);
+    }
     p = nullptr;
     bytes = 0;
   }
@@ -81,6 +101,7 @@ cudaError_t ensure(DevBuf& b, size_t bytes) {
   cudaError_t e = cudaMalloc(&b.p, bytes);
   if (e == cudaSuccess) {
     b.bytes = bytes;
+    dev_bytes_add((long long)bytes);
   } else {
     b.p = nullptr;
     cudaGetLastError();  // clear the non-sticky allocation error
@@ -107,6 +128,16 @@ struct Work {
   // several systems in one evaluation: tile index lists padded per system,
   // atom -> system, per-system first atom and cell edges, per-tile virial
   DevBuf bidx, sys_of, sys_base, sys_edge, vir_tile, vir_type, seg, seg_part, seg_out;
+  size_t bytes() const {
+    const DevBuf* all[] = {&x, &xref, &types, &types_in, &cellc, &cell_count, &cell_fill,
+                           &cell_start, &cell_tmp, &cell_atoms, &off, &nlist, &nn, &T, &dT,
+                           &e_atom, &ffix, &f, &vir_part, &red_part, &red_out, &idx, &ke, &pairs,
+                           &tc_pairs, &tc_hist, &tc_range, &bidx, &sys_of, &sys_base, &sys_edge,
+                           &vir_tile, &vir_type, &seg, &seg_part, &seg_out};
+    size_t b = 0;
+    for (const DevBuf* d : all) b += d->bytes;
+    return b;
+  }
 };
 
 // several independent systems in one atom array (host bookkeeping)
@@ -1555,6 +1586,45 @@ dp_status dp_profile_read(dp_handle* h, double* ms, int64_t* launches) {
     if (ms) ms[p] = t;
     if (launches) launches[p] = (int64_t)h->prof_ev[p].size();
   }
+  return DP_OK;
+}
+
+dp_status dp_memory(const dp_handle* h, int64_t* handle_bytes, int64_t* process_bytes,
+                    int64_t* process_peak, int reset_peak) {
+  if (handle_bytes) {
+    if (!h) return DP_ERR_ARG;
+    const DevBuf* own[] = {&h->emb64,  &h->emb_off,  &h->table,      &h->fit32,    &h->sel_dev,
+                           &h->map_dev, &h->status,  &h->tabF,       &h->tabB,     &h->tc_scratch,
+                           &h->tanh_tab, &h->pg,     &h->pg_fit_part, &h->pg_tab_part,
+                           &h->fitbuf,  &h->fit_bf16, &h->fitbuf_tc, &h->plain_w,  &h->plain_nets,
+                           &h->spare_v};
+    size_t b = h->w.bytes() + (h->spare_work ? h->spare_work->bytes() : 0);
+    for (const DevBuf* d : own) b += d->bytes;
+    *handle_bytes = (int64_t)b;
+  }
+  if (process_bytes) *process_bytes = g_dev_bytes.load();
+  if (process_peak) *process_peak = g_dev_peak.load();
+  if (reset_peak) g_dev_peak.store(g_dev_bytes.load());
+  return DP_OK;
+}
+
+dp_status dp_trim(dp_handle* h) {
+  CKS(check_handle(h));
+  CK(cudaStreamSynchronize(h->st), "sync");
+  // the work area of dp_compute, the buffers kept from destroyed systems and
+  // the fitting and gradient scratch; all are allocated again on demand
+  h->w = Work();
+  h->spare_work.reset();
+  h->spare_v.release();
+  h->fitbuf.release();
+  h->fs = FitScratch{};
+  h->fitbuf_tc.release();
+  h->fs_tc = FitScratchTC{};
+  h->pg.release();
+  h->pg_fit_part.release();
+  h->pg_tab_part.release();
+  // CUDA graphs captured by live systems may point into the scratch
+  g_alloc_gen.fetch_add(1);
   return DP_OK;
 }
 

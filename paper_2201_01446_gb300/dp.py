@@ -48,7 +48,8 @@ EXPORTS = ["dp_options_default", "dp_create", "dp_destroy", "dp_last_error", "dp
            "dp_neighbor_pairs", "dp_table_coeffs", "dp_descriptor", "dp_version",
            "dp_profile", "dp_profile_read", "dp_stats", "dp_neighbor_pairs_static", "dp_fitting",
            "dp_param_sizes", "dp_param_grad", "dp_get_params", "dp_set_params", "dp_compute_batch",
-           "dp_system_create_batch", "dp_system_batch_size", "dp_fma_peak_run"]
+           "dp_system_create_batch", "dp_system_batch_size", "dp_fma_peak_run",
+           "dp_memory", "dp_trim"]
 
 DP_NPHASE = 5
 PHASES = ["neighbor_build", "embed_contract_fwd", "fitting", "embed_contract_bwd_forces",
@@ -95,6 +96,8 @@ def _load():
         "dp_set_params": (i, [vp, vp, vp]),
         "dp_system_batch_size": (i, [vp]),
         "dp_fma_peak_run": (i, [i64, vp, C.POINTER(d)]),
+        "dp_memory": (i, [vp, i64p, i64p, i64p, i]),
+        "dp_trim": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -371,6 +374,20 @@ def dp_neighbor_pairs_static(coords, box, rlist, stream=None, out=None):
                                         b.ctypes.data_as(C.c_void_p), float(rlist), cnt.value,
                                         C.c_void_p(out.data_ptr()), C.byref(cnt), stream), None)
     return out[:cnt.value]
+
+
+def dp_memory(h=None, reset_peak=False):
+    """{"handle": bytes of h (None without h), "process": bytes held by the
+    library, "peak": most held since the last reset} (host counters)."""
+    hb, pb, pk = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib.dp_memory(h, C.byref(hb) if h is not None else None, C.byref(pb), C.byref(pk),
+                         1 if reset_peak else 0), h)
+    return {"handle": hb.value if h is not None else None, "process": pb.value, "peak": pk.value}
+
+
+def dp_trim(h):
+    """Free the handle's caches (work area, kept system buffers, scratch)."""
+    _check(lib.dp_trim(h), h)
 
 
 def dp_fma_peak_run(outer, stream=None):

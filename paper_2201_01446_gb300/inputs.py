@@ -263,15 +263,16 @@ def water_tiled(k: int, seed: int = 3):
 
 def serve_requests(n: int, seed: int = 5, min_atoms: int = 500, max_atoms: int = 500000,
                    p_md: float = 0.5, p_water: float = 0.5, md_steps: int = 50,
-                   water_md_steps: int = 10):
+                   water_md_steps: int = 50):
     """Seeded request mix for the serving loop: copper boxes of log-uniform
     size in [min_atoms, max_atoms] (FCC cells per edge rounded) and water-like
     boxes of 192*k atoms (k log-uniform over powers of two 1..128), each an
     energy/force evaluation or an MD run (md_steps steps for copper,
-    water_md_steps for water: the seeded water model has no bonding, so its H
-    atoms fly free and a longer run leaves the physical distance range), with
-    330 K Maxwell velocities.  Returns a list of dicts (model, kind, x, v, types, box,
-    masses, steps)."""
+    water_md_steps for water), with 330 K Maxwell velocities, except that MD
+    runs of water start at rest: the seeded water model holds no molecule
+    together, and from 330 K its H atoms fly into close contacts within tens
+    of fs (the work of a step is the same).  Returns a list of dicts (model,
+    kind, x, v, types, box, masses, steps)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for i in range(n):
@@ -289,6 +290,8 @@ def serve_requests(n: int, seed: int = 5, min_atoms: int = 500, max_atoms: int =
             masses = [MASS_CU]
             m = np.full(len(x), MASS_CU)
         v = maxwell_velocities(m, 330.0, seed=int(rng.integers(1 << 30)))
+        if water and kind == "md":
+            v = np.zeros_like(v)
         steps = (water_md_steps if water else md_steps) if kind == "md" else 0
         out.append(dict(model="water" if water else "cu", kind=kind, x=x, v=v, types=t, box=box,
                         masses=masses, steps=steps))

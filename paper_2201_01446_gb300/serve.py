@@ -38,6 +38,7 @@ class ModelCfg:
     rcs: float
     sel: list
     options: object = None
+    shape: dict = field(default_factory=dict)  # estimate_bytes: M, fit_widths
 
 
 @dataclass
@@ -63,17 +64,36 @@ class Request:
         return len(self.x) * (self.steps if self.kind == "md" else 1)
 
 
-def estimate_bytes(natoms: int, cfg: ModelCfg, M: int = 128) -> int:
-    """Device bytes a request of natoms holds while it runs: neighbor list
-    (about 1.25 x the pairs within rc + skin, + 32), T and dE/dT, the sorted
-    pairs of the tensor-core embedding, positions, velocities, forces."""
+def estimate_bytes(natoms: int, cfg: ModelCfg, M: int = 128, fit_widths=(240, 240, 240),
+                   nsys: int = 1, skin: float = 2.0) -> int:
+    """Upper estimate of the device bytes a request of natoms adds to a
+    trimmed handle (dp_trim) of the tensor-core modes: per atom the neighbor
+    list with skin (1.5 x N_m scaled to rc + skin, + 64 entries), T and dE/dT,
+    the sorted pairs of the embedding kernels (N_m + 32 per atom slot, tiles
+    of 32 padded per system), bin ends and the per-atom arrays; per fitting
+    row (at most 8 waves of 152 x 128 rows) the activations, their BF16
+    pieces and the gradient rows."""
     nm = int(sum(cfg.sel))
-    cap = int(1.25 * nm * ((cfg.rc + 2.0) / cfg.rc) ** 3) + 32
-    per_atom = 4 * cap + 2 * 4 * 4 * M + 16 * (nm + 64) + 256
-    return natoms * per_atom + (64 << 20)
+    cap = int(1.5 * nm * ((cfg.rc + skin) / cfg.rc) ** 3) + 64
+    slots = natoms + 32 * nsys
+    per_atom = 4 * cap + 2 * 4 * 4 * M + 400
+    per_slot = 16 * ((nm + 32 + 31) // 32 * 32) + 2 * 1024  # sorted pairs, bin ends
+    wmax = max(fit_widths)
+    rows = min(-(-max(natoms, 1) // 128) * 128, 8 * 152 * 128)
+    per_row = wmax * (4 + 2 * 2 * 3) + sum(w * (4 + 4 + 2 * 3) for w in fit_widths)
+    return int(natoms * per_atom + slots * per_slot + rows * per_row + (8 << 20))
 
 
 class Server:
+    """Admission holds the sum of the slots' device bytes under the budget.
+    A slot holds what its handles hold (measured by dp_memory after each
+    request: the model, tables and the buffers kept from finished requests)
+    plus, while it runs, the estimate of what its request adds.  A request
+    that does not fit makes slots release their handles' kept buffers
+    (dp_trim: the taking slot itself, or idle slots) before it waits; one
+    larger than the budget runs alone once nothing else holds more than its
+    model."""
+
     def __init__(self, models: dict, slots: int = 4, budget_bytes: float = 150e9,
                  pack_atoms: int = 32768):
         self.models = models
@@ -84,10 +104,18 @@ class Server:
         self.packed_requests = 0
         self._cond = threading.Condition()
         self._ready = []       # arrived, not yet admitted (FIFO)
-        self._in_use = 0.0
         self._closing = False
         self._done = []
+        self._held = [0.0] * slots    # bytes each slot holds (see above)
+        self._fixed = [0.0] * slots   # bytes of its handles right after creation
+        self._running = [False] * slots
+        self._trim_req = [False] * slots
+        self.trims = 0
         self.peak_in_use = 0.0
+
+    @property
+    def _in_use(self) -> float:
+        return float(sum(self._held))
 
     # ---------------------------------------------------------------- queue
     def _push(self, req: Request) -> None:
@@ -95,62 +123,109 @@ class Server:
             self._ready.append(req)
             self._cond.notify_all()
 
-    def _take(self, can_pack: bool):
-        """The head of the queue once it fits the budget (FIFO admission),
-        with, when the head is a small evaluation and the slot can pack, the
-        queued evaluations of the same model that fit behind it; None when
-        the server closes with nothing left."""
+    def _take(self, k: int, can_pack: bool):
+        """For slot k: the head of the queue once it fits the budget (FIFO
+        admission), with, when the slot can pack and the head is small, the
+        queued requests of the same model and kind (MD: same steps) behind it
+        that fit; "trim" when the slot should release its kept buffers first;
+        None when the server closes with nothing left."""
         with self._cond:
             while True:
+                if self._trim_req[k]:
+                    self._trim_req[k] = False
+                    if self._held[k] > self._fixed[k]:
+                        return "trim"
                 if self._ready:
                     head = self._ready[0]
-                    if self._in_use + head.nbytes <= self.budget or self._in_use == 0.0:
-                        self._ready.pop(0)
-                        self._in_use += head.nbytes
-                        batch = [head]
-                        if can_pack and len(head.x) <= self.pack_atoms:
-                            atoms = len(head.x)
-                            for r in list(self._ready):
-                                if (r.kind == head.kind and r.model == head.model
-                                        and (r.kind == "eval" or r.steps == head.steps)
-                                        and atoms + len(r.x) <= self.pack_atoms
-                                        and self._in_use + r.nbytes <= self.budget):
-                                    self._ready.remove(r)
-                                    self._in_use += r.nbytes
-                                    atoms += len(r.x)
-                                    batch.append(r)
-                        self.peak_in_use = max(self.peak_in_use, self._in_use)
-                        return batch
+                    others = self._in_use - self._held[k]
+                    if others + self._held[k] + head.nbytes <= self.budget:
+                        return self._admit(k, head, can_pack, others)
+                    if self._held[k] > self._fixed[k]:
+                        return "trim"
+                    idle = [j for j in range(self.slots) if j != k and not self._running[j]
+                            and self._held[j] > self._fixed[j]]
+                    for j in idle:
+                        self._trim_req[j] = True
+                    if not idle and not any(self._running):
+                        return self._admit(k, head, False, others)  # larger than the budget
+                    self._cond.notify_all()
                 elif self._closing:
                     return None
                 self._cond.wait(0.05)
 
-    def _finish(self, req: Request) -> None:
+    def _admit(self, k, head, can_pack, others):
+        self._ready.pop(0)
+        held = self._held[k] + head.nbytes
+        batch = [head]
+        if can_pack and len(head.x) <= self.pack_atoms:
+            atoms = len(head.x)
+            for r in list(self._ready):
+                if (r.kind == head.kind and r.model == head.model
+                        and (r.kind == "eval" or r.steps == head.steps)
+                        and atoms + len(r.x) <= self.pack_atoms
+                        and others + held + r.nbytes <= self.budget):
+                    self._ready.remove(r)
+                    held += r.nbytes
+                    atoms += len(r.x)
+                    batch.append(r)
+        self._held[k] = held
+        self._running[k] = True
+        self.peak_in_use = max(self.peak_in_use, self._in_use)
+        return batch
+
+    def _finish(self, k: int, reqs: list, held_after) -> None:
         with self._cond:
-            self._in_use -= req.nbytes
-            self._done.append(req)
+            self._held[k] = self._fixed[k] if held_after is None else float(held_after)
+            self._running[k] = False
+            self.peak_in_use = max(self.peak_in_use, self._in_use)
+            self._done.extend(reqs)
+            self._cond.notify_all()
+
+    def _set_held(self, k: int, held) -> None:
+        with self._cond:
+            self._held[k] = self._fixed[k] if held is None else float(held)
             self._cond.notify_all()
 
     # ---------------------------------------------------------------- run
     def run(self, requests: list, arrivals, executor_factory=None) -> dict:
         """Serve `requests` arriving at `arrivals` (s after the start; 0 for
         all: closed loop).  executor_factory(slot) returns a callable that
-        runs one request (the default runs it through the library)."""
-        for r in requests:
-            r.nbytes = r.nbytes or estimate_bytes(len(r.x), self.models[r.model])
+        runs one request (the default runs it through the library); an
+        executor with bytes() and trim() (device bytes its handles hold,
+        releasing their kept buffers) takes part in the byte accounting."""
         make = executor_factory or self._dp_executor
         execs = [make(i) for i in range(self.slots)]
+        for r in requests:
+            if not r.nbytes:
+                cfg = self.models[r.model]
+                r.nbytes = estimate_bytes(len(r.x), cfg, **getattr(cfg, "shape", {}))
+        for k, ex in enumerate(execs):
+            b = ex.bytes() if hasattr(ex, "bytes") else None
+            self._fixed[k] = float(b or 0.0)
+            self._held[k] = self._fixed[k]
+            self._running[k] = False
+            self._trim_req[k] = False
         self._done = []
         self._closing = False
         self.packed_calls = self.packed_requests = 0
+        self.trims = 0
+        self.peak_in_use = self._in_use
         t0 = time.perf_counter()
 
-        def worker(ex):
+        def worker(k, ex):
             can_pack = self.pack_atoms > 0 and hasattr(ex, "batch")
+            measured = hasattr(ex, "bytes")
             while True:
-                reqs = self._take(can_pack)
+                reqs = self._take(k, can_pack)
                 if reqs is None:
                     return
+                if reqs == "trim":
+                    if hasattr(ex, "trim"):
+                        ex.trim()
+                    with self._cond:
+                        self.trims += 1
+                    self._set_held(k, ex.bytes() if measured else None)
+                    continue
                 for r in reqs:
                     r.t_start = time.perf_counter() - t0
                 try:
@@ -165,11 +240,13 @@ class Server:
                 except Exception as e:  # recorded, the loop goes on
                     for r in reqs:
                         r.error = str(e)
+                t = time.perf_counter() - t0
                 for r in reqs:
-                    r.t_done = time.perf_counter() - t0
-                    self._finish(r)
+                    r.t_done = t
+                self._finish(k, reqs, ex.bytes() if measured else None)
 
-        threads = [threading.Thread(target=worker, args=(ex,), daemon=True) for ex in execs]
+        threads = [threading.Thread(target=worker, args=(k, ex), daemon=True)
+                   for k, ex in enumerate(execs)]
         for th in threads:
             th.start()
         order = np.argsort(np.asarray(arrivals, np.float64), kind="stable")
@@ -197,6 +274,7 @@ class Server:
                 "p99_ms": float(np.percentile(lat, 99)) if len(lat) else 0.0,
                 "atom_steps_per_s": sum(r.atom_steps for r in requests) / max(makespan, 1e-9),
                 "slots": self.slots, "peak_budget_bytes": self.peak_in_use,
+                "budget_bytes": self.budget, "trims": self.trims,
                 "packed_calls": self.packed_calls, "packed_requests": self.packed_requests}
 
     def _dp_executor(self, slot: int):
@@ -254,6 +332,15 @@ class _DpSlot:
             return dp.dp_system_get(h, s, len(req.x))
         finally:
             dp.dp_system_destroy(s)
+
+    def bytes(self) -> int:
+        """Device bytes the slot's handles hold (dp_memory)."""
+        return sum(dp.dp_memory(h)["handle"] for h in self.handles.values())
+
+    def trim(self) -> None:
+        """Release the handles' kept buffers and scratch (dp_trim)."""
+        for h in self.handles.values():
+            dp.dp_trim(h)
 
     def close(self):
         for h in self.handles.values():

@@ -114,3 +114,61 @@ def test_small_evaluations_are_packed():
     # the 9000-atom evaluation exceeds pack_atoms and always runs alone
     assert st["packed_calls"] >= 1
     assert all(4 not in b for b in batches)
+
+
+class _Caching(_Sleep):
+    """Stand-in slot whose handles keep the buffers of its last request until
+    trimmed, like the library's handles; the shared ledger records the bytes
+    all slots hold at once."""
+
+    def __init__(self, log, slot, ledger, fixed=50):
+        super().__init__(log, slot)
+        self.ledger, self.fixed, self.kept = ledger, fixed, 0
+        with ledger["lock"]:
+            ledger["now"] += fixed
+            ledger["peak"] = max(ledger["peak"], ledger["now"])
+
+    def _add(self, b):
+        with self.ledger["lock"]:
+            self.ledger["now"] += b
+            self.ledger["peak"] = max(self.ledger["peak"], self.ledger["now"])
+
+    def __call__(self, req):
+        # a request grows the slot's buffers to max(kept, its need) at worst
+        # kept + need (eval and MD work areas are separate): take the worst
+        self._add(req.nbytes)
+        out = super().__call__(req)
+        self._add(-req.nbytes)
+        grow = max(0, req.nbytes - self.kept)
+        self._add(grow)
+        self.kept += grow
+        return out
+
+    def bytes(self):
+        return self.fixed + self.kept
+
+    def trim(self):
+        self._add(-self.kept)
+        self.kept = 0
+
+
+def test_kept_buffers_are_counted_and_trimmed():
+    import threading
+    models = {"cu": serve.ModelCfg("unused", 1, 8.0, 0.5, [256])}
+    rng = np.random.default_rng(3)
+    sizes = rng.integers(100, 3000, size=60)
+    reqs = _reqs(sizes, ["eval"] * 60)
+    for r in reqs:
+        r.nbytes = int(len(r.x))
+    budget = 6000
+    ledger = {"lock": threading.Lock(), "now": 0, "peak": 0}
+    srv = serve.Server(models, slots=3, budget_bytes=budget, pack_atoms=0)
+    log = []
+    st = srv.run(reqs, inputs.poisson_arrivals(len(reqs), rate=2000.0, seed=4),
+                 executor_factory=lambda s: _Caching(log, s, ledger))
+    assert st["errors"] == 0 and all(r.result == ("ok", r.rid) for r in reqs)
+    # what the slots really held never passed the budget, and the accounting
+    # bounded it; kept buffers had to be released for the larger requests
+    assert ledger["peak"] <= budget, ledger["peak"]
+    assert srv.peak_in_use <= budget
+    assert st["trims"] > 0
