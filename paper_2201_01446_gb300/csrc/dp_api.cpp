@@ -25,8 +25,15 @@ constexpr double kEvA3Bar = 1.602176634e6;
 
 // ------------------------------------------------------------------ fault injection
 // DP_FAULT=alloc:N makes the N-th device allocation of the process fail
-// (host-side injection; nothing on the GPU is disturbed).
+// (host-side injection; nothing on the GPU is disturbed).  DP_FAULT=wait:N
+// gives the N-th launch of the tensor-core embedding forward a limit of zero
+// polls on one bounded wait (its generator warps' wait for the MMAs to
+// release a stage), so that wait runs out and the kernel takes its timeout
+// path (DP_ERR_TIMEOUT); the waits that drain the CTA's own copies and MMAs
+// keep the full limit.
 std::atomic<long> g_alloc_count{0};  // allocations from several host threads
+std::atomic<long> g_fwd_tc_count{0};
+std::atomic<long> g_wait_fail_at{-1};
 // bumped by every device (re)allocation: a captured CUDA graph holds raw
 // pointers and is valid only while no buffer it uses has moved
 std::atomic<unsigned long long> g_alloc_gen{0};
@@ -48,7 +55,16 @@ void parse_fault() {
   std::call_once(g_fault_once, [] {
     const char* s = std::getenv("DP_FAULT");
     if (s && std::strncmp(s, "alloc:", 6) == 0) g_alloc_fail_at = std::atol(s + 6);
+    if (s && std::strncmp(s, "wait:", 5) == 0) g_wait_fail_at = std::atol(s + 5);
   });
+}
+
+// the generator-wait limit of this launch of the tensor-core embedding
+// forward: 0 for the injected launch, else -1 (the full limit)
+long long fwd_tc_wait_limit() {
+  parse_fault();
+  const long k = ++g_fwd_tc_count;
+  return (g_wait_fail_at > 0 && k == g_wait_fail_at) ? 0 : -1;
 }
 
 struct DevBuf {
@@ -734,7 +750,8 @@ dp_status embed_forward(dp_handle* h, Work& w, const EnvParams& ep) {
                           P<int32_t>(w.nn), w.cap, w.geom, ep, P<__nv_bfloat16>(h->tabF),
                           P<float>(h->tc_scratch), P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist),
                           P<int2>(w.tc_range), P<float>(w.T), P<int32_t>(h->status),
-                          P<unsigned long long>(w.pairs)))
+                          P<unsigned long long>(w.pairs), nullptr, nullptr, nullptr,
+                          fwd_tc_wait_limit()))
       return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core embedding cannot run this model shape");
   } else if (h->opt.tabulated) {
     if (launch_tab_fwd(h->st, w.n, P<float4>(w.off), P<uint32_t>(w.nlist), P<int32_t>(w.nn),
@@ -934,7 +951,8 @@ dp_status evaluate_batch(dp_handle* h, Work& w, Batch& b) {
                           w.cap, w.geom, ep, P<__nv_bfloat16>(h->tabF), P<float>(h->tc_scratch),
                           P<float4>(w.tc_pairs), P<uint16_t>(w.tc_hist), P<int2>(w.tc_range),
                           P<float>(w.T), P<int32_t>(h->status), P<unsigned long long>(w.pairs),
-                          P<int32_t>(w.sys_of), P<int32_t>(w.sys_base), P<float4>(w.sys_edge)))
+                          P<int32_t>(w.sys_of), P<int32_t>(w.sys_base), P<float4>(w.sys_edge),
+                          fwd_tc_wait_limit()))
       return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core embedding cannot run this model shape");
   }
   {
@@ -1729,6 +1747,9 @@ dp_status dp_param_grad(dp_handle* h, int64_t natoms, const double* coords, cons
     const EnvParams ep = env_params(h);
     CK(cudaMemsetAsync(w.pairs.p, 0, sizeof(unsigned long long), h->st), "memset");
     CKS(embed_forward(h, w, ep));
+    // a forward that gave up leaves no sorted pairs for the table gradient
+    CKS(read_status(h));
+    CKS(status_errors(h));
     // the fitting stage on the FP32 CUDA-core path, which keeps every
     // layer's input and gradient for the parameter gradients
     for (int t = 0; t < h->ntypes; ++t) {

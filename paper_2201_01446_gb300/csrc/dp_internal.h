@@ -139,7 +139,8 @@ int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, con
                       const __nv_bfloat16* tabF, float* scratch, float4* pairs_out,
                       uint16_t* hist_out, int2* range_out, float* T, int32_t* status,
                       unsigned long long* pair_count, const int32_t* sys_of = nullptr,
-                      const int32_t* sys_base = nullptr, const float4* sys_edge = nullptr);
+                      const int32_t* sys_base = nullptr, const float4* sys_edge = nullptr,
+                      long long gen_wait_limit = -1);
 // vir_tile != NULL: the virial as one FP64 row of 9 per tile (several systems
 // in one launch, tiles padded per system) instead of the per-slot partials
 int launch_tab_bwd_tc(cudaStream_t st, const TileMap& tm, const float4* pairs, const uint16_t* hist,

@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                  float* __restrict__ T,
                  int32_t* __restrict__ status, unsigned long long* __restrict__ pair_count,
                  const int32_t* __restrict__ sys_of, const int32_t* __restrict__ sys_base,
-                 const float4* __restrict__ sys_edge) {
+                 const float4* __restrict__ sys_edge, long long gen_wait_limit) {
   const FwdCfg cf = fwd_cfg(ep);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -563,7 +563,11 @@ __global__ void __launch_bounds__(kThreads, 2)
           kmid = nmid;
           kend = nend;
           kc = kn;
-          if (u > 0 && !mbar_wait(&s_empty[s], (u - 1) & 1, abort_flag)) break;
+          // (gen_wait_limit: the full limit; a test shortens this one wait,
+          // on the MMAs' release of the stage, to make it run out: every wait
+          // that drains the CTA's own copies and MMAs keeps the full limit)
+          if (u > 0 && !mbar_wait_lim(&s_empty[s], (u - 1) & 1, abort_flag, gen_wait_limit))
+            break;
           unsigned char* sa = base + (size_t)s * cf.stage;
 #pragma unroll
           for (int hb = 0; hb < 2; ++hb) {
@@ -668,6 +672,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                  const __nv_bfloat16* __restrict__ tabB, int scap, const float* __restrict__ dT,
                  unsigned long long* __restrict__ ffix, double* __restrict__ vir_part,
                  int32_t* __restrict__ status, double* __restrict__ vir_tile) {
+  // a forward that gave up on a bounded wait left tiles without sorted pairs,
+  // bin ends or ranges: nothing here may index through them (the call
+  // reports DP_ERR_TIMEOUT)
+  if (status[ST_TIMEOUT] != 0) return;
   const BwdCfg cf = bwd_cfg(ep);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -1218,8 +1226,9 @@ int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, con
                       const __nv_bfloat16* tabF, float* scratch, float4* pairs_out,
                       uint16_t* hist_out, int2* range_out, float* T, int32_t* status,
                       unsigned long long* pair_count, const int32_t* sys_of,
-                      const int32_t* sys_base, const float4* sys_edge) {
+                      const int32_t* sys_base, const float4* sys_edge, long long gen_wait_limit) {
   if (ep.M > 128 || ep.M % 4 || ep.M < 16) return -1;
+  if (gen_wait_limit < 0) gen_wait_limit = kSpinLimit;
   if (tm.ntypes < 1 || tm.ntypes > DP_MAXT || tm.ntypes != ep.ntypes) return -1;
   if (((uintptr_t)tabF & 15) || ((uintptr_t)T & 15)) return -1;
   if (tab_tc_supported(ep)) return -1;
@@ -1241,7 +1250,7 @@ int launch_tab_fwd_tc(cudaStream_t st, const TileMap& tm, const float4* off, con
   kern<<<grid, kThreads, cf.smem, st>>>(ntile, tm, off, nlist, nn, cap, g, ep, tabF,
                                         stage_cap_tc(ep), scratch, pairs_out, hist_out,
                                         range_out, T, status, pair_count, sys_of, sys_base,
-                                        sys_edge);
+                                        sys_edge, gen_wait_limit);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -166,6 +166,153 @@ __device__ __forceinline__ void plain_layer2(const PlainNet& w, int d1, int M, P
 }
 
 // ------------------------------------------------------------------ forward
+// One warp per atom.  The pairs within rc of one neighbor type are staged in
+// list order (s and the R row) until a block of kPF = 16 is full; each block
+// then runs the net as register-tiled products: layer 1 with lane (m group of
+// 4 columns, pair group of 8) owning a 4 x 8 tile, layer 2 with lane owning 4
+// embedding columns of all 16 pairs (4 x 16 accumulators: one float4 weight
+// load and four broadcast loads of h1 feed 64 multiply-adds).  G goes
+// straight into the lane's 4 x 4 block of T.  The last block of an atom and
+// type is padded with s = 0, R = 0 (contributes nothing).
+constexpr int kPF = 16;      // pairs per block (forward)
+constexpr int kStage = 48;   // staged pairs: < 16 waiting + one list round of 32
+
+struct PlainFwdSmem {        // per warp
+  float h0[32][kPF];         // layer-0 outputs [k][p]
+  float h1[64][kPF];         // layer-1 outputs [m][p]
+  float4 R[kStage];          // staged R rows
+  float s[kStage];           // staged s
+};
+
+// one block of kPF staged pairs (from the stage front) through the net into
+// the lane's T accumulators
+template <bool VEC1>
+__device__ __forceinline__ void plain_fwd_block(const PlainNet& w, int d1, int M,
+                                                PlainFwdSmem& S, int lane, float (&tacc)[4][4]) {
+  const int d2 = 2 * d1;
+  // layer 0: lane k < d1, all pairs
+  if (lane < d1) {
+    const float W = w.W0[lane], b = w.b0[lane];
+#pragma unroll
+    for (int p = 0; p < kPF; p += 4) {
+      float4 h;
+      h.x = tanhf(fmaf(S.s[p], W, b));
+      h.y = tanhf(fmaf(S.s[p + 1], W, b));
+      h.z = tanhf(fmaf(S.s[p + 2], W, b));
+      h.w = tanhf(fmaf(S.s[p + 3], W, b));
+      *reinterpret_cast<float4*>(&S.h0[lane][p]) = h;
+    }
+  }
+  __syncwarp();
+  // layer 1: columns m0..m0+3, pairs p0..p0+7
+  {
+    const int m0 = (lane & 15) * 4, p0 = (lane >> 4) * 8;
+    if (m0 < d2) {
+      float acc[8][4];
+      float bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bv[q] = m0 + q < d2 ? w.b1[m0 + q] : 0.0f;
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = bv[q];
+#pragma unroll 2
+      for (int k = 0; k < d1; ++k) {
+        float W[4];
+        if (VEC1) {
+          const float4 w4 = __ldg(reinterpret_cast<const float4*>(w.W1 + k * d2 + m0));
+          W[0] = w4.x;
+          W[1] = w4.y;
+          W[2] = w4.z;
+          W[3] = w4.w;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) W[q] = m0 + q < d2 ? __ldg(w.W1 + k * d2 + m0 + q) : 0.0f;
+        }
+        const float4 a0 = *reinterpret_cast<const float4*>(&S.h0[k][p0]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&S.h0[k][p0 + 4]);
+        const float hv[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(hv[p], W[q], acc[p][q]);
+      }
+      // h1 = (h0, h0) + tanh: column m repeats h0 column m mod d1
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int m = m0 + q;
+        if (m < d2) {
+          const int src = m < d1 ? m : m - d1;
+          const float4 a0 = *reinterpret_cast<const float4*>(&S.h0[src][p0]);
+          const float4 a1 = *reinterpret_cast<const float4*>(&S.h0[src][p0 + 4]);
+          *reinterpret_cast<float4*>(&S.h1[m][p0]) =
+              make_float4(a0.x + tanhf(acc[0][q]), a0.y + tanhf(acc[1][q]),
+                          a0.z + tanhf(acc[2][q]), a0.w + tanhf(acc[3][q]));
+          *reinterpret_cast<float4*>(&S.h1[m][p0 + 4]) =
+              make_float4(a1.x + tanhf(acc[4][q]), a1.y + tanhf(acc[5][q]),
+                          a1.z + tanhf(acc[6][q]), a1.w + tanhf(acc[7][q]));
+        }
+      }
+    }
+  }
+  __syncwarp();
+  // layer 2: columns c0..c0+3 of all pairs, then G into T
+  const int c0 = lane * 4;
+  if (c0 < M) {
+    float acc[kPF][4];
+    const float4 b = __ldg(reinterpret_cast<const float4*>(w.b2 + c0));
+#pragma unroll
+    for (int p = 0; p < kPF; ++p) {
+      acc[p][0] = b.x;
+      acc[p][1] = b.y;
+      acc[p][2] = b.z;
+      acc[p][3] = b.w;
+    }
+#pragma unroll 2
+    for (int l = 0; l < d2; ++l) {
+      const float4 W = __ldg(reinterpret_cast<const float4*>(w.W2 + l * M + c0));
+      const float4* hr = reinterpret_cast<const float4*>(&S.h1[l][0]);
+#pragma unroll
+      for (int g4 = 0; g4 < kPF / 4; ++g4) {
+        const float4 a = hr[g4];
+        const float hv[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int p = g4 * 4 + j;
+          acc[p][0] = fmaf(hv[j], W.x, acc[p][0]);
+          acc[p][1] = fmaf(hv[j], W.y, acc[p][1]);
+          acc[p][2] = fmaf(hv[j], W.z, acc[p][2]);
+          acc[p][3] = fmaf(hv[j], W.w, acc[p][3]);
+        }
+      }
+    }
+    // G = (h1, h1) + tanh: column c repeats h1 column c mod d2
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + q;
+      const int src = c - (c / d2) * d2;
+      const float4* hr = reinterpret_cast<const float4*>(&S.h1[src][0]);
+#pragma unroll
+      for (int g4 = 0; g4 < kPF / 4; ++g4) {
+        const float4 a = hr[g4];
+        const float hv[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int p = g4 * 4 + j;
+          const float G = hv[j] + tanhf(acc[p][q]);
+          const float4 R = S.R[p];
+          tacc[0][q] = fmaf(R.x, G, tacc[0][q]);
+          tacc[1][q] = fmaf(R.y, G, tacc[1][q]);
+          tacc[2][q] = fmaf(R.z, G, tacc[2][q]);
+          tacc[3][q] = fmaf(R.w, G, tacc[3][q]);
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+template <bool VEC1>
 __global__ void __launch_bounds__(kWpb * 32) k_plain_fwd(int64_t n, const float4* __restrict__ off,
                                                          const uint32_t* __restrict__ nlist,
                                                          const int32_t* __restrict__ nn, int cap,
@@ -175,7 +322,7 @@ __global__ void __launch_bounds__(kWpb * 32) k_plain_fwd(int64_t n, const float4
                                                          unsigned long long* __restrict__ pair_count) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  PlainSmem& S = reinterpret_cast<PlainSmem*>(smem4)[wib];
+  PlainFwdSmem& S = reinterpret_cast<PlainFwdSmem*>(smem4)[wib];
   const int M = ep.M, nt = ep.ntypes;
   const int cl = lane * 4;
   const unsigned below = (1u << lane) - 1u;
@@ -185,20 +332,24 @@ __global__ void __launch_bounds__(kWpb * 32) k_plain_fwd(int64_t n, const float4
     const int ti = __float_as_int(oi.w);
     const int cnt = min(nn[i], cap);
     const uint32_t* L = nlist + (size_t)i * cap;
-    float acc[4][4];
+    float tacc[4][4];
 #pragma unroll
     for (int c = 0; c < 4; ++c)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[c][q] = 0.0f;
+      for (int q = 0; q < 4; ++q) tacc[c][q] = 0.0f;
     for (int tj = 0; tj < nt; ++tj) {
       const PlainNet w = nets[ti * nt + tj];
+      int nst = 0;  // staged pairs
+      uint32_t e_next = lane < cnt ? L[lane] : 0u;
       for (int b0 = 0; b0 < cnt; b0 += 32) {
         const int k = b0 + lane;
+        const uint32_t e = e_next;
+        if (k + 32 < cnt) e_next = L[k + 32];
         bool in = false;
         float s = 0.f, dsdr, ir, dx = 0.f, dy = 0.f, dz = 0.f;
         if (k < cnt) {
           int t;
-          load_pair_p(oi, off, g, L[k], dx, dy, dz, t);
+          load_pair_p(oi, off, g, e, dx, dy, dz, t);
           const float r2 = dx * dx + dy * dy + dz * dz;
           if (r2 < ep.rc2 && t == tj) {
             in = true;
@@ -206,36 +357,42 @@ __global__ void __launch_bounds__(kWpb * 32) k_plain_fwd(int64_t n, const float4
           }
         }
         const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (in) {
-          const int slot = __popc(m & below);
+        // the stage holds < kPF pairs here, so nst + 32 <= kStage
+        const int slot = nst + __popc(m & below);
+        if (in && slot < kStage) {
           S.s[slot] = s;
-          S.R[slot][0] = s;
-          S.R[slot][1] = s * dx * ir;
-          S.R[slot][2] = s * dy * ir;
-          S.R[slot][3] = s * dz * ir;
+          S.R[slot] = make_float4(s, s * dx * ir, s * dy * ir, s * dz * ir);
         }
+        nst += __popc(m);
+        npairs += __popc(m);
         __syncwarp();
-        const int c = __popc(m);
-        npairs += c;
-        for (int p0 = 0; p0 < c; p0 += kP) {
-          float sv[kP];
-#pragma unroll
-          for (int p = 0; p < kP; ++p) sv[p] = p0 + p < c ? S.s[p0 + p] : 0.0f;
-          plain_layers01(w, d1, S, sv, lane);
-          float G[kP][4], t2[kP][4];
-          plain_layer2(w, d1, M, S, lane, G, t2);
-#pragma unroll
-          for (int p = 0; p < kP; ++p) {
-            if (p0 + p >= c) break;
-            const float4 R = *reinterpret_cast<const float4*>(S.R[p0 + p]);
-            const float rv[4] = {R.x, R.y, R.z, R.w};
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc)
-#pragma unroll
-              for (int q = 0; q < 4; ++q) acc[cc][q] = fmaf(rv[cc], G[p][q], acc[cc][q]);
+        while (nst >= kPF) {
+          plain_fwd_block<VEC1>(w, d1, M, S, lane, tacc);
+          // the rest of the stage (< 32 pairs) to its front
+          const int rest = nst - kPF;
+          float sv = 0.f;
+          float4 rv = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (lane < rest) {
+            sv = S.s[kPF + lane];
+            rv = S.R[kPF + lane];
           }
           __syncwarp();
+          if (lane < rest) {
+            S.s[lane] = sv;
+            S.R[lane] = rv;
+          }
+          __syncwarp();
+          nst = rest;
         }
+      }
+      if (nst > 0) {
+        // the last partial block, padded with zero rows
+        if (lane < kPF && lane >= nst) {
+          S.s[lane] = 0.0f;
+          S.R[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        plain_fwd_block<VEC1>(w, d1, M, S, lane, tacc);
       }
     }
     if (cl < M) {
@@ -243,8 +400,8 @@ __global__ void __launch_bounds__(kWpb * 32) k_plain_fwd(int64_t n, const float4
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc)
         *reinterpret_cast<float4*>(Ti + cc * M) =
-            make_float4(acc[cc][0] * ep.inv_nm, acc[cc][1] * ep.inv_nm, acc[cc][2] * ep.inv_nm,
-                        acc[cc][3] * ep.inv_nm);
+            make_float4(tacc[cc][0] * ep.inv_nm, tacc[cc][1] * ep.inv_nm, tacc[cc][2] * ep.inv_nm,
+                        tacc[cc][3] * ep.inv_nm);
     }
   }
   if (lane == 0 && pair_count) atomicAdd(pair_count, npairs);
@@ -266,7 +423,365 @@ __device__ __forceinline__ float transpose_sum32(float (&v)[32], int lane) {
   return v[0];
 }
 
+// sum of 16 per-lane values across the warp; lanes l and l + 16 receive the
+// total of value l % 16 (a fold of the two half-warps, then a transposing
+// butterfly: 31 shuffles)
+__device__ __forceinline__ float transpose_sum16(float (&v)[16], int lane) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], 16);
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < o; ++k) {
+      const float send = hi ? v[k] : v[k + o];
+      const float keep = hi ? v[k + o] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
 // ------------------------------------------------------------------ backward
+// One warp per atom, pairs staged in blocks of kPF = 16 as in the forward.
+// Per block: the forward recomputed (h0, t1, h1 in shared memory, layer 2 in
+// the lane's 4 x 16 registers), then
+//   dE/dG[c][p] = (1/N_m) sum_cc dT[cc][c] R[p][cc],  dp2 = dE/dG (1 - t2^2),
+//   dE/dR[p][cc] = (1/N_m) sum_c dT[cc][c] G[p][c]   (a transposing warp sum),
+//   dh1 = dE/dG[l] + dE/dG[l + d2] + W2 dp2           (lane tile 4 l x 8 p),
+//   dp1 = dh1 (1 - t1^2),
+//   dh0 = dh1[k] + dh1[k + d1] + W1 dp1               (lane tile 4 k x 4 p),
+//   dE/ds = sum_k W0[k] dh0[k] (1 - h0[k]^2),
+// and the chain rule through Eq. 1 per pair (lanes 0..15) to the forces and
+// the virial.
+struct PlainBwdSmem {        // per warp
+  float h0[32][kPF];         // layer-0 outputs
+  float t1[64][kPF];         // layer-1 tanh part
+  float h1[64][kPF];         // layer-1 outputs, then dE/dh1
+  float dp[128][kPF];        // dE/d(pre-activation): layer 2, then layer 1
+  float4 R[kStage];          // staged pairs: R row
+  float4 geo[kStage];        // ds/dr, 1/r, dx, dy
+  float dz[kStage];
+  float s[kStage];
+  int jj[kStage];            // neighbor atom index
+  float4 gR[kPF];            // dE/dR of the block's pairs
+  float gs[kPF];             // dE/ds (through the net) of the block's pairs
+  double vacc[9];            // the warp's virial (lane 0)
+};
+
+template <bool VEC>
+__device__ __forceinline__ void plain_bwd_block(const PlainNet& w, int d1, int M, float inv_nm,
+                                                PlainBwdSmem& S, int lane,
+                                                const float (&dTv)[4][4],
+                                                const float* __restrict__ dTi, int c, int& nbad,
+                                                float& fx, float& fy, float& fz, float (&vl)[9],
+                                                unsigned long long* __restrict__ ffix) {
+  const int d2 = 2 * d1;
+  // ---- forward: layer 0
+  if (lane < d1) {
+    const float W = w.W0[lane], b = w.b0[lane];
+#pragma unroll
+    for (int p = 0; p < kPF; p += 4) {
+      float4 h;
+      h.x = tanhf(fmaf(S.s[p], W, b));
+      h.y = tanhf(fmaf(S.s[p + 1], W, b));
+      h.z = tanhf(fmaf(S.s[p + 2], W, b));
+      h.w = tanhf(fmaf(S.s[p + 3], W, b));
+      *reinterpret_cast<float4*>(&S.h0[lane][p]) = h;
+    }
+  }
+  __syncwarp();
+  // ---- forward: layer 1 (tile 4 m x 8 p)
+  {
+    const int m0 = (lane & 15) * 4, p0 = (lane >> 4) * 8;
+    if (m0 < d2) {
+      float acc[8][4];
+      float bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bv[q] = m0 + q < d2 ? w.b1[m0 + q] : 0.0f;
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = bv[q];
+            for (int k = 0; k < d1; ++k) {
+        float W[4];
+        if (VEC) {
+          const float4 w4 = __ldg(reinterpret_cast<const float4*>(w.W1 + k * d2 + m0));
+          W[0] = w4.x;
+          W[1] = w4.y;
+          W[2] = w4.z;
+          W[3] = w4.w;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) W[q] = m0 + q < d2 ? __ldg(w.W1 + k * d2 + m0 + q) : 0.0f;
+        }
+        const float4 a0 = *reinterpret_cast<const float4*>(&S.h0[k][p0]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&S.h0[k][p0 + 4]);
+        const float hv[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(hv[p], W[q], acc[p][q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int m = m0 + q;
+        if (m < d2) {
+          const int src = m < d1 ? m : m - d1;
+          float t[8];
+#pragma unroll
+          for (int p = 0; p < 8; ++p) t[p] = tanhf(acc[p][q]);
+          const float4 a0 = *reinterpret_cast<const float4*>(&S.h0[src][p0]);
+          const float4 a1 = *reinterpret_cast<const float4*>(&S.h0[src][p0 + 4]);
+          *reinterpret_cast<float4*>(&S.t1[m][p0]) = make_float4(t[0], t[1], t[2], t[3]);
+          *reinterpret_cast<float4*>(&S.t1[m][p0 + 4]) = make_float4(t[4], t[5], t[6], t[7]);
+          *reinterpret_cast<float4*>(&S.h1[m][p0]) =
+              make_float4(a0.x + t[0], a0.y + t[1], a0.z + t[2], a0.w + t[3]);
+          *reinterpret_cast<float4*>(&S.h1[m][p0 + 4]) =
+              make_float4(a1.x + t[4], a1.y + t[5], a1.z + t[6], a1.w + t[7]);
+        }
+      }
+    }
+  }
+  __syncwarp();
+  // ---- forward layer 2 and its backward epilogue, per half of the pairs
+  // (lane's 4 columns x 8 pairs in registers): G, dE/dG and dp2 of the
+  // lane's columns, and the lane's partial dE/dR summed across the warp (lane
+  // l receives pair 8 h + l / 4, component l % 4)
+  const int c0 = lane * 4;
+#pragma unroll 1
+  for (int hf = 0; hf < 2; ++hf) {
+    const int pb = hf * 8;
+    float acc[8][4];
+    if (c0 < M) {
+      const float4 b = __ldg(reinterpret_cast<const float4*>(w.b2 + c0));
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        acc[p][0] = b.x;
+        acc[p][1] = b.y;
+        acc[p][2] = b.z;
+        acc[p][3] = b.w;
+      }
+            for (int l = 0; l < d2; ++l) {
+        const float4 W = __ldg(reinterpret_cast<const float4*>(w.W2 + l * M + c0));
+        const float4 a0 = *reinterpret_cast<const float4*>(&S.h1[l][pb]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&S.h1[l][pb + 4]);
+        const float hv[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          acc[p][0] = fmaf(hv[p], W.x, acc[p][0]);
+          acc[p][1] = fmaf(hv[p], W.y, acc[p][1]);
+          acc[p][2] = fmaf(hv[p], W.z, acc[p][2]);
+          acc[p][3] = fmaf(hv[p], W.w, acc[p][3]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = 0.0f;
+    }
+#pragma unroll
+    for (int qt = 0; qt < 2; ++qt) {  // quarters of 4 pairs: 16 partial sums each
+      float part[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) part[j] = 0.0f;
+#pragma unroll
+      for (int pq = 0; pq < 4; ++pq) {
+        const int pp = qt * 4 + pq, p = pb + pp;
+        const float4 R = S.R[p];
+        const float rv[4] = {R.x, R.y, R.z, R.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int col = c0 + q;
+          float G = 0.0f, t = 0.0f, dg = 0.0f;
+          if (col < M) {
+            const int src = col - (col / d2) * d2;
+            t = tanhf(acc[pp][q]);
+            G = S.h1[src][p] + t;
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) dg = fmaf(dTv[cc][q], rv[cc], dg);
+            dg *= inv_nm;
+          }
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc)
+            part[pq * 4 + cc] = fmaf(dTv[cc][q], G, part[pq * 4 + cc]);
+          if (col < M) S.dp[col][p] = dg * (1.0f - t * t);
+        }
+      }
+      // lane l (< 16) receives pair pb + 4 qt + l / 4, component l % 4
+      const float dR = transpose_sum16(part, lane) * inv_nm;
+      if (lane < 16) reinterpret_cast<float*>(S.gR)[4 * (pb + 4 * qt) + lane] = dR;
+    }
+  }
+  __syncwarp();
+  // ---- layer 2 backward (tile 4 l x 8 p): dE/dh1 = the (x, x) shortcut's
+  // dE/dG[l] + dE/dG[l + d2] = (1/N_m) R . (dT[.][l] + dT[.][l + d2]), plus
+  // W2 dp2; then dp1
+  {
+    const int l0 = (lane & 15) * 4, p0 = (lane >> 4) * 8;
+    float acc[8][4];
+    if (l0 < d2) {
+      float dsum[4][4];  // [cc][q]: dT[cc][l] + dT[cc][l + d2]
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int l = l0 + q;
+          dsum[cc][q] = l < d2 ? (__ldg(dTi + cc * M + l) + __ldg(dTi + cc * M + l + d2)) * inv_nm
+                               : 0.0f;
+        }
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        const float4 R = S.R[p0 + p];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          acc[p][q] = fmaf(R.x, dsum[0][q],
+                           fmaf(R.y, dsum[1][q], fmaf(R.z, dsum[2][q], R.w * dsum[3][q])));
+      }
+            for (int cc = 0; cc < M; ++cc) {
+        float W[4];
+        if (VEC) {
+          const float4 w4 = __ldg(reinterpret_cast<const float4*>(w.W2T + cc * d2 + l0));
+          W[0] = w4.x;
+          W[1] = w4.y;
+          W[2] = w4.z;
+          W[3] = w4.w;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) W[q] = l0 + q < d2 ? __ldg(w.W2T + cc * d2 + l0 + q) : 0.0f;
+        }
+        const float4 a0 = *reinterpret_cast<const float4*>(&S.dp[cc][p0]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&S.dp[cc][p0 + 4]);
+        const float dv[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(dv[p], W[q], acc[p][q]);
+      }
+    }
+    __syncwarp();  // every lane is done with dp2 and the shortcut part of dE/dh1
+    if (l0 < d2) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int l = l0 + q;
+        if (l < d2) {
+          float dpv[8];
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            const float t = S.t1[l][p0 + p];
+            dpv[p] = acc[p][q] * (1.0f - t * t);
+          }
+          *reinterpret_cast<float4*>(&S.dp[l][p0]) = make_float4(dpv[0], dpv[1], dpv[2], dpv[3]);
+          *reinterpret_cast<float4*>(&S.dp[l][p0 + 4]) =
+              make_float4(dpv[4], dpv[5], dpv[6], dpv[7]);
+          *reinterpret_cast<float4*>(&S.h1[l][p0]) =
+              make_float4(acc[0][q], acc[1][q], acc[2][q], acc[3][q]);
+          *reinterpret_cast<float4*>(&S.h1[l][p0 + 4]) =
+              make_float4(acc[4][q], acc[5][q], acc[6][q], acc[7][q]);
+        }
+      }
+    }
+  }
+  __syncwarp();
+  // ---- layer 1 and layer 0 backward: dh0 (tile 4 k x 4 p), dE/ds
+  {
+    const int k0 = (lane & 7) * 4, p0 = (lane >> 3) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = k0 + q;
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+        acc[p][q] = k < d1 ? S.h1[k][p0 + p] + S.h1[k + d1][p0 + p] : 0.0f;
+    }
+    if (k0 < d1) {
+            for (int m = 0; m < d2; ++m) {
+        float W[4];
+        if (VEC && (d1 % 4) == 0) {
+          const float4 w4 = __ldg(reinterpret_cast<const float4*>(w.W1T + m * d1 + k0));
+          W[0] = w4.x;
+          W[1] = w4.y;
+          W[2] = w4.z;
+          W[3] = w4.w;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) W[q] = k0 + q < d1 ? __ldg(w.W1T + m * d1 + k0 + q) : 0.0f;
+        }
+        const float4 a = *reinterpret_cast<const float4*>(&S.dp[m][p0]);
+        const float dv[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(dv[p], W[q], acc[p][q]);
+      }
+    }
+    float dsp[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      float v = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + q;
+        if (k < d1) {
+          const float h0 = S.h0[k][p0 + p];
+          v = fmaf(w.W0[k] * acc[p][q], 1.0f - h0 * h0, v);
+        }
+      }
+      dsp[p] = v;
+    }
+    // sum over the 8 lanes of a pair group (lane bits 0..2)
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) dsp[p] += __shfl_xor_sync(0xffffffffu, dsp[p], o);
+    if ((lane & 7) == 0) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) S.gs[p0 + p] = dsp[p];
+    }
+  }
+  __syncwarp();
+  // ---- per pair: chain rule through Eq. 1 (lanes 0..c-1 of the block)
+  if (lane < c) {
+    const float4 gR = S.gR[lane];
+    const float gsv = S.gs[lane];
+    const float4 ge = S.geo[lane];
+    const float sgeo = S.s[lane];
+    const float dsr = ge.x, irr = ge.y, ddx = ge.z, ddy = ge.w, ddz = S.dz[lane];
+    const float ux = ddx * irr, uy = ddy * irr, uz = ddz * irr;
+    const float a0 = gR.x + gsv;
+    const float dot = gR.y * ux + gR.z * uy + gR.w * uz;
+    const float sor = sgeo * irr;
+    const float coef = dsr * (a0 + dot) - sor * dot;
+    float gx = coef * ux + sor * gR.y;
+    float gy = coef * uy + sor * gR.z;
+    float gz = coef * uz + sor * gR.w;
+    if (!(isfinite(gx) && isfinite(gy) && isfinite(gz)) || fabsf(gx) > 4.0e6f ||
+        fabsf(gy) > 4.0e6f || fabsf(gz) > 4.0e6f) {
+      ++nbad;
+      gx = gy = gz = 0.0f;
+    }
+    fx += gx;
+    fy += gy;
+    fz += gz;
+    vl[0] -= ddx * gx;
+    vl[1] -= ddx * gy;
+    vl[2] -= ddx * gz;
+    vl[3] -= ddy * gx;
+    vl[4] -= ddy * gy;
+    vl[5] -= ddy * gz;
+    vl[6] -= ddz * gx;
+    vl[7] -= ddz * gy;
+    vl[8] -= ddz * gz;
+    unsigned long long* fj = ffix + (size_t)S.jj[lane] * 3;
+    atomicAdd(fj + 0, (unsigned long long)(-__float2ll_rn(gx * DP_FSCALE_F)));
+    atomicAdd(fj + 1, (unsigned long long)(-__float2ll_rn(gy * DP_FSCALE_F)));
+    atomicAdd(fj + 2, (unsigned long long)(-__float2ll_rn(gz * DP_FSCALE_F)));
+  }
+  __syncwarp();
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(kWpb * 32) k_plain_bwd(int64_t n, const float4* __restrict__ off,
                                                          const uint32_t* __restrict__ nlist,
                                                          const int32_t* __restrict__ nn, int cap,
@@ -278,13 +793,11 @@ __global__ void __launch_bounds__(kWpb * 32) k_plain_bwd(int64_t n, const float4
                                                          int32_t* __restrict__ status) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  PlainSmem& S = reinterpret_cast<PlainSmem*>(smem4)[wib];
-  const int M = ep.M, nt = ep.ntypes, d2 = 2 * d1;
+  PlainBwdSmem& S = reinterpret_cast<PlainBwdSmem*>(smem4)[wib];
+  const int M = ep.M, nt = ep.ntypes;
   const int cl = lane * 4;
   const unsigned below = (1u << lane) - 1u;
-  double vacc[9];
-#pragma unroll
-  for (int a = 0; a < 9; ++a) vacc[a] = 0.0;
+  if (lane < 9) S.vacc[lane] = 0.0;
   int nbad = 0;
   for (int64_t i = (int64_t)blockIdx.x * kWpb + wib; i < n; i += (int64_t)gridDim.x * kWpb) {
     const float4 oi = off[i];
@@ -307,14 +820,16 @@ __global__ void __launch_bounds__(kWpb * 32) k_plain_bwd(int64_t n, const float4
     for (int a = 0; a < 9; ++a) vl[a] = 0.f;
     for (int tj = 0; tj < nt; ++tj) {
       const PlainNet w = nets[ti * nt + tj];
+      int nst = 0;
+      uint32_t e_next = lane < cnt ? L[lane] : 0u;
       for (int b0 = 0; b0 < cnt; b0 += 32) {
         const int k = b0 + lane;
+        const uint32_t e = e_next;
+        if (k + 32 < cnt) e_next = L[k + 32];
         bool in = false;
         float s = 0.f, dsdr = 0.f, ir = 0.f, dx = 0.f, dy = 0.f, dz = 0.f;
-        uint32_t e = 0;
         if (k < cnt) {
           int t;
-          e = L[k];
           load_pair_p(oi, off, g, e, dx, dy, dz, t);
           const float r2 = dx * dx + dy * dy + dz * dz;
           if (r2 < ep.rc2 && t == tj) {
@@ -323,172 +838,51 @@ __global__ void __launch_bounds__(kWpb * 32) k_plain_bwd(int64_t n, const float4
           }
         }
         const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (in) {
-          const int slot = __popc(m & below);
+        // the stage holds < kPF pairs here, so nst + 32 <= kStage
+        const int slot = nst + __popc(m & below);
+        if (in && slot < kStage) {
           S.s[slot] = s;
-          S.R[slot][0] = s;
-          S.R[slot][1] = s * dx * ir;
-          S.R[slot][2] = s * dy * ir;
-          S.R[slot][3] = s * dz * ir;
-          S.geo[slot][0] = dsdr;
-          S.geo[slot][1] = ir;
-          S.geo[slot][2] = dx;
-          S.geo[slot][3] = dy;
-          S.geo[slot][4] = dz;
+          S.R[slot] = make_float4(s, s * dx * ir, s * dy * ir, s * dz * ir);
+          S.geo[slot] = make_float4(dsdr, ir, dx, dy);
+          S.dz[slot] = dz;
           S.jj[slot] = (int)(e >> 5);
         }
+        nst += __popc(m);
         __syncwarp();
-        const int c = __popc(m);
-        for (int p0 = 0; p0 < c; p0 += kP) {
-          float sv[kP];
-#pragma unroll
-          for (int p = 0; p < kP; ++p) sv[p] = p0 + p < c ? S.s[p0 + p] : 0.0f;
-          plain_layers01(w, d1, S, sv, lane);
-          float G[kP][4], t2[kP][4];
-          plain_layer2(w, d1, M, S, lane, G, t2);
-          // dE/dG (lane's columns), dE/d(pre2), partial dE/dR over the columns
-          float part[32];
-#pragma unroll
-          for (int p = 0; p < kP; ++p) {
-            float4 R = *reinterpret_cast<const float4*>(S.R[p0 + p < c ? p0 + p : p0]);
-            if (p0 + p >= c) R = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float rv[4] = {R.x, R.y, R.z, R.w};
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-              float acc = 0.0f;
-#pragma unroll
-              for (int q = 0; q < 4; ++q) acc = fmaf(dTv[cc][q], G[p][q], acc);
-              part[p * 4 + cc] = acc;
-            }
-            if (cl < M) {
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                float dg = 0.0f;
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) dg = fmaf(dTv[cc][q], rv[cc], dg);
-                dg *= ep.inv_nm;
-                S.dg[cl + q][p] = dg;
-                S.dp2[cl + q][p] = dg * (1.0f - t2[p][q] * t2[p][q]);
-              }
-            }
-          }
-          const float dRtot = transpose_sum32(part, lane) * ep.inv_nm;  // (p, c) = (lane/4, lane%4)
-          __syncwarp();
-          // layer 2 backward: lanes own l = lane, lane + 32
-          float dh1[2][kP];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int l = lane + 32 * h;
-#pragma unroll
-            for (int p = 0; p < kP; ++p) dh1[h][p] = 0.0f;
-            if (l < d2) {
-#pragma unroll
-              for (int p = 0; p < kP; ++p) dh1[h][p] = S.dg[l][p] + S.dg[l + d2][p];
-              for (int q = 0; q < M; ++q) {
-                const float W = __ldg(w.W2T + q * d2 + l);
-                const float4 a0 = *reinterpret_cast<const float4*>(&S.dp2[q][0]);
-                const float4 a1 = *reinterpret_cast<const float4*>(&S.dp2[q][4]);
-                dh1[h][0] = fmaf(a0.x, W, dh1[h][0]);
-                dh1[h][1] = fmaf(a0.y, W, dh1[h][1]);
-                dh1[h][2] = fmaf(a0.z, W, dh1[h][2]);
-                dh1[h][3] = fmaf(a0.w, W, dh1[h][3]);
-                dh1[h][4] = fmaf(a1.x, W, dh1[h][4]);
-                dh1[h][5] = fmaf(a1.y, W, dh1[h][5]);
-                dh1[h][6] = fmaf(a1.z, W, dh1[h][6]);
-                dh1[h][7] = fmaf(a1.w, W, dh1[h][7]);
-              }
-            }
+        while (nst >= kPF) {
+          plain_bwd_block<VEC>(w, d1, M, ep.inv_nm, S, lane, dTv, dT + (size_t)i * 4 * M, kPF,
+                               nbad, fx, fy, fz, vl, ffix);
+          const int rest = nst - kPF;
+          float sv = 0.f, dzv = 0.f;
+          float4 rv = make_float4(0.f, 0.f, 0.f, 0.f), gv = rv;
+          int jv = 0;
+          if (lane < rest) {
+            sv = S.s[kPF + lane];
+            rv = S.R[kPF + lane];
+            gv = S.geo[kPF + lane];
+            dzv = S.dz[kPF + lane];
+            jv = S.jj[kPF + lane];
           }
           __syncwarp();
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int l = lane + 32 * h;
-            if (l < d2) {
-#pragma unroll
-              for (int p = 0; p < kP; ++p) {
-                const float t = S.t1[l][p];
-                S.dp1[l][p] = dh1[h][p] * (1.0f - t * t);
-                S.h1[l][p] = dh1[h][p];  // h1 is no longer needed: keep dE/dh1 there
-              }
-            }
+          if (lane < rest) {
+            S.s[lane] = sv;
+            S.R[lane] = rv;
+            S.geo[lane] = gv;
+            S.dz[lane] = dzv;
+            S.jj[lane] = jv;
           }
           __syncwarp();
-          // layer 1 backward and layer 0: lanes own k = lane
-          float dsp[kP];
-#pragma unroll
-          for (int p = 0; p < kP; ++p) dsp[p] = 0.0f;
-          if (lane < d1) {
-            float dh0[kP];
-#pragma unroll
-            for (int p = 0; p < kP; ++p) dh0[p] = S.h1[lane][p] + S.h1[lane + d1][p];
-            for (int mm = 0; mm < d2; ++mm) {
-              const float W = __ldg(w.W1T + mm * d1 + lane);
-              const float4 a0 = *reinterpret_cast<const float4*>(&S.dp1[mm][0]);
-              const float4 a1 = *reinterpret_cast<const float4*>(&S.dp1[mm][4]);
-              dh0[0] = fmaf(a0.x, W, dh0[0]);
-              dh0[1] = fmaf(a0.y, W, dh0[1]);
-              dh0[2] = fmaf(a0.z, W, dh0[2]);
-              dh0[3] = fmaf(a0.w, W, dh0[3]);
-              dh0[4] = fmaf(a1.x, W, dh0[4]);
-              dh0[5] = fmaf(a1.y, W, dh0[5]);
-              dh0[6] = fmaf(a1.z, W, dh0[6]);
-              dh0[7] = fmaf(a1.w, W, dh0[7]);
-            }
-            const float W0 = w.W0[lane];
-#pragma unroll
-            for (int p = 0; p < kP; ++p) {
-              const float h0 = S.h0[lane][p];
-              dsp[p] = W0 * dh0[p] * (1.0f - h0 * h0);
-            }
-          }
-#pragma unroll
-          for (int o = 16; o >= 1; o >>= 1)
-#pragma unroll
-            for (int p = 0; p < kP; ++p) dsp[p] += __shfl_xor_sync(0xffffffffu, dsp[p], o);
-          // per pair: chain rule through Eq. 1, one pair per lane (lanes 0..kP-1)
-          float gR[4];
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) gR[cc] = __shfl_sync(0xffffffffu, dRtot, (4 * lane + cc) & 31);
-          float gsv = dsp[0];
-#pragma unroll
-          for (int p = 1; p < kP; ++p) gsv = lane == p ? dsp[p] : gsv;
-          const int pp = p0 + lane;
-          if (lane < kP && pp < c) {
-            const float sgeo = S.s[pp];
-            const float dsr = S.geo[pp][0], irr = S.geo[pp][1];
-            const float ddx = S.geo[pp][2], ddy = S.geo[pp][3], ddz = S.geo[pp][4];
-            const float ux = ddx * irr, uy = ddy * irr, uz = ddz * irr;
-            const float a0 = gR[0] + gsv;
-            const float dot = gR[1] * ux + gR[2] * uy + gR[3] * uz;
-            const float sor = sgeo * irr;
-            const float coef = dsr * (a0 + dot) - sor * dot;
-            float gx = coef * ux + sor * gR[1];
-            float gy = coef * uy + sor * gR[2];
-            float gz = coef * uz + sor * gR[3];
-            if (!(isfinite(gx) && isfinite(gy) && isfinite(gz)) || fabsf(gx) > 4.0e6f ||
-                fabsf(gy) > 4.0e6f || fabsf(gz) > 4.0e6f) {
-              ++nbad;
-              gx = gy = gz = 0.0f;
-            }
-            fx += gx;
-            fy += gy;
-            fz += gz;
-            vl[0] -= ddx * gx;
-            vl[1] -= ddx * gy;
-            vl[2] -= ddx * gz;
-            vl[3] -= ddy * gx;
-            vl[4] -= ddy * gy;
-            vl[5] -= ddy * gz;
-            vl[6] -= ddz * gx;
-            vl[7] -= ddz * gy;
-            vl[8] -= ddz * gz;
-            unsigned long long* fj = ffix + (size_t)S.jj[pp] * 3;
-            atomicAdd(fj + 0, (unsigned long long)(-__float2ll_rn(gx * DP_FSCALE_F)));
-            atomicAdd(fj + 1, (unsigned long long)(-__float2ll_rn(gy * DP_FSCALE_F)));
-            atomicAdd(fj + 2, (unsigned long long)(-__float2ll_rn(gz * DP_FSCALE_F)));
-          }
-          __syncwarp();
+          nst = rest;
         }
+      }
+      if (nst > 0) {
+        if (lane < kPF && lane >= nst) {
+          S.s[lane] = 0.0f;
+          S.R[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        plain_bwd_block<VEC>(w, d1, M, ep.inv_nm, S, lane, dTv, dT + (size_t)i * 4 * M, nst,
+                             nbad, fx, fy, fz, vl, ffix);
       }
     }
     double red[12] = {fx, fy, fz, vl[0], vl[1], vl[2], vl[3], vl[4], vl[5], vl[6], vl[7], vl[8]};
@@ -502,13 +896,14 @@ __global__ void __launch_bounds__(kWpb * 32) k_plain_bwd(int64_t n, const float4
       atomicAdd(fi + 1, (unsigned long long)__double2ll_rn(red[1] * DP_FSCALE));
       atomicAdd(fi + 2, (unsigned long long)__double2ll_rn(red[2] * DP_FSCALE));
 #pragma unroll
-      for (int a = 0; a < 9; ++a) vacc[a] += red[3 + a];
+      for (int a = 0; a < 9; ++a) S.vacc[a] += red[3 + a];
     }
+    __syncwarp();
   }
   if (lane == 0) {
     double* vp = vir_part + ((size_t)blockIdx.x * kWpb + wib) * 9;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) vp[a] = vacc[a];
+    for (int a = 0; a < 9; ++a) vp[a] = S.vacc[a];
   }
   nbad = __reduce_add_sync(0xffffffffu, nbad);
   if (lane == 0 && nbad) atomicAdd(&status[ST_NONFINITE], nbad);
@@ -773,15 +1168,18 @@ int launch_plain_fwd(cudaStream_t st, int64_t n, const float4* off, const uint32
                      const void* nets, int d1, float* T, unsigned long long* pair_count) {
   if (n <= 0) return 0;
   if (!plain_shape_ok(ep, d1)) return -1;
-  const size_t sm = sizeof(PlainSmem) * kWpb;
-  static std::atomic<bool> attr{false};  // launches from several host threads
-  if (!attr) {
-    cudaFuncSetAttribute(k_plain_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
+  const size_t sm = sizeof(PlainFwdSmem) * kWpb;
+  // float4 rows of W1 when its width 2 d1 is a multiple of 4
+  const bool vec = (2 * d1) % 4 == 0;
   DP_LAUNCHED(1);
-  k_plain_fwd<<<plain_blocks(n), kWpb * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep,
-                                                      (const PlainNet*)nets, d1, T, pair_count);
+  if (vec)
+    k_plain_fwd<true><<<plain_blocks(n), kWpb * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep,
+                                                            (const PlainNet*)nets, d1, T,
+                                                            pair_count);
+  else
+    k_plain_fwd<false><<<plain_blocks(n), kWpb * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep,
+                                                             (const PlainNet*)nets, d1, T,
+                                                             pair_count);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -792,16 +1190,25 @@ int launch_plain_bwd(cudaStream_t st, int64_t n, const float4* off, const uint32
   if (n <= 0) return 0;
   if (!plain_shape_ok(ep, d1)) return -1;
   if (vir_slots < plain_kernel_slots(n)) return -1;
-  const size_t sm = sizeof(PlainSmem) * kWpb;
-  static std::atomic<bool> attr{false};  // launches from several host threads
-  if (!attr) {
-    cudaFuncSetAttribute(k_plain_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
+  const size_t sm = sizeof(PlainBwdSmem) * kWpb;
+  // float4 rows of the transposed weights when the widths are multiples of 4
+  const bool vec = (2 * d1) % 4 == 0;
+  static std::atomic<bool> attr[2] = {{false}, {false}};  // launches from several host threads
+  if (!attr[vec]) {
+    if (cudaFuncSetAttribute(vec ? k_plain_bwd<true> : k_plain_bwd<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+      return -3;
+    attr[vec] = true;
   }
   DP_LAUNCHED(1);
-  k_plain_bwd<<<plain_blocks(n), kWpb * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep,
-                                                      (const PlainNet*)nets, d1, dT, ffix,
-                                                      vir_part, status);
+  if (vec)
+    k_plain_bwd<true><<<plain_blocks(n), kWpb * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep,
+                                                            (const PlainNet*)nets, d1, dT, ffix,
+                                                            vir_part, status);
+  else
+    k_plain_bwd<false><<<plain_blocks(n), kWpb * 32, sm, st>>>(n, off, nlist, nn, cap, g, ep,
+                                                             (const PlainNet*)nets, d1, dT, ffix,
+                                                             vir_part, status);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -52,15 +52,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// bounded wait; false on timeout (which raises the CTA's abort flag) or when
-// another role has already raised it (abort == nullptr: only the time limit)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
+// bounded wait of at most `limit` polls; false on timeout (which raises the
+// CTA's abort flag) or when another role has already raised it (abort ==
+// nullptr: only the time limit)
+__device__ __forceinline__ bool mbar_wait_lim(uint64_t* bar, uint32_t parity,
+                                              volatile int* abort, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (abort && *abort) return false;
   }
   if (abort) *abort = 1;
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  return mbar_wait_lim(bar, parity, abort, kSpinLimit);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {

@@ -77,3 +77,50 @@ def test_injected_allocation_failure_recovers(cu_stress_path, prec):
     else:
         raise AssertionError("every run met a fault")
     assert n > 1 and {"create", "compute", "system"} <= where, (n, where)
+
+
+WAIT_CHILD = r"""
+import hashlib, json, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2201_01446_gb300 import dp, inputs
+path = sys.argv[2]
+o = dp.dp_options_default()
+o.fit_precision = 2
+o.embed_precision = 2
+h = dp.dp_create(path, 1, 8.0, 0.5, [256], options=o, stream=None)
+x, t, box = inputs.fcc_copper(5, sigma=0.05, seed=1)
+codes = []
+for _ in range(2):
+    try:
+        E, F, V, _ = dp.dp_compute(h, x, t, box)
+        codes.append(0)
+    except dp.DPError as e:
+        codes.append(e.code)
+        msg = str(e)
+dig = hashlib.sha256(np.float64(E).tobytes() + F.tobytes() + V.tobytes()).hexdigest()
+dp.dp_destroy(h)
+print(json.dumps({"codes": codes, "digest": dig}))
+"""
+
+
+def test_device_wait_timeout_reports_and_recovers(cu_stress_path):
+    # DP_FAULT=wait:1: the first launch of the tensor-core embedding forward
+    # gives its generator warps' wait on the MMAs zero polls, so the wait
+    # runs out on the device (no fault, no hang: the CTA raises its abort
+    # flag, drains its own copies and MMAs with the full limit, frees its
+    # TMEM and records the timeout).  The call reports DP_ERR_TIMEOUT; the
+    # next call on the same handle gives the result of a run without it.
+    from paper_2201_01446_gb300 import dp  # noqa: F401  (builds the library first)
+    env = dict(os.environ, DP_SKIP_BUILD="1")
+    env.pop("DP_FAULT", None)
+    runs = {}
+    for fault in ("", "wait:1"):
+        e = dict(env, DP_FAULT=fault) if fault else env
+        r = subprocess.run([sys.executable, "-c", WAIT_CHILD, ROOT, cu_stress_path], env=e,
+                           capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, (fault, r.stdout[-2000:], r.stderr[-2000:])
+        runs[fault] = json.loads(r.stdout.strip().splitlines()[-1])
+    assert runs[""]["codes"] == [0, 0]
+    assert runs["wait:1"]["codes"] == [8, 0]
+    assert runs["wait:1"]["digest"] == runs[""]["digest"]
