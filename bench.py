@@ -262,6 +262,24 @@ def fp32_peak_probe(stream, local, launches=7, outer=12000):
                    "each, CUDA events on the bench stream, median of the launches"}
 
 
+def plain_roofline(prof, pairs, peak):
+    """The plain comparator's embedding kernels against the FP32 CUDA-core
+    peak: per pair within rc the net of Eq. 3-5 forward is d1 + d1 d2 + d2 M
+    = 10,272 multiply-adds (1-32-64-128), its gradient twice that (the
+    backward kernel also recomputes the forward, not counted)."""
+    fwd = 2 * 10272
+    out = {}
+    for k, fl in (("embed_contract_fwd", fwd), ("embed_contract_bwd_forces", 2 * fwd)):
+        ms, cnt = prof.get(k, (0.0, 0))
+        if cnt:
+            a = fl * pairs / (ms / cnt / 1e3) / 1e12
+            out[k] = {"achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                      "ms_per_launch": ms / cnt, "flop_per_pair": fl}
+    out["bound"] = "alu"
+    out["peak_source"] = "FP32 FMA probe measured in this run"
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -601,12 +619,14 @@ def main():
         torch.cuda.synchronize()
         pms = max_over_ranks(pg, p0.elapsed_time(p1))
         pprof = dp.dp_profile_read(hp)
+        ppairs = dp.dp_stats(hp, sp)["pairs_within_rc"]
         dp.dp_system_destroy(sp)
         dp.dp_destroy(hp)
         plain = {"value": world * n * args.plain_steps / (pms / 1e3), "unit": UNIT,
                  "md_steps": args.plain_steps, "ms_per_md_step": pms / args.plain_steps,
                  "phases_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in pprof.items()},
                  "speedup_of_tabulated": (value / world) / (n * args.plain_steps / (pms / 1e3)),
+                 "roofline": plain_roofline(pprof, ppairs, fp32["tflops"]),
                  "start": "initial lattice and velocities (as each timed tabulated system), after one untimed MD step"}
     # e2e: host buffers in, 10 MD steps, host buffers out (pinned host
     # memory, allocated and filled before the timed region)
