@@ -226,24 +226,28 @@ __device__ __forceinline__ int sort_atom(int atom, int jb, const float4* __restr
   const uint32_t* L = nlist + (size_t)atom * cap;
   const unsigned below = (1u << lane) - 1u;
   int np = 0;
-  // three-deep software pipeline over the list: while round r computes, the
-  // offsets of rounds r + 1 and r + 2 and the list entries of round r + 3 are
+  // four-deep software pipeline over the list: while round r computes, the
+  // offsets of rounds r + 1 .. r + 3 and the list entries of round r + 4 are
   // in flight
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   uint32_t e_cur = lane < cnt ? L[lane] : 0u;
   uint32_t e_n1 = 32 + lane < cnt ? L[32 + lane] : 0u;
   uint32_t e_n2 = 64 + lane < cnt ? L[64 + lane] : 0u;
+  uint32_t e_n3 = 96 + lane < cnt ? L[96 + lane] : 0u;
   float4 o_cur = lane < cnt ? off[e_cur >> 5] : z4;
   float4 o_n1 = 32 + lane < cnt ? off[e_n1 >> 5] : z4;
+  float4 o_n2 = 64 + lane < cnt ? off[e_n2 >> 5] : z4;
   for (int b0 = 0; b0 < cnt; b0 += 32) {
     const int k = b0 + lane;
     const uint32_t e = e_cur;
     const float4 oj = o_cur;
     o_cur = o_n1;
-    if (k + 64 < cnt) o_n1 = off[e_n2 >> 5];
+    o_n1 = o_n2;
+    if (k + 96 < cnt) o_n2 = off[e_n3 >> 5];
     e_cur = e_n1;
     e_n1 = e_n2;
-    if (k + 96 < cnt) e_n2 = L[k + 96];
+    e_n2 = e_n3;
+    if (k + 128 < cnt) e_n3 = L[k + 128];
     bool in = false;
     int bin = 0;
     Pair Pk;
