@@ -53,6 +53,12 @@ UNIT = "atom-steps/s"
 # nominal FP32 CUDA-core peak of GB300: 152 SMs x 128 FP32 lanes x 2 flop x
 # 2.070 GHz; the rooflines use the FMA probe measured in the run itself
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# 16-bit tensor-core products per multiply-add of each fitting mode (FP16 and
+# BF16 run at the same kind::f16 rate): FP32 CUDA cores, BF16, three BF16
+# pieces (six products), the FP16 pair (h h, h l, l h)
+FIT_PRODUCTS = {0: 1, 1: 1, 2: 6, 3: 3}
+FIT_MODES = ["fp32-cuda-cores", "bf16-tcgen05", "fp32-accurate-tcgen05",
+             "near-fp32-tcgen05-fp16-pair"]
 
 
 def parse():
@@ -68,7 +74,10 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=5,
                     help="MD steps of the plain untabulated comparator (0: skip)")
     ap.add_argument("--fit-precision", type=int, default=2,
-                    help="0 FP32 CUDA cores, 1 BF16 tensor cores, 2 FP32-accurate tensor cores")
+                    choices=[0, 1, 2, 3],
+                    help="0 FP32 CUDA cores, 1 BF16 tensor cores, 2 FP32-accurate tensor cores "
+                         "(BF16 triples, 6 products), 3 near-FP32 tensor cores (FP16 pairs, "
+                         "3 products)")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving leg (0: skip)")
     ap.add_argument("--serve-capacity-requests", type=int, default=400,
@@ -366,7 +375,7 @@ def water_leg(args, stream, pg, world, fp32_peak):
     units = flops_per_unit(M=100, din=1600)
     ach = {k: units[k][1] * (stats["pairs_within_rc"] if units[k][0] == "pair" else n)
            / (prof[k][0] / max(prof[k][1], 1) / 1e3) / 1e12 for k in units if prof[k][1]}
-    nprod = 6 if args.fit_precision == 2 else 1
+    nprod = FIT_PRODUCTS[args.fit_precision]
     bf16 = measured_peaks().get("bf16_tflops_sustained") or 1700.0
     return {"value": value, "unit": UNIT, "natoms": n, "md_steps": steps, "dt_fs": dt,
             "ns_per_day": value / world / n * dt * 86400 * 1e-6,
@@ -581,17 +590,18 @@ def main():
                         "the interval contraction inside runs on tcgen05"}
     if args.fit_precision > 0 and prof.get("fitting", (0, 0))[1]:
         # the fitting chain against the peak of the arithmetic it computes in:
-        # BF16 products for the BF16 mode; for the FP32-accurate mode, whose
-        # every multiply-add is six BF16 piece products, the BF16 peak / 6
-        nprod = 6 if args.fit_precision == 2 else 1
+        # BF16 products for the BF16 mode; for the split modes, whose every
+        # multiply-add is six BF16 (three FP16) piece products, the 16-bit
+        # peak / 6 (/ 3)
+        nprod = FIT_PRODUCTS[args.fit_precision]
         bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
         fa = phase_achieved("fitting")
         roofline["fitting_chain"] = {
             "bound": "tensor", "achieved": fa, "peak": bf16 / nprod, "unit": "TFLOP/s",
-            "frac": fa / (bf16 / nprod), "executed_bf16_tflops": fa * nprod, "bf16_peak": bf16,
+            "frac": fa / (bf16 / nprod), "executed_16bit_tflops": fa * nprod, "bf16_peak": bf16,
             "ms_per_launch": per_launch["fitting"],
             "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
-                            + (" / 6 piece products" if nprod == 6 else "")
+                            + (" / %d piece products" % nprod if nprod > 1 else "")
                             if peaks else "fallback 1.7 PFLOP/s sustained")}
     roofline["phases_ms_per_launch"] = {k: prof[k][0] / max(prof[k][1], 1) for k in prof}
     roofline["phases_achieved_tflops"] = {
@@ -671,8 +681,7 @@ def main():
                                        "1-32-64-128 / 2048-240-240-240-1, rc 8 A, tabulated "
                                        "h=0.01 s<=2, velocity-Verlet dt 1 fs, rebuild every 10, skin 2 A",
                            "md_steps_per_step": MD_PER_STEP, "natoms": n,
-                           "fit_precision": ["fp32-cuda-cores", "bf16-tcgen05",
-                                             "fp32-accurate-tcgen05"][args.fit_precision], "l2": "inputs larger than L2",
+                           "fit_precision": FIT_MODES[args.fit_precision], "l2": "inputs larger than L2",
                            "ns_per_day": value / world / n * DT_FS * 86400 * 1e-6,
                            "parallelism": f"replicas x{world}",
                            "systems": len(block_segments(args.steps)),

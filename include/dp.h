@@ -57,7 +57,13 @@ typedef struct {
                           (Sec. 3.2-3.4) [1]; 0: plain untabulated FP32 net */
   int fit_precision;   /* fitting-net GEMMs: 0 FP32 CUDA cores [0],
                           1 BF16 tcgen05 tensor cores with FP32 accumulation,
-                          2 FP32-accurate tcgen05 (split operands) */
+                          2 FP32-accurate tcgen05: each operand three BF16
+                          pieces x = h + m + l (six piece products per
+                          multiply-add),
+                          3 near-FP32 tcgen05: each operand an FP16 pair
+                          x s = h + l, s a power of two from a bound of |x|
+                          (three piece products; errors about 1.5x those of
+                          mode 2, stated, not bound to the FP32 bars) */
   double table_step;   /* interval h of the table on s (Sec. 3.2) [0.01] */
   double s_max;        /* table domain is [0, ceil(s_max/h)*h]; [2.0], i.e.
                           r >= 0.5 A for rcs = 0.5 */

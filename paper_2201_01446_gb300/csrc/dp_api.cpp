@@ -695,8 +695,14 @@ dp_status rebuild_batch(dp_handle* h, Work& w, const std::vector<int64_t>& base,
   return fail(h, DP_ERR_CUDA, "neighbor list capacity did not converge");
 }
 
+// 16-bit pieces per fitting operand of each fit_precision: 1 one BF16 piece,
+// 2 three BF16 pieces (FP32-accurate), 3 the FP16 pair (near-FP32)
+static int fit_pieces(int fit_precision) {
+  return fit_precision == 2 ? 3 : fit_precision == 3 ? 2 : 1;
+}
+
 dp_status ensure_fit_scratch_tc(dp_handle* h, int64_t rows_needed) {
-  const int PCN = 3;  // room for three pieces serves both tensor-core modes
+  const int PCN = 3;  // room for three pieces serves every tensor-core mode
   // chunks of 8 x 152 tiles of 128 rows (whole waves on 152 SMs)
   int64_t rows = std::min<int64_t>(std::max<int64_t>(rows_needed, 1), 8 * 152 * 128);
   rows = (rows + 127) / 128 * 128;
@@ -730,10 +736,10 @@ dp_status ensure_fit_scratch_tc(dp_handle* h, int64_t rows_needed) {
 // fitting stage of one centre type: E_i and dE/dT for cnt atoms (idx or all)
 dp_status run_fitting(dp_handle* h, int t, int64_t cnt, const int32_t* idx, const float* T,
                       float* dT, double* e_atom) {
-  if (h->opt.fit_precision == 1 || h->opt.fit_precision == 2) {
+  if (h->opt.fit_precision >= 1) {
     CKS(ensure_fit_scratch_tc(h, cnt));
     if (fit_tc(h->st, cnt, idx, h->nets_tc[t], h->M, h->m_lt, T, dT, e_atom, h->fs_tc,
-               h->opt.fit_precision == 1 ? 1 : 3, P<int32_t>(h->status) + ST_TIMEOUT))
+               fit_pieces(h->opt.fit_precision), P<int32_t>(h->status) + ST_TIMEOUT))
       return fail(h, DP_ERR_UNIMPLEMENTED, "tensor-core fitting cannot run this model shape");
     return DP_OK;
   }
@@ -1070,8 +1076,56 @@ dp_status check_handle(dp_handle* h) {
   return DP_OK;
 }
 
-// BF16 pieces of every fitting weight (W^T and W, pre-tiled B operands of the
-// tensor-core fitting) from the FP32 copies in fit32
+// The FP16-pair scales of a type's fitting net from its FP32 weights (host
+// copy `fb`, the fit32 layout): each a power of two that maps an upper bound
+// of the operand's magnitude to at most 2^14 (the FP16 maximum is 65504).
+// Weights: their largest |w|.  Forward activations: z_0 = tanh is within 1,
+// and a shortcut adds at most 1 per layer.  Gradients: dE/dz of the last
+// layer is w_out; through layer k, |dE/dz_{k-1}| <= max_j sum_n |W_k[j][n]|
+// max|dE/da_k| (+ max|dE/dz_k| with a shortcut), and |dE/da| <= |dE/dz| d_max
+// with d_max >= every |tanh'| (the tanh table's polynomial derivative
+// included).
+static void fit_pair_scales(const dp_handle* h, int t, const float* fb, FitNetTC& nt) {
+  const FitNet& nf = h->nets[t];
+  const auto& o = h->fit_ofs[t];
+  auto scale_for = [](double bound) {
+    if (!(bound > 0.0) || !std::isfinite(bound)) return 1.0f;
+    const int e = (int)std::ceil(std::log2(bound));
+    return (float)std::ldexp(1.0, std::max(-100, std::min(100, 14 - e)));
+  };
+  const double dmax = 1.0625;
+  double bz = 0.0;
+  for (int k = 0; k < nf.nl; ++k) {
+    const int wi = nf.win[k], wo = nf.wout[k];
+    double wmax = 0.0;
+    for (int64_t q = 0; q < (int64_t)wi * wo; ++q)
+      wmax = std::max(wmax, (double)std::fabs(fb[o.W[k] + q]));
+    nt.s_w[k] = nt.s_wt[k] = scale_for(wmax);
+    bz = (k > 0 && nf.shortcut[k] ? bz : 0.0) + 1.0;
+    nt.s_z[k] = scale_for(bz);
+  }
+  const int nl = nf.nl, wl = nf.wout[nl - 1];
+  double bgz = 0.0;
+  for (int c = 0; c < wl; ++c) bgz = std::max(bgz, (double)std::fabs(fb[o.wout + c]));
+  double bgp = bgz * dmax;
+  nt.s_g[nl - 1] = scale_for(bgp);
+  for (int k = nl - 1; k >= 1; --k) {
+    const int wi = nf.win[k], wo = nf.wout[k];
+    double rs = 0.0;
+    for (int j = 0; j < wi; ++j) {
+      double a = 0.0;
+      for (int n = 0; n < wo; ++n) a += std::fabs(fb[o.W[k] + (size_t)j * wo + n]);
+      rs = std::max(rs, a);
+    }
+    bgz = rs * bgp + (nf.shortcut[k] ? bgz : 0.0);
+    bgp = bgz * dmax;
+    nt.s_g[k - 1] = scale_for(bgp);
+  }
+}
+
+// pieces of every fitting weight (W^T and W, pre-tiled B operands of the
+// tensor-core fitting) from the FP32 copies in fit32 (fb: their host copy,
+// for the FP16-pair scales)
 // The plain path's FP32 embedding weights, from the embedding nets' FP64
 // parameters in the model file's layout (per (centre, neighbor) type pair,
 // per layer W then b, contiguous): every sub-array padded to a 16-byte
@@ -1135,18 +1189,23 @@ static dp_status upload_plain_nets(dp_handle* h, const double* emb) {
   return DP_OK;
 }
 
-void tile_fit_weights(dp_handle* h) {
+void tile_fit_weights(dp_handle* h, const float* host_fb) {
   const float* fb = P<float>(h->fit32);
   __nv_bfloat16* hb = P<__nv_bfloat16>(h->fit_bf16);
-  const int pc = h->opt.fit_precision == 1 ? 1 : 3;
+  const int pc = fit_pieces(h->opt.fit_precision);  // fit_precision 0: unused
   for (int t = 0; t < h->ntypes; ++t) {
     const FitNet& nf = h->nets[t];
+    FitNetTC& nt = h->nets_tc[t];
     const auto& o = h->fit_ofs[t];
+    for (int k = 0; k < DP_MAXFIT; ++k) nt.s_wt[k] = nt.s_w[k] = nt.s_z[k] = nt.s_g[k] = 1.0f;
+    if (pc == 2) fit_pair_scales(h, t, host_fb, nt);
     for (int k = 0; k < nf.nl; ++k)
       if (nf.wout[k] % 16 == 0 && nf.win[k] % 16 == 0) {
         // W^T (N = wout, K = win), W (N = win, K = wout)
-        launch_tile_operand(h->st, nf.wout[k], nf.win[k], pc, fb + o.WT[k], hb + 3 * o.WT[k]);
-        launch_tile_operand(h->st, nf.win[k], nf.wout[k], pc, fb + o.W[k], hb + 3 * o.W[k]);
+        launch_tile_operand(h->st, nf.wout[k], nf.win[k], pc, nt.s_wt[k], fb + o.WT[k],
+                            hb + 3 * o.WT[k]);
+        launch_tile_operand(h->st, nf.win[k], nf.wout[k], pc, nt.s_w[k], fb + o.W[k],
+                            hb + 3 * o.W[k]);
       }
   }
 }
@@ -1226,7 +1285,7 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
       h->opt.rebuild_every < 1)
     return bail(DP_ERR_ARG);
   if (h->opt.tabulated < 0 || h->opt.tabulated > 1 || h->opt.fit_precision < 0 ||
-      h->opt.fit_precision > 2 || (h->opt.embed_precision != 0 && h->opt.embed_precision != 2) ||
+      h->opt.fit_precision > 3 || (h->opt.embed_precision != 0 && h->opt.embed_precision != 2) ||
       h->opt.tanh_table < 0 || h->opt.tanh_table > 1 || h->opt.md_graphs < 0 ||
       h->opt.md_graphs > 1)
     return bail(DP_ERR_UNIMPLEMENTED);
@@ -1381,7 +1440,7 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
       nt.b_out = nf.b_out;
       nt.tanh_tab = nf.tanh_tab;
     }
-    tile_fit_weights(h);
+    tile_fit_weights(h, fit.data());
   }
   // FP32 embedding weights (and transposes) for the plain untabulated path
   if (m.n_emb == 3 && m.emb_w[0] <= 32) {
@@ -1879,7 +1938,7 @@ dp_status dp_set_params(dp_handle* h, const double* fit, const double* table) {
     CK(cudaMemcpyAsync(h->fit32.p, fb.data(), sizeof(float) * fb.size(), cudaMemcpyHostToDevice,
                        h->st),
        "parameter upload");
-    tile_fit_weights(h);
+    tile_fit_weights(h, fb.data());
     CK(cudaStreamSynchronize(h->st), "parameter upload");
   }
   if (table && !h->opt.tabulated) {

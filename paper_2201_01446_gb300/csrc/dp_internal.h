@@ -209,17 +209,22 @@ int fit_simt(cudaStream_t st, int64_t n, const int32_t* idx, const FitNet& net, 
 // floats of fg->part that fit_simt needs for a net and chunk size
 int64_t fit_grad_part_floats(const FitNet& net, int din, int64_t rows);
 
-// Tensor-core (tcgen05, BF16 operands, FP32 accumulate) fitting stage.  Each
-// BF16 operand has 1 piece (BF16 mode) or 3 pieces x = h + m + l (FP32-
-// accurate mode: six piece products accumulate in FP32).  Operands are kept
-// pre-tiled: per (row tile, 16-wide K chunk) one contiguous block holding all
-// pieces in the tensor core's no-swizzle K-major layout (weights in tiles of
-// N <= 256 rows, activations in tiles of 128 rows).
+// Tensor-core (tcgen05, 16-bit operands, FP32 accumulate) fitting stage.  Each
+// operand has 1 BF16 piece (BF16 mode), an FP16 pair x s = h + l (FP32-
+// accurate, three piece products; s a power of two from a bound of |x|) or
+// 3 BF16 pieces x = h + m + l (FP32-accurate, six piece products).  Operands
+// are kept pre-tiled: per (row tile, 16-wide K chunk) one contiguous block
+// holding all pieces in the tensor core's no-swizzle K-major layout (weights
+// in tiles of N <= 256 rows, activations in tiles of 128 rows).
 struct FitNetTC {
   int nl;
   int win[DP_MAXFIT], wout[DP_MAXFIT], shortcut[DP_MAXFIT];
   const __nv_bfloat16* WTh[DP_MAXFIT];  // tiled pieces of W^T [wout][win]: forward B operand
   const __nv_bfloat16* Wh[DP_MAXFIT];   // tiled pieces of W [win][wout]: backward B operand
+  // FP16-pair scales (powers of two; 1 in the BF16 modes): of the pieces of
+  // W^T and W of layer k, of the layer outputs z_k (the next layer's A) and
+  // of the gradients dE/d(pre-activation) of layer k (the backward's A)
+  float s_wt[DP_MAXFIT], s_w[DP_MAXFIT], s_z[DP_MAXFIT], s_g[DP_MAXFIT];
   const float* b[DP_MAXFIT];
   const float* w_out;
   float b_out;
@@ -234,8 +239,9 @@ struct FitScratchTC {
   float* gz;                     // [rows][wmax]
   __nv_bfloat16* gph[2];         // tiled pieces of [rows][<= wmax] gradients (A operands)
 };
-// FP32 B [N][K] (K contiguous) -> tiled BF16 pieces; -1 on an unsupported shape
-int launch_tile_operand(cudaStream_t st, int N, int K, int pieces, const float* src,
+// FP32 B [N][K] (K contiguous) -> tiled pieces (pieces 1, 3: BF16; 2: the FP16
+// pair of x scale); -1 on an unsupported shape
+int launch_tile_operand(cudaStream_t st, int N, int K, int pieces, float scale, const float* src,
                         __nv_bfloat16* out);
 int fit_tc(cudaStream_t st, int64_t n, const int32_t* idx, const FitNetTC& net, int M, int m_lt,
            const float* T, float* dT, double* e_atom, const FitScratchTC& s, int pieces,

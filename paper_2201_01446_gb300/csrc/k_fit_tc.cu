@@ -1,8 +1,18 @@
 // Fitting net (Sec. 2.1) and descriptor (Eq. 2) on the 5th-generation tensor
-// cores: tcgen05.mma with BF16 operands in shared memory and the FP32
+// cores: tcgen05.mma with 16-bit operands in shared memory and the FP32
 // accumulator in tensor memory (TMEM), read back with tcgen05.ld for fused
 // epilogues (bias, tanh, shortcut, per-atom energy, gradient of tanh, the
 // descriptor's own backward).
+//
+// Operand pieces (PC): 1 = one BF16 piece; 3 = x = h + m + l in BF16, six
+// piece products; 2 = an FP16 pair x s = h + l (22 significant bits), three
+// piece products (h h, h l, l h), the operand first scaled by a power of two
+// s that puts an upper bound of its magnitude at 2^14, below the FP16
+// maximum (the weights: their largest |w|; activations and gradients: bounds
+// that follow from the net, |tanh| <= 1 and |tanh'| <= 1; the descriptor: a
+// Cauchy-Schwarz bound per row from T).  Elements of at least 2^-14 (scaled)
+// keep 2^-22 relative accuracy; the epilogue multiplies the FP32 accumulator
+// by the inverse scales, exactly.
 //
 // C = A B^T (A: rows x K, B: N x K) in 128-row tiles.  The operands live in
 // global memory PRE-TILED in the tensor core's no-swizzle K-major
@@ -42,23 +52,73 @@ constexpr int kTcThreads = 256;
 // exact hi*hi products in columns 0..255 and the five small piece products
 // in columns 256..511, so the dominant sum sees 6x fewer FP32 accumulations
 template <int PC>
+constexpr int kProds = PC == 1 ? 1 : PC == 2 ? 3 : 6;  // piece products per K chunk
+
+template <int PC>
 struct TcCfg {
   static constexpr int A_BYTES = kBM * kBK * 2;          // one piece of an A block
   static constexpr int B_MAX = 256 * kBK * 2;            // one piece of a B block (NT <= 256)
   static constexpr int STAGE = PC * (A_BYTES + B_MAX);
-  static constexpr int NS = PC == 1 ? 12 : 6;            // pipeline stages
-  static constexpr int NPROD = PC == 1 ? 1 : 6;          // piece products per stage
+  static constexpr int NS = PC == 1 ? 12 : PC == 2 ? 8 : 6;  // pipeline stages
+  static constexpr int NPROD = kProds<PC>;
   static constexpr int TMEM_COLS = PC == 1 ? 256 : 512;
   static constexpr size_t SMEM = 128 + (size_t)NS * STAGE;
 };
 
+template <int PC>
+__device__ __forceinline__ uint32_t idesc_of(int M, int N) {
+  return PC == 2 ? make_idesc_f16(M, N) : make_idesc_bf16(M, N);
+}
+
+// the pieces (of A, of B) that piece product q multiplies
+template <int PC>
+__device__ __forceinline__ void pieces_of(int q, int& pa, int& pb) {
+  if (PC == 2) {  // (h,h) (h,l) (l,h)
+    pa = q == 2 ? 1 : 0;
+    pb = q == 1 ? 1 : 0;
+  } else if (PC == 3) {
+    prod_pieces(q, pa, pb);
+  } else {
+    pa = pb = 0;
+  }
+}
+
+// the 16-bit pieces of 8 values: BF16 (PC 1, 3) of x, or the FP16 pair of x s
+// (PC 2)
+template <int PC>
+__device__ __forceinline__ void pieces8(const float* x, float s, uint16_t (&pv)[3][8]) {
+  if constexpr (PC == 2) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float v = x[j] * s;
+      const __half h = __float2half_rn(v);
+      pv[0][j] = __half_as_ushort(h);
+      pv[1][j] = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+    }
+  } else {
+    __nv_bfloat16 b[3][8];
+    split8<PC>(x, b);
+#pragma unroll
+    for (int p = 0; p < PC; ++p)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) pv[p][j] = __bfloat16_as_ushort(b[p][j]);
+  }
+}
+
+// 2^e as a float, e clamped to the normal range
+__device__ __forceinline__ float pow2f(int e) {
+  e = max(-126, min(127, e));
+  return __int_as_float((e + 127) << 23);
+}
+
 // pieces of 8 consecutive columns n..n+7 (n % 8 == 0) of row `row` into an
-// activation stored pre-tiled for the next GEMM (width W = 16 * nkc)
+// activation stored pre-tiled for the next GEMM (width W = 16 * nkc); s is
+// the FP16 pair's scale (PC 2)
 template <int PC>
 __device__ __forceinline__ void store_tiled(__nv_bfloat16* out, int nkc, int row, int n,
-                                            const float* x) {
-  __align__(16) __nv_bfloat16 pv[3][8];
-  split8<PC>(x, pv);
+                                            const float* x, float s) {
+  __align__(16) uint16_t pv[3][8];
+  pieces8<PC>(x, s, pv);
   const size_t o =
       ((size_t)(row >> 7) * nkc + (n >> 4)) * PC * (kBM * kBK) + tile_off(row & 127, n);
 #pragma unroll
@@ -92,6 +152,8 @@ struct TcEpi {
   const int32_t* tidx;
   int Mw;                  // embedding width M
   const float4* tab;       // tanh table (L0, MID, LAST), NULL: tanhf
+  float acc_scale;         // PC 2: the inverse scales of A and B (L0: of B; A per row)
+  float out_scale;         // PC 2: the scale of the pieces written to out_h
 };
 
 // The tiled kernel (one output tile per CTA) runs layer 0 (K = 2048), its A
@@ -111,6 +173,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ __align__(8) uint64_t s_acc;        // accumulator complete
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
+  __shared__ float s_rinv[kBM];                  // PC 2: inverse scale of each row of D
   volatile int* abort_flag = &s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -168,7 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer: NPROD piece products per stage, the stage committed back
-      const uint32_t idesc = make_idesc_bf16(kBM, ntile);
+      const uint32_t idesc = idesc_of<PC>(kBM, ntile);
       for (int kc = 0; kc < nk; ++kc) {
         const int s = kc % NS, u = kc / NS;
         if (!mbar_wait(&s_full[s], u & 1, abort_flag)) break;
@@ -178,10 +241,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
         for (int q = 0; q < C::NPROD; ++q) {
           int pa = 0, pb = 0;
-          if (PC > 1) prod_pieces(q, pa, pb);
+          pieces_of<PC>(q, pa, pb);
           const uint64_t ad = make_desc(st0 + pa * C::A_BYTES, 128, 256);
           const uint64_t bd = make_desc(st0 + a_bytes + pb * b_piece, 128, 256);
-          // accumulator 0: (h,h); accumulator 1 (PC = 3): the other products
+          // accumulator 0: (h,h); accumulator 1 (PC > 1): the other products
           const uint32_t dst = tmem + (q > 0 ? 256u : 0u);
           const uint32_t acc = (kc > 0 || q > 1) ? 1u : 0u;
           asm volatile(
@@ -217,6 +280,63 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         ta[c][a + 2] = v.z;
         ta[c][a + 3] = v.w;
       }
+    float rs = 1.0f;  // PC 2: the scale of this row of D
+    if (PC == 2) {
+      // |D[b][a]| <= |T_b| |T_a| (Cauchy-Schwarz over the 4 components c):
+      // max_b |T_b|^2 over all M columns, each warp over its 32 rows with
+      // coalesced loads (four rows in flight), times max_{a<16} |T_a|^2
+      const int w4 = warp - 4;
+      float nb = 0.0f;
+      for (int i0 = 0; i0 < 32; i0 += 4) {
+        float mx[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int gi = m0 + w4 * 32 + i0 + u;
+          mx[u] = 0.0f;
+          if (gi < M) {
+            const float* tri = ep.T + (size_t)(ep.tidx ? ep.tidx[gi] : gi) * 4 * ep.Mw;
+            for (int b = 4 * lane; b < ep.Mw; b += 128) {
+              float4 q4[4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                q4[c] = __ldg(reinterpret_cast<const float4*>(tri + c * ep.Mw + b));
+              float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f, n3 = 0.0f;
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                n0 = fmaf(q4[c].x, q4[c].x, n0);
+                n1 = fmaf(q4[c].y, q4[c].y, n1);
+                n2 = fmaf(q4[c].z, q4[c].z, n2);
+                n3 = fmaf(q4[c].w, q4[c].w, n3);
+              }
+              mx[u] = fmaxf(mx[u], fmaxf(fmaxf(n0, n1), fmaxf(n2, n3)));
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+          for (int o = 16; o; o >>= 1) mx[u] = fmaxf(mx[u], __shfl_xor_sync(0xffffffffu, mx[u], o));
+          if (lane == i0 + u) nb = mx[u];
+        }
+      }
+      float na = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 16; ++a) {
+        float q = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) q = fmaf(ta[c][a], ta[c][a], q);
+        na = fmaxf(na, q);
+      }
+      // bound^2 = nb na < 2^(E+1): bound < 2^e with e = ceil((E+1)/2), scale 2^(14-e)
+      const float b2 = nb * na;
+      int e = 0;
+      if (b2 > 0.0f) {
+        const int E = ((__float_as_int(b2) >> 23) & 255) - 127;
+        e = (E + 2) >> 1;
+      }
+      rs = b2 > 0.0f ? pow2f(14 - e) : 1.0f;
+      s_rinv[r] = b2 > 0.0f ? pow2f(e - 14) : 1.0f;
+    }
     float4 tb4[4];
     for (int kc = 0; kc < nk; ++kc) {
       const int s = kc % NS, u = kc / NS;
@@ -242,8 +362,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       unsigned char* sa = base + (size_t)s * C::STAGE;
 #pragma unroll
       for (int kg = 0; kg < 2; ++kg) {
-        __align__(16) __nv_bfloat16 pv[3][8];
-        split8<PC>(x + kg * 8, pv);
+        __align__(16) uint16_t pv[3][8];
+        pieces8<PC>(x + kg * 8, rs, pv);
         const int off = (r >> 3) * 256 + kg * 128 + (r & 7) * 16;
 #pragma unroll
         for (int p = 0; p < PC; ++p)
@@ -284,6 +404,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] += v2[k];
       }
+      if (PC == 2) {
+        const float sc = ep.acc_scale * s_rinv[row_t];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] *= sc;
+      }
       if (!rok) continue;
       const int n = n0 + c0;
       const size_t o = (size_t)row * ep.ldo + n;
@@ -306,8 +431,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int k = 0; k < 16; k += 4)
           *reinterpret_cast<float4*>(ep.out_b + o + k) = *reinterpret_cast<const float4*>(oh + k);
       }
-      store_tiled<PC>(ep.out_h, nkc_out, row, n, oh);
-      store_tiled<PC>(ep.out_h, nkc_out, row, n + 8, oh + 8);
+      store_tiled<PC>(ep.out_h, nkc_out, row, n, oh, ep.out_scale);
+      store_tiled<PC>(ep.out_h, nkc_out, row, n + 8, oh + 8, ep.out_scale);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -446,7 +571,7 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
       for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x) {
         for (int n = 0; n < ntn && ok; ++n, ++ti) {
           const int nt = min(NTW, N - n * NTW);
-          const uint32_t idesc = make_idesc_bf16(kBM, nt);
+          const uint32_t idesc = idesc_of<PC>(kBM, nt);
           const int j = ti & 1;
           if (ti >= 2 && !mbar_wait(&t_empty[j], ((ti >> 1) - 1) & 1, abort_flag)) {
             ok = false;
@@ -463,9 +588,9 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
             const uint32_t a0 = smem_u32(st_smem + (size_t)s * C::STAGE);
             const uint32_t b0 = a0 + st_b;
 #pragma unroll
-            for (int q = 0; q < (PC == 1 ? 1 : 6); ++q) {
+            for (int q = 0; q < kProds<PC>; ++q) {
               int pa = 0, pb = 0;
-              if (PC > 1) prod_pieces(q, pa, pb);
+              pieces_of<PC>(q, pa, pb);
               const uint64_t ad = make_desc(a0 + pa * (kBM * kBK * 2), 128, 256);
               const uint64_t bd = make_desc(b0 + pb * C::B_PIECE, 128, 256);
               const uint32_t dst = tmem + (uint32_t)(j * 256) + (!ONE_ACC && q > 0 ? 128u : 0u);
@@ -571,6 +696,10 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
 #pragma unroll
               for (int k = 0; k < 16; ++k) v[k] += v2[k];
             }
+            if (PC == 2) {
+#pragma unroll
+              for (int k = 0; k < 16; ++k) v[k] *= ep.acc_scale;
+            }
             const int ncol = n * NTW + ch * 16;
             if (rok) {
               if (EPI == TC_DT) {
@@ -646,8 +775,8 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
                     *reinterpret_cast<float4*>(ep.out_b + o + k) = *reinterpret_cast<const float4*>(ob + k);
                 }
                 const int nkc_out = ep.ldo / kBK;
-                store_tiled<PC>(ep.out_h, nkc_out, row, ncol, oh);
-                store_tiled<PC>(ep.out_h, nkc_out, row, ncol + 8, oh + 8);
+                store_tiled<PC>(ep.out_h, nkc_out, row, ncol, oh, ep.out_scale);
+                store_tiled<PC>(ep.out_h, nkc_out, row, ncol + 8, oh + 8, ep.out_scale);
               }
             }
           }
@@ -740,9 +869,10 @@ int tc_gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* B, const 
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-// FP32 B [N][K] -> PC BF16 pieces in the pre-tiled B layout: tile nt (rows
-// 256 nt .., ntile of them) at 256 nt K PC, its K chunk kc at kc PC ntile 16
-__global__ void k_tile_operand(int N, int K, int PC, const float* __restrict__ src,
+// FP32 B [N][K] -> PC pieces in the pre-tiled B layout: tile nt (rows
+// 256 nt .., ntile of them) at 256 nt K PC, its K chunk kc at kc PC ntile 16;
+// PC 2: the FP16 pair of x scale
+__global__ void k_tile_operand(int N, int K, int PC, float scale, const float* __restrict__ src,
                                __nv_bfloat16* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)N * K) return;
@@ -751,6 +881,14 @@ __global__ void k_tile_operand(int N, int K, int PC, const float* __restrict__ s
   const size_t ps = (size_t)ntile * kBK;
   const size_t o = (size_t)nt * 256 * K * PC + (size_t)(k / kBK) * PC * ps + tile_off(r, k);
   const float x = src[i];
+  if (PC == 2) {
+    uint16_t* o16 = reinterpret_cast<uint16_t*>(out);
+    const float v = x * scale;
+    const __half hh = __float2half_rn(v);
+    o16[o] = __half_as_ushort(hh);
+    o16[o + ps] = __half_as_ushort(__float2half_rn(v - __half2float(hh)));
+    return;
+  }
   const __nv_bfloat16 h = __float2bfloat16_rn(x);
   out[o] = h;
   if (PC > 1) {
@@ -763,13 +901,13 @@ __global__ void k_tile_operand(int N, int K, int PC, const float* __restrict__ s
 
 }  // namespace
 
-int launch_tile_operand(cudaStream_t st, int N, int K, int pieces, const float* src,
+int launch_tile_operand(cudaStream_t st, int N, int K, int pieces, float scale, const float* src,
                         __nv_bfloat16* out) {
   if (N <= 0 || K <= 0 || K % kBK || N % 16) return -1;
-  if (pieces != 1 && pieces != 3) return -1;
+  if (pieces < 1 || pieces > 3) return -1;
   const int64_t n = (int64_t)N * K;
   DP_LAUNCHED(1);
-  k_tile_operand<<<(int)((n + 255) / 256), 256, 0, st>>>(N, K, pieces, src, out);
+  k_tile_operand<<<(int)((n + 255) / 256), 256, 0, st>>>(N, K, pieces, scale, src, out);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -807,6 +945,8 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       const float* zb = k == 0 ? nullptr : (k == 1 && !TAB ? s.t[0] : s.z[k - 1]);
       int rc;
       if (k == 0) {
+        ep.acc_scale = 1.0f / net.s_wt[0];
+        ep.out_scale = net.s_z[0];
         ep.out_a = s.t[0];
         ep.out_b = s.z[0];
         ep.out_h = s.zh[0];
@@ -815,6 +955,8 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
         ep.Mw = M;
         rc = tc_gemm<TC_L0, PC, TAB>(st, rows, net.wout[0], din, net.WTh[0], ep);
       } else if (k == nl - 1) {
+        ep.acc_scale = 1.0f / (net.s_z[k - 1] * net.s_wt[k]);
+        ep.out_scale = net.s_g[k];
         ep.R = net.shortcut[k] ? zb : nullptr;
         ep.ldr = net.wout[k - 1];
         ep.wout = net.w_out;
@@ -825,6 +967,8 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
         rc = tc_gemm_p<TC_LAST, PC, TAB>(st, rows, net.wout[k], net.win[k], s.zh[k - 1],
                                          net.WTh[k], ep);
       } else {
+        ep.acc_scale = 1.0f / (net.s_z[k - 1] * net.s_wt[k]);
+        ep.out_scale = net.s_z[k];
         ep.R = net.shortcut[k] ? zb : nullptr;
         ep.ldr = net.wout[k - 1];
         ep.out_a = s.t[k];
@@ -842,6 +986,8 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
     int gi = 0;
     for (int k = nl - 1; k >= 1; --k) {
       TcEpi ep{};
+      ep.acc_scale = 1.0f / (net.s_g[k] * net.s_w[k]);
+      ep.out_scale = net.s_g[k - 1];
       ep.R = net.shortcut[k] ? gz_prev : nullptr;
       ep.ldr = ldgz;
       ep.Tt = s.t[k - 1];
@@ -862,6 +1008,7 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       // with T into dE/dT, both factors of Eq. 2's derivative (the x < 16
       // term completed in the epilogue thread's registers)
       TcEpi ep{};
+      ep.acc_scale = 1.0f / (net.s_g[0] * net.s_w[0]);
       ep.ldo = din;
       ep.err = err;
       ep.T = Tc;
@@ -883,6 +1030,9 @@ int fit_tc(cudaStream_t st, int64_t n, const int32_t* idx, const FitNetTC& net, 
   if (pieces == 1)
     return tab ? fit_tc_impl<1, true>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err)
                : fit_tc_impl<1, false>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err);
+  if (pieces == 2)
+    return tab ? fit_tc_impl<2, true>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err)
+               : fit_tc_impl<2, false>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err);
   if (pieces == 3)
     return tab ? fit_tc_impl<3, true>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err)
                : fit_tc_impl<3, false>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err);
