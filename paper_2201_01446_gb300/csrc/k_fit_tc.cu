@@ -639,29 +639,50 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
           tr = ep.T + trow;
           dtr = ep.dT + trow;
         }
+        // the next row tile's T rows (contiguous without an index list) into
+        // L2 while this one is drained: the epilogue's T loads then hit L2
+        const int mn = mt + gridDim.x;
+        if (tid == 128 && !ep.tidx && mn < mtiles) {
+          const int rows_n = min(kBM, M - mn * kBM);
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(
+                           ep.T + (size_t)mn * kBM * 4 * ep.Mw),
+                       "r"((uint32_t)(rows_n * 4 * ep.Mw * 4))
+                       : "memory");
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
-          for (int a = 0; a < 16; ++a) {
-            tl[c][a] = tr ? __ldg(tr + c * ep.Mw + a) : 0.0f;
-            part[c][a] = 0.0f;
+          for (int a = 0; a < 16; a += 4) {
+            const float4 q = tr ? __ldg(reinterpret_cast<const float4*>(tr + c * ep.Mw + a))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            tl[c][a] = q.x;
+            tl[c][a + 1] = q.y;
+            tl[c][a + 2] = q.z;
+            tl[c][a + 3] = q.w;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) part[c][a + k] = 0.0f;
           }
       }
       bool fail = false;
       for (int n = 0; n < ntn; ++n, ++ti) {
         const int j = ti & 1;
         const int nt = min(NTW, N - n * NTW), nch = nt / 16;
-        // TC_DT: T[c][b] of the row for chunk b - NTW/16 n, two chunks ahead in
-        // a ring of three (the first two issued before the accumulator wait)
-        float tq[3][4];
-        auto load_tb = [&](int slot, int chn) {
+        // TC_DT: T[c][b] of the row for the chunks b - NTW/16 n of this N
+        // tile, four chunks per float4 (b a multiple of 4 and M % 4 == 0: in
+        // the row), one group of four ahead in a ring of two (the first two
+        // issued before the accumulator wait)
+        float4 tq4[2][4];
+        auto load_tg = [&](int slot, int g) {
+          const int chn = hf * CPW + 4 * g;
 #pragma unroll
           for (int c = 0; c < 4; ++c)
-            tq[slot][c] = chn < nch ? __ldg(tr + c * ep.Mw + n * (NTW / 16) + chn) : 0.0f;
+            tq4[slot][c] = chn < nch ? __ldg(reinterpret_cast<const float4*>(
+                                           tr + c * ep.Mw + n * (NTW / 16) + chn))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
         };
         if (EPI == TC_DT && rok) {
-          load_tb(0, hf * CPW);
-          load_tb(1, hf * CPW + 1);
+          load_tg(0, 0);
+          load_tg(1, 1);
         }
         if (!mbar_wait(&t_full[j], (ti >> 1) & 1, abort_flag)) {
           fail = true;
@@ -704,11 +725,13 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
             if (rok) {
               if (EPI == TC_DT) {
                 // v = dE/dD[b][0..15], b = ncol / 16 (Eq. 2)
-                if (cc + 2 < CPW) load_tb((cc + 2) % 3, ch + 2);
+                if ((cc & 3) == 0 && cc >= 4 && cc + 4 < CPW) load_tg(((cc >> 2) + 1) & 1, (cc >> 2) + 1);
                 float tb[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                  tb[c] = tq[cc % 3][c];  // T[c][b], b = ncol / 16
+                  const float4 q = tq4[(cc >> 2) & 1][c];
+                  const int u = cc & 3;
+                  tb[c] = u == 0 ? q.x : u == 1 ? q.y : u == 2 ? q.z : q.w;  // T[c][b], b = ncol / 16
                   float acc = 0.0f;
 #pragma unroll
                   for (int a = 0; a < 16; ++a) acc = fmaf(v[a], tl[c][a], acc);
