@@ -141,7 +141,7 @@ struct TcEpi {
   float bout;
   float* out_a;            // FP32 [rows][ldo]: t, or in the table mode the activation
                            // derivative (L0, MID)
-  float* out_b;            // FP32 [rows][ldo]: z (MID) or gz (BWD)
+  float* out_b;            // FP32 [rows][ldo]: z (MID) or gz (BWD; NULL: not kept)
   __nv_bfloat16* out_h;    // the next A operand, pre-tiled, width ldo
   int ldo;
   double* e_atom;          // TC_LAST: E_i written at idx[row] (or row)
@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
                   for (int k = 0; k < 16; k += 4)
                     *reinterpret_cast<float4*>(ep.out_a + o + k) = *reinterpret_cast<const float4*>(oa + k);
                 }
-                if (EPI == TC_MID || EPI == TC_BWD) {
+                if (EPI == TC_MID || (EPI == TC_BWD && ep.out_b)) {
 #pragma unroll
                   for (int k = 0; k < 16; k += 4)
                     *reinterpret_cast<float4*>(ep.out_b + o + k) = *reinterpret_cast<const float4*>(ob + k);
@@ -1015,7 +1015,9 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.ldr = ldgz;
       ep.Tt = s.t[k - 1];
       ep.ldt = net.win[k];
-      ep.out_b = s.gz;
+      // dE/dz_0 (k = 1) is read by nothing after: only its product with tanh', the
+      // pieces of the dE/dD GEMM's A operand, is kept
+      ep.out_b = k > 1 ? s.gz : nullptr;
       ep.out_h = s.gph[gi ^ 1];
       ep.ldo = net.win[k];
       ep.err = err;
