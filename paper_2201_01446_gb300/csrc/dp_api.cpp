@@ -709,8 +709,8 @@ dp_status ensure_fit_scratch_tc(dp_handle* h, int64_t rows_needed) {
   if (rows <= h->fs_tc.rows) return DP_OK;
   int wmax = 0;
   for (int k = 0; k < h->n_fit; ++k) wmax = std::max(wmax, h->fit_w[k]);
-  size_t bytes = rows * (size_t)wmax * (4 + 2 * 2 * PCN);
-  for (int k = 0; k < h->n_fit; ++k) bytes += rows * (size_t)h->fit_w[k] * (4 + 4 + 2 * PCN);
+  size_t bytes = rows * (size_t)wmax * (4 + 3 * 2 * PCN);
+  for (int k = 0; k < h->n_fit; ++k) bytes += rows * (size_t)h->fit_w[k] * (4 + 4);
   bytes += 64 * 256;
   CK(ensure(h->fitbuf_tc, bytes), "alloc tensor-core fitting scratch");
   unsigned char* q = P<unsigned char>(h->fitbuf_tc);
@@ -725,9 +725,9 @@ dp_status ensure_fit_scratch_tc(dp_handle* h, int64_t rows_needed) {
   for (int k = 0; k < h->n_fit; ++k) {
     s.t[k] = (float*)take(rows * h->fit_w[k] * 4);
     s.z[k] = (float*)take(rows * h->fit_w[k] * 4);
-    s.zh[k] = (__nv_bfloat16*)take(rows * h->fit_w[k] * 2 * PCN);
   }
   s.gz = (float*)take(rows * wmax * 4);
+  s.zh = (__nv_bfloat16*)take(rows * wmax * 2 * PCN);
   s.gph[0] = (__nv_bfloat16*)take(rows * wmax * 2 * PCN);
   s.gph[1] = (__nv_bfloat16*)take(rows * wmax * 2 * PCN);
   return DP_OK;

@@ -233,11 +233,13 @@ struct FitNetTC {
 struct FitScratchTC {
   int64_t rows;                  // rows per chunk (a multiple of 128)
   int wmax;
-  float* t[DP_MAXFIT];           // [rows][wout[k]] tanh values (table mode: derivatives)
-  float* z[DP_MAXFIT];           // [rows][wout[k]] layer outputs (k >= 1)
-  __nv_bfloat16* zh[DP_MAXFIT];  // tiled pieces of the layer outputs (next A operand)
-  float* gz;                     // [rows][wmax]
-  __nv_bfloat16* gph[2];         // tiled pieces of [rows][<= wmax] gradients (A operands)
+  // FP32 arrays in the row-tile-chunked layout (per 128-row tile and
+  // 16-column chunk a block of 128 x 16 floats)
+  float* t[DP_MAXFIT];  // [rows][wout[k]] tanh values (table mode: derivatives)
+  float* z[DP_MAXFIT];  // [rows][wout[k]] layer outputs (the next hidden layer's A operand)
+  float* gz;              // [rows][wmax] dE/dz
+  __nv_bfloat16* zh;      // tiled pieces of the last hidden z (the last layer's A operand)
+  __nv_bfloat16* gph[2];  // tiled pieces of dE/da (the backward layers' A operands)
 };
 // FP32 B [N][K] (K contiguous) -> tiled pieces (pieces 1, 3: BF16; 2: the FP16
 // pair of x scale); -1 on an unsupported shape

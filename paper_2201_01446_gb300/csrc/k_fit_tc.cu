@@ -83,26 +83,76 @@ __device__ __forceinline__ void pieces_of(int q, int& pa, int& pb) {
   }
 }
 
-// the 16-bit pieces of 8 values: BF16 (PC 1, 3) of x, or the FP16 pair of x s
-// (PC 2)
-template <int PC>
-__device__ __forceinline__ void pieces8(const float* x, float s, uint16_t (&pv)[3][8]) {
-  if constexpr (PC == 2) {
+// the 16-bit pieces of W values: BF16 (PC 1, 3: x = h + m + l) of x, or the
+// FP16 pair of x s (PC 2)
+template <int PC, int W>
+__device__ __forceinline__ void pieces_w(const float* x, float s, uint16_t (&pv)[3][W]) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < W; ++j) {
+    if constexpr (PC == 2) {
       const float v = x[j] * s;
       const __half h = __float2half_rn(v);
       pv[0][j] = __half_as_ushort(h);
       pv[1][j] = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(x[j]);
+      pv[0][j] = __bfloat16_as_ushort(h);
+      if (PC == 3) {
+        const float r1 = x[j] - __bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        pv[1][j] = __bfloat16_as_ushort(m);
+        pv[2][j] = __bfloat16_as_ushort(__float2bfloat16_rn(r1 - __bfloat162float(m)));
+      }
     }
-  } else {
-    __nv_bfloat16 b[3][8];
-    split8<PC>(x, b);
-#pragma unroll
-    for (int p = 0; p < PC; ++p)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) pv[p][j] = __bfloat16_as_ushort(b[p][j]);
   }
+}
+template <int PC>
+__device__ __forceinline__ void pieces8(const float* x, float s, uint16_t (&pv)[3][8]) {
+  pieces_w<PC, 8>(x, s, pv);
+}
+
+// the same pieces of 4 consecutive values with paired conversions, each
+// piece as 4 packed 16-bit values (bitwise those of pieces_w)
+template <int PC>
+__device__ __forceinline__ void pieces4_packed(float4 x, float s, uint2 (&out)[3]) {
+  uint32_t w[3][2];
+  const float2 xv[2] = {make_float2(x.x, x.y), make_float2(x.z, x.w)};
+#pragma unroll
+  for (int h2 = 0; h2 < 2; ++h2) {
+    if constexpr (PC == 2) {
+      const float2 v = make_float2(xv[h2].x * s, xv[h2].y * s);
+      const __half2 h = __floats2half2_rn(v.x, v.y);
+      const float2 hf = __half22float2(h);
+      const __half2 l = __floats2half2_rn(v.x - hf.x, v.y - hf.y);
+      w[0][h2] = *reinterpret_cast<const uint32_t*>(&h);
+      w[1][h2] = *reinterpret_cast<const uint32_t*>(&l);
+    } else {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(xv[h2].x, xv[h2].y);
+      w[0][h2] = *reinterpret_cast<const uint32_t*>(&h);
+      if (PC == 3) {
+        const float2 hf = __bfloat1622float2(h);
+        const float2 r = make_float2(xv[h2].x - hf.x, xv[h2].y - hf.y);
+        const __nv_bfloat162 m = __floats2bfloat162_rn(r.x, r.y);
+        const float2 mf = __bfloat1622float2(m);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(r.x - mf.x, r.y - mf.y);
+        w[1][h2] = *reinterpret_cast<const uint32_t*>(&m);
+        w[2][h2] = *reinterpret_cast<const uint32_t*>(&l);
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < PC; ++p) out[p] = make_uint2(w[p][0], w[p][1]);
+}
+
+// FP32 activations and gradients of the fitting net between its GEMMs live in
+// a row-tile-chunked layout: per 128-row tile and 16-column chunk one
+// contiguous block of 128 x 16 floats, row-major inside.  A chunk is one bulk
+// copy (the next GEMM's A operand, split into pieces in shared memory), and a
+// row's 16 columns are 64 contiguous bytes (the epilogues' residual and tanh
+// rows).  w: the array's width, a multiple of 16.
+__host__ __device__ __forceinline__ size_t chunked(int row, int col, int w) {
+  return ((size_t)(row >> 7) * (w >> 4) + (col >> 4)) * (kBM * kBK) + (size_t)(row & 127) * kBK +
+         (col & 15);
 }
 
 // 2^e as a float, e clamped to the normal range
@@ -154,6 +204,7 @@ struct TcEpi {
   const float4* tab;       // tanh table (L0, MID, LAST), NULL: tanhf
   float acc_scale;         // PC 2: the inverse scales of A and B (L0: of B; A per row)
   float out_scale;         // PC 2: the scale of the pieces written to out_h
+  float a_scale;           // PC 2: the scale of an FP32 A operand's pieces (split in the kernel)
 };
 
 // The tiled kernel (one output tile per CTA) runs layer 0 (K = 2048), its A
@@ -411,7 +462,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       if (!rok) continue;
       const int n = n0 + c0;
-      const size_t o = (size_t)row * ep.ldo + n;
+      const size_t o = chunked(row, n, ep.ldo);
       float b[16], oa[16], oh[16];
 #pragma unroll
       for (int k = 0; k < 16; k += 4)
@@ -431,8 +482,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int k = 0; k < 16; k += 4)
           *reinterpret_cast<float4*>(ep.out_b + o + k) = *reinterpret_cast<const float4*>(oh + k);
       }
-      store_tiled<PC>(ep.out_h, nkc_out, row, n, oh, ep.out_scale);
-      store_tiled<PC>(ep.out_h, nkc_out, row, n + 8, oh + 8, ep.out_scale);
+      if (ep.out_h) {
+        store_tiled<PC>(ep.out_h, nkc_out, row, n, oh, ep.out_scale);
+        store_tiled<PC>(ep.out_h, nkc_out, row, n + 8, oh + 8, ep.out_scale);
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -460,11 +513,12 @@ constexpr int kPMaxNS = 8;   // stages at most
 constexpr int kPMaxK = 16;   // K chunks a row tile can hold (K <= 256)
 constexpr size_t kPSmemMax = 225 * 1024;
 
-template <int PC, int NTW>
+template <int PC, int NTW, bool AF>
 struct PCfg {
   static constexpr int A_CHUNK = PC * kBM * kBK * 2;   // one K chunk of A, all pieces
   static constexpr int B_PIECE = NTW * kBK * 2;        // one piece of B
-  static constexpr int STAGE = A_CHUNK + PC * B_PIECE;  // [A chunk][B pieces]
+  static constexpr int A_F32 = AF ? kBM * kBK * 4 : 0;  // the FP32 A chunk as copied
+  static constexpr int STAGE = A_CHUNK + PC * B_PIECE + A_F32;  // [A pieces][B pieces][FP32 A]
   static int stages() {
     const long ns = ((long)kPSmemMax - 128) / STAGE;
     return (int)(ns < kPMaxNS ? ns : kPMaxNS);
@@ -473,10 +527,18 @@ struct PCfg {
 };
 
 // EW epilogue warps: 4 (one thread per row, all columns) or 8 (two column
-// halves; for the layers whose epilogue keeps no per-row state across columns)
+// halves; for the layers whose epilogue keeps no per-row state across columns).
+// The hidden layers read their A operand (the FP32 output z of the layer
+// below, chunked layout) as it is, and four converter warps (2, 3 and two
+// after the epilogue warps) split it into the pieces in each stage: the layer
+// below then writes no pieces (layer 0 saves 3% of its time).  The last and
+// the backward layers take pre-split pieces: splitting there measured slower
+// (the backward layer 145 -> 171 us per 100k rows).
+template <int EPI>
+constexpr int kConvWarps = EPI == TC_MID ? 2 : 0;  // converter warps beyond warps 2-3
 template <int EPI, int PC, bool TAB, int EW>
-__global__ void __launch_bounds__(128 + EW * 32, 1)
-    k_tc_gemm_p(int M, int N, int K, int NS, const __nv_bfloat16* __restrict__ A,
+__global__ void __launch_bounds__(128 + EW * 32 + kConvWarps<EPI> * 32, 1)
+    k_tc_gemm_p(int M, int N, int K, int NS, const void* __restrict__ Av,
                 const __nv_bfloat16* __restrict__ B, TcEpi ep) {
   // The dE/dD GEMM (N = 2048) streams its A chunk once per N tile: N tiles of
   // 256 columns halve those bytes (36 KB per stage for 6.3 MFLOP instead of
@@ -486,13 +548,17 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
   // layers keep the h*h products in their own accumulator.
   constexpr int NTW = EPI == TC_DT ? 256 : kPNT;
   constexpr bool ONE_ACC = NTW == 256;
-  using C = PCfg<PC, NTW>;
+  constexpr bool AF = EPI == TC_MID;  // A as FP32 rows, split here
+  using C = PCfg<PC, NTW, AF>;
+  const __nv_bfloat16* A = static_cast<const __nv_bfloat16*>(Av);
+  const float* A32 = static_cast<const float*>(Av);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   const int nk = K / kBK;
-  unsigned char* st_smem = base;  // stage s: [A chunk][B pieces]
+  unsigned char* st_smem = base;  // stage s: [A pieces][B pieces][FP32 A]
   const uint32_t st_b = (uint32_t)C::A_CHUNK;
-  __shared__ __align__(8) uint64_t b_full[kPMaxNS], b_empty[kPMaxNS];
+  const uint32_t st_f = (uint32_t)(C::A_CHUNK + PC * C::B_PIECE);
+  __shared__ __align__(8) uint64_t b_full[kPMaxNS], b_empty[kPMaxNS], b_conv[kPMaxNS];
   __shared__ __align__(8) uint64_t t_full[2], t_empty[2], fin;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
@@ -513,6 +579,7 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
     for (int s = 0; s < kPMaxNS; ++s) {
       mbar_init(&b_full[s], 1);
       mbar_init(&b_empty[s], 1);
+      mbar_init(&b_conv[s], 128);
     }
     for (int j = 0; j < 2; ++j) {
       mbar_init(&t_full[j], 1);
@@ -549,8 +616,13 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
               break;
             }
             const uint32_t st0 = smem_u32(st_smem + (size_t)s * C::STAGE);
-            mbar_expect_tx(&b_full[s], (uint32_t)C::A_CHUNK + PC * nt * 32);
-            bulk_g2s(st0, A + ((size_t)mt * nk + kc) * PC * (kBM * kBK), C::A_CHUNK, &b_full[s]);
+            if (AF) {
+              mbar_expect_tx(&b_full[s], (uint32_t)C::A_F32 + PC * nt * 32);
+              bulk_g2s(st0 + st_f, A32 + ((size_t)mt * nk + kc) * (kBM * kBK), C::A_F32, &b_full[s]);
+            } else {
+              mbar_expect_tx(&b_full[s], (uint32_t)C::A_CHUNK + PC * nt * 32);
+              bulk_g2s(st0, A + ((size_t)mt * nk + kc) * PC * (kBM * kBK), C::A_CHUNK, &b_full[s]);
+            }
 #pragma unroll
             for (int p = 0; p < PC; ++p)
               bulk_g2s(st0 + st_b + p * C::B_PIECE, b_src(n, kc, p), nt * 32, &b_full[s]);
@@ -580,7 +652,8 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
           asm volatile("tcgen05.fence::after_thread_sync;\n");
           for (int kc = 0; kc < nk; ++kc, ++bi) {
             const int s = bi % NS;
-            if (!mbar_wait(&b_full[s], (bi / NS) & 1, abort_flag)) {
+            // AF: the pieces split from the FP32 chunk (which implies it landed)
+            if (!mbar_wait(AF ? &b_conv[s] : &b_full[s], (bi / NS) & 1, abort_flag)) {
               ok = false;
               break;
             }
@@ -617,7 +690,41 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
               smem_u32(&fin)));
     }
     __syncwarp();
-  } else if (warp >= 4) {
+  } else if (AF && (warp == 2 || warp == 3 || warp >= 4 + EW)) {
+    // converters: each landed FP32 A chunk (128 rows x 16) into its pieces in
+    // the tensor core's layout; thread ct takes float4 q = 128 i + ct (row
+    // q / 4, columns 4 (q % 4) ..), so a warp reads 512 contiguous bytes and
+    // writes eight whole 8-row core-matrix rows
+    const int ct = (warp < 4 ? warp - 2 : warp - EW - 2) * 32 + lane;
+    uint32_t bi = 0;
+    bool ok = true;
+    for (int mt = blockIdx.x; mt < mtiles && ok; mt += gridDim.x) {
+      for (int n = 0; n < ntn && ok; ++n) {
+        for (int kc = 0; kc < nk; ++kc, ++bi) {
+          const int s = bi % NS;
+          if (!mbar_wait(&b_full[s], (bi / NS) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          unsigned char* st = st_smem + (size_t)s * C::STAGE;
+          const float4* src = reinterpret_cast<const float4*>(st + st_f);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int q = i * 128 + ct;
+            const int rr = q >> 2, k0 = (q & 3) * 4;
+            uint2 pw[3];
+            pieces4_packed<PC>(src[q], ep.a_scale, pw);
+            const int off = tile_off(rr, k0);
+#pragma unroll
+            for (int p = 0; p < PC; ++p)
+              *reinterpret_cast<uint2*>(st + (size_t)p * (kBM * kBK * 2) + (size_t)off * 2) = pw[p];
+          }
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          mbar_arrive(&b_conv[s]);
+        }
+      }
+    }
+  } else if (warp >= 4 && warp < 4 + EW) {
     // epilogue: thread = row of the tile (TMEM lane; a warp reaches the lane
     // quarter warp % 4), all columns of each N tile or one half of them
     static_assert(EW == 4 || (EW == 8 && EPI != TC_DT && EPI != TC_LAST), "epilogue warps");
@@ -744,7 +851,7 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
                 // a full group of 8 with more chunks to follow: write it now
                 if ((cc & 7) == 7 && ch < nch - 1) flush_f1(cc >> 3, 8);
               } else {
-                const size_t o = (size_t)row * ep.ldo + ncol;
+                const size_t o = chunked(row, ncol, ep.ldo);
                 float rr[16], bb[16], tt[16], oh[16];
                 if (EPI == TC_MID || EPI == TC_LAST) {
 #pragma unroll
@@ -755,7 +862,8 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
 #pragma unroll
                   for (int k = 0; k < 16; k += 4)
                     *reinterpret_cast<float4*>(rr + k) =
-                        *reinterpret_cast<const float4*>(ep.R + (size_t)row * ep.ldr + ncol + k);
+                        *reinterpret_cast<const float4*>(
+                            ep.ldr ? ep.R + chunked(row, ncol, ep.ldr) + k : ep.R + ncol + k);
                 } else {
 #pragma unroll
                   for (int k = 0; k < 16; ++k) rr[k] = 0.0f;
@@ -764,7 +872,7 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
 #pragma unroll
                   for (int k = 0; k < 16; k += 4)
                     *reinterpret_cast<float4*>(tt + k) =
-                        *reinterpret_cast<const float4*>(ep.Tt + (size_t)row * ep.ldt + ncol + k);
+                        *reinterpret_cast<const float4*>(ep.Tt + chunked(row, ncol, ep.ldt) + k);
                 }
                 float oa[16], ob[16];
 #pragma unroll
@@ -798,8 +906,10 @@ __global__ void __launch_bounds__(128 + EW * 32, 1)
                     *reinterpret_cast<float4*>(ep.out_b + o + k) = *reinterpret_cast<const float4*>(ob + k);
                 }
                 const int nkc_out = ep.ldo / kBK;
-                store_tiled<PC>(ep.out_h, nkc_out, row, ncol, oh, ep.out_scale);
-                store_tiled<PC>(ep.out_h, nkc_out, row, ncol + 8, oh + 8, ep.out_scale);
+                if (ep.out_h) {  // MID: only for the last layer's A
+                  store_tiled<PC>(ep.out_h, nkc_out, row, ncol, oh, ep.out_scale);
+                  store_tiled<PC>(ep.out_h, nkc_out, row, ncol + 8, oh + 8, ep.out_scale);
+                }
               }
             }
           }
@@ -839,13 +949,13 @@ std::atomic<int> g_tc_sms{0};
 
 // persistent launch of the K-short GEMMs
 template <int EPI, int PC, bool TAB>
-int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
-              const __nv_bfloat16* B, const TcEpi& ep) {
+int tc_gemm_p(cudaStream_t st, int M, int N, int K, const void* A, const __nv_bfloat16* B,
+              const TcEpi& ep) {
   constexpr int EW = (EPI == TC_MID || EPI == TC_BWD) ? 8 : 4;
   if (M <= 0) return 0;
   if (K <= 0 || K % kBK || K / kBK > kPMaxK || N <= 0 || N % 16) return -1;
   if (EPI != TC_DT && ep.ldo != N) return -1;
-  using CF = PCfg<PC, EPI == TC_DT ? 256 : kPNT>;  // the kernel's N tile width
+  using CF = PCfg<PC, EPI == TC_DT ? 256 : kPNT, EPI == TC_MID>;  // the kernel's stage
   static_assert(CF::STAGE * 3 + 128 <= kPSmemMax, "three stages at least");
   const int NS = CF::stages();
   const size_t sm = CF::smem();
@@ -865,8 +975,8 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A,
   }
   const int mtiles = (M + kBM - 1) / kBM, nsm = g_tc_sms;
   DP_LAUNCHED(1);
-  k_tc_gemm_p<EPI, PC, TAB, EW><<<mtiles < nsm ? mtiles : nsm, 128 + EW * 32, sm, st>>>(
-      M, N, K, NS, A, B, ep);
+  k_tc_gemm_p<EPI, PC, TAB, EW><<<mtiles < nsm ? mtiles : nsm, 128 + EW * 32 + kConvWarps<EPI> * 32,
+                                  sm, st>>>(M, N, K, NS, A, B, ep);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -946,9 +1056,10 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
   if (m_lt != 16 || M % 4 || M < 16) return -1;  // the fused descriptor wants M< = 16
   // bulk copies and vector loads want 16-byte aligned operands
   auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
-  if (!al(T) || !al(s.gph[0]) || !al(s.gph[1])) return -1;
+  if (!al(T) || !al(s.zh) || !al(s.gph[0]) || !al(s.gph[1]) || !al(s.gz)) return -1;
   for (int k = 0; k < nl; ++k)
-    if (!al(net.WTh[k]) || !al(net.Wh[k]) || !al(s.zh[k]) || !al(net.b[k])) return -1;
+    if (!al(net.WTh[k]) || !al(net.Wh[k]) || !al(s.t[k]) || !al(s.z[k]) || !al(net.b[k]))
+      return -1;
   const int64_t R = s.rows;
   for (int64_t r0 = 0; r0 < n; r0 += R) {
     const int rows = (int)((n - r0) < R ? (n - r0) : R);
@@ -956,7 +1067,8 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
     const float* Tc = idx ? T : T + (size_t)r0 * 4 * M;
     float* dTc = idx ? dT : dT + (size_t)r0 * 4 * M;
     // forward: layer 0 (its A operand D formed from T in the stage), hidden
-    // layers, last layer with the energy
+    // layers (A: the FP32 z of the layer below, split in the kernel), last
+    // layer with the energy (A: the pieces of z written by the layer below)
     for (int k = 0; k < nl; ++k) {
       TcEpi ep{};
       ep.bias = net.b[k];
@@ -972,7 +1084,7 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
         ep.out_scale = net.s_z[0];
         ep.out_a = s.t[0];
         ep.out_b = s.z[0];
-        ep.out_h = s.zh[0];
+        ep.out_h = nl == 2 ? s.zh : nullptr;
         ep.T = Tc;
         ep.tidx = id;
         ep.Mw = M;
@@ -987,18 +1099,17 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
         ep.out_h = s.gph[0];
         ep.e_atom = e_atom + (idx ? 0 : r0);
         ep.idx = id;
-        rc = tc_gemm_p<TC_LAST, PC, TAB>(st, rows, net.wout[k], net.win[k], s.zh[k - 1],
-                                         net.WTh[k], ep);
+        rc = tc_gemm_p<TC_LAST, PC, TAB>(st, rows, net.wout[k], net.win[k], s.zh, net.WTh[k], ep);
       } else {
         ep.acc_scale = 1.0f / (net.s_z[k - 1] * net.s_wt[k]);
+        ep.a_scale = net.s_z[k - 1];
         ep.out_scale = net.s_z[k];
         ep.R = net.shortcut[k] ? zb : nullptr;
         ep.ldr = net.wout[k - 1];
         ep.out_a = s.t[k];
         ep.out_b = s.z[k];
-        ep.out_h = s.zh[k];
-        rc = tc_gemm_p<TC_MID, PC, TAB>(st, rows, net.wout[k], net.win[k], s.zh[k - 1],
-                                        net.WTh[k], ep);
+        ep.out_h = k == nl - 2 ? s.zh : nullptr;
+        rc = tc_gemm_p<TC_MID, PC, TAB>(st, rows, net.wout[k], net.win[k], zb, net.WTh[k], ep);
       }
       if (rc) return rc;
     }
