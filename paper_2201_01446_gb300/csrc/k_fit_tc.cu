@@ -526,8 +526,9 @@ struct PCfg {
   static size_t smem() { return 128 + (size_t)stages() * STAGE; }
 };
 
-// EW epilogue warps: 4 (one thread per row, all columns) or 8 (two column
-// halves; for the layers whose epilogue keeps no per-row state across columns).
+// EW epilogue warps: 4 (one thread per row, all columns: the dE/dD GEMM,
+// whose per-row state spans all columns) or 8 (two column halves; the last
+// layer hands the second half's energy sums to the first).
 // The hidden layers read their A operand (the FP32 output z of the layer
 // below, chunked layout) as it is, and four converter warps (2, 3 and two
 // after the epilogue warps) split it into the pieces in each stage: the layer
@@ -560,6 +561,9 @@ __global__ void __launch_bounds__(128 + EW * 32 + kConvWarps<EPI> * 32, 1)
   const uint32_t st_f = (uint32_t)(C::A_CHUNK + PC * C::B_PIECE);
   __shared__ __align__(8) uint64_t b_full[kPMaxNS], b_empty[kPMaxNS], b_conv[kPMaxNS];
   __shared__ __align__(8) uint64_t t_full[2], t_empty[2], fin;
+  // TC_LAST: the second column half's energy sums, handed to the first half
+  __shared__ __align__(8) uint64_t e_full[2], e_empty[2];
+  __shared__ float s_epart[2][kBM];
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   volatile int* abort_flag = &s_abort;
@@ -584,6 +588,8 @@ __global__ void __launch_bounds__(128 + EW * 32 + kConvWarps<EPI> * 32, 1)
     for (int j = 0; j < 2; ++j) {
       mbar_init(&t_full[j], 1);
       mbar_init(&t_empty[j], EW * 32);
+      mbar_init(&e_full[j], kBM);
+      mbar_init(&e_empty[j], kBM);
     }
     mbar_init(&fin, 1);
     s_abort = 0;
@@ -727,13 +733,13 @@ __global__ void __launch_bounds__(128 + EW * 32 + kConvWarps<EPI> * 32, 1)
   } else if (warp >= 4 && warp < 4 + EW) {
     // epilogue: thread = row of the tile (TMEM lane; a warp reaches the lane
     // quarter warp % 4), all columns of each N tile or one half of them
-    static_assert(EW == 4 || (EW == 8 && EPI != TC_DT && EPI != TC_LAST), "epilogue warps");
+    static_assert(EW == 4 || (EW == 8 && EPI != TC_DT), "epilogue warps");
     constexpr int CPW = (NTW / 16) / (EW / 4);  // 16-column chunks per thread and N tile
     const int r = (tid - 128) & (kBM - 1);
     const int hf = EW == 8 ? (warp - 4) >> 2 : 0;
     const uint32_t tl_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    uint32_t ti = 0;
-    for (int mt = blockIdx.x; mt < mtiles; mt += gridDim.x) {
+    uint32_t ti = 0, it = 0;
+    for (int mt = blockIdx.x; mt < mtiles; mt += gridDim.x, ++it) {
       const int row = mt * kBM + r;
       const bool rok = row < M;
       float e_acc = 0.0f;
@@ -924,8 +930,24 @@ __global__ void __launch_bounds__(128 + EW * 32 + kConvWarps<EPI> * 32, 1)
         }
       }
       if (fail) break;
-      if (EPI == TC_LAST && rok)
+      if (EPI == TC_LAST && EW == 8) {
+        // E_i = (first half's sum + second half's) + b_out; the halves meet
+        // in a double-buffered shared array (bounded waits)
+        const int b = it & 1;
+        const uint32_t ph = (it >> 1) & 1;
+        if (hf == 1) {
+          if (it >= 2 && !mbar_wait(&e_empty[b], ph ^ 1, abort_flag)) break;
+          s_epart[b][r] = e_acc;
+          mbar_arrive(&e_full[b]);
+        } else {
+          if (!mbar_wait(&e_full[b], ph, abort_flag)) break;
+          const float e1 = s_epart[b][r];
+          mbar_arrive(&e_empty[b]);
+          if (rok) ep.e_atom[ep.idx ? ep.idx[row] : row] = (double)(e_acc + e1 + ep.bout);
+        }
+      } else if (EPI == TC_LAST && rok) {
         ep.e_atom[ep.idx ? ep.idx[row] : row] = (double)(e_acc + ep.bout);
+      }
       if (EPI == TC_DT && rok) {
         // second factor (x < 16): complete over all N tiles of the row tile;
         // the first factor of b = x was written by this thread above
@@ -951,7 +973,7 @@ std::atomic<int> g_tc_sms{0};
 template <int EPI, int PC, bool TAB>
 int tc_gemm_p(cudaStream_t st, int M, int N, int K, const void* A, const __nv_bfloat16* B,
               const TcEpi& ep) {
-  constexpr int EW = (EPI == TC_MID || EPI == TC_BWD) ? 8 : 4;
+  constexpr int EW = EPI == TC_DT ? 4 : 8;
   if (M <= 0) return 0;
   if (K <= 0 || K % kBK || K / kBK > kPMaxK || N <= 0 || N % 16) return -1;
   if (EPI != TC_DT && ep.ldo != N) return -1;
