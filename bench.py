@@ -240,8 +240,8 @@ def flops_per_unit(M=128, din=2048, w=240):
 # current build (dram__bytes_read.sum + dram__bytes_write.sum, FCC Cu 256,000
 # atoms, scaled per atom: the traffic grows in proportion to the atoms);
 # profiles/k_tab_tc_traffic_cu256k.md
-TRAFFIC_PER_ATOM = {"embed_contract_fwd": (400928512 + 1348396288) / 256000,
-                    "embed_contract_bwd_forces": (1355102976 + 6626816) / 256000}
+TRAFFIC_PER_ATOM = {"embed_contract_fwd": (400750336 + 1346754560) / 256000,
+                    "embed_contract_bwd_forces": (1354780672 + 6333184) / 256000}
 KERNEL_OF_PHASE = {"embed_contract_fwd": "k_tab_fwd_tc", "embed_contract_bwd_forces": "k_tab_bwd_tc"}
 
 
