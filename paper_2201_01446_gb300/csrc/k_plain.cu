@@ -173,7 +173,10 @@ __device__ __forceinline__ void plain_layer2(const PlainNet& w, int d1, int M, P
 // embedding columns of all 16 pairs (4 x 16 accumulators: one float4 weight
 // load and four broadcast loads of h1 feed 64 multiply-adds).  G goes
 // straight into the lane's 4 x 4 block of T.  The last block of an atom and
-// type is padded with s = 0, R = 0 (contributes nothing).
+// type is padded with s = 0, R = 0 (contributes nothing).  Four CTAs (16
+// warps) per SM at 128 registers, a few spilled, measured 4% faster than three
+// at 167: the kernel is issue-bound and needs the warps to hide the shared-
+// memory broadcasts and tanh.
 constexpr int kPF = 16;      // pairs per block (forward)
 constexpr int kStage = 48;   // staged pairs: < 16 waiting + one list round of 32
 
@@ -187,8 +190,11 @@ struct PlainFwdSmem {        // per warp
 // one block of kPF staged pairs (from the stage front) through the net into
 // the lane's T accumulators
 template <bool VEC1>
-__device__ __forceinline__ void plain_fwd_block(const PlainNet& w, int d1, int M,
+__device__ __forceinline__ void plain_fwd_block(const PlainNet* __restrict__ wp, int d1, int M,
                                                 PlainFwdSmem& S, int lane, float (&tacc)[4][4]) {
+  // the weight pointers are read from the (L1-resident) record where used:
+  // none of them stays live in registers across the atom loop
+  const PlainNet& w = *wp;
   const int d2 = 2 * d1;
   // layer 0: lane k < d1, all pairs
   if (lane < d1) {
@@ -313,7 +319,7 @@ __device__ __forceinline__ void plain_fwd_block(const PlainNet& w, int d1, int M
 }
 
 template <bool VEC1>
-__global__ void __launch_bounds__(kWpb * 32) k_plain_fwd(int64_t n, const float4* __restrict__ off,
+__global__ void __launch_bounds__(kWpb * 32, 4) k_plain_fwd(int64_t n, const float4* __restrict__ off,
                                                          const uint32_t* __restrict__ nlist,
                                                          const int32_t* __restrict__ nn, int cap,
                                                          CellGeom g, EnvParams ep,
@@ -338,7 +344,7 @@ __global__ void __launch_bounds__(kWpb * 32) k_plain_fwd(int64_t n, const float4
 #pragma unroll
       for (int q = 0; q < 4; ++q) tacc[c][q] = 0.0f;
     for (int tj = 0; tj < nt; ++tj) {
-      const PlainNet w = nets[ti * nt + tj];
+      const PlainNet* w = nets + ti * nt + tj;
       int nst = 0;  // staged pairs
       uint32_t e_next = lane < cnt ? L[lane] : 0u;
       for (int b0 = 0; b0 < cnt; b0 += 32) {
