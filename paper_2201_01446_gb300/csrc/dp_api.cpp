@@ -703,10 +703,11 @@ static int fit_pieces(int fit_precision) {
 
 dp_status ensure_fit_scratch_tc(dp_handle* h, int64_t rows_needed) {
   const int PCN = 3;  // room for three pieces serves every tensor-core mode
-  // chunks of 16 x 152 tiles of 128 rows (whole waves on 152 SMs; 8 waves
-  // measured 1.1 ms slower per 4M-atom evaluation: twice the launches, each
-  // with its pipeline fill and a last tile whose epilogue nothing overlaps)
-  int64_t rows = std::min<int64_t>(std::max<int64_t>(rows_needed, 1), 16 * 152 * 128);
+  // chunks of 32 x 152 tiles of 128 rows (whole waves on 152 SMs; 8 and 16
+  // waves measured 1.6 and 0.55 ms slower per 4M-atom evaluation: more
+  // launches, each with its pipeline fill and a last tile whose epilogue
+  // nothing overlaps)
+  int64_t rows = std::min<int64_t>(std::max<int64_t>(rows_needed, 1), 32 * 152 * 128);
   rows = (rows + 127) / 128 * 128;
   if (rows <= h->fs_tc.rows) return DP_OK;
   int wmax = 0;

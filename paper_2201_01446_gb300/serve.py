@@ -71,7 +71,7 @@ def estimate_bytes(natoms: int, cfg: ModelCfg, M: int = 128, fit_widths=(240, 24
     list with skin (1.5 x N_m scaled to rc + skin, + 64 entries), T and dE/dT,
     the sorted pairs of the embedding kernels (N_m + 32 per atom slot, tiles
     of 32 padded per system), bin ends and the per-atom arrays; per fitting
-    row (at most 16 waves of 152 x 128 rows) the FP32 activation and gradient
+    row (at most 32 waves of 152 x 128 rows) the FP32 activation and gradient
     rows and the BF16 pieces of the last and the backward layers' A operands."""
     nm = int(sum(cfg.sel))
     cap = int(1.5 * nm * ((cfg.rc + skin) / cfg.rc) ** 3) + 64
@@ -79,7 +79,7 @@ def estimate_bytes(natoms: int, cfg: ModelCfg, M: int = 128, fit_widths=(240, 24
     per_atom = 4 * cap + 2 * 4 * 4 * M + 400
     per_slot = 16 * ((nm + 32 + 31) // 32 * 32) + 2 * 1024  # sorted pairs, bin ends
     wmax = max(fit_widths)
-    rows = min(-(-max(natoms, 1) // 128) * 128, 16 * 152 * 128)
+    rows = min(-(-max(natoms, 1) // 128) * 128, 32 * 152 * 128)
     per_row = wmax * (4 + 3 * 2 * 3) + sum(w * (4 + 4) for w in fit_widths)
     return int(natoms * per_atom + slots * per_slot + rows * per_row + (8 << 20))
 
