@@ -55,10 +55,20 @@ UNIT = "atom-steps/s"
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # 16-bit tensor-core products per multiply-add of each fitting mode (FP16 and
 # BF16 run at the same kind::f16 rate): FP32 CUDA cores, BF16, three BF16
-# pieces (six products), the FP16 pair (h h, h l, l h)
-FIT_PRODUCTS = {0: 1, 1: 1, 2: 6, 3: 3}
+# pieces (six products), the FP16 pair (h h, h l, l h); mode 4 runs three BF16
+# pieces except the dE/dD GEMM (din x w multiply-adds), an FP16 pair
 FIT_MODES = ["fp32-cuda-cores", "bf16-tcgen05", "fp32-accurate-tcgen05",
-             "near-fp32-tcgen05-fp16-pair"]
+             "near-fp32-tcgen05-fp16-pair", "fp32-accurate-tcgen05-fp16-pair-dE/dD"]
+
+
+def fit_products(mode, din=2048, w=240):
+    """16-bit piece products per multiply-add of the fitting chain, averaged
+    over its GEMMs (forward din*w + 2 w*w + w multiply-adds, backward as many,
+    the dE/dD GEMM din*w of them)."""
+    if mode != 4:
+        return {0: 1, 1: 1, 2: 6, 3: 3}[mode]
+    tot = 2 * (din * w + 2 * w * w + w)
+    return (6 * (tot - din * w) + 3 * din * w) / tot
 
 
 def parse():
@@ -74,10 +84,10 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=5,
                     help="MD steps of the plain untabulated comparator (0: skip)")
     ap.add_argument("--fit-precision", type=int, default=2,
-                    choices=[0, 1, 2, 3],
+                    choices=[0, 1, 2, 3, 4],
                     help="0 FP32 CUDA cores, 1 BF16 tensor cores, 2 FP32-accurate tensor cores "
                          "(BF16 triples, 6 products), 3 near-FP32 tensor cores (FP16 pairs, "
-                         "3 products)")
+                         "3 products), 4 BF16 triples with the dE/dD GEMM in FP16 pairs")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving leg (0: skip)")
     ap.add_argument("--serve-capacity-requests", type=int, default=400,
@@ -375,7 +385,7 @@ def water_leg(args, stream, pg, world, fp32_peak):
     units = flops_per_unit(M=100, din=1600)
     ach = {k: units[k][1] * (stats["pairs_within_rc"] if units[k][0] == "pair" else n)
            / (prof[k][0] / max(prof[k][1], 1) / 1e3) / 1e12 for k in units if prof[k][1]}
-    nprod = FIT_PRODUCTS[args.fit_precision]
+    nprod = fit_products(args.fit_precision, din=1600)
     bf16 = measured_peaks().get("bf16_tflops_sustained") or 1700.0
     return {"value": value, "unit": UNIT, "natoms": n, "md_steps": steps, "dt_fs": dt,
             "ns_per_day": value / world / n * dt * 86400 * 1e-6,
@@ -593,7 +603,7 @@ def main():
         # BF16 products for the BF16 mode; for the split modes, whose every
         # multiply-add is six BF16 (three FP16) piece products, the 16-bit
         # peak / 6 (/ 3)
-        nprod = FIT_PRODUCTS[args.fit_precision]
+        nprod = fit_products(args.fit_precision)
         bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
         fa = phase_achieved("fitting")
         roofline["fitting_chain"] = {
@@ -601,7 +611,7 @@ def main():
             "frac": fa / (bf16 / nprod), "executed_16bit_tflops": fa * nprod, "bf16_peak": bf16,
             "ms_per_launch": per_launch["fitting"],
             "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
-                            + (" / %d piece products" % nprod if nprod > 1 else "")
+                            + (" / %.3g piece products" % nprod if nprod > 1 else "")
                             if peaks else "fallback 1.7 PFLOP/s sustained")}
     roofline["phases_ms_per_launch"] = {k: prof[k][0] / max(prof[k][1], 1) for k in prof}
     roofline["phases_achieved_tflops"] = {

@@ -63,7 +63,9 @@ typedef struct {
                           3 near-FP32 tcgen05: each operand an FP16 pair
                           x s = h + l, s a power of two from a bound of |x|
                           (three piece products; errors about 1.5x those of
-                          mode 2, stated, not bound to the FP32 bars) */
+                          mode 2, stated, not bound to the FP32 bars),
+                          4 mode 2 with the dE/dD GEMM (Eq. 2's input
+                          gradient, forces only) on FP16 pairs */
   double table_step;   /* interval h of the table on s (Sec. 3.2) [0.01] */
   double s_max;        /* table domain is [0, ceil(s_max/h)*h]; [2.0], i.e.
                           r >= 0.5 A for rcs = 0.5 */

@@ -696,9 +696,10 @@ dp_status rebuild_batch(dp_handle* h, Work& w, const std::vector<int64_t>& base,
 }
 
 // 16-bit pieces per fitting operand of each fit_precision: 1 one BF16 piece,
-// 2 three BF16 pieces (FP32-accurate), 3 the FP16 pair (near-FP32)
+// 2 three BF16 pieces (FP32-accurate), 3 the FP16 pair (near-FP32), 4 three
+// BF16 pieces with the dE/dD GEMM's operands an FP16 pair (fit_tc's code 4)
 static int fit_pieces(int fit_precision) {
-  return fit_precision == 2 ? 3 : fit_precision == 3 ? 2 : 1;
+  return fit_precision == 2 ? 3 : fit_precision == 3 ? 2 : fit_precision == 4 ? 4 : 1;
 }
 
 dp_status ensure_fit_scratch_tc(dp_handle* h, int64_t rows_needed) {
@@ -1195,20 +1196,22 @@ static dp_status upload_plain_nets(dp_handle* h, const double* emb) {
 void tile_fit_weights(dp_handle* h, const float* host_fb) {
   const float* fb = P<float>(h->fit32);
   __nv_bfloat16* hb = P<__nv_bfloat16>(h->fit_bf16);
-  const int pc = fit_pieces(h->opt.fit_precision);  // fit_precision 0: unused
+  const int pcode = fit_pieces(h->opt.fit_precision);  // fit_precision 0: unused
+  const int pc = pcode == 4 ? 3 : pcode;
   for (int t = 0; t < h->ntypes; ++t) {
     const FitNet& nf = h->nets[t];
     FitNetTC& nt = h->nets_tc[t];
     const auto& o = h->fit_ofs[t];
     for (int k = 0; k < DP_MAXFIT; ++k) nt.s_wt[k] = nt.s_w[k] = nt.s_z[k] = nt.s_g[k] = 1.0f;
-    if (pc == 2) fit_pair_scales(h, t, host_fb, nt);
+    if (pcode == 2 || pcode == 4) fit_pair_scales(h, t, host_fb, nt);
     for (int k = 0; k < nf.nl; ++k)
       if (nf.wout[k] % 16 == 0 && nf.win[k] % 16 == 0) {
         // W^T (N = wout, K = win), W (N = win, K = wout)
         launch_tile_operand(h->st, nf.wout[k], nf.win[k], pc, nt.s_wt[k], fb + o.WT[k],
                             hb + 3 * o.WT[k]);
-        launch_tile_operand(h->st, nf.win[k], nf.wout[k], pc, nt.s_w[k], fb + o.W[k],
-                            hb + 3 * o.W[k]);
+        // W_0 is the dE/dD GEMM's B operand: an FP16 pair in the mixed mode
+        launch_tile_operand(h->st, nf.win[k], nf.wout[k], pcode == 4 && k == 0 ? 2 : pc,
+                            nt.s_w[k], fb + o.W[k], hb + 3 * o.W[k]);
       }
   }
 }
@@ -1288,7 +1291,7 @@ dp_status dp_create(const char* model_path, int ntypes, const int32_t* type_map,
       h->opt.rebuild_every < 1)
     return bail(DP_ERR_ARG);
   if (h->opt.tabulated < 0 || h->opt.tabulated > 1 || h->opt.fit_precision < 0 ||
-      h->opt.fit_precision > 3 || (h->opt.embed_precision != 0 && h->opt.embed_precision != 2) ||
+      h->opt.fit_precision > 4 || (h->opt.embed_precision != 0 && h->opt.embed_precision != 2) ||
       h->opt.tanh_table < 0 || h->opt.tanh_table > 1 || h->opt.md_graphs < 0 ||
       h->opt.md_graphs > 1)
     return bail(DP_ERR_UNIMPLEMENTED);

@@ -245,6 +245,7 @@ struct FitScratchTC {
 // pair of x scale); -1 on an unsupported shape
 int launch_tile_operand(cudaStream_t st, int N, int K, int pieces, float scale, const float* src,
                         __nv_bfloat16* out);
+// pieces: 1, 2 or 3 for every GEMM; 4: 3, the dE/dD GEMM 2
 int fit_tc(cudaStream_t st, int64_t n, const int32_t* idx, const FitNetTC& net, int M, int m_lt,
            const float* T, float* dT, double* e_atom, const FitScratchTC& s, int pieces,
            int32_t* err);

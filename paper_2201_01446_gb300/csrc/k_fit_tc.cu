@@ -537,7 +537,8 @@ struct PCfg {
 // (the backward layer 145 -> 171 us per 100k rows).
 template <int EPI>
 constexpr int kConvWarps = EPI == TC_MID ? 2 : 0;  // converter warps beyond warps 2-3
-template <int EPI, int PC, bool TAB, int EW>
+// PO: the pieces of the next A operand the epilogue writes (out_h)
+template <int EPI, int PC, bool TAB, int EW, int PO>
 __global__ void __launch_bounds__(128 + EW * 32 + kConvWarps<EPI> * 32, 1)
     k_tc_gemm_p(int M, int N, int K, int NS, const void* __restrict__ Av,
                 const __nv_bfloat16* __restrict__ B, TcEpi ep) {
@@ -913,8 +914,8 @@ __global__ void __launch_bounds__(128 + EW * 32 + kConvWarps<EPI> * 32, 1)
                 }
                 const int nkc_out = ep.ldo / kBK;
                 if (ep.out_h) {  // MID: only for the last layer's A
-                  store_tiled<PC>(ep.out_h, nkc_out, row, ncol, oh, ep.out_scale);
-                  store_tiled<PC>(ep.out_h, nkc_out, row, ncol + 8, oh + 8, ep.out_scale);
+                  store_tiled<PO>(ep.out_h, nkc_out, row, ncol, oh, ep.out_scale);
+                  store_tiled<PO>(ep.out_h, nkc_out, row, ncol + 8, oh + 8, ep.out_scale);
                 }
               }
             }
@@ -969,8 +970,8 @@ __global__ void __launch_bounds__(128 + EW * 32 + kConvWarps<EPI> * 32, 1)
 
 std::atomic<int> g_tc_sms{0};
 
-// persistent launch of the K-short GEMMs
-template <int EPI, int PC, bool TAB>
+// persistent launch of the K-short GEMMs (PO: pieces of the A operand written)
+template <int EPI, int PC, bool TAB, int PO = PC>
 int tc_gemm_p(cudaStream_t st, int M, int N, int K, const void* A, const __nv_bfloat16* B,
               const TcEpi& ep) {
   constexpr int EW = EPI == TC_DT ? 4 : 8;
@@ -983,7 +984,7 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const void* A, const __nv_bf
   const size_t sm = CF::smem();
   static std::atomic<size_t> set{0};  // launches from several host threads
   if (sm > set) {
-    if (cudaFuncSetAttribute(k_tc_gemm_p<EPI, PC, TAB, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_tc_gemm_p<EPI, PC, TAB, EW, PO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm) != cudaSuccess)
       return -3;
     set = sm;
@@ -997,8 +998,9 @@ int tc_gemm_p(cudaStream_t st, int M, int N, int K, const void* A, const __nv_bf
   }
   const int mtiles = (M + kBM - 1) / kBM, nsm = g_tc_sms;
   DP_LAUNCHED(1);
-  k_tc_gemm_p<EPI, PC, TAB, EW><<<mtiles < nsm ? mtiles : nsm, 128 + EW * 32 + kConvWarps<EPI> * 32,
-                                  sm, st>>>(M, N, K, NS, A, B, ep);
+  k_tc_gemm_p<EPI, PC, TAB, EW, PO><<<mtiles < nsm ? mtiles : nsm,
+                                      128 + EW * 32 + kConvWarps<EPI> * 32, sm, st>>>(M, N, K, NS, A,
+                                                                                     B, ep);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -1066,7 +1068,9 @@ int launch_tile_operand(cudaStream_t st, int N, int K, int pieces, float scale, 
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-template <int PC, bool TAB>
+// PDT: the pieces of the dE/dD GEMM's operands (its A written by the last
+// backward layer, its B the tiled W_0); PC for every other GEMM
+template <int PC, bool TAB, int PDT = PC>
 static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const FitNetTC& net, int M,
                        int m_lt, const float* T, float* dT, double* e_atom, const FitScratchTC& s,
                        int32_t* err) {
@@ -1154,8 +1158,11 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.out_h = s.gph[gi ^ 1];
       ep.ldo = net.win[k];
       ep.err = err;
-      const int rc = tc_gemm_p<TC_BWD, PC, TAB>(st, rows, net.win[k], net.wout[k], s.gph[gi],
-                                                net.Wh[k], ep);
+      const int rc =
+          k > 1 ? tc_gemm_p<TC_BWD, PC, TAB>(st, rows, net.win[k], net.wout[k], s.gph[gi],
+                                             net.Wh[k], ep)
+                : tc_gemm_p<TC_BWD, PC, TAB, PDT>(st, rows, net.win[k], net.wout[k], s.gph[gi],
+                                                  net.Wh[k], ep);
       if (rc) return rc;
       gz_prev = s.gz;
       ldgz = net.win[k];
@@ -1173,7 +1180,7 @@ static int fit_tc_impl(cudaStream_t st, int64_t n, const int32_t* idx, const Fit
       ep.dT = dTc;
       ep.tidx = id;
       ep.Mw = M;
-      const int rc = tc_gemm_p<TC_DT, PC, TAB>(st, rows, din, net.wout[0], s.gph[gi], net.Wh[0], ep);
+      const int rc = tc_gemm_p<TC_DT, PDT, TAB>(st, rows, din, net.wout[0], s.gph[gi], net.Wh[0], ep);
       if (rc) return rc;
     }
   }
@@ -1194,5 +1201,8 @@ int fit_tc(cudaStream_t st, int64_t n, const int32_t* idx, const FitNetTC& net, 
   if (pieces == 3)
     return tab ? fit_tc_impl<3, true>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err)
                : fit_tc_impl<3, false>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err);
+  if (pieces == 4)  // three BF16 pieces, the dE/dD GEMM an FP16 pair
+    return tab ? fit_tc_impl<3, true, 2>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err)
+               : fit_tc_impl<3, false, 2>(st, n, idx, net, M, m_lt, T, dT, e_atom, s, err);
   return -1;
 }

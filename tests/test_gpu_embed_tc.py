@@ -76,6 +76,20 @@ def test_stress_parity_tc(dp, cu_tc, ncell, sigma):
             e_rel=5e-6)
 
 
+@pytest.mark.parametrize("ncell,sigma", [(5, 0.05), ((3, 4, 5), 0.15), (7, 0.1)])
+def test_stress_parity_tc_pair_dedd(dp, cu_stress_path, ncell, sigma):
+    # fit_precision 4: the dE/dD GEMM (forces only) on FP16 pairs, the same bars
+    h = _handle(dp, cu_stress_path, fit_precision=4)
+    try:
+        m = oracle.Model(cu_stress_path)
+        tab = oracle.Table(m, TABLE_H, CU_SMAX)
+        x, t, box = inputs.fcc_copper(ncell, sigma=sigma, seed=2)
+        _parity(dp, h, m, tab, x, t, box, stress=True,
+                tag=f"tc-embed fit 4 stress Cu {ncell} {sigma}", e_rel=5e-6)
+    finally:
+        dp.dp_destroy(h)
+
+
 def test_water_two_types_tc(dp, water_model_path):
     # two centre types: type-grouped tiles, each with its own table; M = 100
     # (MMA N = 112, padded columns).  Energy bar as for the tensor-core fitting

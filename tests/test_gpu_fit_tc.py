@@ -9,7 +9,8 @@ BF16 pieces, six piece products) is held to the FP32 path's bars; the
 near-FP32 mode (3: an FP16 pair under a power-of-two scale, three products)
 to bars twice as wide (NEAR), its errors measured 1.2-1.5x those of mode 2:
 the tensor core adds the 22-bit FP16 products of a K = 16 step with fewer
-exact bits than the 16-bit BF16 ones."""
+exact bits than the 16-bit BF16 ones.  Mode 4 (mode 2 with the dE/dD GEMM,
+which feeds only the forces, on FP16 pairs) is held to the FP32 bars."""
 import numpy as np
 import pytest
 
@@ -20,7 +21,7 @@ from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, PARITY_LOG, TABLE_H, force_
 pytestmark = pytest.mark.gpu
 
 # bar factor of each split mode against the FP32 path's bars
-NEAR = {2: 1.0, 3: 2.0}
+NEAR = {2: 1.0, 3: 2.0, 4: 1.0}
 
 
 @pytest.fixture(scope="module")
@@ -93,7 +94,7 @@ def test_tc_mode_forces_vs_oracle(dp, cu_model_path):
     assert de < 1e-3 and fr < 0.3 * frms + 1e-9, (de, fr, frms)
 
 
-@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("prec", [2, 3, 4])
 @pytest.mark.parametrize("std", [0.1, 1.0])
 def test_split_tc_fitting_matches_fp32(dp, model_dir, std, prec):
     # FP32-accurate tensor-core modes (the FP16 pair, three BF16 pieces), the
@@ -125,7 +126,7 @@ def test_split_tc_fitting_matches_fp32(dp, model_dir, std, prec):
     assert ddt < 5e-5 * NEAR[prec], ddt
 
 
-@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("prec", [2, 3, 4])
 def test_split_mode_end_to_end(dp, cu_model_path, cu_stress_path, prec):
     for path, stress in ((cu_model_path, False), (cu_stress_path, True)):
         m = oracle.Model(path)
@@ -151,7 +152,7 @@ def test_split_mode_end_to_end(dp, cu_model_path, cu_stress_path, prec):
             assert fr < max(1e-5, 3e-5 * f * frms), (fr, frms)
 
 
-@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("prec", [2, 3, 4])
 def test_split_mode_water_two_types(dp, water_model_path, prec):
     # two centre types (per-type fitting nets gathered through an index list),
     # M = 100: D has 1600 columns, so the dE/dD GEMM ends in a ragged 64-column
@@ -191,7 +192,7 @@ def test_split_mode_water_two_types(dp, water_model_path, prec):
     assert dv < 1e-4 * f * vmax + 1e-9, (dv, vmax)
 
 
-@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("prec", [2, 3, 4])
 def test_split_mode_wide_fitting_fallback(dp, model_dir, prec):
     # fitting layers 256 wide: K = 256 is the most the persistent kernel
     # takes (16 K chunks); every K-short GEMM streams A with B through its
@@ -220,7 +221,7 @@ def test_split_mode_wide_fitting_fallback(dp, model_dir, prec):
     assert fr < max(1e-5, 3e-5 * NEAR[prec] * frms), (fr, frms)
 
 
-@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("prec", [2, 3, 4])
 @pytest.mark.parametrize("std", [1e-3, 4.0])
 def test_fp16_pair_scales_follow_the_magnitudes(dp, model_dir, std, prec):
     # models whose weights, descriptors and gradients sit far outside FP16's
