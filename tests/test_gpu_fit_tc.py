@@ -256,3 +256,56 @@ def test_fp16_pair_scales_follow_the_magnitudes(dp, model_dir, std, prec):
     scale = float(np.abs(eo).max())
     assert d2 < 1e-4 * scale + 1e-12, (d2, d0, scale)
     assert ddt < 5e-3, ddt
+
+
+@pytest.mark.parametrize("prec", [2, 4])
+@pytest.mark.parametrize("fit_w", [(240, 240), (240, 160, 160, 160), (128, 240, 240)])
+def test_split_mode_fitting_shapes(dp, model_dir, fit_w, prec):
+    # fitting nets other than three 240-wide layers: two layers (layer 0 writes
+    # the last layer's pieces itself), two hidden layers with a width change
+    # (no shortcut there, a shortcut after), a narrow layer 0 (N = 128) below
+    # wider ones; end to end against the oracle, beside the FP32 CUDA-core path
+    # on the same inputs
+    spec = inputs.ModelSpec(1, (32, 64, 128), 16, fit_w)
+    path = str(model_dir / f"cu_fit_{'_'.join(map(str, fit_w))}.model")
+    inputs.write_seeded_model(path, spec, seed=11, std=1.0)
+    m = oracle.Model(path)
+    tab = oracle.Table(m, TABLE_H, CU_SMAX)
+    x, t, box = inputs.fcc_copper((4, 5, 5), sigma=0.1, seed=6)
+    r = oracle.evaluate(m, tab, CU_RC, CU_RCS, CU_SEL, x, t, box)
+    err = {}
+    for pr in (0, prec):
+        o = dp.dp_options_default()
+        o.fit_precision = pr
+        o.embed_precision = 2 if pr else 0
+        h = dp.dp_create(path, 1, CU_RC, CU_RCS, [CU_SEL], options=o, stream=None)
+        try:
+            E, F, V, Ei = dp.dp_compute(h, x, t, box, atom_energy=True)
+        finally:
+            dp.dp_destroy(h)
+        assert np.isfinite(E) and np.all(np.isfinite(F))
+        err[pr] = (abs(E - r["energy"]) / len(x), float(np.abs(Ei - r["atom_energy"]).max()),
+                   rmse(F, r["force"]), float(np.abs(V - r["virial"]).max()))
+    emean = float(np.abs(r["atom_energy"]).mean())
+    emax = float(np.abs(r["atom_energy"]).max())
+    frms = float(np.sqrt((r["force"] ** 2).mean()))
+    vmax = float(np.abs(r["virial"]).max())
+    de, dei, fr, dv = err[prec]
+    PARITY_LOG.append(dict(case=f"tc split mode {prec} Cu {len(x)} fitting {fit_w}",
+                           natoms=len(x), dE_per_atom=de, max_dEi=dei, force_rmse=fr,
+                           force_rms=frms, max_dvirial=dv, mean_abs_Ei=emean,
+                           fp32_path=dict(zip(("dE_per_atom", "max_dEi", "force_rmse",
+                                               "max_dvirial"), err[0]))))
+    # these shapes test the kernels' shape handling (ragged N tiles, K chunk
+    # counts, layers without a shortcut, layer 0 writing the last layer's
+    # pieces): a mis-tiled operand or a skipped term gives errors of the order
+    # of the values.  The accuracy bars proper are those of the configured
+    # shapes; on these nets the split modes measured up to 2.4x the FP32
+    # CUDA-core path's force error and 9x its total-energy error (the tensor
+    # core's accumulation bias, which depends on the net), so the bound is
+    # the stress-model bars or a few times the FP32 path's own error
+    f0 = err[0]
+    assert de < max(1e-6, 5e-6 * emean, 12 * f0[0]), (de, emean, f0)
+    assert dei < max(2e-5 * emax, 3 * f0[1]), (dei, emax, f0)
+    assert fr < max(1e-5, 3e-5 * frms, 3 * f0[2]), (fr, frms, f0)
+    assert dv < max(1e-4 * vmax + 1e-9, 15 * f0[3]), (dv, vmax, f0)
