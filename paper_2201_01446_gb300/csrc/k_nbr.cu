@@ -192,6 +192,20 @@ __global__ void __launch_bounds__(128) k_build_list(
     my_s = cell_start[cid];
     my_e = cell_start[cid + 1];
     my_img = (im[0] + 1) * 9 + (im[1] + 1) * 3 + (im[2] + 1);
+    // the slot's cell is skipped when its nearest point is farther from atom
+    // i than r_list (oi: i's offset from its own cell's centre; along a
+    // shifted axis the cell starts half an edge beyond the centre), with a
+    // margin of 1e-4 on r^2 far above the FP32 error of the offsets: no atom
+    // of a skipped cell could pass the test below, so the list is unchanged
+    const float oia[3] = {oi.x, oi.y, oi.z};
+    float d2 = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (o[a] != 0) {
+        const float d = 0.5f * g.edgef[a] - (float)o[a] * oia[a];
+        if (d > 0.0f) d2 = fmaf(d, d, d2);
+      }
+    if (d2 > hi) my_e = my_s;
   }
   int cnt = 0;
   int cnt_t[DP_MAXT];
