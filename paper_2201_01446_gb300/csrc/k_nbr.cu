@@ -229,6 +229,14 @@ __global__ void __launch_bounds__(128) k_build_list(
     base -= 32;
     advance(slot, base, e);
   }
+  // the current slot's image shift (recomputed when the slot changes)
+  auto shift_of = [&](int sl, float& x0, float& y0, float& z0) {
+    x0 = (sl / 9 - 1) * g.edgef[0];
+    y0 = ((sl / 3) % 3 - 1) * g.edgef[1];
+    z0 = (sl % 3 - 1) * g.edgef[2];
+  };
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  if (slot < 27) shift_of(slot, sx, sy, sz);
   // prefetched candidate of the current round
   int j_c = 0;
   float4 o_c = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -247,8 +255,6 @@ __global__ void __launch_bounds__(128) k_build_list(
       o_n = off[j_n];
     }
     const int img_code = __shfl_sync(0xffffffffu, my_img, slot);
-    const int o0 = slot / 9 - 1, o1 = (slot / 3) % 3 - 1, o2 = slot % 3 - 1;
-    const float sx = o0 * g.edgef[0], sy = o1 * g.edgef[1], sz = o2 * g.edgef[2];
     const int k = base + lane;
     bool in = false, inrc = false;
     const int j = j_c;
@@ -284,6 +290,7 @@ __global__ void __launch_bounds__(128) k_build_list(
     }
     cnt += __popc(m);
     for (int t = 0; t < ntypes; ++t) cnt_t[t] += __popc(__ballot_sync(0xffffffffu, inrc && tj == t));
+    if (nslot != slot && nslot < 27) shift_of(nslot, sx, sy, sz);
     slot = nslot;
     base = nbase;
     e = ne;
