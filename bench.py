@@ -83,7 +83,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=5,
                     help="MD steps of the plain untabulated comparator (0: skip)")
-    ap.add_argument("--fit-precision", type=int, default=2,
+    ap.add_argument("--fit-precision", type=int, default=4,
                     choices=[0, 1, 2, 3, 4],
                     help="0 FP32 CUDA cores, 1 BF16 tensor cores, 2 FP32-accurate tensor cores "
                          "(BF16 triples, 6 products), 3 near-FP32 tensor cores (FP16 pairs, "

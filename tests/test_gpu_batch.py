@@ -19,10 +19,10 @@ def dp():
     return _dp
 
 
-def _tc(dp, path, ntypes=1, rc=CU_RC, rcs=CU_RCS, sel=(CU_SEL,), s_max=CU_SMAX):
+def _tc(dp, path, ntypes=1, rc=CU_RC, rcs=CU_RCS, sel=(CU_SEL,), s_max=CU_SMAX, fit=2):
     o = dp.dp_options_default()
     o.embed_precision = 2
-    o.fit_precision = 2
+    o.fit_precision = fit
     o.s_max = s_max
     return dp.dp_create(path, ntypes, rc, rcs, list(sel), options=o, stream=None)
 
@@ -39,15 +39,16 @@ def _check_alone(dp, h, systems, tag):
     return E, F, V
 
 
-def test_batch_copper_matches_alone_and_oracle(dp, cu_stress_path):
-    h = _tc(dp, cu_stress_path)
+@pytest.mark.parametrize("fit", [2, 4])
+def test_batch_copper_matches_alone_and_oracle(dp, cu_stress_path, fit):
+    h = _tc(dp, cu_stress_path, fit=fit)
     try:
         systems = [inputs.fcc_copper(5, sigma=0.05, seed=1),
                    inputs.fcc_copper((3, 4, 5), sigma=0.15, seed=2),
                    (np.zeros((0, 3)), np.zeros(0, np.int32), np.diag([30.0, 30.0, 30.0])),
                    (np.array([[1.0, 2.0, 3.0]]), np.zeros(1, np.int32), np.diag([40.0] * 3)),
                    inputs.fcc_copper(4, sigma=0.1, seed=3)]
-        E, F, V = _check_alone(dp, h, systems, "Cu 500 + 240 + 0 + 1 + 256")
+        E, F, V = _check_alone(dp, h, systems, f"Cu 500 + 240 + 0 + 1 + 256, fit {fit}")
         assert E[2] == 0.0 and F[2].shape == (0, 3) and not V[2].any()
         # the 240-atom system (ragged tiles, non-cubic box) against the oracle
         m = oracle.Model(cu_stress_path)

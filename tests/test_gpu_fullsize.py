@@ -13,10 +13,11 @@ from conftest import CU_RC, CU_RCS, CU_SEL, CU_SMAX, PARITY_LOG, TABLE_H, force_
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec,embed", [(0, 0), (2, 2)])
+@pytest.mark.parametrize("prec,embed", [(0, 0), (2, 2), (4, 2)])
 def test_fullsize_4m_copper_sampled(cu_model_path, prec, embed):
     # (0, 0): FP32 CUDA cores; (2, 2): FP32-accurate tensor cores for the
-    # fitting net and the tabulated contraction (the bench's modes)
+    # fitting net and the tabulated contraction; (4, 2): the same with the
+    # dE/dD GEMM on FP16 pairs (the bench's modes)
     from paper_2201_01446_gb300 import dp
     x, t, box = inputs.fcc_copper(100, sigma=0.0)
     v = inputs.maxwell_velocities(np.full(len(x), inputs.MASS_CU), 330.0, seed=2)

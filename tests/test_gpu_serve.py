@@ -16,8 +16,10 @@ def test_results_bitwise_alone_and_in_the_mix(cu_model_path, model_dir):
     inputs.write_seeded_model(wpath, inputs.WATER_SPEC, seed=4, std=0.1)
 
     def opts(s_max):
+        # the bench's modes (the split-BF16 mode 2 is covered packed and alone
+        # by the batch tests)
         o = dp.dp_options_default()
-        o.fit_precision = 2
+        o.fit_precision = 4
         o.embed_precision = 2
         o.s_max = s_max
         return o
