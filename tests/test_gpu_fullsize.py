@@ -142,3 +142,56 @@ def test_fullsize_4m_stress_every_atom_benchmarked_mode(cu_stress_path, prec):
     assert fr < max(1e-5, 3e-5 * f * frms), (fr, frms)
     assert frmd < max(1e-5, 3e-5 * f * frms), (frmd, frms)
     assert dv < 1e-4 * f * vmax, (dv, vmax)
+
+
+def test_13m_stress_every_atom_64bit_offsets(cu_stress_path):
+    """The paper's strong-scaling system size, 13.5M copper atoms (150^3 FCC
+    cells), in the bench's modes on the stress model: 10^3 copies of a
+    displaced 15^3-cell box (13,500 atoms), so the oracle's full evaluation of
+    the small box gives the expected E_i and force of every atom.  At this
+    size the neighbor list (13.5M rows of its capacity), the sorted pairs
+    (421,875 tiles x 32 x (N_m + 32) records) and the bin ends run past 2^31
+    elements, which no 4M-atom case reaches: every atom's result checks the
+    64-bit offsets."""
+    from paper_2201_01446_gb300 import dp
+    x0, t0, box0 = inputs.fcc_copper(15, sigma=0.1, seed=43)
+    reps = 10
+    x, t, box = inputs.replicate(x0, t0, box0, reps)
+    n = len(x)
+    assert n == 13_500_000
+    m = oracle.Model(cu_stress_path)
+    tab = oracle.Table(m, TABLE_H, CU_SMAX)
+    r = oracle.evaluate(m, tab, CU_RC, CU_RCS, CU_SEL, x0, t0, box0)
+    ncopy = reps ** 3
+    o = dp.dp_options_default()
+    o.fit_precision = 4
+    o.embed_precision = 2
+    h = dp.dp_create(cu_stress_path, 1, CU_RC, CU_RCS, [CU_SEL], options=o, stream=None)
+    try:
+        E, F, V, Ei = dp.dp_compute(h, x, t, box, atom_energy=True)
+        stats = dp.dp_stats(h)
+    finally:
+        dp.dp_destroy(h)
+    e_ref = r["atom_energy"]
+    f_ref = r["force"]
+    emean = float(np.abs(e_ref).mean())
+    emax = float(np.abs(e_ref).max())
+    frms = float(np.sqrt((f_ref ** 2).mean()))
+    # compare copy by copy (each copy is the small box's atoms in order)
+    Ei = Ei.reshape(ncopy, len(x0))
+    F = F.reshape(ncopy, len(x0), 3)
+    dei = float(np.abs(Ei - e_ref[None, :]).max())
+    fr = float(np.sqrt(((F - f_ref[None, :, :]) ** 2).mean()))
+    de = abs(E - ncopy * r["energy"]) / n
+    dv = float(np.abs(V - ncopy * r["virial"]).max())
+    vmax = float(np.abs(ncopy * r["virial"]).max())
+    PARITY_LOG.append(dict(case="13.5M Cu stress, every atom, fit 4 embed 2", natoms=n, stress=True,
+                           dE_per_atom=de, max_dEi=dei, force_rmse=fr, force_rms=frms,
+                           max_dvirial=dv, max_virial=vmax, mean_abs_Ei=emean,
+                           pairs_within_rc=int(stats["pairs_within_rc"])))
+    assert stats["natoms"] == n and stats["list_capacity"] * n > 2 ** 31
+    # the bars of the 4M-atom stress case
+    assert de < max(1e-6, 5e-6 * emean), (de, emean)
+    assert dei < 2e-5 * emax, (dei, emax)
+    assert fr < max(1e-5, 3e-5 * frms), (fr, frms)
+    assert dv < 1e-4 * vmax, (dv, vmax)
