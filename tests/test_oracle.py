@@ -435,6 +435,29 @@ def test_two_types_water(water_model_path):
         assert abs(fd - r["force"][i, 2]) < 1e-7
 
 
+@pytest.mark.parametrize("tabulated", [False, True])
+def test_two_types_water_virial_and_total_force(water_model_path, tabulated):
+    # the two-type path (per type-pair nets or tables, sel sections [46, 92],
+    # two fitting nets): zero total force, a symmetric virial, and the virial
+    # as the energy's derivative under a diagonal strain of box and positions
+    m = oracle.Model(water_model_path)
+    tab = oracle.Table(m, TABLE_H, 1.25) if tabulated else None
+    x, t, box = inputs.water_like(16, L=7.82, seed=3)  # 48 atoms
+    ev = lambda xx, bb: oracle.evaluate(m, tab, 6.0, 0.5, [46, 92], xx, t, bb)
+    r = ev(x, box)
+    F, V = r["force"], r["virial"]
+    assert np.abs(F.sum(0)).max() < 1e-10 * max(1.0, np.abs(F).max())
+    assert np.abs(V - V.T).max() < 1e-10 * max(1.0, np.abs(V).max())
+    h = 1e-6
+    for a in range(3):
+        S = np.eye(3)
+        S[a, a] += h
+        rp = ev(x @ S.T, box @ S.T)
+        S[a, a] -= 2 * h
+        rm = ev(x @ S.T, box @ S.T)
+        assert abs(-_dE(rp, rm) / (2 * h) - V[a, a]) < 1e-7 * max(1, abs(V[a, a]))
+
+
 def test_sel_overflow_and_table_range_reported(stress):
     m, tab = stress
     x, t, box = inputs.fcc_copper(3, sigma=0.0)
