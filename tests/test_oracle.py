@@ -469,6 +469,30 @@ def test_sel_overflow_and_table_range_reported(stress):
     assert r["status"] == 6 and r["n_range"] >= 2
 
 
+def test_sel_overflow_per_neighbor_type_water(water_model_path):
+    # N_m is sectioned by neighbor type (sel [46, 92]): an atom overflows when
+    # its count of one type passes that type's section.  The counts come from
+    # a minimum-image brute force here (rc = 6 < L / 2), independent of the
+    # oracle's cell list; the oracle must flag exactly the atoms they flag.
+    m = oracle.Model(water_model_path)
+    tab = oracle.Table(m, TABLE_H, 1.25)
+    x, t, box = inputs.water_like(64, L=12.417, seed=3)
+    L = np.diag(box)
+    d = x[None, :, :] - x[:, None, :]
+    d -= L * np.round(d / L)
+    r2 = (d ** 2).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    within = r2 < 6.0 ** 2
+    cnt = np.stack([(within & (t[None, :] == k)).sum(1) for k in (0, 1)], 1)
+    r = oracle.evaluate(m, tab, 6.0, 0.5, [46, 92], x, t, box)
+    assert r["status"] == 0 and cnt[:, 0].max() <= 46 and cnt[:, 1].max() <= 92
+    for k in (0, 1):
+        sel = [46, 92]
+        sel[k] = int(cnt[:, k].max()) - 1
+        r = oracle.evaluate(m, tab, 6.0, 0.5, sel, x, t, box, check=False)
+        assert r["status"] == 5 and r["n_sel"] == int((cnt[:, k] > sel[k]).sum()), (k, r["n_sel"])
+
+
 def test_subset_matches_full(stress):
     m, tab = stress
     x, t, box = inputs.fcc_copper(4, sigma=0.1, seed=12)
