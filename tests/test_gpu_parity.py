@@ -245,6 +245,40 @@ def test_sel_overflow(dp, cu_stress_path):
         dp.dp_destroy(h)
 
 
+@pytest.mark.parametrize("embed", [0, 2])
+def test_sel_sections_at_their_limits_water(dp, water_model_path, embed):
+    # N_m sectioned by neighbor type: with each section exactly at the largest
+    # count of its type (counted here by a minimum-image brute force, rc = 6 <
+    # L / 2) the evaluation runs and matches the oracle with the same sections
+    # (which set N_m); one below in either section is DP_ERR_SEL_OVERFLOW
+    m = oracle.Model(water_model_path)
+    tab = oracle.Table(m, TABLE_H, 1.25)
+    x, t, box = inputs.water_like(64, L=12.417, seed=3)
+    L = np.diag(box)
+    d = x[None, :, :] - x[:, None, :]
+    d -= L * np.round(d / L)
+    r2 = (d ** 2).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    within = r2 < 6.0 ** 2
+    mx = [int((within & (t[None, :] == k)).sum(1).max()) for k in (0, 1)]
+    for sel, ok in [(mx, True), ([mx[0] - 1, 92], False), ([46, mx[1] - 1], False)]:
+        h = _handle(dp, water_model_path, ntypes=2, rc=6.0, rcs=0.5, sel=tuple(sel), s_max=1.25,
+                    embed_precision=embed, fit_precision=0)
+        try:
+            if ok:
+                # (the tensor-core contraction: the water allowance of its
+                # total-energy accumulation bias, as in the other water cases)
+                _parity(dp, h, m, tab, x, t, box, sel=sel, rc=6.0, rcs=0.5, stress=True,
+                        tag=f"water sel at the counts {sel} embed {embed}",
+                        e_rel=1e-5 if embed == 2 else 2e-6)
+            else:
+                with pytest.raises(dp.DPError) as e:
+                    dp.dp_compute(h, x, t, box)
+                assert e.value.code == 5, sel
+        finally:
+            dp.dp_destroy(h)
+
+
 def test_bitwise_reproducible(dp, cu_stress):
     h, _, _ = cu_stress
     x, t, box = inputs.fcc_copper(6, sigma=0.1, seed=4)
