@@ -55,6 +55,42 @@ def test_md_matches_oracle_trajectory(dp, stress):
     assert np.array_equal(th[:, 0], np.arange(1, 13))
 
 
+@pytest.mark.parametrize("fit,embed", [(0, 0), (4, 2)])
+def test_md_two_masses_water_matches_oracle(dp, water_model_path, fit, embed):
+    # two-type water (O 15.999, H 1.008 amu) on the stress model, whose H atoms
+    # feel ~10 eV/A: 12 steps of 0.1 fs (crossing the list rebuild at step 10)
+    # against the oracle's MD.  A mass taken from the wrong type would move an
+    # H atom ~0.1 A off; FP32 forces move it ~1e-6 A
+    m = oracle.Model(water_model_path)
+    tab = oracle.Table(m, TABLE_H, 2.0)
+    x, t, box = inputs.water_like(64, L=12.417, seed=3)
+    masses = [inputs.MASS_O, inputs.MASS_H]
+    v = inputs.maxwell_velocities(np.where(t == 0, inputs.MASS_O, inputs.MASS_H), 30.0, seed=5)
+    o = dp.dp_options_default()
+    o.fit_precision = fit
+    o.embed_precision = embed
+    o.s_max = 2.0
+    h = dp.dp_create(water_model_path, 2, 6.0, 0.5, [46, 92], options=o, stream=None)
+    try:
+        s = dp.dp_system_create(h, x, v, t, masses, box)
+        dp.dp_md_step(h, s, 12, 0.1)
+        xg, vg, fg = dp.dp_system_get(h, s, len(x))
+        dp.dp_system_destroy(s)
+    finally:
+        dp.dp_destroy(h)
+    xo, vo, fo, _ = oracle.md(m, tab, 6.0, 0.5, [46, 92], x, v, t, masses, box, 0.1, 12)
+    L = np.diag(box)
+    dx = (xg - xo) - L * np.round((xg - xo) / L)
+    moved = (xo - x) - L * np.round((xo - x) / L)
+    PARITY_LOG.append(dict(case=f"water MD 12 x 0.1 fs fit {fit} embed {embed}", natoms=len(x),
+                           max_dx=float(np.abs(dx).max()), max_dv=float(np.abs(vg - vo).max()),
+                           force_rmse=rmse(fg, fo), max_moved=float(np.abs(moved).max())))
+    assert np.abs(moved).max() > 1e-2  # the check below resolves the motion
+    assert np.abs(dx).max() < 1e-5
+    assert np.abs(vg - vo).max() < 1e-5
+    assert rmse(fg, fo) < 3e-5 * float(np.sqrt((fo ** 2).mean()))
+
+
 def test_checkpoint_resume_bitwise(dp, stress, tmp_path):
     h, _, _ = stress
     x, v, t, box = _system(5, seed=15)

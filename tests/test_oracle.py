@@ -534,6 +534,37 @@ def test_md_energy_conservation_and_reversibility(stress):
     assert np.abs(x2 - x).max() < 1e-9 and np.abs(v2 + v).max() < 1e-10
 
 
+def test_md_two_masses_water(water_model_path):
+    # velocity-Verlet with a mass per type (O 15.999, H 1.008 amu).  One step
+    # from rest moves every atom by dt^2/2 * F/m (the unit factor from CODATA:
+    # 1 eV/A/amu in A/fs^2), which pins each type's mass in the kicks; then
+    # the energy drift falls as dt^2 and a run reversed returns to its start
+    m = oracle.Model(water_model_path)
+    tab = oracle.Table(m, TABLE_H, 2.0)
+    x, t, box = inputs.water_like(16, L=7.82, seed=3)  # 48 atoms
+    masses = np.array([inputs.MASS_O, inputs.MASS_H])
+    mass = masses[t]
+    kappa = 1.602176634e-19 / 1e-10 / 1.66053906660e-27 * 1e-20  # (eV/A/amu) -> A/fs^2
+    f0 = oracle.evaluate(m, tab, 6.0, 0.5, [46, 92], x, t, box)["force"]
+    dt = 0.05
+    x1, _, _, _ = oracle.md(m, tab, 6.0, 0.5, [46, 92], x, np.zeros_like(x), t, masses, box, dt, 1)
+    L = np.diag(box)
+    dx = (x1 - x) - L * np.round((x1 - x) / L)
+    want = 0.5 * dt * dt * kappa * f0 / mass[:, None]
+    assert np.abs(dx - want).max() < 1e-9 * np.abs(want).max(), np.abs(dx - want).max()
+    v = inputs.maxwell_velocities(mass, 30.0, seed=5)
+    drift = []
+    for dt in [0.1, 0.05, 0.025]:
+        _, _, _, th = oracle.md(m, tab, 6.0, 0.5, [46, 92], x, v, t, masses, box, dt,
+                                int(round(1.0 / dt)))
+        etot = th[:, 0] + th[:, 1]
+        drift.append(np.abs(etot - etot[0]).max())
+    assert 3.5 < drift[0] / drift[1] < 4.5 and 3.5 < drift[1] / drift[2] < 4.5, drift
+    x1, v1, _, _ = oracle.md(m, tab, 6.0, 0.5, [46, 92], x, v, t, masses, box, 0.1, 10)
+    x2, v2, _, _ = oracle.md(m, tab, 6.0, 0.5, [46, 92], x1, -v1, t, masses, box, 0.1, 10)
+    assert np.abs(x2 - x).max() < 1e-9 and np.abs(v2 + v).max() < 1e-10
+
+
 # ------------------------------------------------------------------ Sec. 3.5 tanh table
 def test_tanh_table_pins():
     import math
